@@ -1,0 +1,212 @@
+"""FP64 CPU oracle of the DTSDF render + ICP hot path.
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import or execute anything in this package.
+It shares no code, headers, tables or constants with the CUDA library and never
+imports it; the two meet only through the seeded inputs of ``scenes``.
+
+* ``dtsdf_oracle.c`` (plain C, double precision): preprocessing, block
+  allocation, voxel-projection fusion and ray-cast rendering (Sec. 3, 4, 6).
+* ``icp.py`` (numpy, double precision): pyramid, projective association,
+  point-to-plane residuals and Jacobians in SE(3) and Sim(3), photometric
+  frame-to-keyframe rows, normal equations, Cholesky solve and the exponential
+  map (Sec. 5, 5.2, 5.3, 6).
+
+Floating-point comparisons that decide an integer or a set are taken in single
+precision with the kernel's operation order (which pixel, which block, inlier or
+not); values are computed in double.
+
+Parity status per function is listed in ``PARITY`` below. Every entry is pinned by
+a test under ``tests/`` against closed forms, brute force, library routines or
+invariants; none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+PARITY = {
+    "w_dir": "pinned: closed-form values, partition of unity (tests/test_oracle_weights.py)",
+    "preprocess": "pinned: exact plane normals, filter counts by brute force (tests/test_oracle_fusion.py)",
+    "segment_blocks": "pinned: brute-force slab test (tests/test_oracle_alloc.py)",
+    "integrate": "pinned: per-voxel closed form on planes, running-average identity (tests/test_oracle_fusion.py)",
+    "render": "pinned: analytic plane, sphere bound, thin-sheet lemma (tests/test_oracle_render.py)",
+    "icp": "pinned: finite differences, exact recovery of known SE(3)/Sim(3) (tests/test_oracle_icp.py)",
+    "exp": "pinned: Rodrigues closed form, group identities (tests/test_oracle_icp.py)",
+}
+
+
+def build(force: bool = False) -> str:
+    src = os.path.join(_HERE, "dtsdf_oracle.c")
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(src):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                               "-o", tmp, src, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            P, F, I, D = ctypes.c_void_p, ctypes.c_float, ctypes.c_int, ctypes.c_double
+            L.om_create.argtypes = [F, F, F, F, F, F, F, F, I, I, P, I]
+            L.om_create.restype = P
+            L.om_free.argtypes = [P]
+            L.om_num_bricks.argtypes = [P]
+            L.om_num_bricks.restype = ctypes.c_int64
+            L.om_bricks.argtypes = [P, P]
+            L.om_brick_data.argtypes = [P, I, I, I, I, P]
+            L.om_brick_data.restype = I
+            L.om_preprocess.argtypes = [P, I, I, F, F, F, F, F, F, F, P, P, P, P, P, P, P]
+            L.om_preprocess.restype = I
+            L.om_segment_blocks.argtypes = [P, P, F, P, P, I]
+            L.om_segment_blocks.restype = I
+            L.om_w_dir.argtypes = [D, D]
+            L.om_w_dir.restype = D
+            L.om_integrate.argtypes = [P, P, P, I, I, F, F, F, F, P]
+            L.om_integrate.restype = I
+            L.om_eval.argtypes = [P, P, P, P]
+            L.om_eval.restype = I
+            L.om_render.argtypes = [P, P, I, I, F, F, F, F, P, ctypes.c_long, P, P, P, P]
+            L.om_render.restype = I
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def w_dir(cos_angle: float, theta: float) -> float:
+    """Eq. direction_weight (as read: clamp((theta - acos<n,v>) / (2 theta - pi/2), 0, 1))."""
+    return _load().om_w_dir(float(cos_angle), float(theta))
+
+
+def preprocess(depth: np.ndarray, K, z_min: float, z_max: float, delta_sup: float) -> dict:
+    """Depth outlier filter and cross-product normals (Sec. 6)."""
+    L = _load()
+    d = np.ascontiguousarray(depth, np.float32)
+    H, W = d.shape
+    out = dict(ok=np.zeros((H, W), np.uint8), nok=np.zeros((H, W), np.uint8), z=np.zeros((H, W), np.float32),
+               Pf=np.zeros((H, W, 3), np.float32), nf=np.zeros((H, W, 3), np.float32),
+               Pd=np.zeros((H, W, 3), np.float64), nd=np.zeros((H, W, 3), np.float64))
+    rc = L.om_preprocess(_p(d), W, H, K.fx, K.fy, K.cx, K.cy, z_min, z_max, delta_sup,
+                         _p(out["ok"]), _p(out["nok"]), _p(out["z"]), _p(out["Pf"]), _p(out["nf"]),
+                         _p(out["Pd"]), _p(out["nd"]))
+    assert rc == 0
+    return out
+
+
+def segment_blocks(a, b, block_size: float, origin=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """Blocks crossed by segment a-b (single-precision 3D DDA, Sec. 6 allocation)."""
+    L = _load()
+    A = np.ascontiguousarray(a, np.float32)
+    B = np.ascontiguousarray(b, np.float32)
+    O = np.ascontiguousarray(origin, np.float32)
+    cells = np.zeros((64, 3), np.int32)
+    n = L.om_segment_blocks(_p(A), _p(B), block_size, _p(O), _p(cells), 64)
+    return cells[: min(n, 64)].copy()
+
+
+class Params:
+    """Map parameters (nominal single-precision values, as the library takes them)."""
+
+    def __init__(self, voxel_size=0.005, truncation=0.02, theta=3 * np.pi / 8, w_max=255.0, w_carve=0.1,
+                 z_min=0.1, z_max=6.0, delta_sup=None, carve_radius=2, dense_dim=0, origin=(0.0, 0.0, 0.0),
+                 color=True):
+        self.voxel_size = voxel_size
+        self.truncation = truncation
+        self.theta = theta
+        self.w_max = w_max
+        self.w_carve = w_carve
+        self.z_min = z_min
+        self.z_max = z_max
+        self.delta_sup = truncation / 2 if delta_sup is None else delta_sup
+        self.carve_radius = carve_radius
+        self.dense_dim = dense_dim
+        self.origin = tuple(origin)
+        self.color = color
+
+
+class OracleMap:
+    """Directional TSDF in double precision: (block, D) hash of 8^3 bricks (Sec. 6)."""
+
+    def __init__(self, params: Params):
+        self.params = params
+        L = _load()
+        o = np.asarray(params.origin, np.float32)
+        self._h = L.om_create(params.voxel_size, params.truncation, params.theta, params.w_max, params.w_carve,
+                              params.z_min, params.z_max, params.delta_sup, params.carve_radius,
+                              params.dense_dim, _p(o), int(params.color))
+        if not self._h:
+            raise MemoryError("oracle map creation failed")
+        self._L = L
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            self._L.om_free(self._h)
+            self._h = None
+
+    def integrate(self, depth, rgb, K, T_wc):
+        d = np.ascontiguousarray(depth, np.float32)
+        c = None if rgb is None else np.ascontiguousarray(rgb, np.uint8)
+        T = np.ascontiguousarray(T_wc, np.float64)
+        rc = self._L.om_integrate(self._h, _p(d), _p(c), d.shape[1], d.shape[0], K.fx, K.fy, K.cx, K.cy, _p(T))
+        if rc != 0:
+            raise MemoryError("oracle integrate failed")
+
+    def num_bricks(self) -> int:
+        return int(self._L.om_num_bricks(self._h))
+
+    def bricks(self) -> np.ndarray:
+        """n x 5 int32: bx, by, bz, D, frame of first allocation."""
+        n = self.num_bricks()
+        out = np.zeros((n, 5), np.int32)
+        if n:
+            self._L.om_bricks(self._h, _p(out))
+        return out
+
+    def brick(self, bx, by, bz, D) -> np.ndarray | None:
+        """512 x 6 doubles (sdf, w, r, g, b, wc), voxel index i + 8 j + 64 k."""
+        out = np.zeros((512, 6), np.float64)
+        rc = self._L.om_brick_data(self._h, int(bx), int(by), int(bz), int(D), _p(out))
+        return None if rc != 0 else out
+
+    def eval(self, x, r):
+        info = np.zeros(9, np.float64)
+        ok = self._L.om_eval(self._h, _p(np.ascontiguousarray(x, np.float64)),
+                             _p(np.ascontiguousarray(r, np.float64)), _p(info))
+        return bool(ok), info
+
+    def render(self, K, T_wc, pixels: np.ndarray | None = None):
+        """Ray-cast depth (0 = miss), camera-frame normals, colour, colour validity."""
+        T = np.ascontiguousarray(T_wc, np.float64)
+        if pixels is None:
+            n = K.width * K.height
+            pix = None
+        else:
+            pix = np.ascontiguousarray(pixels, np.int32).reshape(-1, 2)
+            n = pix.shape[0]
+        depth = np.zeros(n, np.float64)
+        normal = np.zeros((n, 3), np.float64)
+        color = np.zeros((n, 3), np.float64)
+        cok = np.zeros(n, np.uint8)
+        self._L.om_render(self._h, _p(T), K.width, K.height, K.fx, K.fy, K.cx, K.cy, _p(pix), n,
+                          _p(depth), _p(normal), _p(color), _p(cok))
+        if pixels is None:
+            return (depth.reshape(K.height, K.width), normal.reshape(K.height, K.width, 3),
+                    color.reshape(K.height, K.width, 3), cok.reshape(K.height, K.width))
+        return depth, normal, color, cok

@@ -1,0 +1,869 @@
+/*
+ * FP64 CPU oracle of DTSDF fusion and rendering (test infrastructure only).
+ *
+ * This file is a plain, slow, obviously correct restatement of what the paper
+ * computes, used only by the tests, the smoke check and the CPU baseline of the
+ * benchmark. It shares no code with the CUDA path. Values are computed in
+ * double precision. Where a floating-point comparison decides an integer or a
+ * set (which pixel a voxel projects to, which blocks a segment crosses, whether
+ * a voxel lies in the truncation band, whether a pixel survives the outlier
+ * filter), the decision is taken in single precision with a fixed operation
+ * order and no contraction, because that is the precision of the kernel being
+ * checked; the values that follow a decision are then computed in double.
+ *
+ * Paper references (Splietker & Behnke, "Rendering the Directional TSDF for
+ * Tracking and Multi-Sensor Registration with Point-To-Plane Scale ICP"):
+ *   Sec. 3  Eq. angular_threshold, Eq. direction_weight, Eq. combined_fusion_weight,
+ *           Eq. color_weight, Eq. point-to-plane, free-space carving, voxel
+ *           projection fusion.
+ *   Sec. 4  ray-cast rendering (regular probing, then refinement of the first
+ *           positive-to-negative transition), Eq. combine_weight,
+ *           Eq. combine_tsdf_weight (no-gradient fallback).
+ *   Sec. 6  voxel-block hashing of 8^3 blocks keyed by (x, y, z, D); depth
+ *           outlier filter (two supporting neighbours) and cross-product normals.
+ *   Sec. 5.1 Eq. ICP_weight, reused as the fusion depth weight.
+ *
+ * Readings of points the paper leaves open (each also listed in the design notes):
+ *   direction weight  w_dir = clamp((theta - acos<n,v>) / (2 theta - pi/2), 0, 1)
+ *   depth weight      w_depth = 1 / (z + 1 - z_min)^2       (the ICP weight)
+ *   angle weight      w_angle = max(0, <n, -r>)             (r: unit pixel ray)
+ *   SDF sign          d = <x - p, n> / tau with n facing the camera (d > 0 in front)
+ *   carving           d_raw > tau and no valid depth within 2 px differs by more
+ *                     than tau: sdf <- running average with value 1, weight w_carve
+ *   presence          a direction counts at x only if all 8 trilinear corners
+ *                     exist and have weight > 0; its gradient (central differences
+ *                     of the trilinear field at +-h) only if the 6 offset samples
+ *                     are present
+ *   render march      samples at t = k * h/2 along the unit ray; the first pair of
+ *                     consecutive defined samples with Phi > 0 >= Phi is the hit,
+ *                     refined by bisection to 1e-10 m
+ *
+ * Build: gcc -O2 -fPIC -shared -fopenmp -ffp-contract=off (see oracle/__init__.py).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ND 6
+#define BLK 8
+#define BVOX 512
+
+/* Direction axis vectors v^D: X+, X-, Y+, Y-, Z+, Z- (Sec. 3). */
+static const double VDIR[ND][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+
+typedef struct {
+  double sdf, w, r, g, b, wc;
+} ovox;
+
+typedef struct {
+  /* parameters: nominal single-precision values, widened for the FP64 path */
+  float hf, tauf, thetaf, wmaxf, wcarvef, zminf, zmaxf, dsupf, costhf, originf[3];
+  double h, tau, theta, wmax, wcarve, zmin, zmax, dsup, origin[3];
+  int carve_r, dense_dim, color;
+  /* hash: (bx, by, bz, D) -> brick index, open addressing, linear probing */
+  uint64_t* keys;
+  int32_t* vals;
+  size_t cap, count;
+  /* bricks */
+  ovox* vox;
+  int32_t* coord; /* 4 per brick: bx, by, bz, D */
+  int32_t* first_frame;
+  size_t nbricks, brick_cap;
+  int frames;
+} omap;
+
+#define EMPTY_KEY 0xFFFFFFFFFFFFFFFFull
+
+static uint64_t pack_key(int bx, int by, int bz, int D) {
+  return ((uint64_t)(uint32_t)(bx + (1 << 19)) & 0xFFFFFull) << 44 |
+         ((uint64_t)(uint32_t)(by + (1 << 19)) & 0xFFFFFull) << 24 |
+         ((uint64_t)(uint32_t)(bz + (1 << 19)) & 0xFFFFFull) << 4 | (uint64_t)D;
+}
+
+static uint64_t mix64(uint64_t x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  x ^= x >> 33;
+  return x;
+}
+
+static int32_t hash_find(const omap* m, int bx, int by, int bz, int D) {
+  uint64_t k = pack_key(bx, by, bz, D);
+  size_t i = mix64(k) & (m->cap - 1);
+  for (;;) {
+    if (m->keys[i] == k) return m->vals[i];
+    if (m->keys[i] == EMPTY_KEY) return -1;
+    i = (i + 1) & (m->cap - 1);
+  }
+}
+
+static void hash_put(omap* m, uint64_t k, int32_t v) {
+  size_t i = mix64(k) & (m->cap - 1);
+  while (m->keys[i] != EMPTY_KEY && m->keys[i] != k) i = (i + 1) & (m->cap - 1);
+  if (m->keys[i] == EMPTY_KEY) m->count++;
+  m->keys[i] = k;
+  m->vals[i] = v;
+}
+
+static int hash_grow(omap* m) {
+  size_t oc = m->cap;
+  uint64_t* ok = m->keys;
+  int32_t* ov = m->vals;
+  m->cap = oc * 2;
+  m->keys = (uint64_t*)malloc(m->cap * sizeof(uint64_t));
+  m->vals = (int32_t*)malloc(m->cap * sizeof(int32_t));
+  if (!m->keys || !m->vals) return -1;
+  memset(m->keys, 0xFF, m->cap * sizeof(uint64_t));
+  m->count = 0;
+  for (size_t i = 0; i < oc; ++i)
+    if (ok[i] != EMPTY_KEY) hash_put(m, ok[i], ov[i]);
+  free(ok);
+  free(ov);
+  return 0;
+}
+
+/* Allocate brick (bx, by, bz, D) if absent. Initial voxel: sdf 1, weights 0, colour 0. */
+static int32_t brick_alloc(omap* m, int bx, int by, int bz, int D, int frame) {
+  int32_t b = hash_find(m, bx, by, bz, D);
+  if (b >= 0) return b;
+  if (m->nbricks == m->brick_cap) {
+    size_t nc = m->brick_cap ? m->brick_cap * 2 : 1024;
+    ovox* nv = (ovox*)realloc(m->vox, nc * BVOX * sizeof(ovox));
+    int32_t* ncd = (int32_t*)realloc(m->coord, nc * 4 * sizeof(int32_t));
+    int32_t* nff = (int32_t*)realloc(m->first_frame, nc * sizeof(int32_t));
+    if (!nv || !ncd || !nff) return -1;
+    m->vox = nv;
+    m->coord = ncd;
+    m->first_frame = nff;
+    m->brick_cap = nc;
+  }
+  if ((m->count + 1) * 2 > m->cap && hash_grow(m) != 0) return -1;
+  b = (int32_t)m->nbricks++;
+  ovox* v = m->vox + (size_t)b * BVOX;
+  for (int i = 0; i < BVOX; ++i) {
+    v[i].sdf = 1.0;
+    v[i].w = v[i].r = v[i].g = v[i].b = v[i].wc = 0.0;
+  }
+  m->coord[4 * b] = bx;
+  m->coord[4 * b + 1] = by;
+  m->coord[4 * b + 2] = bz;
+  m->coord[4 * b + 3] = D;
+  m->first_frame[b] = frame;
+  hash_put(m, pack_key(bx, by, bz, D), b);
+  return b;
+}
+
+omap* om_create(float voxel_size, float truncation, float theta, float w_max, float w_carve, float z_min,
+                float z_max, float delta_sup, int carve_radius, int dense_dim, const float* origin, int color) {
+  omap* m = (omap*)calloc(1, sizeof(omap));
+  if (!m) return NULL;
+  m->hf = voxel_size;
+  m->tauf = truncation;
+  m->thetaf = theta;
+  m->wmaxf = w_max;
+  m->wcarvef = w_carve;
+  m->zminf = z_min;
+  m->zmaxf = z_max;
+  m->dsupf = delta_sup;
+  m->costhf = (float)cos((double)theta);
+  m->h = voxel_size;
+  m->tau = truncation;
+  m->theta = theta;
+  m->wmax = w_max;
+  m->wcarve = w_carve;
+  m->zmin = z_min;
+  m->zmax = z_max;
+  m->dsup = delta_sup;
+  m->carve_r = carve_radius;
+  m->dense_dim = dense_dim;
+  m->color = color;
+  for (int a = 0; a < 3; ++a) {
+    m->originf[a] = origin ? origin[a] : 0.0f;
+    m->origin[a] = m->originf[a];
+  }
+  m->cap = 1 << 12;
+  m->keys = (uint64_t*)malloc(m->cap * sizeof(uint64_t));
+  m->vals = (int32_t*)malloc(m->cap * sizeof(int32_t));
+  memset(m->keys, 0xFF, m->cap * sizeof(uint64_t));
+  if (dense_dim > 0) {
+    /* dense grid: every (block, D) of the dense_dim^3 voxel cube exists from the start */
+    int nb = dense_dim / BLK;
+    for (int D = 0; D < ND; ++D)
+      for (int z = 0; z < nb; ++z)
+        for (int y = 0; y < nb; ++y)
+          for (int x = 0; x < nb; ++x)
+            if (brick_alloc(m, x, y, z, D, 0) < 0) return NULL;
+  }
+  return m;
+}
+
+void om_free(omap* m) {
+  if (!m) return;
+  free(m->keys);
+  free(m->vals);
+  free(m->vox);
+  free(m->coord);
+  free(m->first_frame);
+  free(m);
+}
+
+int64_t om_num_bricks(const omap* m) { return (int64_t)m->nbricks; }
+
+/* Brick list: n x 5 (bx, by, bz, D, first frame). */
+void om_bricks(const omap* m, int32_t* out) {
+  for (size_t b = 0; b < m->nbricks; ++b) {
+    for (int a = 0; a < 4; ++a) out[5 * b + a] = m->coord[4 * b + a];
+    out[5 * b + 4] = m->first_frame[b];
+  }
+}
+
+/* Voxel data of one brick: 512 x 6 doubles (sdf, w, r, g, b, wc), x fastest. Returns -1 if absent. */
+int om_brick_data(const omap* m, int bx, int by, int bz, int D, double* out) {
+  int32_t b = hash_find(m, bx, by, bz, D);
+  if (b < 0) return -1;
+  const ovox* v = m->vox + (size_t)b * BVOX;
+  for (int i = 0; i < BVOX; ++i) {
+    out[6 * i] = v[i].sdf;
+    out[6 * i + 1] = v[i].w;
+    out[6 * i + 2] = v[i].r;
+    out[6 * i + 3] = v[i].g;
+    out[6 * i + 4] = v[i].b;
+    out[6 * i + 5] = v[i].wc;
+  }
+  return 0;
+}
+
+/* ===================================================== preprocessing (A0) == */
+/*
+ * Depth outlier filter (Sec. 6): a pixel with depth in [z_min, z_max] is kept only
+ * if at least two of its 8 neighbours are in range and differ by at most
+ * delta_sup. Normals: cross product of the central differences of the
+ * back-projected neighbours in x and y (Sec. 6), oriented toward the camera;
+ * valid only where the centre and the 4 neighbours survived the filter.
+ * Back-projection follows Eq. reprojection: (z (u - cx)/fx, z (v - cy)/fy, z).
+ */
+typedef struct {
+  int W, H;
+  float fx, fy, cx, cy;
+  float* z;      /* filtered depth */
+  uint8_t* ok;   /* survived filter */
+  uint8_t* nok;  /* has a normal */
+  float* Pf;     /* FP32 camera point (decisions) */
+  float* nf;     /* FP32 camera normal (decisions) */
+  double* Pd;    /* FP64 camera point */
+  double* nd;    /* FP64 camera normal */
+} oframe;
+
+static void frame_free(oframe* f) {
+  free(f->z);
+  free(f->ok);
+  free(f->nok);
+  free(f->Pf);
+  free(f->nf);
+  free(f->Pd);
+  free(f->nd);
+}
+
+static int in_range(float z, float zmin, float zmax) { return z > 0.0f && z >= zmin && z <= zmax; }
+
+static int frame_prepare(oframe* f, const float* depth, int W, int H, float fx, float fy, float cx, float cy,
+                         float zmin, float zmax, float dsup) {
+  size_t n = (size_t)W * H;
+  f->W = W;
+  f->H = H;
+  f->fx = fx;
+  f->fy = fy;
+  f->cx = cx;
+  f->cy = cy;
+  f->z = (float*)calloc(n, sizeof(float));
+  f->ok = (uint8_t*)calloc(n, 1);
+  f->nok = (uint8_t*)calloc(n, 1);
+  f->Pf = (float*)calloc(3 * n, sizeof(float));
+  f->nf = (float*)calloc(3 * n, sizeof(float));
+  f->Pd = (double*)calloc(3 * n, sizeof(double));
+  f->nd = (double*)calloc(3 * n, sizeof(double));
+  if (!f->z || !f->ok || !f->nok || !f->Pf || !f->nf || !f->Pd || !f->nd) return -1;
+  for (int v = 0; v < H; ++v)
+    for (int u = 0; u < W; ++u) {
+      size_t i = (size_t)v * W + u;
+      float z = depth[i];
+      if (!in_range(z, zmin, zmax)) continue;
+      int support = 0;
+      for (int dv = -1; dv <= 1; ++dv)
+        for (int du = -1; du <= 1; ++du) {
+          if (!du && !dv) continue;
+          int uu = u + du, vv = v + dv;
+          if (uu < 0 || vv < 0 || uu >= W || vv >= H) continue;
+          float zn = depth[(size_t)vv * W + uu];
+          if (!in_range(zn, zmin, zmax)) continue;
+          if (fabsf(zn - z) <= dsup) support++;
+        }
+      if (support >= 2) {
+        f->ok[i] = 1;
+        f->z[i] = z;
+        float a = ((float)u - cx) / fx;
+        float b = ((float)v - cy) / fy;
+        f->Pf[3 * i] = z * a;
+        f->Pf[3 * i + 1] = z * b;
+        f->Pf[3 * i + 2] = z;
+        double zd = z;
+        f->Pd[3 * i] = zd * (((double)u - cx) / fx);
+        f->Pd[3 * i + 1] = zd * (((double)v - cy) / fy);
+        f->Pd[3 * i + 2] = zd;
+      }
+    }
+  for (int v = 1; v < H - 1; ++v)
+    for (int u = 1; u < W - 1; ++u) {
+      size_t i = (size_t)v * W + u;
+      size_t il = i - 1, ir = i + 1, iu = i - W, idn = i + W;
+      if (!f->ok[i] || !f->ok[il] || !f->ok[ir] || !f->ok[iu] || !f->ok[idn]) continue;
+      /* FP32 */
+      float dx[3], dy[3], nn[3];
+      for (int a = 0; a < 3; ++a) {
+        dx[a] = f->Pf[3 * ir + a] - f->Pf[3 * il + a];
+        dy[a] = f->Pf[3 * idn + a] - f->Pf[3 * iu + a];
+      }
+      nn[0] = dx[1] * dy[2] - dx[2] * dy[1];
+      nn[1] = dx[2] * dy[0] - dx[0] * dy[2];
+      nn[2] = dx[0] * dy[1] - dx[1] * dy[0];
+      float len = sqrtf((nn[0] * nn[0] + nn[1] * nn[1]) + nn[2] * nn[2]);
+      if (!(len > 0.0f)) continue;
+      for (int a = 0; a < 3; ++a) nn[a] = nn[a] / len;
+      const float* P = f->Pf + 3 * i;
+      if ((nn[0] * P[0] + nn[1] * P[1]) + nn[2] * P[2] > 0.0f)
+        for (int a = 0; a < 3; ++a) nn[a] = -nn[a];
+      for (int a = 0; a < 3; ++a) f->nf[3 * i + a] = nn[a];
+      /* FP64 */
+      double ddx[3], ddy[3], nd[3];
+      for (int a = 0; a < 3; ++a) {
+        ddx[a] = f->Pd[3 * ir + a] - f->Pd[3 * il + a];
+        ddy[a] = f->Pd[3 * idn + a] - f->Pd[3 * iu + a];
+      }
+      nd[0] = ddx[1] * ddy[2] - ddx[2] * ddy[1];
+      nd[1] = ddx[2] * ddy[0] - ddx[0] * ddy[2];
+      nd[2] = ddx[0] * ddy[1] - ddx[1] * ddy[0];
+      double dl = sqrt(nd[0] * nd[0] + nd[1] * nd[1] + nd[2] * nd[2]);
+      for (int a = 0; a < 3; ++a) f->nd[3 * i + a] = nd[a] / dl;
+      /* orient the FP64 normal to the side the FP32 decision chose (toward the camera) */
+      double dot = f->nd[3 * i] * nn[0] + f->nd[3 * i + 1] * nn[1] + f->nd[3 * i + 2] * nn[2];
+      if (dot < 0)
+        for (int a = 0; a < 3; ++a) f->nd[3 * i + a] = -f->nd[3 * i + a];
+      f->nok[i] = 1;
+    }
+  return 0;
+}
+
+/* Expose preprocessing: out_ok, out_nok (u8 [n]); Pf, nf (f32 [3n]); Pd, nd (f64 [3n]); z (f32 [n]). */
+int om_preprocess(const float* depth, int W, int H, float fx, float fy, float cx, float cy, float zmin, float zmax,
+                  float dsup, uint8_t* ok, uint8_t* nok, float* zf, float* Pf, float* nf, double* Pd, double* nd) {
+  oframe f;
+  memset(&f, 0, sizeof(f));
+  if (frame_prepare(&f, depth, W, H, fx, fy, cx, cy, zmin, zmax, dsup) != 0) {
+    frame_free(&f);
+    return -1;
+  }
+  size_t n = (size_t)W * H;
+  if (ok) memcpy(ok, f.ok, n);
+  if (nok) memcpy(nok, f.nok, n);
+  if (zf) memcpy(zf, f.z, n * sizeof(float));
+  if (Pf) memcpy(Pf, f.Pf, 3 * n * sizeof(float));
+  if (nf) memcpy(nf, f.nf, 3 * n * sizeof(float));
+  if (Pd) memcpy(Pd, f.Pd, 3 * n * sizeof(double));
+  if (nd) memcpy(nd, f.nd, 3 * n * sizeof(double));
+  frame_free(&f);
+  return 0;
+}
+
+/* ======================================================== allocation (A1) == */
+/*
+ * Blocks of 8^3 voxels (Sec. 6) are allocated for every (block, D) whose cube
+ * the segment [p - tau r, p + tau r] crosses, for each direction D the pixel's
+ * world normal belongs to (Eq. angular_threshold: <n, v^D> > cos(theta)).
+ * The traversal is a 3D digital differential analyser (Amanatides & Woo) in
+ * block units, single precision, ties broken x before y before z.
+ * Returns the number of cells written to `cells` (x, y, z triples), at most max_cells.
+ */
+int om_segment_blocks(const float* a, const float* b, float block_size, const float* origin, int32_t* cells,
+                      int max_cells) {
+  float A[3], B[3], d[3], tmax[3], tdel[3];
+  int c[3], e[3], st[3];
+  for (int k = 0; k < 3; ++k) {
+    A[k] = (a[k] - origin[k]) / block_size;
+    B[k] = (b[k] - origin[k]) / block_size;
+    d[k] = B[k] - A[k];
+    c[k] = (int)floorf(A[k]);
+    e[k] = (int)floorf(B[k]);
+    if (d[k] > 0.0f) {
+      st[k] = 1;
+      tdel[k] = 1.0f / d[k];
+      tmax[k] = ((float)(c[k] + 1) - A[k]) / d[k];
+    } else if (d[k] < 0.0f) {
+      st[k] = -1;
+      tdel[k] = -1.0f / d[k];
+      tmax[k] = ((float)c[k] - A[k]) / d[k];
+    } else {
+      st[k] = 0;
+      tdel[k] = INFINITY;
+      tmax[k] = INFINITY;
+    }
+  }
+  int n = 0;
+  for (int it = 0; it < 64; ++it) {
+    if (n < max_cells) {
+      cells[3 * n] = c[0];
+      cells[3 * n + 1] = c[1];
+      cells[3 * n + 2] = c[2];
+    }
+    n++;
+    if (c[0] == e[0] && c[1] == e[1] && c[2] == e[2]) break;
+    int ax = 0;
+    if (tmax[1] < tmax[ax]) ax = 1;
+    if (tmax[2] < tmax[ax]) ax = 2;
+    if (tmax[ax] > 1.0f) break;
+    c[ax] += st[ax];
+    tmax[ax] += tdel[ax];
+  }
+  return n;
+}
+
+/* Single-precision world transform of a camera-frame vector, fixed order, no contraction. */
+static void rot_f(const float R[9], const float* x, float* y) {
+  for (int a = 0; a < 3; ++a) y[a] = (R[3 * a] * x[0] + R[3 * a + 1] * x[1]) + R[3 * a + 2] * x[2];
+}
+
+static void pose_f(const double* T, float R[9], float t[3]) {
+  for (int a = 0; a < 3; ++a) {
+    for (int b = 0; b < 3; ++b) R[3 * a + b] = (float)T[4 * a + b];
+    t[a] = (float)T[4 * a + 3];
+  }
+}
+
+static int allocate_frame(omap* m, const oframe* f, const double* T, int frame) {
+  float R[9], t[3];
+  pose_f(T, R, t);
+  float bs = 8.0f * m->hf;
+  int32_t cells[3 * 64];
+  for (int v = 0; v < f->H; ++v)
+    for (int u = 0; u < f->W; ++u) {
+      size_t i = (size_t)v * f->W + u;
+      if (!f->nok[i]) continue;
+      float nw[3], rv[3], pw[3];
+      rot_f(R, f->nf + 3 * i, nw);
+      unsigned mask = 0;
+      for (int D = 0; D < ND; ++D) {
+        float c = (D & 1) ? -nw[D >> 1] : nw[D >> 1];
+        if (c > m->costhf) mask |= 1u << D;
+      }
+      if (!mask) continue;
+      rot_f(R, f->Pf + 3 * i, rv);
+      for (int a = 0; a < 3; ++a) pw[a] = rv[a] + t[a];
+      float len = sqrtf((rv[0] * rv[0] + rv[1] * rv[1]) + rv[2] * rv[2]);
+      float rh[3], A[3], B[3];
+      for (int a = 0; a < 3; ++a) {
+        rh[a] = rv[a] / len;
+        A[a] = pw[a] - m->tauf * rh[a];
+        B[a] = pw[a] + m->tauf * rh[a];
+      }
+      int n = om_segment_blocks(A, B, bs, m->originf, cells, 64);
+      if (n > 64) n = 64;
+      for (int k = 0; k < n; ++k)
+        for (int D = 0; D < ND; ++D)
+          if (mask & (1u << D))
+            if (brick_alloc(m, cells[3 * k], cells[3 * k + 1], cells[3 * k + 2], D, frame) < 0) return -1;
+    }
+  return 0;
+}
+
+/* ============================================================ fusion (A2) == */
+
+static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+/* Eq. direction_weight, as read: 1 in the exclusive zone, 0 beyond theta, linear in between. */
+double om_w_dir(double cos_angle, double theta) {
+  double alpha = acos(clampd(cos_angle, -1.0, 1.0));
+  return clampd((theta - alpha) / (2.0 * theta - M_PI / 2.0), 0.0, 1.0);
+}
+
+static int fuse_frame(omap* m, const oframe* f, const uint8_t* rgb, const double* T) {
+  float R[9], t[3];
+  pose_f(T, R, t);
+  const int W = f->W, H = f->H;
+  const float tau = m->tauf;
+  const float bsz = m->hf;
+  double Rd[9], td[3];
+  for (int a = 0; a < 3; ++a) {
+    for (int b = 0; b < 3; ++b) Rd[3 * a + b] = T[4 * a + b];
+    td[a] = T[4 * a + 3];
+  }
+#pragma omp parallel for schedule(dynamic, 16)
+  for (long b = 0; b < (long)m->nbricks; ++b) {
+    const int32_t* bc = m->coord + 4 * b;
+    const int D = bc[3];
+    ovox* vb = m->vox + (size_t)b * BVOX;
+    for (int k = 0; k < BLK; ++k)
+      for (int j = 0; j < BLK; ++j)
+        for (int i = 0; i < BLK; ++i) {
+          int gi[3] = {BLK * bc[0] + i, BLK * bc[1] + j, BLK * bc[2] + k};
+          /* FP32 decision path: voxel centre, camera frame, projection, band test */
+          float x[3], dxw[3], xc[3];
+          for (int a = 0; a < 3; ++a) {
+            x[a] = (float)gi[a] * bsz + m->originf[a];
+            dxw[a] = x[a] - t[a];
+          }
+          for (int a = 0; a < 3; ++a) xc[a] = (R[a] * dxw[0] + R[3 + a] * dxw[1]) + R[6 + a] * dxw[2];
+          if (!(xc[2] > 0.0f)) continue;
+          float uf = (xc[0] / xc[2]) * f->fx + f->cx;
+          float vf = (xc[1] / xc[2]) * f->fy + f->cy;
+          float ur = floorf(uf + 0.5f), vr = floorf(vf + 0.5f);
+          if (!(ur >= 0.0f && vr >= 0.0f && ur < (float)W && vr < (float)H)) continue;
+          int u = (int)ur, v = (int)vr;
+          size_t pi = (size_t)v * W + u;
+          if (!f->nok[pi]) continue;
+          const float* P = f->Pf + 3 * pi;
+          const float* n = f->nf + 3 * pi;
+          float draw = ((xc[0] - P[0]) * n[0] + (xc[1] - P[1]) * n[1]) + (xc[2] - P[2]) * n[2];
+          if (draw < -tau) continue;
+          ovox* vx = vb + (k * BLK + j) * BLK + i;
+          if (draw > tau) {
+            /* free-space carving, unless a depth jump > tau lies within the carve radius */
+            int jump = 0;
+            float zc = f->z[pi];
+            for (int dv = -m->carve_r; dv <= m->carve_r && !jump; ++dv)
+              for (int du = -m->carve_r; du <= m->carve_r; ++du) {
+                int uu = u + du, vv = v + dv;
+                if (uu < 0 || vv < 0 || uu >= W || vv >= H) continue;
+                size_t qi = (size_t)vv * W + uu;
+                if (!f->ok[qi]) continue;
+                if (fabsf(f->z[qi] - zc) > tau) {
+                  jump = 1;
+                  break;
+                }
+              }
+            if (jump) continue;
+            double wn = vx->w + m->wcarve;
+            vx->sdf = (vx->w * vx->sdf + m->wcarve * 1.0) / wn;
+            vx->w = wn < m->wmax ? wn : m->wmax;
+            continue;
+          }
+          /* membership of the pixel normal in direction D (single-precision decision) */
+          float nw[3];
+          rot_f(R, n, nw);
+          float cd = (D & 1) ? -nw[D >> 1] : nw[D >> 1];
+          if (!(cd > m->costhf)) continue;
+          if (!(((n[0] * P[0] + n[1] * P[1]) + n[2] * P[2]) < 0.0f)) continue;
+          /* FP64 values */
+          double xd[3], xcd[3], rel[3];
+          for (int a = 0; a < 3; ++a) {
+            xd[a] = (double)gi[a] * m->h + m->origin[a];
+            rel[a] = xd[a] - td[a];
+          }
+          for (int a = 0; a < 3; ++a) xcd[a] = Rd[a] * rel[0] + Rd[3 + a] * rel[1] + Rd[6 + a] * rel[2];
+          const double* Pd = f->Pd + 3 * pi;
+          const double* nd = f->nd + 3 * pi;
+          double dr = (xcd[0] - Pd[0]) * nd[0] + (xcd[1] - Pd[1]) * nd[1] + (xcd[2] - Pd[2]) * nd[2];
+          double d = clampd(dr / m->tau, -1.0, 1.0);
+          double zp = Pd[2];
+          double w_depth = 1.0 / ((zp + 1.0 - m->zmin) * (zp + 1.0 - m->zmin));
+          double pl = sqrt(Pd[0] * Pd[0] + Pd[1] * Pd[1] + Pd[2] * Pd[2]);
+          double w_angle = -(nd[0] * Pd[0] + nd[1] * Pd[1] + nd[2] * Pd[2]) / pl;
+          if (w_angle < 0) w_angle = 0;
+          double nwd[3];
+          for (int a = 0; a < 3; ++a) nwd[a] = Rd[3 * a] * nd[0] + Rd[3 * a + 1] * nd[1] + Rd[3 * a + 2] * nd[2];
+          double cdd = (D & 1) ? -nwd[D >> 1] : nwd[D >> 1];
+          double w_d = w_depth * w_angle * om_w_dir(cdd, m->theta);
+          if (!(w_d > 0)) continue;
+          double wn = vx->w + w_d;
+          vx->sdf = (vx->w * vx->sdf + w_d * d) / wn;
+          vx->w = wn < m->wmax ? wn : m->wmax;
+          if (m->color && rgb) {
+            double dist = sqrt((Pd[0] - xcd[0]) * (Pd[0] - xcd[0]) + (Pd[1] - xcd[1]) * (Pd[1] - xcd[1]) +
+                               (Pd[2] - xcd[2]) * (Pd[2] - xcd[2]));
+            double w_c = w_d * (1.0 - (dist / m->tau < 1.0 ? dist / m->tau : 1.0));
+            if (w_c > 0) {
+              const uint8_t* c = rgb + 3 * pi;
+              double wcn = vx->wc + w_c;
+              vx->r = (vx->wc * vx->r + w_c * c[0]) / wcn;
+              vx->g = (vx->wc * vx->g + w_c * c[1]) / wcn;
+              vx->b = (vx->wc * vx->b + w_c * c[2]) / wcn;
+              vx->wc = wcn < m->wmax ? wcn : m->wmax;
+            }
+          }
+        }
+  }
+  return 0;
+}
+
+/* Fuse one frame: preprocess, allocate (hash mode only), voxel-projection fusion. */
+int om_integrate(omap* m, const float* depth, const uint8_t* rgb, int W, int H, float fx, float fy, float cx,
+                 float cy, const double* T_wc) {
+  oframe f;
+  memset(&f, 0, sizeof(f));
+  int rc = frame_prepare(&f, depth, W, H, fx, fy, cx, cy, m->zminf, m->zmaxf, m->dsupf);
+  if (rc == 0 && m->dense_dim <= 0) rc = allocate_frame(m, &f, T_wc, m->frames);
+  if (rc == 0) rc = fuse_frame(m, &f, rgb, T_wc);
+  frame_free(&f);
+  m->frames++;
+  return rc;
+}
+
+/* ============================================================ render (A3-A5) */
+
+typedef struct {
+  int present;
+  double phi, w, wc, col[3];
+  int has_grad;
+  double n[3];
+} dsample;
+
+/* Trilinear sample of direction D at continuous voxel coordinate g (voxel units from the origin). */
+static int trilinear(const omap* m, int D, const double* g, double* phi, double* w, double* wc, double* col) {
+  double fl[3], fr[3];
+  int b[3];
+  for (int a = 0; a < 3; ++a) {
+    fl[a] = floor(g[a]);
+    fr[a] = g[a] - fl[a];
+    b[a] = (int)fl[a];
+  }
+  double acc_s = 0, acc_w = 0, acc_wc = 0, acc_c[3] = {0, 0, 0};
+  for (int c = 0; c < 8; ++c) {
+    int o[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+    int vi[3];
+    double wt = 1.0;
+    for (int a = 0; a < 3; ++a) {
+      vi[a] = b[a] + o[a];
+      wt *= o[a] ? fr[a] : 1.0 - fr[a];
+    }
+    int bx = (int)floor(vi[0] / 8.0), by = (int)floor(vi[1] / 8.0), bz = (int)floor(vi[2] / 8.0);
+    int32_t br = hash_find(m, bx, by, bz, D);
+    if (br < 0) return 0;
+    const ovox* vx = m->vox + (size_t)br * BVOX + ((vi[2] - 8 * bz) * 8 + (vi[1] - 8 * by)) * 8 + (vi[0] - 8 * bx);
+    if (!(vx->w > 0)) return 0;
+    acc_s += wt * vx->sdf;
+    acc_w += wt * vx->w;
+    acc_wc += wt * vx->wc;
+    acc_c[0] += wt * vx->r;
+    acc_c[1] += wt * vx->g;
+    acc_c[2] += wt * vx->b;
+  }
+  *phi = acc_s;
+  if (w) *w = acc_w;
+  if (wc) *wc = acc_wc;
+  if (col) {
+    col[0] = acc_c[0];
+    col[1] = acc_c[1];
+    col[2] = acc_c[2];
+  }
+  return 1;
+}
+
+static void sample_dir(const omap* m, int D, const double* x, dsample* s) {
+  double g[3];
+  for (int a = 0; a < 3; ++a) g[a] = (x[a] - m->origin[a]) / m->h;
+  s->present = trilinear(m, D, g, &s->phi, &s->w, &s->wc, s->col);
+  s->has_grad = 0;
+  if (!s->present) return;
+  double grad[3];
+  for (int a = 0; a < 3; ++a) {
+    double gp[3] = {g[0], g[1], g[2]}, gm[3] = {g[0], g[1], g[2]};
+    gp[a] += 1.0;
+    gm[a] -= 1.0;
+    double fp, fm;
+    if (!trilinear(m, D, gp, &fp, NULL, NULL, NULL)) return;
+    if (!trilinear(m, D, gm, &fm, NULL, NULL, NULL)) return;
+    grad[a] = (fp - fm) / (2.0 * m->h);
+  }
+  double nrm = sqrt(grad[0] * grad[0] + grad[1] * grad[1] + grad[2] * grad[2]);
+  if (!(nrm > 1e-12)) return;
+  for (int a = 0; a < 3; ++a) s->n[a] = grad[a] / nrm;
+  s->has_grad = 1;
+}
+
+/*
+ * Combined SDF at world point x for unit view ray r (Eq. combine_weight, with the
+ * Eq. combine_tsdf_weight fallback). Returns 1 if defined. wsum_comb receives the
+ * sum of combination weights (0 when the fallback was used).
+ */
+typedef struct {
+  double phi, wsum_comb;
+  double n[3];
+  int ncomb;
+  double col[3];
+  int col_ok;
+} combo;
+
+static int combine(const omap* m, const double* x, const double* r, combo* out) {
+  dsample s[ND];
+  double ws = 0, acc = 0, nacc[3] = {0, 0, 0}, cw = 0, cacc[3] = {0, 0, 0};
+  int any = 0;
+  for (int D = 0; D < ND; ++D) {
+    sample_dir(m, D, x, &s[D]);
+    if (!s[D].present) continue;
+    any = 1;
+    if (!s[D].has_grad) continue;
+    double cosv = (D & 1) ? -s[D].n[D >> 1] : s[D].n[D >> 1];
+    double facing = -(s[D].n[0] * r[0] + s[D].n[1] * r[1] + s[D].n[2] * r[2]);
+    if (facing < 0) facing = 0;
+    double wcomb = om_w_dir(cosv, m->theta) * facing * s[D].w;
+    if (!(wcomb > 0)) continue;
+    ws += wcomb;
+    acc += wcomb * s[D].phi;
+    for (int a = 0; a < 3; ++a) nacc[a] += wcomb * s[D].n[a];
+    if (s[D].wc > 0) {
+      cw += wcomb;
+      for (int a = 0; a < 3; ++a) cacc[a] += wcomb * s[D].col[a];
+    }
+  }
+  if (!any) return 0;
+  out->col_ok = 0;
+  if (ws > 0) {
+    out->phi = acc / ws;
+    out->wsum_comb = ws;
+    double nl = sqrt(nacc[0] * nacc[0] + nacc[1] * nacc[1] + nacc[2] * nacc[2]);
+    for (int a = 0; a < 3; ++a) out->n[a] = nl > 0 ? nacc[a] / nl : 0.0;
+    out->ncomb = nl > 0;
+    if (cw > 0) {
+      for (int a = 0; a < 3; ++a) out->col[a] = cacc[a] / cw;
+      out->col_ok = 1;
+    }
+    return 1;
+  }
+  double wf = 0, af = 0;
+  for (int D = 0; D < ND; ++D) {
+    if (!s[D].present) continue;
+    double facing = -(VDIR[D][0] * r[0] + VDIR[D][1] * r[1] + VDIR[D][2] * r[2]);
+    if (facing < 0) facing = 0;
+    double w = s[D].w * facing;
+    if (!(w > 0)) continue;
+    wf += w;
+    af += w * s[D].phi;
+  }
+  if (!(wf > 0)) return 0;
+  out->phi = af / wf;
+  out->wsum_comb = 0;
+  out->ncomb = 0;
+  return 1;
+}
+
+/* Exposed for tests: combined SDF at a world point. Returns 1 if defined; info = phi, wsum, n[3], col[3], col_ok. */
+int om_eval(const omap* m, const double* x, const double* r, double* info) {
+  combo c;
+  memset(&c, 0, sizeof(c));
+  int ok = combine(m, x, r, &c);
+  info[0] = c.phi;
+  info[1] = c.wsum_comb;
+  for (int a = 0; a < 3; ++a) {
+    info[2 + a] = c.n[a];
+    info[5 + a] = c.col[a];
+  }
+  info[8] = c.col_ok;
+  return ok;
+}
+
+static int cell_has_any(const omap* m, int cx, int cy, int cz) {
+  for (int D = 0; D < ND; ++D)
+    if (hash_find(m, cx, cy, cz, D) >= 0) return 1;
+  return 0;
+}
+
+/*
+ * Ray-cast one pixel (Sec. 4). Outputs depth (z, 0 = miss), camera-frame normal,
+ * colour and colour validity. Returns 1 on a hit.
+ */
+static int render_pixel(const omap* m, const double* T, double fx, double fy, double cx, double cy, int u, int v,
+                        double* depth, double* ncam, double* col, int* col_ok) {
+  double rc[3] = {((double)u - cx) / fx, ((double)v - cy) / fy, 1.0};
+  double rl = sqrt(rc[0] * rc[0] + rc[1] * rc[1] + rc[2] * rc[2]);
+  double r[3], o[3] = {T[3], T[7], T[11]};
+  for (int a = 0; a < 3; ++a) r[a] = (T[4 * a] * rc[0] + T[4 * a + 1] * rc[1] + T[4 * a + 2] * rc[2]) / rl;
+  double step = 0.5 * m->h;
+  double tn = m->zmin * rl, tf = m->zmax * rl;
+  long k0 = (long)ceil(tn / step), k1 = (long)floor(tf / step);
+  int prev_def = 0;
+  double prev_phi = 0, prev_t = 0;
+  int cell[3] = {0x7fffffff, 0, 0}, cell_any = 0;
+  double bs = 8.0 * m->h;
+  for (long k = k0; k <= k1; ++k) {
+    double t = k * step;
+    double x[3] = {o[0] + t * r[0], o[1] + t * r[1], o[2] + t * r[2]};
+    int c[3];
+    for (int a = 0; a < 3; ++a) c[a] = (int)floor((x[a] - m->origin[a]) / bs);
+    if (c[0] != cell[0] || c[1] != cell[1] || c[2] != cell[2]) {
+      cell[0] = c[0];
+      cell[1] = c[1];
+      cell[2] = c[2];
+      cell_any = cell_has_any(m, c[0], c[1], c[2]);
+    }
+    combo cb;
+    if (!cell_any || !combine(m, x, r, &cb)) {
+      prev_def = 0;
+      continue;
+    }
+    if (prev_def && prev_phi > 0 && cb.phi <= 0) {
+      /* refine the root of the continuous Phi(t) in [prev_t, t] by bisection */
+      double lo = prev_t, hi = t, flo = prev_phi, fhi = cb.phi;
+      int broken = 0;
+      while (hi - lo > 1e-10) {
+        double mid = 0.5 * (lo + hi);
+        double xm[3] = {o[0] + mid * r[0], o[1] + mid * r[1], o[2] + mid * r[2]};
+        combo cm;
+        if (!combine(m, xm, r, &cm)) {
+          broken = 1;
+          break;
+        }
+        if (cm.phi > 0) {
+          lo = mid;
+          flo = cm.phi;
+        } else {
+          hi = mid;
+          fhi = cm.phi;
+        }
+      }
+      double ts = broken ? lo + (hi - lo) * flo / (flo - fhi) : 0.5 * (lo + hi);
+      double xs[3] = {o[0] + ts * r[0], o[1] + ts * r[1], o[2] + ts * r[2]};
+      combo ch;
+      if (!combine(m, xs, r, &ch) || !(ch.wsum_comb > 0) || !ch.ncomb) return 0;
+      *depth = ts / rl;
+      for (int a = 0; a < 3; ++a) ncam[a] = T[a] * ch.n[0] + T[4 + a] * ch.n[1] + T[8 + a] * ch.n[2];
+      if (ch.col_ok)
+        for (int a = 0; a < 3; ++a) col[a] = ch.col[a];
+      *col_ok = ch.col_ok;
+      return 1;
+    }
+    prev_def = 1;
+    prev_phi = cb.phi;
+    prev_t = t;
+  }
+  return 0;
+}
+
+/*
+ * Render pixels. If pix is NULL all W*H pixels are rendered (row-major);
+ * otherwise npix (u, v) pairs. Outputs per rendered pixel: depth (0 = miss),
+ * normal (3, camera frame), colour (3, 0..255) and colour validity.
+ */
+int om_render(const omap* m, const double* T_wc, int W, int H, float fx, float fy, float cx, float cy,
+              const int32_t* pix, long npix, double* depth, double* normal, double* color, uint8_t* color_ok) {
+  long n = pix ? npix : (long)W * H;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (long i = 0; i < n; ++i) {
+    int u = pix ? pix[2 * i] : (int)(i % W);
+    int v = pix ? pix[2 * i + 1] : (int)(i / W);
+    double d = 0, nc[3] = {0, 0, 0}, col[3] = {0, 0, 0};
+    int cok = 0;
+    if (!render_pixel(m, T_wc, fx, fy, cx, cy, u, v, &d, nc, col, &cok)) {
+      d = 0;
+      nc[0] = nc[1] = nc[2] = 0;
+      cok = 0;
+    }
+    depth[i] = d;
+    if (normal)
+      for (int a = 0; a < 3; ++a) normal[3 * i + a] = nc[a];
+    if (color)
+      for (int a = 0; a < 3; ++a) color[3 * i + a] = cok ? col[a] : 0.0;
+    if (color_ok) color_ok[i] = (uint8_t)cok;
+  }
+  return 0;
+}
