@@ -1,0 +1,226 @@
+/*
+ * dtsdf.h - C ABI of the Directional TSDF render + ICP library (libdtsdf.so).
+ *
+ * The library implements the data-parallel hot path of Splietker & Behnke,
+ * "Rendering the Directional TSDF for Tracking and Multi-Sensor Registration with
+ * Point-To-Plane Scale ICP": fusing RGB-D frames into a Directional TSDF (six
+ * per-axis TSDFs in one voxel-block hash keyed by block and direction), ray-cast
+ * rendering of depth, normal and colour images from it, and the point-to-plane
+ * ICP normal-equation reduction and solve in SE(3) and Sim(3), with the optional
+ * frame-to-keyframe photometric term.
+ *
+ * Conventions shared by every call
+ *   - Pointers documented as "device" are CUDA device pointers owned by the caller;
+ *     "host" pointers are ordinary CPU memory read or written before the call returns.
+ *   - Images are row-major, pixel (u, v) at index v * width + u; pixel centres sit
+ *     at integer (u, v). Camera frame: x right, y down, z forward.
+ *   - Poses are row-major 4x4 double matrices. T_wc maps camera to world.
+ *   - Depth is z-depth in metres; 0 marks an invalid or missing value.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     All device work is ordered on it. Calls returning host results synchronise it.
+ *   - Errors are reported only through dtsdf_status; dtsdf_last_error() returns a
+ *     message for the calling thread's most recent failure. Nothing throws.
+ *   - A map or ICP context may be used by one host thread at a time.
+ */
+#ifndef DTSDF_H
+#define DTSDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DTSDF_API __attribute__((visibility("default")))
+#else
+#define DTSDF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dtsdf_map_s* dtsdf_map;
+typedef struct dtsdf_icp_s* dtsdf_icp;
+
+typedef enum {
+  DTSDF_OK = 0,
+  DTSDF_ERR_INVALID_ARG = 1, /* null pointer, bad size, bad parameter */
+  DTSDF_ERR_OOM = 2,         /* device allocation failed */
+  DTSDF_ERR_MAP_FULL = 3,    /* block pool, directory or hash table exhausted */
+  DTSDF_ERR_CUDA = 4,        /* a CUDA runtime error (message in dtsdf_last_error) */
+  DTSDF_ERR_DEGENERATE = 5,  /* ICP normal equations not positive definite / too few rows */
+  DTSDF_ERR_TIMEOUT = 6      /* a bounded device wait ran out */
+} dtsdf_status;
+
+typedef enum { DTSDF_STORE_FP32 = 0, DTSDF_STORE_FP16 = 1 } dtsdf_storage;
+
+/* Map parameters (Sec. 3, Sec. 4, Sec. 6 of the paper; see the readings in the design notes). */
+typedef struct {
+  float voxel_size;     /* h, metres */
+  float truncation;     /* tau, metres (Eq. point-to-plane normalises by it) */
+  float theta;          /* angular threshold of Eq. angular_threshold, radians, in (acos(1/sqrt3), pi/2] */
+  float w_max;          /* cap of the accumulated depth and colour weights */
+  float w_carve;        /* constant weight of a free-space carving update (Sec. 3) */
+  float z_min, z_max;   /* valid depth range, metres; z_min also enters Eq. ICP_weight */
+  float delta_sup;      /* outlier filter: neighbour supports a depth if |dz| <= delta_sup (Sec. 6) */
+  int32_t carve_radius; /* carving needs no depth jump > tau within this many pixels (Sec. 3: 2) */
+  int32_t dense_dim;    /* > 0: dense grid of dense_dim^3 voxels (multiple of 8), every block
+                           allocated at creation; 0: sparse voxel-block hash */
+  float dense_origin[3];/* world position of voxel (0,0,0); voxel (i,j,k) of block b is at
+                           origin + (8 b + (i,j,k)) * h */
+  uint32_t max_blocks;  /* pool capacity in (block, direction) bricks of 8^3 voxels */
+  int32_t storage;      /* dtsdf_storage: FP32 sdf+weight (8 B) or FP16 sdf + u16 weight (4 B) */
+  int32_t color;        /* 1: integrate and render colour */
+} dtsdf_params;
+
+typedef struct {
+  int32_t width, height;
+  float fx, fy, cx, cy;
+} dtsdf_intrinsics;
+
+/* One RGB-D frame in device memory. */
+typedef struct {
+  const float* depth;  /* device, height*width float32 z-depth, 0 = invalid */
+  const uint8_t* rgb;  /* device, height*width*3 uint8, or NULL */
+  dtsdf_intrinsics K;
+} dtsdf_frame;
+
+/* Render output buffers, device memory owned by the caller, sized height*width*(1|4). */
+typedef struct {
+  float* depth;   /* z-depth of the first positive-to-negative crossing, 0 = miss */
+  float* normals; /* float4 per pixel: camera-frame unit normal (x, y, z) and w = depth; 0 on a miss */
+  float* color;   /* float4 per pixel: r, g, b in [0, 255] and w = 1 where colour is defined; or NULL */
+} dtsdf_render_out;
+
+/* Map statistics (dtsdf_map_stats synchronises the stream). */
+typedef struct {
+  int64_t bricks;          /* allocated (block, direction) bricks */
+  int64_t blocks;          /* distinct allocated block coordinates */
+  int64_t bricks_per_dir[6];
+  int64_t capacity;        /* max_blocks */
+  uint32_t error_flags;    /* bit 0: pool full, bit 1: directory full, bit 2: hash probe limit */
+  int32_t frames;          /* frames integrated */
+} dtsdf_map_stats_t;
+
+/* ----------------------------------------------------------------- map ---- */
+
+/* Create an empty map. Allocates max_blocks bricks of device memory up front
+ * (FP32: 24 B per voxel with colour, 8 B without; FP16: 8 / 4 B). */
+DTSDF_API dtsdf_status dtsdf_create(const dtsdf_params* params, void* stream, dtsdf_map* out);
+DTSDF_API dtsdf_status dtsdf_destroy(dtsdf_map map);
+
+/* Fuse one frame taken at pose T_wc (Sec. 3 voxel-projection fusion): outlier filter and
+ * cross-product normals (Sec. 6), allocation of the (block, direction) bricks that the
+ * segment [p - tau r, p + tau r] of every pixel with a normal crosses, for each direction
+ * of Eq. angular_threshold, then the weighted running average of Eq. point-to-plane with
+ * the weights of Eq. combined_fusion_weight and Eq. color_weight, and free-space carving.
+ * Asynchronous. Pool exhaustion sets an error flag reported by dtsdf_map_stats and by the
+ * next dtsdf_integrate call (DTSDF_ERR_MAP_FULL). The first call with a new frame size
+ * allocates scratch memory. */
+DTSDF_API dtsdf_status dtsdf_integrate(dtsdf_map map, const dtsdf_frame* frame, const double T_wc[16], void* stream);
+
+/* Ray-cast depth, normals and colour at pose T_wc with intrinsics K (Sec. 4): per pixel,
+ * march the combined SDF of Eq. combine_weight (fallback Eq. combine_tsdf_weight) along
+ * the ray from z_min to z_max, find the first positive-to-negative crossing between
+ * consecutive samples of the h/2 grid and refine it. Asynchronous. */
+DTSDF_API dtsdf_status dtsdf_render(dtsdf_map map, const dtsdf_intrinsics* K, const double T_wc[16],
+                          const dtsdf_render_out* out, void* stream);
+
+DTSDF_API dtsdf_status dtsdf_map_stats(dtsdf_map map, dtsdf_map_stats_t* stats, void* stream);
+
+/* Copy the map to host memory: coords (n x 4 int32: bx, by, bz, D) and voxels
+ * (n x 512 x 6 float: sdf, w, r, g, b, wc, voxel index i + 8 j + 64 k). At most `cap`
+ * bricks are written; *n_out receives the total count. Synchronous. */
+DTSDF_API dtsdf_status dtsdf_map_export(dtsdf_map map, int32_t* coords, float* voxels, int64_t cap, int64_t* n_out,
+                              void* stream);
+
+/* Load bricks from host memory, in the layout dtsdf_map_export writes: coords (n x 4:
+ * bx, by, bz, D) and voxels (n x 512 x 6: sdf, w, r, g, b, wc). Missing bricks are
+ * allocated (sparse maps); existing ones are overwritten. Restores a saved map or loads a
+ * map built elsewhere. Synchronous. DTSDF_ERR_MAP_FULL if the pool cannot hold them. */
+DTSDF_API dtsdf_status dtsdf_map_import(dtsdf_map map, const int32_t* coords, const float* voxels, int64_t n,
+                                        void* stream);
+
+/* ----------------------------------------------------------------- ICP ---- */
+
+typedef struct {
+  int32_t levels;       /* pyramid levels used, 1..4 (level 0 = full resolution) */
+  int32_t iters[4];     /* iteration cap per level, index = level (0 finest) */
+  float eps[4];         /* distance outlier threshold per level, metres (Sec. 7: 0.005 fine / 0.05 coarse) */
+  float photo_thr[4];   /* intensity outlier threshold per level (Sec. 7: 0.05 fine / 0.175 coarse) */
+  float lambda;         /* photometric weight of Eq. combined_icp (0.1); 0 disables the term */
+  float z_min;          /* z_min of Eq. ICP_weight */
+  double stop_norm;     /* stop a level when ||xi|| < stop_norm (Sec. 7: 1e-6) */
+  int32_t min_rows;     /* fewer rows than this -> DTSDF_ERR_DEGENERATE */
+} dtsdf_icp_opts;
+
+/* Result of one Gauss-Newton iteration. H (row-major, dim x dim in the top-left of 7x7
+ * storage) and g are the normal equations of Eq. ICP_Hessian without the factor 2, for
+ * xi = (nu, omega) or (nu, omega, sigma). */
+typedef struct {
+  double H[49];
+  double g[7];
+  double xi[7];
+  double error;        /* sum of w r^2 */
+  int64_t rows;        /* geometric + photometric rows used */
+  int64_t rows_photo;
+  double step_norm;    /* ||xi|| */
+  int32_t dim;         /* 6 or 7 */
+  int32_t status;      /* 0 ok, DTSDF_ERR_DEGENERATE */
+  int32_t converged;   /* step_norm < stop_norm */
+  int32_t iterations;  /* iterations run (dtsdf_icp_solve) */
+} dtsdf_icp_stats;
+
+/* ICP context: current-frame pyramid, keyframe pyramid, reduction scratch, device pose. */
+DTSDF_API dtsdf_status dtsdf_icp_create(int32_t max_width, int32_t max_height, int32_t levels, dtsdf_icp* out);
+DTSDF_API dtsdf_status dtsdf_icp_destroy(dtsdf_icp icp);
+
+/* Current frame: outlier filter (Sec. 6), then the depth pyramid (2x2 mean of valid depths,
+ * f/2, (c - 0.5)/2) and, if rgb is given, the intensity pyramid I = (0.299 R + 0.587 G +
+ * 0.114 B) / 255. Asynchronous. */
+DTSDF_API dtsdf_status dtsdf_icp_set_frame(dtsdf_icp icp, const dtsdf_frame* cur, float z_min, float z_max,
+                                 float delta_sup, void* stream);
+
+/* Keyframe of the frame-to-keyframe photometric term (Eq. keyframe_icp): intensity pyramid
+ * and central-difference gradients of its rgb. Asynchronous. */
+DTSDF_API dtsdf_status dtsdf_icp_set_keyframe(dtsdf_icp icp, const dtsdf_frame* kf, void* stream);
+
+/* One Gauss-Newton iteration on pyramid `level` against the render `ref` (intrinsics K_ref):
+ * point-to-plane rows of Eq. geometric_ICP / Eq. ICP_geometric_dx with weights of
+ * Eq. ICP_weight, plus photometric rows against the keyframe when T_rs (render camera ->
+ * keyframe camera, host, row-major) is non-NULL and opts->lambda > 0; deterministic
+ * reduction, Cholesky solve of Eq. ICP_solution and the update of Eq. deltaT_update.
+ * T_rel (host, row-major, current camera -> render camera) is read and, unless the system
+ * is degenerate, overwritten. Synchronous (returns stats). */
+DTSDF_API dtsdf_status dtsdf_icp_step(dtsdf_icp icp, const dtsdf_render_out* ref, const dtsdf_intrinsics* K_ref,
+                            int32_t level, double T_rel[16], const double* T_rs, const dtsdf_icp_opts* opts,
+                            dtsdf_icp_stats* stats, void* stream);
+
+/* Same in Sim(3) (Sec. 5.3, Eq. sim3_derivative): T_rel = [s R | t], 7x7 normal equations. */
+DTSDF_API dtsdf_status dtsdf_icp_sim3_step(dtsdf_icp icp, const dtsdf_render_out* ref, const dtsdf_intrinsics* K_ref,
+                                 int32_t level, double T_rel[16], const double* T_rs,
+                                 const dtsdf_icp_opts* opts, dtsdf_icp_stats* stats, void* stream);
+
+/* Whole coarse-to-fine schedule (levels-1 .. 0, opts->iters[l] iterations, early stop per
+ * level), entirely on the device: T_rel_dev (device, 16 doubles) is read and updated in
+ * place; stats_dev (device, one dtsdf_icp_stats) receives the last iteration's statistics.
+ * Asynchronous and free of host synchronisation, so it can be captured in a CUDA graph.
+ * sim3 = 0: SE(3), 1: Sim(3). */
+DTSDF_API dtsdf_status dtsdf_icp_solve(dtsdf_icp icp, const dtsdf_render_out* ref, const dtsdf_intrinsics* K_ref,
+                             int32_t sim3, double* T_rel_dev, const double* T_rs, const dtsdf_icp_opts* opts,
+                             dtsdf_icp_stats* stats_dev, void* stream);
+
+/* Exponential map of se(3) (sim3 = 0, xi[6]) or sim(3) (sim3 = 1, xi[7]) evaluated by the
+ * library's device code (the closed form of the matrix exponential of the 4x4 generator);
+ * out: host 16 doubles. Synchronous; exposed for verification. */
+DTSDF_API dtsdf_status dtsdf_exp(int32_t sim3, const double* xi, double out[16]);
+
+/* Message of the calling thread's most recent error ("" if none). */
+DTSDF_API const char* dtsdf_last_error(void);
+
+/* Library version string. */
+DTSDF_API const char* dtsdf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DTSDF_H */

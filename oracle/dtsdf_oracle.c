@@ -36,7 +36,10 @@
  *                     are present
  *   render march      samples at t = k * h/2 along the unit ray; the first pair of
  *                     consecutive defined samples with Phi > 0 >= Phi is the hit,
- *                     refined by bisection to 1e-10 m
+ *                     refined by two regular 8-step scans for the first sign change
+ *                     and linear interpolation; the normal and colour are taken at
+ *                     the first grid sample behind the crossing (else the sample in
+ *                     front of it, else the root)
  *
  * Build: gcc -O2 -fPIC -shared -fopenmp -ffp-contract=off (see oracle/__init__.py).
  */
@@ -48,6 +51,8 @@
 #define ND 6
 #define BLK 8
 #define BVOX 512
+/* smallest weight of an admitted update (keeps "weight > 0" a property of the decision) */
+#define W_FLOOR 1e-12
 
 /* Direction axis vectors v^D: X+, X-, Y+, Y-, Z+, Z- (Sec. 3). */
 static const double VDIR[ND][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
@@ -561,8 +566,10 @@ static int fuse_frame(omap* m, const oframe* f, const uint8_t* rgb, const double
             rel[a] = xd[a] - td[a];
           }
           for (int a = 0; a < 3; ++a) xcd[a] = Rd[a] * rel[0] + Rd[3 + a] * rel[1] + Rd[6 + a] * rel[2];
+          /* the pixel normal is estimated once, in single precision (it decides the
+             direction membership above); every value below is computed in double */
           const double* Pd = f->Pd + 3 * pi;
-          const double* nd = f->nd + 3 * pi;
+          const double nd[3] = {(double)n[0], (double)n[1], (double)n[2]};
           double dr = (xcd[0] - Pd[0]) * nd[0] + (xcd[1] - Pd[1]) * nd[1] + (xcd[2] - Pd[2]) * nd[2];
           double d = clampd(dr / m->tau, -1.0, 1.0);
           double zp = Pd[2];
@@ -573,16 +580,22 @@ static int fuse_frame(omap* m, const oframe* f, const uint8_t* rgb, const double
           double nwd[3];
           for (int a = 0; a < 3; ++a) nwd[a] = Rd[3 * a] * nd[0] + Rd[3 * a + 1] * nd[1] + Rd[3 * a + 2] * nd[2];
           double cdd = (D & 1) ? -nwd[D >> 1] : nwd[D >> 1];
+          /* an update the single-precision tests admitted always carries a positive weight */
           double w_d = w_depth * w_angle * om_w_dir(cdd, m->theta);
-          if (!(w_d > 0)) continue;
+          if (!(w_d > W_FLOOR)) w_d = W_FLOOR;
           double wn = vx->w + w_d;
           vx->sdf = (vx->w * vx->sdf + w_d * d) / wn;
           vx->w = wn < m->wmax ? wn : m->wmax;
           if (m->color && rgb) {
-            double dist = sqrt((Pd[0] - xcd[0]) * (Pd[0] - xcd[0]) + (Pd[1] - xcd[1]) * (Pd[1] - xcd[1]) +
-                               (Pd[2] - xcd[2]) * (Pd[2] - xcd[2]));
-            double w_c = w_d * (1.0 - (dist / m->tau < 1.0 ? dist / m->tau : 1.0));
-            if (w_c > 0) {
+            /* colour is fused only within tau of the observed point (Eq. color_weight);
+               that test is a single-precision decision */
+            float e0 = P[0] - xc[0], e1 = P[1] - xc[1], e2 = P[2] - xc[2];
+            float distf = sqrtf((e0 * e0 + e1 * e1) + e2 * e2);
+            if (distf < tau) {
+              double dist = sqrt((Pd[0] - xcd[0]) * (Pd[0] - xcd[0]) + (Pd[1] - xcd[1]) * (Pd[1] - xcd[1]) +
+                                 (Pd[2] - xcd[2]) * (Pd[2] - xcd[2]));
+              double w_c = w_d * (1.0 - (dist / m->tau < 1.0 ? dist / m->tau : 1.0));
+              if (!(w_c > W_FLOOR)) w_c = W_FLOOR;
               const uint8_t* c = rgb + 3 * pi;
               double wcn = vx->wc + w_c;
               vx->r = (vx->wc * vx->r + w_c * c[0]) / wcn;
@@ -802,29 +815,45 @@ static int render_pixel(const omap* m, const double* T, double fx, double fy, do
       continue;
     }
     if (prev_def && prev_phi > 0 && cb.phi <= 0) {
-      /* refine the root of the continuous Phi(t) in [prev_t, t] by bisection */
-      double lo = prev_t, hi = t, flo = prev_phi, fhi = cb.phi;
-      int broken = 0;
-      while (hi - lo > 1e-10) {
-        double mid = 0.5 * (lo + hi);
-        double xm[3] = {o[0] + mid * r[0], o[1] + mid * r[1], o[2] + mid * r[2]};
-        combo cm;
-        if (!combine(m, xm, r, &cm)) {
-          broken = 1;
-          break;
+      /* refine the crossing in [prev_t, t] by small regular steps (Sec. 4): two scans of
+         8 sub-steps each keep the first sub-interval where Phi turns <= 0 (an undefined
+         probe counts as free space); the root is the linear interpolation of Phi over the
+         final h/128-wide bracket */
+      double lo = prev_t, hi = t;
+      for (int lvl = 0; lvl < 2; ++lvl) {
+        double a0 = lo, dt = (hi - lo) / 8.0, prev = lo;
+        for (int j = 1; j < 8; ++j) {
+          double tj = a0 + j * dt;
+          double xj[3] = {o[0] + tj * r[0], o[1] + tj * r[1], o[2] + tj * r[2]};
+          combo cj;
+          if (combine(m, xj, r, &cj) && cj.phi <= 0) {
+            hi = tj;
+            break;
+          }
+          prev = tj;
         }
-        if (cm.phi > 0) {
-          lo = mid;
-          flo = cm.phi;
-        } else {
-          hi = mid;
-          fhi = cm.phi;
-        }
+        lo = prev;
       }
-      double ts = broken ? lo + (hi - lo) * flo / (flo - fhi) : 0.5 * (lo + hi);
-      double xs[3] = {o[0] + ts * r[0], o[1] + ts * r[1], o[2] + ts * r[2]};
+      double ts;
+      {
+        double xa[3] = {o[0] + lo * r[0], o[1] + lo * r[1], o[2] + lo * r[2]};
+        double xb[3] = {o[0] + hi * r[0], o[1] + hi * r[1], o[2] + hi * r[2]};
+        combo ca, cbb;
+        int da = combine(m, xa, r, &ca) && ca.phi > 0;
+        int db = combine(m, xb, r, &cbb) && cbb.phi <= 0;
+        ts = (da && db) ? lo + (hi - lo) * ca.phi / (ca.phi - cbb.phi) : 0.5 * (lo + hi);
+      }
+      /* normal and colour: at the first grid sample behind the crossing (the one that
+         decided the hit), else at the sample in front of it, else at the root; a miss if
+         the combination weights vanish at all three */
       combo ch;
-      if (!combine(m, xs, r, &ch) || !(ch.wsum_comb > 0) || !ch.ncomb) return 0;
+      int have = 0;
+      double ends[3] = {t, prev_t, ts};
+      for (int e = 0; e < 3 && !have; ++e) {
+        double xs[3] = {o[0] + ends[e] * r[0], o[1] + ends[e] * r[1], o[2] + ends[e] * r[2]};
+        have = combine(m, xs, r, &ch) && ch.wsum_comb > 0 && ch.ncomb;
+      }
+      if (!have) return 0;
       *depth = ts / rl;
       for (int a = 0; a < 3; ++a) ncam[a] = T[a] * ch.n[0] + T[4 + a] * ch.n[1] + T[8 + a] * ch.n[2];
       if (ch.col_ok)

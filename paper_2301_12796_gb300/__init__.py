@@ -1,0 +1,272 @@
+"""Python binding of libdtsdf (the C ABI declared in include/dtsdf.h).
+
+Argument marshalling only: every step of fusion, rendering and ICP runs in the
+library's CUDA kernels. PyTorch tensors provide device memory and streams; their
+data pointers are passed straight through. There is no CPU fallback: if the
+shared library is missing or cannot be loaded, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdtsdf.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_MAP_FULL, ERR_CUDA, ERR_DEGENERATE, ERR_TIMEOUT = range(7)
+STORE_FP32, STORE_FP16 = 0, 1
+_STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "MAP_FULL", 4: "CUDA", 5: "DEGENERATE", 6: "TIMEOUT"}
+
+c_float, c_int32, c_uint32, c_int64, c_double, c_void_p = (ctypes.c_float, ctypes.c_int32, ctypes.c_uint32,
+                                                          ctypes.c_int64, ctypes.c_double, ctypes.c_void_p)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("voxel_size", c_float), ("truncation", c_float), ("theta", c_float), ("w_max", c_float),
+                ("w_carve", c_float), ("z_min", c_float), ("z_max", c_float), ("delta_sup", c_float),
+                ("carve_radius", c_int32), ("dense_dim", c_int32), ("dense_origin", c_float * 3),
+                ("max_blocks", c_uint32), ("storage", c_int32), ("color", c_int32)]
+
+
+class Intrinsics(ctypes.Structure):
+    _fields_ = [("width", c_int32), ("height", c_int32), ("fx", c_float), ("fy", c_float), ("cx", c_float),
+                ("cy", c_float)]
+
+
+class Frame(ctypes.Structure):
+    _fields_ = [("depth", c_void_p), ("rgb", c_void_p), ("K", Intrinsics)]
+
+
+class RenderOut(ctypes.Structure):
+    _fields_ = [("depth", c_void_p), ("normals", c_void_p), ("color", c_void_p)]
+
+
+class MapStats(ctypes.Structure):
+    _fields_ = [("bricks", c_int64), ("blocks", c_int64), ("bricks_per_dir", c_int64 * 6), ("capacity", c_int64),
+                ("error_flags", c_uint32), ("frames", c_int32)]
+
+
+class IcpOpts(ctypes.Structure):
+    _fields_ = [("levels", c_int32), ("iters", c_int32 * 4), ("eps", c_float * 4), ("photo_thr", c_float * 4),
+                ("lambda_", c_float), ("z_min", c_float), ("stop_norm", c_double), ("min_rows", c_int32)]
+
+
+class IcpStats(ctypes.Structure):
+    _fields_ = [("H", c_double * 49), ("g", c_double * 7), ("xi", c_double * 7), ("error", c_double),
+                ("rows", c_int64), ("rows_photo", c_int64), ("step_norm", c_double), ("dim", c_int32),
+                ("status", c_int32), ("converged", c_int32), ("iterations", c_int32)]
+
+    def H_matrix(self) -> np.ndarray:
+        d = self.dim
+        return np.array(self.H[:], np.float64).reshape(7, 7)[:d, :d].copy()
+
+    def g_vector(self) -> np.ndarray:
+        return np.array(self.g[: self.dim], np.float64)
+
+
+# exported symbols and their signatures (same order as include/dtsdf.h)
+P = c_void_p
+SIGNATURES = {
+    "dtsdf_create": ([ctypes.POINTER(Params), P, ctypes.POINTER(P)], c_int32),
+    "dtsdf_destroy": ([P], c_int32),
+    "dtsdf_integrate": ([P, ctypes.POINTER(Frame), P, P], c_int32),
+    "dtsdf_render": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), P], c_int32),
+    "dtsdf_map_stats": ([P, ctypes.POINTER(MapStats), P], c_int32),
+    "dtsdf_map_export": ([P, P, P, c_int64, ctypes.POINTER(c_int64), P], c_int32),
+    "dtsdf_map_import": ([P, P, P, c_int64, P], c_int32),
+    "dtsdf_icp_create": ([c_int32, c_int32, c_int32, ctypes.POINTER(P)], c_int32),
+    "dtsdf_icp_destroy": ([P], c_int32),
+    "dtsdf_icp_set_frame": ([P, ctypes.POINTER(Frame), c_float, c_float, c_float, P], c_int32),
+    "dtsdf_icp_set_keyframe": ([P, ctypes.POINTER(Frame), P], c_int32),
+    "dtsdf_icp_step": ([P, ctypes.POINTER(RenderOut), ctypes.POINTER(Intrinsics), c_int32, P, P,
+                        ctypes.POINTER(IcpOpts), ctypes.POINTER(IcpStats), P], c_int32),
+    "dtsdf_icp_sim3_step": ([P, ctypes.POINTER(RenderOut), ctypes.POINTER(Intrinsics), c_int32, P, P,
+                             ctypes.POINTER(IcpOpts), ctypes.POINTER(IcpStats), P], c_int32),
+    "dtsdf_icp_solve": ([P, ctypes.POINTER(RenderOut), ctypes.POINTER(Intrinsics), c_int32, P, P,
+                         ctypes.POINTER(IcpOpts), P, P], c_int32),
+    "dtsdf_exp": ([c_int32, P, P], c_int32),
+    "dtsdf_last_error": ([], ctypes.c_char_p),
+    "dtsdf_version": ([], ctypes.c_char_p),
+}
+
+
+class DtsdfError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib():
+    """Load libdtsdf.so (build it first with paper_2301_12796_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libdtsdf.so not built ({LIB_PATH}); run python -m paper_2301_12796_gb300.build")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def check(status: int, where: str):
+    if status != OK:
+        raise DtsdfError(status, where, lib().dtsdf_last_error().decode())
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def intrinsics(K) -> Intrinsics:
+    return Intrinsics(int(K.width), int(K.height), float(K.fx), float(K.fy), float(K.cx), float(K.cy))
+
+
+def pose_buf(T) -> ctypes.Array:
+    a = np.ascontiguousarray(np.asarray(T, np.float64).reshape(16))
+    return (c_double * 16)(*a.tolist())
+
+
+def params(voxel_size=0.005, truncation=0.02, theta=3 * np.pi / 8, w_max=255.0, w_carve=0.1, z_min=0.1, z_max=6.0,
+           delta_sup=None, carve_radius=2, dense_dim=0, origin=(0.0, 0.0, 0.0), max_blocks=1 << 16,
+           storage=STORE_FP32, color=True) -> Params:
+    return Params(voxel_size, truncation, theta, w_max, w_carve, z_min, z_max,
+                  truncation / 2 if delta_sup is None else delta_sup, carve_radius, dense_dim,
+                  (c_float * 3)(*origin), max_blocks, storage, int(color))
+
+
+class Map:
+    """A Directional TSDF in device memory (dtsdf_create / dtsdf_destroy)."""
+
+    def __init__(self, p: Params, stream=None):
+        self.params = p
+        h = c_void_p()
+        check(lib().dtsdf_create(ctypes.byref(p), _stream_ptr(stream), ctypes.byref(h)), "dtsdf_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().dtsdf_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def integrate(self, depth, rgb, K, T_wc, stream=None):
+        """depth: float32 CUDA tensor [H, W]; rgb: uint8 CUDA tensor [H, W, 3] or None."""
+        f = Frame(depth.data_ptr(), None if rgb is None else rgb.data_ptr(), intrinsics(K))
+        check(lib().dtsdf_integrate(self._h, ctypes.byref(f), pose_buf(T_wc), _stream_ptr(stream)),
+              "dtsdf_integrate")
+
+    def render(self, K, T_wc, depth, normals, color=None, stream=None):
+        """depth [H, W] float32, normals [H, W, 4] float32, color [H, W, 4] float32 or None (CUDA tensors)."""
+        out = RenderOut(depth.data_ptr(), normals.data_ptr(), None if color is None else color.data_ptr())
+        Ki = intrinsics(K)
+        check(lib().dtsdf_render(self._h, ctypes.byref(Ki), pose_buf(T_wc), ctypes.byref(out), _stream_ptr(stream)),
+              "dtsdf_render")
+
+    def stats(self, stream=None) -> MapStats:
+        st = MapStats()
+        check(lib().dtsdf_map_stats(self._h, ctypes.byref(st), _stream_ptr(stream)), "dtsdf_map_stats")
+        return st
+
+    def export(self, stream=None):
+        """(coords int32 [n, 4] = bx, by, bz, D; voxels float32 [n, 512, 6] = sdf, w, r, g, b, wc)."""
+        n = c_int64()
+        check(lib().dtsdf_map_export(self._h, None, None, 0, ctypes.byref(n), _stream_ptr(stream)), "export")
+        coords = np.zeros((n.value, 4), np.int32)
+        vox = np.zeros((n.value, 512, 6), np.float32)
+        if n.value:
+            check(lib().dtsdf_map_export(self._h, coords.ctypes.data_as(c_void_p), vox.ctypes.data_as(c_void_p),
+                                         n.value, ctypes.byref(n), _stream_ptr(stream)), "export")
+        return coords, vox
+
+
+def _import(self, coords, voxels, stream=None):
+    """Load bricks (coords int32 [n, 4], voxels float32 [n, 512, 6]) into the map."""
+    c = np.ascontiguousarray(coords, np.int32)
+    v = np.ascontiguousarray(voxels, np.float32)
+    assert c.shape[0] == v.shape[0] and c.shape[1:] == (4,) and v.shape[1:] == (512, 6)
+    check(lib().dtsdf_map_import(self._h, c.ctypes.data_as(c_void_p), v.ctypes.data_as(c_void_p), c.shape[0],
+                                 _stream_ptr(stream)), "dtsdf_map_import")
+
+
+Map.import_bricks = _import
+
+
+def icp_opts(levels=3, iters=(10, 5, 4), eps=(0.005, 0.05, 0.05), photo_thr=(0.05, 0.175, 0.175), lam=0.1,
+             z_min=0.1, stop_norm=1e-6, min_rows=10) -> IcpOpts:
+    it = list(iters) + [0] * (4 - len(iters))
+    ep = list(eps) + [0.05] * (4 - len(eps))
+    th = list(photo_thr) + [0.175] * (4 - len(photo_thr))
+    return IcpOpts(levels, (c_int32 * 4)(*it), (c_float * 4)(*ep), (c_float * 4)(*th), lam, z_min, stop_norm,
+                   min_rows)
+
+
+class Icp:
+    """ICP context (dtsdf_icp_create / dtsdf_icp_destroy)."""
+
+    def __init__(self, max_width: int, max_height: int, levels: int = 3):
+        h = c_void_p()
+        check(lib().dtsdf_icp_create(max_width, max_height, levels, ctypes.byref(h)), "dtsdf_icp_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().dtsdf_icp_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def set_frame(self, depth, rgb, K, z_min=0.1, z_max=6.0, delta_sup=0.01, stream=None):
+        f = Frame(depth.data_ptr(), None if rgb is None else rgb.data_ptr(), intrinsics(K))
+        check(lib().dtsdf_icp_set_frame(self._h, ctypes.byref(f), z_min, z_max, delta_sup, _stream_ptr(stream)),
+              "dtsdf_icp_set_frame")
+
+    def set_keyframe(self, rgb, K, stream=None):
+        f = Frame(None, rgb.data_ptr(), intrinsics(K))
+        check(lib().dtsdf_icp_set_keyframe(self._h, ctypes.byref(f), _stream_ptr(stream)), "dtsdf_icp_set_keyframe")
+
+    def step(self, ref_depth, ref_normals, K_ref, level, T_rel, opts: IcpOpts, sim3=False, T_rs=None, stream=None,
+             raise_on_degenerate=False):
+        """One Gauss-Newton iteration; returns (new T_rel, IcpStats)."""
+        out = RenderOut(ref_depth.data_ptr(), ref_normals.data_ptr(), None)
+        Ki = intrinsics(K_ref)
+        T = pose_buf(T_rel)
+        st = IcpStats()
+        rs = None if T_rs is None else pose_buf(T_rs)
+        fn = lib().dtsdf_icp_sim3_step if sim3 else lib().dtsdf_icp_step
+        s = fn(self._h, ctypes.byref(out), ctypes.byref(Ki), level, T, rs, ctypes.byref(opts), ctypes.byref(st),
+               _stream_ptr(stream))
+        if s != OK and (s != ERR_DEGENERATE or raise_on_degenerate):
+            check(s, "dtsdf_icp_step")
+        return np.array(T[:], np.float64).reshape(4, 4), st
+
+    def solve(self, ref_depth, ref_normals, K_ref, T_rel_dev, opts: IcpOpts, sim3=False, T_rs=None, stats_dev=None,
+              stream=None):
+        """Whole schedule on the device; T_rel_dev: float64 CUDA tensor [4, 4] updated in place."""
+        out = RenderOut(ref_depth.data_ptr(), ref_normals.data_ptr(), None)
+        Ki = intrinsics(K_ref)
+        rs = None if T_rs is None else pose_buf(T_rs)
+        check(lib().dtsdf_icp_solve(self._h, ctypes.byref(out), ctypes.byref(Ki), int(sim3), T_rel_dev.data_ptr(), rs,
+                                    ctypes.byref(opts), None if stats_dev is None else stats_dev.data_ptr(),
+                                    _stream_ptr(stream)), "dtsdf_icp_solve")
+
+
+def exp(xi) -> np.ndarray:
+    """Device exponential map (se(3) for 6 entries, sim(3) for 7)."""
+    x = np.ascontiguousarray(xi, np.float64)
+    out = np.zeros(16, np.float64)
+    check(lib().dtsdf_exp(1 if x.shape[0] == 7 else 0, x.ctypes.data_as(c_void_p), out.ctypes.data_as(c_void_p)),
+          "dtsdf_exp")
+    return out.reshape(4, 4)

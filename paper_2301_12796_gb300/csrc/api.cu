@@ -1,0 +1,632 @@
+// C ABI of libdtsdf: argument checking, device memory ownership, stream ordering and
+// status codes around the kernels of map.cu, render.cu and icp.cu.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+using namespace dtsdf;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+dtsdf_status fail(dtsdf_status s, const char* msg) {
+  g_last_error = msg;
+  return s;
+}
+
+dtsdf_status cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? DTSDF_ERR_OOM : DTSDF_ERR_CUDA;
+}
+
+#define CK(call)                                          \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+  } while (0)
+
+#define CK_LAUNCH(where)                                  \
+  do {                                                    \
+    cudaError_t e_ = cudaGetLastError();                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where);   \
+  } while (0)
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 132;
+  }
+  return n;
+}
+
+Pose32 to_pose32(const double* T) {
+  Pose32 p;
+  for (int a = 0; a < 3; ++a) {
+    for (int b = 0; b < 3; ++b) p.R[3 * a + b] = (float)T[4 * a + b];
+    p.t[a] = (float)T[4 * a + 3];
+  }
+  return p;
+}
+
+Intr to_intr(const dtsdf_intrinsics& K) {
+  Intr k;
+  k.W = K.width;
+  k.H = K.height;
+  k.fx = K.fx;
+  k.fy = K.fy;
+  k.cx = K.cx;
+  k.cy = K.cy;
+  return k;
+}
+
+bool intr_ok(const dtsdf_intrinsics* K) {
+  return K && K->width > 0 && K->height > 0 && K->width <= 16384 && K->height <= 16384 && K->fx > 0 && K->fy > 0 &&
+         isfinite(K->cx) && isfinite(K->cy);
+}
+
+bool pose_ok(const double* T) {
+  if (!T) return false;
+  for (int i = 0; i < 16; ++i)
+    if (!isfinite(T[i])) return false;
+  return true;
+}
+
+uint32_t next_pow2(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return (uint32_t)p;
+}
+
+}  // namespace
+
+struct dtsdf_map_s {
+  dtsdf_params p;
+  MapView v;
+  int frames = 0;
+  // frame scratch
+  float4* P = nullptr;
+  float4* N = nullptr;
+  size_t ws_pixels = 0;
+  // error flag mirror (pinned) and the event of its last copy
+  uint32_t* err_host = nullptr;
+  cudaEvent_t err_event = nullptr;
+  bool err_pending = false;
+};
+
+static void map_free(dtsdf_map m) {
+  if (!m) return;
+  cudaFree(m->v.keys);
+  cudaFree(m->v.vals);
+  cudaFree(m->v.req);
+  cudaFree(m->v.dir_slots);
+  cudaFree(m->v.dir_coord);
+  cudaFree(m->v.geom);
+  cudaFree(m->v.geom16);
+  cudaFree(m->v.col);
+  cudaFree(m->v.col8);
+  cudaFree(m->v.brick_dir);
+  cudaFree(m->v.counters);
+  cudaFree(m->v.work);
+  cudaFree(m->P);
+  cudaFree(m->N);
+  if (m->err_host) cudaFreeHost(m->err_host);
+  if (m->err_event) cudaEventDestroy(m->err_event);
+  delete m;
+}
+
+extern "C" {
+
+const char* dtsdf_last_error(void) { return g_last_error.c_str(); }
+
+const char* dtsdf_version(void) { return "dtsdf-gb300 0.1 (sm_103a)"; }
+
+dtsdf_status dtsdf_create(const dtsdf_params* params, void* stream, dtsdf_map* out) {
+  if (!params || !out) return fail(DTSDF_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  const dtsdf_params& p = *params;
+  if (!(p.voxel_size > 0) || !(p.truncation > 0) || !(p.theta > 0.9553166f && p.theta <= 1.5707964f) ||
+      !(p.w_max > 0) || !(p.w_carve >= 0) || !(p.z_min > 0) || !(p.z_max > p.z_min) || !(p.delta_sup > 0) ||
+      p.carve_radius < 0 || p.carve_radius > 16 || p.dense_dim < 0 || (p.dense_dim % 8) != 0 ||
+      (p.storage != DTSDF_STORE_FP32 && p.storage != DTSDF_STORE_FP16))
+    return fail(DTSDF_ERR_INVALID_ARG, "invalid map parameters");
+  uint64_t bricks = p.max_blocks;
+  int nb = 0;
+  if (p.dense_dim > 0) {
+    nb = p.dense_dim / 8;
+    if (nb > 256) return fail(DTSDF_ERR_INVALID_ARG, "dense_dim too large");
+    bricks = (uint64_t)nb * nb * nb * ND;
+  }
+  if (bricks == 0 || bricks > (1ull << 27)) return fail(DTSDF_ERR_INVALID_ARG, "max_blocks out of range");
+  cudaStream_t s = (cudaStream_t)stream;
+  dtsdf_map m = new (std::nothrow) dtsdf_map_s();
+  if (!m) return fail(DTSDF_ERR_OOM, "host allocation");
+  memset(&m->v, 0, sizeof(m->v));
+  m->p = p;
+  MapView& v = m->v;
+  v.h = p.voxel_size;
+  v.tau = p.truncation;
+  v.theta = p.theta;
+  v.wmax = p.w_max;
+  v.wcarve = p.w_carve;
+  v.zmin = p.z_min;
+  v.zmax = p.z_max;
+  v.dsup = p.delta_sup;
+  v.costh = (float)cos((double)p.theta);
+  v.ox = p.dense_origin[0];
+  v.oy = p.dense_origin[1];
+  v.oz = p.dense_origin[2];
+  v.carve_r = p.carve_radius;
+  v.dense_dim = p.dense_dim;
+  v.color = p.color ? 1 : 0;
+  v.storage = p.storage;
+  v.pool_cap = (uint32_t)bricks;
+  v.dir_cap = p.dense_dim > 0 ? (uint32_t)(nb * nb * nb) : (uint32_t)bricks;
+  const uint32_t hcap = next_pow2(2ull * v.dir_cap + 64);
+  v.hmask = hcap - 1;
+  v.work_cap = v.dir_cap;
+  cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, bytes)                                    \
+  if (e == cudaSuccess) e = cudaMalloc((void**)&(ptr), (bytes));
+  ALLOC(v.keys, sizeof(unsigned long long) * hcap);
+  ALLOC(v.vals, sizeof(int32_t) * hcap);
+  ALLOC(v.req, sizeof(uint32_t) * hcap);
+  ALLOC(v.dir_slots, sizeof(int32_t) * 8 * (size_t)v.dir_cap);
+  ALLOC(v.dir_coord, sizeof(int32_t) * 4 * (size_t)v.dir_cap);
+  if (p.storage == DTSDF_STORE_FP16) {
+    ALLOC(v.geom16, sizeof(uint32_t) * BVOX * (size_t)bricks);
+    if (p.color) ALLOC(v.col8, sizeof(uint32_t) * BVOX * (size_t)bricks);
+  } else {
+    ALLOC(v.geom, sizeof(float2) * BVOX * (size_t)bricks);
+    if (p.color) ALLOC(v.col, sizeof(float4) * BVOX * (size_t)bricks);
+  }
+  ALLOC(v.brick_dir, sizeof(int32_t) * (size_t)bricks);
+  ALLOC(v.counters, sizeof(uint32_t) * C_COUNT);
+  ALLOC(v.work, sizeof(int32_t) * (size_t)v.work_cap);
+#undef ALLOC
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&m->err_host, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->err_event, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    map_free(m);
+    return cuda_fail(e, "dtsdf_create allocation");
+  }
+  *m->err_host = 0;
+  if ((e = cudaMemsetAsync(v.keys, 0xFF, sizeof(unsigned long long) * hcap, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(v.vals, 0xFF, sizeof(int32_t) * hcap, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(v.req, 0, sizeof(uint32_t) * hcap, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(v.dir_slots, 0xFF, sizeof(int32_t) * 8 * (size_t)v.dir_cap, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(v.counters, 0, sizeof(uint32_t) * C_COUNT, s)) != cudaSuccess) {
+    map_free(m);
+    return cuda_fail(e, "dtsdf_create init");
+  }
+  // allocated-direction masks start at 0
+  {
+    // dir_slots[d*8 + 6] = 0 for all d: done by a tiny fill through the dense path or here
+    // (mask word and unused word are reset with a strided memset)
+    e = cudaMemset2DAsync(v.dir_slots + SLOT_MASK, 8 * sizeof(int32_t), 0, 2 * sizeof(int32_t), v.dir_cap, s);
+    if (e != cudaSuccess) {
+      map_free(m);
+      return cuda_fail(e, "dtsdf_create mask init");
+    }
+  }
+  launch_pool_init(v, p.color, num_sms(), s);
+  if (p.dense_dim > 0) {
+    launch_dense_fill(v, nb, s);
+    const uint32_t cnt[2] = {(uint32_t)(nb * nb * nb), (uint32_t)bricks};
+    e = cudaMemcpyAsync(v.counters, cnt, sizeof(cnt), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      map_free(m);
+      return cuda_fail(e, "dtsdf_create dense");
+    }
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    map_free(m);
+    return cuda_fail(e, "dtsdf_create kernels");
+  }
+  *out = m;
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_destroy(dtsdf_map map) {
+  if (!map) return fail(DTSDF_ERR_INVALID_ARG, "null map");
+  cudaDeviceSynchronize();
+  map_free(map);
+  return DTSDF_OK;
+}
+
+static dtsdf_status ensure_ws(dtsdf_map m, size_t npix) {
+  if (m->ws_pixels >= npix) return DTSDF_OK;
+  cudaFree(m->P);
+  cudaFree(m->N);
+  m->P = m->N = nullptr;
+  m->ws_pixels = 0;
+  CK(cudaMalloc((void**)&m->P, sizeof(float4) * npix));
+  CK(cudaMalloc((void**)&m->N, sizeof(float4) * npix));
+  m->ws_pixels = npix;
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_integrate(dtsdf_map m, const dtsdf_frame* f, const double T_wc[16], void* stream) {
+  if (!m || !f || !f->depth || !intr_ok(&f->K) || !pose_ok(T_wc)) return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  // errors flagged by earlier calls (read without stalling the stream)
+  if (m->err_pending && cudaEventQuery(m->err_event) == cudaSuccess) {
+    m->err_pending = false;
+    if (*m->err_host & (ERR_POOL_FULL | ERR_DIR_FULL | ERR_HASH_FULL | ERR_WORK_FULL))
+      return fail(DTSDF_ERR_MAP_FULL, "map capacity exhausted (max_blocks)");
+  }
+  const Intr K = to_intr(f->K);
+  const size_t npix = (size_t)K.W * K.H;
+  dtsdf_status st = ensure_ws(m, npix);
+  if (st != DTSDF_OK) return st;
+  const Pose32 T = to_pose32(T_wc);
+  launch_preprocess(f->depth, K, m->v.zmin, m->v.zmax, m->v.dsup, m->P, m->N, s);
+  CK_LAUNCH("preprocess");
+  if (m->p.dense_dim <= 0) {
+    CK(cudaMemsetAsync(m->v.counters + C_WORK, 0, sizeof(uint32_t), s));
+    launch_alloc(m->v, m->P, m->N, (int)npix, T, num_sms(), s);
+    CK_LAUNCH("alloc");
+  }
+  launch_fuse(m->v, K, T, m->P, m->N, m->p.color ? f->rgb : nullptr, num_sms(), s);
+  CK_LAUNCH("fuse");
+  if (!m->err_pending) {
+    CK(cudaMemcpyAsync(m->err_host, m->v.counters + C_ERR, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(m->err_event, s));
+    m->err_pending = true;
+  }
+  m->frames++;
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_render(dtsdf_map m, const dtsdf_intrinsics* K, const double T_wc[16], const dtsdf_render_out* out,
+                          void* stream) {
+  if (!m || !intr_ok(K) || !pose_ok(T_wc) || !out || !out->depth || !out->normals)
+    return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  launch_render(m->v, to_intr(*K), to_pose32(T_wc), out->depth, (float4*)out->normals, (float4*)out->color,
+                (cudaStream_t)stream);
+  CK_LAUNCH("render");
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_map_stats(dtsdf_map m, dtsdf_map_stats_t* st, void* stream) {
+  if (!m || !st) return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t c[C_COUNT];
+  CK(cudaMemcpyAsync(c, m->v.counters, sizeof(c), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  memset(st, 0, sizeof(*st));
+  const uint32_t nb = c[C_POOL] < m->v.pool_cap ? c[C_POOL] : m->v.pool_cap;
+  st->bricks = nb;
+  st->blocks = c[C_DIR] < m->v.dir_cap ? c[C_DIR] : m->v.dir_cap;
+  st->capacity = m->v.pool_cap;
+  st->error_flags = c[C_ERR];
+  st->frames = m->frames;
+  if (nb) {
+    int32_t* bd = new (std::nothrow) int32_t[nb];
+    if (!bd) return fail(DTSDF_ERR_OOM, "host allocation");
+    cudaError_t e = cudaMemcpy(bd, m->v.brick_dir, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      delete[] bd;
+      return cuda_fail(e, "map_stats");
+    }
+    for (uint32_t i = 0; i < nb; ++i) st->bricks_per_dir[bd[i] & 7]++;
+    delete[] bd;
+  }
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_map_export(dtsdf_map m, int32_t* coords, float* voxels, int64_t cap, int64_t* n_out,
+                              void* stream) {
+  if (!m || !n_out || cap < 0 || (cap > 0 && (!coords || !voxels))) return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t cnt = 0;
+  CK(cudaMemcpyAsync(&cnt, m->v.counters + C_POOL, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const int64_t nb = cnt < m->v.pool_cap ? cnt : m->v.pool_cap;
+  *n_out = nb;
+  const int64_t n = nb < cap ? nb : cap;
+  if (n == 0) return DTSDF_OK;
+  int32_t* dc = nullptr;
+  float* dv = nullptr;
+  cudaError_t e = cudaMalloc((void**)&dc, sizeof(int32_t) * 4 * n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dv, sizeof(float) * 6 * BVOX * n);
+  if (e == cudaSuccess) {
+    launch_export(m->v, n, dc, dv, num_sms(), s);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(coords, dc, sizeof(int32_t) * 4 * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(voxels, dv, sizeof(float) * 6 * BVOX * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(dc);
+  cudaFree(dv);
+  if (e != cudaSuccess) return cuda_fail(e, "map_export");
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_map_import(dtsdf_map m, const int32_t* coords, const float* voxels, int64_t n, void* stream) {
+  if (!m || n < 0 || (n > 0 && (!coords || !voxels)) || n > (int64_t)m->v.pool_cap)
+    return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  for (int64_t i = 0; i < n; ++i)
+    if (coords[4 * i + 3] < 0 || coords[4 * i + 3] >= ND) return fail(DTSDF_ERR_INVALID_ARG, "direction out of range");
+  if (n == 0) return DTSDF_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t* dc = nullptr;
+  float* dv = nullptr;
+  cudaError_t e = cudaMalloc((void**)&dc, sizeof(int32_t) * 4 * n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dv, sizeof(float) * 6 * BVOX * n);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dc, coords, sizeof(int32_t) * 4 * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dv, voxels, sizeof(float) * 6 * BVOX * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && m->p.dense_dim <= 0) e = cudaMemsetAsync(m->v.counters + C_WORK, 0, sizeof(uint32_t), s);
+  if (e == cudaSuccess) {
+    launch_import(m->v, dc, dv, n, m->p.dense_dim <= 0, num_sms(), s);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(dc);
+  cudaFree(dv);
+  if (e != cudaSuccess) return cuda_fail(e, "map_import");
+  uint32_t flags = 0;
+  e = cudaMemcpy(&flags, m->v.counters + C_ERR, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "map_import");
+  if (flags) return fail(DTSDF_ERR_MAP_FULL, "map capacity exhausted during import");
+  return DTSDF_OK;
+}
+
+}  // extern "C"
+
+// =================================================================== ICP ====
+
+struct dtsdf_icp_s {
+  int max_w = 0, max_h = 0, levels = 0;
+  Intr K[4];
+  Intr Kkf[4];
+  bool has_frame = false, has_rgb = false, has_kf = false;
+  float* depth[4] = {nullptr, nullptr, nullptr, nullptr};
+  float* inten[4] = {nullptr, nullptr, nullptr, nullptr};
+  float* kf_tmp[4] = {nullptr, nullptr, nullptr, nullptr};
+  float4* kf[4] = {nullptr, nullptr, nullptr, nullptr};
+  float4* P = nullptr;
+  float4* N = nullptr;
+  float* partials = nullptr;
+  int grid = 0;
+  double* pose = nullptr;
+  dtsdf_icp_stats* stats = nullptr;
+  uint32_t* ticket = nullptr;
+  int32_t* stop = nullptr;
+  double* host_pose = nullptr;
+  dtsdf_icp_stats* host_stats = nullptr;
+};
+
+static void icp_free(dtsdf_icp c) {
+  if (!c) return;
+  for (int l = 0; l < 4; ++l) {
+    cudaFree(c->depth[l]);
+    cudaFree(c->inten[l]);
+    cudaFree(c->kf_tmp[l]);
+    cudaFree(c->kf[l]);
+  }
+  cudaFree(c->P);
+  cudaFree(c->N);
+  cudaFree(c->partials);
+  cudaFree(c->pose);
+  cudaFree(c->stats);
+  cudaFree(c->ticket);
+  cudaFree(c->stop);
+  if (c->host_pose) cudaFreeHost(c->host_pose);
+  if (c->host_stats) cudaFreeHost(c->host_stats);
+  delete c;
+}
+
+static Intr level_intr(Intr k, int level) {
+  for (int l = 0; l < level; ++l) {
+    Intr n;
+    n.W = k.W / 2;
+    n.H = k.H / 2;
+    n.fx = k.fx / 2.0f;
+    n.fy = k.fy / 2.0f;
+    n.cx = (k.cx - 0.5f) / 2.0f;
+    n.cy = (k.cy - 0.5f) / 2.0f;
+    k = n;
+  }
+  return k;
+}
+
+extern "C" {
+
+dtsdf_status dtsdf_icp_create(int32_t max_width, int32_t max_height, int32_t levels, dtsdf_icp* out) {
+  if (!out || max_width < 8 || max_height < 8 || max_width > 16384 || max_height > 16384 || levels < 1 || levels > 4)
+    return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  *out = nullptr;
+  dtsdf_icp c = new (std::nothrow) dtsdf_icp_s();
+  if (!c) return fail(DTSDF_ERR_OOM, "host allocation");
+  c->max_w = max_width;
+  c->max_h = max_height;
+  c->levels = levels;
+  cudaError_t e = cudaSuccess;
+  const size_t n0 = (size_t)max_width * max_height;
+  for (int l = 0; l < levels && e == cudaSuccess; ++l) {
+    const size_t n = (size_t)(max_width >> l) * (max_height >> l);
+    e = cudaMalloc((void**)&c->depth[l], sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->inten[l], sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->kf_tmp[l], sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->kf[l], sizeof(float4) * n);
+  }
+  c->grid = num_sms() * 2;
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->P, sizeof(float4) * n0);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->N, sizeof(float4) * n0);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->partials, sizeof(float) * 64 * c->grid);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->pose, sizeof(double) * 16);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->stats, sizeof(dtsdf_icp_stats));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->ticket, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->stop, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->host_pose, sizeof(double) * 16);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->host_stats, sizeof(dtsdf_icp_stats));
+  if (e == cudaSuccess) e = cudaMemset(c->ticket, 0, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(c->stop, 0, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(c->stats, 0, sizeof(dtsdf_icp_stats));
+  if (e != cudaSuccess) {
+    icp_free(c);
+    return cuda_fail(e, "dtsdf_icp_create");
+  }
+  *out = c;
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_icp_destroy(dtsdf_icp c) {
+  if (!c) return fail(DTSDF_ERR_INVALID_ARG, "null context");
+  cudaDeviceSynchronize();
+  icp_free(c);
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_icp_set_frame(dtsdf_icp c, const dtsdf_frame* f, float z_min, float z_max, float delta_sup,
+                                 void* stream) {
+  if (!c || !f || !f->depth || !intr_ok(&f->K) || f->K.width > c->max_w || f->K.height > c->max_h ||
+      !(z_min > 0) || !(z_max > z_min) || !(delta_sup > 0))
+    return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Intr K0 = to_intr(f->K);
+  for (int l = 0; l < c->levels; ++l) c->K[l] = level_intr(K0, l);
+  launch_preprocess(f->depth, K0, z_min, z_max, delta_sup, c->P, c->N, s);
+  launch_frame_pyramid(c->P, f->rgb, c->levels, c->K, c->depth, c->inten, s);
+  CK_LAUNCH("icp_set_frame");
+  c->has_frame = true;
+  c->has_rgb = f->rgb != nullptr;
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_icp_set_keyframe(dtsdf_icp c, const dtsdf_frame* f, void* stream) {
+  if (!c || !f || !f->rgb || !intr_ok(&f->K) || f->K.width > c->max_w || f->K.height > c->max_h)
+    return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  const Intr K0 = to_intr(f->K);
+  for (int l = 0; l < c->levels; ++l) c->Kkf[l] = level_intr(K0, l);
+  launch_keyframe_pyramid(f->rgb, c->levels, c->Kkf, c->kf_tmp, c->kf, (cudaStream_t)stream);
+  CK_LAUNCH("icp_set_keyframe");
+  c->has_kf = true;
+  return DTSDF_OK;
+}
+
+static bool opts_ok(const dtsdf_icp_opts* o, int levels) {
+  if (!o || o->levels < 1 || o->levels > levels || !(o->z_min > 0) || !(o->stop_norm >= 0) || o->min_rows < 0)
+    return false;
+  for (int l = 0; l < o->levels; ++l)
+    if (o->iters[l] < 0 || o->iters[l] > 1000 || !(o->eps[l] > 0) || !(o->photo_thr[l] >= 0)) return false;
+  return true;
+}
+
+static void fill_launch(dtsdf_icp c, IcpLaunch& L, const dtsdf_render_out* ref, const dtsdf_intrinsics* K_ref, int level,
+                        const double* T_rs, const dtsdf_icp_opts* o, bool& photo) {
+  L.depth = c->depth[level];
+  L.inten = c->inten[level];
+  L.K = c->K[level];
+  L.ref = (const float4*)ref->normals;
+  L.Kr = to_intr(*K_ref);
+  L.eps = o->eps[level];
+  L.zmin = o->z_min;
+  photo = T_rs && o->lambda > 0 && c->has_kf && c->has_rgb;
+  L.kf = c->kf[level];
+  L.Kk = c->Kkf[level];
+  for (int i = 0; i < 9; ++i) L.Rrs[i] = 0.f;
+  for (int i = 0; i < 3; ++i) L.trs[i] = 0.f;
+  if (photo) {
+    for (int a = 0; a < 3; ++a) {
+      for (int b = 0; b < 3; ++b) L.Rrs[3 * a + b] = (float)T_rs[4 * a + b];
+      L.trs[a] = (float)T_rs[4 * a + 3];
+    }
+  }
+  L.thr = o->photo_thr[level];
+  L.lambda = o->lambda;
+  L.pose = c->pose;
+  L.partials = c->partials;
+  L.ticket = c->ticket;
+  L.stop = c->stop;
+  L.stats = c->stats;
+  L.min_rows = o->min_rows;
+  L.stop_norm = o->stop_norm;
+}
+
+static dtsdf_status icp_step_impl(dtsdf_icp c, const dtsdf_render_out* ref, const dtsdf_intrinsics* K_ref, int level,
+                                  double* T_rel, const double* T_rs, const dtsdf_icp_opts* o, dtsdf_icp_stats* stats,
+                                  void* stream, int sim3) {
+  if (!c || !ref || !ref->normals || !intr_ok(K_ref) || !pose_ok(T_rel) || !opts_ok(o, c->levels) || level < 0 ||
+      level >= o->levels || !c->has_frame)
+    return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  memcpy(c->host_pose, T_rel, sizeof(double) * 16);
+  CK(cudaMemcpyAsync(c->pose, c->host_pose, sizeof(double) * 16, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(c->stop, 0, sizeof(int32_t), s));
+  CK(cudaMemsetAsync(c->stats, 0, sizeof(dtsdf_icp_stats), s));
+  IcpLaunch L;
+  bool photo = false;
+  fill_launch(c, L, ref, K_ref, level, T_rs, o, photo);
+  launch_icp(L, sim3, photo, c->grid, s);
+  CK_LAUNCH("icp_step");
+  CK(cudaMemcpyAsync(c->host_pose, c->pose, sizeof(double) * 16, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->host_stats, c->stats, sizeof(dtsdf_icp_stats), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  memcpy(T_rel, c->host_pose, sizeof(double) * 16);
+  if (stats) *stats = *c->host_stats;
+  if (c->host_stats->status == DTSDF_ERR_DEGENERATE) return fail(DTSDF_ERR_DEGENERATE, "degenerate normal equations");
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_icp_step(dtsdf_icp c, const dtsdf_render_out* ref, const dtsdf_intrinsics* K_ref, int32_t level,
+                            double T_rel[16], const double* T_rs, const dtsdf_icp_opts* o, dtsdf_icp_stats* stats,
+                            void* stream) {
+  return icp_step_impl(c, ref, K_ref, level, T_rel, T_rs, o, stats, stream, 0);
+}
+
+dtsdf_status dtsdf_icp_sim3_step(dtsdf_icp c, const dtsdf_render_out* ref, const dtsdf_intrinsics* K_ref,
+                                 int32_t level, double T_rel[16], const double* T_rs, const dtsdf_icp_opts* o,
+                                 dtsdf_icp_stats* stats, void* stream) {
+  return icp_step_impl(c, ref, K_ref, level, T_rel, T_rs, o, stats, stream, 1);
+}
+
+dtsdf_status dtsdf_icp_solve(dtsdf_icp c, const dtsdf_render_out* ref, const dtsdf_intrinsics* K_ref, int32_t sim3,
+                             double* T_rel_dev, const double* T_rs, const dtsdf_icp_opts* o,
+                             dtsdf_icp_stats* stats_dev, void* stream) {
+  if (!c || !ref || !ref->normals || !intr_ok(K_ref) || !T_rel_dev || !opts_ok(o, c->levels) || !c->has_frame ||
+      (sim3 != 0 && sim3 != 1))
+    return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(c->pose, T_rel_dev, sizeof(double) * 16, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(c->stats, 0, sizeof(dtsdf_icp_stats), s));
+  for (int l = o->levels - 1; l >= 0; --l) {
+    CK(cudaMemsetAsync(c->stop, 0, sizeof(int32_t), s));
+    IcpLaunch L;
+    bool photo = false;
+    fill_launch(c, L, ref, K_ref, l, T_rs, o, photo);
+    for (int it = 0; it < o->iters[l]; ++it) launch_icp(L, sim3, photo, c->grid, s);
+    CK_LAUNCH("icp_solve");
+  }
+  CK(cudaMemcpyAsync(T_rel_dev, c->pose, sizeof(double) * 16, cudaMemcpyDeviceToDevice, s));
+  if (stats_dev) CK(cudaMemcpyAsync(stats_dev, c->stats, sizeof(dtsdf_icp_stats), cudaMemcpyDeviceToDevice, s));
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_exp(int32_t sim3, const double* xi, double out[16]) {
+  if (!xi || !out || (sim3 != 0 && sim3 != 1)) return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  double* d = nullptr;
+  CK(cudaMalloc((void**)&d, sizeof(double) * 23));
+  cudaError_t e = cudaMemcpy(d, xi, sizeof(double) * (sim3 ? 7 : 6), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    launch_exp(sim3 ? 7 : 6, d, d + 7, 0);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, d + 7, sizeof(double) * 16, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "dtsdf_exp");
+  return DTSDF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+// Shared device-side definitions of libdtsdf (sm_103a).
+//
+// Decision paths (which pixel a voxel projects to, which blocks a segment crosses,
+// band and membership tests, projective association) use explicitly rounded
+// single-precision operations (__fmul_rn & co.), which the compiler never fuses
+// into FMAs, so that every such integer/boolean outcome is a fixed function of
+// the float inputs. Value paths use ordinary FP32 arithmetic.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dtsdf.h"
+
+namespace dtsdf {
+
+constexpr int ND = 6;          // directions X+, X-, Y+, Y-, Z+, Z- (Sec. 3)
+constexpr int BVOX = 512;      // voxels per 8^3 block (Sec. 6)
+constexpr unsigned long long EMPTY_KEY = ~0ull;
+constexpr int MAX_PROBE = 256;  // linear-probe bound; the table is kept at most half full
+constexpr int SLOT_MASK = 6;    // dir_slots[d * 8 + 6]: bitmask of allocated directions
+
+// error flags (MapView::counters[C_ERR])
+constexpr uint32_t ERR_POOL_FULL = 1u;
+constexpr uint32_t ERR_DIR_FULL = 2u;
+constexpr uint32_t ERR_HASH_FULL = 4u;
+constexpr uint32_t ERR_WORK_FULL = 8u;
+
+// device counters
+enum { C_DIR = 0, C_POOL = 1, C_WORK = 2, C_ERR = 3, C_DIR_BEFORE = 4, C_POOL_BEFORE = 5, C_COUNT = 8 };
+
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float rsqrt_exact(float a) { return __fsqrt_rn(a); }
+
+// ((a0*b0 + a1*b1) + a2*b2), each step rounded
+__device__ __forceinline__ float rdot3(float a0, float a1, float a2, float b0, float b1, float b2) {
+  return radd(radd(rmul(a0, b0), rmul(a1, b1)), rmul(a2, b2));
+}
+
+struct Pose32 {
+  float R[9];  // row-major rotation (or s R) of camera -> world
+  float t[3];
+};
+
+struct Intr {
+  int W, H;
+  float fx, fy, cx, cy;
+};
+
+// Single-precision rounded rotation: y_a = (R[a0] x0 + R[a1] x1) + R[a2] x2
+__device__ __forceinline__ void rrot(const float* R, float x0, float x1, float x2, float& y0, float& y1, float& y2) {
+  y0 = rdot3(R[0], R[1], R[2], x0, x1, x2);
+  y1 = rdot3(R[3], R[4], R[5], x0, x1, x2);
+  y2 = rdot3(R[6], R[7], R[8], x0, x1, x2);
+}
+
+// Transposed rotation (world -> camera of a camera -> world R): y_a = (R[0a] x0 + R[1a] x1) + R[2a] x2
+__device__ __forceinline__ void rrotT(const float* R, float x0, float x1, float x2, float& y0, float& y1,
+                                      float& y2) {
+  y0 = rdot3(R[0], R[3], R[6], x0, x1, x2);
+  y1 = rdot3(R[1], R[4], R[7], x0, x1, x2);
+  y2 = rdot3(R[2], R[5], R[8], x0, x1, x2);
+}
+
+__device__ __forceinline__ bool depth_in_range(float z, float zmin, float zmax) {
+  return z > 0.0f && z >= zmin && z <= zmax;
+}
+
+// ---------------------------------------------------------------- hash ----
+__host__ __device__ __forceinline__ unsigned long long pack_block(int bx, int by, int bz) {
+  return ((unsigned long long)((uint32_t)(bx + (1 << 20)) & 0x1FFFFFu) << 42) |
+         ((unsigned long long)((uint32_t)(by + (1 << 20)) & 0x1FFFFFu) << 21) |
+         (unsigned long long)((uint32_t)(bz + (1 << 20)) & 0x1FFFFFu);
+}
+
+__host__ __device__ __forceinline__ void unpack_block(unsigned long long k, int& bx, int& by, int& bz) {
+  bx = (int)((k >> 42) & 0x1FFFFFu) - (1 << 20);
+  by = (int)((k >> 21) & 0x1FFFFFu) - (1 << 20);
+  bz = (int)(k & 0x1FFFFFu) - (1 << 20);
+}
+
+__host__ __device__ __forceinline__ uint32_t hash_slot(unsigned long long k, uint32_t mask) {
+  k ^= k >> 31;
+  k *= 0x7fb5d329728ea185ull;
+  k ^= k >> 27;
+  k *= 0x81dadef4bc2dd44dull;
+  k ^= k >> 33;
+  return (uint32_t)k & mask;
+}
+
+// Device view of a map, passed by value to kernels.
+struct MapView {
+  float h, tau, theta, wmax, wcarve, zmin, zmax, dsup, costh;
+  float ox, oy, oz;
+  int carve_r, dense_dim, color, storage;
+  // hash: block coordinate -> directory index
+  unsigned long long* keys;
+  int32_t* vals;
+  uint32_t* req;  // per hash slot: directions requested this frame
+  uint32_t hmask;
+  // directory: 8 ints per entry: slots of the 6 directions, allocated mask, unused
+  int32_t* dir_slots;
+  int32_t* dir_coord;  // 4 ints per entry: bx, by, bz, 0
+  uint32_t dir_cap;
+  // brick pool
+  float2* geom;     // FP32: (sdf, weight) per voxel
+  uint32_t* geom16; // FP16: half sdf | u16 weight (1/256 units) per voxel
+  float4* col;      // FP32: (r, g, b, colour weight)
+  uint32_t* col8;   // FP16 storage: u8 r, g, b, u8 colour weight (1/ (255/w_max) units)
+  int32_t* brick_dir;  // per brick: dir index * 8 + D
+  uint32_t pool_cap;
+  uint32_t* counters;
+  int32_t* work;
+  uint32_t work_cap;
+};
+
+__device__ __forceinline__ int hash_find(const MapView& m, int bx, int by, int bz) {
+  const unsigned long long k = pack_block(bx, by, bz);
+  uint32_t i = hash_slot(k, m.hmask);
+#pragma unroll 1
+  for (int p = 0; p < MAX_PROBE; ++p) {
+    const unsigned long long kk = __ldg(m.keys + i);
+    if (kk == k) return __ldg(m.vals + i);
+    if (kk == EMPTY_KEY) return -1;
+    i = (i + 1) & m.hmask;
+  }
+  return -1;
+}
+
+// Storage accessors ---------------------------------------------------------
+// FP16 form: sdf as IEEE half, weight as an unsigned 16-bit count of 1/256 units.
+constexpr float W16_SCALE = 256.0f;
+
+__device__ __forceinline__ float2 unpack_geom16(uint32_t v) {
+  __half_raw hr;
+  hr.x = (unsigned short)(v & 0xFFFFu);
+  const float sdf = __half2float(__half(hr));
+  const float w = (float)(v >> 16) * (1.0f / W16_SCALE);
+  return make_float2(sdf, w);
+}
+
+__device__ __forceinline__ uint32_t pack_geom16(float sdf, float w) {
+  const __half hs = __float2half_rn(sdf);
+  const __half_raw hr = hs;
+  float q = rintf(w * W16_SCALE);
+  q = fminf(fmaxf(q, 0.0f), 65535.0f);
+  return (uint32_t)hr.x | ((uint32_t)q << 16);
+}
+
+}  // namespace dtsdf

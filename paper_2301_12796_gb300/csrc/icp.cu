@@ -1,0 +1,502 @@
+// Point-to-plane ICP in SE(3) and Sim(3) with the frame-to-keyframe photometric term
+// (Sec. 5, 5.2, 5.3; Sec. 6 pyramid; Sec. 7 thresholds).
+//
+// One launch = one Gauss-Newton iteration: a persistent grid (2 CTAs per SM) walks the
+// pixels of the current pyramid level grid-stride, forms each pixel's point-to-plane row
+// (and photometric row) in registers, accumulates w J J^T (upper triangle), w J r, w r^2
+// and the row counts in FP32, reduces them by warp shuffles and across warps in a fixed
+// order, and stores one partial per CTA. The last CTA to finish (atomic ticket) adds the
+// partials in FP64 in CTA order - so the result is bitwise reproducible - then one
+// thread solves H xi = -g by FP64 Cholesky and applies dT <- exp(xi) dT on the device.
+#include <math.h>
+
+#include "internal.h"
+
+namespace dtsdf {
+
+constexpr int ICP_THREADS = 256;
+
+// ------------------------------------------------------------- pyramid ----
+__global__ void k_extract_depth(const float4* __restrict__ P, int n, float* __restrict__ d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float4 p = P[i];
+    d[i] = p.w > 0 ? p.z : 0.0f;
+  }
+}
+
+__global__ void k_intensity(const uint8_t* __restrict__ rgb, int n, float* __restrict__ I) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float r = rgb[3 * i], g = rgb[3 * i + 1], b = rgb[3 * i + 2];
+    I[i] = rdiv(radd(radd(rmul(0.299f, r), rmul(0.587f, g)), rmul(0.114f, b)), 255.0f);
+  }
+}
+
+// 2x2 mean of the valid children in the order (0,0), (1,0), (0,1), (1,1); plain 2x2 mean of intensity.
+__global__ void k_down(const float* __restrict__ din, const float* __restrict__ Iin, int Win, int Wout, int Hout,
+                       float* __restrict__ dout, float* __restrict__ Iout) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y * blockDim.y + threadIdx.y;
+  if (u >= Wout || v >= Hout) return;
+  const int i00 = (2 * v) * Win + 2 * u;
+  const float c[4] = {din[i00], din[i00 + 1], din[i00 + Win], din[i00 + Win + 1]};
+  float s = 0.0f;
+  int n = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (c[q] > 0.0f) {
+      s = radd(s, c[q]);
+      ++n;
+    }
+  dout[v * Wout + u] = n ? rdiv(s, (float)n) : 0.0f;
+  if (Iin) Iout[v * Wout + u] = 0.25f * (Iin[i00] + Iin[i00 + 1] + Iin[i00 + Win] + Iin[i00 + Win + 1]);
+}
+
+__global__ void k_down_intensity(const float* __restrict__ Iin, int Win, int Wout, int Hout, float* __restrict__ Iout) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y * blockDim.y + threadIdx.y;
+  if (u >= Wout || v >= Hout) return;
+  const int i00 = (2 * v) * Win + 2 * u;
+  Iout[v * Wout + u] = 0.25f * (Iin[i00] + Iin[i00 + 1] + Iin[i00 + Win] + Iin[i00 + Win + 1]);
+}
+
+// Keyframe level: (I, dI/du, dI/dv, 0) with central differences / 2, zero on the border.
+__global__ void k_kf_grad(const float* __restrict__ I, int W, int H, float4* __restrict__ out) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y * blockDim.y + threadIdx.y;
+  if (u >= W || v >= H) return;
+  const int i = v * W + u;
+  const float gx = (u >= 1 && u < W - 1) ? 0.5f * (I[i + 1] - I[i - 1]) : 0.0f;
+  const float gy = (v >= 1 && v < H - 1) ? 0.5f * (I[i + W] - I[i - W]) : 0.0f;
+  out[i] = make_float4(I[i], gx, gy, 0.0f);
+}
+
+// ------------------------------------------------------------- FP64 math --
+__device__ void mat4_mul(const double* A, const double* B, double* C) {
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double s = 0;
+      for (int k = 0; k < 4; ++k) s += A[4 * i + k] * B[4 * k + j];
+      C[4 * i + j] = s;
+    }
+}
+
+// Exponential of the 4x4 generator [[omega^ + sigma I, nu], [0, 0]]:
+//   upper block e^sigma exp(omega^) (Rodrigues), translation V nu with
+//   V = A I + B omega^ + C omega^2, A = int_0^1 e^{s sigma} ds,
+//   B = (1/th) int_0^1 e^{s sigma} sin(s th) ds, C = (1/th^2) (A - int_0^1 e^{s sigma} cos(s th) ds),
+// with series where th or sigma vanish.
+__host__ __device__ void exp_sim3(const double* xi, int dim, double* T) {
+  const double nu0 = xi[0], nu1 = xi[1], nu2 = xi[2];
+  const double w0 = xi[3], w1 = xi[4], w2 = xi[5];
+  const double sg = dim == 7 ? xi[6] : 0.0;
+  const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
+  const double th = sqrt(th2);
+  double a, b;  // Rodrigues coefficients sin(th)/th, (1 - cos th)/th^2
+  if (th < 1e-4) {
+    a = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
+    b = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+  } else {
+    a = sin(th) / th;
+    b = (1.0 - cos(th)) / th2;
+  }
+  const double es = exp(sg);
+  const double A = sg != 0.0 ? expm1(sg) / sg : 1.0;
+  double B, C;
+  if (th < 1e-4) {
+    // expansions of the integrals in th (exact in sigma), leading orders
+    double I1, I2, I3;  // int s e^{s sg}, int s^2 e^{s sg} / 2, int s^3 e^{s sg} / 6 over [0, 1]
+    if (fabs(sg) < 1e-2) {
+      // sum_n sg^n / (n! (n + k)) with k = 2, 3, 4
+      double t = 1.0;
+      I1 = I2 = I3 = 0.0;
+      for (int n = 0; n < 6; ++n) {
+        I1 += t / (n + 2);
+        I2 += t / (2.0 * (n + 3));
+        I3 += t / (6.0 * (n + 4));
+        t *= sg / (n + 1);
+      }
+    } else {
+      const double s2 = sg * sg, s3 = s2 * sg, s4 = s3 * sg;
+      I1 = ((sg - 1.0) * es + 1.0) / s2;
+      I2 = ((s2 - 2.0 * sg + 2.0) * es - 2.0) / (2.0 * s3);
+      I3 = ((s3 - 3.0 * s2 + 6.0 * sg - 6.0) * es + 6.0) / (6.0 * s4);
+    }
+    // sin(s th)/th = s - th^2 s^3/6 + ..., (1 - cos(s th))/th^2 = s^2/2 - ...
+    B = I1 - th2 * I3;
+    C = I2;
+  } else {
+    const double D = sg * sg + th2;
+    const double Is = (es * (sg * sin(th) - th * cos(th)) + th) / D;
+    const double Ic = (es * (sg * cos(th) + th * sin(th)) - sg) / D;
+    B = Is / th;
+    C = (A - Ic) / th2;
+  }
+  // omega^ and omega^2
+  const double W[9] = {0, -w2, w1, w2, 0, -w0, -w1, w0, 0};
+  double W2[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) W2[3 * i + j] = W[3 * i] * W[j] + W[3 * i + 1] * W[3 + j] + W[3 * i + 2] * W[6 + j];
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) {
+      const double id = i == j ? 1.0 : 0.0;
+      T[4 * i + j] = es * (id + a * W[3 * i + j] + b * W2[3 * i + j]);
+    }
+    const double V0 = A * (i == 0) + B * W[3 * i] + C * W2[3 * i];
+    const double V1 = A * (i == 1) + B * W[3 * i + 1] + C * W2[3 * i + 1];
+    const double V2 = A * (i == 2) + B * W[3 * i + 2] + C * W2[3 * i + 2];
+    T[4 * i + 3] = V0 * nu0 + V1 * nu1 + V2 * nu2;
+  }
+  T[12] = T[13] = T[14] = 0.0;
+  T[15] = 1.0;
+}
+
+__global__ void k_exp(int dim, const double* xi, double* T) { exp_sim3(xi, dim, T); }
+
+// ---------------------------------------------------------- reduction -----
+struct IcpArgs {
+  // current level
+  const float* depth;
+  const float* inten;
+  int W, H;
+  float fx, fy, cx, cy;
+  // reference render (full resolution)
+  const float4* ref;  // normal xyz, w = depth
+  int rW, rH;
+  float rfx, rfy, rcx, rcy;
+  float eps, zmin;
+  // photometric
+  const float4* kf;  // (I, gx, gy, 0) at this level
+  int kW, kH;
+  float kfx, kfy, kcx, kcy;
+  float Rrs[9], trs[3];
+  float thr, lambda;
+  // state
+  double* pose;
+  float* partials;
+  uint32_t* ticket;
+  int32_t* stop;
+  dtsdf_icp_stats* stats;
+  int min_rows;
+  double stop_norm;
+};
+
+template <int DIM>
+struct Acc {
+  static constexpr int NH = DIM * (DIM + 1) / 2;
+  static constexpr int N = NH + DIM + 3;  // H upper, g, E, rows_geo, rows_photo
+  float v[N];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = 0.f;
+  }
+  __device__ __forceinline__ void row(const float J[DIM], float r, float w) {
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      const float wj = w * J[i];
+#pragma unroll
+      for (int j = i; j < DIM; ++j) v[k++] += wj * J[j];
+      v[NH + i] += wj * r;
+    }
+    v[NH + DIM] += w * r * r;
+  }
+};
+
+template <int DIM, bool PHOTO>
+__global__ void __launch_bounds__(ICP_THREADS) k_icp(IcpArgs a) {
+  using A = Acc<DIM>;
+  __shared__ float s_red[ICP_THREADS / 32][A::N];
+  __shared__ double s_sum[A::N];
+  __shared__ int s_last;
+  if (*((volatile int32_t*)a.stop)) return;  // level finished (converged or degenerate)
+
+  // current estimate: x = p + ((A p) + t), A = sR - I (single precision, rounded)
+  float Am[9], tv[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Am[3 * i + j] = (float)(a.pose[4 * i + j] - (i == j ? 1.0 : 0.0));
+    tv[i] = (float)a.pose[4 * i + 3];
+  }
+  A acc;
+  acc.zero();
+  const int n = a.W * a.H;
+  const float eps2 = rmul(a.eps, a.eps);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const float z = __ldg(a.depth + p);
+    if (!(z > 0.0f)) continue;
+    const int u = p % a.W, v = p / a.W;
+    const float P0 = rmul(z, rdiv(rsub((float)u, a.cx), a.fx));
+    const float P1 = rmul(z, rdiv(rsub((float)v, a.cy), a.fy));
+    const float P2 = z;
+    const float d0 = radd(rdot3(Am[0], Am[1], Am[2], P0, P1, P2), tv[0]);
+    const float d1 = radd(rdot3(Am[3], Am[4], Am[5], P0, P1, P2), tv[1]);
+    const float d2 = radd(rdot3(Am[6], Am[7], Am[8], P0, P1, P2), tv[2]);
+    const float x0 = radd(P0, d0), x1 = radd(P1, d1), x2 = radd(P2, d2);
+    const float zw = z + 1.0f - a.zmin;
+    const float wz = 1.0f / (zw * zw);  // Eq. ICP_weight
+    if (x2 > 0.0f) {
+      // projective association into the full-resolution render, nearest pixel
+      const float uf = radd(rmul(rdiv(x0, x2), a.rfx), a.rcx);
+      const float vf = radd(rmul(rdiv(x1, x2), a.rfy), a.rcy);
+      const float ur = floorf(radd(uf, 0.5f)), vr = floorf(radd(vf, 0.5f));
+      if (ur >= 0.0f && vr >= 0.0f && ur < (float)a.rW && vr < (float)a.rH) {
+        const float4 nq = __ldg(a.ref + (int)vr * a.rW + (int)ur);
+        const float dr = nq.w;
+        if (dr > 0.0f) {
+          const float q0 = rmul(dr, rdiv(rsub(ur, a.rcx), a.rfx));
+          const float q1 = rmul(dr, rdiv(rsub(vr, a.rcy), a.rfy));
+          const float q2 = dr;
+          const float e0 = rsub(q0, x0), e1 = rsub(q1, x1), e2 = rsub(q2, x2);
+          if (rdot3(e0, e1, e2, e0, e1, e2) <= eps2) {
+            // r = <q - x, n> evaluated as <(q - p) - delta, n> (no cancellation of metre-sized terms)
+            const float r = ((q0 - P0) - d0) * nq.x + ((q1 - P1) - d1) * nq.y + ((q2 - P2) - d2) * nq.z;
+            float J[DIM];
+            J[0] = -nq.x;
+            J[1] = -nq.y;
+            J[2] = -nq.z;
+            J[3] = -(x1 * nq.z - x2 * nq.y);
+            J[4] = -(x2 * nq.x - x0 * nq.z);
+            J[5] = -(x0 * nq.y - x1 * nq.x);
+            if (DIM == 7) J[DIM - 1] = -(nq.x * x0 + nq.y * x1 + nq.z * x2);
+            acc.row(J, r, wz);
+            acc.v[A::N - 2] += 1.0f;
+          }
+        }
+      }
+    }
+    if (PHOTO) {
+      // frame-to-keyframe photometric row (Eq. keyframe_icp), y = T_rs x
+      const float y0 = radd(rdot3(a.Rrs[0], a.Rrs[1], a.Rrs[2], x0, x1, x2), a.trs[0]);
+      const float y1 = radd(rdot3(a.Rrs[3], a.Rrs[4], a.Rrs[5], x0, x1, x2), a.trs[1]);
+      const float y2 = radd(rdot3(a.Rrs[6], a.Rrs[7], a.Rrs[8], x0, x1, x2), a.trs[2]);
+      if (y2 > 0.0f) {
+        const float uk = radd(rmul(rdiv(y0, y2), a.kfx), a.kcx);
+        const float vk = radd(rmul(rdiv(y1, y2), a.kfy), a.kcy);
+        if (uk >= 1.0f && vk >= 1.0f && uk < (float)(a.kW - 2) && vk < (float)(a.kH - 2)) {
+          const float fu = floorf(uk), fv = floorf(vk);
+          const int iu = (int)fu, iv = (int)fv;
+          const float au = uk - fu, av = vk - fv;
+          const float4 c00 = __ldg(a.kf + iv * a.kW + iu), c10 = __ldg(a.kf + iv * a.kW + iu + 1);
+          const float4 c01 = __ldg(a.kf + (iv + 1) * a.kW + iu), c11 = __ldg(a.kf + (iv + 1) * a.kW + iu + 1);
+          const float w00 = (1 - au) * (1 - av), w10 = au * (1 - av), w01 = (1 - au) * av, w11 = au * av;
+          const float Ik = w00 * c00.x + w10 * c10.x + w01 * c01.x + w11 * c11.x;
+          const float gx = w00 * c00.y + w10 * c10.y + w01 * c01.y + w11 * c11.y;
+          const float gy = w00 * c00.z + w10 * c10.z + w01 * c01.z + w11 * c11.z;
+          const float r = __ldg(a.inten + p) - Ik;
+          if (fabsf(r) <= a.thr) {
+            // dr/dy = -(gx, gy) d(pi)/dy, then dr/dx = (dr/dy) R_rs
+            const float iz = 1.0f / y2;
+            const float dy0 = -gx * a.kfx * iz;
+            const float dy1 = -gy * a.kfy * iz;
+            const float dy2 = (gx * a.kfx * y0 + gy * a.kfy * y1) * iz * iz;
+            const float ax0 = dy0 * a.Rrs[0] + dy1 * a.Rrs[3] + dy2 * a.Rrs[6];
+            const float ax1 = dy0 * a.Rrs[1] + dy1 * a.Rrs[4] + dy2 * a.Rrs[7];
+            const float ax2 = dy0 * a.Rrs[2] + dy1 * a.Rrs[5] + dy2 * a.Rrs[8];
+            float J[DIM];
+            J[0] = ax0;
+            J[1] = ax1;
+            J[2] = ax2;
+            J[3] = x1 * ax2 - x2 * ax1;
+            J[4] = x2 * ax0 - x0 * ax2;
+            J[5] = x0 * ax1 - x1 * ax0;
+            if (DIM == 7) J[DIM - 1] = ax0 * x0 + ax1 * x1 + ax2 * x2;
+            acc.row(J, r, a.lambda * wz);
+            acc.v[A::N - 1] += 1.0f;
+          }
+        }
+      }
+    }
+  }
+
+  // ---- block reduction in a fixed order
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < A::N; ++i) {
+    float x = acc.v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) s_red[warp][i] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < A::N) {
+    float s = 0.f;
+#pragma unroll
+    for (int w = 0; w < ICP_THREADS / 32; ++w) s += s_red[w][threadIdx.x];
+    a.partials[blockIdx.x * A::N + threadIdx.x] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(a.ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+
+  // ---- last CTA: FP64 sum of the partials in CTA order, then solve on one thread
+  if (threadIdx.x < A::N) {
+    double s = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) s += (double)__ldcg(a.partials + b * A::N + threadIdx.x);
+    s_sum[threadIdx.x] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  *a.ticket = 0u;
+  double H[7][7], g[7];
+  {
+    int k = 0;
+    for (int i = 0; i < DIM; ++i)
+      for (int j = i; j < DIM; ++j) {
+        H[i][j] = H[j][i] = s_sum[k++];
+      }
+    for (int i = 0; i < DIM; ++i) g[i] = s_sum[A::NH + i];
+  }
+  dtsdf_icp_stats* st = a.stats;
+  for (int i = 0; i < 49; ++i) st->H[i] = 0.0;
+  for (int i = 0; i < DIM; ++i)
+    for (int j = 0; j < DIM; ++j) st->H[7 * i + j] = H[i][j];
+  for (int i = 0; i < 7; ++i) {
+    st->g[i] = i < DIM ? g[i] : 0.0;
+    st->xi[i] = 0.0;
+  }
+  st->error = s_sum[A::NH + DIM];
+  st->rows_photo = (int64_t)s_sum[A::N - 1];
+  st->rows = (int64_t)s_sum[A::N - 2] + st->rows_photo;
+  st->dim = DIM;
+  st->iterations += 1;
+  st->step_norm = 0.0;
+  st->converged = 0;
+  // Cholesky H = L L^T; a pivot below 1e-10 max diag(H) is a degenerate system
+  double dmax = 0.0;
+  for (int i = 0; i < DIM; ++i) dmax = fmax(dmax, H[i][i]);
+  bool ok = st->rows >= a.min_rows && dmax > 0.0;
+  double L[7][7];
+  for (int j = 0; j < DIM && ok; ++j) {
+    double s = H[j][j];
+    for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+    if (!(s > 1e-10 * dmax)) {
+      ok = false;
+      break;
+    }
+    L[j][j] = sqrt(s);
+    for (int i = j + 1; i < DIM; ++i) {
+      double t = H[i][j];
+      for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+      L[i][j] = t / L[j][j];
+    }
+  }
+  if (!ok) {
+    st->status = DTSDF_ERR_DEGENERATE;
+    *a.stop = 1;
+    return;
+  }
+  double y[7], xi[7];
+  for (int i = 0; i < DIM; ++i) {
+    double t = -g[i];
+    for (int k = 0; k < i; ++k) t -= L[i][k] * y[k];
+    y[i] = t / L[i][i];
+  }
+  for (int i = DIM - 1; i >= 0; --i) {
+    double t = y[i];
+    for (int k = i + 1; k < DIM; ++k) t -= L[k][i] * xi[k];
+    xi[i] = t / L[i][i];
+  }
+  double nrm = 0.0;
+  for (int i = 0; i < DIM; ++i) {
+    st->xi[i] = xi[i];
+    nrm += xi[i] * xi[i];
+  }
+  nrm = sqrt(nrm);
+  double E[16], T0[16], T1[16];
+  exp_sim3(xi, DIM, E);
+  for (int i = 0; i < 16; ++i) T0[i] = a.pose[i];
+  mat4_mul(E, T0, T1);
+  for (int i = 0; i < 16; ++i) a.pose[i] = T1[i];
+  st->status = 0;
+  st->step_norm = nrm;
+  if (nrm < a.stop_norm) {
+    st->converged = 1;
+    *a.stop = 1;
+  }
+}
+
+// ------------------------------------------------------------ launchers ---
+void launch_frame_pyramid(const float4* P, const uint8_t* rgb, int levels, const Intr* K, float* const* depth,
+                          float* const* inten, cudaStream_t s) {
+  const int n0 = K[0].W * K[0].H;
+  k_extract_depth<<<(n0 + 255) / 256, 256, 0, s>>>(P, n0, depth[0]);
+  if (rgb) k_intensity<<<(n0 + 255) / 256, 256, 0, s>>>(rgb, n0, inten[0]);
+  for (int l = 1; l < levels; ++l) {
+    dim3 blk(32, 8), grd((K[l].W + 31) / 32, (K[l].H + 7) / 8);
+    k_down<<<grd, blk, 0, s>>>(depth[l - 1], rgb ? inten[l - 1] : nullptr, K[l - 1].W, K[l].W, K[l].H, depth[l],
+                               rgb ? inten[l] : nullptr);
+  }
+}
+
+void launch_keyframe_pyramid(const uint8_t* rgb, int levels, const Intr* K, float* const* tmpI, float4* const* kf,
+                             cudaStream_t s) {
+  const int n0 = K[0].W * K[0].H;
+  k_intensity<<<(n0 + 255) / 256, 256, 0, s>>>(rgb, n0, tmpI[0]);
+  for (int l = 1; l < levels; ++l) {
+    dim3 blk(32, 8), grd((K[l].W + 31) / 32, (K[l].H + 7) / 8);
+    k_down_intensity<<<grd, blk, 0, s>>>(tmpI[l - 1], K[l - 1].W, K[l].W, K[l].H, tmpI[l]);
+  }
+  for (int l = 0; l < levels; ++l) {
+    dim3 blk(32, 8), grd((K[l].W + 31) / 32, (K[l].H + 7) / 8);
+    k_kf_grad<<<grd, blk, 0, s>>>(tmpI[l], K[l].W, K[l].H, kf[l]);
+  }
+}
+
+void launch_icp(const IcpLaunch& L, int sim3, bool photo, int grid, cudaStream_t s) {
+  IcpArgs a;
+  a.depth = L.depth;
+  a.inten = L.inten;
+  a.W = L.K.W;
+  a.H = L.K.H;
+  a.fx = L.K.fx;
+  a.fy = L.K.fy;
+  a.cx = L.K.cx;
+  a.cy = L.K.cy;
+  a.ref = L.ref;
+  a.rW = L.Kr.W;
+  a.rH = L.Kr.H;
+  a.rfx = L.Kr.fx;
+  a.rfy = L.Kr.fy;
+  a.rcx = L.Kr.cx;
+  a.rcy = L.Kr.cy;
+  a.eps = L.eps;
+  a.zmin = L.zmin;
+  a.kf = L.kf;
+  a.kW = L.Kk.W;
+  a.kH = L.Kk.H;
+  a.kfx = L.Kk.fx;
+  a.kfy = L.Kk.fy;
+  a.kcx = L.Kk.cx;
+  a.kcy = L.Kk.cy;
+  for (int i = 0; i < 9; ++i) a.Rrs[i] = L.Rrs[i];
+  for (int i = 0; i < 3; ++i) a.trs[i] = L.trs[i];
+  a.thr = L.thr;
+  a.lambda = L.lambda;
+  a.pose = L.pose;
+  a.partials = L.partials;
+  a.ticket = L.ticket;
+  a.stop = L.stop;
+  a.stats = L.stats;
+  a.min_rows = L.min_rows;
+  a.stop_norm = L.stop_norm;
+  if (sim3) {
+    if (photo)
+      k_icp<7, true><<<grid, ICP_THREADS, 0, s>>>(a);
+    else
+      k_icp<7, false><<<grid, ICP_THREADS, 0, s>>>(a);
+  } else {
+    if (photo)
+      k_icp<6, true><<<grid, ICP_THREADS, 0, s>>>(a);
+    else
+      k_icp<6, false><<<grid, ICP_THREADS, 0, s>>>(a);
+  }
+}
+
+void launch_exp(int dim, const double* xi, double* T, cudaStream_t s) { k_exp<<<1, 1, 0, s>>>(dim, xi, T); }
+
+}  // namespace dtsdf

@@ -1,0 +1,48 @@
+// Host-side declarations shared by the translation units of libdtsdf.
+#pragma once
+
+#include "common.cuh"
+
+namespace dtsdf {
+
+struct IcpLaunch {
+  const float* depth;
+  const float* inten;
+  Intr K;
+  const float4* ref;
+  Intr Kr;
+  float eps, zmin;
+  const float4* kf;
+  Intr Kk;
+  float Rrs[9], trs[3];
+  float thr, lambda;
+  double* pose;
+  float* partials;
+  uint32_t* ticket;
+  int32_t* stop;
+  dtsdf_icp_stats* stats;
+  int min_rows;
+  double stop_norm;
+};
+
+void launch_preprocess(const float* depth, const Intr& K, float zmin, float zmax, float dsup, float4* P, float4* N,
+                       cudaStream_t s);
+void launch_alloc(const MapView& m, const float4* P, const float4* N, int npix, const Pose32& T, int num_sms,
+                  cudaStream_t s);
+void launch_dense_fill(const MapView& m, int nb, cudaStream_t s);
+void launch_pool_init(const MapView& m, int with_color, int num_sms, cudaStream_t s);
+void launch_fuse(const MapView& m, const Intr& K, const Pose32& T, const float4* P, const float4* N,
+                 const uint8_t* rgb, int num_sms, cudaStream_t s);
+void launch_import(const MapView& m, const int32_t* coords, const float* vox, int64_t n, bool allocate, int num_sms,
+                   cudaStream_t s);
+void launch_export(const MapView& m, int64_t cap, int32_t* coords, float* vox, int num_sms, cudaStream_t s);
+void launch_render(const MapView& m, const Intr& K, const Pose32& T, float* depth, float4* normals, float4* color,
+                   cudaStream_t s);
+void launch_frame_pyramid(const float4* P, const uint8_t* rgb, int levels, const Intr* K, float* const* depth,
+                          float* const* inten, cudaStream_t s);
+void launch_keyframe_pyramid(const uint8_t* rgb, int levels, const Intr* K, float* const* tmpI, float4* const* kf,
+                             cudaStream_t s);
+void launch_icp(const IcpLaunch& L, int sim3, bool photo, int grid, cudaStream_t s);
+void launch_exp(int dim, const double* xi, double* T, cudaStream_t s);
+
+}  // namespace dtsdf

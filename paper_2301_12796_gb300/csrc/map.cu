@@ -1,0 +1,555 @@
+// Map construction: frame preprocessing (Sec. 6), voxel-block allocation in the
+// (block, direction) hash (Sec. 6), and voxel-projection fusion of depth and colour
+// with free-space carving (Sec. 3).
+//
+// HBM layout of a map (all allocated once at creation, sized by max_blocks):
+//   keys/vals   open-addressing hash, block coordinate (21 bits per axis) -> directory index
+//   dir_slots   8 int32 per block coordinate: brick index of each of the 6 directions
+//               (-1 absent) and the bitmask of allocated directions; one probe of the
+//               hash yields all six directions, which is what the ray marcher needs
+//   geom        one 512-voxel brick per (block, direction): float2 (sdf, weight), x fastest
+//   col         matching float4 (r, g, b, colour weight) bricks when colour is enabled
+// The voxel (i, j, k) of block b sits at origin + (8 b + (i, j, k)) h.
+#include <math.h>
+
+#include "internal.h"
+
+namespace dtsdf {
+
+// ------------------------------------------------------------ preprocessing
+// Depth outlier filter: a depth in [z_min, z_max] survives if at least two of its eight
+// neighbours are in range and within delta_sup of it. Survivors are back-projected with
+// Eq. reprojection: P = (z (u - cx)/fx, z (v - cy)/fy, z). P.w = 1 marks a survivor.
+__global__ void k_filter(const float* __restrict__ depth, Intr K, float zmin, float zmax, float dsup,
+                         float4* __restrict__ P) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y * blockDim.y + threadIdx.y;
+  if (u >= K.W || v >= K.H) return;
+  const int i = v * K.W + u;
+  const float z = depth[i];
+  float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (depth_in_range(z, zmin, zmax)) {
+    int support = 0;
+    for (int dv = -1; dv <= 1; ++dv)
+      for (int du = -1; du <= 1; ++du) {
+        if (!du && !dv) continue;
+        const int uu = u + du, vv = v + dv;
+        if (uu < 0 || vv < 0 || uu >= K.W || vv >= K.H) continue;
+        const float zn = depth[vv * K.W + uu];
+        if (!depth_in_range(zn, zmin, zmax)) continue;
+        if (fabsf(rsub(zn, z)) <= dsup) ++support;
+      }
+    if (support >= 2) {
+      const float a = rdiv(rsub((float)u, K.cx), K.fx);
+      const float b = rdiv(rsub((float)v, K.cy), K.fy);
+      out = make_float4(rmul(z, a), rmul(z, b), z, 1.0f);
+    }
+  }
+  P[i] = out;
+}
+
+// Normals: cross product of the central differences of the back-projected x and y
+// neighbours (Sec. 6), normalised and turned toward the camera. N.w = 1 marks a normal.
+__global__ void k_normals(const float4* __restrict__ P, Intr K, float4* __restrict__ N) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y * blockDim.y + threadIdx.y;
+  if (u >= K.W || v >= K.H) return;
+  const int i = v * K.W + u;
+  float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (u >= 1 && v >= 1 && u < K.W - 1 && v < K.H - 1) {
+    const float4 c = P[i], l = P[i - 1], r = P[i + 1], t = P[i - K.W], b = P[i + K.W];
+    if (c.w > 0 && l.w > 0 && r.w > 0 && t.w > 0 && b.w > 0) {
+      const float dx0 = rsub(r.x, l.x), dx1 = rsub(r.y, l.y), dx2 = rsub(r.z, l.z);
+      const float dy0 = rsub(b.x, t.x), dy1 = rsub(b.y, t.y), dy2 = rsub(b.z, t.z);
+      float n0 = rsub(rmul(dx1, dy2), rmul(dx2, dy1));
+      float n1 = rsub(rmul(dx2, dy0), rmul(dx0, dy2));
+      float n2 = rsub(rmul(dx0, dy1), rmul(dx1, dy0));
+      const float len = rsqrt_exact(radd(radd(rmul(n0, n0), rmul(n1, n1)), rmul(n2, n2)));
+      if (len > 0.0f) {
+        n0 = rdiv(n0, len);
+        n1 = rdiv(n1, len);
+        n2 = rdiv(n2, len);
+        if (rdot3(n0, n1, n2, c.x, c.y, c.z) > 0.0f) {
+          n0 = -n0;
+          n1 = -n1;
+          n2 = -n2;
+        }
+        out = make_float4(n0, n1, n2, 1.0f);
+      }
+    }
+  }
+  N[i] = out;
+}
+
+// ---------------------------------------------------------------- allocation
+// Record that block (bx, by, bz) needs the directions in `mask`.
+__device__ void request_block(const MapView& m, int bx, int by, int bz, uint32_t mask) {
+  const unsigned long long k = pack_block(bx, by, bz);
+  uint32_t i = hash_slot(k, m.hmask);
+  int p = 0;
+  for (; p < MAX_PROBE; ++p) {
+    unsigned long long kk = *((volatile unsigned long long*)(m.keys + i));
+    if (kk == EMPTY_KEY) {
+      kk = atomicCAS(m.keys + i, EMPTY_KEY, k);
+      if (kk == EMPTY_KEY) kk = k;
+    }
+    if (kk == k) break;
+    i = (i + 1) & m.hmask;
+  }
+  if (p == MAX_PROBE) {
+    atomicOr(m.counters + C_ERR, ERR_HASH_FULL);
+    return;
+  }
+  const int d = *((volatile int32_t*)(m.vals + i));
+  if (d >= 0) {
+    const uint32_t have = (uint32_t)*((volatile int32_t*)(m.dir_slots + (size_t)d * 8 + SLOT_MASK));
+    if ((mask & ~have) == 0) return;
+  }
+  const uint32_t old = atomicOr(m.req + i, mask);
+  if (old == 0) {
+    const uint32_t w = atomicAdd(m.counters + C_WORK, 1u);
+    if (w < m.work_cap)
+      m.work[w] = (int32_t)i;
+    else
+      atomicOr(m.counters + C_ERR, ERR_WORK_FULL);
+  }
+}
+
+// Per pixel with a normal: directions of Eq. angular_threshold (<n_w, v^D> > cos theta),
+// then every block the segment [p - tau r, p + tau r] crosses, by a 3D DDA in block
+// units (ties broken x, y, z).
+__global__ void k_alloc_request(MapView m, const float4* __restrict__ P, const float4* __restrict__ N, int npix,
+                                Pose32 T) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npix) return;
+  const float4 n = N[i];
+  if (!(n.w > 0)) return;
+  float nw[3];
+  rrot(T.R, n.x, n.y, n.z, nw[0], nw[1], nw[2]);
+  uint32_t mask = 0;
+#pragma unroll
+  for (int D = 0; D < ND; ++D) {
+    const float c = (D & 1) ? -nw[D >> 1] : nw[D >> 1];
+    if (c > m.costh) mask |= 1u << D;
+  }
+  if (!mask) return;
+  const float4 p = P[i];
+  float rv[3], pw[3], rh[3], A[3], B[3];
+  rrot(T.R, p.x, p.y, p.z, rv[0], rv[1], rv[2]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) pw[a] = radd(rv[a], T.t[a]);
+  const float len = rsqrt_exact(rdot3(rv[0], rv[1], rv[2], rv[0], rv[1], rv[2]));
+  const float org[3] = {m.ox, m.oy, m.oz};
+  const float bs = rmul(8.0f, m.h);
+  float d[3], tmax[3], tdel[3];
+  int c[3], e[3], st[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    rh[a] = rdiv(rv[a], len);
+    A[a] = rsub(pw[a], rmul(m.tau, rh[a]));
+    B[a] = radd(pw[a], rmul(m.tau, rh[a]));
+    const float Ab = rdiv(rsub(A[a], org[a]), bs);
+    const float Bb = rdiv(rsub(B[a], org[a]), bs);
+    d[a] = rsub(Bb, Ab);
+    c[a] = (int)floorf(Ab);
+    e[a] = (int)floorf(Bb);
+    if (d[a] > 0.0f) {
+      st[a] = 1;
+      tdel[a] = rdiv(1.0f, d[a]);
+      tmax[a] = rdiv(rsub((float)(c[a] + 1), Ab), d[a]);
+    } else if (d[a] < 0.0f) {
+      st[a] = -1;
+      tdel[a] = rdiv(-1.0f, d[a]);
+      tmax[a] = rdiv(rsub((float)c[a], Ab), d[a]);
+    } else {
+      st[a] = 0;
+      tdel[a] = INFINITY;
+      tmax[a] = INFINITY;
+    }
+  }
+  for (int it = 0; it < 64; ++it) {
+    request_block(m, c[0], c[1], c[2], mask);
+    if (c[0] == e[0] && c[1] == e[1] && c[2] == e[2]) break;
+    int ax = 0;
+    if (tmax[1] < tmax[ax]) ax = 1;
+    if (tmax[2] < tmax[ax]) ax = 2;
+    if (tmax[ax] > 1.0f) break;
+    c[ax] += st[ax];
+    tmax[ax] = radd(tmax[ax], tdel[ax]);
+  }
+}
+
+// Assign directory entries and bricks to the requests of this frame (one thread per
+// requested hash slot, so each directory entry has a single writer).
+__global__ void k_alloc_assign(MapView m) {
+  const uint32_t nwork = min(*((volatile uint32_t*)(m.counters + C_WORK)), m.work_cap);
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwork; w += gridDim.x * blockDim.x) {
+    const int i = m.work[w];
+    int d = m.vals[i];
+    if (d < 0) {
+      const uint32_t nd = atomicAdd(m.counters + C_DIR, 1u);
+      if (nd >= m.dir_cap) {
+        atomicOr(m.counters + C_ERR, ERR_DIR_FULL);
+        m.req[i] = 0;
+        continue;
+      }
+      d = (int)nd;
+      int bx, by, bz;
+      unpack_block(m.keys[i], bx, by, bz);
+      m.dir_coord[4 * d] = bx;
+      m.dir_coord[4 * d + 1] = by;
+      m.dir_coord[4 * d + 2] = bz;
+      m.dir_coord[4 * d + 3] = 0;
+      __threadfence();
+      *((volatile int32_t*)(m.vals + i)) = d;
+    }
+    const uint32_t want = m.req[i];
+    m.req[i] = 0;
+    int32_t* slots = m.dir_slots + (size_t)d * 8;
+    uint32_t have = (uint32_t)slots[SLOT_MASK];
+    for (int D = 0; D < ND; ++D) {
+      if (!(want & (1u << D)) || (have & (1u << D))) continue;
+      const uint32_t s = atomicAdd(m.counters + C_POOL, 1u);
+      if (s >= m.pool_cap) {
+        atomicOr(m.counters + C_ERR, ERR_POOL_FULL);
+        continue;
+      }
+      m.brick_dir[s] = d * 8 + D;
+      slots[D] = (int32_t)s;
+      have |= 1u << D;
+    }
+    __threadfence();
+    slots[SLOT_MASK] = (int32_t)have;
+  }
+}
+
+// Dense mode: every (block, direction) of an n^3-block grid, directory index = linear block
+// index, brick = 6 * index + D.
+__global__ void k_dense_fill(MapView m, int nb) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nb * nb * nb) return;
+  const int bx = idx % nb, by = (idx / nb) % nb, bz = idx / (nb * nb);
+  const unsigned long long k = pack_block(bx, by, bz);
+  uint32_t i = hash_slot(k, m.hmask);
+  for (int p = 0; p < MAX_PROBE; ++p) {
+    const unsigned long long kk = atomicCAS(m.keys + i, EMPTY_KEY, k);
+    if (kk == EMPTY_KEY || kk == k) break;
+    i = (i + 1) & m.hmask;
+  }
+  m.vals[i] = idx;
+  m.dir_coord[4 * idx] = bx;
+  m.dir_coord[4 * idx + 1] = by;
+  m.dir_coord[4 * idx + 2] = bz;
+  m.dir_coord[4 * idx + 3] = 0;
+  for (int D = 0; D < ND; ++D) {
+    m.dir_slots[(size_t)idx * 8 + D] = idx * ND + D;
+    m.brick_dir[idx * ND + D] = idx * 8 + D;
+  }
+  m.dir_slots[(size_t)idx * 8 + SLOT_MASK] = 0x3F;
+  m.dir_slots[(size_t)idx * 8 + 7] = 0;
+}
+
+__global__ void k_pool_init(MapView m, int with_color) {
+  const size_t n = (size_t)m.pool_cap * BVOX;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if (m.storage == DTSDF_STORE_FP16)
+      m.geom16[i] = pack_geom16(1.0f, 0.0f);
+    else
+      m.geom[i] = make_float2(1.0f, 0.0f);
+    if (with_color) {
+      if (m.storage == DTSDF_STORE_FP16)
+        m.col8[i] = 0u;
+      else
+        m.col[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ fusion
+struct FuseFrame {
+  Intr K;
+  Pose32 T;  // camera -> world
+  const float4* P;
+  const float4* N;
+  const uint8_t* rgb;
+  // conservative frustum planes through the camera centre (camera frame, unit normals)
+  float pl[4][3];
+};
+
+__device__ __forceinline__ float w_dir_of(float c, float theta) {
+  const float alpha = acosf(fminf(fmaxf(c, -1.0f), 1.0f));
+  return fminf(fmaxf((theta - alpha) / (2.0f * theta - 1.57079632679489662f), 0.0f), 1.0f);
+}
+
+template <int STORE>
+__device__ __forceinline__ float2 load_geom(const MapView& m, size_t i) {
+  if (STORE == DTSDF_STORE_FP16) return unpack_geom16(m.geom16[i]);
+  return m.geom[i];
+}
+
+template <int STORE>
+__device__ __forceinline__ void store_geom(const MapView& m, size_t i, float sdf, float w) {
+  if (STORE == DTSDF_STORE_FP16)
+    m.geom16[i] = pack_geom16(sdf, w);
+  else
+    m.geom[i] = make_float2(sdf, w);
+}
+
+// One CTA per brick at a time (grid-stride over the pool): cull the block against the
+// frustum, then every voxel is projected to its nearest pixel and updated with the
+// weighted running average (Sec. 3). A voxel has one writer, so fusion is deterministic.
+template <int STORE>
+__global__ void __launch_bounds__(256) k_fuse(MapView m, FuseFrame f) {
+  const uint32_t nb = min(*((volatile uint32_t*)(m.counters + C_POOL)), m.pool_cap);
+  const float h = m.h;
+  const float half_diag = 0.8660254f * 8.0f * h + h;
+  for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    const int bd = __ldg(m.brick_dir + b);
+    const int d = bd >> 3, D = bd & 7;
+    const int bx = __ldg(m.dir_coord + 4 * d), by = __ldg(m.dir_coord + 4 * d + 1),
+              bz = __ldg(m.dir_coord + 4 * d + 2);
+    // block centre in the camera frame, bounding-sphere frustum test
+    {
+      const float cw0 = m.ox + (8.0f * bx + 3.5f) * h - f.T.t[0];
+      const float cw1 = m.oy + (8.0f * by + 3.5f) * h - f.T.t[1];
+      const float cw2 = m.oz + (8.0f * bz + 3.5f) * h - f.T.t[2];
+      const float cz = f.T.R[2] * cw0 + f.T.R[5] * cw1 + f.T.R[8] * cw2;
+      if (cz <= -half_diag) continue;
+      const float cx = f.T.R[0] * cw0 + f.T.R[3] * cw1 + f.T.R[6] * cw2;
+      const float cy = f.T.R[1] * cw0 + f.T.R[4] * cw1 + f.T.R[7] * cw2;
+      bool out = false;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) out |= (f.pl[q][0] * cx + f.pl[q][1] * cy + f.pl[q][2] * cz) < -half_diag;
+      if (out) continue;
+    }
+    for (int vi = threadIdx.x; vi < BVOX; vi += blockDim.x) {
+      const int i = vi & 7, j = (vi >> 3) & 7, k = vi >> 6;
+      // single-precision decision path: voxel centre, camera frame, projection
+      const float x0 = radd(rmul((float)(8 * bx + i), h), m.ox);
+      const float x1 = radd(rmul((float)(8 * by + j), h), m.oy);
+      const float x2 = radd(rmul((float)(8 * bz + k), h), m.oz);
+      float xc0, xc1, xc2;
+      rrotT(f.T.R, rsub(x0, f.T.t[0]), rsub(x1, f.T.t[1]), rsub(x2, f.T.t[2]), xc0, xc1, xc2);
+      if (!(xc2 > 0.0f)) continue;
+      const float uf = radd(rmul(rdiv(xc0, xc2), f.K.fx), f.K.cx);
+      const float vf = radd(rmul(rdiv(xc1, xc2), f.K.fy), f.K.cy);
+      const float ur = floorf(radd(uf, 0.5f)), vr = floorf(radd(vf, 0.5f));
+      if (!(ur >= 0.0f && vr >= 0.0f && ur < (float)f.K.W && vr < (float)f.K.H)) continue;
+      const int u = (int)ur, v = (int)vr;
+      const int pi = v * f.K.W + u;
+      const float4 n = __ldg(f.N + pi);
+      if (!(n.w > 0)) continue;
+      const float4 P = __ldg(f.P + pi);
+      const float e0 = rsub(xc0, P.x), e1 = rsub(xc1, P.y), e2 = rsub(xc2, P.z);
+      const float draw = rdot3(e0, e1, e2, n.x, n.y, n.z);
+      if (draw < -m.tau) continue;
+      const size_t gi = (size_t)b * BVOX + vi;
+      if (draw > m.tau) {
+        // free-space carving, unless a depth jump > tau lies within the carving radius
+        bool jump = false;
+        for (int dv = -m.carve_r; dv <= m.carve_r && !jump; ++dv)
+          for (int du = -m.carve_r; du <= m.carve_r; ++du) {
+            const int uu = u + du, vv = v + dv;
+            if (uu < 0 || vv < 0 || uu >= f.K.W || vv >= f.K.H) continue;
+            const float4 q = __ldg(f.P + vv * f.K.W + uu);
+            if (!(q.w > 0)) continue;
+            if (fabsf(rsub(q.z, P.z)) > m.tau) {
+              jump = true;
+              break;
+            }
+          }
+        if (jump) continue;
+        const float2 g = load_geom<STORE>(m, gi);
+        const float wn = g.y + m.wcarve;
+        store_geom<STORE>(m, gi, (g.y * g.x + m.wcarve) / wn, fminf(wn, m.wmax));
+        continue;
+      }
+      // membership of the pixel normal in direction D, and a camera-facing normal
+      float nw0, nw1, nw2;
+      rrot(f.T.R, n.x, n.y, n.z, nw0, nw1, nw2);
+      const float cd = (D == 0) ? nw0 : (D == 1) ? -nw0 : (D == 2) ? nw1 : (D == 3) ? -nw1 : (D == 4) ? nw2 : -nw2;
+      if (!(cd > m.costh)) continue;
+      const float ndp = rdot3(n.x, n.y, n.z, P.x, P.y, P.z);
+      if (!(ndp < 0.0f)) continue;
+      // values (Eq. point-to-plane, Eq. combined_fusion_weight)
+      const float sd = fminf(fmaxf(draw / m.tau, -1.0f), 1.0f);
+      const float zz = P.z + 1.0f - m.zmin;
+      const float w_depth = 1.0f / (zz * zz);
+      const float plen = sqrtf(P.x * P.x + P.y * P.y + P.z * P.z);
+      const float w_angle = fmaxf(-ndp / plen, 0.0f);
+      float w_d = w_depth * w_angle * w_dir_of(cd, m.theta);
+      if (!(w_d > 1e-12f)) w_d = 1e-12f;
+      const float2 g = load_geom<STORE>(m, gi);
+      const float wn = g.y + w_d;
+      store_geom<STORE>(m, gi, (g.y * g.x + w_d * sd) / wn, fminf(wn, m.wmax));
+      if (m.color && f.rgb) {
+        const float dist = rsqrt_exact(rdot3(e0, e1, e2, e0, e1, e2));
+        if (dist < m.tau) {
+          float w_c = w_d * (1.0f - fminf(1.0f, dist / m.tau));
+          if (!(w_c > 1e-12f)) w_c = 1e-12f;
+          const uint8_t* c = f.rgb + 3 * pi;
+          if (STORE == DTSDF_STORE_FP16) {
+            // 8-bit colour, colour weight in 1/ (w_max / 255) steps of the 8-bit field
+            const uint32_t cv = m.col8[gi];
+            const float wq = m.wmax / 255.0f;
+            const float wc0 = (float)(cv >> 24) * wq;
+            const float wcn = wc0 + w_c;
+            const float r = ((float)(cv & 0xFF) * wc0 + w_c * c[0]) / wcn;
+            const float gg = ((float)((cv >> 8) & 0xFF) * wc0 + w_c * c[1]) / wcn;
+            const float bb = ((float)((cv >> 16) & 0xFF) * wc0 + w_c * c[2]) / wcn;
+            const float wcq = fminf(fmaxf(rintf(fminf(wcn, m.wmax) / wq), 1.0f), 255.0f);
+            m.col8[gi] = (uint32_t)fminf(rintf(r), 255.f) | ((uint32_t)fminf(rintf(gg), 255.f) << 8) |
+                         ((uint32_t)fminf(rintf(bb), 255.f) << 16) | ((uint32_t)wcq << 24);
+          } else {
+            float4 cv = m.col[gi];
+            const float wcn = cv.w + w_c;
+            cv.x = (cv.w * cv.x + w_c * c[0]) / wcn;
+            cv.y = (cv.w * cv.y + w_c * c[1]) / wcn;
+            cv.z = (cv.w * cv.z + w_c * c[2]) / wcn;
+            cv.w = fminf(wcn, m.wmax);
+            m.col[gi] = cv;
+          }
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ import
+// Request the (block, direction) bricks of an imported map (same hash path as allocation).
+__global__ void k_import_request(MapView m, const int32_t* __restrict__ coords, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int D = coords[4 * i + 3];
+  if (D < 0 || D >= ND) return;
+  request_block(m, coords[4 * i], coords[4 * i + 1], coords[4 * i + 2], 1u << D);
+}
+
+// Write imported voxel data (sdf, w, r, g, b, wc per voxel) into the bricks.
+__global__ void k_import_write(MapView m, const int32_t* __restrict__ coords, const float* __restrict__ vox,
+                               int64_t n) {
+  for (int64_t b = blockIdx.x; b < n; b += gridDim.x) {
+    const int D = coords[4 * b + 3];
+    if (D < 0 || D >= ND) continue;
+    const int d = hash_find(m, coords[4 * b], coords[4 * b + 1], coords[4 * b + 2]);
+    if (d < 0) continue;
+    const int slot = m.dir_slots[(size_t)d * 8 + D];
+    if (slot < 0) continue;
+    for (int vi = threadIdx.x; vi < BVOX; vi += blockDim.x) {
+      const float* in = vox + ((size_t)b * BVOX + vi) * 6;
+      const size_t gi = (size_t)slot * BVOX + vi;
+      if (m.storage == DTSDF_STORE_FP16)
+        m.geom16[gi] = pack_geom16(in[0], in[1]);
+      else
+        m.geom[gi] = make_float2(in[0], in[1]);
+      if (m.color) {
+        if (m.storage == DTSDF_STORE_FP16) {
+          const float wq = m.wmax / 255.0f;
+          const uint32_t cw = (uint32_t)fminf(fmaxf(rintf(in[5] / wq), in[5] > 0 ? 1.f : 0.f), 255.f);
+          m.col8[gi] = (uint32_t)fminf(rintf(in[2]), 255.f) | ((uint32_t)fminf(rintf(in[3]), 255.f) << 8) |
+                       ((uint32_t)fminf(rintf(in[4]), 255.f) << 16) | (cw << 24);
+        } else {
+          m.col[gi] = make_float4(in[2], in[3], in[4], in[5]);
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ export
+__global__ void k_export(MapView m, int64_t cap, int32_t* coords, float* vox) {
+  const uint32_t nb = min(*((volatile uint32_t*)(m.counters + C_POOL)), m.pool_cap);
+  for (uint32_t b = blockIdx.x; b < nb && b < cap; b += gridDim.x) {
+    const int bd = m.brick_dir[b];
+    const int d = bd >> 3;
+    if (threadIdx.x < 4)
+      coords[4 * (size_t)b + threadIdx.x] = threadIdx.x < 3 ? m.dir_coord[4 * d + threadIdx.x] : (bd & 7);
+    for (int vi = threadIdx.x; vi < BVOX; vi += blockDim.x) {
+      const size_t gi = (size_t)b * BVOX + vi;
+      float* o = vox + gi * 6;
+      float2 g = (m.storage == DTSDF_STORE_FP16) ? unpack_geom16(m.geom16[gi]) : m.geom[gi];
+      o[0] = g.x;
+      o[1] = g.y;
+      if (m.color) {
+        if (m.storage == DTSDF_STORE_FP16) {
+          const uint32_t cv = m.col8[gi];
+          o[2] = (float)(cv & 0xFF);
+          o[3] = (float)((cv >> 8) & 0xFF);
+          o[4] = (float)((cv >> 16) & 0xFF);
+          o[5] = (float)(cv >> 24) * (m.wmax / 255.0f);
+        } else {
+          const float4 c = m.col[gi];
+          o[2] = c.x;
+          o[3] = c.y;
+          o[4] = c.z;
+          o[5] = c.w;
+        }
+      } else {
+        o[2] = o[3] = o[4] = o[5] = 0.f;
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------- launchers
+void launch_preprocess(const float* depth, const Intr& K, float zmin, float zmax, float dsup, float4* P, float4* N,
+                       cudaStream_t s) {
+  dim3 blk(32, 8), grd((K.W + 31) / 32, (K.H + 7) / 8);
+  k_filter<<<grd, blk, 0, s>>>(depth, K, zmin, zmax, dsup, P);
+  k_normals<<<grd, blk, 0, s>>>(P, K, N);
+}
+
+void launch_alloc(const MapView& m, const float4* P, const float4* N, int npix, const Pose32& T, int num_sms,
+                  cudaStream_t s) {
+  k_alloc_request<<<(npix + 255) / 256, 256, 0, s>>>(m, P, N, npix, T);
+  k_alloc_assign<<<num_sms * 2, 256, 0, s>>>(m);
+}
+
+void launch_dense_fill(const MapView& m, int nb, cudaStream_t s) {
+  const int n = nb * nb * nb;
+  k_dense_fill<<<(n + 127) / 128, 128, 0, s>>>(m, nb);
+}
+
+void launch_pool_init(const MapView& m, int with_color, int num_sms, cudaStream_t s) {
+  k_pool_init<<<num_sms * 8, 256, 0, s>>>(m, with_color);
+}
+
+void launch_fuse(const MapView& m, const Intr& K, const Pose32& T, const float4* P, const float4* N,
+                 const uint8_t* rgb, int num_sms, cudaStream_t s) {
+  FuseFrame f;
+  f.K = K;
+  f.T = T;
+  f.P = P;
+  f.N = N;
+  f.rgb = rgb;
+  // inward unit normals of the four side planes (pixel edges at -0.5 and W-0.5)
+  auto set = [&](int q, float a, float b, float c) {
+    const float l = sqrtf(a * a + b * b + c * c);
+    f.pl[q][0] = a / l;
+    f.pl[q][1] = b / l;
+    f.pl[q][2] = c / l;
+  };
+  set(0, K.fx, 0.f, K.cx + 0.5f);
+  set(1, -K.fx, 0.f, (float)K.W - 0.5f - K.cx);
+  set(2, 0.f, K.fy, K.cy + 0.5f);
+  set(3, 0.f, -K.fy, (float)K.H - 0.5f - K.cy);
+  if (m.storage == DTSDF_STORE_FP16)
+    k_fuse<DTSDF_STORE_FP16><<<num_sms * 8, 256, 0, s>>>(m, f);
+  else
+    k_fuse<DTSDF_STORE_FP32><<<num_sms * 8, 256, 0, s>>>(m, f);
+}
+
+void launch_import(const MapView& m, const int32_t* coords, const float* vox, int64_t n, bool allocate, int num_sms,
+                   cudaStream_t s) {
+  if (allocate && n > 0) {
+    k_import_request<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m, coords, n);
+    k_alloc_assign<<<num_sms * 2, 256, 0, s>>>(m);
+  }
+  if (n > 0) k_import_write<<<num_sms * 4, 256, 0, s>>>(m, coords, vox, n);
+}
+
+void launch_export(const MapView& m, int64_t cap, int32_t* coords, float* vox, int num_sms, cudaStream_t s) {
+  k_export<<<num_sms * 4, 256, 0, s>>>(m, cap, coords, vox);
+}
+
+}  // namespace dtsdf

@@ -1,0 +1,99 @@
+"""The C ABI library loads and exports every symbol include/dtsdf.h declares, and the
+Python binding's struct layouts match the header (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+import paper_2301_12796_gb300 as dt
+from paper_2301_12796_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dtsdf.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return dt.lib()
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"DTSDF_API\s+[\w\s\*]+?\b(dtsdf_\w+)\s*\(", txt)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("dtsdf_create", "dtsdf_integrate", "dtsdf_render", "dtsdf_icp_step", "dtsdf_icp_sim3_step"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r" T (dtsdf_\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    assert set(declared_functions()) == set(dt.SIGNATURES)
+
+
+def test_struct_layouts_match_header():
+    src = r"""
+    #include <stdio.h>
+    #include <stddef.h>
+    #include "dtsdf.h"
+    int main(void) {
+      printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(dtsdf_params), sizeof(dtsdf_intrinsics),
+             sizeof(dtsdf_frame), sizeof(dtsdf_render_out), sizeof(dtsdf_map_stats_t),
+             sizeof(dtsdf_icp_opts), sizeof(dtsdf_icp_stats));
+      printf("%zu %zu %zu\n", offsetof(dtsdf_icp_opts, stop_norm), offsetof(dtsdf_icp_stats, rows),
+             offsetof(dtsdf_params, max_blocks));
+      return 0;
+    }
+    """
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "t")
+        subprocess.run(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe], check=True)
+        lines = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    sizes = [int(x) for x in lines[0].split()]
+    offs = [int(x) for x in lines[1].split()]
+    assert sizes == [ctypes.sizeof(x) for x in (dt.Params, dt.Intrinsics, dt.Frame, dt.RenderOut, dt.MapStats,
+                                                dt.IcpOpts, dt.IcpStats)]
+    assert offs == [dt.IcpOpts.stop_norm.offset, dt.IcpStats.rows.offset, dt.Params.max_blocks.offset]
+
+
+def test_invalid_parameters_rejected_on_host(lib):
+    # argument checks run before any CUDA call
+    h = ctypes.c_void_p()
+    bad = dt.params(voxel_size=-1.0)
+    assert lib.dtsdf_create(ctypes.byref(bad), None, ctypes.byref(h)) == dt.ERR_INVALID_ARG
+    bad = dt.params(theta=0.5)  # below acos(1/sqrt(3)): some normals would belong to no direction
+    assert lib.dtsdf_create(ctypes.byref(bad), None, ctypes.byref(h)) == dt.ERR_INVALID_ARG
+    bad = dt.params(dense_dim=60)
+    assert lib.dtsdf_create(ctypes.byref(bad), None, ctypes.byref(h)) == dt.ERR_INVALID_ARG
+    assert lib.dtsdf_create(None, None, ctypes.byref(h)) == dt.ERR_INVALID_ARG
+    assert b"invalid" in lib.dtsdf_last_error() or b"null" in lib.dtsdf_last_error()
+    assert lib.dtsdf_icp_create(4, 4, 3, ctypes.byref(h)) == dt.ERR_INVALID_ARG
+    assert lib.dtsdf_icp_create(640, 480, 9, ctypes.byref(h)) == dt.ERR_INVALID_ARG
+    assert lib.dtsdf_destroy(None) == dt.ERR_INVALID_ARG
+
+
+def test_product_path_has_no_cpu_fallback(tmp_path, monkeypatch):
+    # with the shared library absent the binding raises instead of computing anything itself
+    monkeypatch.setattr(dt, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(dt, "_lib", None)
+    with pytest.raises(RuntimeError):
+        dt.lib()
+
+
+def test_package_does_not_import_oracle():
+    import sys
+    src = open(os.path.join(ROOT, "paper_2301_12796_gb300", "__init__.py")).read()
+    assert "oracle" not in re.findall(r"^\s*(?:import|from)\s+(\w+)", src, flags=re.M)
+    for f in os.listdir(os.path.join(ROOT, "paper_2301_12796_gb300", "csrc")):
+        assert "oracle" not in open(os.path.join(ROOT, "paper_2301_12796_gb300", "csrc", f)).read()
