@@ -1,0 +1,398 @@
+"""Benchmark of the DTSDF render + ICP hot path on the Kinect-shaped workload.
+
+Workload (synthetic, seeded; stands in for the paper's 640x480 indoor RGB-D sequences):
+4 x 4 x 3 m room of boxes, cylinders and 3 mm sheets with Perlin colour, 5 mm voxels,
+2 cm truncation, colour fused, 300 frames at 640x480 (fx = fy = 525, depth noise
+0.0012 z^2 m). The map is built from all 300 frames before timing. One step = one
+tracking frame through the whole hot path:
+  render depth + normals + colour at the previous estimated pose (640x480),
+  current-frame preprocessing and 3-level pyramid,
+  coarse-to-fine SE(3) point-to-plane ICP (4 / 5 / 10 iterations) with the
+  frame-to-keyframe photometric term (keyframe every 10 frames),
+  fusion of the frame (allocation + voxel-projection fusion) at the estimated pose.
+Every pose stays on the device; nothing synchronises with the host inside a step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "render+ICP frames/s @640x480, % HBM roofline; p50/p99 serve latency"
+WORKLOAD = ("kinect-shaped FP32: 4x4x3 m synthetic room, 5 mm voxels, tau 2 cm, 6 directions, RGB; 300-frame "
+            "map; per frame render 640x480 depth+normal+colour, 3-level SE(3) ICP 4/5/10 it + f2kf photometric, "
+            "fusion")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=300)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="small run for ncu: map of 60 frames, few steps")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks ---
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names[1:], p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "of measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "of fallback"
+
+
+# ---------------------------------------------------------------- workload ---
+def make_workload(n_frames: int):
+    import scenes
+    s = scenes.kinect_room(1, n_frames=n_frames)
+    frames = [s.frame(i) for i in range(s.n_frames)]
+    return s, frames
+
+
+def opts_kinect(dt):
+    return dt.icp_opts(levels=3, iters=(10, 5, 4), eps=(0.005, 0.05, 0.05), photo_thr=(0.05, 0.175, 0.175),
+                       lam=0.1, z_min=0.1, stop_norm=1e-6, min_rows=10)
+
+
+LAUNCHES = {"render": 1, "set_frame": 6, "set_keyframe": 6, "compose": 1, "solve": 19, "integrate": 5}
+
+
+class Tracker:
+    """Device-resident tracking loop over the frames (map, ICP context, buffers, poses)."""
+
+    def __init__(self, dt, torch, s, frames, dev, map_frames):
+        self.dt, self.torch, self.s, self.dev = dt, torch, s, dev
+        K = s.K
+        self.K = K
+        self.map = dt.Map(dt.params(voxel_size=0.005, truncation=0.02, max_blocks=1 << 19, z_max=s.z_max, color=True))
+        self.icp = dt.Icp(K.width, K.height, 3)
+        self.opts = opts_kinect(dt)
+        H, W = K.height, K.width
+        self.depth = [torch.from_numpy(f.depth).to(dev) for f in frames]
+        self.rgb = [torch.from_numpy(f.rgb).to(dev) for f in frames]
+        self.gt = torch.from_numpy(np.stack([f.pose for f in frames])).to(dev)
+        self.est = self.gt.clone()
+        self.ref_d = torch.zeros(H, W, device=dev)
+        self.ref_n = torch.zeros(H, W, 4, device=dev)
+        self.ref_c = torch.zeros(H, W, 4, device=dev)
+        self.dT = torch.eye(4, dtype=torch.float64, device=dev)
+        self.eye = torch.eye(4, dtype=torch.float64, device=dev)
+        self.T_rs = torch.eye(4, dtype=torch.float64, device=dev)
+        self.kf = -1
+        self.launches = 0
+        for i in map_frames:
+            self.map.integrate(self.depth[i], self.rgb[i], K, frames[i].pose)
+        torch.cuda.synchronize()
+        self.n = len(frames)
+
+    def step(self, i, ev=None):
+        """Track frame f = 1 + i mod (n - 1). ev: optional list of 4 events (render, icp, fuse phases)."""
+        dt, K = self.dt, self.K
+        f = 1 + i % (self.n - 1)
+        if f == 1:
+            self.est[0].copy_(self.gt[0])
+        ref = self.est[f - 1]
+        if ev:
+            ev[0].record()
+        self.map.render_dev(K, ref, self.ref_d, self.ref_n, self.ref_c)
+        if ev:
+            ev[1].record()
+        self.icp.set_frame(self.depth[f], self.rgb[f], K, 0.1, self.s.z_max, 0.01)
+        kf = 10 * ((f - 1) // 10)
+        n = LAUNCHES["render"] + LAUNCHES["set_frame"]
+        if kf != self.kf:
+            self.icp.set_keyframe(self.rgb[kf], K)
+            self.kf = kf
+            n += LAUNCHES["set_keyframe"]
+        dt.pose_compose(self.est[kf], ref, self.T_rs, invert_a=True)
+        self.dT.copy_(self.eye)
+        self.icp.solve(self.ref_d, self.ref_n, K, self.dT, self.opts, T_rs_dev=self.T_rs)
+        dt.pose_compose(ref, self.dT, self.est[f])
+        if ev:
+            ev[2].record()
+        self.map.integrate_dev(self.depth[f], self.rgb[f], K, self.est[f])
+        if ev:
+            ev[3].record()
+        self.launches += n + 2 * LAUNCHES["compose"] + LAUNCHES["solve"] + LAUNCHES["integrate"]
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+# --------------------------------------------------------------- cpu side ---
+class OracleBench:
+    """The FP64 oracle on a bounded sample of one tracking frame of the workload."""
+
+    def __init__(self, s, frames):
+        import oracle
+        from oracle import icp as oicp
+        self.oracle, self.oicp = oracle, oicp
+        self.s, self.frames = s, frames
+        t0 = time.perf_counter()
+        P = oracle.Params(voxel_size=0.005, truncation=0.02, z_max=s.z_max, color=True)
+        self.om = oracle.OracleMap(P)
+        self.map_frames = list(range(0, len(frames), max(1, len(frames) // 6)))
+        for i in self.map_frames:
+            self.om.integrate(frames[i].depth, frames[i].rgb, s.K, frames[i].pose)
+        self.f = len(frames) // 2
+        f, K = self.f, s.K
+        ref = s.render(frames[f - 1].pose, noise=False, exact=True)
+        self.ref_d = ref.depth
+        self.ref_n = np.zeros(ref.normals.shape[:2] + (4,), np.float32)
+        self.ref_n[..., :3] = ref.normals
+        pre = oracle.preprocess(frames[f].depth, K, 0.1, s.z_max, 0.01)
+        self.levels = oicp.pyramid(pre["z"], K, 3, frames[f].rgb)
+        self.kf_levels = oicp.pyramid(pre["z"], K, 3, frames[f - 1].rgb)
+        self.setup_s = time.perf_counter() - t0
+
+    def step(self, stride: int = 16):
+        """Returns (frames/s extrapolated to one whole frame, parts)."""
+        s, frames, K, f = self.s, self.frames, self.s.K, self.f
+        vv, uu = np.mgrid[0:K.height:stride, 0:K.width:stride]
+        pix = np.stack([uu.ravel(), vv.ravel()], 1).astype(np.int32)
+        t0 = time.perf_counter()
+        self.om.render(K, frames[f - 1].pose, pix)
+        t_render = (time.perf_counter() - t0) * (K.width * K.height) / len(pix)
+        st = self.oicp.Settings(eps=(0.005, 0.05, 0.05))
+        t_icp = 0.0
+        for l, iters in zip(range(3), (10, 5, 4)):
+            t0 = time.perf_counter()
+            self.oicp.step(self.levels[l], self.ref_d, self.ref_n, K, np.eye(4), st.eps[l], st,
+                           photo=(self.kf_levels[l].I, K.scaled(l), np.eye(4)), level_index=l)
+            t_icp += (time.perf_counter() - t0) * iters
+        t0 = time.perf_counter()
+        self.om.integrate(frames[f].depth, frames[f].rgb, K, frames[f].pose)
+        t_fuse = time.perf_counter() - t0
+        return 1.0 / (t_render + t_icp + t_fuse), dict(render_s=t_render, icp_s=t_icp, fuse_s=t_fuse, stride=stride)
+
+    def describe(self, parts) -> str:
+        st = parts["stride"]
+        return (f"oracle map fused from {len(self.map_frames)} of the frames; per frame: render of 1/{st * st} of the "
+                f"640x480 pixels scaled up ({parts['render_s']:.1f} s/frame), one ICP iteration per level on the full "
+                f"frame with photometric rows scaled to 4/5/10 iterations ({parts['icp_s']:.1f} s), one full "
+                f"fusion ({parts['fuse_s']:.1f} s)")
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------- reference --
+def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores, one bounded sample of a tracking frame per step."""
+    if rank != 0:
+        return
+    s, frames = make_workload(args.frames)
+    ob = OracleBench(s, frames)
+    vals, parts = [], None
+    for i in range(args.warmup + args.steps):
+        v, parts = ob.step(stride=32)
+        if i >= args.warmup:
+            vals.append(v)
+    value = float(np.mean(vals))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD},
+           "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cpu_cores(), "kind": "oracle",
+                            "sample": ob.describe(parts)},
+           "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------- main --
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    import torch
+    import torch.distributed as tdist
+    import paper_2301_12796_gb300 as dt
+    from paper_2301_12796_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+        tdist.barrier()
+        B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    assert args.warmup >= 3 or args.profile, "at least 3 warm-up steps"
+    n_frames = 60 if args.profile else args.frames
+    s, frames = make_workload(n_frames)
+    tr = Tracker(dt, torch, s, frames, dev, range(n_frames))
+    st = tr.map.stats()
+    l2 = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MB > L2
+    for i in range(args.warmup):
+        tr.step(i)
+    torch.cuda.synchronize()
+    # algorithmic bytes of the render at the poses rendered in the timed loop (first 8)
+    tb = []
+    for i in range(args.warmup, args.warmup + min(8, args.steps)):
+        f = 1 + i % (tr.n - 1)
+        tb.append(tr.map.touched(s.K, frames[f - 1].pose))
+    geom_b, col_b = np.mean([x[0] for x in tb]), np.mean([x[1] for x in tb])
+    march = tr.map.touched(s.K, frames[1 + args.warmup % (tr.n - 1) - 1].pose, counters=True)[2]
+    npix = s.K.width * s.K.height
+    render_bytes = geom_b * 512 * 8 + col_b * 512 * 16 + npix * (4 + 16 + 16)
+    # ---------------- timed region
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    clk = ClockSampler(local)
+    clk.start()
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    tr.launches = 0
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush_l2(l2)
+        tr.step(args.warmup + k, evs[k])
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        tdist.barrier()
+    clocks = clk.stop()
+    ph = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])] for e in evs])
+    step_ms = ph.sum(1)
+    total_ms = float(step_ms.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1000.0)
+    launches = tr.launches
+    # pose error of the tracked frames against ground truth (sanity, not a parity claim)
+    est = tr.est.cpu().numpy()
+    gt = tr.gt.cpu().numpy()
+    fr = [1 + (args.warmup + k) % (tr.n - 1) for k in range(args.steps)]
+    terr = float(np.median([np.linalg.norm(est[f][:3, 3] - gt[f][:3, 3]) for f in fr]))
+    # ---------------- e2e through host buffers (pinned), pose read back every step
+    e2e = None
+    if not args.no_e2e:
+        hd = [torch.from_numpy(frames[i].depth).pin_memory() for i in range(min(tr.n, 64))]
+        hc = [torch.from_numpy(frames[i].rgb).pin_memory() for i in range(min(tr.n, 64))]
+        host_pose = torch.empty(4, 4, dtype=torch.float64).pin_memory()
+        n_e2e = min(args.steps, 60)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(n_e2e):
+            f = 1 + k % (len(hd) - 1)
+            tr.depth[f].copy_(hd[f], non_blocking=True)  # host -> device, inside the timed region
+            tr.rgb[f].copy_(hc[f], non_blocking=True)
+            tr.step(f - 1)
+            host_pose.copy_(tr.est[f], non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": world * n_e2e / e2e_s, "unit": "frames/s",
+               "h2d_bytes_per_step": int(hd[0].numel() * 4 + hc[0].numel()), "d2h_bytes_per_step": 128,
+               "steps": n_e2e}
+    # ---------------- roofline of the dominant kernel
+    render_ms = float(ph[:, 0].mean())
+    peak, peak_kind = measured_hbm_peak()
+    achieved = render_bytes / (render_ms / 1000.0) / 1e9
+    roof = {"kernel": "k_render (direct DTSDF ray-cast)", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+            "algorithmic_bytes_per_launch": render_bytes, "geom_bricks": geom_b, "color_bricks": col_b,
+            "launch_ms": render_ms}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu and not args.profile:
+        ob = OracleBench(s, frames)
+        v, parts = ob.step(stride=2)
+        cpu = {"value": v, "unit": "frames/s", "cores": cpu_cores(), "kind": "oracle", "sample": ob.describe(parts)}
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": WORKLOAD, "resolution": "640x480", "map_frames": n_frames,
+                          "map_bricks": int(st.bricks), "map_voxels_per_direction_M": [round(x * 512 / 1e6, 2)
+                                                                                      for x in st.bricks_per_dir],
+                          "l2": "flushed between steps (512 MB write outside the timed events)",
+                          "parallelism": f"replicas x{world}",
+                          "phase_ms": {"render": render_ms, "preprocess_pyramid_icp": float(ph[:, 1].mean()),
+                                       "fusion": float(ph[:, 2].mean())},
+                          "rays_per_s": world * npix * args.steps / (total_ms / 1000.0),
+                          "march_counts_per_frame": march,
+                          "wall_s_timed_loop": t_wall, "median_translation_error_m": terr},
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

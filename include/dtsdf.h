@@ -118,12 +118,36 @@ DTSDF_API dtsdf_status dtsdf_destroy(dtsdf_map map);
  * allocates scratch memory. */
 DTSDF_API dtsdf_status dtsdf_integrate(dtsdf_map map, const dtsdf_frame* frame, const double T_wc[16], void* stream);
 
+/* Same as dtsdf_integrate with the pose read from device memory (16 doubles, row-major),
+ * so a tracking loop can fuse at the pose its ICP produced without a host round trip. */
+DTSDF_API dtsdf_status dtsdf_integrate_dev(dtsdf_map map, const dtsdf_frame* frame, const double* T_wc_dev,
+                                           void* stream);
+
 /* Ray-cast depth, normals and colour at pose T_wc with intrinsics K (Sec. 4): per pixel,
  * march the combined SDF of Eq. combine_weight (fallback Eq. combine_tsdf_weight) along
  * the ray from z_min to z_max, find the first positive-to-negative crossing between
  * consecutive samples of the h/2 grid and refine it. Asynchronous. */
 DTSDF_API dtsdf_status dtsdf_render(dtsdf_map map, const dtsdf_intrinsics* K, const double T_wc[16],
                           const dtsdf_render_out* out, void* stream);
+
+/* Same as dtsdf_render with the pose read from device memory (16 doubles, row-major). */
+DTSDF_API dtsdf_status dtsdf_render_dev(dtsdf_map map, const dtsdf_intrinsics* K, const double* T_wc_dev,
+                                        const dtsdf_render_out* out, void* stream);
+
+/* Instrumented render at T_wc that counts the distinct bricks the march reads: geometry
+ * bricks (sdf + weight) and colour bricks. Defines the algorithmic bytes of a render for
+ * roofline accounting. counters (host, 8 int64, or NULL) receives totals over all rays:
+ * samples, full combinations, cells entered, allocated cells entered, hits, cells jumped
+ * because every allocated direction is positive throughout them. Synchronous;
+ * allocates scratch. */
+DTSDF_API dtsdf_status dtsdf_render_touched(dtsdf_map map, const dtsdf_intrinsics* K, const double T_wc[16],
+                                            int64_t* geom_bricks, int64_t* color_bricks, int64_t* counters,
+                                            void* stream);
+
+/* C = A B, or A^-1 B when invert_a != 0, for 4x4 affine transforms (rigid or similarity) in
+ * device memory; one thread, asynchronous. Chains poses in a device-resident tracking loop. */
+DTSDF_API dtsdf_status dtsdf_pose_compose(const double* A_dev, int32_t invert_a, const double* B_dev, double* C_dev,
+                                          void* stream);
 
 DTSDF_API dtsdf_status dtsdf_map_stats(dtsdf_map map, dtsdf_map_stats_t* stats, void* stream);
 
@@ -202,12 +226,13 @@ DTSDF_API dtsdf_status dtsdf_icp_sim3_step(dtsdf_icp icp, const dtsdf_render_out
 
 /* Whole coarse-to-fine schedule (levels-1 .. 0, opts->iters[l] iterations, early stop per
  * level), entirely on the device: T_rel_dev (device, 16 doubles) is read and updated in
- * place; stats_dev (device, one dtsdf_icp_stats) receives the last iteration's statistics.
- * Asynchronous and free of host synchronisation, so it can be captured in a CUDA graph.
- * sim3 = 0: SE(3), 1: Sim(3). */
+ * place; T_rs_dev (device, 16 doubles, or NULL: no photometric term) is the render ->
+ * keyframe camera transform; stats_dev (device, one dtsdf_icp_stats, or NULL) receives the
+ * last iteration's statistics. Asynchronous and free of host synchronisation, so it can be
+ * captured in a CUDA graph. sim3 = 0: SE(3), 1: Sim(3). */
 DTSDF_API dtsdf_status dtsdf_icp_solve(dtsdf_icp icp, const dtsdf_render_out* ref, const dtsdf_intrinsics* K_ref,
-                             int32_t sim3, double* T_rel_dev, const double* T_rs, const dtsdf_icp_opts* opts,
-                             dtsdf_icp_stats* stats_dev, void* stream);
+                                       int32_t sim3, double* T_rel_dev, const double* T_rs_dev,
+                                       const dtsdf_icp_opts* opts, dtsdf_icp_stats* stats_dev, void* stream);
 
 /* Exponential map of se(3) (sim3 = 0, xi[6]) or sim(3) (sim3 = 1, xi[7]) evaluated by the
  * library's device code (the closed form of the matrix exponential of the 4x4 generator);

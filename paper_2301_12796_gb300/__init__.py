@@ -75,7 +75,12 @@ SIGNATURES = {
     "dtsdf_create": ([ctypes.POINTER(Params), P, ctypes.POINTER(P)], c_int32),
     "dtsdf_destroy": ([P], c_int32),
     "dtsdf_integrate": ([P, ctypes.POINTER(Frame), P, P], c_int32),
+    "dtsdf_integrate_dev": ([P, ctypes.POINTER(Frame), P, P], c_int32),
     "dtsdf_render": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), P], c_int32),
+    "dtsdf_render_dev": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), P], c_int32),
+    "dtsdf_render_touched": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64),
+                              P, P], c_int32),
+    "dtsdf_pose_compose": ([P, c_int32, P, P, P], c_int32),
     "dtsdf_map_stats": ([P, ctypes.POINTER(MapStats), P], c_int32),
     "dtsdf_map_export": ([P, P, P, c_int64, ctypes.POINTER(c_int64), P], c_int32),
     "dtsdf_map_import": ([P, P, P, c_int64, P], c_int32),
@@ -175,6 +180,31 @@ class Map:
         check(lib().dtsdf_render(self._h, ctypes.byref(Ki), pose_buf(T_wc), ctypes.byref(out), _stream_ptr(stream)),
               "dtsdf_render")
 
+    def integrate_dev(self, depth, rgb, K, T_dev, stream=None):
+        """Fuse at the pose held by the float64 CUDA tensor T_dev [4, 4]."""
+        f = Frame(depth.data_ptr(), None if rgb is None else rgb.data_ptr(), intrinsics(K))
+        check(lib().dtsdf_integrate_dev(self._h, ctypes.byref(f), T_dev.data_ptr(), _stream_ptr(stream)),
+              "dtsdf_integrate_dev")
+
+    def render_dev(self, K, T_dev, depth, normals, color=None, stream=None):
+        out = RenderOut(depth.data_ptr(), normals.data_ptr(), None if color is None else color.data_ptr())
+        Ki = intrinsics(K)
+        check(lib().dtsdf_render_dev(self._h, ctypes.byref(Ki), T_dev.data_ptr(), ctypes.byref(out),
+                                     _stream_ptr(stream)), "dtsdf_render_dev")
+
+    def touched(self, K, T_wc, stream=None, counters=False):
+        """(geometry bricks, colour bricks) read by one render at T_wc; with counters=True also
+        a dict of per-frame totals (samples, full combinations, cells, allocated cells, hits)."""
+        g, c = c_int64(), c_int64()
+        ctr = (c_int64 * 8)()
+        Ki = intrinsics(K)
+        check(lib().dtsdf_render_touched(self._h, ctypes.byref(Ki), pose_buf(T_wc), ctypes.byref(g), ctypes.byref(c),
+                                         ctr, _stream_ptr(stream)), "dtsdf_render_touched")
+        if counters:
+            names = ["samples", "full", "cells", "alloc_cells", "hits", "cell_jumps"]
+            return g.value, c.value, {n: int(ctr[i]) for i, n in enumerate(names)}
+        return g.value, c.value
+
     def stats(self, stream=None) -> MapStats:
         st = MapStats()
         check(lib().dtsdf_map_stats(self._h, ctypes.byref(st), _stream_ptr(stream)), "dtsdf_map_stats")
@@ -252,15 +282,22 @@ class Icp:
             check(s, "dtsdf_icp_step")
         return np.array(T[:], np.float64).reshape(4, 4), st
 
-    def solve(self, ref_depth, ref_normals, K_ref, T_rel_dev, opts: IcpOpts, sim3=False, T_rs=None, stats_dev=None,
-              stream=None):
-        """Whole schedule on the device; T_rel_dev: float64 CUDA tensor [4, 4] updated in place."""
+    def solve(self, ref_depth, ref_normals, K_ref, T_rel_dev, opts: IcpOpts, sim3=False, T_rs_dev=None,
+              stats_dev=None, stream=None):
+        """Whole schedule on the device; T_rel_dev: float64 CUDA tensor [4, 4] updated in place;
+        T_rs_dev: float64 CUDA tensor [4, 4] (render -> keyframe camera) or None."""
         out = RenderOut(ref_depth.data_ptr(), ref_normals.data_ptr(), None)
         Ki = intrinsics(K_ref)
-        rs = None if T_rs is None else pose_buf(T_rs)
+        rs = None if T_rs_dev is None else T_rs_dev.data_ptr()
         check(lib().dtsdf_icp_solve(self._h, ctypes.byref(out), ctypes.byref(Ki), int(sim3), T_rel_dev.data_ptr(), rs,
                                     ctypes.byref(opts), None if stats_dev is None else stats_dev.data_ptr(),
                                     _stream_ptr(stream)), "dtsdf_icp_solve")
+
+
+def pose_compose(A_dev, B_dev, C_dev, invert_a=False, stream=None):
+    """C = A B (or A^-1 B) on the device for float64 CUDA tensors [4, 4]."""
+    check(lib().dtsdf_pose_compose(A_dev.data_ptr(), int(invert_a), B_dev.data_ptr(), C_dev.data_ptr(),
+                                   _stream_ptr(stream)), "dtsdf_pose_compose")
 
 
 def exp(xi) -> np.ndarray:

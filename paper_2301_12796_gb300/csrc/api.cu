@@ -113,6 +113,7 @@ static void map_free(dtsdf_map m) {
   cudaFree(m->v.col);
   cudaFree(m->v.col8);
   cudaFree(m->v.brick_dir);
+  cudaFree(m->v.bound);
   cudaFree(m->v.counters);
   cudaFree(m->v.work);
   cudaFree(m->P);
@@ -144,7 +145,7 @@ dtsdf_status dtsdf_create(const dtsdf_params* params, void* stream, dtsdf_map* o
     if (nb > 256) return fail(DTSDF_ERR_INVALID_ARG, "dense_dim too large");
     bricks = (uint64_t)nb * nb * nb * ND;
   }
-  if (bricks == 0 || bricks > (1ull << 27)) return fail(DTSDF_ERR_INVALID_ARG, "max_blocks out of range");
+  if (bricks == 0 || bricks >= (1ull << 26)) return fail(DTSDF_ERR_INVALID_ARG, "max_blocks out of range");
   cudaStream_t s = (cudaStream_t)stream;
   dtsdf_map m = new (std::nothrow) dtsdf_map_s();
   if (!m) return fail(DTSDF_ERR_OOM, "host allocation");
@@ -188,6 +189,7 @@ dtsdf_status dtsdf_create(const dtsdf_params* params, void* stream, dtsdf_map* o
     if (p.color) ALLOC(v.col, sizeof(float4) * BVOX * (size_t)bricks);
   }
   ALLOC(v.brick_dir, sizeof(int32_t) * (size_t)bricks);
+  ALLOC(v.bound, sizeof(float) * (size_t)bricks);
   ALLOC(v.counters, sizeof(uint32_t) * C_COUNT);
   ALLOC(v.work, sizeof(int32_t) * (size_t)v.work_cap);
 #undef ALLOC
@@ -199,7 +201,7 @@ dtsdf_status dtsdf_create(const dtsdf_params* params, void* stream, dtsdf_map* o
   }
   *m->err_host = 0;
   if ((e = cudaMemsetAsync(v.keys, 0xFF, sizeof(unsigned long long) * hcap, s)) != cudaSuccess ||
-      (e = cudaMemsetAsync(v.vals, 0xFF, sizeof(int32_t) * hcap, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(v.vals, 0xFF, sizeof(uint32_t) * hcap, s)) != cudaSuccess ||
       (e = cudaMemsetAsync(v.req, 0, sizeof(uint32_t) * hcap, s)) != cudaSuccess ||
       (e = cudaMemsetAsync(v.dir_slots, 0xFF, sizeof(int32_t) * 8 * (size_t)v.dir_cap, s)) != cudaSuccess ||
       (e = cudaMemsetAsync(v.counters, 0, sizeof(uint32_t) * C_COUNT, s)) != cudaSuccess) {
@@ -256,8 +258,10 @@ static dtsdf_status ensure_ws(dtsdf_map m, size_t npix) {
   return DTSDF_OK;
 }
 
-dtsdf_status dtsdf_integrate(dtsdf_map m, const dtsdf_frame* f, const double T_wc[16], void* stream) {
-  if (!m || !f || !f->depth || !intr_ok(&f->K) || !pose_ok(T_wc)) return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+static dtsdf_status integrate_impl(dtsdf_map m, const dtsdf_frame* f, const double* T_wc, const double* T_dev,
+                                   void* stream) {
+  if (!m || !f || !f->depth || !intr_ok(&f->K) || (T_wc ? !pose_ok(T_wc) : !T_dev))
+    return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
   cudaStream_t s = (cudaStream_t)stream;
   // errors flagged by earlier calls (read without stalling the stream)
   if (m->err_pending && cudaEventQuery(m->err_event) == cudaSuccess) {
@@ -269,16 +273,24 @@ dtsdf_status dtsdf_integrate(dtsdf_map m, const dtsdf_frame* f, const double T_w
   const size_t npix = (size_t)K.W * K.H;
   dtsdf_status st = ensure_ws(m, npix);
   if (st != DTSDF_OK) return st;
-  const Pose32 T = to_pose32(T_wc);
+  Pose32 T;
+  memset(&T, 0, sizeof(T));
+  if (T_wc) T = to_pose32(T_wc);
   launch_preprocess(f->depth, K, m->v.zmin, m->v.zmax, m->v.dsup, m->P, m->N, s);
   CK_LAUNCH("preprocess");
   if (m->p.dense_dim <= 0) {
     CK(cudaMemsetAsync(m->v.counters + C_WORK, 0, sizeof(uint32_t), s));
-    launch_alloc(m->v, m->P, m->N, (int)npix, T, num_sms(), s);
+    CK(cudaMemcpyAsync(m->v.counters + C_POOL_BEFORE, m->v.counters + C_POOL, sizeof(uint32_t),
+                       cudaMemcpyDeviceToDevice, s));
+    launch_alloc(m->v, m->P, m->N, (int)npix, T, T_dev, num_sms(), s);
     CK_LAUNCH("alloc");
   }
-  launch_fuse(m->v, K, T, m->P, m->N, m->p.color ? f->rgb : nullptr, num_sms(), s);
+  launch_fuse(m->v, K, T, T_dev, m->P, m->N, m->p.color ? f->rgb : nullptr, num_sms(), s);
   CK_LAUNCH("fuse");
+  if (m->p.dense_dim <= 0) {
+    launch_bounds_refresh(m->v, 1, 0, 0, num_sms(), s);
+    CK_LAUNCH("bounds");
+  }
   if (!m->err_pending) {
     CK(cudaMemcpyAsync(m->err_host, m->v.counters + C_ERR, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(m->err_event, s));
@@ -288,13 +300,87 @@ dtsdf_status dtsdf_integrate(dtsdf_map m, const dtsdf_frame* f, const double T_w
   return DTSDF_OK;
 }
 
+dtsdf_status dtsdf_integrate(dtsdf_map m, const dtsdf_frame* f, const double T_wc[16], void* stream) {
+  if (!T_wc) return fail(DTSDF_ERR_INVALID_ARG, "null pose");
+  return integrate_impl(m, f, T_wc, nullptr, stream);
+}
+
+dtsdf_status dtsdf_integrate_dev(dtsdf_map m, const dtsdf_frame* f, const double* T_wc_dev, void* stream) {
+  if (!T_wc_dev) return fail(DTSDF_ERR_INVALID_ARG, "null pose");
+  return integrate_impl(m, f, nullptr, T_wc_dev, stream);
+}
+
 dtsdf_status dtsdf_render(dtsdf_map m, const dtsdf_intrinsics* K, const double T_wc[16], const dtsdf_render_out* out,
                           void* stream) {
   if (!m || !intr_ok(K) || !pose_ok(T_wc) || !out || !out->depth || !out->normals)
     return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
-  launch_render(m->v, to_intr(*K), to_pose32(T_wc), out->depth, (float4*)out->normals, (float4*)out->color,
+  launch_render(m->v, to_intr(*K), to_pose32(T_wc), nullptr, out->depth, (float4*)out->normals, (float4*)out->color,
                 (cudaStream_t)stream);
   CK_LAUNCH("render");
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_render_dev(dtsdf_map m, const dtsdf_intrinsics* K, const double* T_wc_dev,
+                              const dtsdf_render_out* out, void* stream) {
+  if (!m || !intr_ok(K) || !T_wc_dev || !out || !out->depth || !out->normals)
+    return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  Pose32 T;
+  memset(&T, 0, sizeof(T));
+  launch_render(m->v, to_intr(*K), T, T_wc_dev, out->depth, (float4*)out->normals, (float4*)out->color,
+                (cudaStream_t)stream);
+  CK_LAUNCH("render");
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_render_touched(dtsdf_map m, const dtsdf_intrinsics* K, const double T_wc[16], int64_t* geom_bricks,
+                                  int64_t* color_bricks, int64_t* counters, void* stream) {
+  if (!m || !intr_ok(K) || !pose_ok(T_wc) || !geom_bricks || !color_bricks)
+    return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t npix = (size_t)K->width * K->height;
+  const size_t nflags = 2 * (size_t)m->v.pool_cap + 8 * sizeof(unsigned long long);
+  uint8_t* flags = nullptr;
+  float* depth = nullptr;
+  float4* nrm = nullptr;
+  float4* col = nullptr;
+  cudaError_t e = cudaMalloc((void**)&flags, nflags);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&depth, sizeof(float) * npix);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&nrm, sizeof(float4) * npix);
+  if (e == cudaSuccess && m->p.color) e = cudaMalloc((void**)&col, sizeof(float4) * npix);
+  if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, nflags, s);
+  if (e == cudaSuccess) {
+    launch_render(m->v, to_intr(*K), to_pose32(T_wc), nullptr, depth, nrm, col, s, flags);
+    e = cudaGetLastError();
+  }
+  uint8_t* host = nullptr;
+  if (e == cudaSuccess) host = new (std::nothrow) uint8_t[nflags];
+  if (e == cudaSuccess && !host) e = cudaErrorMemoryAllocation;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, flags, nflags, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) {
+    int64_t g = 0, c = 0;
+    for (size_t i = 0; i < m->v.pool_cap; ++i) {
+      g += host[i] != 0;
+      c += host[m->v.pool_cap + i] != 0;
+    }
+    *geom_bricks = g;
+    *color_bricks = c;
+    if (counters) memcpy(counters, host + 2 * (size_t)m->v.pool_cap, 8 * sizeof(int64_t));
+  }
+  delete[] host;
+  cudaFree(flags);
+  cudaFree(depth);
+  cudaFree(nrm);
+  cudaFree(col);
+  if (e != cudaSuccess) return cuda_fail(e, "render_touched");
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_pose_compose(const double* A_dev, int32_t invert_a, const double* B_dev, double* C_dev,
+                                void* stream) {
+  if (!A_dev || !B_dev || !C_dev) return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  launch_pose_compose(A_dev, invert_a ? 1 : 0, B_dev, C_dev, (cudaStream_t)stream);
+  CK_LAUNCH("pose_compose");
   return DTSDF_OK;
 }
 
@@ -369,6 +455,7 @@ dtsdf_status dtsdf_map_import(dtsdf_map m, const int32_t* coords, const float* v
   if (e == cudaSuccess && m->p.dense_dim <= 0) e = cudaMemsetAsync(m->v.counters + C_WORK, 0, sizeof(uint32_t), s);
   if (e == cudaSuccess) {
     launch_import(m->v, dc, dv, n, m->p.dense_dim <= 0, num_sms(), s);
+    launch_bounds_refresh(m->v, 0, 0, m->v.pool_cap, num_sms(), s);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -525,7 +612,7 @@ static bool opts_ok(const dtsdf_icp_opts* o, int levels) {
 }
 
 static void fill_launch(dtsdf_icp c, IcpLaunch& L, const dtsdf_render_out* ref, const dtsdf_intrinsics* K_ref, int level,
-                        const double* T_rs, const dtsdf_icp_opts* o, bool& photo) {
+                        const double* T_rs, const double* T_rs_dev, const dtsdf_icp_opts* o, bool& photo) {
   L.depth = c->depth[level];
   L.inten = c->inten[level];
   L.K = c->K[level];
@@ -533,12 +620,13 @@ static void fill_launch(dtsdf_icp c, IcpLaunch& L, const dtsdf_render_out* ref, 
   L.Kr = to_intr(*K_ref);
   L.eps = o->eps[level];
   L.zmin = o->z_min;
-  photo = T_rs && o->lambda > 0 && c->has_kf && c->has_rgb;
+  photo = (T_rs || T_rs_dev) && o->lambda > 0 && c->has_kf && c->has_rgb;
+  L.Trs_dev = photo ? T_rs_dev : nullptr;
   L.kf = c->kf[level];
   L.Kk = c->Kkf[level];
   for (int i = 0; i < 9; ++i) L.Rrs[i] = 0.f;
   for (int i = 0; i < 3; ++i) L.trs[i] = 0.f;
-  if (photo) {
+  if (photo && T_rs) {
     for (int a = 0; a < 3; ++a) {
       for (int b = 0; b < 3; ++b) L.Rrs[3 * a + b] = (float)T_rs[4 * a + b];
       L.trs[a] = (float)T_rs[4 * a + 3];
@@ -568,7 +656,7 @@ static dtsdf_status icp_step_impl(dtsdf_icp c, const dtsdf_render_out* ref, cons
   CK(cudaMemsetAsync(c->stats, 0, sizeof(dtsdf_icp_stats), s));
   IcpLaunch L;
   bool photo = false;
-  fill_launch(c, L, ref, K_ref, level, T_rs, o, photo);
+  fill_launch(c, L, ref, K_ref, level, T_rs, nullptr, o, photo);
   launch_icp(L, sim3, photo, c->grid, s);
   CK_LAUNCH("icp_step");
   CK(cudaMemcpyAsync(c->host_pose, c->pose, sizeof(double) * 16, cudaMemcpyDeviceToHost, s));
@@ -593,7 +681,7 @@ dtsdf_status dtsdf_icp_sim3_step(dtsdf_icp c, const dtsdf_render_out* ref, const
 }
 
 dtsdf_status dtsdf_icp_solve(dtsdf_icp c, const dtsdf_render_out* ref, const dtsdf_intrinsics* K_ref, int32_t sim3,
-                             double* T_rel_dev, const double* T_rs, const dtsdf_icp_opts* o,
+                             double* T_rel_dev, const double* T_rs_dev, const dtsdf_icp_opts* o,
                              dtsdf_icp_stats* stats_dev, void* stream) {
   if (!c || !ref || !ref->normals || !intr_ok(K_ref) || !T_rel_dev || !opts_ok(o, c->levels) || !c->has_frame ||
       (sim3 != 0 && sim3 != 1))
@@ -605,7 +693,7 @@ dtsdf_status dtsdf_icp_solve(dtsdf_icp c, const dtsdf_render_out* ref, const dts
     CK(cudaMemsetAsync(c->stop, 0, sizeof(int32_t), s));
     IcpLaunch L;
     bool photo = false;
-    fill_launch(c, L, ref, K_ref, l, T_rs, o, photo);
+    fill_launch(c, L, ref, K_ref, l, nullptr, T_rs_dev, o, photo);
     for (int it = 0; it < o->iters[l]; ++it) launch_icp(L, sim3, photo, c->grid, s);
     CK_LAUNCH("icp_solve");
   }

@@ -27,6 +27,13 @@ constexpr uint32_t ERR_DIR_FULL = 2u;
 constexpr uint32_t ERR_HASH_FULL = 4u;
 constexpr uint32_t ERR_WORK_FULL = 8u;
 
+// hash values pack the directory index (26 bits) with the allocated-direction mask (6 bits)
+constexpr uint32_t VAL_EMPTY = 0xFFFFFFFFu;
+constexpr uint32_t VAL_DIR_MASK = 0x3FFFFFFu;
+__host__ __device__ __forceinline__ uint32_t pack_val(int d, uint32_t mask) { return (uint32_t)d | (mask << 26); }
+__host__ __device__ __forceinline__ int val_dir(uint32_t v) { return v == VAL_EMPTY ? -1 : (int)(v & VAL_DIR_MASK); }
+__host__ __device__ __forceinline__ uint32_t val_mask(uint32_t v) { return v == VAL_EMPTY ? 0u : v >> 26; }
+
 // device counters
 enum { C_DIR = 0, C_POOL = 1, C_WORK = 2, C_ERR = 3, C_DIR_BEFORE = 4, C_POOL_BEFORE = 5, C_COUNT = 8 };
 
@@ -45,6 +52,19 @@ struct Pose32 {
   float R[9];  // row-major rotation (or s R) of camera -> world
   float t[3];
 };
+
+// Pose given in device memory (row-major 4x4 double), rounded to single precision exactly
+// as the host does for poses passed by value.
+__device__ __forceinline__ Pose32 pose_from_device(const double* T) {
+  Pose32 p;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) p.R[3 * a + b] = __double2float_rn(T[4 * a + b]);
+    p.t[a] = __double2float_rn(T[4 * a + 3]);
+  }
+  return p;
+}
 
 struct Intr {
   int W, H;
@@ -99,7 +119,7 @@ struct MapView {
   int carve_r, dense_dim, color, storage;
   // hash: block coordinate -> directory index
   unsigned long long* keys;
-  int32_t* vals;
+  uint32_t* vals;  // pack_val(directory index, allocated mask), VAL_EMPTY before assignment
   uint32_t* req;  // per hash slot: directions requested this frame
   uint32_t hmask;
   // directory: 8 ints per entry: slots of the 6 directions, allocated mask, unused
@@ -112,23 +132,37 @@ struct MapView {
   float4* col;      // FP32: (r, g, b, colour weight)
   uint32_t* col8;   // FP16 storage: u8 r, g, b, u8 colour weight (1/ (255/w_max) units)
   int32_t* brick_dir;  // per brick: dir index * 8 + D
+  float* bound;        // per brick: lower bound of sdf over its voxels and its +1 apron with weight > 0
   uint32_t pool_cap;
   uint32_t* counters;
   int32_t* work;
   uint32_t work_cap;
 };
 
-__device__ __forceinline__ int hash_find(const MapView& m, int bx, int by, int bz) {
+// Packed hash value of block (bx, by, bz), VAL_EMPTY if absent.
+__device__ __forceinline__ uint32_t hash_find_packed(const MapView& m, int bx, int by, int bz) {
   const unsigned long long k = pack_block(bx, by, bz);
   uint32_t i = hash_slot(k, m.hmask);
 #pragma unroll 1
   for (int p = 0; p < MAX_PROBE; ++p) {
     const unsigned long long kk = __ldg(m.keys + i);
     if (kk == k) return __ldg(m.vals + i);
-    if (kk == EMPTY_KEY) return -1;
+    if (kk == EMPTY_KEY) return VAL_EMPTY;
     i = (i + 1) & m.hmask;
   }
-  return -1;
+  return VAL_EMPTY;
+}
+
+__device__ __forceinline__ int hash_find(const MapView& m, int bx, int by, int bz) {
+  return val_dir(hash_find_packed(m, bx, by, bz));
+}
+
+// float atomic minimum through the integer orderings of positive and negative floats
+__device__ __forceinline__ void atomic_min_float(float* addr, float v) {
+  if (v >= 0.0f)
+    atomicMin((int*)addr, __float_as_int(v));
+  else
+    atomicMax((unsigned int*)addr, __float_as_uint(v));
 }
 
 // Storage accessors ---------------------------------------------------------

@@ -171,6 +171,7 @@ struct IcpArgs {
   int kW, kH;
   float kfx, kfy, kcx, kcy;
   float Rrs[9], trs[3];
+  const double* Trs_dev;  // render -> keyframe camera in device memory (overrides Rrs/trs)
   float thr, lambda;
   // state
   double* pose;
@@ -219,6 +220,14 @@ __global__ void __launch_bounds__(ICP_THREADS) k_icp(IcpArgs a) {
 #pragma unroll
     for (int j = 0; j < 3; ++j) Am[3 * i + j] = (float)(a.pose[4 * i + j] - (i == j ? 1.0 : 0.0));
     tv[i] = (float)a.pose[4 * i + 3];
+  }
+  if (PHOTO && a.Trs_dev) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) a.Rrs[3 * i + j] = __double2float_rn(a.Trs_dev[4 * i + j]);
+      a.trs[i] = __double2float_rn(a.Trs_dev[4 * i + 3]);
+    }
   }
   A acc;
   acc.zero();
@@ -475,6 +484,7 @@ void launch_icp(const IcpLaunch& L, int sim3, bool photo, int grid, cudaStream_t
   a.kcy = L.Kk.cy;
   for (int i = 0; i < 9; ++i) a.Rrs[i] = L.Rrs[i];
   for (int i = 0; i < 3; ++i) a.trs[i] = L.trs[i];
+  a.Trs_dev = L.Trs_dev;
   a.thr = L.thr;
   a.lambda = L.lambda;
   a.pose = L.pose;

@@ -15,6 +15,7 @@ struct IcpLaunch {
   const float4* kf;
   Intr Kk;
   float Rrs[9], trs[3];
+  const double* Trs_dev;
   float thr, lambda;
   double* pose;
   float* partials;
@@ -27,17 +28,20 @@ struct IcpLaunch {
 
 void launch_preprocess(const float* depth, const Intr& K, float zmin, float zmax, float dsup, float4* P, float4* N,
                        cudaStream_t s);
-void launch_alloc(const MapView& m, const float4* P, const float4* N, int npix, const Pose32& T, int num_sms,
-                  cudaStream_t s);
+void launch_alloc(const MapView& m, const float4* P, const float4* N, int npix, const Pose32& T, const double* Tdev,
+                  int num_sms, cudaStream_t s);
 void launch_dense_fill(const MapView& m, int nb, cudaStream_t s);
 void launch_pool_init(const MapView& m, int with_color, int num_sms, cudaStream_t s);
-void launch_fuse(const MapView& m, const Intr& K, const Pose32& T, const float4* P, const float4* N,
-                 const uint8_t* rgb, int num_sms, cudaStream_t s);
+void launch_fuse(const MapView& m, const Intr& K, const Pose32& T, const double* Tdev, const float4* P,
+                 const float4* N, const uint8_t* rgb, int num_sms, cudaStream_t s);
+void launch_bounds_refresh(const MapView& m, int from_counter, uint32_t begin, uint32_t end, int num_sms,
+                           cudaStream_t s);
+void launch_pose_compose(const double* A, int invert_a, const double* B, double* C, cudaStream_t s);
 void launch_import(const MapView& m, const int32_t* coords, const float* vox, int64_t n, bool allocate, int num_sms,
                    cudaStream_t s);
 void launch_export(const MapView& m, int64_t cap, int32_t* coords, float* vox, int num_sms, cudaStream_t s);
-void launch_render(const MapView& m, const Intr& K, const Pose32& T, float* depth, float4* normals, float4* color,
-                   cudaStream_t s);
+void launch_render(const MapView& m, const Intr& K, const Pose32& T, const double* Tdev, float* depth,
+                   float4* normals, float4* color, cudaStream_t s, uint8_t* touched = nullptr);
 void launch_frame_pyramid(const float4* P, const uint8_t* rgb, int levels, const Intr* K, float* const* depth,
                           float* const* inten, cudaStream_t s);
 void launch_keyframe_pyramid(const uint8_t* rgb, int levels, const Intr* K, float* const* tmpI, float4* const* kf,

@@ -100,11 +100,8 @@ __device__ void request_block(const MapView& m, int bx, int by, int bz, uint32_t
     atomicOr(m.counters + C_ERR, ERR_HASH_FULL);
     return;
   }
-  const int d = *((volatile int32_t*)(m.vals + i));
-  if (d >= 0) {
-    const uint32_t have = (uint32_t)*((volatile int32_t*)(m.dir_slots + (size_t)d * 8 + SLOT_MASK));
-    if ((mask & ~have) == 0) return;
-  }
+  const uint32_t v = *((volatile uint32_t*)(m.vals + i));
+  if (v != VAL_EMPTY && (mask & ~val_mask(v)) == 0) return;
   const uint32_t old = atomicOr(m.req + i, mask);
   if (old == 0) {
     const uint32_t w = atomicAdd(m.counters + C_WORK, 1u);
@@ -119,9 +116,10 @@ __device__ void request_block(const MapView& m, int bx, int by, int bz, uint32_t
 // then every block the segment [p - tau r, p + tau r] crosses, by a 3D DDA in block
 // units (ties broken x, y, z).
 __global__ void k_alloc_request(MapView m, const float4* __restrict__ P, const float4* __restrict__ N, int npix,
-                                Pose32 T) {
+                                Pose32 Tv, const double* __restrict__ Tdev) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npix) return;
+  const Pose32 T = Tdev ? pose_from_device(Tdev) : Tv;
   const float4 n = N[i];
   if (!(n.w > 0)) return;
   float nw[3];
@@ -185,7 +183,7 @@ __global__ void k_alloc_assign(MapView m) {
   const uint32_t nwork = min(*((volatile uint32_t*)(m.counters + C_WORK)), m.work_cap);
   for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwork; w += gridDim.x * blockDim.x) {
     const int i = m.work[w];
-    int d = m.vals[i];
+    int d = val_dir(m.vals[i]);
     if (d < 0) {
       const uint32_t nd = atomicAdd(m.counters + C_DIR, 1u);
       if (nd >= m.dir_cap) {
@@ -201,7 +199,7 @@ __global__ void k_alloc_assign(MapView m) {
       m.dir_coord[4 * d + 2] = bz;
       m.dir_coord[4 * d + 3] = 0;
       __threadfence();
-      *((volatile int32_t*)(m.vals + i)) = d;
+      *((volatile uint32_t*)(m.vals + i)) = pack_val(d, 0u);
     }
     const uint32_t want = m.req[i];
     m.req[i] = 0;
@@ -215,11 +213,14 @@ __global__ void k_alloc_assign(MapView m) {
         continue;
       }
       m.brick_dir[s] = d * 8 + D;
+      // a new brick's apron may already hold data: no bound until it is recomputed
+      m.bound[s] = -INFINITY;
       slots[D] = (int32_t)s;
       have |= 1u << D;
     }
     __threadfence();
     slots[SLOT_MASK] = (int32_t)have;
+    *((volatile uint32_t*)(m.vals + i)) = pack_val(d, have);
   }
 }
 
@@ -236,7 +237,7 @@ __global__ void k_dense_fill(MapView m, int nb) {
     if (kk == EMPTY_KEY || kk == k) break;
     i = (i + 1) & m.hmask;
   }
-  m.vals[i] = idx;
+  m.vals[i] = pack_val(idx, 0x3Fu);
   m.dir_coord[4 * idx] = bx;
   m.dir_coord[4 * idx + 1] = by;
   m.dir_coord[4 * idx + 2] = bz;
@@ -256,6 +257,7 @@ __global__ void k_pool_init(MapView m, int with_color) {
       m.geom16[i] = pack_geom16(1.0f, 0.0f);
     else
       m.geom[i] = make_float2(1.0f, 0.0f);
+    if (i < m.pool_cap) m.bound[i] = INFINITY;
     if (with_color) {
       if (m.storage == DTSDF_STORE_FP16)
         m.col8[i] = 0u;
@@ -268,7 +270,8 @@ __global__ void k_pool_init(MapView m, int with_color) {
 // ------------------------------------------------------------------ fusion
 struct FuseFrame {
   Intr K;
-  Pose32 T;  // camera -> world
+  Pose32 T;            // camera -> world (unless Tdev is given)
+  const double* Tdev;  // camera -> world in device memory, or null
   const float4* P;
   const float4* N;
   const uint8_t* rgb;
@@ -298,9 +301,64 @@ __device__ __forceinline__ void store_geom(const MapView& m, size_t i, float sdf
 // One CTA per brick at a time (grid-stride over the pool): cull the block against the
 // frustum, then every voxel is projected to its nearest pixel and updated with the
 // weighted running average (Sec. 3). A voxel has one writer, so fusion is deterministic.
+// Lower bounds of updated voxel values, per brick and per apron category: a voxel with
+// i == 0 (resp. j, k) also lies in the +1 apron of the brick at bx - 1 (by - 1, bz - 1).
+struct BoundAcc {
+  float v[8];  // own, x, y, z, xy, xz, yz, xyz
+  __device__ __forceinline__ void reset() {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = INFINITY;
+  }
+  __device__ __forceinline__ void note(int i, int j, int k, float sdf) {
+    v[0] = fminf(v[0], sdf);
+    if (i == 0) v[1] = fminf(v[1], sdf);
+    if (j == 0) v[2] = fminf(v[2], sdf);
+    if (k == 0) v[3] = fminf(v[3], sdf);
+    if (i == 0 && j == 0) v[4] = fminf(v[4], sdf);
+    if (i == 0 && k == 0) v[5] = fminf(v[5], sdf);
+    if (j == 0 && k == 0) v[6] = fminf(v[6], sdf);
+    if (i == 0 && j == 0 && k == 0) v[7] = fminf(v[7], sdf);
+  }
+};
+
+// Fold a CTA's bound accumulators into the brick bounds (own brick and the up-to-7 bricks
+// whose apron contains updated voxels of this brick).
+__device__ void publish_bounds(const MapView& m, BoundAcc& acc, int b, int bx, int by, int bz, int D) {
+  __shared__ float s_min[8][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    float x = acc.v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if (lane == 0) s_min[warp][q] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    const int q = threadIdx.x;
+    float x = INFINITY;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x = fminf(x, s_min[w][q]);
+    if (x < INFINITY) {
+      if (q == 0) {
+        atomic_min_float(m.bound + b, x);
+      } else {
+        const int dx = (q == 1 || q == 4 || q == 5 || q == 7) ? -1 : 0;
+        const int dy = (q == 2 || q == 4 || q == 6 || q == 7) ? -1 : 0;
+        const int dz = (q == 3 || q == 5 || q == 6 || q == 7) ? -1 : 0;
+        const int d = hash_find(m, bx + dx, by + dy, bz + dz);
+        const int slot = d >= 0 ? m.dir_slots[(size_t)d * 8 + D] : -1;
+        if (slot >= 0) atomic_min_float(m.bound + slot, x);
+      }
+    }
+  }
+  __syncthreads();
+}
+
 template <int STORE>
 __global__ void __launch_bounds__(256) k_fuse(MapView m, FuseFrame f) {
   const uint32_t nb = min(*((volatile uint32_t*)(m.counters + C_POOL)), m.pool_cap);
+  if (f.Tdev) f.T = pose_from_device(f.Tdev);
+  BoundAcc bacc;
   const float h = m.h;
   const float half_diag = 0.8660254f * 8.0f * h + h;
   for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
@@ -322,6 +380,7 @@ __global__ void __launch_bounds__(256) k_fuse(MapView m, FuseFrame f) {
       for (int q = 0; q < 4; ++q) out |= (f.pl[q][0] * cx + f.pl[q][1] * cy + f.pl[q][2] * cz) < -half_diag;
       if (out) continue;
     }
+    bacc.reset();
     for (int vi = threadIdx.x; vi < BVOX; vi += blockDim.x) {
       const int i = vi & 7, j = (vi >> 3) & 7, k = vi >> 6;
       // single-precision decision path: voxel centre, camera frame, projection
@@ -361,7 +420,9 @@ __global__ void __launch_bounds__(256) k_fuse(MapView m, FuseFrame f) {
         if (jump) continue;
         const float2 g = load_geom<STORE>(m, gi);
         const float wn = g.y + m.wcarve;
-        store_geom<STORE>(m, gi, (g.y * g.x + m.wcarve) / wn, fminf(wn, m.wmax));
+        const float nsdf = (g.y * g.x + m.wcarve) / wn;
+        store_geom<STORE>(m, gi, nsdf, fminf(wn, m.wmax));
+        bacc.note(i, j, k, STORE == DTSDF_STORE_FP16 ? unpack_geom16(pack_geom16(nsdf, 0.f)).x : nsdf);
         continue;
       }
       // membership of the pixel normal in direction D, and a camera-facing normal
@@ -381,7 +442,9 @@ __global__ void __launch_bounds__(256) k_fuse(MapView m, FuseFrame f) {
       if (!(w_d > 1e-12f)) w_d = 1e-12f;
       const float2 g = load_geom<STORE>(m, gi);
       const float wn = g.y + w_d;
-      store_geom<STORE>(m, gi, (g.y * g.x + w_d * sd) / wn, fminf(wn, m.wmax));
+      const float nsdf = (g.y * g.x + w_d * sd) / wn;
+      store_geom<STORE>(m, gi, nsdf, fminf(wn, m.wmax));
+      bacc.note(i, j, k, STORE == DTSDF_STORE_FP16 ? unpack_geom16(pack_geom16(nsdf, 0.f)).x : nsdf);
       if (m.color && f.rgb) {
         const float dist = rsqrt_exact(rdot3(e0, e1, e2, e0, e1, e2));
         if (dist < m.tau) {
@@ -412,7 +475,64 @@ __global__ void __launch_bounds__(256) k_fuse(MapView m, FuseFrame f) {
         }
       }
     }
+    publish_bounds(m, bacc, (int)b, bx, by, bz, D);
   }
+}
+
+// Exact bound of bricks [begin, end): minimum sdf over the brick and its +1 apron among
+// voxels with weight > 0 (+inf if none). Used for new bricks after fusion and after import.
+template <int STORE>
+__global__ void k_bounds_refresh(MapView m, int from_counter, uint32_t begin_arg, uint32_t end_arg) {
+  __shared__ int s_slot[8];
+  __shared__ float s_red[8];
+  const uint32_t count = min(*((volatile uint32_t*)(m.counters + C_POOL)), m.pool_cap);
+  uint32_t begin = begin_arg, end = min(end_arg, count);
+  if (from_counter) {
+    begin = *((volatile uint32_t*)(m.counters + C_POOL_BEFORE));
+    end = count;
+  }
+  for (uint32_t b = begin + blockIdx.x; b < end; b += gridDim.x) {
+    const int bd = m.brick_dir[b];
+    const int d = bd >> 3, D = bd & 7;
+    const int bx = m.dir_coord[4 * d], by = m.dir_coord[4 * d + 1], bz = m.dir_coord[4 * d + 2];
+    if (threadIdx.x < 8) {
+      const int q = threadIdx.x;
+      if (q == 0) {
+        s_slot[0] = (int)b;
+      } else {
+        const int dd = hash_find(m, bx + (q & 1), by + ((q >> 1) & 1), bz + ((q >> 2) & 1));
+        s_slot[q] = dd >= 0 ? m.dir_slots[(size_t)dd * 8 + D] : -1;
+      }
+    }
+    __syncthreads();
+    float mn = INFINITY;
+    for (int vi = threadIdx.x; vi < 729; vi += blockDim.x) {
+      const int x = vi % 9, y = (vi / 9) % 9, z = vi / 81;
+      const int q = (x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2);
+      const int slot = s_slot[q];
+      if (slot < 0) continue;
+      const float2 g = load_geom<STORE>(m, (size_t)slot * BVOX + ((z & 7) * 8 + (y & 7)) * 8 + (x & 7));
+      if (g.y > 0.0f) mn = fminf(mn, g.x);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = mn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float x = INFINITY;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x = fminf(x, s_red[w]);
+      m.bound[b] = x;
+    }
+    __syncthreads();
+  }
+}
+
+void launch_bounds_refresh(const MapView& m, int from_counter, uint32_t begin, uint32_t end, int num_sms,
+                           cudaStream_t s) {
+  if (m.storage == DTSDF_STORE_FP16)
+    k_bounds_refresh<DTSDF_STORE_FP16><<<num_sms * 4, 256, 0, s>>>(m, from_counter, begin, end);
+  else
+    k_bounds_refresh<DTSDF_STORE_FP32><<<num_sms * 4, 256, 0, s>>>(m, from_counter, begin, end);
 }
 
 // ------------------------------------------------------------------ import
@@ -454,6 +574,41 @@ __global__ void k_import_write(MapView m, const int32_t* __restrict__ coords, co
       }
     }
   }
+}
+
+// ------------------------------------------------------------------- poses
+// C = op(A) B for 4x4 affine transforms in device memory (op(A) = A or A^-1).
+__global__ void k_pose_compose(const double* A, int invert_a, const double* B, double* C) {
+  double M[16];
+  if (invert_a) {
+    const double a = A[0], b = A[1], c = A[2], d = A[4], e = A[5], f = A[6], g = A[8], h = A[9], k = A[10];
+    const double co0 = e * k - f * h, co1 = f * g - d * k, co2 = d * h - e * g;
+    const double det = a * co0 + b * co1 + c * co2;
+    const double id = 1.0 / det;
+    const double inv[9] = {co0 * id, (c * h - b * k) * id, (b * f - c * e) * id,
+                           co1 * id, (a * k - c * g) * id, (c * d - a * f) * id,
+                           co2 * id, (b * g - a * h) * id, (a * e - b * d) * id};
+    for (int i = 0; i < 3; ++i) {
+      for (int j = 0; j < 3; ++j) M[4 * i + j] = inv[3 * i + j];
+      M[4 * i + 3] = -(inv[3 * i] * A[3] + inv[3 * i + 1] * A[7] + inv[3 * i + 2] * A[11]);
+    }
+    M[12] = M[13] = M[14] = 0.0;
+    M[15] = 1.0;
+  } else {
+    for (int i = 0; i < 16; ++i) M[i] = A[i];
+  }
+  double out[16];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double acc = 0;
+      for (int q = 0; q < 4; ++q) acc += M[4 * i + q] * B[4 * q + j];
+      out[4 * i + j] = acc;
+    }
+  for (int i = 0; i < 16; ++i) C[i] = out[i];
+}
+
+void launch_pose_compose(const double* A, int invert_a, const double* B, double* C, cudaStream_t s) {
+  k_pose_compose<<<1, 1, 0, s>>>(A, invert_a, B, C);
 }
 
 // ------------------------------------------------------------------ export
@@ -499,9 +654,9 @@ void launch_preprocess(const float* depth, const Intr& K, float zmin, float zmax
   k_normals<<<grd, blk, 0, s>>>(P, K, N);
 }
 
-void launch_alloc(const MapView& m, const float4* P, const float4* N, int npix, const Pose32& T, int num_sms,
-                  cudaStream_t s) {
-  k_alloc_request<<<(npix + 255) / 256, 256, 0, s>>>(m, P, N, npix, T);
+void launch_alloc(const MapView& m, const float4* P, const float4* N, int npix, const Pose32& T, const double* Tdev,
+                  int num_sms, cudaStream_t s) {
+  k_alloc_request<<<(npix + 255) / 256, 256, 0, s>>>(m, P, N, npix, T, Tdev);
   k_alloc_assign<<<num_sms * 2, 256, 0, s>>>(m);
 }
 
@@ -514,11 +669,12 @@ void launch_pool_init(const MapView& m, int with_color, int num_sms, cudaStream_
   k_pool_init<<<num_sms * 8, 256, 0, s>>>(m, with_color);
 }
 
-void launch_fuse(const MapView& m, const Intr& K, const Pose32& T, const float4* P, const float4* N,
-                 const uint8_t* rgb, int num_sms, cudaStream_t s) {
+void launch_fuse(const MapView& m, const Intr& K, const Pose32& T, const double* Tdev, const float4* P,
+                 const float4* N, const uint8_t* rgb, int num_sms, cudaStream_t s) {
   FuseFrame f;
   f.K = K;
   f.T = T;
+  f.Tdev = Tdev;
   f.P = P;
   f.N = N;
   f.rgb = rgb;

@@ -20,57 +20,91 @@
 namespace dtsdf {
 
 constexpr int RT_X = 16, RT_Y = 8, RT_N = RT_X * RT_Y;
-constexpr int UNPROBED = -2;
 
 struct RenderArgs {
   Intr K;
-  Pose32 T;        // camera -> world
+  Pose32 T;            // camera -> world (unless Tdev is given)
+  const double* Tdev;  // camera -> world in device memory, or null
+  uint8_t* touched;    // instrumentation: brick flags (COUNT build only)
   float* depth;
   float4* normals;
   float4* color;
   int max_samples;
 };
 
-// Per-thread cache of the directory indices of the 27 blocks around the current cell,
-// held in shared memory (transposed so a warp's accesses are conflict free).
-struct NbCache {
-  int* s;
+// Per-thread view of the block cell the ray is in. Shared memory (strided by RT_N so a
+// warp's accesses hit distinct banks) holds the directory indices of the 27 surrounding
+// blocks and, for the directions allocated in the cell, the brick slots of the 2x2x2
+// blocks cell + {0,1}^3 that the trilinear corners of samples inside the cell can touch.
+// Both are filled lazily; `probed` / `filled` record which entries are valid.
+struct Cell {
+  int* dirc;        // 27 directory indices
+  int* slot;        // 6 x 8 brick slots: slot[(D * 8 + j) * RT_N]
   int cx, cy, cz;
-  __device__ __forceinline__ void reset(int x, int y, int z) {
+  uint32_t probed;  // bit j27: dirc[j27] valid
+  uint32_t filled;  // bit j8: slot row j8 valid for every direction in cmask
+  uint32_t cmask;   // directions allocated in the cell that hold weighted voxels near it
+  bool positive;    // every allocated direction's brick bound (brick + apron) is > 0
+  bool jumped;      // the march already jumped over this cell's positive samples
+
+  __device__ __noinline__ int dir_at(const MapView& m, int dx, int dy, int dz) {
+    if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) return hash_find(m, cx + dx, cy + dy, cz + dz);
+    const int j = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+    if (!((probed >> j) & 1u)) {
+      dirc[j * RT_N] = hash_find(m, cx + dx, cy + dy, cz + dz);
+      probed |= 1u << j;
+    }
+    return dirc[j * RT_N];
+  }
+  __device__ __noinline__ void enter(const MapView& m, int x, int y, int z) {
     cx = x;
     cy = y;
     cz = z;
-#pragma unroll
-    for (int j = 0; j < 27; ++j) s[j * RT_N] = UNPROBED;
-  }
-  __device__ __forceinline__ int dir(const MapView& m, int dx, int dy, int dz) {
-    if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) return hash_find(m, cx + dx, cy + dy, cz + dz);
-    const int j = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
-    int v = s[j * RT_N];
-    if (v == UNPROBED) {
-      v = hash_find(m, cx + dx, cy + dy, cz + dz);
-      s[j * RT_N] = v;
+    probed = 1u << 13;
+    filled = 0;
+    jumped = false;
+    const uint32_t v = hash_find_packed(m, x, y, z);
+    const int d0 = val_dir(v);
+    dirc[13 * RT_N] = d0;
+    cmask = val_mask(v);
+    positive = true;
+    if (cmask) {
+      uint32_t active = 0;
+      for (uint32_t mm = cmask; mm; mm &= mm - 1) {
+        const int E = __ffs(mm) - 1;
+        const int sl = __ldg(m.dir_slots + (size_t)d0 * 8 + E);
+        slot[(E * 8) * RT_N] = sl;
+        const float lb = sl >= 0 ? __ldg(m.bound + sl) : INFINITY;
+        // a bound of +inf: no voxel with weight in brick + apron, the direction is never present here
+        if (lb < INFINITY) active |= 1u << E;
+        positive &= lb > 0.0f;
+      }
+      cmask = active;
+      filled = 1u;
     }
-    return v;
+  }
+  __device__ __noinline__ void fill_row(const MapView& m, int j8) {
+    const int d = dir_at(m, j8 & 1, (j8 >> 1) & 1, j8 >> 2);
+    for (uint32_t mm = cmask; mm; mm &= mm - 1) {
+      const int E = __ffs(mm) - 1;
+      slot[(E * 8 + j8) * RT_N] = d >= 0 ? __ldg(m.dir_slots + (size_t)d * 8 + E) : -1;
+    }
+    filled |= 1u << j8;
+  }
+  // brick of direction D (allocated in the cell) in block cell + (j8 & 1, j8 >> 1 & 1, j8 >> 2)
+  __device__ __forceinline__ int slot_plus(const MapView& m, int D, int j8) {
+    if (!((filled >> j8) & 1u)) fill_row(m, j8);
+    return slot[(D * 8 + j8) * RT_N];
   }
 };
 
-template <int STORE>
-__device__ __forceinline__ float2 ld_geom(const MapView& m, size_t i) {
+// COUNT: instrumentation build of the marcher that flags every brick it reads
+// (touched[brick] for geometry, touched[pool_cap + brick] for colour); off in normal use.
+template <int STORE, bool COUNT>
+__device__ __forceinline__ float2 ld_geom(const MapView& m, size_t i, uint8_t* touched) {
+  if (COUNT) touched[i >> 9] = 1;
   if (STORE == DTSDF_STORE_FP16) return unpack_geom16(__ldg(m.geom16 + i));
   return __ldg(m.geom + i);
-}
-
-// Voxel (gx, gy, gz) of direction D; false if its brick is absent or its weight is 0.
-template <int STORE>
-__device__ __forceinline__ bool voxel(const MapView& m, NbCache& c, int D, int gx, int gy, int gz, float2& out) {
-  const int bx = gx >> 3, by = gy >> 3, bz = gz >> 3;
-  const int d = c.dir(m, bx - c.cx, by - c.cy, bz - c.cz);
-  if (d < 0) return false;
-  const int slot = __ldg(m.dir_slots + (size_t)d * 8 + D);
-  if (slot < 0) return false;
-  out = ld_geom<STORE>(m, (size_t)slot * BVOX + ((gz & 7) * 8 + (gy & 7)) * 8 + (gx & 7));
-  return out.y > 0.0f;
 }
 
 __device__ __forceinline__ float tri(const float v[8], float fx, float fy, float fz) {
@@ -83,35 +117,52 @@ __device__ __forceinline__ float tri(const float v[8], float fx, float fy, float
   return e + fz * (f - e);
 }
 
-// The 8 trilinear corners (corner c = (c&1, c>>1&1, c>>2&1)) of direction D at base voxel g.
-template <int STORE>
-__device__ __forceinline__ bool corners(const MapView& m, NbCache& c, int D, int g0, int g1, int g2, float sdf[8],
-                                        float w[8]) {
+__device__ __noinline__ int slot_far(const MapView& m, Cell& c, int D, int bx, int by, int bz) {
+  const int d = c.dir_at(m, bx, by, bz);
+  return d >= 0 ? __ldg(m.dir_slots + (size_t)d * 8 + D) : -1;
+}
+
+// Brick slot of direction D for voxel (gx, gy, gz) anywhere in the 27-block neighbourhood.
+__device__ __forceinline__ int slot_of(const MapView& m, Cell& c, int D, int gx, int gy, int gz) {
+  const int bx = (gx >> 3) - c.cx, by = (gy >> 3) - c.cy, bz = (gz >> 3) - c.cz;
+  if ((bx | by | bz) >= 0 && bx <= 1 && by <= 1 && bz <= 1) return c.slot_plus(m, D, bx | (by << 1) | (bz << 2));
+  return slot_far(m, c, D, bx, by, bz);
+}
+
+// The 8 trilinear corners (corner q = (q&1, q>>1&1, q>>2&1)) of direction D at base voxel g;
+// false unless all exist with weight > 0. Fully unrolled so the corner values stay in
+// registers; only the rare slot-table fills are out of line.
+template <int STORE, bool COUNT>
+__device__ __forceinline__ bool corners(const MapView& m, Cell& c, int D, int g0, int g1, int g2, float sdf[8],
+                                        float w[8], uint8_t* touched) {
   const int l0 = g0 & 7, l1 = g1 & 7, l2 = g2 & 7;
-  if (l0 < 7 && l1 < 7 && l2 < 7 && (g0 >> 3) == c.cx && (g1 >> 3) == c.cy && (g2 >> 3) == c.cz) {
-    // all corners inside the current cell's brick
-    const int d = c.dir(m, 0, 0, 0);
-    const int slot = __ldg(m.dir_slots + (size_t)d * 8 + D);
+  bool ok = true;
+  if (l0 < 7 && l1 < 7 && l2 < 7) {
+    // all corners in one brick
+    const int slot = slot_of(m, c, D, g0, g1, g2);
     if (slot < 0) return false;
     const size_t base = (size_t)slot * BVOX + (l2 * 8 + l1) * 8 + l0;
-    bool ok = true;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const float2 v = ld_geom<STORE>(m, base + ((q >> 2) & 1) * 64 + ((q >> 1) & 1) * 8 + (q & 1));
+      const float2 v = ld_geom<STORE, COUNT>(m, base + ((q >> 2) & 1) * 64 + ((q >> 1) & 1) * 8 + (q & 1), touched);
       sdf[q] = v.x;
       w[q] = v.y;
       ok &= v.y > 0.0f;
     }
     return ok;
   }
+  // corners spread over several bricks (base voxel on a brick face)
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    float2 v;
-    if (!voxel<STORE>(m, c, D, g0 + (q & 1), g1 + ((q >> 1) & 1), g2 + ((q >> 2) & 1), v)) return false;
+    const int x0 = g0 + (q & 1), x1 = g1 + ((q >> 1) & 1), x2 = g2 + ((q >> 2) & 1);
+    const int slot = ok ? slot_of(m, c, D, x0, x1, x2) : -1;
+    float2 v = make_float2(1.0f, 0.0f);
+    if (slot >= 0) v = ld_geom<STORE, COUNT>(m, (size_t)slot * BVOX + ((x2 & 7) * 8 + (x1 & 7)) * 8 + (x0 & 7), touched);
     sdf[q] = v.x;
     w[q] = v.y;
+    ok &= v.y > 0.0f;
   }
-  return true;
+  return ok;
 }
 
 __device__ __forceinline__ float w_dir_r(float c, float theta) {
@@ -129,8 +180,9 @@ struct Combined {
 };
 
 // Full combination of Eq. combine_weight at voxel coordinate g (fallback Eq. combine_tsdf_weight).
-template <int STORE, bool COLOR>
-__device__ Combined combine_full(const MapView& m, NbCache& c, uint32_t dmask, const float g[3], const float r[3]) {
+template <int STORE, bool COLOR, bool COUNT>
+__device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, const float g[3], const float r[3],
+                                                 uint8_t* touched, bool want_color) {
   Combined out;
   out.defined = 0;
   out.phi = 0.f;
@@ -145,10 +197,10 @@ __device__ Combined combine_full(const MapView& m, NbCache& c, uint32_t dmask, c
   bool any = false;
   const float inv2h = 0.5f / m.h;
 #pragma unroll 1
-  for (int D = 0; D < ND; ++D) {
-    if (!(dmask & (1u << D))) continue;
+  for (uint32_t mm = c.cmask; mm; mm &= mm - 1) {
+    const int D = __ffs(mm) - 1;
     float s[8], w[8];
-    if (!corners<STORE>(m, c, D, g0, g1, g2, s, w)) continue;
+    if (!corners<STORE, COUNT>(m, c, D, g0, g1, g2, s, w, touched)) continue;
     any = true;
     const float phiD = tri(s, fx, fy, fz);
     const float WD = tri(w, fx, fy, fz);
@@ -157,21 +209,27 @@ __device__ Combined combine_full(const MapView& m, NbCache& c, uint32_t dmask, c
     const float wf = WD * fmaxf(vr, 0.0f);
     fw += wf;
     facc += wf * phiD;
-    // central differences of the trilinear field at +-h along each axis
-    float grad[3];
+    // central differences of the trilinear field at +-h along each axis (one corner gather
+    // in a loop over the six offsets; accumulation by selects, no dynamic indexing)
+    float gx = 0.f, gy = 0.f, gz = 0.f;
     bool gok = true;
-#pragma unroll
-    for (int a = 0; a < 3 && gok; ++a) {
-      float sp[8], wp[8], sm[8], wm[8];
-      const int p0 = g0 + (a == 0), p1 = g1 + (a == 1), p2 = g2 + (a == 2);
-      const int m0 = g0 - (a == 0), m1 = g1 - (a == 1), m2 = g2 - (a == 2);
-      if (!corners<STORE>(m, c, D, p0, p1, p2, sp, wp) || !corners<STORE>(m, c, D, m0, m1, m2, sm, wm)) {
+#pragma unroll 1
+    for (int e = 0; e < 6; ++e) {
+      const int ax = e >> 1;
+      const int sgn = (e & 1) ? -1 : 1;
+      float se[8], we[8];
+      if (!corners<STORE, COUNT>(m, c, D, g0 + (ax == 0 ? sgn : 0), g1 + (ax == 1 ? sgn : 0), g2 + (ax == 2 ? sgn : 0),
+                                 se, we, touched)) {
         gok = false;
         break;
       }
-      grad[a] = (tri(sp, fx, fy, fz) - tri(sm, fx, fy, fz)) * inv2h;
+      const float val = (float)sgn * tri(se, fx, fy, fz) * inv2h;
+      gx += ax == 0 ? val : 0.f;
+      gy += ax == 1 ? val : 0.f;
+      gz += ax == 2 ? val : 0.f;
     }
     if (!gok) continue;
+    const float grad[3] = {gx, gy, gz};
     const float gn = sqrtf(grad[0] * grad[0] + grad[1] * grad[1] + grad[2] * grad[2]);
     if (!(gn > 1e-12f)) continue;
     const float n0 = grad[0] / gn, n1 = grad[1] / gn, n2 = grad[2] / gn;
@@ -185,7 +243,7 @@ __device__ Combined combine_full(const MapView& m, NbCache& c, uint32_t dmask, c
     out.n[0] += wc * n0;
     out.n[1] += wc * n1;
     out.n[2] += wc * n2;
-    if (COLOR) {
+    if (COLOR && want_color) {
       // trilinear colour of the 8 corners; contributes where the trilinear colour weight > 0
       const int gq[3] = {g0, g1, g2};
       float cr[8], cg[8], cb[8], cwt[8];
@@ -193,13 +251,13 @@ __device__ Combined combine_full(const MapView& m, NbCache& c, uint32_t dmask, c
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int x0 = gq[0] + (q & 1), x1 = gq[1] + ((q >> 1) & 1), x2 = gq[2] + ((q >> 2) & 1);
-        const int d = c.dir(m, (x0 >> 3) - c.cx, (x1 >> 3) - c.cy, (x2 >> 3) - c.cz);
-        const int slot = d >= 0 ? __ldg(m.dir_slots + (size_t)d * 8 + D) : -1;
+        const int slot = slot_of(m, c, D, x0, x1, x2);
         if (slot < 0) {
           cok = false;
           break;
         }
         const size_t vi = (size_t)slot * BVOX + ((x2 & 7) * 8 + (x1 & 7)) * 8 + (x0 & 7);
+        if (COUNT) touched[m.pool_cap + (vi >> 9)] = 1;
         if (STORE == DTSDF_STORE_FP16) {
           const uint32_t cv = __ldg(m.col8 + vi);
           cr[q] = (float)(cv & 0xFF);
@@ -235,19 +293,19 @@ __device__ Combined combine_full(const MapView& m, NbCache& c, uint32_t dmask, c
 
 // Sign of Phi from the present directions' trilinear values.
 // Returns 0 undefined, 1 positive, -1 non-positive, 2 undecided (needs the full combination).
-template <int STORE>
-__device__ __forceinline__ int sign_fast(const MapView& m, NbCache& c, uint32_t dmask, const float g[3],
-                                         const float r[3], float& lo) {
+template <int STORE, bool COUNT>
+__device__ __forceinline__ int sign_fast(const MapView& m, Cell& c, const float g[3], const float r[3], float& lo,
+                                         uint8_t* touched) {
   const float f0 = floorf(g[0]), f1 = floorf(g[1]), f2 = floorf(g[2]);
   const int g0 = (int)f0, g1 = (int)f1, g2 = (int)f2;
   const float fx = g[0] - f0, fy = g[1] - f1, fz = g[2] - f2;
   float mn = 2.f, mx = -2.f;
   bool any = false, facing = false;
 #pragma unroll 1
-  for (int D = 0; D < ND; ++D) {
-    if (!(dmask & (1u << D))) continue;
+  for (uint32_t mm = c.cmask; mm; mm &= mm - 1) {
+    const int D = __ffs(mm) - 1;
     float s[8], w[8];
-    if (!corners<STORE>(m, c, D, g0, g1, g2, s, w)) continue;
+    if (!corners<STORE, COUNT>(m, c, D, g0, g1, g2, s, w, touched)) continue;
     const float phiD = tri(s, fx, fy, fz);
     any = true;
     mn = fminf(mn, phiD);
@@ -263,17 +321,33 @@ __device__ __forceinline__ int sign_fast(const MapView& m, NbCache& c, uint32_t 
   return 2;
 }
 
-template <int STORE, bool COLOR>
-__global__ void __launch_bounds__(RT_N) k_render(MapView m, RenderArgs a) {
-  __shared__ int s_cache[27 * RT_N];
+// One loop, one state machine per lane: marching (MARCH), the two regular sub-step scans
+// of the refinement (SCAN), the full evaluations at the final bracket ends (ENDS_A/B) and
+// the output evaluations (OUT) all evaluate the field at one call site of the sign test
+// and one of the full combination, so lanes in different phases stay converged.
+enum { S_MARCH = 0, S_SCAN = 1, S_ENDS_A = 2, S_ENDS_B = 3, S_OUT = 4, S_DONE = 5 };
+
+template <int STORE, bool COLOR, bool COUNT>
+__global__ void __launch_bounds__(RT_N, 4) k_render(MapView m, RenderArgs a) {
+  __shared__ int s_dirc[27 * RT_N];
+  __shared__ int s_slot[ND * 8 * RT_N];
+  uint8_t* touched = a.touched;
+  // COUNT build: per-ray event counts (samples, full combinations, cells, allocated cells, hits, jumps)
+  unsigned long long* ctr = COUNT ? (unsigned long long*)(touched + 2 * (size_t)m.pool_cap) : nullptr;
+  uint32_t n_samples = 0, n_full = 0, n_cells = 0, n_acells = 0, n_jumps = 0;
   const int tid = threadIdx.y * RT_X + threadIdx.x;
   const int u = blockIdx.x * RT_X + threadIdx.x;
   const int v = blockIdx.y * RT_Y + threadIdx.y;
   if (u >= a.K.W || v >= a.K.H) return;
   const int pix = v * a.K.W + u;
-  NbCache cache;
-  cache.s = s_cache + tid;
-  cache.cx = cache.cy = cache.cz = 0x7fffffff;
+  if (a.Tdev) a.T = pose_from_device(a.Tdev);
+  Cell cell;
+  cell.dirc = s_dirc + tid;
+  cell.slot = s_slot + tid;
+  cell.cx = cell.cy = cell.cz = 0x7fffffff;
+  cell.cmask = 0;
+  cell.positive = false;
+  cell.jumped = true;
 
   // unit ray in camera and world frame
   const float rc0 = (u - a.K.cx) / a.K.fx, rc1 = (v - a.K.cy) / a.K.fy;
@@ -287,182 +361,210 @@ __global__ void __launch_bounds__(RT_N) k_render(MapView m, RenderArgs a) {
   const float org[3] = {m.ox, m.oy, m.oz};
   const float inv_h = 1.0f / m.h;
   const float step = 0.5f * m.h;
-  const int k0 = (int)ceilf(m.zmin * rl / step);
   const int k1 = (int)floorf(m.zmax * rl / step);
   const float bsz = 8.0f * m.h;
 
-  uint32_t cmask = 0;
+  int state = S_MARCH;
+  int k = (int)ceilf(m.zmin * rl / step);
   bool prev_def = false;
   float prev_phi = 0.f;
   int hit_k = -1;
-  int k = k0;
-  for (int it = 0; it < a.max_samples && k <= k1; ++it) {
-    const float t = (float)k * step;
+  // refinement state
+  float ta = 0.f, tb = 0.f, a0 = 0.f, dt = 0.f, sprev = 0.f, fa = 0.f, ts = 0.f;
+  int lvl = 0, j = 0, out_e = 0;
+  bool da = false;
+  float out_depth = 0.f;
+  float4 out_n = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 out_c = make_float4(0.f, 0.f, 0.f, 0.f);
+
+  for (int it = 0; it < a.max_samples && state != S_DONE; ++it) {
+    float t;
+    if (state == S_MARCH) {
+      if (k > k1) break;
+      t = (float)k * step;
+    } else if (state == S_SCAN) {
+      t = a0 + (float)j * dt;
+    } else if (state == S_ENDS_A) {
+      t = ta;
+    } else if (state == S_ENDS_B) {
+      t = tb;
+    } else {
+      t = out_e == 0 ? (float)hit_k * step : (out_e == 1 ? (float)(hit_k - 1) * step : ts);
+    }
     float g[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) g[q] = (o[q] + t * r[q] - org[q]) * inv_h;
     const int cx = ((int)floorf(g[0])) >> 3, cy = ((int)floorf(g[1])) >> 3, cz = ((int)floorf(g[2])) >> 3;
-    if (cx != cache.cx || cy != cache.cy || cz != cache.cz) {
-      cache.reset(cx, cy, cz);
-      const int d0 = cache.dir(m, 0, 0, 0);
-      cmask = d0 >= 0 ? (uint32_t)__ldg(m.dir_slots + (size_t)d0 * 8 + SLOT_MASK) : 0u;
-    }
-    if (cmask == 0) {
-      // no direction allocated in this cell: no sample in it can be defined; jump past it
-      float tex = 3.4e38f;
-      const int cc[3] = {cx, cy, cz};
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        if (r[q] > 0.f)
-          tex = fminf(tex, (org[q] + (cc[q] + 1) * bsz - o[q]) / r[q]);
-        else if (r[q] < 0.f)
-          tex = fminf(tex, (org[q] + cc[q] * bsz - o[q]) / r[q]);
+    if (cx != cell.cx || cy != cell.cy || cz != cell.cz) {
+      cell.enter(m, cx, cy, cz);
+      if (COUNT && state == S_MARCH) {
+        ++n_cells;
+        n_acells += cell.cmask != 0;
       }
-      const int kn = (int)ceilf(tex / step);
-      prev_def = false;
-      k = max(k + 1, kn);
-      continue;
     }
-    float lo = 0.f;
-    int sg = sign_fast<STORE>(m, cache, cmask, g, r, lo);
-    if (sg == 2) {
-      const Combined cb = combine_full<STORE, false>(m, cache, cmask, g, r);
-      sg = cb.defined ? (cb.phi > 0.f ? 1 : -1) : 0;
-      lo = cb.phi;
+    if (state == S_MARCH) {
+      const bool empty = cell.cmask == 0;
+      if (empty || (cell.positive && !cell.jumped)) {
+        // an empty cell holds no defined sample; in an all-positive cell (brick bounds cover
+        // the +1 apron its trilinear corners reach) no sample can end a crossing: resume two
+        // samples before its exit, the first of which fixes the state
+        float tex = 3.4e38f;
+        const int cc[3] = {cx, cy, cz};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          if (r[q] > 0.f)
+            tex = fminf(tex, (org[q] + (cc[q] + 1) * bsz - o[q]) / r[q]);
+          else if (r[q] < 0.f)
+            tex = fminf(tex, (org[q] + cc[q] * bsz - o[q]) / r[q]);
+        }
+        if (empty) {
+          if (COUNT) ++n_samples;
+          prev_def = false;
+          k = max(k + 1, (int)ceilf(tex / step));
+          continue;
+        }
+        cell.jumped = true;
+        const int kj = (int)floorf(tex / step) - 1;
+        if (kj > k) {
+          if (COUNT) ++n_jumps;
+          k = kj;
+          prev_def = false;
+          continue;
+        }
+      }
+      if (COUNT) ++n_samples;
     }
-    if (sg == 0) {
-      prev_def = false;
-      ++k;
-      continue;
+    // ---- evaluate the field at t (single call sites)
+    int sg = 0;
+    float val = 0.f;
+    Combined C;
+    C.defined = 0;
+    C.wsum = 0.f;
+    if (cell.cmask) {
+      bool full = state >= S_ENDS_A;
+      if (!full) {
+        sg = sign_fast<STORE, COUNT>(m, cell, g, r, val, touched);
+        full = sg == 2;
+      }
+      if (full) {
+        if (COUNT && state == S_MARCH) ++n_full;
+        C = combine_full<STORE, COLOR, COUNT>(m, cell, g, r, touched, state == S_OUT);
+        sg = C.defined ? (C.phi > 0.f ? 1 : -1) : 0;
+        val = C.phi;
+      }
     }
-    if (sg < 0 && prev_def && prev_phi > 0.f) {
-      hit_k = k;
-      break;
+    // ---- transitions
+    if (state == S_MARCH) {
+      if (sg == 0) {
+        prev_def = false;
+        ++k;
+      } else if (sg < 0 && prev_def && prev_phi > 0.f) {
+        // crossing between samples k-1 and k: two scans of 8 regular sub-steps
+        hit_k = k;
+        ta = (float)(k - 1) * step;
+        tb = (float)k * step;
+        lvl = 0;
+        a0 = ta;
+        dt = (tb - ta) * 0.125f;
+        sprev = ta;
+        j = 1;
+        state = S_SCAN;
+      } else {
+        prev_def = true;
+        prev_phi = sg > 0 ? val : -1.f;
+        ++k;
+      }
+    } else if (state == S_SCAN) {
+      // an undefined probe counts as free space
+      bool level_done = false;
+      if (sg < 0) {
+        tb = t;
+        level_done = true;
+      } else {
+        sprev = t;
+        level_done = ++j == 8;
+      }
+      if (level_done) {
+        ta = sprev;
+        if (++lvl == 2) {
+          state = S_ENDS_A;
+        } else {
+          a0 = ta;
+          dt = (tb - ta) * 0.125f;
+          sprev = ta;
+          j = 1;
+        }
+      }
+    } else if (state == S_ENDS_A) {
+      da = C.defined && C.phi > 0.f;
+      fa = C.phi;
+      state = S_ENDS_B;
+    } else if (state == S_ENDS_B) {
+      // root: linear interpolation of Phi over the final bracket
+      const bool db = C.defined && C.phi <= 0.f;
+      ts = (da && db) ? ta + (tb - ta) * fa / (fa - C.phi) : 0.5f * (ta + tb);
+      out_e = 0;
+      state = S_OUT;
+    } else {
+      // normal and colour at the first grid sample behind the crossing, else at the
+      // sample in front of it, else at the root
+      const float nl = sqrtf(C.n[0] * C.n[0] + C.n[1] * C.n[1] + C.n[2] * C.n[2]);
+      if (C.defined && C.wsum > 0.f && nl > 0.f) {
+        const float n0 = C.n[0] / nl, n1 = C.n[1] / nl, n2 = C.n[2] / nl;
+        // world -> camera: R^T n
+        const float c0 = a.T.R[0] * n0 + a.T.R[3] * n1 + a.T.R[6] * n2;
+        const float c1 = a.T.R[1] * n0 + a.T.R[4] * n1 + a.T.R[7] * n2;
+        const float c2 = a.T.R[2] * n0 + a.T.R[5] * n1 + a.T.R[8] * n2;
+        out_depth = ts / rl;
+        out_n = make_float4(c0, c1, c2, out_depth);
+        if (COLOR && C.cw > 0.f) out_c = make_float4(C.rgb[0] / C.cw, C.rgb[1] / C.cw, C.rgb[2] / C.cw, 1.0f);
+        state = S_DONE;
+      } else if (++out_e == 3) {
+        state = S_DONE;
+      }
     }
-    prev_def = true;
-    prev_phi = sg > 0 ? lo : -1.f;
-    ++k;
   }
-
-  float out_depth = 0.f;
-  float4 out_n = make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 out_c = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (hit_k >= 0) {
-    // bracket [t_a, t_b] with Phi(t_a) > 0 >= Phi(t_b)
-    float ta = (float)(hit_k - 1) * step, tb = (float)hit_k * step;
-    auto eval = [&](float t) -> Combined {
-      float g[3];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) g[q] = (o[q] + t * r[q] - org[q]) * inv_h;
-      const int cx = ((int)floorf(g[0])) >> 3, cy = ((int)floorf(g[1])) >> 3, cz = ((int)floorf(g[2])) >> 3;
-      if (cx != cache.cx || cy != cache.cy || cz != cache.cz) {
-        cache.reset(cx, cy, cz);
-        const int d0 = cache.dir(m, 0, 0, 0);
-        cmask = d0 >= 0 ? (uint32_t)__ldg(m.dir_slots + (size_t)d0 * 8 + SLOT_MASK) : 0u;
-      }
-      Combined cb;
-      if (cmask == 0) {
-        cb.defined = 0;
-        cb.wsum = 0.f;
-        return cb;
-      }
-      return combine_full<STORE, false>(m, cache, cmask, g, r);
-    };
-    // small regular steps: two scans of 8 sub-steps keep the first sub-interval where
-    // Phi turns <= 0 (an undefined probe counts as free space); sign tests only
-#pragma unroll 1
-    for (int lvl = 0; lvl < 2; ++lvl) {
-      const float a0 = ta, dt = (tb - ta) * 0.125f;
-      float prev = ta;
-#pragma unroll 1
-      for (int j = 1; j < 8; ++j) {
-        const float tj = a0 + (float)j * dt;
-        float g[3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) g[q] = (o[q] + tj * r[q] - org[q]) * inv_h;
-        const int cx = ((int)floorf(g[0])) >> 3, cy = ((int)floorf(g[1])) >> 3, cz = ((int)floorf(g[2])) >> 3;
-        if (cx != cache.cx || cy != cache.cy || cz != cache.cz) {
-          cache.reset(cx, cy, cz);
-          const int d0 = cache.dir(m, 0, 0, 0);
-          cmask = d0 >= 0 ? (uint32_t)__ldg(m.dir_slots + (size_t)d0 * 8 + SLOT_MASK) : 0u;
-        }
-        int sg = 0;
-        if (cmask) {
-          float lo;
-          sg = sign_fast<STORE>(m, cache, cmask, g, r, lo);
-          if (sg == 2) {
-            const Combined cb = combine_full<STORE, false>(m, cache, cmask, g, r);
-            sg = cb.defined ? (cb.phi > 0.f ? 1 : -1) : 0;
-          }
-        }
-        if (sg < 0) {
-          tb = tj;
-          break;
-        }
-        prev = tj;
-      }
-      ta = prev;
-    }
-    // root: linear interpolation of Phi over the final bracket
-    const Combined A = eval(ta), B = eval(tb);
-    float ts = 0.5f * (ta + tb);
-    if (A.defined && A.phi > 0.f && B.defined && B.phi <= 0.f) ts = ta + (tb - ta) * A.phi / (A.phi - B.phi);
-    // normal and colour at the first grid sample behind the crossing (the sample that
-    // decided the hit), else at the sample in front of it, else at the refined root
-    const float ends[3] = {(float)hit_k * step, (float)(hit_k - 1) * step, ts};
-#pragma unroll 1
-    for (int e = 0; e < 3; ++e) {
-      float g[3];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) g[q] = (o[q] + ends[e] * r[q] - org[q]) * inv_h;
-      const int cx = ((int)floorf(g[0])) >> 3, cy = ((int)floorf(g[1])) >> 3, cz = ((int)floorf(g[2])) >> 3;
-      if (cx != cache.cx || cy != cache.cy || cz != cache.cz) {
-        cache.reset(cx, cy, cz);
-        const int d0 = cache.dir(m, 0, 0, 0);
-        cmask = d0 >= 0 ? (uint32_t)__ldg(m.dir_slots + (size_t)d0 * 8 + SLOT_MASK) : 0u;
-      }
-      if (!cmask) continue;
-      const Combined H = combine_full<STORE, COLOR>(m, cache, cmask, g, r);
-      const float nl = sqrtf(H.n[0] * H.n[0] + H.n[1] * H.n[1] + H.n[2] * H.n[2]);
-      if (!(H.defined && H.wsum > 0.f && nl > 0.f)) continue;
-      const float n0 = H.n[0] / nl, n1 = H.n[1] / nl, n2 = H.n[2] / nl;
-      // world -> camera: R^T n
-      const float c0 = a.T.R[0] * n0 + a.T.R[3] * n1 + a.T.R[6] * n2;
-      const float c1 = a.T.R[1] * n0 + a.T.R[4] * n1 + a.T.R[7] * n2;
-      const float c2 = a.T.R[2] * n0 + a.T.R[5] * n1 + a.T.R[8] * n2;
-      out_depth = ts / rl;
-      out_n = make_float4(c0, c1, c2, out_depth);
-      if (COLOR && H.cw > 0.f) out_c = make_float4(H.rgb[0] / H.cw, H.rgb[1] / H.cw, H.rgb[2] / H.cw, 1.0f);
-      break;
-    }
+  if (COUNT) {
+    atomicAdd(ctr + 0, (unsigned long long)n_samples);
+    atomicAdd(ctr + 1, (unsigned long long)n_full);
+    atomicAdd(ctr + 2, (unsigned long long)n_cells);
+    atomicAdd(ctr + 3, (unsigned long long)n_acells);
+    atomicAdd(ctr + 4, (unsigned long long)(out_depth > 0.f));
+    atomicAdd(ctr + 5, (unsigned long long)n_jumps);
   }
   a.depth[pix] = out_depth;
   a.normals[pix] = out_n;
   if (COLOR && a.color) a.color[pix] = out_c;
 }
 
-void launch_render(const MapView& m, const Intr& K, const Pose32& T, float* depth, float4* normals, float4* color,
-                   cudaStream_t s) {
+void launch_render(const MapView& m, const Intr& K, const Pose32& T, const double* Tdev, float* depth,
+                   float4* normals, float4* color, cudaStream_t s, uint8_t* touched) {
   RenderArgs a;
   a.K = K;
   a.T = T;
+  a.Tdev = Tdev;
+  a.touched = touched;
   a.depth = depth;
   a.normals = normals;
   a.color = color;
-  a.max_samples = 1 << 16;
+  a.max_samples = 1 << 17;
   dim3 blk(RT_X, RT_Y), grd((K.W + RT_X - 1) / RT_X, (K.H + RT_Y - 1) / RT_Y);
   const bool col = m.color && color;
-  if (m.storage == DTSDF_STORE_FP16) {
-    if (col)
-      k_render<DTSDF_STORE_FP16, true><<<grd, blk, 0, s>>>(m, a);
-    else
-      k_render<DTSDF_STORE_FP16, false><<<grd, blk, 0, s>>>(m, a);
+#define DTSDF_RENDER(ST, CO, CN) k_render<ST, CO, CN><<<grd, blk, 0, s>>>(m, a)
+  if (touched) {
+    if (m.storage == DTSDF_STORE_FP16) {
+      if (col) DTSDF_RENDER(DTSDF_STORE_FP16, true, true); else DTSDF_RENDER(DTSDF_STORE_FP16, false, true);
+    } else {
+      if (col) DTSDF_RENDER(DTSDF_STORE_FP32, true, true); else DTSDF_RENDER(DTSDF_STORE_FP32, false, true);
+    }
   } else {
-    if (col)
-      k_render<DTSDF_STORE_FP32, true><<<grd, blk, 0, s>>>(m, a);
-    else
-      k_render<DTSDF_STORE_FP32, false><<<grd, blk, 0, s>>>(m, a);
+    if (m.storage == DTSDF_STORE_FP16) {
+      if (col) DTSDF_RENDER(DTSDF_STORE_FP16, true, false); else DTSDF_RENDER(DTSDF_STORE_FP16, false, false);
+    } else {
+      if (col) DTSDF_RENDER(DTSDF_STORE_FP32, true, false); else DTSDF_RENDER(DTSDF_STORE_FP32, false, false);
+    }
   }
+#undef DTSDF_RENDER
 }
 
 }  // namespace dtsdf
