@@ -114,6 +114,7 @@ static void map_free(dtsdf_map m) {
   cudaFree(m->v.col8);
   cudaFree(m->v.brick_dir);
   cudaFree(m->v.bound);
+  cudaFree(m->v.occ);
   cudaFree(m->v.counters);
   cudaFree(m->v.work);
   cudaFree(m->P);
@@ -190,6 +191,7 @@ dtsdf_status dtsdf_create(const dtsdf_params* params, void* stream, dtsdf_map* o
   }
   ALLOC(v.brick_dir, sizeof(int32_t) * (size_t)bricks);
   ALLOC(v.bound, sizeof(float) * (size_t)bricks);
+  ALLOC(v.occ, sizeof(uint32_t) * 2 * (size_t)OCC_WORDS);
   ALLOC(v.counters, sizeof(uint32_t) * C_COUNT);
   ALLOC(v.work, sizeof(int32_t) * (size_t)v.work_cap);
 #undef ALLOC
@@ -204,7 +206,8 @@ dtsdf_status dtsdf_create(const dtsdf_params* params, void* stream, dtsdf_map* o
       (e = cudaMemsetAsync(v.vals, 0xFF, sizeof(uint32_t) * hcap, s)) != cudaSuccess ||
       (e = cudaMemsetAsync(v.req, 0, sizeof(uint32_t) * hcap, s)) != cudaSuccess ||
       (e = cudaMemsetAsync(v.dir_slots, 0xFF, sizeof(int32_t) * 8 * (size_t)v.dir_cap, s)) != cudaSuccess ||
-      (e = cudaMemsetAsync(v.counters, 0, sizeof(uint32_t) * C_COUNT, s)) != cudaSuccess) {
+      (e = cudaMemsetAsync(v.counters, 0, sizeof(uint32_t) * C_COUNT, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(v.occ, 0, sizeof(uint32_t) * 2 * (size_t)OCC_WORDS, s)) != cudaSuccess) {
     map_free(m);
     return cuda_fail(e, "dtsdf_create init");
   }

@@ -133,6 +133,7 @@ struct MapView {
   uint32_t* col8;   // FP16 storage: u8 r, g, b, u8 colour weight (1/ (255/w_max) units)
   int32_t* brick_dir;  // per brick: dir index * 8 + D
   float* bound;        // per brick: lower bound of sdf over its voxels and its +1 apron with weight > 0
+  uint32_t* occ;       // occupancy filters: 2 x OCC_WORDS words (blocks, then 4^3-block super-cells)
   uint32_t pool_cap;
   uint32_t* counters;
   int32_t* work;
@@ -163,6 +164,25 @@ __device__ __forceinline__ void atomic_min_float(float* addr, float v) {
     atomicMin((int*)addr, __float_as_int(v));
   else
     atomicMax((unsigned int*)addr, __float_as_uint(v));
+}
+
+// Occupancy filters: one bit per hashed block (and per hashed super-cell of 4^3 blocks),
+// set when a block gets a directory entry. No false negatives; a false positive only costs
+// the real hash probe.
+constexpr uint32_t OCC_BITS_LOG2 = 23;
+constexpr uint32_t OCC_WORDS = 1u << (OCC_BITS_LOG2 - 5);
+__host__ __device__ __forceinline__ uint32_t occ_bit(int bx, int by, int bz, int level) {
+  const unsigned long long k = pack_block(bx, by, bz) ^ (level ? 0x5bd1e9955bd1e995ull : 0ull);
+  return hash_slot(k, (1u << OCC_BITS_LOG2) - 1u);
+}
+__device__ __forceinline__ void occ_set(const MapView& m, int bx, int by, int bz) {
+  const uint32_t a = occ_bit(bx, by, bz, 0), b = occ_bit(bx >> 2, by >> 2, bz >> 2, 1);
+  atomicOr(m.occ + (a >> 5), 1u << (a & 31));
+  atomicOr(m.occ + OCC_WORDS + (b >> 5), 1u << (b & 31));
+}
+__device__ __forceinline__ bool occ_test(const MapView& m, int bx, int by, int bz, int level) {
+  const uint32_t a = level ? occ_bit(bx >> 2, by >> 2, bz >> 2, 1) : occ_bit(bx, by, bz, 0);
+  return (__ldg(m.occ + (level ? OCC_WORDS : 0) + (a >> 5)) >> (a & 31)) & 1u;
 }
 
 // Storage accessors ---------------------------------------------------------

@@ -194,6 +194,7 @@ __global__ void k_alloc_assign(MapView m) {
       d = (int)nd;
       int bx, by, bz;
       unpack_block(m.keys[i], bx, by, bz);
+      occ_set(m, bx, by, bz);
       m.dir_coord[4 * d] = bx;
       m.dir_coord[4 * d + 1] = by;
       m.dir_coord[4 * d + 2] = bz;
@@ -238,6 +239,7 @@ __global__ void k_dense_fill(MapView m, int nb) {
     i = (i + 1) & m.hmask;
   }
   m.vals[i] = pack_val(idx, 0x3Fu);
+  occ_set(m, bx, by, bz);
   m.dir_coord[4 * idx] = bx;
   m.dir_coord[4 * idx + 1] = by;
   m.dir_coord[4 * idx + 2] = bz;

@@ -32,10 +32,25 @@ struct RenderArgs {
   int max_samples;
 };
 
-// Per-thread view of the block cell the ray is in. Shared memory (strided by RT_N so a
-// warp's accesses hit distinct banks) holds the directory indices of the 27 surrounding
-// blocks and, for the directions allocated in the cell, the brick slots of the 2x2x2
-// blocks cell + {0,1}^3 that the trilinear corners of samples inside the cell can touch.
+// Out-of-line hash probe over explicit pointers (keeps callers' state in registers).
+__device__ __noinline__ uint32_t probe_block(const unsigned long long* __restrict__ keys,
+                                             const uint32_t* __restrict__ vals, uint32_t hmask, int bx, int by,
+                                             int bz) {
+  const unsigned long long k = pack_block(bx, by, bz);
+  uint32_t i = hash_slot(k, hmask);
+  for (int p = 0; p < MAX_PROBE; ++p) {
+    const unsigned long long kk = __ldg(keys + i);
+    if (kk == k) return __ldg(vals + i);
+    if (kk == EMPTY_KEY) return VAL_EMPTY;
+    i = (i + 1) & hmask;
+  }
+  return VAL_EMPTY;
+}
+
+// Per-thread state of the block cell the ray is in, kept in registers. Shared memory
+// (strided by RT_N so a warp's accesses hit distinct banks) holds the directory indices of
+// the 27 surrounding blocks and, for the directions active in the cell, the brick slots of
+// the 2x2x2 blocks cell + {0,1}^3 that trilinear corners of samples in the cell can touch.
 // Both are filled lazily; `probed` / `filled` record which entries are valid.
 struct Cell {
   int* dirc;        // 27 directory indices
@@ -44,59 +59,69 @@ struct Cell {
   uint32_t probed;  // bit j27: dirc[j27] valid
   uint32_t filled;  // bit j8: slot row j8 valid for every direction in cmask
   uint32_t cmask;   // directions allocated in the cell that hold weighted voxels near it
-  bool positive;    // every allocated direction's brick bound (brick + apron) is > 0
+  bool positive;    // every active direction's brick bound (brick + apron) is > 0
   bool jumped;      // the march already jumped over this cell's positive samples
-
-  __device__ __noinline__ int dir_at(const MapView& m, int dx, int dy, int dz) {
-    if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) return hash_find(m, cx + dx, cy + dy, cz + dz);
-    const int j = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
-    if (!((probed >> j) & 1u)) {
-      dirc[j * RT_N] = hash_find(m, cx + dx, cy + dy, cz + dz);
-      probed |= 1u << j;
-    }
-    return dirc[j * RT_N];
-  }
-  __device__ __noinline__ void enter(const MapView& m, int x, int y, int z) {
-    cx = x;
-    cy = y;
-    cz = z;
-    probed = 1u << 13;
-    filled = 0;
-    jumped = false;
-    const uint32_t v = hash_find_packed(m, x, y, z);
-    const int d0 = val_dir(v);
-    dirc[13 * RT_N] = d0;
-    cmask = val_mask(v);
-    positive = true;
-    if (cmask) {
-      uint32_t active = 0;
-      for (uint32_t mm = cmask; mm; mm &= mm - 1) {
-        const int E = __ffs(mm) - 1;
-        const int sl = __ldg(m.dir_slots + (size_t)d0 * 8 + E);
-        slot[(E * 8) * RT_N] = sl;
-        const float lb = sl >= 0 ? __ldg(m.bound + sl) : INFINITY;
-        // a bound of +inf: no voxel with weight in brick + apron, the direction is never present here
-        if (lb < INFINITY) active |= 1u << E;
-        positive &= lb > 0.0f;
-      }
-      cmask = active;
-      filled = 1u;
-    }
-  }
-  __device__ __noinline__ void fill_row(const MapView& m, int j8) {
-    const int d = dir_at(m, j8 & 1, (j8 >> 1) & 1, j8 >> 2);
-    for (uint32_t mm = cmask; mm; mm &= mm - 1) {
-      const int E = __ffs(mm) - 1;
-      slot[(E * 8 + j8) * RT_N] = d >= 0 ? __ldg(m.dir_slots + (size_t)d * 8 + E) : -1;
-    }
-    filled |= 1u << j8;
-  }
-  // brick of direction D (allocated in the cell) in block cell + (j8 & 1, j8 >> 1 & 1, j8 >> 2)
-  __device__ __forceinline__ int slot_plus(const MapView& m, int D, int j8) {
-    if (!((filled >> j8) & 1u)) fill_row(m, j8);
-    return slot[(D * 8 + j8) * RT_N];
-  }
 };
+
+__device__ __forceinline__ int cell_dir(const MapView& m, Cell& c, int dx, int dy, int dz) {
+  if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1)
+    return val_dir(probe_block(m.keys, m.vals, m.hmask, c.cx + dx, c.cy + dy, c.cz + dz));
+  const int j = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+  if (!((c.probed >> j) & 1u)) {
+    c.dirc[j * RT_N] = val_dir(probe_block(m.keys, m.vals, m.hmask, c.cx + dx, c.cy + dy, c.cz + dz));
+    c.probed |= 1u << j;
+  }
+  return c.dirc[j * RT_N];
+}
+
+__device__ __forceinline__ void cell_enter(const MapView& m, Cell& c, int x, int y, int z) {
+  c.cx = x;
+  c.cy = y;
+  c.cz = z;
+  c.probed = 1u << 13;
+  c.filled = 0;
+  c.jumped = false;
+  const uint32_t v = probe_block(m.keys, m.vals, m.hmask, x, y, z);
+  const int d0 = val_dir(v);
+  c.dirc[13 * RT_N] = d0;
+  uint32_t active = 0;
+  bool positive = true;
+#pragma unroll 1
+  for (uint32_t mm = val_mask(v); mm; mm &= mm - 1) {
+    const int E = __ffs(mm) - 1;
+    const int sl = __ldg(m.dir_slots + (size_t)d0 * 8 + E);
+    c.slot[(E * 8) * RT_N] = sl;
+    const float lb = sl >= 0 ? __ldg(m.bound + sl) : INFINITY;
+    // a bound of +inf: no voxel with weight in brick + apron, the direction is never present here
+    if (lb < INFINITY) active |= 1u << E;
+    positive &= lb > 0.0f;
+  }
+  c.cmask = active;
+  c.positive = positive;
+  c.filled = active ? 1u : 0u;
+}
+
+// brick of direction D (active in the cell) in block cell + (j8 & 1, j8 >> 1 & 1, j8 >> 2)
+__device__ __forceinline__ int slot_plus(const MapView& m, Cell& c, int D, int j8) {
+  if (!((c.filled >> j8) & 1u)) {
+    const int d = cell_dir(m, c, j8 & 1, (j8 >> 1) & 1, j8 >> 2);
+#pragma unroll 1
+    for (uint32_t mm = c.cmask; mm; mm &= mm - 1) {
+      const int E = __ffs(mm) - 1;
+      c.slot[(E * 8 + j8) * RT_N] = d >= 0 ? __ldg(m.dir_slots + (size_t)d * 8 + E) : -1;
+    }
+    c.filled |= 1u << j8;
+  }
+  return c.slot[(D * 8 + j8) * RT_N];
+}
+
+// Brick slot of direction D for voxel (gx, gy, gz) anywhere in the 27-block neighbourhood.
+__device__ __forceinline__ int slot_of(const MapView& m, Cell& c, int D, int gx, int gy, int gz) {
+  const int bx = (gx >> 3) - c.cx, by = (gy >> 3) - c.cy, bz = (gz >> 3) - c.cz;
+  if ((bx | by | bz) >= 0 && bx <= 1 && by <= 1 && bz <= 1) return slot_plus(m, c, D, bx | (by << 1) | (bz << 2));
+  const int d = cell_dir(m, c, bx, by, bz);
+  return d >= 0 ? __ldg(m.dir_slots + (size_t)d * 8 + D) : -1;
+}
 
 // COUNT: instrumentation build of the marcher that flags every brick it reads
 // (touched[brick] for geometry, touched[pool_cap + brick] for colour); off in normal use.
@@ -107,62 +132,51 @@ __device__ __forceinline__ float2 ld_geom(const MapView& m, size_t i, uint8_t* t
   return __ldg(m.geom + i);
 }
 
-__device__ __forceinline__ float tri(const float v[8], float fx, float fy, float fz) {
-  const float a = v[0] + fx * (v[1] - v[0]);
-  const float b = v[2] + fx * (v[3] - v[2]);
-  const float c = v[4] + fx * (v[5] - v[4]);
-  const float d = v[6] + fx * (v[7] - v[6]);
-  const float e = a + fy * (b - a);
-  const float f = c + fy * (d - c);
-  return e + fz * (f - e);
+// Trilinear weight of corner q = (q&1, q>>1&1, q>>2&1).
+__device__ __forceinline__ float corner_w(int q, float fx, float fy, float fz) {
+  return ((q & 1) ? fx : 1.0f - fx) * ((q & 2) ? fy : 1.0f - fy) * ((q & 4) ? fz : 1.0f - fz);
 }
 
-__device__ __noinline__ int slot_far(const MapView& m, Cell& c, int D, int bx, int by, int bz) {
-  const int d = c.dir_at(m, bx, by, bz);
-  return d >= 0 ? __ldg(m.dir_slots + (size_t)d * 8 + D) : -1;
-}
-
-// Brick slot of direction D for voxel (gx, gy, gz) anywhere in the 27-block neighbourhood.
-__device__ __forceinline__ int slot_of(const MapView& m, Cell& c, int D, int gx, int gy, int gz) {
-  const int bx = (gx >> 3) - c.cx, by = (gy >> 3) - c.cy, bz = (gz >> 3) - c.cz;
-  if ((bx | by | bz) >= 0 && bx <= 1 && by <= 1 && bz <= 1) return c.slot_plus(m, D, bx | (by << 1) | (bz << 2));
-  return slot_far(m, c, D, bx, by, bz);
-}
-
-// The 8 trilinear corners (corner q = (q&1, q>>1&1, q>>2&1)) of direction D at base voxel g;
-// false unless all exist with weight > 0. Fully unrolled so the corner values stay in
-// registers; only the rare slot-table fills are out of line.
+// Trilinear sdf and weight of direction D at base voxel g with fractions (fx, fy, fz);
+// false unless all 8 corners exist with weight > 0. Accumulates on the fly (no arrays).
 template <int STORE, bool COUNT>
-__device__ __forceinline__ bool corners(const MapView& m, Cell& c, int D, int g0, int g1, int g2, float sdf[8],
-                                        float w[8], uint8_t* touched) {
+__device__ __forceinline__ bool interp(const MapView& m, Cell& c, int D, int g0, int g1, int g2, float fx, float fy,
+                                       float fz, float& phi, float& W, uint8_t* touched) {
   const int l0 = g0 & 7, l1 = g1 & 7, l2 = g2 & 7;
-  bool ok = true;
+  float acc = 0.f, accw = 0.f;
   if (l0 < 7 && l1 < 7 && l2 < 7) {
     // all corners in one brick
     const int slot = slot_of(m, c, D, g0, g1, g2);
     if (slot < 0) return false;
     const size_t base = (size_t)slot * BVOX + (l2 * 8 + l1) * 8 + l0;
+    bool ok = true;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const float2 v = ld_geom<STORE, COUNT>(m, base + ((q >> 2) & 1) * 64 + ((q >> 1) & 1) * 8 + (q & 1), touched);
-      sdf[q] = v.x;
-      w[q] = v.y;
+      const float wq = corner_w(q, fx, fy, fz);
       ok &= v.y > 0.0f;
+      acc += wq * v.x;
+      accw += wq * v.y;
     }
+    phi = acc;
+    W = accw;
     return ok;
   }
   // corners spread over several bricks (base voxel on a brick face)
-#pragma unroll
+#pragma unroll 1
   for (int q = 0; q < 8; ++q) {
     const int x0 = g0 + (q & 1), x1 = g1 + ((q >> 1) & 1), x2 = g2 + ((q >> 2) & 1);
-    const int slot = ok ? slot_of(m, c, D, x0, x1, x2) : -1;
-    float2 v = make_float2(1.0f, 0.0f);
-    if (slot >= 0) v = ld_geom<STORE, COUNT>(m, (size_t)slot * BVOX + ((x2 & 7) * 8 + (x1 & 7)) * 8 + (x0 & 7), touched);
-    sdf[q] = v.x;
-    w[q] = v.y;
-    ok &= v.y > 0.0f;
+    const int slot = slot_of(m, c, D, x0, x1, x2);
+    if (slot < 0) return false;
+    const float2 v = ld_geom<STORE, COUNT>(m, (size_t)slot * BVOX + ((x2 & 7) * 8 + (x1 & 7)) * 8 + (x0 & 7), touched);
+    if (!(v.y > 0.0f)) return false;
+    const float wq = corner_w(q, fx, fy, fz);
+    acc += wq * v.x;
+    accw += wq * v.y;
   }
-  return ok;
+  phi = acc;
+  W = accw;
+  return true;
 }
 
 __device__ __forceinline__ float w_dir_r(float c, float theta) {
@@ -199,42 +213,37 @@ __device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, cons
 #pragma unroll 1
   for (uint32_t mm = c.cmask; mm; mm &= mm - 1) {
     const int D = __ffs(mm) - 1;
-    float s[8], w[8];
-    if (!corners<STORE, COUNT>(m, c, D, g0, g1, g2, s, w, touched)) continue;
+    float phiD, WD;
+    if (!interp<STORE, COUNT>(m, c, D, g0, g1, g2, fx, fy, fz, phiD, WD, touched)) continue;
     any = true;
-    const float phiD = tri(s, fx, fy, fz);
-    const float WD = tri(w, fx, fy, fz);
     // fallback weight W^D max(0, <v^D, -r>)
     const float vr = (D & 1) ? r[D >> 1] : -r[D >> 1];
     const float wf = WD * fmaxf(vr, 0.0f);
     fw += wf;
     facc += wf * phiD;
-    // central differences of the trilinear field at +-h along each axis (one corner gather
-    // in a loop over the six offsets; accumulation by selects, no dynamic indexing)
+    // central differences of the trilinear field at +-h along each axis
     float gx = 0.f, gy = 0.f, gz = 0.f;
     bool gok = true;
 #pragma unroll 1
     for (int e = 0; e < 6; ++e) {
       const int ax = e >> 1;
       const int sgn = (e & 1) ? -1 : 1;
-      float se[8], we[8];
-      if (!corners<STORE, COUNT>(m, c, D, g0 + (ax == 0 ? sgn : 0), g1 + (ax == 1 ? sgn : 0), g2 + (ax == 2 ? sgn : 0),
-                                 se, we, touched)) {
+      float pe, we;
+      if (!interp<STORE, COUNT>(m, c, D, g0 + (ax == 0 ? sgn : 0), g1 + (ax == 1 ? sgn : 0), g2 + (ax == 2 ? sgn : 0),
+                                fx, fy, fz, pe, we, touched)) {
         gok = false;
         break;
       }
-      const float val = (float)sgn * tri(se, fx, fy, fz) * inv2h;
+      const float val = (float)sgn * pe * inv2h;
       gx += ax == 0 ? val : 0.f;
       gy += ax == 1 ? val : 0.f;
       gz += ax == 2 ? val : 0.f;
     }
     if (!gok) continue;
-    const float grad[3] = {gx, gy, gz};
-    const float gn = sqrtf(grad[0] * grad[0] + grad[1] * grad[1] + grad[2] * grad[2]);
+    const float gn = sqrtf(gx * gx + gy * gy + gz * gz);
     if (!(gn > 1e-12f)) continue;
-    const float n0 = grad[0] / gn, n1 = grad[1] / gn, n2 = grad[2] / gn;
-    const float nD[3] = {n0, n1, n2};
-    const float cosv = (D & 1) ? -nD[D >> 1] : nD[D >> 1];
+    const float n0 = gx / gn, n1 = gy / gn, n2 = gz / gn;
+    const float cosv = (D == 0) ? n0 : (D == 1) ? -n0 : (D == 2) ? n1 : (D == 3) ? -n1 : (D == 4) ? n2 : -n2;
     const float facing = fmaxf(-(n0 * r[0] + n1 * r[1] + n2 * r[2]), 0.0f);
     const float wc = w_dir_r(cosv, m.theta) * facing * WD;
     if (!(wc > 0.0f)) continue;
@@ -245,12 +254,11 @@ __device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, cons
     out.n[2] += wc * n2;
     if (COLOR && want_color) {
       // trilinear colour of the 8 corners; contributes where the trilinear colour weight > 0
-      const int gq[3] = {g0, g1, g2};
-      float cr[8], cg[8], cb[8], cwt[8];
+      float cr = 0.f, cg = 0.f, cb = 0.f, cwt = 0.f;
       bool cok = true;
-#pragma unroll
+#pragma unroll 1
       for (int q = 0; q < 8; ++q) {
-        const int x0 = gq[0] + (q & 1), x1 = gq[1] + ((q >> 1) & 1), x2 = gq[2] + ((q >> 2) & 1);
+        const int x0 = g0 + (q & 1), x1 = g1 + ((q >> 1) & 1), x2 = g2 + ((q >> 2) & 1);
         const int slot = slot_of(m, c, D, x0, x1, x2);
         if (slot < 0) {
           cok = false;
@@ -258,25 +266,26 @@ __device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, cons
         }
         const size_t vi = (size_t)slot * BVOX + ((x2 & 7) * 8 + (x1 & 7)) * 8 + (x0 & 7);
         if (COUNT) touched[m.pool_cap + (vi >> 9)] = 1;
+        const float wq = corner_w(q, fx, fy, fz);
         if (STORE == DTSDF_STORE_FP16) {
           const uint32_t cv = __ldg(m.col8 + vi);
-          cr[q] = (float)(cv & 0xFF);
-          cg[q] = (float)((cv >> 8) & 0xFF);
-          cb[q] = (float)((cv >> 16) & 0xFF);
-          cwt[q] = (float)(cv >> 24);
+          cr += wq * (float)(cv & 0xFF);
+          cg += wq * (float)((cv >> 8) & 0xFF);
+          cb += wq * (float)((cv >> 16) & 0xFF);
+          cwt += wq * (float)(cv >> 24);
         } else {
           const float4 cv = __ldg(m.col + vi);
-          cr[q] = cv.x;
-          cg[q] = cv.y;
-          cb[q] = cv.z;
-          cwt[q] = cv.w;
+          cr += wq * cv.x;
+          cg += wq * cv.y;
+          cb += wq * cv.z;
+          cwt += wq * cv.w;
         }
       }
-      if (cok && tri(cwt, fx, fy, fz) > 0.0f) {
+      if (cok && cwt > 0.0f) {
         out.cw += wc;
-        out.rgb[0] += wc * tri(cr, fx, fy, fz);
-        out.rgb[1] += wc * tri(cg, fx, fy, fz);
-        out.rgb[2] += wc * tri(cb, fx, fy, fz);
+        out.rgb[0] += wc * cr;
+        out.rgb[1] += wc * cg;
+        out.rgb[2] += wc * cb;
       }
     }
   }
@@ -291,7 +300,7 @@ __device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, cons
   return out;
 }
 
-// Sign of Phi from the present directions' trilinear values.
+// Sign of Phi from the present directions' trilinear values (Phi is their convex combination).
 // Returns 0 undefined, 1 positive, -1 non-positive, 2 undecided (needs the full combination).
 template <int STORE, bool COUNT>
 __device__ __forceinline__ int sign_fast(const MapView& m, Cell& c, const float g[3], const float r[3], float& lo,
@@ -304,9 +313,8 @@ __device__ __forceinline__ int sign_fast(const MapView& m, Cell& c, const float 
 #pragma unroll 1
   for (uint32_t mm = c.cmask; mm; mm &= mm - 1) {
     const int D = __ffs(mm) - 1;
-    float s[8], w[8];
-    if (!corners<STORE, COUNT>(m, c, D, g0, g1, g2, s, w, touched)) continue;
-    const float phiD = tri(s, fx, fy, fz);
+    float phiD, WD;
+    if (!interp<STORE, COUNT>(m, c, D, g0, g1, g2, fx, fy, fz, phiD, WD, touched)) continue;
     any = true;
     mn = fminf(mn, phiD);
     mx = fmaxf(mx, phiD);
@@ -396,7 +404,31 @@ __global__ void __launch_bounds__(RT_N, 4) k_render(MapView m, RenderArgs a) {
     for (int q = 0; q < 3; ++q) g[q] = (o[q] + t * r[q] - org[q]) * inv_h;
     const int cx = ((int)floorf(g[0])) >> 3, cy = ((int)floorf(g[1])) >> 3, cz = ((int)floorf(g[2])) >> 3;
     if (cx != cell.cx || cy != cell.cy || cz != cell.cz) {
-      cell.enter(m, cx, cy, cz);
+      if (state == S_MARCH) {
+        // occupancy filters: cross an empty super-cell (4^3 blocks) or block without a probe
+        const int lv = occ_test(m, cx, cy, cz, 1) ? (occ_test(m, cx, cy, cz, 0) ? -1 : 0) : 1;
+        if (lv >= 0) {
+          const int sh = lv ? 2 : 0;
+          const float cs = bsz * (float)(1 << sh);
+          const int cc[3] = {cx >> sh, cy >> sh, cz >> sh};
+          float tex = 3.4e38f;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            if (r[q] > 0.f)
+              tex = fminf(tex, (org[q] + (cc[q] + 1) * cs - o[q]) / r[q]);
+            else if (r[q] < 0.f)
+              tex = fminf(tex, (org[q] + cc[q] * cs - o[q]) / r[q]);
+          }
+          if (COUNT) {
+            ++n_cells;
+            ++n_samples;
+          }
+          prev_def = false;
+          k = max(k + 1, (int)ceilf(tex / step));
+          continue;
+        }
+      }
+      cell_enter(m, cell, cx, cy, cz);
       if (COUNT && state == S_MARCH) {
         ++n_cells;
         n_acells += cell.cmask != 0;
