@@ -234,6 +234,26 @@ DTSDF_API dtsdf_status dtsdf_icp_solve(dtsdf_icp icp, const dtsdf_render_out* re
                                        int32_t sim3, double* T_rel_dev, const double* T_rs_dev,
                                        const dtsdf_icp_opts* opts, dtsdf_icp_stats* stats_dev, void* stream);
 
+/* One Gauss-Newton iteration of geometric point-to-plane ICP (SE(3) or Sim(3)) that allocates
+ * no device memory. The paper has no counterpart: this serves callers that cannot allocate when
+ * they run ICP - inside CUDA stream capture (cudaMalloc is not allowed there), in real-time loops
+ * where cudaMalloc's implicit device synchronisation would stall other streams, or under a host
+ * application that owns all device memory. Every input and output is a caller-owned device
+ * buffer: depth (K_cur->height x K_cur->width float32, already outlier-filtered, 0 invalid),
+ * ref (the render's normals, float4 with the depth in w; K_ref its intrinsics), T_rel_dev
+ * (16 doubles, current -> render camera, read and updated in place unless degenerate) and
+ * stats_dev (one dtsdf_icp_stats, overwritten). The reduction's scratch is a fixed file-scope
+ * device array of 256 KB that every GPU loading the library keeps until exit; images of more
+ * than 1048576 pixels are rejected (DTSDF_ERR_INVALID_ARG). The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress) and should be made before any stream
+ * capture. All calls share the scratch and it keeps the last call's contents; calls that
+ * overlap on the GPU race on it. Asynchronous on `stream`. */
+DTSDF_API dtsdf_status dtsdf_icp_step_noalloc(const float* depth, const dtsdf_intrinsics* K_cur,
+                                              const dtsdf_render_out* ref, const dtsdf_intrinsics* K_ref,
+                                              int32_t sim3, float eps, float z_min, int32_t min_rows,
+                                              double stop_norm, double* T_rel_dev, dtsdf_icp_stats* stats_dev,
+                                              void* stream);
+
 /* Exponential map of se(3) (sim3 = 0, xi[6]) or sim(3) (sim3 = 1, xi[7]) evaluated by the
  * library's device code (the closed form of the matrix exponential of the 4x4 generator);
  * out: host 16 doubles. Synchronous; exposed for verification. */

@@ -94,6 +94,9 @@ SIGNATURES = {
                              ctypes.POINTER(IcpOpts), ctypes.POINTER(IcpStats), P], c_int32),
     "dtsdf_icp_solve": ([P, ctypes.POINTER(RenderOut), ctypes.POINTER(Intrinsics), c_int32, P, P,
                          ctypes.POINTER(IcpOpts), P, P], c_int32),
+    "dtsdf_icp_step_noalloc": ([P, ctypes.POINTER(Intrinsics), ctypes.POINTER(RenderOut),
+                                ctypes.POINTER(Intrinsics), c_int32, c_float, c_float, c_int32, c_double, P, P, P],
+                               c_int32),
     "dtsdf_exp": ([c_int32, P, P], c_int32),
     "dtsdf_last_error": ([], ctypes.c_char_p),
     "dtsdf_version": ([], ctypes.c_char_p),

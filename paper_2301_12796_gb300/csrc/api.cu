@@ -87,6 +87,11 @@ uint32_t next_pow2(uint64_t x) {
 
 }  // namespace
 
+dtsdf_status dtsdf::set_error(dtsdf_status s, const char* msg) {
+  g_last_error = msg;
+  return s;
+}
+
 struct dtsdf_map_s {
   dtsdf_params p;
   MapView v;

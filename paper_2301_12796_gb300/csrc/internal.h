@@ -26,6 +26,9 @@ struct IcpLaunch {
   double stop_norm;
 };
 
+// Record a message for dtsdf_last_error() and return the status.
+dtsdf_status set_error(dtsdf_status s, const char* msg);
+
 void launch_preprocess(const float* depth, const Intr& K, float zmin, float zmax, float dsup, float4* P, float4* N,
                        cudaStream_t s);
 void launch_alloc(const MapView& m, const float4* P, const float4* N, int npix, const Pose32& T, const double* Tdev,
