@@ -36,7 +36,7 @@
  *                     are present
  *   render march      samples at t = k * h/2 along the unit ray; the first pair of
  *                     consecutive defined samples with Phi > 0 >= Phi is the hit,
- *                     refined by two regular 8-step scans for the first sign change
+ *                     refined by one regular 4-step scan for the first sign change
  *                     and linear interpolation; the normal and colour are taken at
  *                     the first grid sample behind the crossing (else the sample in
  *                     front of it, else the root)
@@ -815,14 +815,14 @@ static int render_pixel(const omap* m, const double* T, double fx, double fy, do
       continue;
     }
     if (prev_def && prev_phi > 0 && cb.phi <= 0) {
-      /* refine the crossing in [prev_t, t] by small regular steps (Sec. 4): two scans of
-         8 sub-steps each keep the first sub-interval where Phi turns <= 0 (an undefined
-         probe counts as free space); the root is the linear interpolation of Phi over the
-         final h/128-wide bracket */
+      /* refine the crossing in [prev_t, t] by small regular steps (Sec. 4): a scan of 4
+         sub-steps keeps the first sub-interval where Phi turns <= 0 (an undefined probe
+         counts as free space); the root is the linear interpolation of Phi over that
+         h/8-wide bracket */
       double lo = prev_t, hi = t;
-      for (int lvl = 0; lvl < 2; ++lvl) {
-        double a0 = lo, dt = (hi - lo) / 8.0, prev = lo;
-        for (int j = 1; j < 8; ++j) {
+      for (int lvl = 0; lvl < 1; ++lvl) {
+        double a0 = lo, dt = (hi - lo) / 4.0, prev = lo;
+        for (int j = 1; j < 4; ++j) {
           double tj = a0 + j * dt;
           double xj[3] = {o[0] + tj * r[0], o[1] + tj * r[1], o[2] + tj * r[2]};
           combo cj;

@@ -8,11 +8,12 @@
 // combined SDF Phi of Eq. combine_weight is a convex combination of the present
 // directions' trilinear values Phi^D, so its sign follows from min/max of those alone
 // whenever they agree (8 voxel reads per direction); the full combination with
-// central-difference gradients (32 voxel reads per direction) is computed only where
+// central-difference gradients (7 trilinear gathers per direction) is computed only where
 // the signs disagree and for the outputs. The reported crossing is the first pair of
-// consecutive defined samples with Phi > 0 >= Phi; it is refined by two scans of 8
-// regular sub-steps to the first sign change and linear interpolation over the final
-// h/128-wide bracket.
+// consecutive defined samples with Phi > 0 >= Phi; it is refined by a scan of 4 regular
+// sub-steps to the first sign change and linear interpolation over the final h/8-wide
+// bracket. The per-block occupancy filters let empty space be crossed without probes, and
+// per-brick lower bounds let cells whose present directions are all positive be jumped.
 #include <math.h>
 
 #include "internal.h"
@@ -329,7 +330,7 @@ __device__ __forceinline__ int sign_fast(const MapView& m, Cell& c, const float 
   return 2;
 }
 
-// One loop, one state machine per lane: marching (MARCH), the two regular sub-step scans
+// One loop, one state machine per lane: marching (MARCH), the regular sub-step scan
 // of the refinement (SCAN), the full evaluations at the final bracket ends (ENDS_A/B) and
 // the output evaluations (OUT) all evaluate the field at one call site of the sign test
 // and one of the full combination, so lanes in different phases stay converged.
@@ -379,7 +380,7 @@ __global__ void __launch_bounds__(RT_N, 4) k_render(MapView m, RenderArgs a) {
   int hit_k = -1;
   // refinement state
   float ta = 0.f, tb = 0.f, a0 = 0.f, dt = 0.f, sprev = 0.f, fa = 0.f, ts = 0.f;
-  int lvl = 0, j = 0, out_e = 0;
+  int j = 0, out_e = 0;
   bool da = false;
   float out_depth = 0.f;
   float4 out_n = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -491,13 +492,12 @@ __global__ void __launch_bounds__(RT_N, 4) k_render(MapView m, RenderArgs a) {
         prev_def = false;
         ++k;
       } else if (sg < 0 && prev_def && prev_phi > 0.f) {
-        // crossing between samples k-1 and k: two scans of 8 regular sub-steps
+        // crossing between samples k-1 and k: a scan of 4 regular sub-steps
         hit_k = k;
         ta = (float)(k - 1) * step;
         tb = (float)k * step;
-        lvl = 0;
         a0 = ta;
-        dt = (tb - ta) * 0.125f;
+        dt = (tb - ta) * 0.25f;
         sprev = ta;
         j = 1;
         state = S_SCAN;
@@ -514,18 +514,11 @@ __global__ void __launch_bounds__(RT_N, 4) k_render(MapView m, RenderArgs a) {
         level_done = true;
       } else {
         sprev = t;
-        level_done = ++j == 8;
+        level_done = ++j == 4;
       }
       if (level_done) {
         ta = sprev;
-        if (++lvl == 2) {
-          state = S_ENDS_A;
-        } else {
-          a0 = ta;
-          dt = (tb - ta) * 0.125f;
-          sprev = ta;
-          j = 1;
-        }
+        state = S_ENDS_A;
       }
     } else if (state == S_ENDS_A) {
       da = C.defined && C.phi > 0.f;
