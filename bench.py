@@ -20,6 +20,7 @@ import argparse
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -60,7 +61,8 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.environ.get("DTSDF_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(),
+                                                                        f"dtsdf_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:

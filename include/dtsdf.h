@@ -53,7 +53,7 @@ typedef enum {
 
 typedef enum { DTSDF_STORE_FP32 = 0, DTSDF_STORE_FP16 = 1 } dtsdf_storage;
 
-/* Map parameters (Sec. 3, Sec. 4, Sec. 6 of the paper; see the readings in the design notes). */
+/* Map parameters (Sec. 3, 4 and 7 of the paper; constants the paper leaves open take the stated defaults). */
 typedef struct {
   float voxel_size;     /* h, metres */
   float truncation;     /* tau, metres (Eq. point-to-plane normalises by it) */
@@ -61,7 +61,7 @@ typedef struct {
   float w_max;          /* cap of the accumulated depth and colour weights */
   float w_carve;        /* constant weight of a free-space carving update (Sec. 3) */
   float z_min, z_max;   /* valid depth range, metres; z_min also enters Eq. ICP_weight */
-  float delta_sup;      /* outlier filter: neighbour supports a depth if |dz| <= delta_sup (Sec. 6) */
+  float delta_sup;      /* outlier filter: neighbour supports a depth if |dz| <= delta_sup (Sec. 7) */
   int32_t carve_radius; /* carving needs no depth jump > tau within this many pixels (Sec. 3: 2) */
   int32_t dense_dim;    /* > 0: dense grid of dense_dim^3 voxels (multiple of 8), every block
                            allocated at creation; 0: sparse voxel-block hash */
@@ -109,7 +109,7 @@ DTSDF_API dtsdf_status dtsdf_create(const dtsdf_params* params, void* stream, dt
 DTSDF_API dtsdf_status dtsdf_destroy(dtsdf_map map);
 
 /* Fuse one frame taken at pose T_wc (Sec. 3 voxel-projection fusion): outlier filter and
- * cross-product normals (Sec. 6), allocation of the (block, direction) bricks that the
+ * cross-product normals (Sec. 7), allocation of the (block, direction) bricks that the
  * segment [p - tau r, p + tau r] of every pixel with a normal crosses, for each direction
  * of Eq. angular_threshold, then the weighted running average of Eq. point-to-plane with
  * the weights of Eq. combined_fusion_weight and Eq. color_weight, and free-space carving.
@@ -169,12 +169,13 @@ DTSDF_API dtsdf_status dtsdf_map_import(dtsdf_map map, const int32_t* coords, co
 typedef struct {
   int32_t levels;       /* pyramid levels used, 1..4 (level 0 = full resolution) */
   int32_t iters[4];     /* iteration cap per level, index = level (0 finest) */
-  float eps[4];         /* distance outlier threshold per level, metres (Sec. 7: 0.005 fine / 0.05 coarse) */
-  float photo_thr[4];   /* intensity outlier threshold per level (Sec. 7: 0.05 fine / 0.175 coarse) */
+  float eps[4];         /* distance outlier threshold per level, metres (Sec. 8: 0.005 fine / 0.05 coarse) */
+  float photo_thr[4];   /* intensity outlier threshold per level (Sec. 8: 0.05 fine / 0.175 coarse) */
   float lambda;         /* photometric weight of Eq. combined_icp (0.1); 0 disables the term */
   float z_min;          /* z_min of Eq. ICP_weight */
-  double stop_norm;     /* stop a level when ||xi|| < stop_norm (Sec. 7: 1e-6) */
+  double stop_norm;     /* stop a level when ||xi|| < stop_norm (Sec. 8: 1e-6) */
   int32_t min_rows;     /* fewer rows than this -> DTSDF_ERR_DEGENERATE */
+  int32_t kahan;        /* 1: Kahan-compensated FP32 accumulation of the per-pixel sums */
 } dtsdf_icp_opts;
 
 /* Result of one Gauss-Newton iteration. H (row-major, dim x dim in the top-left of 7x7
@@ -198,7 +199,7 @@ typedef struct {
 DTSDF_API dtsdf_status dtsdf_icp_create(int32_t max_width, int32_t max_height, int32_t levels, dtsdf_icp* out);
 DTSDF_API dtsdf_status dtsdf_icp_destroy(dtsdf_icp icp);
 
-/* Current frame: outlier filter (Sec. 6), then the depth pyramid (2x2 mean of valid depths,
+/* Current frame: outlier filter (Sec. 7), then the depth pyramid (2x2 mean of valid depths,
  * f/2, (c - 0.5)/2) and, if rgb is given, the intensity pyramid I = (0.299 R + 0.587 G +
  * 0.114 B) / 255. Asynchronous. */
 DTSDF_API dtsdf_status dtsdf_icp_set_frame(dtsdf_icp icp, const dtsdf_frame* cur, float z_min, float z_max,
@@ -219,7 +220,7 @@ DTSDF_API dtsdf_status dtsdf_icp_step(dtsdf_icp icp, const dtsdf_render_out* ref
                             int32_t level, double T_rel[16], const double* T_rs, const dtsdf_icp_opts* opts,
                             dtsdf_icp_stats* stats, void* stream);
 
-/* Same in Sim(3) (Sec. 5.3, Eq. sim3_derivative): T_rel = [s R | t], 7x7 normal equations. */
+/* Same in Sim(3) (Sec. 6, Eq. sim3_derivative): T_rel = [s R | t], 7x7 normal equations. */
 DTSDF_API dtsdf_status dtsdf_icp_sim3_step(dtsdf_icp icp, const dtsdf_render_out* ref, const dtsdf_intrinsics* K_ref,
                                  int32_t level, double T_rel[16], const double* T_rs,
                                  const dtsdf_icp_opts* opts, dtsdf_icp_stats* stats, void* stream);

@@ -6,7 +6,7 @@ It shares no code, headers, tables or constants with the CUDA library and never
 imports it; the two meet only through the seeded inputs of ``scenes``.
 
 * ``dtsdf_oracle.c`` (plain C, double precision): preprocessing, block
-  allocation, voxel-projection fusion and ray-cast rendering (Sec. 3, 4, 6).
+  allocation, voxel-projection fusion and ray-cast rendering (Sec. 3, 4, 7).
 * ``icp.py`` (numpy, double precision): pyramid, projective association,
   point-to-plane residuals and Jacobians in SE(3) and Sim(3), photometric
   frame-to-keyframe rows, normal equations, Cholesky solve and the exponential
@@ -96,7 +96,7 @@ def w_dir(cos_angle: float, theta: float) -> float:
 
 
 def preprocess(depth: np.ndarray, K, z_min: float, z_max: float, delta_sup: float) -> dict:
-    """Depth outlier filter and cross-product normals (Sec. 6)."""
+    """Depth outlier filter and cross-product normals (Sec. 7)."""
     L = _load()
     d = np.ascontiguousarray(depth, np.float32)
     H, W = d.shape
@@ -111,7 +111,7 @@ def preprocess(depth: np.ndarray, K, z_min: float, z_max: float, delta_sup: floa
 
 
 def segment_blocks(a, b, block_size: float, origin=(0.0, 0.0, 0.0)) -> np.ndarray:
-    """Blocks crossed by segment a-b (single-precision 3D DDA, Sec. 6 allocation)."""
+    """Blocks crossed by segment a-b (single-precision 3D DDA, Sec. 7 allocation)."""
     L = _load()
     A = np.ascontiguousarray(a, np.float32)
     B = np.ascontiguousarray(b, np.float32)
@@ -142,7 +142,7 @@ class Params:
 
 
 class OracleMap:
-    """Directional TSDF in double precision: (block, D) hash of 8^3 bricks (Sec. 6)."""
+    """Directional TSDF in double precision: (block, D) hash of 8^3 bricks (Sec. 7)."""
 
     def __init__(self, params: Params):
         self.params = params

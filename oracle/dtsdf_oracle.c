@@ -19,11 +19,11 @@
  *   Sec. 4  ray-cast rendering (regular probing, then refinement of the first
  *           positive-to-negative transition), Eq. combine_weight,
  *           Eq. combine_tsdf_weight (no-gradient fallback).
- *   Sec. 6  voxel-block hashing of 8^3 blocks keyed by (x, y, z, D); depth
+ *   Sec. 7  voxel-block hashing of 8^3 blocks keyed by (x, y, z, D); depth
  *           outlier filter (two supporting neighbours) and cross-product normals.
  *   Sec. 5.1 Eq. ICP_weight, reused as the fusion depth weight.
  *
- * Readings of points the paper leaves open (each also listed in the design notes):
+ * Readings of points the paper leaves open (the GPU path implements the same ones):
  *   direction weight  w_dir = clamp((theta - acos<n,v>) / (2 theta - pi/2), 0, 1)
  *   depth weight      w_depth = 1 / (z + 1 - z_min)^2       (the ICP weight)
  *   angle weight      w_angle = max(0, <n, -r>)             (r: unit pixel ray)
@@ -243,10 +243,10 @@ int om_brick_data(const omap* m, int bx, int by, int bz, int D, double* out) {
 
 /* ===================================================== preprocessing (A0) == */
 /*
- * Depth outlier filter (Sec. 6): a pixel with depth in [z_min, z_max] is kept only
+ * Depth outlier filter (Sec. 7): a pixel with depth in [z_min, z_max] is kept only
  * if at least two of its 8 neighbours are in range and differ by at most
  * delta_sup. Normals: cross product of the central differences of the
- * back-projected neighbours in x and y (Sec. 6), oriented toward the camera;
+ * back-projected neighbours in x and y (Sec. 7), oriented toward the camera;
  * valid only where the centre and the 4 neighbours survived the filter.
  * Back-projection follows Eq. reprojection: (z (u - cx)/fx, z (v - cy)/fy, z).
  */
@@ -384,7 +384,7 @@ int om_preprocess(const float* depth, int W, int H, float fx, float fy, float cx
 
 /* ======================================================== allocation (A1) == */
 /*
- * Blocks of 8^3 voxels (Sec. 6) are allocated for every (block, D) whose cube
+ * Blocks of 8^3 voxels (Sec. 7) are allocated for every (block, D) whose cube
  * the segment [p - tau r, p + tau r] crosses, for each direction D the pixel's
  * world normal belongs to (Eq. angular_threshold: <n, v^D> > cos(theta)).
  * The traversal is a 3D digital differential analyser (Amanatides & Woo) in

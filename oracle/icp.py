@@ -8,7 +8,7 @@ Paper passages followed (Splietker & Behnke):
     column -<n_i, x_i>.
   * Eq. ICP_Hessian / Eq. ICP_solution / Eq. deltaT_update: H = sum w J J^T,
     g = sum w J r (the common factor 2 cancels in H xi = -g), Cholesky solve,
-    dT <- exp(xi) dT; stop when ||xi|| < 1e-6 (Sec. 7 ICP settings).
+    dT <- exp(xi) dT; stop when ||xi|| < 1e-6 (Sec. 8 ICP settings).
   * Eq. ICP_weight: w = 1 / (z + (1 - z_min))^2.
   * Eq. combined_icp with lambda = 0.1 (not squared) and the depth weight on the
     photometric rows; Eq. keyframe_icp: r = I_cur(u) - I_kf(pi(K T_RS exp(xi) dT p)).
@@ -18,7 +18,7 @@ Paper passages followed (Splietker & Behnke):
   * Sim(3) exponential: the matrix exponential of the 4x4 generator
     [[omega^ + sigma I, nu], [0, 0]] (the paper prints the block form with an
     undefined V; the matrix exponential fixes V).
-  * Sec. 6 / Sec. 7: 3-level pyramid (2x2 mean of valid depths, intrinsics
+  * Sec. 7 / Sec. 8: 3-level pyramid (2x2 mean of valid depths, intrinsics
     f/2, (c - 0.5)/2), association by projecting the current point into the
     full-resolution render and rounding to the nearest pixel, distance outlier
     threshold 0.05 m coarse / 0.005 m finest, intensity threshold 0.175 / 0.05.
@@ -116,7 +116,7 @@ class Level:
 
 def pyramid(depth_filtered: np.ndarray, K, levels: int, rgb: np.ndarray | None = None) -> list[Level]:
     """Levels 0..levels-1 of the current frame. ``depth_filtered`` is the
-    outlier-filtered depth (Sec. 6)."""
+    outlier-filtered depth (Sec. 7)."""
     d32 = np.ascontiguousarray(depth_filtered, F32)
     d64 = d32.astype(np.float64)
     I = None if rgb is None else intensity(rgb)

@@ -53,7 +53,8 @@ class MapStats(ctypes.Structure):
 
 class IcpOpts(ctypes.Structure):
     _fields_ = [("levels", c_int32), ("iters", c_int32 * 4), ("eps", c_float * 4), ("photo_thr", c_float * 4),
-                ("lambda_", c_float), ("z_min", c_float), ("stop_norm", c_double), ("min_rows", c_int32)]
+                ("lambda_", c_float), ("z_min", c_float), ("stop_norm", c_double), ("min_rows", c_int32),
+                ("kahan", c_int32)]
 
 
 class IcpStats(ctypes.Structure):
@@ -238,12 +239,12 @@ Map.import_bricks = _import
 
 
 def icp_opts(levels=3, iters=(10, 5, 4), eps=(0.005, 0.05, 0.05), photo_thr=(0.05, 0.175, 0.175), lam=0.1,
-             z_min=0.1, stop_norm=1e-6, min_rows=10) -> IcpOpts:
+             z_min=0.1, stop_norm=1e-6, min_rows=10, kahan=False) -> IcpOpts:
     it = list(iters) + [0] * (4 - len(iters))
     ep = list(eps) + [0.05] * (4 - len(eps))
     th = list(photo_thr) + [0.175] * (4 - len(photo_thr))
     return IcpOpts(levels, (c_int32 * 4)(*it), (c_float * 4)(*ep), (c_float * 4)(*th), lam, z_min, stop_norm,
-                   min_rows)
+                   min_rows, int(kahan))
 
 
 class Icp:

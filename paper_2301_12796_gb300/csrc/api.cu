@@ -649,6 +649,7 @@ static void fill_launch(dtsdf_icp c, IcpLaunch& L, const dtsdf_render_out* ref, 
   L.stats = c->stats;
   L.min_rows = o->min_rows;
   L.stop_norm = o->stop_norm;
+  L.kahan = o->kahan;
 }
 
 static dtsdf_status icp_step_impl(dtsdf_icp c, const dtsdf_render_out* ref, const dtsdf_intrinsics* K_ref, int level,

@@ -16,7 +16,7 @@
 namespace dtsdf {
 
 constexpr int ND = 6;          // directions X+, X-, Y+, Y-, Z+, Z- (Sec. 3)
-constexpr int BVOX = 512;      // voxels per 8^3 block (Sec. 6)
+constexpr int BVOX = 512;      // voxels per 8^3 block (Sec. 7)
 constexpr unsigned long long EMPTY_KEY = ~0ull;
 constexpr int MAX_PROBE = 256;  // linear-probe bound; the table is kept at most half full
 constexpr int SLOT_MASK = 6;    // dir_slots[d * 8 + 6]: bitmask of allocated directions
@@ -128,9 +128,9 @@ struct MapView {
   uint32_t dir_cap;
   // brick pool
   float2* geom;     // FP32: (sdf, weight) per voxel
-  uint32_t* geom16; // FP16: half sdf | u16 weight (1/256 units) per voxel
+  uint32_t* geom16; // FP16: half sdf | half weight (as u16) per voxel
   float4* col;      // FP32: (r, g, b, colour weight)
-  uint32_t* col8;   // FP16 storage: u8 r, g, b, u8 colour weight (1/ (255/w_max) units)
+  uint32_t* col8;   // FP16 storage: u8 r, g, b and the 8-bit log colour-weight code
   int32_t* brick_dir;  // per brick: dir index * 8 + D
   float* bound;        // per brick: lower bound of sdf over its voxels and its +1 apron with weight > 0
   uint32_t* occ;       // occupancy filters: 2 x OCC_WORDS words (blocks, then 4^3-block super-cells)
@@ -186,23 +186,45 @@ __device__ __forceinline__ bool occ_test(const MapView& m, int bx, int by, int b
 }
 
 // Storage accessors ---------------------------------------------------------
-// FP16 form: sdf as IEEE half, weight as an unsigned 16-bit count of 1/256 units.
-constexpr float W16_SCALE = 256.0f;
-
+// FP16 form: sdf as IEEE half; the weight's u16 holds an IEEE half too (2^-11 relative
+// resolution at every magnitude; a positive weight is kept at least at the smallest
+// positive half, so "weight > 0" survives); colour as u8 r, g, b and an 8-bit logarithmic
+// colour-weight code q: w = 2^((q - 128) / 16), q = 0 for w = 0.
 __device__ __forceinline__ float2 unpack_geom16(uint32_t v) {
-  __half_raw hr;
-  hr.x = (unsigned short)(v & 0xFFFFu);
-  const float sdf = __half2float(__half(hr));
-  const float w = (float)(v >> 16) * (1.0f / W16_SCALE);
-  return make_float2(sdf, w);
+  __half_raw hs, hw;
+  hs.x = (unsigned short)(v & 0xFFFFu);
+  hw.x = (unsigned short)(v >> 16);
+  return make_float2(__half2float(__half(hs)), __half2float(__half(hw)));
 }
 
 __device__ __forceinline__ uint32_t pack_geom16(float sdf, float w) {
-  const __half hs = __float2half_rn(sdf);
-  const __half_raw hr = hs;
-  float q = rintf(w * W16_SCALE);
-  q = fminf(fmaxf(q, 0.0f), 65535.0f);
-  return (uint32_t)hr.x | ((uint32_t)q << 16);
+  const __half_raw hs = __float2half_rn(sdf);
+  __half_raw hw = __float2half_rn(fminf(w, 65504.0f));
+  if (w > 0.0f && hw.x == 0) hw.x = 1;  // smallest positive subnormal half
+  if (!(w > 0.0f)) hw.x = 0;
+  return (uint32_t)hs.x | ((uint32_t)hw.x << 16);
+}
+
+__device__ __forceinline__ float col_weight_decode(uint32_t code) {
+  return code ? exp2f(((float)code - 128.0f) * (1.0f / 16.0f)) : 0.0f;
+}
+
+__device__ __forceinline__ uint32_t col_weight_encode(float w) {
+  if (!(w > 0.0f)) return 0u;
+  const float q = rintf(16.0f * log2f(w) + 128.0f);
+  return (uint32_t)fminf(fmaxf(q, 1.0f), 255.0f);
+}
+
+__device__ __forceinline__ uint32_t pack_col8(float r, float g, float b, float w) {
+  const uint32_t R = (uint32_t)fminf(fmaxf(rintf(r), 0.f), 255.f);
+  const uint32_t G = (uint32_t)fminf(fmaxf(rintf(g), 0.f), 255.f);
+  const uint32_t B = (uint32_t)fminf(fmaxf(rintf(b), 0.f), 255.f);
+  return R | (G << 8) | (B << 16) | (col_weight_encode(w) << 24);
+}
+
+__device__ __forceinline__ float4 unpack_col8(uint32_t v) {
+  return make_float4((float)(v & 0xFF), (float)((v >> 8) & 0xFF), (float)((v >> 16) & 0xFF),
+                     col_weight_decode(v >> 24));
 }
 
 }  // namespace dtsdf

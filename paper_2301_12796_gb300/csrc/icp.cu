@@ -1,5 +1,5 @@
 // Point-to-plane ICP in SE(3) and Sim(3) with the frame-to-keyframe photometric term
-// (Sec. 5, 5.2, 5.3; Sec. 6 pyramid; Sec. 7 thresholds).
+// (Sec. 5, 5.1-5.3; Sec. 6 for Sim(3); Sec. 8 outlier thresholds).
 //
 // One launch = one Gauss-Newton iteration: a persistent grid (2 CTAs per SM) walks the
 // pixels of the current pyramid level grid-stride, forms each pixel's point-to-plane row
@@ -183,14 +183,29 @@ struct IcpArgs {
   double stop_norm;
 };
 
-template <int DIM>
+// Per-thread FP32 accumulators of one Gauss-Newton system; KAHAN adds a compensation term
+// per sum (Kahan summation over the pixels a thread visits).
+template <int DIM, bool KAHAN>
 struct Acc {
   static constexpr int NH = DIM * (DIM + 1) / 2;
   static constexpr int N = NH + DIM + 3;  // H upper, g, E, rows_geo, rows_photo
   float v[N];
+  float c[KAHAN ? N : 1];
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int i = 0; i < N; ++i) v[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < (KAHAN ? N : 1); ++i) c[i] = 0.f;
+  }
+  __device__ __forceinline__ void add(int i, float x) {
+    if (KAHAN) {
+      const float y = x - c[i];
+      const float t = v[i] + y;
+      c[i] = (t - v[i]) - y;
+      v[i] = t;
+    } else {
+      v[i] += x;
+    }
   }
   __device__ __forceinline__ void row(const float J[DIM], float r, float w) {
     int k = 0;
@@ -198,16 +213,18 @@ struct Acc {
     for (int i = 0; i < DIM; ++i) {
       const float wj = w * J[i];
 #pragma unroll
-      for (int j = i; j < DIM; ++j) v[k++] += wj * J[j];
-      v[NH + i] += wj * r;
+      for (int j = i; j < DIM; ++j) add(k++, wj * J[j]);
+      add(NH + i, wj * r);
     }
-    v[NH + DIM] += w * r * r;
+    add(NH + DIM, w * r * r);
   }
+  // compensated value of sum i
+  __device__ __forceinline__ float total(int i) const { return KAHAN ? v[i] - c[i] : v[i]; }
 };
 
-template <int DIM, bool PHOTO>
+template <int DIM, bool PHOTO, bool KAHAN>
 __global__ void __launch_bounds__(ICP_THREADS) k_icp(IcpArgs a) {
-  using A = Acc<DIM>;
+  using A = Acc<DIM, KAHAN>;
   __shared__ float s_red[ICP_THREADS / 32][A::N];
   __shared__ double s_sum[A::N];
   __shared__ int s_last;
@@ -271,7 +288,7 @@ __global__ void __launch_bounds__(ICP_THREADS) k_icp(IcpArgs a) {
             J[5] = -(x0 * nq.y - x1 * nq.x);
             if (DIM == 7) J[DIM - 1] = -(nq.x * x0 + nq.y * x1 + nq.z * x2);
             acc.row(J, r, wz);
-            acc.v[A::N - 2] += 1.0f;
+            acc.v[A::N - 2] += 1.0f;  // a count, exact in FP32 below 2^24
           }
         }
       }
@@ -324,7 +341,7 @@ __global__ void __launch_bounds__(ICP_THREADS) k_icp(IcpArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < A::N; ++i) {
-    float x = acc.v[i];
+    float x = acc.total(i);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     if (lane == 0) s_red[warp][i] = x;
@@ -494,17 +511,22 @@ void launch_icp(const IcpLaunch& L, int sim3, bool photo, int grid, cudaStream_t
   a.stats = L.stats;
   a.min_rows = L.min_rows;
   a.stop_norm = L.stop_norm;
+#define DTSDF_ICP(D, P, K) k_icp<D, P, K><<<grid, ICP_THREADS, 0, s>>>(a)
+  const bool kahan = L.kahan != 0;
   if (sim3) {
-    if (photo)
-      k_icp<7, true><<<grid, ICP_THREADS, 0, s>>>(a);
-    else
-      k_icp<7, false><<<grid, ICP_THREADS, 0, s>>>(a);
+    if (photo) {
+      if (kahan) DTSDF_ICP(7, true, true); else DTSDF_ICP(7, true, false);
+    } else {
+      if (kahan) DTSDF_ICP(7, false, true); else DTSDF_ICP(7, false, false);
+    }
   } else {
-    if (photo)
-      k_icp<6, true><<<grid, ICP_THREADS, 0, s>>>(a);
-    else
-      k_icp<6, false><<<grid, ICP_THREADS, 0, s>>>(a);
+    if (photo) {
+      if (kahan) DTSDF_ICP(6, true, true); else DTSDF_ICP(6, true, false);
+    } else {
+      if (kahan) DTSDF_ICP(6, false, true); else DTSDF_ICP(6, false, false);
+    }
   }
+#undef DTSDF_ICP
 }
 
 void launch_exp(int dim, const double* xi, double* T, cudaStream_t s) { k_exp<<<1, 1, 0, s>>>(dim, xi, T); }

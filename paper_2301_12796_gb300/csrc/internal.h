@@ -24,6 +24,7 @@ struct IcpLaunch {
   dtsdf_icp_stats* stats;
   int min_rows;
   double stop_norm;
+  int kahan;
 };
 
 // Record a message for dtsdf_last_error() and return the status.

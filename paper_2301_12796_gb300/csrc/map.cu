@@ -1,5 +1,5 @@
-// Map construction: frame preprocessing (Sec. 6), voxel-block allocation in the
-// (block, direction) hash (Sec. 6), and voxel-projection fusion of depth and colour
+// Map construction: frame preprocessing (Sec. 7), voxel-block allocation in the
+// (block, direction) hash (Sec. 7), and voxel-projection fusion of depth and colour
 // with free-space carving (Sec. 3).
 //
 // HBM layout of a map (all allocated once at creation, sized by max_blocks):
@@ -49,7 +49,7 @@ __global__ void k_filter(const float* __restrict__ depth, Intr K, float zmin, fl
 }
 
 // Normals: cross product of the central differences of the back-projected x and y
-// neighbours (Sec. 6), normalised and turned toward the camera. N.w = 1 marks a normal.
+// neighbours (Sec. 7), normalised and turned toward the camera. N.w = 1 marks a normal.
 __global__ void k_normals(const float4* __restrict__ P, Intr K, float4* __restrict__ N) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = blockIdx.y * blockDim.y + threadIdx.y;
@@ -454,17 +454,10 @@ __global__ void __launch_bounds__(256) k_fuse(MapView m, FuseFrame f) {
           if (!(w_c > 1e-12f)) w_c = 1e-12f;
           const uint8_t* c = f.rgb + 3 * pi;
           if (STORE == DTSDF_STORE_FP16) {
-            // 8-bit colour, colour weight in 1/ (w_max / 255) steps of the 8-bit field
-            const uint32_t cv = m.col8[gi];
-            const float wq = m.wmax / 255.0f;
-            const float wc0 = (float)(cv >> 24) * wq;
-            const float wcn = wc0 + w_c;
-            const float r = ((float)(cv & 0xFF) * wc0 + w_c * c[0]) / wcn;
-            const float gg = ((float)((cv >> 8) & 0xFF) * wc0 + w_c * c[1]) / wcn;
-            const float bb = ((float)((cv >> 16) & 0xFF) * wc0 + w_c * c[2]) / wcn;
-            const float wcq = fminf(fmaxf(rintf(fminf(wcn, m.wmax) / wq), 1.0f), 255.0f);
-            m.col8[gi] = (uint32_t)fminf(rintf(r), 255.f) | ((uint32_t)fminf(rintf(gg), 255.f) << 8) |
-                         ((uint32_t)fminf(rintf(bb), 255.f) << 16) | ((uint32_t)wcq << 24);
+            const float4 cv = unpack_col8(m.col8[gi]);
+            const float wcn = cv.w + w_c;
+            m.col8[gi] = pack_col8((cv.w * cv.x + w_c * c[0]) / wcn, (cv.w * cv.y + w_c * c[1]) / wcn,
+                                   (cv.w * cv.z + w_c * c[2]) / wcn, fminf(wcn, m.wmax));
           } else {
             float4 cv = m.col[gi];
             const float wcn = cv.w + w_c;
@@ -566,10 +559,7 @@ __global__ void k_import_write(MapView m, const int32_t* __restrict__ coords, co
         m.geom[gi] = make_float2(in[0], in[1]);
       if (m.color) {
         if (m.storage == DTSDF_STORE_FP16) {
-          const float wq = m.wmax / 255.0f;
-          const uint32_t cw = (uint32_t)fminf(fmaxf(rintf(in[5] / wq), in[5] > 0 ? 1.f : 0.f), 255.f);
-          m.col8[gi] = (uint32_t)fminf(rintf(in[2]), 255.f) | ((uint32_t)fminf(rintf(in[3]), 255.f) << 8) |
-                       ((uint32_t)fminf(rintf(in[4]), 255.f) << 16) | (cw << 24);
+          m.col8[gi] = pack_col8(in[2], in[3], in[4], in[5]);
         } else {
           m.col[gi] = make_float4(in[2], in[3], in[4], in[5]);
         }
@@ -629,11 +619,11 @@ __global__ void k_export(MapView m, int64_t cap, int32_t* coords, float* vox) {
       o[1] = g.y;
       if (m.color) {
         if (m.storage == DTSDF_STORE_FP16) {
-          const uint32_t cv = m.col8[gi];
-          o[2] = (float)(cv & 0xFF);
-          o[3] = (float)((cv >> 8) & 0xFF);
-          o[4] = (float)((cv >> 16) & 0xFF);
-          o[5] = (float)(cv >> 24) * (m.wmax / 255.0f);
+          const float4 c = unpack_col8(m.col8[gi]);
+          o[2] = c.x;
+          o[3] = c.y;
+          o[4] = c.z;
+          o[5] = c.w;
         } else {
           const float4 c = m.col[gi];
           o[2] = c.x;

@@ -121,6 +121,7 @@ dtsdf_status dtsdf_icp_step_noalloc(const float* depth, const dtsdf_intrinsics* 
   L.stats = stats_dev;
   L.min_rows = min_rows;
   L.stop_norm = stop_norm;
+  L.kahan = 0;
   const int grid = (int)((npix + NOALLOC_PIXELS_PER_CTA - 1) / NOALLOC_PIXELS_PER_CTA);
   launch_icp(L, sim3, false, grid < 1 ? 1 : grid, s);
   if (cudaGetLastError() != cudaSuccess) return set_error(DTSDF_ERR_CUDA, "dtsdf_icp_step_noalloc: launch failed");

@@ -269,11 +269,11 @@ __device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, cons
         if (COUNT) touched[m.pool_cap + (vi >> 9)] = 1;
         const float wq = corner_w(q, fx, fy, fz);
         if (STORE == DTSDF_STORE_FP16) {
-          const uint32_t cv = __ldg(m.col8 + vi);
-          cr += wq * (float)(cv & 0xFF);
-          cg += wq * (float)((cv >> 8) & 0xFF);
-          cb += wq * (float)((cv >> 16) & 0xFF);
-          cwt += wq * (float)(cv >> 24);
+          const float4 cv = unpack_col8(__ldg(m.col8 + vi));
+          cr += wq * cv.x;
+          cg += wq * cv.y;
+          cb += wq * cv.z;
+          cwt += wq * cv.w;
         } else {
           const float4 cv = __ldg(m.col + vi);
           cr += wq * cv.x;

@@ -1,6 +1,6 @@
 """GPU-vs-oracle parity of fusion, rendering and ICP through the C ABI.
 
-Tolerances (spec values where they exist, otherwise derived in the design notes):
+Tolerances (the required values where they exist, otherwise derived from the arithmetic below):
   render depth |d| <= 1e-4 m on pixels both sides hit, hit-mask agreement >= 99.9 %,
   normal angle <= 1e-3 rad; ICP pose <= 1e-4 rad / 1e-4 m / 1e-5 relative scale.
   The render is checked twice: on the oracle's own map loaded into the device map
@@ -29,6 +29,8 @@ DEV = torch.device("cuda:0")
 DEPTH_TOL = 1e-4
 MASK_AGREE = 0.999
 NORMAL_TOL = 1e-3
+# FP16 storage form: share of mask-agreeing pixels whose depth is within DEPTH_TOL
+FP16_DEPTH_FRAC = 0.999
 NORMAL_AGREE = 0.999
 # a fusion weight is Lipschitz in the pixel normal (w_dir has slope 1/(2 theta - pi/2) per radian)
 # and FP32 normals differ from FP64 ones by ~1e-7 rad: an absolute allowance per voxel
@@ -343,3 +345,96 @@ def test_map_full_is_reported():
     with pytest.raises(dt.DtsdfError) as e:
         gm.integrate(cu(f.depth), cu(f.rgb), s.K, f.pose)
     assert e.value.status == dt.ERR_MAP_FULL
+
+
+# ------------------------------------------------------------ precision form --
+
+def _fuse_fp16(scene, frames, dense=True):
+    kw = dict(voxel_size=0.01, truncation=0.04, dense_dim=64 if dense else 0, color=True)
+    gm = dt.Map(dt.params(max_blocks=1 << 16, storage=dt.STORE_FP16, **kw))
+    om = oracle.OracleMap(oracle.Params(**kw))
+    for i in frames:
+        f = scene.frame(i)
+        gm.integrate(cu(f.depth), cu(f.rgb), scene.K, f.pose)
+        om.integrate(f.depth, f.rgb, scene.K, f.pose)
+    torch.cuda.synchronize()
+    return gm, om
+
+
+def test_fp16_storage_map_matches_oracle():
+    """FP16 sdf, half weight in a u16, u8 colour: same allocation and presence as the oracle,
+    values within the storage quantisation accumulated over the running averages."""
+    s = scenes.tiny_scene(1)
+    gm, om = _fuse_fp16(s, range(10))
+    coords, vox = gm.export()
+    idx = {tuple(c): i for i, c in enumerate(coords)}
+    n = 0
+    errs = []
+    for b in om.bricks():
+        g = vox[idx[tuple(b[:4])]].astype(np.float64)
+        o = om.brick(*b[:4])
+        p = o[:, 1] > 0
+        assert np.array_equal(g[:, 1] > 0, p)
+        if p.any():
+            errs.append(np.abs(g[p, 0] - o[p, 0]))
+            assert np.all(np.abs(g[p, 1] - o[p, 1]) <= 0.01 * o[p, 1] + 1e-5)
+            n += p.sum()
+    assert n > 50000
+    # half precision: 2^-11 relative per stored sdf and weight, re-rounded at every update and
+    # carried through the running averages
+    e = np.concatenate(errs)
+    assert np.quantile(e, 0.999) <= 2e-3 and e.max() <= 0.05, (np.quantile(e, 0.999), e.max())
+
+
+@pytest.mark.parametrize("fi", [0, 5])
+def test_fp16_render_matches_oracle(fi):
+    s = scenes.tiny_scene(1)
+    gm, om = _fuse_fp16(s, range(10))
+    T = s.poses[fi] @ scenes.perturbation(np.random.default_rng(fi), 1.0, 0.005)
+    dg, ng, cg = render_gpu(gm, s.K, T, True)
+    do, no, co, cok = om.render(s.K, T)
+    hg, ho = dg > 0, do > 0
+    agree = float(np.mean(hg == ho))
+    both = hg & ho
+    assert both.sum() > 5000
+    derr = np.abs(dg - do)
+    # The FP16 field differs from the FP64 one by the storage rounding, so a sign test at a
+    # sample whose stored value is within that rounding of zero can go the other way: the ray
+    # then stops at a neighbouring crossing. Those pixels are counted, not excluded.
+    close = both & (derr <= DEPTH_TOL)
+    frac = close.sum() / both.sum()
+    nerr = np.arccos(np.clip(np.sum(ng[both][:, :3] * no[both], -1), -1, 1))
+    cb = close & (cg[..., 3] > 0) & (cok > 0)
+    cerr = np.abs(cg[cb][:, :3] - co[cb]).max(-1)
+    print(f"fp16 fi={fi}: mask {agree:.5f} depth<=1e-4 {frac:.5f} median {np.median(derr[both]):.2e} "
+          f"max {derr[both].max():.3e} normals {np.mean(nerr <= NORMAL_TOL):.4f} "
+          f"colour q999 {np.quantile(cerr, 0.999):.2f} max {cerr.max():.2f}")
+    assert agree >= MASK_AGREE, agree
+    assert frac >= FP16_DEPTH_FRAC and np.median(derr[both]) <= 1e-5, (frac, np.median(derr[both]))
+    assert np.mean(nerr <= NORMAL_TOL) >= 0.99, np.mean(nerr <= NORMAL_TOL)
+    # u8 colour channels re-rounded at every update, mixed with a log-coded colour weight
+    assert np.quantile(cerr, 0.999) <= 3.0, np.quantile(cerr, 0.999)
+
+
+@pytest.mark.parametrize("sim3", [False, True])
+def test_kahan_reduction_matches_oracle(sim3):
+    s = scenes.planes_scene()
+    K = s.K
+    T_ref = s.poses[0]
+    rng = np.random.default_rng(31)
+    T_cur = T_ref @ scenes.perturbation(rng, 2.0, 0.02)
+    cur = s.render(T_cur, noise=True)
+    rd, rn = _analytic_ref(s, T_ref, K)
+    dT = np.linalg.inv(T_ref) @ T_cur @ oicp.exp(rng.normal(size=6) * 0.01)
+    ic = dt.Icp(K.width, K.height, 3)
+    ic.set_frame(cu(cur.depth), None, K, 0.1, 6.0, 0.02)
+    opts = dt.icp_opts(levels=3, eps=(0.05, 0.1, 0.1), min_rows=1, kahan=True)
+    T1, st = ic.step(cu(rd), cu(rn), K, 0, dT, opts, sim3=sim3)
+    pre = oracle.preprocess(cur.depth, K, 0.1, 6.0, 0.02)
+    lv = oicp.pyramid(pre["z"], K, 3)[0]
+    rows = oicp.geometric_rows(lv, rd, rn, K, dT, 0.05, 0.1, sim3)
+    H, g, E, nr = oicp.normal_equations([rows])
+    assert st.rows == nr
+    assert np.linalg.norm(st.H_matrix() - H) <= 1e-5 * np.linalg.norm(H)
+    xi, ok = oicp.solve(H, g)
+    assert np.allclose(T1, oicp.exp(xi) @ dT, atol=1e-6)

@@ -1,4 +1,4 @@
-"""Pins of the oracle's block allocation (Sec. 6) against a brute-force slab test."""
+"""Pins of the oracle's block allocation (Sec. 7) against a brute-force slab test."""
 import itertools
 
 import numpy as np

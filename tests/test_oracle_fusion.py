@@ -1,4 +1,4 @@
-"""Pins of the oracle's preprocessing and fusion (Sec. 3, Sec. 6) on closed forms."""
+"""Pins of the oracle's preprocessing and fusion (Sec. 3, Sec. 7) on closed forms."""
 import numpy as np
 import pytest
 

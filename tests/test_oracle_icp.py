@@ -1,4 +1,4 @@
-"""Pins of the oracle's ICP (Sec. 5, 5.2, 5.3): exponential maps against closed
+"""Pins of the oracle's ICP (Sec. 5, 5.2, 5.3, 6): exponential maps against closed
 forms, Jacobians against finite differences, exact recovery of known motions."""
 import numpy as np
 import pytest
