@@ -134,6 +134,18 @@ DTSDF_API dtsdf_status dtsdf_render(dtsdf_map map, const dtsdf_intrinsics* K, co
 DTSDF_API dtsdf_status dtsdf_render_dev(dtsdf_map map, const dtsdf_intrinsics* K, const double* T_wc_dev,
                                         const dtsdf_render_out* out, void* stream);
 
+/* Launch shape of the map's renders (no counterpart in the paper: scheduling only, the
+ * results do not depend on it). ctas: CTAs of the persistent render grid, 0 = one wave of
+ * resident CTAs; lane_refill: 1 = a lane whose ray is finished takes the next ray at once,
+ * 0 = a warp takes the next 8x4 tile of rays when all its lanes have finished. Defaults:
+ * {0, 0}. Returns DTSDF_ERR_INVALID_ARG for ctas < 0 or lane_refill not 0/1. */
+typedef struct {
+  int32_t ctas;
+  int32_t lane_refill;
+} dtsdf_render_opts;
+
+DTSDF_API dtsdf_status dtsdf_set_render_opts(dtsdf_map map, const dtsdf_render_opts* opts);
+
 /* Instrumented render at T_wc that counts the distinct bricks the march reads: geometry
  * bricks (sdf + weight) and colour bricks. Defines the algorithmic bytes of a render for
  * roofline accounting. counters (host, 8 int64, or NULL) receives totals over all rays:

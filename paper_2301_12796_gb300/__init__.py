@@ -46,6 +46,10 @@ class RenderOut(ctypes.Structure):
     _fields_ = [("depth", c_void_p), ("normals", c_void_p), ("color", c_void_p)]
 
 
+class RenderOpts(ctypes.Structure):
+    _fields_ = [("ctas", c_int32), ("lane_refill", c_int32)]
+
+
 class MapStats(ctypes.Structure):
     _fields_ = [("bricks", c_int64), ("blocks", c_int64), ("bricks_per_dir", c_int64 * 6), ("capacity", c_int64),
                 ("error_flags", c_uint32), ("frames", c_int32)]
@@ -79,6 +83,7 @@ SIGNATURES = {
     "dtsdf_integrate_dev": ([P, ctypes.POINTER(Frame), P, P], c_int32),
     "dtsdf_render": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), P], c_int32),
     "dtsdf_render_dev": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), P], c_int32),
+    "dtsdf_set_render_opts": ([P, ctypes.POINTER(RenderOpts)], c_int32),
     "dtsdf_render_touched": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64),
                               P, P], c_int32),
     "dtsdf_pose_compose": ([P, c_int32, P, P, P], c_int32),
@@ -195,6 +200,11 @@ class Map:
         Ki = intrinsics(K)
         check(lib().dtsdf_render_dev(self._h, ctypes.byref(Ki), T_dev.data_ptr(), ctypes.byref(out),
                                      _stream_ptr(stream)), "dtsdf_render_dev")
+
+    def set_render_opts(self, ctas: int = 0, lane_refill: bool = False):
+        """Launch shape of this map's renders (persistent CTAs, 0 = one resident wave; refill policy)."""
+        o = RenderOpts(int(ctas), int(bool(lane_refill)))
+        check(lib().dtsdf_set_render_opts(self._h, ctypes.byref(o)), "dtsdf_set_render_opts")
 
     def touched(self, K, T_wc, stream=None, counters=False):
         """(geometry bricks, colour bricks) read by one render at T_wc; with counters=True also

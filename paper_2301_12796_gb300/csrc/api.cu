@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 #include <string>
 
@@ -104,7 +105,14 @@ struct dtsdf_map_s {
   uint32_t* err_host = nullptr;
   cudaEvent_t err_event = nullptr;
   bool err_pending = false;
+  // work counters of render launches: a ring, one slot per launch, zeroed on the launch's
+  // stream before the kernel, so concurrent renders on different streams use different slots
+  unsigned* render_q = nullptr;
+  std::atomic<uint32_t> render_q_next{0};
+  dtsdf_render_opts ropts = {0, 0};
 };
+
+constexpr uint32_t RENDER_Q_SLOTS = 1024;
 
 static void map_free(dtsdf_map m) {
   if (!m) return;
@@ -122,11 +130,34 @@ static void map_free(dtsdf_map m) {
   cudaFree(m->v.occ);
   cudaFree(m->v.counters);
   cudaFree(m->v.work);
+  cudaFree(m->render_q);
   cudaFree(m->P);
   cudaFree(m->N);
   if (m->err_host) cudaFreeHost(m->err_host);
   if (m->err_event) cudaEventDestroy(m->err_event);
   delete m;
+}
+
+// One render launch: take a work-counter slot of the ring, zero it on the stream, launch.
+static unsigned* render_slot(dtsdf_map m) {
+  return m->render_q + (m->render_q_next.fetch_add(1, std::memory_order_relaxed) % RENDER_Q_SLOTS);
+}
+
+static dtsdf_status render_launch(dtsdf_map m, const dtsdf_intrinsics& K, const Pose32& T, const double* Tdev,
+                                  const dtsdf_render_out* out, cudaStream_t s, uint8_t* touched) {
+  unsigned* q = render_slot(m);
+  CK(cudaMemsetAsync(q, 0, sizeof(unsigned), s));
+  RenderJob J;
+  memset(&J, 0, sizeof(J));
+  J.K = to_intr(K);
+  J.Tdev = Tdev;
+  J.T = T;
+  J.depth = out->depth;
+  J.normals = (float4*)out->normals;
+  J.color = (float4*)out->color;
+  launch_render_jobs(m->v, &J, 1, q, s, touched, m->ropts.ctas, m->ropts.lane_refill);
+  CK_LAUNCH("render");
+  return DTSDF_OK;
 }
 
 extern "C" {
@@ -199,6 +230,7 @@ dtsdf_status dtsdf_create(const dtsdf_params* params, void* stream, dtsdf_map* o
   ALLOC(v.occ, sizeof(uint32_t) * 2 * (size_t)OCC_WORDS);
   ALLOC(v.counters, sizeof(uint32_t) * C_COUNT);
   ALLOC(v.work, sizeof(int32_t) * (size_t)v.work_cap);
+  ALLOC(m->render_q, sizeof(unsigned) * RENDER_Q_SLOTS);
 #undef ALLOC
   if (e == cudaSuccess) e = cudaMallocHost((void**)&m->err_host, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->err_event, cudaEventDisableTiming);
@@ -322,10 +354,7 @@ dtsdf_status dtsdf_render(dtsdf_map m, const dtsdf_intrinsics* K, const double T
                           void* stream) {
   if (!m || !intr_ok(K) || !pose_ok(T_wc) || !out || !out->depth || !out->normals)
     return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
-  launch_render(m->v, to_intr(*K), to_pose32(T_wc), nullptr, out->depth, (float4*)out->normals, (float4*)out->color,
-                (cudaStream_t)stream);
-  CK_LAUNCH("render");
-  return DTSDF_OK;
+  return render_launch(m, *K, to_pose32(T_wc), nullptr, out, (cudaStream_t)stream, nullptr);
 }
 
 dtsdf_status dtsdf_render_dev(dtsdf_map m, const dtsdf_intrinsics* K, const double* T_wc_dev,
@@ -334,9 +363,13 @@ dtsdf_status dtsdf_render_dev(dtsdf_map m, const dtsdf_intrinsics* K, const doub
     return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
   Pose32 T;
   memset(&T, 0, sizeof(T));
-  launch_render(m->v, to_intr(*K), T, T_wc_dev, out->depth, (float4*)out->normals, (float4*)out->color,
-                (cudaStream_t)stream);
-  CK_LAUNCH("render");
+  return render_launch(m, *K, T, T_wc_dev, out, (cudaStream_t)stream, nullptr);
+}
+
+dtsdf_status dtsdf_set_render_opts(dtsdf_map m, const dtsdf_render_opts* o) {
+  if (!m || !o || o->ctas < 0 || (o->lane_refill != 0 && o->lane_refill != 1))
+    return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  m->ropts = *o;
   return DTSDF_OK;
 }
 
@@ -357,8 +390,19 @@ dtsdf_status dtsdf_render_touched(dtsdf_map m, const dtsdf_intrinsics* K, const 
   if (e == cudaSuccess && m->p.color) e = cudaMalloc((void**)&col, sizeof(float4) * npix);
   if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, nflags, s);
   if (e == cudaSuccess) {
-    launch_render(m->v, to_intr(*K), to_pose32(T_wc), nullptr, depth, nrm, col, s, flags);
-    e = cudaGetLastError();
+    unsigned* q = render_slot(m);
+    e = cudaMemsetAsync(q, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) {
+      RenderJob J;
+      memset(&J, 0, sizeof(J));
+      J.K = to_intr(*K);
+      J.T = to_pose32(T_wc);
+      J.depth = depth;
+      J.normals = nrm;
+      J.color = col;
+      launch_render_jobs(m->v, &J, 1, q, s, flags, m->ropts.ctas, m->ropts.lane_refill);
+      e = cudaGetLastError();
+    }
   }
   uint8_t* host = nullptr;
   if (e == cudaSuccess) host = new (std::nothrow) uint8_t[nflags];

@@ -44,8 +44,39 @@ void launch_pose_compose(const double* A, int invert_a, const double* B, double*
 void launch_import(const MapView& m, const int32_t* coords, const float* vox, int64_t n, bool allocate, int num_sms,
                    cudaStream_t s);
 void launch_export(const MapView& m, int64_t cap, int32_t* coords, float* vox, int num_sms, cudaStream_t s);
-void launch_render(const MapView& m, const Intr& K, const Pose32& T, const double* Tdev, float* depth,
-                   float4* normals, float4* color, cudaStream_t s, uint8_t* touched = nullptr);
+// One frame of a render launch: intrinsics, camera -> world pose (device pointer, else T) and
+// caller-owned outputs. tiles_x / start are filled in by launch_render_jobs.
+struct RenderJob {
+  Intr K;
+  const double* Tdev;
+  Pose32 T;
+  float* depth;
+  float4* normals;
+  float4* color;
+  int tiles_x;
+  int start;
+};
+
+constexpr int MAX_RENDER_JOBS = 64;
+
+// Kernel arguments of a render launch over NJ frames. The work items are the pixels of the
+// frames' 8x4 tiles, frame after frame; `queue` counts the items handed out and must be
+// zero when the launch starts.
+template <int NJ>
+struct RenderBatch {
+  RenderJob job[NJ];
+  int njobs;
+  int total;
+  unsigned* queue;
+  uint8_t* touched;  // instrumentation build only (brick flags + counters), else null
+  int max_samples;
+  int lane_refill;   // 1: a finished lane takes the next ray; 0: a warp takes a tile when all lanes finish
+};
+
+// Render njobs (1..MAX_RENDER_JOBS) frames in one persistent launch; ctas <= 0 picks one
+// wave of resident CTAs.
+void launch_render_jobs(const MapView& m, const RenderJob* jobs, int njobs, unsigned* queue, cudaStream_t s,
+                        uint8_t* touched = nullptr, int ctas = 0, int lane_refill = 0);
 void launch_frame_pyramid(const float4* P, const uint8_t* rgb, int levels, const Intr* K, float* const* depth,
                           float* const* inten, cudaStream_t s);
 void launch_keyframe_pyramid(const uint8_t* rgb, int levels, const Intr* K, float* const* tmpI, float4* const* kf,

@@ -20,18 +20,7 @@
 
 namespace dtsdf {
 
-constexpr int RT_X = 16, RT_Y = 8, RT_N = RT_X * RT_Y;
-
-struct RenderArgs {
-  Intr K;
-  Pose32 T;            // camera -> world (unless Tdev is given)
-  const double* Tdev;  // camera -> world in device memory, or null
-  uint8_t* touched;    // instrumentation: brick flags (COUNT build only)
-  float* depth;
-  float4* normals;
-  float4* color;
-  int max_samples;
-};
+constexpr int RT_N = 128;  // threads per CTA of the persistent render grid
 
 // Out-of-line hash probe over explicit pointers (keeps callers' state in registers).
 __device__ __noinline__ uint32_t probe_block(const unsigned long long* __restrict__ keys,
@@ -333,48 +322,40 @@ __device__ __forceinline__ int sign_fast(const MapView& m, Cell& c, const float 
 // One loop, one state machine per lane: marching (MARCH), the regular sub-step scan
 // of the refinement (SCAN), the full evaluations at the final bracket ends (ENDS_A/B) and
 // the output evaluations (OUT) all evaluate the field at one call site of the sign test
-// and one of the full combination, so lanes in different phases stay converged.
+// and one of the full combination, so lanes in different phases stay converged. A lane
+// whose ray is finished (DONE) takes the next ray from the launch's work counter at the
+// top of the loop, so a warp stays full until the work runs out: rays of very different
+// lengths (grazing rays cross long stretches of allocated band) do not hold a warp, or a
+// CTA, on one slow lane.
 enum { S_MARCH = 0, S_SCAN = 1, S_ENDS_A = 2, S_ENDS_B = 3, S_OUT = 4, S_DONE = 5 };
 
-template <int STORE, bool COLOR, bool COUNT>
-__global__ void __launch_bounds__(RT_N, 4) k_render(MapView m, RenderArgs a) {
+template <int STORE, bool COLOR, bool COUNT, int NJ>
+__global__ void __launch_bounds__(RT_N, 4) k_render(MapView m, RenderBatch<NJ> a) {
   __shared__ int s_dirc[27 * RT_N];
   __shared__ int s_slot[ND * 8 * RT_N];
+  __shared__ Pose32 s_pose[NJ];
   uint8_t* touched = a.touched;
   // COUNT build: per-ray event counts (samples, full combinations, cells, allocated cells, hits, jumps)
   unsigned long long* ctr = COUNT ? (unsigned long long*)(touched + 2 * (size_t)m.pool_cap) : nullptr;
-  uint32_t n_samples = 0, n_full = 0, n_cells = 0, n_acells = 0, n_jumps = 0;
-  const int tid = threadIdx.y * RT_X + threadIdx.x;
-  const int u = blockIdx.x * RT_X + threadIdx.x;
-  const int v = blockIdx.y * RT_Y + threadIdx.y;
-  if (u >= a.K.W || v >= a.K.H) return;
-  const int pix = v * a.K.W + u;
-  if (a.Tdev) a.T = pose_from_device(a.Tdev);
+  uint32_t n_samples = 0, n_full = 0, n_cells = 0, n_acells = 0, n_jumps = 0, n_hits = 0;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  for (int jb = tid; jb < a.njobs; jb += RT_N) s_pose[jb] = a.job[jb].Tdev ? pose_from_device(a.job[jb].Tdev) : a.job[jb].T;
+  __syncthreads();
+
   Cell cell;
   cell.dirc = s_dirc + tid;
   cell.slot = s_slot + tid;
-  cell.cx = cell.cy = cell.cz = 0x7fffffff;
-  cell.cmask = 0;
-  cell.positive = false;
-  cell.jumped = true;
-
-  // unit ray in camera and world frame
-  const float rc0 = (u - a.K.cx) / a.K.fx, rc1 = (v - a.K.cy) / a.K.fy;
-  const float rl = sqrtf(rc0 * rc0 + rc1 * rc1 + 1.0f);
-  const float q0 = rc0 / rl, q1 = rc1 / rl, q2 = 1.0f / rl;
-  float r[3];
-  r[0] = a.T.R[0] * q0 + a.T.R[1] * q1 + a.T.R[2] * q2;
-  r[1] = a.T.R[3] * q0 + a.T.R[4] * q1 + a.T.R[5] * q2;
-  r[2] = a.T.R[6] * q0 + a.T.R[7] * q1 + a.T.R[8] * q2;
-  const float o[3] = {a.T.t[0], a.T.t[1], a.T.t[2]};
   const float org[3] = {m.ox, m.oy, m.oz};
   const float inv_h = 1.0f / m.h;
   const float step = 0.5f * m.h;
-  const int k1 = (int)floorf(m.zmax * rl / step);
   const float bsz = 8.0f * m.h;
 
-  int state = S_MARCH;
-  int k = (int)ceilf(m.zmin * rl / step);
+  // per-ray state
+  bool alive = true;
+  int state = S_DONE;
+  int jb = 0, pix = 0, it = 0, k = 0, k1 = 0;
+  float r[3] = {0.f, 0.f, 0.f}, o[3] = {0.f, 0.f, 0.f}, rl = 1.f;
   bool prev_def = false;
   float prev_phi = 0.f;
   int hit_k = -1;
@@ -386,10 +367,70 @@ __global__ void __launch_bounds__(RT_N, 4) k_render(MapView m, RenderArgs a) {
   float4 out_n = make_float4(0.f, 0.f, 0.f, 0.f);
   float4 out_c = make_float4(0.f, 0.f, 0.f, 0.f);
 
-  for (int it = 0; it < a.max_samples && state != S_DONE; ++it) {
-    float t;
+  for (;;) {
+    // ---- lanes without a ray take the next work items (warp-aggregated atomic)
+    const bool need = alive && state == S_DONE;
+    const unsigned nm = __ballot_sync(0xffffffffu, need);
+    // lane refill: any finished lane takes a new ray; warp refill: the warp takes a new tile
+    // of 32 rays once every lane has finished (coherent, but lanes wait for the slowest)
+    const bool busy = __any_sync(0xffffffffu, alive && state != S_DONE);
+    if (nm && (a.lane_refill || !busy)) {
+      const int leader = __ffs(nm) - 1;
+      unsigned base = 0;
+      if (lane == leader) base = atomicAdd(a.queue, (unsigned)__popc(nm));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (need) {
+        const unsigned item = base + (unsigned)__popc(nm & ((1u << lane) - 1u));
+        if (item >= (unsigned)a.total) {
+          alive = false;
+        } else {
+          jb = 0;
+#pragma unroll 1
+          while (jb + 1 < a.njobs && item >= (unsigned)a.job[jb + 1].start) ++jb;
+          const RenderJob& J = a.job[jb];
+          const int loc = (int)(item - (unsigned)J.start);
+          const int tile = loc >> 5, w = loc & 31;
+          const int u = (tile % J.tiles_x) * 8 + (w & 7);
+          const int v = (tile / J.tiles_x) * 4 + (w >> 3);
+          if (u < J.K.W && v < J.K.H) {
+            pix = v * J.K.W + u;
+            const Pose32& T = s_pose[jb];
+            // unit ray in camera and world frame
+            const float rc0 = (u - J.K.cx) / J.K.fx, rc1 = (v - J.K.cy) / J.K.fy;
+            rl = sqrtf(rc0 * rc0 + rc1 * rc1 + 1.0f);
+            const float q0 = rc0 / rl, q1 = rc1 / rl, q2 = 1.0f / rl;
+            r[0] = T.R[0] * q0 + T.R[1] * q1 + T.R[2] * q2;
+            r[1] = T.R[3] * q0 + T.R[4] * q1 + T.R[5] * q2;
+            r[2] = T.R[6] * q0 + T.R[7] * q1 + T.R[8] * q2;
+            o[0] = T.t[0];
+            o[1] = T.t[1];
+            o[2] = T.t[2];
+            k1 = (int)floorf(m.zmax * rl / step);
+            k = (int)ceilf(m.zmin * rl / step);
+            state = S_MARCH;
+            it = 0;
+            prev_def = false;
+            prev_phi = 0.f;
+            hit_k = -1;
+            out_depth = 0.f;
+            out_n = make_float4(0.f, 0.f, 0.f, 0.f);
+            out_c = make_float4(0.f, 0.f, 0.f, 0.f);
+            cell.cx = cell.cy = cell.cz = 0x7fffffff;
+            cell.cmask = 0;
+            cell.positive = false;
+            cell.jumped = true;
+          }
+        }
+      }
+    }
+    if (!__any_sync(0xffffffffu, alive)) break;
+    if (!alive || state == S_DONE) continue;
+
+    // ---- one sample of this lane's ray
+    bool finish = ++it > a.max_samples;
+    float t = 0.f;
     if (state == S_MARCH) {
-      if (k > k1) break;
+      finish |= k > k1;
       t = (float)k * step;
     } else if (state == S_SCAN) {
       t = a0 + (float)j * dt;
@@ -399,6 +440,15 @@ __global__ void __launch_bounds__(RT_N, 4) k_render(MapView m, RenderArgs a) {
       t = tb;
     } else {
       t = out_e == 0 ? (float)hit_k * step : (out_e == 1 ? (float)(hit_k - 1) * step : ts);
+    }
+    if (finish) {
+      // a miss (or the sample limit): write the zero outputs
+      const RenderJob& J = a.job[jb];
+      J.depth[pix] = 0.f;
+      J.normals[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (COLOR && J.color) J.color[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
+      state = S_DONE;
+      continue;
     }
     float g[3];
 #pragma unroll
@@ -534,17 +584,27 @@ __global__ void __launch_bounds__(RT_N, 4) k_render(MapView m, RenderArgs a) {
       // normal and colour at the first grid sample behind the crossing, else at the
       // sample in front of it, else at the root
       const float nl = sqrtf(C.n[0] * C.n[0] + C.n[1] * C.n[1] + C.n[2] * C.n[2]);
+      bool done = false;
       if (C.defined && C.wsum > 0.f && nl > 0.f) {
+        const Pose32& T = s_pose[jb];
         const float n0 = C.n[0] / nl, n1 = C.n[1] / nl, n2 = C.n[2] / nl;
         // world -> camera: R^T n
-        const float c0 = a.T.R[0] * n0 + a.T.R[3] * n1 + a.T.R[6] * n2;
-        const float c1 = a.T.R[1] * n0 + a.T.R[4] * n1 + a.T.R[7] * n2;
-        const float c2 = a.T.R[2] * n0 + a.T.R[5] * n1 + a.T.R[8] * n2;
+        const float c0 = T.R[0] * n0 + T.R[3] * n1 + T.R[6] * n2;
+        const float c1 = T.R[1] * n0 + T.R[4] * n1 + T.R[7] * n2;
+        const float c2 = T.R[2] * n0 + T.R[5] * n1 + T.R[8] * n2;
         out_depth = ts / rl;
         out_n = make_float4(c0, c1, c2, out_depth);
         if (COLOR && C.cw > 0.f) out_c = make_float4(C.rgb[0] / C.cw, C.rgb[1] / C.cw, C.rgb[2] / C.cw, 1.0f);
-        state = S_DONE;
+        done = true;
       } else if (++out_e == 3) {
+        done = true;
+      }
+      if (done) {
+        const RenderJob& J = a.job[jb];
+        J.depth[pix] = out_depth;
+        J.normals[pix] = out_n;
+        if (COLOR && J.color) J.color[pix] = out_c;
+        if (COUNT) n_hits += out_depth > 0.f;
         state = S_DONE;
       }
     }
@@ -554,29 +614,44 @@ __global__ void __launch_bounds__(RT_N, 4) k_render(MapView m, RenderArgs a) {
     atomicAdd(ctr + 1, (unsigned long long)n_full);
     atomicAdd(ctr + 2, (unsigned long long)n_cells);
     atomicAdd(ctr + 3, (unsigned long long)n_acells);
-    atomicAdd(ctr + 4, (unsigned long long)(out_depth > 0.f));
+    atomicAdd(ctr + 4, (unsigned long long)n_hits);
     atomicAdd(ctr + 5, (unsigned long long)n_jumps);
   }
-  a.depth[pix] = out_depth;
-  a.normals[pix] = out_n;
-  if (COLOR && a.color) a.color[pix] = out_c;
 }
 
-void launch_render(const MapView& m, const Intr& K, const Pose32& T, const double* Tdev, float* depth,
-                   float4* normals, float4* color, cudaStream_t s, uint8_t* touched) {
-  RenderArgs a;
-  a.K = K;
-  a.T = T;
-  a.Tdev = Tdev;
-  a.touched = touched;
-  a.depth = depth;
-  a.normals = normals;
-  a.color = color;
-  a.max_samples = 1 << 17;
-  dim3 blk(RT_X, RT_Y), grd((K.W + RT_X - 1) / RT_X, (K.H + RT_Y - 1) / RT_Y);
-  const bool col = m.color && color;
-#define DTSDF_RENDER(ST, CO, CN) k_render<ST, CO, CN><<<grd, blk, 0, s>>>(m, a)
-  if (touched) {
+namespace {
+
+// CTAs of the persistent render grid that fit on the device at once (per kernel instance).
+template <typename KernelT>
+int resident_ctas(KernelT kern) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RT_N, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+  return sms * per_sm;
+}
+
+template <int STORE, bool COLOR, bool COUNT, int NJ>
+void launch_k_render(const MapView& m, const RenderBatch<NJ>& a, int ctas, cudaStream_t s) {
+  static thread_local int cached_dev = -1, cached_ctas = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != cached_dev) {
+    cached_ctas = resident_ctas(k_render<STORE, COLOR, COUNT, NJ>);
+    cached_dev = dev;
+  }
+  int grid = ctas > 0 ? ctas : cached_ctas;
+  const int need = (a.total + RT_N - 1) / RT_N;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  k_render<STORE, COLOR, COUNT, NJ><<<grid, RT_N, 0, s>>>(m, a);
+}
+
+template <int NJ>
+void dispatch_render(const MapView& m, const RenderBatch<NJ>& a, bool col, int ctas, cudaStream_t s) {
+  const bool cnt = a.touched != nullptr;
+#define DTSDF_RENDER(ST, CO, CN) launch_k_render<ST, CO, CN, NJ>(m, a, ctas, s)
+  if (cnt) {
     if (m.storage == DTSDF_STORE_FP16) {
       if (col) DTSDF_RENDER(DTSDF_STORE_FP16, true, true); else DTSDF_RENDER(DTSDF_STORE_FP16, false, true);
     } else {
@@ -590,6 +665,42 @@ void launch_render(const MapView& m, const Intr& K, const Pose32& T, const doubl
     }
   }
 #undef DTSDF_RENDER
+}
+
+template <int NJ>
+void fill_batch(RenderBatch<NJ>& a, const RenderJob* jobs, int njobs, unsigned* queue, uint8_t* touched,
+                int lane_refill) {
+  a.njobs = njobs;
+  a.queue = queue;
+  a.touched = touched;
+  a.max_samples = 1 << 17;
+  a.lane_refill = lane_refill;
+  int start = 0;
+  for (int i = 0; i < njobs; ++i) {
+    a.job[i] = jobs[i];
+    a.job[i].tiles_x = (jobs[i].K.W + 7) / 8;
+    a.job[i].start = start;
+    start += a.job[i].tiles_x * ((jobs[i].K.H + 3) / 4) * 32;
+  }
+  a.total = start;
+}
+
+}  // namespace
+
+void launch_render_jobs(const MapView& m, const RenderJob* jobs, int njobs, unsigned* queue, cudaStream_t s,
+                        uint8_t* touched, int ctas, int lane_refill) {
+  bool col = false;
+  for (int i = 0; i < njobs; ++i) col |= jobs[i].color != nullptr;
+  col &= m.color != 0;
+  if (njobs == 1) {
+    RenderBatch<1> a;
+    fill_batch(a, jobs, njobs, queue, touched, lane_refill);
+    dispatch_render(m, a, col, ctas, s);
+  } else {
+    RenderBatch<MAX_RENDER_JOBS> a;
+    fill_batch(a, jobs, njobs, queue, touched, lane_refill);
+    dispatch_render(m, a, col, ctas, s);
+  }
 }
 
 }  // namespace dtsdf
