@@ -97,7 +97,8 @@ typedef struct {
   int64_t blocks;          /* distinct allocated block coordinates */
   int64_t bricks_per_dir[6];
   int64_t capacity;        /* max_blocks */
-  uint32_t error_flags;    /* bit 0: pool full, bit 1: directory full, bit 2: hash probe limit */
+  uint32_t error_flags;    /* bit 0: pool full, bit 1: directory full, bit 2: hash probe limit,
+                              bit 3: allocation work list full */
   int32_t frames;          /* frames integrated */
 } dtsdf_map_stats_t;
 
@@ -134,11 +135,11 @@ DTSDF_API dtsdf_status dtsdf_render(dtsdf_map map, const dtsdf_intrinsics* K, co
 DTSDF_API dtsdf_status dtsdf_render_dev(dtsdf_map map, const dtsdf_intrinsics* K, const double* T_wc_dev,
                                         const dtsdf_render_out* out, void* stream);
 
-/* Launch shape of the map's renders (no counterpart in the paper: scheduling only, the
- * results do not depend on it). ctas: CTAs of the persistent render grid, 0 = one wave of
- * resident CTAs; lane_refill: 1 = a lane whose ray is finished takes the next ray at once,
- * 0 = a warp takes the next 8x4 tile of rays when all its lanes have finished. Defaults:
- * {0, 0}. Returns DTSDF_ERR_INVALID_ARG for ctas < 0 or lane_refill not 0/1. */
+/* Launch shape of the map's renders (no counterpart in the paper: scheduling only; every
+ * shape computes the same samples, decisions and outputs). ctas: CTAs of the persistent
+ * render grid, 0 = one wave of resident CTAs. lane_refill: 1 = a lane whose ray is finished
+ * takes the next ray at once, 0 = a warp takes the next 8x4 tile of rays when all its lanes
+ * have finished. Defaults {0, 0}. DTSDF_ERR_INVALID_ARG for ctas < 0 or lane_refill not 0/1. */
 typedef struct {
   int32_t ctas;
   int32_t lane_refill;

@@ -202,7 +202,8 @@ class Map:
                                      _stream_ptr(stream)), "dtsdf_render_dev")
 
     def set_render_opts(self, ctas: int = 0, lane_refill: bool = False):
-        """Launch shape of this map's renders (persistent CTAs, 0 = one resident wave; refill policy)."""
+        """Launch shape of this map's renders: persistent CTAs (0 = one resident wave) and the
+        refill policy of finished lanes. Every shape gives the same outputs."""
         o = RenderOpts(int(ctas), int(bool(lane_refill)))
         check(lib().dtsdf_set_render_opts(self._h, ctypes.byref(o)), "dtsdf_set_render_opts")
 

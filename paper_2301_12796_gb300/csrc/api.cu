@@ -109,7 +109,7 @@ struct dtsdf_map_s {
   // stream before the kernel, so concurrent renders on different streams use different slots
   unsigned* render_q = nullptr;
   std::atomic<uint32_t> render_q_next{0};
-  dtsdf_render_opts ropts = {0, 0};
+  RenderShape shape;
 };
 
 constexpr uint32_t RENDER_Q_SLOTS = 1024;
@@ -155,7 +155,7 @@ static dtsdf_status render_launch(dtsdf_map m, const dtsdf_intrinsics& K, const 
   J.depth = out->depth;
   J.normals = (float4*)out->normals;
   J.color = (float4*)out->color;
-  launch_render_jobs(m->v, &J, 1, q, s, touched, m->ropts.ctas, m->ropts.lane_refill);
+  launch_render_jobs(m->v, &J, 1, q, s, touched, m->shape);
   CK_LAUNCH("render");
   return DTSDF_OK;
 }
@@ -369,7 +369,8 @@ dtsdf_status dtsdf_render_dev(dtsdf_map m, const dtsdf_intrinsics* K, const doub
 dtsdf_status dtsdf_set_render_opts(dtsdf_map m, const dtsdf_render_opts* o) {
   if (!m || !o || o->ctas < 0 || (o->lane_refill != 0 && o->lane_refill != 1))
     return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
-  m->ropts = *o;
+  m->shape.ctas = o->ctas;
+  m->shape.lane_refill = o->lane_refill;
   return DTSDF_OK;
 }
 
@@ -400,7 +401,7 @@ dtsdf_status dtsdf_render_touched(dtsdf_map m, const dtsdf_intrinsics* K, const 
       J.depth = depth;
       J.normals = nrm;
       J.color = col;
-      launch_render_jobs(m->v, &J, 1, q, s, flags, m->ropts.ctas, m->ropts.lane_refill);
+      launch_render_jobs(m->v, &J, 1, q, s, flags, m->shape);
       e = cudaGetLastError();
     }
   }

@@ -73,10 +73,17 @@ struct RenderBatch {
   int lane_refill;   // 1: a finished lane takes the next ray; 0: a warp takes a tile when all lanes finish
 };
 
-// Render njobs (1..MAX_RENDER_JOBS) frames in one persistent launch; ctas <= 0 picks one
-// wave of resident CTAs.
+// Launch shape of a render: persistent CTAs (0 = one wave of resident CTAs) and the refill
+// policy of finished lanes (1: take the next ray at once; 0: the warp takes a new tile when
+// all its lanes have finished).
+struct RenderShape {
+  int ctas = 0;
+  int lane_refill = 0;
+};
+
+// Render njobs (1..MAX_RENDER_JOBS) frames in one persistent launch.
 void launch_render_jobs(const MapView& m, const RenderJob* jobs, int njobs, unsigned* queue, cudaStream_t s,
-                        uint8_t* touched = nullptr, int ctas = 0, int lane_refill = 0);
+                        uint8_t* touched, const RenderShape& shape);
 void launch_frame_pyramid(const float4* P, const uint8_t* rgb, int levels, const Intr* K, float* const* depth,
                           float* const* inten, cudaStream_t s);
 void launch_keyframe_pyramid(const uint8_t* rgb, int levels, const Intr* K, float* const* tmpI, float4* const* kf,

@@ -122,37 +122,46 @@ __device__ __forceinline__ float2 ld_geom(const MapView& m, size_t i, uint8_t* t
   return __ldg(m.geom + i);
 }
 
-// Trilinear weight of corner q = (q&1, q>>1&1, q>>2&1).
+// Trilinear weight of corner q = (q&1, q>>1&1, q>>2&1) (colour interpolation).
 __device__ __forceinline__ float corner_w(int q, float fx, float fy, float fz) {
   return ((q & 1) ? fx : 1.0f - fx) * ((q & 2) ? fy : 1.0f - fy) * ((q & 4) ? fz : 1.0f - fz);
 }
 
 // Trilinear sdf and weight of direction D at base voxel g with fractions (fx, fy, fz);
-// false unless all 8 corners exist with weight > 0. Accumulates on the fly (no arrays).
+// false unless all 8 corners exist with weight > 0. Evaluated as nested linear
+// interpolations (x, then y, then z) with explicit fused multiply-adds, identically on both
+// paths below, so a constant field interpolates to exactly its value: the central
+// differences of a flat (truncated) region are exactly zero, as in the double-precision
+// definition, instead of a rounding residue that would pass the gradient test.
+__device__ __forceinline__ float lerp_rn(float a, float b, float t) { return __fmaf_rn(t, b - a, a); }
+
 template <int STORE, bool COUNT>
 __device__ __forceinline__ bool interp(const MapView& m, Cell& c, int D, int g0, int g1, int g2, float fx, float fy,
                                        float fz, float& phi, float& W, uint8_t* touched) {
   const int l0 = g0 & 7, l1 = g1 & 7, l2 = g2 & 7;
-  float acc = 0.f, accw = 0.f;
   if (l0 < 7 && l1 < 7 && l2 < 7) {
     // all corners in one brick
     const int slot = slot_of(m, c, D, g0, g1, g2);
     if (slot < 0) return false;
     const size_t base = (size_t)slot * BVOX + (l2 * 8 + l1) * 8 + l0;
+    float2 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      v[q] = ld_geom<STORE, COUNT>(m, base + ((q >> 2) & 1) * 64 + ((q >> 1) & 1) * 8 + (q & 1), touched);
     bool ok = true;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float2 v = ld_geom<STORE, COUNT>(m, base + ((q >> 2) & 1) * 64 + ((q >> 1) & 1) * 8 + (q & 1), touched);
-      const float wq = corner_w(q, fx, fy, fz);
-      ok &= v.y > 0.0f;
-      acc += wq * v.x;
-      accw += wq * v.y;
-    }
-    phi = acc;
-    W = accw;
+    for (int q = 0; q < 8; ++q) ok &= v[q].y > 0.0f;
+    const float s00 = lerp_rn(v[0].x, v[1].x, fx), s10 = lerp_rn(v[2].x, v[3].x, fx);
+    const float s01 = lerp_rn(v[4].x, v[5].x, fx), s11 = lerp_rn(v[6].x, v[7].x, fx);
+    const float w00 = lerp_rn(v[0].y, v[1].y, fx), w10 = lerp_rn(v[2].y, v[3].y, fx);
+    const float w01 = lerp_rn(v[4].y, v[5].y, fx), w11 = lerp_rn(v[6].y, v[7].y, fx);
+    phi = lerp_rn(lerp_rn(s00, s10, fy), lerp_rn(s01, s11, fy), fz);
+    W = lerp_rn(lerp_rn(w00, w10, fy), lerp_rn(w01, w11, fy), fz);
     return ok;
   }
-  // corners spread over several bricks (base voxel on a brick face)
+  // corners spread over several bricks (base voxel on a brick face): the same nested
+  // interpolation, carried in scalars through the corner loop
+  float sa = 0.f, wa = 0.f, sx0 = 0.f, wx0 = 0.f, sy0 = 0.f, wy0 = 0.f;
 #pragma unroll 1
   for (int q = 0; q < 8; ++q) {
     const int x0 = g0 + (q & 1), x1 = g1 + ((q >> 1) & 1), x2 = g2 + ((q >> 2) & 1);
@@ -160,12 +169,26 @@ __device__ __forceinline__ bool interp(const MapView& m, Cell& c, int D, int g0,
     if (slot < 0) return false;
     const float2 v = ld_geom<STORE, COUNT>(m, (size_t)slot * BVOX + ((x2 & 7) * 8 + (x1 & 7)) * 8 + (x0 & 7), touched);
     if (!(v.y > 0.0f)) return false;
-    const float wq = corner_w(q, fx, fy, fz);
-    acc += wq * v.x;
-    accw += wq * v.y;
+    if (!(q & 1)) {
+      sa = v.x;
+      wa = v.y;
+      continue;
+    }
+    const float sx = lerp_rn(sa, v.x, fx), wx = lerp_rn(wa, v.y, fx);
+    if (!(q & 2)) {
+      sx0 = sx;
+      wx0 = wx;
+      continue;
+    }
+    const float sy = lerp_rn(sx0, sx, fy), wy = lerp_rn(wx0, wx, fy);
+    if (!(q & 4)) {
+      sy0 = sy;
+      wy0 = wy;
+      continue;
+    }
+    phi = lerp_rn(sy0, sy, fz);
+    W = lerp_rn(wy0, wy, fz);
   }
-  phi = acc;
-  W = accw;
   return true;
 }
 
@@ -211,8 +234,10 @@ __device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, cons
     const float wf = WD * fmaxf(vr, 0.0f);
     fw += wf;
     facc += wf * phiD;
-    // central differences of the trilinear field at +-h along each axis
-    float gx = 0.f, gy = 0.f, gz = 0.f;
+    // central differences (phi(+h) - phi(-h)) / 2h of the trilinear field along each axis;
+    // exactly zero where the field is flat (a sum of +-phi/2h terms could leave a rounding
+    // residue that passes the gradient test)
+    float gx = 0.f, gy = 0.f, gz = 0.f, pplus = 0.f;
     bool gok = true;
 #pragma unroll 1
     for (int e = 0; e < 6; ++e) {
@@ -224,10 +249,14 @@ __device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, cons
         gok = false;
         break;
       }
-      const float val = (float)sgn * pe * inv2h;
-      gx += ax == 0 ? val : 0.f;
-      gy += ax == 1 ? val : 0.f;
-      gz += ax == 2 ? val : 0.f;
+      if (!(e & 1)) {
+        pplus = pe;
+        continue;
+      }
+      const float d = (pplus - pe) * inv2h;
+      gx = ax == 0 ? d : gx;
+      gy = ax == 1 ? d : gy;
+      gz = ax == 2 ? d : gz;
     }
     if (!gok) continue;
     const float gn = sqrtf(gx * gx + gy * gy + gz * gz);
@@ -688,7 +717,8 @@ void fill_batch(RenderBatch<NJ>& a, const RenderJob* jobs, int njobs, unsigned* 
 }  // namespace
 
 void launch_render_jobs(const MapView& m, const RenderJob* jobs, int njobs, unsigned* queue, cudaStream_t s,
-                        uint8_t* touched, int ctas, int lane_refill) {
+                        uint8_t* touched, const RenderShape& sh) {
+  const int ctas = sh.ctas, lane_refill = sh.lane_refill;
   bool col = false;
   for (int i = 0; i < njobs; ++i) col |= jobs[i].color != nullptr;
   col &= m.color != 0;
