@@ -268,6 +268,62 @@ DTSDF_API dtsdf_status dtsdf_icp_step_noalloc(const float* depth, const dtsdf_in
                                               double stop_norm, double* T_rel_dev, dtsdf_icp_stats* stats_dev,
                                               void* stream);
 
+/* ------------------------------------------------------------- batches ---- */
+
+/* One registration problem of a batch: the current frame held by `icp` (prepared with
+ * dtsdf_icp_set_frame; its pyramid must have at least opts->levels levels), the reference
+ * render `ref` (device; its normals carry the depth in w) with intrinsics K_ref, the pose
+ * T_rel_dev (device, 16 doubles, current camera -> render camera, read and updated) and
+ * stats_dev (device, one dtsdf_icp_stats, or NULL). sim3 = 1: Sim(3) (Sec. 6, 7x7 system),
+ * 0: SE(3). Problems of one batch may have different image sizes. */
+typedef struct {
+  dtsdf_icp icp;
+  dtsdf_render_out ref;
+  dtsdf_intrinsics K_ref;
+  double* T_rel_dev;
+  dtsdf_icp_stats* stats_dev;
+  int32_t sim3;
+} dtsdf_icp_problem;
+
+/* Launch shape of a batched registration (no counterpart in the paper): CTAs per problem
+ * (a thread-block cluster: 1, 2, 4, 8 or 16) and threads per CTA (128, 256 or 512). */
+typedef struct {
+  int32_t cluster;
+  int32_t threads;
+} dtsdf_batch_shape;
+
+/* Whole geometric coarse-to-fine schedule of dtsdf_icp_solve for n problems in one launch per
+ * 64 problems: each problem is one thread-block cluster that runs opts->levels levels of
+ * opts->iters[l] Gauss-Newton iterations (early stop per level at ||xi|| < opts->stop_norm),
+ * with the deterministic reduction (rank order, FP64), the FP64 Cholesky solve and the pose
+ * update on the device (Eqs. geometric_ICP, ICP_weight, ICP_Hessian, ICP_solution,
+ * deltaT_update; Sim(3) exponential of Sec. 6). No photometric term (opts->lambda is ignored);
+ * opts->kahan selects compensated summation. shape NULL: {8, 256}. Asynchronous, allocates
+ * nothing and synchronises nothing: can be captured in a CUDA graph. DTSDF_ERR_INVALID_ARG
+ * for a bad problem, option or shape; DTSDF_ERR_CUDA if the cluster cannot be scheduled. */
+DTSDF_API dtsdf_status dtsdf_icp_batch(const dtsdf_icp_problem* problems, int32_t n, const dtsdf_icp_opts* opts,
+                                       const dtsdf_batch_shape* shape, void* stream);
+
+/* Autotuner of dtsdf_icp_batch: times every supported shape on these problems (scratch copies
+ * of the poses; the problems' poses and stats are left unchanged) and returns the fastest in
+ * *best and its time in *best_ms (host). Synchronous; allocates scratch. */
+DTSDF_API dtsdf_status dtsdf_icp_batch_tune(const dtsdf_icp_problem* problems, int32_t n,
+                                            const dtsdf_icp_opts* opts, dtsdf_batch_shape* best, float* best_ms,
+                                            void* stream);
+
+/* One frame of a batched render: intrinsics, pose (device, 16 doubles, camera -> world) and
+ * caller-owned outputs as for dtsdf_render. */
+typedef struct {
+  dtsdf_intrinsics K;
+  const double* T_wc_dev;
+  dtsdf_render_out out;
+} dtsdf_render_job;
+
+/* Ray-cast n frames of any sizes (Sec. 4, as dtsdf_render) in one persistent launch per 64
+ * frames: the pixels of all frames form one work list that the CTAs take in 8x4 tiles, so
+ * uneven frames share the GPU without a tail per frame. Asynchronous, allocates nothing. */
+DTSDF_API dtsdf_status dtsdf_render_batch(dtsdf_map map, const dtsdf_render_job* jobs, int32_t n, void* stream);
+
 /* Exponential map of se(3) (sim3 = 0, xi[6]) or sim(3) (sim3 = 1, xi[7]) evaluated by the
  * library's device code (the closed form of the matrix exponential of the 4x4 generator);
  * out: host 16 doubles. Synchronous; exposed for verification. */

@@ -50,6 +50,19 @@ class RenderOpts(ctypes.Structure):
     _fields_ = [("ctas", c_int32), ("lane_refill", c_int32)]
 
 
+class IcpProblem(ctypes.Structure):
+    _fields_ = [("icp", c_void_p), ("ref", RenderOut), ("K_ref", Intrinsics), ("T_rel_dev", c_void_p),
+                ("stats_dev", c_void_p), ("sim3", c_int32)]
+
+
+class BatchShape(ctypes.Structure):
+    _fields_ = [("cluster", c_int32), ("threads", c_int32)]
+
+
+class RenderJob(ctypes.Structure):
+    _fields_ = [("K", Intrinsics), ("T_wc_dev", c_void_p), ("out", RenderOut)]
+
+
 class MapStats(ctypes.Structure):
     _fields_ = [("bricks", c_int64), ("blocks", c_int64), ("bricks_per_dir", c_int64 * 6), ("capacity", c_int64),
                 ("error_flags", c_uint32), ("frames", c_int32)]
@@ -103,6 +116,11 @@ SIGNATURES = {
     "dtsdf_icp_step_noalloc": ([P, ctypes.POINTER(Intrinsics), ctypes.POINTER(RenderOut),
                                 ctypes.POINTER(Intrinsics), c_int32, c_float, c_float, c_int32, c_double, P, P, P],
                                c_int32),
+    "dtsdf_icp_batch": ([ctypes.POINTER(IcpProblem), c_int32, ctypes.POINTER(IcpOpts), ctypes.POINTER(BatchShape), P],
+                        c_int32),
+    "dtsdf_icp_batch_tune": ([ctypes.POINTER(IcpProblem), c_int32, ctypes.POINTER(IcpOpts),
+                              ctypes.POINTER(BatchShape), ctypes.POINTER(ctypes.c_float), P], c_int32),
+    "dtsdf_render_batch": ([P, ctypes.POINTER(RenderJob), c_int32, P], c_int32),
     "dtsdf_exp": ([c_int32, P, P], c_int32),
     "dtsdf_last_error": ([], ctypes.c_char_p),
     "dtsdf_version": ([], ctypes.c_char_p),
@@ -200,6 +218,15 @@ class Map:
         Ki = intrinsics(K)
         check(lib().dtsdf_render_dev(self._h, ctypes.byref(Ki), T_dev.data_ptr(), ctypes.byref(out),
                                      _stream_ptr(stream)), "dtsdf_render_dev")
+
+    def render_batch(self, jobs, stream=None):
+        """Render several frames in one launch. jobs: list of (K, T_dev float64 [4, 4] CUDA tensor,
+        depth [H, W], normals [H, W, 4], color [H, W, 4] or None)."""
+        arr = (RenderJob * max(len(jobs), 1))()
+        for i, (K, T_dev, depth, normals, color) in enumerate(jobs):
+            arr[i] = RenderJob(intrinsics(K), T_dev.data_ptr(),
+                               RenderOut(depth.data_ptr(), normals.data_ptr(), None if color is None else color.data_ptr()))
+        check(lib().dtsdf_render_batch(self._h, arr, len(jobs), _stream_ptr(stream)), "dtsdf_render_batch")
 
     def set_render_opts(self, ctas: int = 0, lane_refill: bool = False):
         """Launch shape of this map's renders: persistent CTAs (0 = one resident wave) and the
@@ -307,6 +334,47 @@ class Icp:
         check(lib().dtsdf_icp_solve(self._h, ctypes.byref(out), ctypes.byref(Ki), int(sim3), T_rel_dev.data_ptr(), rs,
                                     ctypes.byref(opts), None if stats_dev is None else stats_dev.data_ptr(),
                                     _stream_ptr(stream)), "dtsdf_icp_solve")
+
+
+def _problems(items):
+    """items: (icp, ref_normals, K_ref, T_dev, sim3[, stats_dev]) -> ctypes array of IcpProblem."""
+    arr = (IcpProblem * max(len(items), 1))()
+    for i, it in enumerate(items):
+        icp, ref_n, K_ref, T_dev, sim3 = it[:5]
+        st = it[5] if len(it) > 5 else None
+        arr[i] = IcpProblem(icp._h, RenderOut(None, ref_n.data_ptr(), None), intrinsics(K_ref), T_dev.data_ptr(),
+                            None if st is None else st.data_ptr(), int(bool(sim3)))
+    return arr
+
+
+def icp_batch(items, opts: IcpOpts, shape=None, stream=None):
+    """Whole geometric schedule for several problems in one launch (dtsdf_icp_batch).
+    items: list of (icp: Icp with its frame set, ref_normals CUDA tensor [H, W, 4], K_ref,
+    T_dev float64 CUDA tensor [4, 4] updated in place, sim3 bool[, stats_dev uint8 CUDA tensor]);
+    shape: (cluster, threads) or None."""
+    arr = _problems(items)
+    sh = None if shape is None else ctypes.byref(BatchShape(*shape))
+    check(lib().dtsdf_icp_batch(arr, len(items), ctypes.byref(opts), sh, _stream_ptr(stream)), "dtsdf_icp_batch")
+
+
+def icp_batch_tune(items, opts: IcpOpts, stream=None):
+    """Fastest (cluster, threads) for these problems and its time in ms (dtsdf_icp_batch_tune)."""
+    arr = _problems(items)
+    best = BatchShape()
+    ms = ctypes.c_float()
+    check(lib().dtsdf_icp_batch_tune(arr, len(items), ctypes.byref(opts), ctypes.byref(best), ctypes.byref(ms),
+                                     _stream_ptr(stream)), "dtsdf_icp_batch_tune")
+    return (best.cluster, best.threads), ms.value
+
+
+STATS_BYTES = ctypes.sizeof(IcpStats)
+
+
+def stats_from_device(buf) -> IcpStats:
+    """IcpStats from a uint8 CUDA tensor of STATS_BYTES bytes written by the device."""
+    st = IcpStats()
+    ctypes.memmove(ctypes.byref(st), bytes(buf.cpu().numpy().tobytes()), STATS_BYTES)
+    return st
 
 
 def pose_compose(A_dev, B_dev, C_dev, invert_a=False, stream=None):

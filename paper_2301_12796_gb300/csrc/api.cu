@@ -7,6 +7,7 @@
 #include <atomic>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 
@@ -753,6 +754,150 @@ dtsdf_status dtsdf_icp_solve(dtsdf_icp c, const dtsdf_render_out* ref, const dts
   }
   CK(cudaMemcpyAsync(T_rel_dev, c->pose, sizeof(double) * 16, cudaMemcpyDeviceToDevice, s));
   if (stats_dev) CK(cudaMemcpyAsync(stats_dev, c->stats, sizeof(dtsdf_icp_stats), cudaMemcpyDeviceToDevice, s));
+  return DTSDF_OK;
+}
+
+// ------------------------------------------------------------------ batches
+
+static bool shape_ok(const dtsdf_batch_shape& b) {
+  return (b.cluster == 1 || b.cluster == 2 || b.cluster == 4 || b.cluster == 8 || b.cluster == 16) &&
+         (b.threads == 128 || b.threads == 256 || b.threads == 512);
+}
+
+static bool problem_ok(const dtsdf_icp_problem& p, const dtsdf_icp_opts* o) {
+  return p.icp && p.icp->has_frame && p.ref.normals && intr_ok(&p.K_ref) && p.T_rel_dev &&
+         (p.sim3 == 0 || p.sim3 == 1) && o->levels <= p.icp->levels;
+}
+
+static dtsdf_status batch_launch(const dtsdf_icp_problem* pr, int32_t n, const dtsdf_icp_opts* o,
+                                 const dtsdf_batch_shape& b, double* const* pose_override, cudaStream_t s) {
+  for (int32_t i0 = 0; i0 < n; i0 += ICP_BATCH_MAX) {
+    const int m = n - i0 < ICP_BATCH_MAX ? n - i0 : ICP_BATCH_MAX;
+    IcpBatchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = m;
+    a.levels = o->levels;
+    for (int l = 0; l < o->levels; ++l) {
+      a.iters[l] = o->iters[l];
+      a.eps[l] = o->eps[l];
+    }
+    a.zmin = o->z_min;
+    a.min_rows = o->min_rows;
+    a.stop_norm = o->stop_norm;
+    for (int i = 0; i < m; ++i) {
+      const dtsdf_icp_problem& p = pr[i0 + i];
+      IcpProblemDev& d = a.p[i];
+      for (int l = 0; l < o->levels; ++l) {
+        d.depth[l] = p.icp->depth[l];
+        d.K[l] = p.icp->K[l];
+      }
+      d.ref = (const float4*)p.ref.normals;
+      d.Kr = to_intr(p.K_ref);
+      d.pose = pose_override ? pose_override[i0 + i] : p.T_rel_dev;
+      d.stats = pose_override ? nullptr : p.stats_dev;
+      d.sim3 = p.sim3;
+    }
+    cudaError_t e = cudaSuccess;
+    launch_icp_batch(a, o->kahan, b.cluster, b.threads, s, &e);
+    if (e != cudaSuccess) return cuda_fail(e, "dtsdf_icp_batch launch");
+  }
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_icp_batch(const dtsdf_icp_problem* problems, int32_t n, const dtsdf_icp_opts* o,
+                             const dtsdf_batch_shape* shape, void* stream) {
+  if (!problems || n < 0 || !o || !opts_ok(o, ICP_MAX_LEVELS)) return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  dtsdf_batch_shape b = shape ? *shape : dtsdf_batch_shape{8, 256};
+  if (!shape_ok(b)) return fail(DTSDF_ERR_INVALID_ARG, "unsupported batch shape");
+  for (int32_t i = 0; i < n; ++i)
+    if (!problem_ok(problems[i], o)) return fail(DTSDF_ERR_INVALID_ARG, "bad problem");
+  if (n == 0) return DTSDF_OK;
+  return batch_launch(problems, n, o, b, nullptr, (cudaStream_t)stream);
+}
+
+dtsdf_status dtsdf_icp_batch_tune(const dtsdf_icp_problem* problems, int32_t n, const dtsdf_icp_opts* o,
+                                  dtsdf_batch_shape* best, float* best_ms, void* stream) {
+  if (!problems || n <= 0 || !o || !best || !opts_ok(o, ICP_MAX_LEVELS))
+    return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  for (int32_t i = 0; i < n; ++i)
+    if (!problem_ok(problems[i], o)) return fail(DTSDF_ERR_INVALID_ARG, "bad problem");
+  cudaStream_t s = (cudaStream_t)stream;
+  double* scratch = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  std::vector<double*> poses((size_t)n);
+  cudaError_t e = cudaMalloc((void**)&scratch, sizeof(double) * 16 * (size_t)n);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float bt = 3.4e38f;
+  dtsdf_batch_shape bb = {8, 256};
+  dtsdf_status st = DTSDF_OK;
+  for (int32_t i = 0; i < n; ++i) poses[(size_t)i] = scratch + 16 * (size_t)i;
+  const int clusters[5] = {1, 2, 4, 8, 16};
+  const int threads[3] = {128, 256, 512};
+  for (int ci = 0; ci < 5 && e == cudaSuccess && st == DTSDF_OK; ++ci) {
+    for (int ti = 0; ti < 3 && e == cudaSuccess && st == DTSDF_OK; ++ti) {
+      const dtsdf_batch_shape b = {clusters[ci], threads[ti]};
+      float best_rep = 3.4e38f;
+      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        // every trial starts from the problems' own poses
+        for (int32_t i = 0; i < n && e == cudaSuccess; ++i)
+          e = cudaMemcpyAsync(poses[(size_t)i], problems[i].T_rel_dev, sizeof(double) * 16, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) break;
+        e = cudaEventRecord(e0, s);
+        if (e != cudaSuccess) break;
+        st = batch_launch(problems, n, o, b, poses.data(), s);
+        if (st != DTSDF_OK) {
+          // a shape the device cannot schedule is skipped
+          cudaGetLastError();
+          st = DTSDF_OK;
+          best_rep = 3.4e38f;
+          break;
+        }
+        e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best_rep) best_rep = ms;
+      }
+      if (e == cudaSuccess && best_rep < bt) {
+        bt = best_rep;
+        bb = b;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "dtsdf_icp_batch_tune");
+  if (!(bt < 3.4e38f)) return fail(DTSDF_ERR_CUDA, "no batch shape could be scheduled");
+  *best = bb;
+  if (best_ms) *best_ms = bt;
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_render_batch(dtsdf_map m, const dtsdf_render_job* jobs, int32_t n, void* stream) {
+  if (!m || !jobs || n < 0) return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  for (int32_t i = 0; i < n; ++i)
+    if (!intr_ok(&jobs[i].K) || !jobs[i].T_wc_dev || !jobs[i].out.depth || !jobs[i].out.normals)
+      return fail(DTSDF_ERR_INVALID_ARG, "bad render job");
+  cudaStream_t s = (cudaStream_t)stream;
+  RenderJob J[MAX_RENDER_JOBS];
+  for (int32_t i0 = 0; i0 < n; i0 += MAX_RENDER_JOBS) {
+    const int k = n - i0 < MAX_RENDER_JOBS ? n - i0 : MAX_RENDER_JOBS;
+    memset(J, 0, sizeof(J));
+    for (int i = 0; i < k; ++i) {
+      const dtsdf_render_job& j = jobs[i0 + i];
+      J[i].K = to_intr(j.K);
+      J[i].Tdev = j.T_wc_dev;
+      J[i].depth = j.out.depth;
+      J[i].normals = (float4*)j.out.normals;
+      J[i].color = (float4*)j.out.color;
+    }
+    unsigned* q = render_slot(m);
+    CK(cudaMemsetAsync(q, 0, sizeof(unsigned), s));
+    launch_render_jobs(m->v, J, k, q, s, nullptr, m->shape);
+    CK_LAUNCH("render_batch");
+  }
   return DTSDF_OK;
 }
 

@@ -10,6 +10,8 @@
 // thread solves H xi = -g by FP64 Cholesky and applies dT <- exp(xi) dT on the device.
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 #include "internal.h"
 
 namespace dtsdf {
@@ -154,6 +156,96 @@ __host__ __device__ void exp_sim3(const double* xi, int dim, double* T) {
 
 __global__ void k_exp(int dim, const double* xi, double* T) { exp_sim3(xi, dim, T); }
 
+// Solve and update of one Gauss-Newton iteration from the FP64 sums (layout of Acc<DIM>:
+// upper triangle of H, g, E, geometric rows, photometric rows) for the leading dsolve
+// unknowns (dsolve = DIM, or 6 for an SE(3) problem accumulated with DIM = 7): FP64
+// Cholesky of H xi = -g (Eq. ICP_solution; a pivot below 1e-10 max diag(H), or fewer than
+// min_rows rows, is a degenerate system), then pose <- exp(xi) pose (Eq. deltaT_update).
+// Records the iteration in *st. Returns true when the level is finished (converged:
+// ||xi|| < stop_norm, or degenerate: pose unchanged).
+template <int DIM>
+__device__ bool icp_solve_update(const double* sum, int dsolve, double* pose, dtsdf_icp_stats* st, int min_rows,
+                                 double stop_norm) {
+  constexpr int NH = DIM * (DIM + 1) / 2;
+  constexpr int N = NH + DIM + 3;
+  double H[7][7], g[7];
+  {
+    int k = 0;
+    for (int i = 0; i < DIM; ++i)
+      for (int j = i; j < DIM; ++j) {
+        H[i][j] = H[j][i] = sum[k++];
+      }
+    for (int i = 0; i < DIM; ++i) g[i] = sum[NH + i];
+  }
+  const int D = dsolve;
+  for (int i = 0; i < 49; ++i) st->H[i] = 0.0;
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) st->H[7 * i + j] = H[i][j];
+  for (int i = 0; i < 7; ++i) {
+    st->g[i] = i < D ? g[i] : 0.0;
+    st->xi[i] = 0.0;
+  }
+  st->error = sum[NH + DIM];
+  st->rows_photo = (int64_t)sum[N - 1];
+  st->rows = (int64_t)sum[N - 2] + st->rows_photo;
+  st->dim = D;
+  st->iterations += 1;
+  st->step_norm = 0.0;
+  st->converged = 0;
+  // Cholesky H = L L^T; a pivot below 1e-10 max diag(H) is a degenerate system
+  double dmax = 0.0;
+  for (int i = 0; i < D; ++i) dmax = fmax(dmax, H[i][i]);
+  bool ok = st->rows >= min_rows && dmax > 0.0;
+  double L[7][7];
+  for (int j = 0; j < D && ok; ++j) {
+    double s = H[j][j];
+    for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+    if (!(s > 1e-10 * dmax)) {
+      ok = false;
+      break;
+    }
+    L[j][j] = sqrt(s);
+    for (int i = j + 1; i < D; ++i) {
+      double t = H[i][j];
+      for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+      L[i][j] = t / L[j][j];
+    }
+  }
+  if (!ok) {
+    st->status = DTSDF_ERR_DEGENERATE;
+    return true;
+  }
+  double y[7], xi[7];
+  for (int i = 0; i < D; ++i) {
+    double t = -g[i];
+    for (int k = 0; k < i; ++k) t -= L[i][k] * y[k];
+    y[i] = t / L[i][i];
+  }
+  for (int i = D - 1; i >= 0; --i) {
+    double t = y[i];
+    for (int k = i + 1; k < D; ++k) t -= L[k][i] * xi[k];
+    xi[i] = t / L[i][i];
+  }
+  double nrm = 0.0;
+  for (int i = 0; i < D; ++i) {
+    st->xi[i] = xi[i];
+    nrm += xi[i] * xi[i];
+  }
+  nrm = sqrt(nrm);
+  double E[16], T0[16], T1[16];
+  exp_sim3(xi, D, E);
+  for (int i = 0; i < 16; ++i) T0[i] = pose[i];
+  mat4_mul(E, T0, T1);
+  for (int i = 0; i < 16; ++i) pose[i] = T1[i];
+  st->status = 0;
+  st->step_norm = nrm;
+  if (nrm < stop_norm) {
+    st->converged = 1;
+    return true;
+  }
+  return false;
+}
+
 // ---------------------------------------------------------- reduction -----
 struct IcpArgs {
   // current level
@@ -222,6 +314,58 @@ struct Acc {
   __device__ __forceinline__ float total(int i) const { return KAHAN ? v[i] - c[i] : v[i]; }
 };
 
+// Point-to-plane row of one current-frame pixel (Eq. geometric_ICP, Eq. ICP_geometric_dx,
+// weight of Eq. ICP_weight): back-project depth z at (u, v) with the level intrinsics, move
+// it by the estimate x = p + ((A p) + t) (A = sR - I), associate it with the nearest pixel of
+// the full-resolution render (normals with the depth in w) and, for an inlier
+// (||q - x|| <= eps), add w J J^T, w J r, w r^2 and the row count. The scale column of
+// Sim(3) is filled when `scale` is set (DIM = 7), else left zero. Returns the moved point
+// and the depth weight for the photometric row.
+template <int DIM, bool KAHAN>
+__device__ __forceinline__ void geo_row(Acc<DIM, KAHAN>& acc, float z, int u, int v, float fx, float fy, float cx,
+                                        float cy, const float Am[9], const float tv[3], const float4* __restrict__ ref,
+                                        int rW, int rH, float rfx, float rfy, float rcx, float rcy, float eps2,
+                                        float zmin, bool scale, float& x0, float& x1, float& x2, float& wz) {
+  using A = Acc<DIM, KAHAN>;
+  const float P0 = rmul(z, rdiv(rsub((float)u, cx), fx));
+  const float P1 = rmul(z, rdiv(rsub((float)v, cy), fy));
+  const float P2 = z;
+  const float d0 = radd(rdot3(Am[0], Am[1], Am[2], P0, P1, P2), tv[0]);
+  const float d1 = radd(rdot3(Am[3], Am[4], Am[5], P0, P1, P2), tv[1]);
+  const float d2 = radd(rdot3(Am[6], Am[7], Am[8], P0, P1, P2), tv[2]);
+  x0 = radd(P0, d0);
+  x1 = radd(P1, d1);
+  x2 = radd(P2, d2);
+  const float zw = z + 1.0f - zmin;
+  wz = 1.0f / (zw * zw);  // Eq. ICP_weight
+  if (!(x2 > 0.0f)) return;
+  // projective association into the full-resolution render, nearest pixel
+  const float uf = radd(rmul(rdiv(x0, x2), rfx), rcx);
+  const float vf = radd(rmul(rdiv(x1, x2), rfy), rcy);
+  const float ur = floorf(radd(uf, 0.5f)), vr = floorf(radd(vf, 0.5f));
+  if (!(ur >= 0.0f && vr >= 0.0f && ur < (float)rW && vr < (float)rH)) return;
+  const float4 nq = __ldg(ref + (int)vr * rW + (int)ur);
+  const float dr = nq.w;
+  if (!(dr > 0.0f)) return;
+  const float q0 = rmul(dr, rdiv(rsub(ur, rcx), rfx));
+  const float q1 = rmul(dr, rdiv(rsub(vr, rcy), rfy));
+  const float q2 = dr;
+  const float e0 = rsub(q0, x0), e1 = rsub(q1, x1), e2 = rsub(q2, x2);
+  if (!(rdot3(e0, e1, e2, e0, e1, e2) <= eps2)) return;
+  // r = <q - x, n> evaluated as <(q - p) - delta, n> (no cancellation of metre-sized terms)
+  const float r = ((q0 - P0) - d0) * nq.x + ((q1 - P1) - d1) * nq.y + ((q2 - P2) - d2) * nq.z;
+  float J[DIM];
+  J[0] = -nq.x;
+  J[1] = -nq.y;
+  J[2] = -nq.z;
+  J[3] = -(x1 * nq.z - x2 * nq.y);
+  J[4] = -(x2 * nq.x - x0 * nq.z);
+  J[5] = -(x0 * nq.y - x1 * nq.x);
+  if (DIM == 7) J[DIM - 1] = scale ? -(nq.x * x0 + nq.y * x1 + nq.z * x2) : 0.0f;
+  acc.row(J, r, wz);
+  acc.v[A::N - 2] += 1.0f;  // a count, exact in FP32 below 2^24
+}
+
 template <int DIM, bool PHOTO, bool KAHAN>
 __global__ void __launch_bounds__(ICP_THREADS) k_icp(IcpArgs a) {
   using A = Acc<DIM, KAHAN>;
@@ -254,45 +398,9 @@ __global__ void __launch_bounds__(ICP_THREADS) k_icp(IcpArgs a) {
     const float z = __ldg(a.depth + p);
     if (!(z > 0.0f)) continue;
     const int u = p % a.W, v = p / a.W;
-    const float P0 = rmul(z, rdiv(rsub((float)u, a.cx), a.fx));
-    const float P1 = rmul(z, rdiv(rsub((float)v, a.cy), a.fy));
-    const float P2 = z;
-    const float d0 = radd(rdot3(Am[0], Am[1], Am[2], P0, P1, P2), tv[0]);
-    const float d1 = radd(rdot3(Am[3], Am[4], Am[5], P0, P1, P2), tv[1]);
-    const float d2 = radd(rdot3(Am[6], Am[7], Am[8], P0, P1, P2), tv[2]);
-    const float x0 = radd(P0, d0), x1 = radd(P1, d1), x2 = radd(P2, d2);
-    const float zw = z + 1.0f - a.zmin;
-    const float wz = 1.0f / (zw * zw);  // Eq. ICP_weight
-    if (x2 > 0.0f) {
-      // projective association into the full-resolution render, nearest pixel
-      const float uf = radd(rmul(rdiv(x0, x2), a.rfx), a.rcx);
-      const float vf = radd(rmul(rdiv(x1, x2), a.rfy), a.rcy);
-      const float ur = floorf(radd(uf, 0.5f)), vr = floorf(radd(vf, 0.5f));
-      if (ur >= 0.0f && vr >= 0.0f && ur < (float)a.rW && vr < (float)a.rH) {
-        const float4 nq = __ldg(a.ref + (int)vr * a.rW + (int)ur);
-        const float dr = nq.w;
-        if (dr > 0.0f) {
-          const float q0 = rmul(dr, rdiv(rsub(ur, a.rcx), a.rfx));
-          const float q1 = rmul(dr, rdiv(rsub(vr, a.rcy), a.rfy));
-          const float q2 = dr;
-          const float e0 = rsub(q0, x0), e1 = rsub(q1, x1), e2 = rsub(q2, x2);
-          if (rdot3(e0, e1, e2, e0, e1, e2) <= eps2) {
-            // r = <q - x, n> evaluated as <(q - p) - delta, n> (no cancellation of metre-sized terms)
-            const float r = ((q0 - P0) - d0) * nq.x + ((q1 - P1) - d1) * nq.y + ((q2 - P2) - d2) * nq.z;
-            float J[DIM];
-            J[0] = -nq.x;
-            J[1] = -nq.y;
-            J[2] = -nq.z;
-            J[3] = -(x1 * nq.z - x2 * nq.y);
-            J[4] = -(x2 * nq.x - x0 * nq.z);
-            J[5] = -(x0 * nq.y - x1 * nq.x);
-            if (DIM == 7) J[DIM - 1] = -(nq.x * x0 + nq.y * x1 + nq.z * x2);
-            acc.row(J, r, wz);
-            acc.v[A::N - 2] += 1.0f;  // a count, exact in FP32 below 2^24
-          }
-        }
-      }
-    }
+    float x0, x1, x2, wz;
+    geo_row<DIM, KAHAN>(acc, z, u, v, a.fx, a.fy, a.cx, a.cy, Am, tv, a.ref, a.rW, a.rH, a.rfx, a.rfy, a.rcx, a.rcy,
+                        eps2, a.zmin, true, x0, x1, x2, wz);
     if (PHOTO) {
       // frame-to-keyframe photometric row (Eq. keyframe_icp), y = T_rs x
       const float y0 = radd(rdot3(a.Rrs[0], a.Rrs[1], a.Rrs[2], x0, x1, x2), a.trs[0]);
@@ -368,82 +476,140 @@ __global__ void __launch_bounds__(ICP_THREADS) k_icp(IcpArgs a) {
   __syncthreads();
   if (threadIdx.x != 0) return;
   *a.ticket = 0u;
-  double H[7][7], g[7];
-  {
-    int k = 0;
-    for (int i = 0; i < DIM; ++i)
-      for (int j = i; j < DIM; ++j) {
-        H[i][j] = H[j][i] = s_sum[k++];
+  if (icp_solve_update<DIM>(s_sum, DIM, a.pose, a.stats, a.min_rows, a.stop_norm)) *a.stop = 1;
+}
+
+// ------------------------------------------------------------- batched ----
+// Batched registration: one thread-block cluster per problem runs the whole coarse-to-fine
+// schedule (levels-1 .. 0, iters[l] Gauss-Newton iterations, early stop per level) in one
+// launch. Per iteration the CTAs of the cluster walk the problem's pixels, reduce their rows
+// in FP32 (warp shuffles, then warps in a fixed order) into a partial in their shared memory;
+// after a cluster barrier, rank 0 adds the partials in FP64 in rank order through distributed
+// shared memory, solves and updates the pose; after a second barrier every CTA copies the
+// pose and the level decision from rank 0. The published pose is double-buffered by
+// iteration parity, so a CTA still copying one iteration's pose cannot see the next one.
+// Only hardware cluster barriers are waited on: the CTAs of a cluster are co-scheduled.
+namespace cg = cooperative_groups;
+
+constexpr int BATCH_MAX_THREADS = 512;
+
+template <bool KAHAN>
+__global__ void __launch_bounds__(BATCH_MAX_THREADS) k_icp_batch(const __grid_constant__ IcpBatchArgs a) {
+  using A = Acc<7, KAHAN>;
+  cg::cluster_group cl = cg::this_cluster();
+  const int CL = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int prob = blockIdx.x / CL;
+  __shared__ float s_red[BATCH_MAX_THREADS / 32][A::N];
+  __shared__ float s_part[A::N];
+  __shared__ double s_sum[A::N];
+  __shared__ double s_pose[2][16];  // rank 0: published estimate by iteration parity
+  __shared__ int s_done[2];
+  __shared__ double s_cur[16];      // this CTA's copy of the estimate
+  __shared__ dtsdf_icp_stats s_st;  // rank 0
+  if (prob >= a.n) return;  // the whole cluster (no barrier reached)
+  const IcpProblemDev& P = a.p[prob];
+  const int dsolve = P.sim3 ? 7 : 6;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  if (tid < 16) s_cur[tid] = P.pose[tid];
+  if (rank == 0 && tid == 0) {
+    memset(&s_st, 0, sizeof(s_st));
+    s_done[0] = s_done[1] = 0;
+  }
+  __syncthreads();
+  int gi = 0;  // iterations run so far (all levels): parity of the published buffers
+  for (int l = a.levels - 1; l >= 0; --l) {
+    const float* __restrict__ depth = P.depth[l];
+    const Intr K = P.K[l];
+    const int n = K.W * K.H;
+    const float eps2 = rmul(a.eps[l], a.eps[l]);
+    for (int it = 0; it < a.iters[l]; ++it, ++gi) {
+      float Am[9], tv[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Am[3 * i + j] = (float)(s_cur[4 * i + j] - (i == j ? 1.0 : 0.0));
+        tv[i] = (float)s_cur[4 * i + 3];
       }
-    for (int i = 0; i < DIM; ++i) g[i] = s_sum[A::NH + i];
-  }
-  dtsdf_icp_stats* st = a.stats;
-  for (int i = 0; i < 49; ++i) st->H[i] = 0.0;
-  for (int i = 0; i < DIM; ++i)
-    for (int j = 0; j < DIM; ++j) st->H[7 * i + j] = H[i][j];
-  for (int i = 0; i < 7; ++i) {
-    st->g[i] = i < DIM ? g[i] : 0.0;
-    st->xi[i] = 0.0;
-  }
-  st->error = s_sum[A::NH + DIM];
-  st->rows_photo = (int64_t)s_sum[A::N - 1];
-  st->rows = (int64_t)s_sum[A::N - 2] + st->rows_photo;
-  st->dim = DIM;
-  st->iterations += 1;
-  st->step_norm = 0.0;
-  st->converged = 0;
-  // Cholesky H = L L^T; a pivot below 1e-10 max diag(H) is a degenerate system
-  double dmax = 0.0;
-  for (int i = 0; i < DIM; ++i) dmax = fmax(dmax, H[i][i]);
-  bool ok = st->rows >= a.min_rows && dmax > 0.0;
-  double L[7][7];
-  for (int j = 0; j < DIM && ok; ++j) {
-    double s = H[j][j];
-    for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
-    if (!(s > 1e-10 * dmax)) {
-      ok = false;
-      break;
+      A acc;
+      acc.zero();
+      for (int p = rank * nth + tid; p < n; p += CL * nth) {
+        const float z = __ldg(depth + p);
+        if (!(z > 0.0f)) continue;
+        float x0, x1, x2, wz;
+        geo_row<7, KAHAN>(acc, z, p % K.W, p / K.W, K.fx, K.fy, K.cx, K.cy, Am, tv, P.ref, P.Kr.W, P.Kr.H, P.Kr.fx,
+                          P.Kr.fy, P.Kr.cx, P.Kr.cy, eps2, a.zmin, P.sim3 != 0, x0, x1, x2, wz);
+      }
+      // CTA partial: warp shuffles, then warps in a fixed order
+      const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+      for (int i = 0; i < A::N; ++i) {
+        float x = acc.total(i);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) s_red[warp][i] = x;
+      }
+      __syncthreads();
+      if (tid < A::N) {
+        float sm = 0.f;
+        for (int w = 0; w < nth / 32; ++w) sm += s_red[w][tid];
+        s_part[tid] = sm;
+      }
+      cl.sync();  // every partial of the cluster is in place
+      const int b = gi & 1;
+      if (rank == 0) {
+        if (tid < A::N) {
+          double sm = 0.0;
+          for (int r = 0; r < CL; ++r) sm += (double)*cl.map_shared_rank(&s_part[tid], r);
+          s_sum[tid] = sm;
+        }
+        __syncthreads();
+        if (tid == 0) {
+          const bool stop = icp_solve_update<7>(s_sum, dsolve, s_cur, &s_st, a.min_rows, a.stop_norm);
+          for (int i = 0; i < 16; ++i) s_pose[b][i] = s_cur[i];
+          s_done[b] = stop ? 1 : 0;
+        }
+      }
+      cl.sync();  // the estimate and the level decision are published
+      __shared__ int s_stop;
+      if (rank != 0 && tid < 16) s_cur[tid] = *cl.map_shared_rank(&s_pose[b][tid], 0);
+      if (tid == 0) s_stop = rank == 0 ? s_done[b] : *cl.map_shared_rank(&s_done[b], 0);
+      __syncthreads();
+      if (s_stop) {
+        ++gi;
+        break;
+      }
     }
-    L[j][j] = sqrt(s);
-    for (int i = j + 1; i < DIM; ++i) {
-      double t = H[i][j];
-      for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
-      L[i][j] = t / L[j][j];
-    }
   }
-  if (!ok) {
-    st->status = DTSDF_ERR_DEGENERATE;
-    *a.stop = 1;
-    return;
+  cl.sync();  // rank 0's shared memory stays alive until every copy from it is done
+  if (rank == 0 && tid == 0) {
+    for (int i = 0; i < 16; ++i) P.pose[i] = s_cur[i];
+    if (P.stats) *P.stats = s_st;
   }
-  double y[7], xi[7];
-  for (int i = 0; i < DIM; ++i) {
-    double t = -g[i];
-    for (int k = 0; k < i; ++k) t -= L[i][k] * y[k];
-    y[i] = t / L[i][i];
+}
+
+void launch_icp_batch(const IcpBatchArgs& a, int kahan, int cluster, int threads, cudaStream_t s, cudaError_t* err) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.n * cluster), 1, 1);
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e;
+  if (kahan) {
+    if (cluster > 8) cudaFuncSetAttribute(k_icp_batch<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaLaunchKernelEx(&cfg, k_icp_batch<true>, a);
+  } else {
+    if (cluster > 8) cudaFuncSetAttribute(k_icp_batch<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaLaunchKernelEx(&cfg, k_icp_batch<false>, a);
   }
-  for (int i = DIM - 1; i >= 0; --i) {
-    double t = y[i];
-    for (int k = i + 1; k < DIM; ++k) t -= L[k][i] * xi[k];
-    xi[i] = t / L[i][i];
-  }
-  double nrm = 0.0;
-  for (int i = 0; i < DIM; ++i) {
-    st->xi[i] = xi[i];
-    nrm += xi[i] * xi[i];
-  }
-  nrm = sqrt(nrm);
-  double E[16], T0[16], T1[16];
-  exp_sim3(xi, DIM, E);
-  for (int i = 0; i < 16; ++i) T0[i] = a.pose[i];
-  mat4_mul(E, T0, T1);
-  for (int i = 0; i < 16; ++i) a.pose[i] = T1[i];
-  st->status = 0;
-  st->step_norm = nrm;
-  if (nrm < a.stop_norm) {
-    st->converged = 1;
-    *a.stop = 1;
-  }
+  *err = e;
 }
 
 // ------------------------------------------------------------ launchers ---

@@ -91,4 +91,31 @@ void launch_keyframe_pyramid(const uint8_t* rgb, int levels, const Intr* K, floa
 void launch_icp(const IcpLaunch& L, int sim3, bool photo, int grid, cudaStream_t s);
 void launch_exp(int dim, const double* xi, double* T, cudaStream_t s);
 
+// One problem of a batched registration: current-frame pyramid (levels of the batch),
+// reference render, pose (device, 16 doubles, read and written) and optional stats.
+constexpr int ICP_MAX_LEVELS = 4;
+struct IcpProblemDev {
+  const float* depth[ICP_MAX_LEVELS];
+  Intr K[ICP_MAX_LEVELS];
+  const float4* ref;
+  Intr Kr;
+  double* pose;
+  dtsdf_icp_stats* stats;
+  int sim3;
+};
+
+constexpr int ICP_BATCH_MAX = 64;
+struct IcpBatchArgs {
+  IcpProblemDev p[ICP_BATCH_MAX];
+  int n, levels;
+  int iters[ICP_MAX_LEVELS];
+  float eps[ICP_MAX_LEVELS];
+  float zmin;
+  int min_rows;
+  double stop_norm;
+};
+
+// Batched registration, one cluster of `cluster` CTAs (threads each) per problem.
+void launch_icp_batch(const IcpBatchArgs& a, int kahan, int cluster, int threads, cudaStream_t s, cudaError_t* err);
+
 }  // namespace dtsdf

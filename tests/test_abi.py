@@ -51,6 +51,10 @@ def test_struct_layouts_match_header():
              sizeof(dtsdf_icp_opts), sizeof(dtsdf_icp_stats));
       printf("%zu %zu %zu\n", offsetof(dtsdf_icp_opts, stop_norm), offsetof(dtsdf_icp_stats, rows),
              offsetof(dtsdf_params, max_blocks));
+      printf("%zu %zu %zu %zu\n", sizeof(dtsdf_render_opts), sizeof(dtsdf_icp_problem), sizeof(dtsdf_batch_shape),
+             sizeof(dtsdf_render_job));
+      printf("%zu %zu %zu\n", offsetof(dtsdf_icp_problem, K_ref), offsetof(dtsdf_icp_problem, sim3),
+             offsetof(dtsdf_render_job, out));
       return 0;
     }
     """
@@ -65,6 +69,10 @@ def test_struct_layouts_match_header():
     assert sizes == [ctypes.sizeof(x) for x in (dt.Params, dt.Intrinsics, dt.Frame, dt.RenderOut, dt.MapStats,
                                                 dt.IcpOpts, dt.IcpStats)]
     assert offs == [dt.IcpOpts.stop_norm.offset, dt.IcpStats.rows.offset, dt.Params.max_blocks.offset]
+    assert [int(x) for x in lines[2].split()] == [ctypes.sizeof(x) for x in (dt.RenderOpts, dt.IcpProblem,
+                                                                             dt.BatchShape, dt.RenderJob)]
+    assert [int(x) for x in lines[3].split()] == [dt.IcpProblem.K_ref.offset, dt.IcpProblem.sim3.offset,
+                                                  dt.RenderJob.out.offset]
 
 
 def test_invalid_parameters_rejected_on_host(lib):
@@ -81,6 +89,14 @@ def test_invalid_parameters_rejected_on_host(lib):
     assert lib.dtsdf_icp_create(4, 4, 3, ctypes.byref(h)) == dt.ERR_INVALID_ARG
     assert lib.dtsdf_icp_create(640, 480, 9, ctypes.byref(h)) == dt.ERR_INVALID_ARG
     assert lib.dtsdf_destroy(None) == dt.ERR_INVALID_ARG
+    # batch entry points check their arguments before any CUDA call
+    opts = dt.icp_opts()
+    assert lib.dtsdf_icp_batch(None, 1, ctypes.byref(opts), None, None) == dt.ERR_INVALID_ARG
+    pr = (dt.IcpProblem * 1)()
+    assert lib.dtsdf_icp_batch(pr, 1, ctypes.byref(opts), None, None) == dt.ERR_INVALID_ARG
+    assert lib.dtsdf_icp_batch(pr, 0, ctypes.byref(opts), ctypes.byref(dt.BatchShape(3, 256)), None) == \
+        dt.ERR_INVALID_ARG
+    assert lib.dtsdf_render_batch(None, None, 1, None) == dt.ERR_INVALID_ARG
 
 
 def test_product_path_has_no_cpu_fallback(tmp_path, monkeypatch):
