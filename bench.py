@@ -34,6 +34,11 @@ METRIC = "render+ICP frames/s @640x480, % HBM roofline; p50/p99 serve latency"
 WORKLOAD = ("kinect-shaped FP32: 4x4x3 m synthetic room, 5 mm voxels, tau 2 cm, 6 directions, RGB; 300-frame "
             "map; per frame render 640x480 depth+normal+colour, 3-level SE(3) ICP 4/5/10 it + f2kf photometric, "
             "fusion")
+WORKLOAD_FP16 = WORKLOAD.replace("kinect-shaped FP32", "kinect-shaped FP16 storage (half sdf, half weight, u8 colour)")
+WORKLOAD_MS = ("multi-sensor Sim(3): map of the 4x4x3 m room from 300 sensor-A frames (640x480, f 525, 5 mm voxels); "
+               "per step {n} sensor-B frames 1280x720 (f 910, depth x s, s in U[0.9, 1.1]) with priors perturbed "
+               "5 deg / 10 cm: preprocessing + pyramid, one batched render at the priors, one batched Sim(3) ICP "
+               "(3 levels x 20 iterations), the step captured in a CUDA graph")
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -47,6 +52,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile", action="store_true", help="small run for ncu: map of 60 frames, few steps")
+    ap.add_argument("--workload", default="tracking", choices=["tracking", "multi_sensor"],
+                    help="tracking: Kinect-shaped tracking frames (default); multi_sensor: batched Sim(3) "
+                         "registration of 1280x720 second-sensor frames against the 640x480 map")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
+                    help="map storage: FP32 sdf/weight/colour, or FP16 sdf + half weight + u8 colour")
+    ap.add_argument("--problems", type=int, default=64, help="multi_sensor: registration problems per step")
     return ap.parse_args()
 
 
@@ -129,11 +140,12 @@ LAUNCHES = {"render": 1, "set_frame": 6, "set_keyframe": 6, "compose": 1, "solve
 class Tracker:
     """Device-resident tracking loop over the frames (map, ICP context, buffers, poses)."""
 
-    def __init__(self, dt, torch, s, frames, dev, map_frames):
+    def __init__(self, dt, torch, s, frames, dev, map_frames, storage=0):
         self.dt, self.torch, self.s, self.dev = dt, torch, s, dev
         K = s.K
         self.K = K
-        self.map = dt.Map(dt.params(voxel_size=0.005, truncation=0.02, max_blocks=1 << 19, z_max=s.z_max, color=True))
+        self.map = dt.Map(dt.params(voxel_size=0.005, truncation=0.02, max_blocks=1 << 19, z_max=s.z_max, color=True,
+                                    storage=storage))
         self.icp = dt.Icp(K.width, K.height, 3)
         self.opts = opts_kinect(dt)
         H, W = K.height, K.width
@@ -273,30 +285,17 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
-# --------------------------------------------------------------------- main --
-def main():
-    args = parse()
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        return run_reference(args, rank, world)
-    import torch
-    import torch.distributed as tdist
-    import paper_2301_12796_gb300 as dt
-    from paper_2301_12796_gb300 import build as B
-    if rank == 0:
-        B.build()
-    if world > 1:
-        tdist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
-        tdist.barrier()
-        B.build()
-    torch.cuda.set_device(local)
-    dev = torch.device(f"cuda:{local}")
-    assert args.warmup >= 3 or args.profile, "at least 3 warm-up steps"
+# --------------------------------------------------------------- tracking --
+def voxel_bytes(storage: int) -> tuple[int, int]:
+    """Bytes per voxel of a geometry brick and of a colour brick."""
+    return (4, 4) if storage == 1 else (8, 16)
+
+
+def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
+    storage = 1 if args.storage == "fp16" else 0
     n_frames = 60 if args.profile else args.frames
     s, frames = make_workload(n_frames)
-    tr = Tracker(dt, torch, s, frames, dev, range(n_frames))
+    tr = Tracker(dt, torch, s, frames, dev, range(n_frames), storage)
     st = tr.map.stats()
     l2 = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MB > L2
     for i in range(args.warmup):
@@ -310,7 +309,8 @@ def main():
     geom_b, col_b = np.mean([x[0] for x in tb]), np.mean([x[1] for x in tb])
     march = tr.map.touched(s.K, frames[1 + args.warmup % (tr.n - 1) - 1].pose, counters=True)[2]
     npix = s.K.width * s.K.height
-    render_bytes = geom_b * 512 * 8 + col_b * 512 * 16 + npix * (4 + 16 + 16)
+    gvb, cvb = voxel_bytes(storage)
+    render_bytes = geom_b * 512 * gvb + col_b * 512 * cvb + npix * (4 + 16 + 16)
     # ---------------- timed region
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     clk = ClockSampler(local)
@@ -380,7 +380,8 @@ def main():
         out = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "config": {"workload": WORKLOAD, "resolution": "640x480", "map_frames": n_frames,
+               "config": {"workload": WORKLOAD if not storage else WORKLOAD_FP16, "resolution": "640x480",
+                          "storage": args.storage, "map_frames": n_frames,
                           "map_bricks": int(st.bricks), "map_voxels_per_direction_M": [round(x * 512 / 1e6, 2)
                                                                                       for x in st.bricks_per_dir],
                           "l2": "flushed between steps (512 MB write outside the timed events)",
@@ -392,6 +393,256 @@ def main():
                           "wall_s_timed_loop": t_wall, "median_translation_error_m": terr},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------- multi-sensor --
+MS_ITERS = (20, 20, 20)
+MS_EPS = (0.01, 0.1, 0.2)
+MS_LAUNCHES_PER_FRAME = 5  # outlier filter, normals, depth extraction, 2 pyramid levels
+
+
+class MultiSensor:
+    """Batched Sim(3) registration of second-sensor frames against the first sensor's map."""
+
+    def __init__(self, dt, torch, dev, n_problems, n_frames, storage):
+        import scenes
+        self.dt, self.torch, self.dev = dt, torch, dev
+        self.room = room = scenes.kinect_room(1, n_frames=n_frames)
+        self.map = dt.Map(dt.params(voxel_size=0.005, truncation=0.02, max_blocks=1 << 19, z_max=room.z_max,
+                                    color=False, storage=storage))
+        for i in range(n_frames):
+            f = room.frame(i)
+            self.map.integrate(torch.from_numpy(f.depth).to(dev), None, room.K, f.pose)
+        self.probs = scenes.multi_sensor_problems(room, n_problems, seed=1)
+        self.K = self.probs[0]["K"]
+        H, W = self.K.height, self.K.width
+        n = n_problems
+        self.depth = [torch.from_numpy(p["depth"]).to(dev) for p in self.probs]
+        self.icps = [dt.Icp(W, H, 3) for _ in range(n)]
+        self.ref_d = torch.zeros(n, H, W, device=dev)
+        self.ref_n = torch.zeros(n, H, W, 4, device=dev)
+        self.prior = torch.from_numpy(np.stack([p["prior"] for p in self.probs])).to(dev)
+        self.T = torch.zeros(n, 4, 4, dtype=torch.float64, device=dev)
+        self.eye = torch.eye(4, dtype=torch.float64, device=dev).expand(n, 4, 4).contiguous()
+        self.stats = torch.zeros(n, dt.STATS_BYTES, dtype=torch.uint8, device=dev)
+        self.opts = dt.icp_opts(levels=3, iters=MS_ITERS, eps=MS_EPS, stop_norm=1e-6, min_rows=10)
+        self.jobs = [(self.K, self.prior[i], self.ref_d[i], self.ref_n[i], None) for i in range(n)]
+        self.items = [(self.icps[i], self.ref_n[i], self.K, self.T[i], True, self.stats[i]) for i in range(n)]
+        self.shape = None
+        self.n = n
+
+    def preprocess(self, stream=None):
+        for i in range(self.n):
+            self.icps[i].set_frame(self.depth[i], None, self.K, 0.1, 6.0, 0.01, stream=stream)
+
+    def render(self, stream=None):
+        self.map.render_batch(self.jobs, stream=stream)
+
+    def register(self, stream=None):
+        self.T.copy_(self.eye)
+        self.dt.icp_batch(self.items, self.opts, shape=self.shape, stream=stream)
+
+    def step(self, stream=None):
+        self.preprocess(stream)
+        self.render(stream)
+        self.register(stream)
+
+    def errors(self):
+        """Rotation (deg), translation (m) and relative scale errors against the true poses."""
+        T = self.T.cpu().numpy()
+        rot, tr, sc = [], [], []
+        for i, p in enumerate(self.probs):
+            E = np.linalg.inv(p["prior"]) @ p["T_true"]  # render camera <- true camera, unscaled
+            s_est = np.cbrt(np.linalg.det(T[i][:3, :3]))
+            R_est = T[i][:3, :3] / s_est
+            ang = np.degrees(np.arccos(np.clip((np.trace(R_est.T @ E[:3, :3]) - 1) / 2, -1, 1)))
+            rot.append(ang)
+            tr.append(np.linalg.norm(T[i][:3, 3] - E[:3, 3]))
+            sc.append(abs(s_est * p["scale"] - 1))
+        return np.array(rot), np.array(tr), np.array(sc)
+
+
+def ms_cpu_baseline(ms, n_frames):
+    """The oracle on a bounded sample of one registration problem, scaled to the whole batch."""
+    import oracle
+    from oracle import icp as oicp
+    room, p, K = ms.room, ms.probs[0], ms.K
+    P = oracle.Params(voxel_size=0.005, truncation=0.02, z_max=room.z_max, color=False)
+    om = oracle.OracleMap(P)
+    for i in range(0, n_frames, max(1, n_frames // 6)):
+        f = room.frame(i)
+        om.integrate(f.depth, None, room.K, f.pose)
+    stride = 32
+    vv, uu = np.mgrid[0:K.height:stride, 0:K.width:stride]
+    pix = np.stack([uu.ravel(), vv.ravel()], 1).astype(np.int32)
+    t0 = time.perf_counter()
+    om.render(K, p["prior"], pix)
+    t_render = (time.perf_counter() - t0) * (K.width * K.height) / len(pix)
+    ref = room.render(p["prior"], K=K, noise=False, exact=True)
+    rn = np.zeros(ref.normals.shape[:2] + (4,), np.float32)
+    rn[..., :3] = ref.normals
+    pre = oracle.preprocess(p["depth"], K, 0.1, 6.0, 0.01)
+    levels = oicp.pyramid(pre["z"], K, 3)
+    st = oicp.Settings(sim3=True, eps=MS_EPS, iters=MS_ITERS)
+    t_icp = 0.0
+    for l in range(3):
+        t0 = time.perf_counter()
+        oicp.step(levels[l], ref.depth, rn, K, np.eye(4), st.eps[l], st, level_index=l)
+        t_icp += (time.perf_counter() - t0) * MS_ITERS[l]
+    per_problem = t_render + t_icp
+    sample = (f"one problem: oracle render of 1/{stride * stride} of the 1280x720 pixels scaled up "
+              f"({t_render:.1f} s), one Sim(3) iteration per level on the full pyramid scaled to 20 per level "
+              f"({t_icp:.1f} s); oracle map fused from 1/50 of the sensor-A frames")
+    return 1.0 / per_problem, sample
+
+
+def run_multi_sensor(args, dt, torch, tdist, dev, rank, world, local):
+    storage = 1 if args.storage == "fp16" else 0
+    n_frames = 60 if args.profile else args.frames
+    ms = MultiSensor(dt, torch, dev, args.problems, n_frames, storage)
+    stream = torch.cuda.current_stream()
+    # autotuner: launch shape of the batched registration on these problems
+    ms.preprocess()
+    ms.render()
+    ms.T.copy_(ms.eye)
+    shape, tune_ms = dt.icp_batch_tune(ms.items, ms.opts)
+    ms.shape = shape
+    for _ in range(2):
+        ms.step()
+    torch.cuda.synchronize()
+    # phase times of one eager step (events on the launching stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ph = []
+    for _ in range(3):
+        ev[0].record()
+        ms.preprocess()
+        ev[1].record()
+        ms.render()
+        ev[2].record()
+        ms.register()
+        ev[3].record()
+        torch.cuda.synchronize()
+        ph.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])])
+    ph = np.array(ph).mean(0)
+    # one step captured in a CUDA graph
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            ms.step(side)
+    stream.wait_stream(side)
+    l2 = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clk = ClockSampler(local)
+    clk.start()
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush_l2(l2)
+        evs[k][0].record()
+        g.replay()
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    if world > 1:
+        tdist.barrier()
+    clocks = clk.stop()
+    total_ms = float(sum(a.elapsed_time(b) for a, b in evs))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    n = ms.n
+    value = world * n * args.steps / (total_ms / 1000.0)
+    rot, tr, sc = ms.errors()
+    # e2e through host buffers: sensor-B depth frames from pinned memory, poses read back
+    e2e = None
+    if not args.no_e2e:
+        hd = [torch.from_numpy(p["depth"]).pin_memory() for p in ms.probs]
+        host_T = torch.empty(n, 4, 4, dtype=torch.float64).pin_memory()
+        n_e2e = min(args.steps, 10)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            for i in range(n):
+                ms.depth[i].copy_(hd[i], non_blocking=True)
+            ms.step()
+            host_T.copy_(ms.T, non_blocking=True)
+            stream.synchronize()
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": world * n * n_e2e / e2e_s, "unit": "registrations/s",
+               "h2d_bytes_per_step": int(sum(x.numel() * 4 for x in hd)), "d2h_bytes_per_step": n * 128,
+               "steps": n_e2e}
+    # roofline of the dominant kernel (the batched render): touched bricks of a sample of problems
+    gvb, _ = voxel_bytes(storage)
+    sample = list(range(0, n, max(1, n // 8)))
+    geom = np.mean([ms.map.touched(ms.K, ms.probs[i]["prior"])[0] for i in sample])
+    npix = ms.K.width * ms.K.height
+    render_bytes = n * (geom * 512 * gvb + npix * (4 + 16))
+    peak, peak_kind = measured_hbm_peak()
+    achieved = render_bytes / (ph[1] / 1000.0) / 1e9
+    # batched ICP: per pixel-iteration 4 B depth + 16 B gathered render tap (upper bound, L2 reuse lowers it)
+    st_all = [dt.stats_from_device(ms.stats[i]) for i in range(n)]
+    iters = float(np.mean([x.iterations for x in st_all]))
+    roof = {"kernel": "k_render (batched direct DTSDF ray-cast)", "bound": "hbm", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+            "algorithmic_bytes_per_launch": render_bytes, "geom_bricks_per_problem": geom, "launch_ms": float(ph[1])}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu and not args.profile:
+        v, sample_desc = ms_cpu_baseline(ms, n_frames)
+        cpu = {"value": v, "unit": "registrations/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample_desc}
+    if rank == 0:
+        out = {"metric": "multi-sensor Sim(3) registrations/s (1280x720 vs 640x480 map)", "value": value,
+               "unit": "registrations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": WORKLOAD_MS.format(n=n), "problems": n, "storage": args.storage,
+                          "map_frames": n_frames, "map_bricks": int(ms.map.stats().bricks),
+                          "l2": "flushed between steps (512 MB write outside the timed events)",
+                          "parallelism": f"replicas x{world}", "cuda_graph": True,
+                          "batch_shape": {"cluster": shape[0], "threads": shape[1], "tuned_ms": tune_ms},
+                          "phase_ms_eager": {"preprocess": float(ph[0]), "render_batch": float(ph[1]),
+                                             "icp_batch": float(ph[2])},
+                          "icp_iterations_mean": iters,
+                          "rays_per_s": world * n * npix * args.steps / (total_ms / 1000.0),
+                          "errors_vs_truth": {"rot_deg_median": float(np.median(rot)),
+                                              "trans_m_median": float(np.median(tr)),
+                                              "scale_median": float(np.median(sc)),
+                                              "success_rate": float(np.mean((rot < 1.0) & (tr < 0.02)))}},
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": n * MS_LAUNCHES_PER_FRAME + 2 * ((n + 63) // 64), "clocks": clocks}
+        print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------- main --
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    import torch
+    import torch.distributed as tdist
+    import paper_2301_12796_gb300 as dt
+    from paper_2301_12796_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+        tdist.barrier()
+        B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    assert args.warmup >= 3 or args.profile, "at least 3 warm-up steps"
+    if args.workload == "multi_sensor":
+        run_multi_sensor(args, dt, torch, tdist, dev, rank, world, local)
+    else:
+        run_tracking(args, dt, torch, tdist, dev, rank, world, local)
     if world > 1:
         tdist.destroy_process_group()
 

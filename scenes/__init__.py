@@ -320,6 +320,21 @@ def sensor_b(room: Scene, seed: int = 1) -> tuple[Intrinsics, float, np.random.G
     return Intrinsics(1280, 720, 910.0, 910.0, 639.5, 359.5), scale, rng
 
 
+def multi_sensor_problems(room: Scene, n: int = 64, seed: int = 1, rot_deg: float = 5.0,
+                          trans_m: float = 0.10) -> list[dict]:
+    """n registrations of the second sensor (sensor_b) against a map of ``room`` built from the
+    first sensor: true pose near the first sensor's trajectory, seeded depth scale, prior = the
+    true pose perturbed by rot_deg degrees and trans_m metres."""
+    out = []
+    for i in range(n):
+        K, scale, rng = sensor_b(room, seed + i)
+        T_true = room.poses[(i * len(room.poses)) // n] @ perturbation(rng, 2.0, 0.05)
+        frame = room.render(T_true, K=K, frame_id=100000 + i, noise=True, depth_scale=scale)
+        prior = T_true @ perturbation(rng, rot_deg, trans_m)
+        out.append(dict(K=K, scale=scale, T_true=T_true, prior=prior, depth=frame.depth))
+    return out
+
+
 def planes_scene(seed: int = 3) -> Scene:
     """Only planar surfaces (room corner and a tilted box): point-to-plane ICP
     has its exact optimum at the true pose on such a scene."""
