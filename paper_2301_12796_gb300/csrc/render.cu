@@ -91,15 +91,32 @@ __device__ __forceinline__ void cell_enter(const MapView& m, Cell& c, int x, int
   c.filled = active ? 1u : 0u;
 }
 
+// Fill slot row j8 (block cell + (j8 & 1, j8 >> 1 & 1, j8 >> 2)) for the directions in cmask,
+// probing the block's directory entry if it is not known yet; returns the updated probed mask.
+// Out of line with explicit arguments, so the callers' cell state stays in registers.
+__device__ __noinline__ uint32_t fill_slot_row(const unsigned long long* __restrict__ keys,
+                                               const uint32_t* __restrict__ vals, uint32_t hmask,
+                                               const int32_t* __restrict__ dir_slots, int* dirc, int* slot, int cx,
+                                               int cy, int cz, uint32_t cmask, uint32_t probed, int j8) {
+  const int dx = j8 & 1, dy = (j8 >> 1) & 1, dz = j8 >> 2;
+  const int j = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+  if (!((probed >> j) & 1u)) {
+    dirc[j * RT_N] = val_dir(probe_block(keys, vals, hmask, cx + dx, cy + dy, cz + dz));
+    probed |= 1u << j;
+  }
+  const int d = dirc[j * RT_N];
+  for (uint32_t mm = cmask; mm; mm &= mm - 1) {
+    const int E = __ffs(mm) - 1;
+    slot[(E * 8 + j8) * RT_N] = d >= 0 ? __ldg(dir_slots + (size_t)d * 8 + E) : -1;
+  }
+  return probed;
+}
+
 // brick of direction D (active in the cell) in block cell + (j8 & 1, j8 >> 1 & 1, j8 >> 2)
 __device__ __forceinline__ int slot_plus(const MapView& m, Cell& c, int D, int j8) {
   if (!((c.filled >> j8) & 1u)) {
-    const int d = cell_dir(m, c, j8 & 1, (j8 >> 1) & 1, j8 >> 2);
-#pragma unroll 1
-    for (uint32_t mm = c.cmask; mm; mm &= mm - 1) {
-      const int E = __ffs(mm) - 1;
-      c.slot[(E * 8 + j8) * RT_N] = d >= 0 ? __ldg(m.dir_slots + (size_t)d * 8 + E) : -1;
-    }
+    c.probed = fill_slot_row(m.keys, m.vals, m.hmask, m.dir_slots, c.dirc, c.slot, c.cx, c.cy, c.cz, c.cmask, c.probed,
+                             j8);
     c.filled |= 1u << j8;
   }
   return c.slot[(D * 8 + j8) * RT_N];
@@ -139,15 +156,21 @@ template <int STORE, bool COUNT>
 __device__ __forceinline__ bool interp(const MapView& m, Cell& c, int D, int g0, int g1, int g2, float fx, float fy,
                                        float fz, float& phi, float& W, uint8_t* touched) {
   const int l0 = g0 & 7, l1 = g1 & 7, l2 = g2 & 7;
-  if (l0 < 7 && l1 < 7 && l2 < 7) {
-    // all corners in one brick
-    const int slot = slot_of(m, c, D, g0, g1, g2);
-    if (slot < 0) return false;
-    const size_t base = (size_t)slot * BVOX + (l2 * 8 + l1) * 8 + l0;
+  if ((((g0 >> 3) - c.cx) | ((g1 >> 3) - c.cy) | ((g2 >> 3) - c.cz)) == 0) {
+    // base voxel in the cell (every sample of the march): the corners lie in the blocks
+    // cell + {0,1}^3 whose brick slots the cell table holds. All 8 indices are formed first
+    // and the 8 loads issued together, whether or not the corners straddle a brick face.
+    size_t idx[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int x = l0 + (q & 1), y = l1 + ((q >> 1) & 1), z = l2 + ((q >> 2) & 1);
+      const int sl = slot_plus(m, c, D, (x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2));
+      if (sl < 0) return false;
+      idx[q] = (size_t)sl * BVOX + ((z & 7) * 8 + (y & 7)) * 8 + (x & 7);
+    }
     float2 v[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-      v[q] = ld_geom<STORE, COUNT>(m, base + ((q >> 2) & 1) * 64 + ((q >> 1) & 1) * 8 + (q & 1), touched);
+    for (int q = 0; q < 8; ++q) v[q] = ld_geom<STORE, COUNT>(m, idx[q], touched);
     bool ok = true;
 #pragma unroll
     for (int q = 0; q < 8; ++q) ok &= v[q].y > 0.0f;
@@ -159,8 +182,8 @@ __device__ __forceinline__ bool interp(const MapView& m, Cell& c, int D, int g0,
     W = lerp_rn(lerp_rn(w00, w10, fy), lerp_rn(w01, w11, fy), fz);
     return ok;
   }
-  // corners spread over several bricks (base voxel on a brick face): the same nested
-  // interpolation, carried in scalars through the corner loop
+  // base voxel in a neighbouring block (the -h offsets of a gradient): corner by corner, the
+  // same nested interpolation carried in scalars through the loop
   float sa = 0.f, wa = 0.f, sx0 = 0.f, wx0 = 0.f, sy0 = 0.f, wy0 = 0.f;
 #pragma unroll 1
   for (int q = 0; q < 8; ++q) {
