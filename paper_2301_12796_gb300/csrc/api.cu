@@ -128,6 +128,7 @@ static void map_free(dtsdf_map m) {
   cudaFree(m->v.col8);
   cudaFree(m->v.brick_dir);
   cudaFree(m->v.bound);
+  cudaFree(m->v.stamp);
   cudaFree(m->v.occ);
   cudaFree(m->v.counters);
   cudaFree(m->v.work);
@@ -220,14 +221,15 @@ dtsdf_status dtsdf_create(const dtsdf_params* params, void* stream, dtsdf_map* o
   ALLOC(v.dir_slots, sizeof(int32_t) * 8 * (size_t)v.dir_cap);
   ALLOC(v.dir_coord, sizeof(int32_t) * 4 * (size_t)v.dir_cap);
   if (p.storage == DTSDF_STORE_FP16) {
-    ALLOC(v.geom16, sizeof(uint32_t) * BVOX * (size_t)bricks);
+    ALLOC(v.geom16, sizeof(uint32_t) * PVOX * (size_t)bricks);
     if (p.color) ALLOC(v.col8, sizeof(uint32_t) * BVOX * (size_t)bricks);
   } else {
-    ALLOC(v.geom, sizeof(float2) * BVOX * (size_t)bricks);
+    ALLOC(v.geom, sizeof(float2) * PVOX * (size_t)bricks);
     if (p.color) ALLOC(v.col, sizeof(float4) * BVOX * (size_t)bricks);
   }
   ALLOC(v.brick_dir, sizeof(int32_t) * (size_t)bricks);
   ALLOC(v.bound, sizeof(float) * (size_t)bricks);
+  ALLOC(v.stamp, sizeof(uint32_t) * (size_t)bricks);
   ALLOC(v.occ, sizeof(uint32_t) * 2 * (size_t)OCC_WORDS);
   ALLOC(v.counters, sizeof(uint32_t) * C_COUNT);
   ALLOC(v.work, sizeof(int32_t) * (size_t)v.work_cap);
@@ -245,6 +247,7 @@ dtsdf_status dtsdf_create(const dtsdf_params* params, void* stream, dtsdf_map* o
       (e = cudaMemsetAsync(v.req, 0, sizeof(uint32_t) * hcap, s)) != cudaSuccess ||
       (e = cudaMemsetAsync(v.dir_slots, 0xFF, sizeof(int32_t) * 8 * (size_t)v.dir_cap, s)) != cudaSuccess ||
       (e = cudaMemsetAsync(v.counters, 0, sizeof(uint32_t) * C_COUNT, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(v.stamp, 0xFF, sizeof(uint32_t) * (size_t)bricks, s)) != cudaSuccess ||
       (e = cudaMemsetAsync(v.occ, 0, sizeof(uint32_t) * 2 * (size_t)OCC_WORDS, s)) != cudaSuccess) {
     map_free(m);
     return cuda_fail(e, "dtsdf_create init");
@@ -317,6 +320,7 @@ static dtsdf_status integrate_impl(dtsdf_map m, const dtsdf_frame* f, const doub
   Pose32 T;
   memset(&T, 0, sizeof(T));
   if (T_wc) T = to_pose32(T_wc);
+  m->v.frame = (uint32_t)m->frames;
   launch_preprocess(f->depth, K, m->v.zmin, m->v.zmax, m->v.dsup, m->P, m->N, s);
   CK_LAUNCH("preprocess");
   if (m->p.dense_dim <= 0) {
@@ -328,10 +332,6 @@ static dtsdf_status integrate_impl(dtsdf_map m, const dtsdf_frame* f, const doub
   }
   launch_fuse(m->v, K, T, T_dev, m->P, m->N, m->p.color ? f->rgb : nullptr, num_sms(), s);
   CK_LAUNCH("fuse");
-  if (m->p.dense_dim <= 0) {
-    launch_bounds_refresh(m->v, 1, 0, 0, num_sms(), s);
-    CK_LAUNCH("bounds");
-  }
   if (!m->err_pending) {
     CK(cudaMemcpyAsync(m->err_host, m->v.counters + C_ERR, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(m->err_event, s));
@@ -509,7 +509,7 @@ dtsdf_status dtsdf_map_import(dtsdf_map m, const int32_t* coords, const float* v
   if (e == cudaSuccess && m->p.dense_dim <= 0) e = cudaMemsetAsync(m->v.counters + C_WORK, 0, sizeof(uint32_t), s);
   if (e == cudaSuccess) {
     launch_import(m->v, dc, dv, n, m->p.dense_dim <= 0, num_sms(), s);
-    launch_bounds_refresh(m->v, 0, 0, m->v.pool_cap, num_sms(), s);
+    launch_apron_refresh_all(m->v, num_sms(), s);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

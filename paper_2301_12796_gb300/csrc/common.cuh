@@ -17,6 +17,15 @@ namespace dtsdf {
 
 constexpr int ND = 6;          // directions X+, X-, Y+, Y-, Z+, Z- (Sec. 3)
 constexpr int BVOX = 512;      // voxels per 8^3 block (Sec. 7)
+// Geometry bricks are stored padded: the 8^3 voxels of the block plus an apron that
+// copies the neighbouring blocks' voxels at local coordinates -1 and 8, 9 on every axis,
+// so every voxel that a sample with its base voxel in the block reads (8 trilinear
+// corners, and the 24 further taps of the central differences at +-h) sits in one brick.
+constexpr int PAD = 11;                 // padded edge: local coordinates -1 .. 9
+constexpr int PVOX = PAD * PAD * PAD;   // 1331 voxels per padded geometry brick
+__host__ __device__ __forceinline__ int pad_index(int x, int y, int z) {
+  return ((z + 1) * PAD + (y + 1)) * PAD + (x + 1);
+}
 constexpr unsigned long long EMPTY_KEY = ~0ull;
 constexpr int MAX_PROBE = 256;  // linear-probe bound; the table is kept at most half full
 constexpr int SLOT_MASK = 6;    // dir_slots[d * 8 + 6]: bitmask of allocated directions
@@ -127,12 +136,14 @@ struct MapView {
   int32_t* dir_coord;  // 4 ints per entry: bx, by, bz, 0
   uint32_t dir_cap;
   // brick pool
-  float2* geom;     // FP32: (sdf, weight) per voxel
-  uint32_t* geom16; // FP16: half sdf | half weight (as u16) per voxel
-  float4* col;      // FP32: (r, g, b, colour weight)
-  uint32_t* col8;   // FP16 storage: u8 r, g, b and the 8-bit log colour-weight code
+  float2* geom;     // FP32: (sdf, weight) per voxel, PVOX per brick (padded, see pad_index)
+  uint32_t* geom16; // FP16: half sdf | half weight (as u16) per voxel, PVOX per brick
+  float4* col;      // FP32: (r, g, b, colour weight), BVOX per brick (unpadded)
+  uint32_t* col8;   // FP16 storage: u8 r, g, b and the 8-bit log colour-weight code, BVOX per brick
   int32_t* brick_dir;  // per brick: dir index * 8 + D
-  float* bound;        // per brick: lower bound of sdf over its voxels and its +1 apron with weight > 0
+  float* bound;        // per brick: minimum sdf over local voxels [0, 8]^3 with weight > 0 (+inf if none)
+  uint32_t* stamp;     // per brick: last frame whose fusion or allocation changed its voxels
+  uint32_t frame;      // id of the frame being fused
   uint32_t* occ;       // occupancy filters: 2 x OCC_WORDS words (blocks, then 4^3-block super-cells)
   uint32_t pool_cap;
   uint32_t* counters;

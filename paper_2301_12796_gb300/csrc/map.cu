@@ -7,10 +7,15 @@
 //   dir_slots   8 int32 per block coordinate: brick index of each of the 6 directions
 //               (-1 absent) and the bitmask of allocated directions; one probe of the
 //               hash yields all six directions, which is what the ray marcher needs
-//   geom        one 512-voxel brick per (block, direction): float2 (sdf, weight), x fastest
-//   col         matching float4 (r, g, b, colour weight) bricks when colour is enabled
+//   geom        one padded brick per (block, direction): float2 (sdf, weight), x fastest, the
+//               8^3 voxels of the block plus an apron (local coordinates -1, 8, 9) that
+//               mirrors the neighbouring blocks and is refreshed after every fusion
+//   col         matching unpadded float4 (r, g, b, colour weight) 8^3 bricks when colour is enabled
+//   bound       per brick: minimum sdf of the weighted voxels at local coordinates [0, 8]^3
+//               (the trilinear corners of every sample whose base voxel is in the block)
 // The voxel (i, j, k) of block b sits at origin + (8 b + (i, j, k)) h.
 #include <math.h>
+#include <string.h>
 
 #include "internal.h"
 
@@ -216,6 +221,7 @@ __global__ void k_alloc_assign(MapView m) {
       m.brick_dir[s] = d * 8 + D;
       // a new brick's apron may already hold data: no bound until it is recomputed
       m.bound[s] = -INFINITY;
+      m.stamp[s] = m.frame;
       slots[D] = (int32_t)s;
       have |= 1u << D;
     }
@@ -252,15 +258,16 @@ __global__ void k_dense_fill(MapView m, int nb) {
   m.dir_slots[(size_t)idx * 8 + 7] = 0;
 }
 
+// Every voxel starts at sdf 1, weight 0 (geometry including the aprons), colour 0.
 __global__ void k_pool_init(MapView m, int with_color) {
-  const size_t n = (size_t)m.pool_cap * BVOX;
+  const size_t n = (size_t)m.pool_cap * PVOX;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     if (m.storage == DTSDF_STORE_FP16)
       m.geom16[i] = pack_geom16(1.0f, 0.0f);
     else
       m.geom[i] = make_float2(1.0f, 0.0f);
     if (i < m.pool_cap) m.bound[i] = INFINITY;
-    if (with_color) {
+    if (with_color && i < (size_t)m.pool_cap * BVOX) {
       if (m.storage == DTSDF_STORE_FP16)
         m.col8[i] = 0u;
       else
@@ -300,89 +307,41 @@ __device__ __forceinline__ void store_geom(const MapView& m, size_t i, float sdf
     m.geom[i] = make_float2(sdf, w);
 }
 
+// Conservative frustum test of block (bx, by, bz): its bounding sphere, grown by `margin`,
+// reaches the camera's half-space z > 0 and the four side planes.
+__device__ __forceinline__ bool block_visible(const MapView& m, const FuseFrame& f, int bx, int by, int bz,
+                                              float margin) {
+  const float h = m.h;
+  const float r = 0.8660254f * 8.0f * h + h + margin;
+  const float cw0 = m.ox + (8.0f * bx + 3.5f) * h - f.T.t[0];
+  const float cw1 = m.oy + (8.0f * by + 3.5f) * h - f.T.t[1];
+  const float cw2 = m.oz + (8.0f * bz + 3.5f) * h - f.T.t[2];
+  const float cz = f.T.R[2] * cw0 + f.T.R[5] * cw1 + f.T.R[8] * cw2;
+  if (cz <= -r) return false;
+  const float cx = f.T.R[0] * cw0 + f.T.R[3] * cw1 + f.T.R[6] * cw2;
+  const float cy = f.T.R[1] * cw0 + f.T.R[4] * cw1 + f.T.R[7] * cw2;
+  bool out = false;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) out |= (f.pl[q][0] * cx + f.pl[q][1] * cy + f.pl[q][2] * cz) < -r;
+  return !out;
+}
+
 // One CTA per brick at a time (grid-stride over the pool): cull the block against the
 // frustum, then every voxel is projected to its nearest pixel and updated with the
 // weighted running average (Sec. 3). A voxel has one writer, so fusion is deterministic.
-// Lower bounds of updated voxel values, per brick and per apron category: a voxel with
-// i == 0 (resp. j, k) also lies in the +1 apron of the brick at bx - 1 (by - 1, bz - 1).
-struct BoundAcc {
-  float v[8];  // own, x, y, z, xy, xz, yz, xyz
-  __device__ __forceinline__ void reset() {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = INFINITY;
-  }
-  __device__ __forceinline__ void note(int i, int j, int k, float sdf) {
-    v[0] = fminf(v[0], sdf);
-    if (i == 0) v[1] = fminf(v[1], sdf);
-    if (j == 0) v[2] = fminf(v[2], sdf);
-    if (k == 0) v[3] = fminf(v[3], sdf);
-    if (i == 0 && j == 0) v[4] = fminf(v[4], sdf);
-    if (i == 0 && k == 0) v[5] = fminf(v[5], sdf);
-    if (j == 0 && k == 0) v[6] = fminf(v[6], sdf);
-    if (i == 0 && j == 0 && k == 0) v[7] = fminf(v[7], sdf);
-  }
-};
-
-// Fold a CTA's bound accumulators into the brick bounds (own brick and the up-to-7 bricks
-// whose apron contains updated voxels of this brick).
-__device__ void publish_bounds(const MapView& m, BoundAcc& acc, int b, int bx, int by, int bz, int D) {
-  __shared__ float s_min[8][8];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    float x = acc.v[q];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
-    if (lane == 0) s_min[warp][q] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x < 8) {
-    const int q = threadIdx.x;
-    float x = INFINITY;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x = fminf(x, s_min[w][q]);
-    if (x < INFINITY) {
-      if (q == 0) {
-        atomic_min_float(m.bound + b, x);
-      } else {
-        const int dx = (q == 1 || q == 4 || q == 5 || q == 7) ? -1 : 0;
-        const int dy = (q == 2 || q == 4 || q == 6 || q == 7) ? -1 : 0;
-        const int dz = (q == 3 || q == 5 || q == 6 || q == 7) ? -1 : 0;
-        const int d = hash_find(m, bx + dx, by + dy, bz + dz);
-        const int slot = d >= 0 ? m.dir_slots[(size_t)d * 8 + D] : -1;
-        if (slot >= 0) atomic_min_float(m.bound + slot, x);
-      }
-    }
-  }
-  __syncthreads();
-}
-
+// A brick with an updated voxel is stamped with the frame id for the apron refresh.
 template <int STORE>
 __global__ void __launch_bounds__(256) k_fuse(MapView m, FuseFrame f) {
   const uint32_t nb = min(*((volatile uint32_t*)(m.counters + C_POOL)), m.pool_cap);
   if (f.Tdev) f.T = pose_from_device(f.Tdev);
-  BoundAcc bacc;
   const float h = m.h;
-  const float half_diag = 0.8660254f * 8.0f * h + h;
   for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
     const int bd = __ldg(m.brick_dir + b);
     const int d = bd >> 3, D = bd & 7;
     const int bx = __ldg(m.dir_coord + 4 * d), by = __ldg(m.dir_coord + 4 * d + 1),
               bz = __ldg(m.dir_coord + 4 * d + 2);
-    // block centre in the camera frame, bounding-sphere frustum test
-    {
-      const float cw0 = m.ox + (8.0f * bx + 3.5f) * h - f.T.t[0];
-      const float cw1 = m.oy + (8.0f * by + 3.5f) * h - f.T.t[1];
-      const float cw2 = m.oz + (8.0f * bz + 3.5f) * h - f.T.t[2];
-      const float cz = f.T.R[2] * cw0 + f.T.R[5] * cw1 + f.T.R[8] * cw2;
-      if (cz <= -half_diag) continue;
-      const float cx = f.T.R[0] * cw0 + f.T.R[3] * cw1 + f.T.R[6] * cw2;
-      const float cy = f.T.R[1] * cw0 + f.T.R[4] * cw1 + f.T.R[7] * cw2;
-      bool out = false;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) out |= (f.pl[q][0] * cx + f.pl[q][1] * cy + f.pl[q][2] * cz) < -half_diag;
-      if (out) continue;
-    }
-    bacc.reset();
+    if (!block_visible(m, f, bx, by, bz, 0.0f)) continue;
+    bool updated = false;
     for (int vi = threadIdx.x; vi < BVOX; vi += blockDim.x) {
       const int i = vi & 7, j = (vi >> 3) & 7, k = vi >> 6;
       // single-precision decision path: voxel centre, camera frame, projection
@@ -404,7 +363,8 @@ __global__ void __launch_bounds__(256) k_fuse(MapView m, FuseFrame f) {
       const float e0 = rsub(xc0, P.x), e1 = rsub(xc1, P.y), e2 = rsub(xc2, P.z);
       const float draw = rdot3(e0, e1, e2, n.x, n.y, n.z);
       if (draw < -m.tau) continue;
-      const size_t gi = (size_t)b * BVOX + vi;
+      const size_t gi = (size_t)b * PVOX + pad_index(i, j, k);  // geometry (padded brick)
+      const size_t ci = (size_t)b * BVOX + vi;                  // colour
       if (draw > m.tau) {
         // free-space carving, unless a depth jump > tau lies within the carving radius
         bool jump = false;
@@ -424,7 +384,7 @@ __global__ void __launch_bounds__(256) k_fuse(MapView m, FuseFrame f) {
         const float wn = g.y + m.wcarve;
         const float nsdf = (g.y * g.x + m.wcarve) / wn;
         store_geom<STORE>(m, gi, nsdf, fminf(wn, m.wmax));
-        bacc.note(i, j, k, STORE == DTSDF_STORE_FP16 ? unpack_geom16(pack_geom16(nsdf, 0.f)).x : nsdf);
+        updated = true;
         continue;
       }
       // membership of the pixel normal in direction D, and a camera-facing normal
@@ -446,7 +406,7 @@ __global__ void __launch_bounds__(256) k_fuse(MapView m, FuseFrame f) {
       const float wn = g.y + w_d;
       const float nsdf = (g.y * g.x + w_d * sd) / wn;
       store_geom<STORE>(m, gi, nsdf, fminf(wn, m.wmax));
-      bacc.note(i, j, k, STORE == DTSDF_STORE_FP16 ? unpack_geom16(pack_geom16(nsdf, 0.f)).x : nsdf);
+      updated = true;
       if (m.color && f.rgb) {
         const float dist = rsqrt_exact(rdot3(e0, e1, e2, e0, e1, e2));
         if (dist < m.tau) {
@@ -454,60 +414,77 @@ __global__ void __launch_bounds__(256) k_fuse(MapView m, FuseFrame f) {
           if (!(w_c > 1e-12f)) w_c = 1e-12f;
           const uint8_t* c = f.rgb + 3 * pi;
           if (STORE == DTSDF_STORE_FP16) {
-            const float4 cv = unpack_col8(m.col8[gi]);
+            const float4 cv = unpack_col8(m.col8[ci]);
             const float wcn = cv.w + w_c;
-            m.col8[gi] = pack_col8((cv.w * cv.x + w_c * c[0]) / wcn, (cv.w * cv.y + w_c * c[1]) / wcn,
+            m.col8[ci] = pack_col8((cv.w * cv.x + w_c * c[0]) / wcn, (cv.w * cv.y + w_c * c[1]) / wcn,
                                    (cv.w * cv.z + w_c * c[2]) / wcn, fminf(wcn, m.wmax));
           } else {
-            float4 cv = m.col[gi];
+            float4 cv = m.col[ci];
             const float wcn = cv.w + w_c;
             cv.x = (cv.w * cv.x + w_c * c[0]) / wcn;
             cv.y = (cv.w * cv.y + w_c * c[1]) / wcn;
             cv.z = (cv.w * cv.z + w_c * c[2]) / wcn;
             cv.w = fminf(wcn, m.wmax);
-            m.col[gi] = cv;
+            m.col[ci] = cv;
           }
         }
       }
     }
-    publish_bounds(m, bacc, (int)b, bx, by, bz, D);
+    if (__syncthreads_or(updated) && threadIdx.x == 0) m.stamp[b] = m.frame;
   }
 }
 
-// Exact bound of bricks [begin, end): minimum sdf over the brick and its +1 apron among
-// voxels with weight > 0 (+inf if none). Used for new bricks after fusion and after import.
+// Apron refresh and exact bound. A brick whose 3x3x3 neighbourhood of blocks holds a brick
+// stamped with this frame (every brick when `all`) copies its neighbours' voxels at local
+// coordinates -1, 8 and 9 into its apron (an unallocated neighbour reads as sdf 1, weight 0,
+// the initial value, so it stays absent for presence tests) and recomputes its bound over
+// [0, 8]^3. Reads touch only cores and writes only aprons, so bricks refresh concurrently.
 template <int STORE>
-__global__ void k_bounds_refresh(MapView m, int from_counter, uint32_t begin_arg, uint32_t end_arg) {
-  __shared__ int s_slot[8];
+__global__ void __launch_bounds__(256) k_apron_refresh(MapView m, FuseFrame f, int all) {
+  __shared__ int s_nb[27];
   __shared__ float s_red[8];
-  const uint32_t count = min(*((volatile uint32_t*)(m.counters + C_POOL)), m.pool_cap);
-  uint32_t begin = begin_arg, end = min(end_arg, count);
-  if (from_counter) {
-    begin = *((volatile uint32_t*)(m.counters + C_POOL_BEFORE));
-    end = count;
-  }
-  for (uint32_t b = begin + blockIdx.x; b < end; b += gridDim.x) {
+  const uint32_t nb = min(*((volatile uint32_t*)(m.counters + C_POOL)), m.pool_cap);
+  if (!all && f.Tdev) f.T = pose_from_device(f.Tdev);
+  // neighbours of a block visible to the fusion lie within one block diagonal of it; new
+  // bricks lie within tau of a back-projected pixel
+  const float margin = 8.0f * 1.7320508f * m.h + m.tau;
+  for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
     const int bd = m.brick_dir[b];
     const int d = bd >> 3, D = bd & 7;
     const int bx = m.dir_coord[4 * d], by = m.dir_coord[4 * d + 1], bz = m.dir_coord[4 * d + 2];
-    if (threadIdx.x < 8) {
+    if (!all && !block_visible(m, f, bx, by, bz, margin)) continue;
+    bool changed = false;
+    if (threadIdx.x < 27) {
       const int q = threadIdx.x;
-      if (q == 0) {
-        s_slot[0] = (int)b;
-      } else {
-        const int dd = hash_find(m, bx + (q & 1), by + ((q >> 1) & 1), bz + ((q >> 2) & 1));
-        s_slot[q] = dd >= 0 ? m.dir_slots[(size_t)dd * 8 + D] : -1;
+      int sl = (int)b;
+      if (q != 13) {
+        const int dd = hash_find(m, bx + q % 3 - 1, by + (q / 3) % 3 - 1, bz + q / 9 - 1);
+        sl = dd >= 0 ? m.dir_slots[(size_t)dd * 8 + D] : -1;
       }
+      s_nb[q] = sl;
+      changed = sl >= 0 && m.stamp[sl] == m.frame;
     }
-    __syncthreads();
+    if (!__syncthreads_or(changed || all)) continue;
     float mn = INFINITY;
-    for (int vi = threadIdx.x; vi < 729; vi += blockDim.x) {
-      const int x = vi % 9, y = (vi / 9) % 9, z = vi / 81;
-      const int q = (x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2);
-      const int slot = s_slot[q];
-      if (slot < 0) continue;
-      const float2 g = load_geom<STORE>(m, (size_t)slot * BVOX + ((z & 7) * 8 + (y & 7)) * 8 + (x & 7));
-      if (g.y > 0.0f) mn = fminf(mn, g.x);
+    const size_t base = (size_t)b * PVOX;
+    for (int vi = threadIdx.x; vi < PVOX; vi += blockDim.x) {
+      const int x = vi % PAD - 1, y = (vi / PAD) % PAD - 1, z = vi / (PAD * PAD) - 1;
+      float2 g;
+      if ((unsigned)x < 8u && (unsigned)y < 8u && (unsigned)z < 8u) {
+        g = load_geom<STORE>(m, base + vi);
+      } else {
+        const int sl = s_nb[((z >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((x >> 3) + 1)];
+        const size_t src = (size_t)sl * PVOX + pad_index(x & 7, y & 7, z & 7);
+        if (STORE == DTSDF_STORE_FP16) {
+          const uint32_t raw = sl >= 0 ? m.geom16[src] : pack_geom16(1.0f, 0.0f);
+          m.geom16[base + vi] = raw;
+          g = unpack_geom16(raw);
+        } else {
+          g = sl >= 0 ? m.geom[src] : make_float2(1.0f, 0.0f);
+          m.geom[base + vi] = g;
+        }
+      }
+      if (x <= 8 && y <= 8 && z <= 8 && x >= 0 && y >= 0 && z >= 0 && g.y > 0.0f) mn = fminf(mn, g.x);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
@@ -520,14 +497,6 @@ __global__ void k_bounds_refresh(MapView m, int from_counter, uint32_t begin_arg
     }
     __syncthreads();
   }
-}
-
-void launch_bounds_refresh(const MapView& m, int from_counter, uint32_t begin, uint32_t end, int num_sms,
-                           cudaStream_t s) {
-  if (m.storage == DTSDF_STORE_FP16)
-    k_bounds_refresh<DTSDF_STORE_FP16><<<num_sms * 4, 256, 0, s>>>(m, from_counter, begin, end);
-  else
-    k_bounds_refresh<DTSDF_STORE_FP32><<<num_sms * 4, 256, 0, s>>>(m, from_counter, begin, end);
 }
 
 // ------------------------------------------------------------------ import
@@ -552,16 +521,17 @@ __global__ void k_import_write(MapView m, const int32_t* __restrict__ coords, co
     if (slot < 0) continue;
     for (int vi = threadIdx.x; vi < BVOX; vi += blockDim.x) {
       const float* in = vox + ((size_t)b * BVOX + vi) * 6;
-      const size_t gi = (size_t)slot * BVOX + vi;
+      const size_t gi = (size_t)slot * PVOX + pad_index(vi & 7, (vi >> 3) & 7, vi >> 6);
+      const size_t ci = (size_t)slot * BVOX + vi;
       if (m.storage == DTSDF_STORE_FP16)
         m.geom16[gi] = pack_geom16(in[0], in[1]);
       else
         m.geom[gi] = make_float2(in[0], in[1]);
       if (m.color) {
         if (m.storage == DTSDF_STORE_FP16) {
-          m.col8[gi] = pack_col8(in[2], in[3], in[4], in[5]);
+          m.col8[ci] = pack_col8(in[2], in[3], in[4], in[5]);
         } else {
-          m.col[gi] = make_float4(in[2], in[3], in[4], in[5]);
+          m.col[ci] = make_float4(in[2], in[3], in[4], in[5]);
         }
       }
     }
@@ -612,20 +582,21 @@ __global__ void k_export(MapView m, int64_t cap, int32_t* coords, float* vox) {
     if (threadIdx.x < 4)
       coords[4 * (size_t)b + threadIdx.x] = threadIdx.x < 3 ? m.dir_coord[4 * d + threadIdx.x] : (bd & 7);
     for (int vi = threadIdx.x; vi < BVOX; vi += blockDim.x) {
-      const size_t gi = (size_t)b * BVOX + vi;
-      float* o = vox + gi * 6;
+      const size_t ci = (size_t)b * BVOX + vi;
+      const size_t gi = (size_t)b * PVOX + pad_index(vi & 7, (vi >> 3) & 7, vi >> 6);
+      float* o = vox + ci * 6;
       float2 g = (m.storage == DTSDF_STORE_FP16) ? unpack_geom16(m.geom16[gi]) : m.geom[gi];
       o[0] = g.x;
       o[1] = g.y;
       if (m.color) {
         if (m.storage == DTSDF_STORE_FP16) {
-          const float4 c = unpack_col8(m.col8[gi]);
+          const float4 c = unpack_col8(m.col8[ci]);
           o[2] = c.x;
           o[3] = c.y;
           o[4] = c.z;
           o[5] = c.w;
         } else {
-          const float4 c = m.col[gi];
+          const float4 c = m.col[ci];
           o[2] = c.x;
           o[3] = c.y;
           o[4] = c.z;
@@ -681,10 +652,22 @@ void launch_fuse(const MapView& m, const Intr& K, const Pose32& T, const double*
   set(1, -K.fx, 0.f, (float)K.W - 0.5f - K.cx);
   set(2, 0.f, K.fy, K.cy + 0.5f);
   set(3, 0.f, -K.fy, (float)K.H - 0.5f - K.cy);
-  if (m.storage == DTSDF_STORE_FP16)
+  if (m.storage == DTSDF_STORE_FP16) {
     k_fuse<DTSDF_STORE_FP16><<<num_sms * 8, 256, 0, s>>>(m, f);
-  else
+    k_apron_refresh<DTSDF_STORE_FP16><<<num_sms * 8, 256, 0, s>>>(m, f, 0);
+  } else {
     k_fuse<DTSDF_STORE_FP32><<<num_sms * 8, 256, 0, s>>>(m, f);
+    k_apron_refresh<DTSDF_STORE_FP32><<<num_sms * 8, 256, 0, s>>>(m, f, 0);
+  }
+}
+
+void launch_apron_refresh_all(const MapView& m, int num_sms, cudaStream_t s) {
+  FuseFrame f;
+  memset(&f, 0, sizeof(f));
+  if (m.storage == DTSDF_STORE_FP16)
+    k_apron_refresh<DTSDF_STORE_FP16><<<num_sms * 8, 256, 0, s>>>(m, f, 1);
+  else
+    k_apron_refresh<DTSDF_STORE_FP32><<<num_sms * 8, 256, 0, s>>>(m, f, 1);
 }
 
 void launch_import(const MapView& m, const int32_t* coords, const float* vox, int64_t n, bool allocate, int num_sms,

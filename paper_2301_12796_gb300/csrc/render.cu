@@ -4,7 +4,9 @@
 // samples t_k = k h/2 from z_min to z_max (Sec. 4: regular probing until the SDF turns
 // negative, then small SDF-sized steps). Per block cell the hash is probed once; the
 // directory entry gives the bricks of all six directions, and cells with no allocated
-// direction are skipped whole (no sample in them can be defined). At a sample, the
+// direction are skipped whole (no sample in them can be defined). Geometry bricks are
+// padded with an apron that mirrors the neighbouring blocks, so every voxel a sample in the
+// cell reads (trilinear corners and gradient taps) is at a fixed offset from one index. At a sample, the
 // combined SDF Phi of Eq. combine_weight is a convex combination of the present
 // directions' trilinear values Phi^D, so its sign follows from min/max of those alone
 // whenever they agree (8 voxel reads per direction); the full combination with
@@ -37,182 +39,90 @@ __device__ __noinline__ uint32_t probe_block(const unsigned long long* __restric
   return VAL_EMPTY;
 }
 
-// Per-thread state of the block cell the ray is in, kept in registers. Shared memory
-// (strided by RT_N so a warp's accesses hit distinct banks) holds the directory indices of
-// the 27 surrounding blocks and, for the directions active in the cell, the brick slots of
-// the 2x2x2 blocks cell + {0,1}^3 that trilinear corners of samples in the cell can touch.
-// Both are filled lazily; `probed` / `filled` record which entries are valid.
+// Per-thread state of the block cell the ray is in. The brick slots of the directions
+// allocated in the cell are kept in shared memory (strided by RT_N so a warp's accesses hit
+// distinct banks); every voxel that a sample in the cell reads lies in those padded bricks.
 struct Cell {
-  int* dirc;        // 27 directory indices
-  int* slot;        // 6 x 8 brick slots: slot[(D * 8 + j) * RT_N]
+  int* slot;        // 6 brick slots: slot[D * RT_N], valid for the allocated directions
   int cx, cy, cz;
-  uint32_t probed;  // bit j27: dirc[j27] valid
-  uint32_t filled;  // bit j8: slot row j8 valid for every direction in cmask
-  uint32_t cmask;   // directions allocated in the cell that hold weighted voxels near it
-  bool positive;    // every active direction's brick bound (brick + apron) is > 0
+  uint32_t cmask;   // directions allocated in the cell with weighted voxels among [0, 8]^3
+  bool positive;    // every active direction's brick bound is > 0
   bool jumped;      // the march already jumped over this cell's positive samples
 };
-
-__device__ __forceinline__ int cell_dir(const MapView& m, Cell& c, int dx, int dy, int dz) {
-  if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1)
-    return val_dir(probe_block(m.keys, m.vals, m.hmask, c.cx + dx, c.cy + dy, c.cz + dz));
-  const int j = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
-  if (!((c.probed >> j) & 1u)) {
-    c.dirc[j * RT_N] = val_dir(probe_block(m.keys, m.vals, m.hmask, c.cx + dx, c.cy + dy, c.cz + dz));
-    c.probed |= 1u << j;
-  }
-  return c.dirc[j * RT_N];
-}
 
 __device__ __forceinline__ void cell_enter(const MapView& m, Cell& c, int x, int y, int z) {
   c.cx = x;
   c.cy = y;
   c.cz = z;
-  c.probed = 1u << 13;
-  c.filled = 0;
   c.jumped = false;
   const uint32_t v = probe_block(m.keys, m.vals, m.hmask, x, y, z);
   const int d0 = val_dir(v);
-  c.dirc[13 * RT_N] = d0;
   uint32_t active = 0;
   bool positive = true;
 #pragma unroll 1
   for (uint32_t mm = val_mask(v); mm; mm &= mm - 1) {
     const int E = __ffs(mm) - 1;
     const int sl = __ldg(m.dir_slots + (size_t)d0 * 8 + E);
-    c.slot[(E * 8) * RT_N] = sl;
+    c.slot[E * RT_N] = sl;
     const float lb = sl >= 0 ? __ldg(m.bound + sl) : INFINITY;
-    // a bound of +inf: no voxel with weight in brick + apron, the direction is never present here
+    // a bound of +inf: no weighted voxel among the corners, the direction is never present here
     if (lb < INFINITY) active |= 1u << E;
     positive &= lb > 0.0f;
   }
   c.cmask = active;
   c.positive = positive;
-  c.filled = active ? 1u : 0u;
-}
-
-// Fill slot row j8 (block cell + (j8 & 1, j8 >> 1 & 1, j8 >> 2)) for the directions in cmask,
-// probing the block's directory entry if it is not known yet; returns the updated probed mask.
-// Out of line with explicit arguments, so the callers' cell state stays in registers.
-__device__ __noinline__ uint32_t fill_slot_row(const unsigned long long* __restrict__ keys,
-                                               const uint32_t* __restrict__ vals, uint32_t hmask,
-                                               const int32_t* __restrict__ dir_slots, int* dirc, int* slot, int cx,
-                                               int cy, int cz, uint32_t cmask, uint32_t probed, int j8) {
-  const int dx = j8 & 1, dy = (j8 >> 1) & 1, dz = j8 >> 2;
-  const int j = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
-  if (!((probed >> j) & 1u)) {
-    dirc[j * RT_N] = val_dir(probe_block(keys, vals, hmask, cx + dx, cy + dy, cz + dz));
-    probed |= 1u << j;
-  }
-  const int d = dirc[j * RT_N];
-  for (uint32_t mm = cmask; mm; mm &= mm - 1) {
-    const int E = __ffs(mm) - 1;
-    slot[(E * 8 + j8) * RT_N] = d >= 0 ? __ldg(dir_slots + (size_t)d * 8 + E) : -1;
-  }
-  return probed;
-}
-
-// brick of direction D (active in the cell) in block cell + (j8 & 1, j8 >> 1 & 1, j8 >> 2)
-__device__ __forceinline__ int slot_plus(const MapView& m, Cell& c, int D, int j8) {
-  if (!((c.filled >> j8) & 1u)) {
-    c.probed = fill_slot_row(m.keys, m.vals, m.hmask, m.dir_slots, c.dirc, c.slot, c.cx, c.cy, c.cz, c.cmask, c.probed,
-                             j8);
-    c.filled |= 1u << j8;
-  }
-  return c.slot[(D * 8 + j8) * RT_N];
-}
-
-// Brick slot of direction D for voxel (gx, gy, gz) anywhere in the 27-block neighbourhood.
-__device__ __forceinline__ int slot_of(const MapView& m, Cell& c, int D, int gx, int gy, int gz) {
-  const int bx = (gx >> 3) - c.cx, by = (gy >> 3) - c.cy, bz = (gz >> 3) - c.cz;
-  if ((bx | by | bz) >= 0 && bx <= 1 && by <= 1 && bz <= 1) return slot_plus(m, c, D, bx | (by << 1) | (bz << 2));
-  const int d = cell_dir(m, c, bx, by, bz);
-  return d >= 0 ? __ldg(m.dir_slots + (size_t)d * 8 + D) : -1;
 }
 
 // COUNT: instrumentation build of the marcher that flags every brick it reads
 // (touched[brick] for geometry, touched[pool_cap + brick] for colour); off in normal use.
 template <int STORE, bool COUNT>
 __device__ __forceinline__ float2 ld_geom(const MapView& m, size_t i, uint8_t* touched) {
-  if (COUNT) touched[i >> 9] = 1;
+  if (COUNT) touched[i / PVOX] = 1;
   if (STORE == DTSDF_STORE_FP16) return unpack_geom16(__ldg(m.geom16 + i));
   return __ldg(m.geom + i);
 }
 
-// Trilinear weight of corner q = (q&1, q>>1&1, q>>2&1) (colour interpolation).
+// Offset of trilinear corner q = (q&1, q>>1&1, q>>2&1) in a padded brick.
+__host__ __device__ __forceinline__ constexpr int coff(int q) {
+  return (q & 1) + PAD * ((q >> 1) & 1) + PAD * PAD * (q >> 2);
+}
+
+// Trilinear weight of corner q (colour interpolation).
 __device__ __forceinline__ float corner_w(int q, float fx, float fy, float fz) {
   return ((q & 1) ? fx : 1.0f - fx) * ((q & 2) ? fy : 1.0f - fy) * ((q & 4) ? fz : 1.0f - fz);
 }
 
-// Trilinear sdf and weight of direction D at base voxel g with fractions (fx, fy, fz);
-// false unless all 8 corners exist with weight > 0. Evaluated as nested linear
-// interpolations (x, then y, then z) with explicit fused multiply-adds, identically on both
-// paths below, so a constant field interpolates to exactly its value: the central
+// Trilinear interpolation as nested linear interpolations (x, then y, then z) with explicit
+// fused multiply-adds, so a constant field interpolates to exactly its value: the central
 // differences of a flat (truncated) region are exactly zero, as in the double-precision
 // definition, instead of a rounding residue that would pass the gradient test.
 __device__ __forceinline__ float lerp_rn(float a, float b, float t) { return __fmaf_rn(t, b - a, a); }
 
+__device__ __forceinline__ float tri(const float* v, float fx, float fy, float fz) {
+  const float s00 = lerp_rn(v[0], v[1], fx), s10 = lerp_rn(v[2], v[3], fx);
+  const float s01 = lerp_rn(v[4], v[5], fx), s11 = lerp_rn(v[6], v[7], fx);
+  return lerp_rn(lerp_rn(s00, s10, fy), lerp_rn(s01, s11, fy), fz);
+}
+
+// Trilinear sdf and weight of one direction at the sample whose base voxel has index `base`
+// in its padded brick; false unless all 8 corners have weight > 0.
 template <int STORE, bool COUNT>
-__device__ __forceinline__ bool interp(const MapView& m, Cell& c, int D, int g0, int g1, int g2, float fx, float fy,
-                                       float fz, float& phi, float& W, uint8_t* touched) {
-  const int l0 = g0 & 7, l1 = g1 & 7, l2 = g2 & 7;
-  if ((((g0 >> 3) - c.cx) | ((g1 >> 3) - c.cy) | ((g2 >> 3) - c.cz)) == 0) {
-    // base voxel in the cell (every sample of the march): the corners lie in the blocks
-    // cell + {0,1}^3 whose brick slots the cell table holds. All 8 indices are formed first
-    // and the 8 loads issued together, whether or not the corners straddle a brick face.
-    size_t idx[8];
+__device__ __forceinline__ bool interp(const MapView& m, size_t base, float fx, float fy, float fz, float& phi,
+                                       float& W, uint8_t* touched) {
+  float2 v[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int x = l0 + (q & 1), y = l1 + ((q >> 1) & 1), z = l2 + ((q >> 2) & 1);
-      const int sl = slot_plus(m, c, D, (x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2));
-      if (sl < 0) return false;
-      idx[q] = (size_t)sl * BVOX + ((z & 7) * 8 + (y & 7)) * 8 + (x & 7);
-    }
-    float2 v[8];
+  for (int q = 0; q < 8; ++q) v[q] = ld_geom<STORE, COUNT>(m, base + coff(q), touched);
+  bool ok = true;
+  float s[8], w[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = ld_geom<STORE, COUNT>(m, idx[q], touched);
-    bool ok = true;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) ok &= v[q].y > 0.0f;
-    const float s00 = lerp_rn(v[0].x, v[1].x, fx), s10 = lerp_rn(v[2].x, v[3].x, fx);
-    const float s01 = lerp_rn(v[4].x, v[5].x, fx), s11 = lerp_rn(v[6].x, v[7].x, fx);
-    const float w00 = lerp_rn(v[0].y, v[1].y, fx), w10 = lerp_rn(v[2].y, v[3].y, fx);
-    const float w01 = lerp_rn(v[4].y, v[5].y, fx), w11 = lerp_rn(v[6].y, v[7].y, fx);
-    phi = lerp_rn(lerp_rn(s00, s10, fy), lerp_rn(s01, s11, fy), fz);
-    W = lerp_rn(lerp_rn(w00, w10, fy), lerp_rn(w01, w11, fy), fz);
-    return ok;
-  }
-  // base voxel in a neighbouring block (the -h offsets of a gradient): corner by corner, the
-  // same nested interpolation carried in scalars through the loop
-  float sa = 0.f, wa = 0.f, sx0 = 0.f, wx0 = 0.f, sy0 = 0.f, wy0 = 0.f;
-#pragma unroll 1
   for (int q = 0; q < 8; ++q) {
-    const int x0 = g0 + (q & 1), x1 = g1 + ((q >> 1) & 1), x2 = g2 + ((q >> 2) & 1);
-    const int slot = slot_of(m, c, D, x0, x1, x2);
-    if (slot < 0) return false;
-    const float2 v = ld_geom<STORE, COUNT>(m, (size_t)slot * BVOX + ((x2 & 7) * 8 + (x1 & 7)) * 8 + (x0 & 7), touched);
-    if (!(v.y > 0.0f)) return false;
-    if (!(q & 1)) {
-      sa = v.x;
-      wa = v.y;
-      continue;
-    }
-    const float sx = lerp_rn(sa, v.x, fx), wx = lerp_rn(wa, v.y, fx);
-    if (!(q & 2)) {
-      sx0 = sx;
-      wx0 = wx;
-      continue;
-    }
-    const float sy = lerp_rn(sx0, sx, fy), wy = lerp_rn(wx0, wx, fy);
-    if (!(q & 4)) {
-      sy0 = sy;
-      wy0 = wy;
-      continue;
-    }
-    phi = lerp_rn(sy0, sy, fz);
-    W = lerp_rn(wy0, wy, fz);
+    ok &= v[q].y > 0.0f;
+    s[q] = v[q].x;
+    w[q] = v[q].y;
   }
-  return true;
+  phi = tri(s, fx, fy, fz);
+  W = tri(w, fx, fy, fz);
+  return ok;
 }
 
 __device__ __forceinline__ float w_dir_r(float c, float theta) {
@@ -229,7 +139,19 @@ struct Combined {
   float cw;      // sum of w_comb over directions with colour
 };
 
+// Colour brick of direction D holding voxel (gx, gy, gz): the cell's brick, else a hash probe
+// (colour bricks are unpadded and read only for the outputs).
+__device__ __forceinline__ int col_slot(const MapView& m, const Cell& c, int D, int gx, int gy, int gz) {
+  const int bx = gx >> 3, by = gy >> 3, bz = gz >> 3;
+  if (bx == c.cx && by == c.cy && bz == c.cz) return c.slot[D * RT_N];
+  const int d = val_dir(probe_block(m.keys, m.vals, m.hmask, bx, by, bz));
+  return d >= 0 ? __ldg(m.dir_slots + (size_t)d * 8 + D) : -1;
+}
+
 // Full combination of Eq. combine_weight at voxel coordinate g (fallback Eq. combine_tsdf_weight).
+// Per present direction: trilinear value and weight from the 8 corners, and the gradient as
+// the central differences (phi(+h) - phi(-h)) / 2h of the trilinear field along each axis,
+// whose further 24 taps (4 per side and axis) lie in the same padded brick.
 template <int STORE, bool COLOR, bool COUNT>
 __device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, const float g[3], const float r[3],
                                                  uint8_t* touched, bool want_color) {
@@ -243,48 +165,60 @@ __device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, cons
   const float f0 = floorf(g[0]), f1 = floorf(g[1]), f2 = floorf(g[2]);
   const int g0 = (int)f0, g1 = (int)f1, g2 = (int)f2;
   const float fx = g[0] - f0, fy = g[1] - f1, fz = g[2] - f2;
+  const int lofs = pad_index(g0 - 8 * c.cx, g1 - 8 * c.cy, g2 - 8 * c.cz);
   float acc = 0.f, facc = 0.f, fw = 0.f;
   bool any = false;
   const float inv2h = 0.5f / m.h;
 #pragma unroll 1
   for (uint32_t mm = c.cmask; mm; mm &= mm - 1) {
     const int D = __ffs(mm) - 1;
-    float phiD, WD;
-    if (!interp<STORE, COUNT>(m, c, D, g0, g1, g2, fx, fy, fz, phiD, WD, touched)) continue;
+    const size_t base = (size_t)c.slot[D * RT_N] * PVOX + lofs;
+    float2 cv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) cv[q] = ld_geom<STORE, COUNT>(m, base + coff(q), touched);
+    bool ok = true;
+    float s[8], w[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      ok &= cv[q].y > 0.0f;
+      s[q] = cv[q].x;
+      w[q] = cv[q].y;
+    }
+    if (!ok) continue;
+    const float phiD = tri(s, fx, fy, fz);
+    const float WD = tri(w, fx, fy, fz);
     any = true;
     // fallback weight W^D max(0, <v^D, -r>)
     const float vr = (D & 1) ? r[D >> 1] : -r[D >> 1];
     const float wf = WD * fmaxf(vr, 0.0f);
     fw += wf;
     facc += wf * phiD;
-    // central differences (phi(+h) - phi(-h)) / 2h of the trilinear field along each axis;
-    // exactly zero where the field is flat (a sum of +-phi/2h terms could leave a rounding
-    // residue that passes the gradient test)
-    float gx = 0.f, gy = 0.f, gz = 0.f, pplus = 0.f;
+    // axis a: the cube shifted by +h reuses the base cube's corners with bit a set, and its
+    // corners with bit a set lie one voxel beyond the base cube; the cube shifted by -h reuses
+    // the base corners without bit a, and its corners without bit a lie one voxel before it
     bool gok = true;
-#pragma unroll 1
-    for (int e = 0; e < 6; ++e) {
-      const int ax = e >> 1;
-      const int sgn = (e & 1) ? -1 : 1;
-      float pe, we;
-      if (!interp<STORE, COUNT>(m, c, D, g0 + (ax == 0 ? sgn : 0), g1 + (ax == 1 ? sgn : 0), g2 + (ax == 2 ? sgn : 0),
-                                fx, fy, fz, pe, we, touched)) {
-        gok = false;
-        break;
+    float gr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int S = a == 0 ? 1 : (a == 1 ? PAD : PAD * PAD);
+      const int bit = 1 << a;
+      float2 t[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        t[q] = ld_geom<STORE, COUNT>(m, (q & bit) ? base + S + coff(q) : base - S + coff(q), touched);
+      float vp[8], vn[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        gok &= t[q].y > 0.0f;
+        vp[q] = (q & bit) ? t[q].x : s[q | bit];
+        vn[q] = (q & bit) ? s[q & ~bit] : t[q].x;
       }
-      if (!(e & 1)) {
-        pplus = pe;
-        continue;
-      }
-      const float d = (pplus - pe) * inv2h;
-      gx = ax == 0 ? d : gx;
-      gy = ax == 1 ? d : gy;
-      gz = ax == 2 ? d : gz;
+      gr[a] = (tri(vp, fx, fy, fz) - tri(vn, fx, fy, fz)) * inv2h;
     }
     if (!gok) continue;
-    const float gn = sqrtf(gx * gx + gy * gy + gz * gz);
+    const float gn = sqrtf(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
     if (!(gn > 1e-12f)) continue;
-    const float n0 = gx / gn, n1 = gy / gn, n2 = gz / gn;
+    const float n0 = gr[0] / gn, n1 = gr[1] / gn, n2 = gr[2] / gn;
     const float cosv = (D == 0) ? n0 : (D == 1) ? -n0 : (D == 2) ? n1 : (D == 3) ? -n1 : (D == 4) ? n2 : -n2;
     const float facing = fmaxf(-(n0 * r[0] + n1 * r[1] + n2 * r[2]), 0.0f);
     const float wc = w_dir_r(cosv, m.theta) * facing * WD;
@@ -301,7 +235,7 @@ __device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, cons
 #pragma unroll 1
       for (int q = 0; q < 8; ++q) {
         const int x0 = g0 + (q & 1), x1 = g1 + ((q >> 1) & 1), x2 = g2 + ((q >> 2) & 1);
-        const int slot = slot_of(m, c, D, x0, x1, x2);
+        const int slot = col_slot(m, c, D, x0, x1, x2);
         if (slot < 0) {
           cok = false;
           break;
@@ -309,19 +243,11 @@ __device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, cons
         const size_t vi = (size_t)slot * BVOX + ((x2 & 7) * 8 + (x1 & 7)) * 8 + (x0 & 7);
         if (COUNT) touched[m.pool_cap + (vi >> 9)] = 1;
         const float wq = corner_w(q, fx, fy, fz);
-        if (STORE == DTSDF_STORE_FP16) {
-          const float4 cv = unpack_col8(__ldg(m.col8 + vi));
-          cr += wq * cv.x;
-          cg += wq * cv.y;
-          cb += wq * cv.z;
-          cwt += wq * cv.w;
-        } else {
-          const float4 cv = __ldg(m.col + vi);
-          cr += wq * cv.x;
-          cg += wq * cv.y;
-          cb += wq * cv.z;
-          cwt += wq * cv.w;
-        }
+        const float4 cv4 = STORE == DTSDF_STORE_FP16 ? unpack_col8(__ldg(m.col8 + vi)) : __ldg(m.col + vi);
+        cr += wq * cv4.x;
+        cg += wq * cv4.y;
+        cb += wq * cv4.z;
+        cwt += wq * cv4.w;
       }
       if (cok && cwt > 0.0f) {
         out.cw += wc;
@@ -350,13 +276,14 @@ __device__ __forceinline__ int sign_fast(const MapView& m, Cell& c, const float 
   const float f0 = floorf(g[0]), f1 = floorf(g[1]), f2 = floorf(g[2]);
   const int g0 = (int)f0, g1 = (int)f1, g2 = (int)f2;
   const float fx = g[0] - f0, fy = g[1] - f1, fz = g[2] - f2;
+  const int lofs = pad_index(g0 - 8 * c.cx, g1 - 8 * c.cy, g2 - 8 * c.cz);
   float mn = 2.f, mx = -2.f;
   bool any = false, facing = false;
 #pragma unroll 1
   for (uint32_t mm = c.cmask; mm; mm &= mm - 1) {
     const int D = __ffs(mm) - 1;
     float phiD, WD;
-    if (!interp<STORE, COUNT>(m, c, D, g0, g1, g2, fx, fy, fz, phiD, WD, touched)) continue;
+    if (!interp<STORE, COUNT>(m, (size_t)c.slot[D * RT_N] * PVOX + lofs, fx, fy, fz, phiD, WD, touched)) continue;
     any = true;
     mn = fminf(mn, phiD);
     mx = fmaxf(mx, phiD);
@@ -383,8 +310,7 @@ enum { S_MARCH = 0, S_SCAN = 1, S_ENDS_A = 2, S_ENDS_B = 3, S_OUT = 4, S_DONE = 
 
 template <int STORE, bool COLOR, bool COUNT, int NJ>
 __global__ void __launch_bounds__(RT_N, 4) k_render(MapView m, RenderBatch<NJ> a) {
-  __shared__ int s_dirc[27 * RT_N];
-  __shared__ int s_slot[ND * 8 * RT_N];
+  __shared__ int s_slot[ND * RT_N];
   __shared__ Pose32 s_pose[NJ];
   uint8_t* touched = a.touched;
   // COUNT build: per-ray event counts (samples, full combinations, cells, allocated cells, hits, jumps)
@@ -396,7 +322,6 @@ __global__ void __launch_bounds__(RT_N, 4) k_render(MapView m, RenderBatch<NJ> a
   __syncthreads();
 
   Cell cell;
-  cell.dirc = s_dirc + tid;
   cell.slot = s_slot + tid;
   const float org[3] = {m.ox, m.oy, m.oz};
   const float inv_h = 1.0f / m.h;
