@@ -324,6 +324,86 @@ typedef struct {
  * uneven frames share the GPU without a tail per frame. Asynchronous, allocates nothing. */
 DTSDF_API dtsdf_status dtsdf_render_batch(dtsdf_map map, const dtsdf_render_job* jobs, int32_t n, void* stream);
 
+/* ------------------------------------------------------------- serving ---- */
+
+/* A request server over device-resident maps (no counterpart in the paper: it schedules the
+ * paper's tracking step - preprocessing and pyramid of a depth frame (Sec. 7), a render of
+ * the map at a prior pose (Sec. 4), coarse-to-fine point-to-plane registration in SE(3) or
+ * Sim(3) (Secs. 5, 6) - for many sensors at once). A worker thread owned by the server admits
+ * requests in arrival order when their device working set fits in a fixed arena of
+ * hbm_budget bytes (allocated at creation) and a host slot is free, and keeps up to `streams`
+ * batches on the device: whenever a stream is idle, every pending request that fits (at most
+ * max_batch) is launched as one batch - per-request copy, preprocessing and pyramid, one
+ * render launch per map over the batch's frames of any sizes, one batched registration launch
+ * (opts: levels, iterations, eps, stop; no photometric term) - so requests arriving while
+ * others run join the next batch and batches overlap on the device. A request's result does
+ * not depend on the batch it was served in. The maps stay owned by the caller and must not be
+ * modified or destroyed while the server exists. */
+typedef struct dtsdf_server_s* dtsdf_server;
+
+typedef struct {
+  int64_t hbm_budget;       /* bytes of device memory for request working sets (the admission limit) */
+  int32_t max_inflight;     /* requests admitted at once, 1..4096 (pinned host slots are allocated for them) */
+  int32_t max_batch;        /* requests per batch, 1..64 */
+  int32_t streams;          /* batches on the device at once (one CUDA stream each), 1..16 */
+  int32_t max_width, max_height; /* largest accepted frame */
+  float z_min, z_max, delta_sup; /* preprocessing of request depth (outlier filter, Sec. 7) */
+  dtsdf_icp_opts opts;      /* registration schedule of every request (lambda ignored) */
+  dtsdf_batch_shape shape;  /* launch shape of the batched registration */
+} dtsdf_server_params;
+
+typedef struct {
+  int32_t map;              /* index into the maps given to dtsdf_server_create */
+  int32_t sim3;             /* 0: SE(3), 1: Sim(3) */
+  dtsdf_intrinsics K;       /* frame size (<= max_width x max_height) and intrinsics */
+  const float* depth;       /* host, K.height * K.width float32 z-depth; read when the request is
+                               admitted, so it must stay valid until its result is returned; page-
+                               locked memory is copied directly, other memory through a pinned slot */
+  double T_prior[16];       /* camera -> world prior pose (row-major); the map is rendered there */
+  uint64_t tag;             /* caller's tag, returned with the result */
+} dtsdf_request;
+
+typedef struct {
+  uint64_t tag;
+  uint64_t seq;             /* submission order */
+  int32_t status;           /* DTSDF_OK, or DTSDF_ERR_DEGENERATE from the last iteration */
+  int32_t batch_size;       /* requests in the batch that served it */
+  double T_rel[16];         /* current camera -> render camera after registration */
+  double T_wc[16];          /* refined camera -> world pose, T_prior T_rel */
+  dtsdf_icp_stats stats;    /* last iteration's statistics */
+  double t_submit, t_admit, t_done; /* seconds on the server clock: submission, launch, completion seen */
+} dtsdf_result;
+
+typedef struct {
+  int64_t submitted, admitted, completed, batches, pending, inflight, peak_inflight;
+  int64_t bytes_in_use, peak_bytes; /* arena bytes held by admitted requests */
+} dtsdf_server_stats_t;
+
+/* Create a server over n_maps maps of the current device. DTSDF_ERR_INVALID_ARG for bad
+ * parameters, DTSDF_ERR_OOM if the arena or host slots cannot be allocated. */
+DTSDF_API dtsdf_status dtsdf_server_create(const dtsdf_map* maps, int32_t n_maps, const dtsdf_server_params* params,
+                                           dtsdf_server* out);
+
+/* Queue one request (thread-safe, returns at once; *seq, if given, receives its submission
+ * number). DTSDF_ERR_INVALID_ARG for a bad request or one whose working set exceeds the
+ * whole budget. */
+DTSDF_API dtsdf_status dtsdf_server_submit(dtsdf_server s, const dtsdf_request* r, uint64_t* seq);
+
+/* Move up to cap completed results, oldest completion first, into out (host); *n receives the
+ * count. Waits up to wait_us microseconds when none is ready. DTSDF_ERR_CUDA if a batch failed
+ * on the device (message in dtsdf_last_error). */
+DTSDF_API dtsdf_status dtsdf_server_poll(dtsdf_server s, dtsdf_result* out, int32_t cap, int32_t* n,
+                                         int32_t wait_us);
+
+DTSDF_API dtsdf_status dtsdf_server_stats(dtsdf_server s, dtsdf_server_stats_t* st);
+
+/* Seconds since the server was created (the clock of the result time stamps). */
+DTSDF_API double dtsdf_server_clock(dtsdf_server s);
+
+/* Finish every submitted request, stop the worker and free the server's memory. Results not
+ * yet polled are dropped. */
+DTSDF_API dtsdf_status dtsdf_server_destroy(dtsdf_server s);
+
 /* Exponential map of se(3) (sim3 = 0, xi[6]) or sim(3) (sim3 = 1, xi[7]) evaluated by the
  * library's device code (the closed form of the matrix exponential of the 4x4 generator);
  * out: host 16 doubles. Synchronous; exposed for verification. */

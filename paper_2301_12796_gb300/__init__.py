@@ -87,6 +87,28 @@ class IcpStats(ctypes.Structure):
         return np.array(self.g[: self.dim], np.float64)
 
 
+class ServerParams(ctypes.Structure):
+    _fields_ = [("hbm_budget", c_int64), ("max_inflight", c_int32), ("max_batch", c_int32), ("streams", c_int32),
+                ("max_width", c_int32), ("max_height", c_int32), ("z_min", c_float), ("z_max", c_float),
+                ("delta_sup", c_float), ("opts", IcpOpts), ("shape", BatchShape)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("map", c_int32), ("sim3", c_int32), ("K", Intrinsics), ("depth", c_void_p),
+                ("T_prior", c_double * 16), ("tag", ctypes.c_uint64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("seq", ctypes.c_uint64), ("status", c_int32), ("batch_size", c_int32),
+                ("T_rel", c_double * 16), ("T_wc", c_double * 16), ("stats", IcpStats), ("t_submit", c_double),
+                ("t_admit", c_double), ("t_done", c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, c_int64) for n in ("submitted", "admitted", "completed", "batches", "pending", "inflight",
+                                       "peak_inflight", "bytes_in_use", "peak_bytes")]
+
+
 # exported symbols and their signatures (same order as include/dtsdf.h)
 P = c_void_p
 SIGNATURES = {
@@ -121,6 +143,12 @@ SIGNATURES = {
     "dtsdf_icp_batch_tune": ([ctypes.POINTER(IcpProblem), c_int32, ctypes.POINTER(IcpOpts),
                               ctypes.POINTER(BatchShape), ctypes.POINTER(ctypes.c_float), P], c_int32),
     "dtsdf_render_batch": ([P, ctypes.POINTER(RenderJob), c_int32, P], c_int32),
+    "dtsdf_server_create": ([ctypes.POINTER(P), c_int32, ctypes.POINTER(ServerParams), ctypes.POINTER(P)], c_int32),
+    "dtsdf_server_submit": ([P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)], c_int32),
+    "dtsdf_server_poll": ([P, ctypes.POINTER(Result), c_int32, ctypes.POINTER(c_int32), c_int32], c_int32),
+    "dtsdf_server_stats": ([P, ctypes.POINTER(ServerStats)], c_int32),
+    "dtsdf_server_clock": ([P], c_double),
+    "dtsdf_server_destroy": ([P], c_int32),
     "dtsdf_exp": ([c_int32, P, P], c_int32),
     "dtsdf_last_error": ([], ctypes.c_char_p),
     "dtsdf_version": ([], ctypes.c_char_p),
@@ -390,3 +418,59 @@ def exp(xi) -> np.ndarray:
     check(lib().dtsdf_exp(1 if x.shape[0] == 7 else 0, x.ctypes.data_as(c_void_p), out.ctypes.data_as(c_void_p)),
           "dtsdf_exp")
     return out.reshape(4, 4)
+
+
+def server_params(hbm_budget=8 << 30, max_inflight=256, max_batch=32, streams=4, max_width=1280, max_height=720,
+                  z_min=0.1, z_max=6.0, delta_sup=0.01, opts: IcpOpts | None = None, shape=(8, 256)) -> ServerParams:
+    o = opts if opts is not None else icp_opts(levels=3, iters=(10, 5, 4), eps=(0.01, 0.05, 0.1), lam=0.0)
+    return ServerParams(int(hbm_budget), max_inflight, max_batch, streams, max_width, max_height, z_min, z_max,
+                        delta_sup, o, BatchShape(*shape))
+
+
+class Server:
+    """Request server over device-resident maps (dtsdf_server_*): submit depth frames with
+    prior poses, poll results. Input arrays are kept referenced until their results are polled."""
+
+    def __init__(self, maps, p: ServerParams):
+        hs = (c_void_p * len(maps))(*[m._h.value for m in maps])
+        h = c_void_p()
+        check(lib().dtsdf_server_create(hs, len(maps), ctypes.byref(p), ctypes.byref(h)), "dtsdf_server_create")
+        self._h = h
+        self._keep = {}
+        self.params = p
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().dtsdf_server_destroy(self._h)
+            self._h = None
+            self._keep = {}
+
+    __del__ = close
+
+    def submit(self, map_index: int, depth: np.ndarray, K, T_prior, sim3=False, tag=0) -> int:
+        """depth: host float32 array [H, W] (C-contiguous; pinned memory is copied directly)."""
+        d = depth if (isinstance(depth, np.ndarray) and depth.dtype == np.float32 and depth.flags.c_contiguous) \
+            else np.ascontiguousarray(depth, np.float32)
+        ptr = d.ctypes.data if isinstance(d, np.ndarray) else d.data_ptr()
+        r = Request(int(map_index), int(bool(sim3)), intrinsics(K), ptr, pose_buf(T_prior), int(tag))
+        seq = ctypes.c_uint64()
+        check(lib().dtsdf_server_submit(self._h, ctypes.byref(r), ctypes.byref(seq)), "dtsdf_server_submit")
+        self._keep[seq.value] = d
+        return seq.value
+
+    def poll(self, cap: int = 64, wait_us: int = 0):
+        out = (Result * max(cap, 1))()
+        n = c_int32()
+        check(lib().dtsdf_server_poll(self._h, out, cap, ctypes.byref(n), int(wait_us)), "dtsdf_server_poll")
+        res = [out[i] for i in range(n.value)]
+        for r in res:
+            self._keep.pop(r.seq, None)
+        return res
+
+    def stats(self) -> ServerStats:
+        st = ServerStats()
+        check(lib().dtsdf_server_stats(self._h, ctypes.byref(st)), "dtsdf_server_stats")
+        return st
+
+    def clock(self) -> float:
+        return lib().dtsdf_server_clock(self._h)

@@ -23,6 +23,9 @@
 namespace dtsdf {
 
 constexpr int RT_N = 128;  // threads per CTA of the persistent render grid
+#ifndef DTSDF_RENDER_MINB
+#define DTSDF_RENDER_MINB 4   // resident CTAs per SM the register allocation is sized for
+#endif
 
 // Out-of-line hash probe over explicit pointers (keeps callers' state in registers).
 __device__ __noinline__ uint32_t probe_block(const unsigned long long* __restrict__ keys,
@@ -309,7 +312,7 @@ __device__ __forceinline__ int sign_fast(const MapView& m, Cell& c, const float 
 enum { S_MARCH = 0, S_SCAN = 1, S_ENDS_A = 2, S_ENDS_B = 3, S_OUT = 4, S_DONE = 5 };
 
 template <int STORE, bool COLOR, bool COUNT, int NJ>
-__global__ void __launch_bounds__(RT_N, 4) k_render(MapView m, RenderBatch<NJ> a) {
+__global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, RenderBatch<NJ> a) {
   __shared__ int s_slot[ND * RT_N];
   __shared__ Pose32 s_pose[NJ];
   uint8_t* touched = a.touched;

@@ -374,3 +374,45 @@ def plane_scene(normal=(0.3, -0.2, 1.0), offset: float = 0.0, seed: int = 5) -> 
         poses.append(look_at(eye, n * offset + a * rng.uniform(-0.05, 0.05), up=tuple(b)))
     return Scene("plane", np.stack(prims), K, poses, noise_s0=0.0, noise_s2=0.0, z_min=0.1, z_max=6.0,
                  seed=seed, tex_seed=seed + 1000, extra=dict(normal=n, offset=offset))
+
+
+# ---------------------------------------------------------------- serving --
+
+# sensor classes of the serving workload and their shares of the requests
+SERVE_SENSORS = (
+    (Intrinsics(320, 240, 262.5, 262.5, 159.5, 119.5), 0.3),
+    (Intrinsics(640, 480, 525.0, 525.0, 319.5, 239.5), 0.5),
+    (Intrinsics(1280, 720, 910.0, 910.0, 639.5, 359.5), 0.2),
+)
+
+
+def serve_requests(rooms: list, n: int, seed: int = 1, rate: float = 2000.0, sim3_every: int = 4,
+                   rot_deg: float = 2.0, trans_m: float = 0.02, pool: int | None = None) -> list[dict]:
+    """n render + registration requests against maps of ``rooms``: Poisson arrival times at
+    ``rate`` per second (key t, seconds), the map drawn uniformly, the sensor drawn with the
+    SERVE_SENSORS shares, every ``sim3_every``-th request a Sim(3) one whose depth is scaled by a
+    seeded factor in [0.9, 1.1]; the true pose is a seeded frame of the room's trajectory moved
+    by 2 deg / 5 cm, the prior that pose perturbed by rot_deg / trans_m. With ``pool`` the frames
+    of the first ``pool`` requests are reused cyclically by the later ones (same map, sensor,
+    kind, poses and depth), so long request streams need few ray-traced frames."""
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    shares = np.array([w for _, w in SERVE_SENSORS])
+    out = []
+    for i in range(n):
+        if pool is not None and i >= pool:
+            q = dict(out[i % pool])
+            q["t"] = float(arrivals[i])
+            out.append(q)
+            continue
+        mi = int(rng.integers(len(rooms)))
+        room = rooms[mi]
+        K = SERVE_SENSORS[int(rng.choice(len(SERVE_SENSORS), p=shares))][0]
+        sim3 = (i % sim3_every) == sim3_every - 1
+        scale = float(rng.uniform(0.9, 1.1)) if sim3 else 1.0
+        T_true = room.poses[int(rng.integers(room.n_frames))] @ perturbation(rng, 2.0, 0.05)
+        frame = room.render(T_true, K=K, frame_id=200000 + i, noise=True, depth_scale=scale)
+        prior = T_true @ perturbation(rng, rot_deg, trans_m)
+        out.append(dict(t=float(arrivals[i]), map=mi, K=K, sim3=sim3, scale=scale, T_true=T_true, prior=prior,
+                        depth=frame.depth))
+    return out

@@ -55,6 +55,10 @@ def test_struct_layouts_match_header():
              sizeof(dtsdf_render_job));
       printf("%zu %zu %zu\n", offsetof(dtsdf_icp_problem, K_ref), offsetof(dtsdf_icp_problem, sim3),
              offsetof(dtsdf_render_job, out));
+      printf("%zu %zu %zu %zu\n", sizeof(dtsdf_server_params), sizeof(dtsdf_request), sizeof(dtsdf_result),
+             sizeof(dtsdf_server_stats_t));
+      printf("%zu %zu %zu %zu\n", offsetof(dtsdf_server_params, opts), offsetof(dtsdf_server_params, shape),
+             offsetof(dtsdf_request, T_prior), offsetof(dtsdf_result, stats));
       return 0;
     }
     """
@@ -73,6 +77,10 @@ def test_struct_layouts_match_header():
                                                                              dt.BatchShape, dt.RenderJob)]
     assert [int(x) for x in lines[3].split()] == [dt.IcpProblem.K_ref.offset, dt.IcpProblem.sim3.offset,
                                                   dt.RenderJob.out.offset]
+    assert [int(x) for x in lines[4].split()] == [ctypes.sizeof(x) for x in (dt.ServerParams, dt.Request, dt.Result,
+                                                                             dt.ServerStats)]
+    assert [int(x) for x in lines[5].split()] == [dt.ServerParams.opts.offset, dt.ServerParams.shape.offset,
+                                                  dt.Request.T_prior.offset, dt.Result.stats.offset]
 
 
 def test_invalid_parameters_rejected_on_host(lib):
@@ -97,6 +105,16 @@ def test_invalid_parameters_rejected_on_host(lib):
     assert lib.dtsdf_icp_batch(pr, 0, ctypes.byref(opts), ctypes.byref(dt.BatchShape(3, 256)), None) == \
         dt.ERR_INVALID_ARG
     assert lib.dtsdf_render_batch(None, None, 1, None) == dt.ERR_INVALID_ARG
+    # the server checks its parameters before allocating anything
+    sp = dt.server_params(hbm_budget=0)
+    maps = (ctypes.c_void_p * 1)(1)
+    assert lib.dtsdf_server_create(maps, 1, ctypes.byref(sp), ctypes.byref(h)) == dt.ERR_INVALID_ARG
+    sp = dt.server_params(streams=99)
+    assert lib.dtsdf_server_create(maps, 1, ctypes.byref(sp), ctypes.byref(h)) == dt.ERR_INVALID_ARG
+    sp = dt.server_params(shape=(3, 256))
+    assert lib.dtsdf_server_create(maps, 1, ctypes.byref(sp), ctypes.byref(h)) == dt.ERR_INVALID_ARG
+    assert lib.dtsdf_server_create(None, 1, ctypes.byref(dt.server_params()), ctypes.byref(h)) == dt.ERR_INVALID_ARG
+    assert lib.dtsdf_server_submit(None, None, None) == dt.ERR_INVALID_ARG
 
 
 def test_product_path_has_no_cpu_fallback(tmp_path, monkeypatch):

@@ -1,0 +1,132 @@
+"""Serving (continuous batching over device-resident maps): every request served in a mix of
+concurrent batches gives the same registration as the same request served alone, and the same
+as the library's direct render + batched registration; admission keeps the working sets inside
+the memory budget. Maps: two seeded rooms, one in FP16 storage and one in FP32."""
+import time
+
+import numpy as np
+import pytest
+
+import scenes
+
+torch = pytest.importorskip("torch")
+import paper_2301_12796_gb300 as dt  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+OPTS = dict(levels=3, iters=(10, 10, 10), eps=(0.01, 0.1, 0.2), lam=0.0, stop_norm=1e-6, min_rows=10)
+SHAPE = (8, 256)
+BUDGET = 1 << 30
+
+
+@pytest.fixture(scope="module")
+def setup():
+    dev = torch.device("cuda:0")
+    rooms = [scenes.kinect_room(s, n_frames=20) for s in (1, 2)]
+    maps = []
+    for storage, room in zip((dt.STORE_FP16, dt.STORE_FP32), rooms):
+        m = dt.Map(dt.params(voxel_size=0.005, truncation=0.02, max_blocks=1 << 17, z_max=room.z_max, color=False,
+                             storage=storage))
+        for i in range(room.n_frames):
+            f = room.frame(i)
+            m.integrate(torch.from_numpy(f.depth).to(dev), None, room.K, f.pose)
+        maps.append(m)
+    torch.cuda.synchronize()
+    reqs = scenes.serve_requests(rooms, 16, seed=3)
+    yield maps, rooms, reqs
+    for m in maps:
+        m.close()
+
+
+def serve(maps, reqs, which, budget=BUDGET, streams=4):
+    p = dt.server_params(hbm_budget=budget, max_inflight=64, max_batch=16, streams=streams,
+                         opts=dt.icp_opts(**OPTS), shape=SHAPE)
+    srv = dt.Server(maps, p)
+    try:
+        for i in which:
+            q = reqs[i]
+            srv.submit(q["map"], q["depth"], q["K"], q["prior"], sim3=q["sim3"], tag=i)
+        out = {}
+        deadline = time.time() + 120
+        while len(out) < len(which):
+            assert time.time() < deadline, "server did not finish"
+            for r in srv.poll(64, wait_us=100000):
+                out[r.tag] = r
+        st = srv.stats()
+    finally:
+        srv.close()
+    return out, st
+
+
+def pose(r, key="T_rel"):
+    return np.array(getattr(r, key)[:], np.float64).reshape(4, 4)
+
+
+def test_result_same_alone_and_in_the_mix(setup):
+    maps, _, reqs = setup
+    alone = {}
+    for i in range(len(reqs)):
+        res, st = serve(maps, reqs, [i])
+        assert st.batches == 1 and res[i].batch_size == 1
+        alone[i] = res[i]
+    mix, st = serve(maps, reqs, list(range(len(reqs))))
+    assert st.completed == len(reqs)
+    assert max(r.batch_size for r in mix.values()) > 1, "requests never shared a batch"
+    for i in range(len(reqs)):
+        a, b = alone[i], mix[i]
+        # every kernel of a request is independent of the rest of its launch: identical bits
+        assert np.array_equal(pose(a), pose(b)), i
+        assert np.array_equal(pose(a, "T_wc"), pose(b, "T_wc")), i
+        assert a.stats.rows == b.stats.rows and a.stats.error == b.stats.error and a.status == b.status
+
+
+def test_server_equals_direct_library_path(setup):
+    maps, _, reqs = setup
+    dev = torch.device("cuda:0")
+    which = [0, 1, 2, 3, 5, 7]
+    res, _ = serve(maps, reqs, which)
+    opts = dt.icp_opts(**OPTS)
+    for i in which:
+        q = reqs[i]
+        K = q["K"]
+        prior = torch.from_numpy(q["prior"]).to(dev)
+        d = torch.zeros(K.height, K.width, device=dev)
+        n = torch.zeros(K.height, K.width, 4, device=dev)
+        maps[q["map"]].render_dev(K, prior, d, n)
+        icp = dt.Icp(K.width, K.height, 3)
+        icp.set_frame(torch.from_numpy(q["depth"]).to(dev), None, K, 0.1, 6.0, 0.01)
+        T = torch.eye(4, dtype=torch.float64, device=dev)
+        dt.icp_batch([(icp, n, K, T, q["sim3"])], opts, shape=SHAPE)
+        torch.cuda.synchronize()
+        assert np.array_equal(T.cpu().numpy(), pose(res[i])), i
+        icp.close()
+
+
+def test_registration_recovers_the_truth(setup):
+    maps, _, reqs = setup
+    res, _ = serve(maps, reqs, list(range(len(reqs))))
+    ok = 0
+    for i, q in enumerate(reqs):
+        T = pose(res[i], "T_wc")
+        s = np.cbrt(np.linalg.det(T[:3, :3]))
+        # a Sim(3) request recovers the sensor's depth scale as the inverse scale of T_rel
+        dt_err = np.linalg.norm(T[:3, 3] - q["T_true"][:3, 3])
+        sc_err = abs(s * q["scale"] - 1.0)
+        ok += dt_err < 0.01 and sc_err < 0.01
+    assert ok >= len(reqs) - 1, ok
+
+
+def test_admission_by_memory_budget(setup):
+    maps, _, reqs = setup
+    sel = [i for i, q in enumerate(reqs) if q["K"].width == 640][:6]
+    assert len(sel) >= 3
+    _, st1 = serve(maps, reqs, sel[:1])
+    footprint = st1.peak_bytes
+    assert footprint > 640 * 480 * 40
+    budget = int(2.5 * footprint)
+    res, st = serve(maps, reqs, sel, budget=budget)
+    assert st.completed == len(sel)
+    assert st.peak_bytes <= budget and st.peak_inflight <= 2
+    alone, _ = serve(maps, reqs, sel)
+    for i in sel:
+        assert np.array_equal(pose(res[i]), pose(alone[i]))
