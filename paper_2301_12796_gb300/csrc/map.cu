@@ -330,6 +330,47 @@ __device__ __forceinline__ bool block_visible(const MapView& m, const FuseFrame&
 // frustum, then every voxel is projected to its nearest pixel and updated with the
 // weighted running average (Sec. 3). A voxel has one writer, so fusion is deterministic.
 // A brick with an updated voxel is stamped with the frame id for the apron refresh.
+// Apron maintenance by the brick that changed: brick b (block (bx, by, bz), direction D)
+// copies its core voxels into the aprons of its 26 neighbours. The apron voxel at local
+// coordinate x of the neighbour at block offset -e comes from this brick's core voxel x - 8 e
+// (e = floor(x / 8) per axis). It reads only its own core, which no other CTA writes, and
+// writes only aprons, which nobody reads during fusion, so bricks push concurrently. The
+// brick and the neighbours whose bound region [0, 8]^3 holds its voxels (offsets -e with e in
+// {0, 1}^3) are stamped with the frame for the exact bound pass.
+template <int STORE>
+__device__ void push_borders(const MapView& m, int b, int bx, int by, int bz, int D) {
+  __shared__ int s_nb[27];
+  if (threadIdx.x < 27) {
+    const int q = threadIdx.x;  // neighbour at block offset (q % 3 - 1, q / 3 % 3 - 1, q / 9 - 1)
+    int sl = -1;
+    if (q != 13) {
+      const int dd = hash_find(m, bx + q % 3 - 1, by + (q / 3) % 3 - 1, bz + q / 9 - 1);
+      sl = dd >= 0 ? m.dir_slots[(size_t)dd * 8 + D] : -1;
+    }
+    s_nb[q] = sl;
+    // bound regions that contain this brick's voxels: its own and those at offsets in {-1, 0}^3
+    if (q == 13)
+      m.stamp[b] = m.frame;
+    else if (sl >= 0 && q % 3 != 2 && (q / 3) % 3 != 2 && q / 9 != 2)
+      m.stamp[sl] = m.frame;
+  }
+  __syncthreads();
+  const size_t src = (size_t)b * PVOX;
+  for (int vi = threadIdx.x; vi < PVOX; vi += blockDim.x) {
+    const int x = vi % PAD - 1, y = (vi / PAD) % PAD - 1, z = vi / (PAD * PAD) - 1;
+    const int ex = x >> 3, ey = y >> 3, ez = z >> 3;
+    if ((ex | ey | ez) == 0) continue;  // core position: no neighbour holds it in an apron
+    const int sl = s_nb[(1 - ez) * 9 + (1 - ey) * 3 + (1 - ex)];
+    if (sl < 0) continue;
+    const size_t from = src + pad_index(x & 7, y & 7, z & 7);
+    if (STORE == DTSDF_STORE_FP16)
+      m.geom16[(size_t)sl * PVOX + vi] = m.geom16[from];
+    else
+      m.geom[(size_t)sl * PVOX + vi] = m.geom[from];
+  }
+  __syncthreads();
+}
+
 template <int STORE>
 __global__ void __launch_bounds__(256) k_fuse(MapView m, FuseFrame f) {
   const uint32_t nb = min(*((volatile uint32_t*)(m.counters + C_POOL)), m.pool_cap);
@@ -430,30 +471,50 @@ __global__ void __launch_bounds__(256) k_fuse(MapView m, FuseFrame f) {
         }
       }
     }
-    if (__syncthreads_or(updated) && threadIdx.x == 0) m.stamp[b] = m.frame;
+    if (!__syncthreads_or(updated)) continue;
+    push_borders<STORE>(m, (int)b, bx, by, bz, D);
   }
 }
 
-// Apron refresh and exact bound. A brick whose 3x3x3 neighbourhood of blocks holds a brick
-// stamped with this frame (every brick when `all`) copies its neighbours' voxels at local
-// coordinates -1, 8 and 9 into its apron (an unallocated neighbour reads as sdf 1, weight 0,
-// the initial value, so it stays absent for presence tests) and recomputes its bound over
-// [0, 8]^3. Reads touch only cores and writes only aprons, so bricks refresh concurrently.
+// Exact bound of a brick: minimum sdf over its voxels at local coordinates [0, 8]^3 with
+// weight > 0 (+inf if none), reduced over the CTA.
 template <int STORE>
-__global__ void __launch_bounds__(256) k_apron_refresh(MapView m, FuseFrame f, int all) {
-  __shared__ int s_nb[27];
+__device__ void exact_bound(const MapView& m, uint32_t b) {
   __shared__ float s_red[8];
+  const size_t base = (size_t)b * PVOX;
+  float mn = INFINITY;
+  for (int vi = threadIdx.x; vi < 729; vi += blockDim.x) {
+    const int x = vi % 9, y = (vi / 9) % 9, z = vi / 81;
+    const float2 g = load_geom<STORE>(m, base + pad_index(x, y, z));
+    if (g.y > 0.0f) mn = fminf(mn, g.x);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = mn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float x = INFINITY;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x = fminf(x, s_red[w]);
+    m.bound[b] = x;
+  }
+  __syncthreads();
+}
+
+// Apron pull: the bricks [C_POOL_BEFORE, C_POOL) allocated this frame (every brick when `all`)
+// copy their neighbours' voxels at local coordinates -1, 8 and 9 into their apron (an
+// unallocated neighbour reads as sdf 1, weight 0, the initial value, so it stays absent for
+// presence tests). Runs before fusion for new bricks (fusion then pushes what it changes) and
+// after an import for every brick; reads touch only cores and writes only aprons. With `all`
+// the exact bound follows.
+template <int STORE>
+__global__ void __launch_bounds__(256) k_apron_pull(MapView m, int all) {
+  __shared__ int s_nb[27];
   const uint32_t nb = min(*((volatile uint32_t*)(m.counters + C_POOL)), m.pool_cap);
-  if (!all && f.Tdev) f.T = pose_from_device(f.Tdev);
-  // neighbours of a block visible to the fusion lie within one block diagonal of it; new
-  // bricks lie within tau of a back-projected pixel
-  const float margin = 8.0f * 1.7320508f * m.h + m.tau;
-  for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+  const uint32_t b0 = all ? 0u : min(*((volatile uint32_t*)(m.counters + C_POOL_BEFORE)), nb);
+  for (uint32_t b = b0 + blockIdx.x; b < nb; b += gridDim.x) {
     const int bd = m.brick_dir[b];
     const int d = bd >> 3, D = bd & 7;
     const int bx = m.dir_coord[4 * d], by = m.dir_coord[4 * d + 1], bz = m.dir_coord[4 * d + 2];
-    if (!all && !block_visible(m, f, bx, by, bz, margin)) continue;
-    bool changed = false;
     if (threadIdx.x < 27) {
       const int q = threadIdx.x;
       int sl = (int)b;
@@ -462,41 +523,30 @@ __global__ void __launch_bounds__(256) k_apron_refresh(MapView m, FuseFrame f, i
         sl = dd >= 0 ? m.dir_slots[(size_t)dd * 8 + D] : -1;
       }
       s_nb[q] = sl;
-      changed = sl >= 0 && m.stamp[sl] == m.frame;
     }
-    if (!__syncthreads_or(changed || all)) continue;
-    float mn = INFINITY;
+    __syncthreads();
     const size_t base = (size_t)b * PVOX;
     for (int vi = threadIdx.x; vi < PVOX; vi += blockDim.x) {
       const int x = vi % PAD - 1, y = (vi / PAD) % PAD - 1, z = vi / (PAD * PAD) - 1;
-      float2 g;
-      if ((unsigned)x < 8u && (unsigned)y < 8u && (unsigned)z < 8u) {
-        g = load_geom<STORE>(m, base + vi);
-      } else {
-        const int sl = s_nb[((z >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((x >> 3) + 1)];
-        const size_t src = (size_t)sl * PVOX + pad_index(x & 7, y & 7, z & 7);
-        if (STORE == DTSDF_STORE_FP16) {
-          const uint32_t raw = sl >= 0 ? m.geom16[src] : pack_geom16(1.0f, 0.0f);
-          m.geom16[base + vi] = raw;
-          g = unpack_geom16(raw);
-        } else {
-          g = sl >= 0 ? m.geom[src] : make_float2(1.0f, 0.0f);
-          m.geom[base + vi] = g;
-        }
-      }
-      if (x <= 8 && y <= 8 && z <= 8 && x >= 0 && y >= 0 && z >= 0 && g.y > 0.0f) mn = fminf(mn, g.x);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = mn;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float x = INFINITY;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x = fminf(x, s_red[w]);
-      m.bound[b] = x;
+      if ((unsigned)x < 8u && (unsigned)y < 8u && (unsigned)z < 8u) continue;
+      const int sl = s_nb[((z >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((x >> 3) + 1)];
+      const size_t src = (size_t)sl * PVOX + pad_index(x & 7, y & 7, z & 7);
+      if (STORE == DTSDF_STORE_FP16)
+        m.geom16[base + vi] = sl >= 0 ? m.geom16[src] : pack_geom16(1.0f, 0.0f);
+      else
+        m.geom[base + vi] = sl >= 0 ? m.geom[src] : make_float2(1.0f, 0.0f);
     }
     __syncthreads();
+    if (all) exact_bound<STORE>(m, b);
   }
+}
+
+// Exact bounds of the bricks whose bound region changed this frame (stamped by fusion).
+template <int STORE>
+__global__ void __launch_bounds__(256) k_bounds_exact(MapView m) {
+  const uint32_t nb = min(*((volatile uint32_t*)(m.counters + C_POOL)), m.pool_cap);
+  for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x)
+    if (m.stamp[b] == m.frame) exact_bound<STORE>(m, b);
 }
 
 // ------------------------------------------------------------------ import
@@ -652,22 +702,23 @@ void launch_fuse(const MapView& m, const Intr& K, const Pose32& T, const double*
   set(1, -K.fx, 0.f, (float)K.W - 0.5f - K.cx);
   set(2, 0.f, K.fy, K.cy + 0.5f);
   set(3, 0.f, -K.fy, (float)K.H - 0.5f - K.cy);
+  const bool sparse = m.dense_dim <= 0;
   if (m.storage == DTSDF_STORE_FP16) {
+    if (sparse) k_apron_pull<DTSDF_STORE_FP16><<<num_sms * 4, 256, 0, s>>>(m, 0);
     k_fuse<DTSDF_STORE_FP16><<<num_sms * 8, 256, 0, s>>>(m, f);
-    k_apron_refresh<DTSDF_STORE_FP16><<<num_sms * 8, 256, 0, s>>>(m, f, 0);
+    k_bounds_exact<DTSDF_STORE_FP16><<<num_sms * 8, 256, 0, s>>>(m);
   } else {
+    if (sparse) k_apron_pull<DTSDF_STORE_FP32><<<num_sms * 4, 256, 0, s>>>(m, 0);
     k_fuse<DTSDF_STORE_FP32><<<num_sms * 8, 256, 0, s>>>(m, f);
-    k_apron_refresh<DTSDF_STORE_FP32><<<num_sms * 8, 256, 0, s>>>(m, f, 0);
+    k_bounds_exact<DTSDF_STORE_FP32><<<num_sms * 8, 256, 0, s>>>(m);
   }
 }
 
 void launch_apron_refresh_all(const MapView& m, int num_sms, cudaStream_t s) {
-  FuseFrame f;
-  memset(&f, 0, sizeof(f));
   if (m.storage == DTSDF_STORE_FP16)
-    k_apron_refresh<DTSDF_STORE_FP16><<<num_sms * 8, 256, 0, s>>>(m, f, 1);
+    k_apron_pull<DTSDF_STORE_FP16><<<num_sms * 8, 256, 0, s>>>(m, 1);
   else
-    k_apron_refresh<DTSDF_STORE_FP32><<<num_sms * 8, 256, 0, s>>>(m, f, 1);
+    k_apron_pull<DTSDF_STORE_FP32><<<num_sms * 8, 256, 0, s>>>(m, 1);
 }
 
 void launch_import(const MapView& m, const int32_t* coords, const float* vox, int64_t n, bool allocate, int num_sms,
