@@ -52,12 +52,18 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile", action="store_true", help="small run for ncu: map of 60 frames, few steps")
-    ap.add_argument("--workload", default="tracking", choices=["tracking", "multi_sensor"],
+    ap.add_argument("--workload", default="tracking", choices=["tracking", "multi_sensor", "serve"],
                     help="tracking: Kinect-shaped tracking frames (default); multi_sensor: batched Sim(3) "
-                         "registration of 1280x720 second-sensor frames against the 640x480 map")
+                         "registration of 1280x720 second-sensor frames against the 640x480 map; serve: "
+                         "a Poisson stream of render + registration requests of mixed sizes served by the "
+                         "continuous-batching server over FP16 maps, against serial FP32 solves")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
                     help="map storage: FP32 sdf/weight/colour, or FP16 sdf + half weight + u8 colour")
     ap.add_argument("--problems", type=int, default=64, help="multi_sensor: registration problems per step")
+    ap.add_argument("--requests", type=int, default=512, help="serve: requests in the arrival stream")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrival rate, requests/s")
+    ap.add_argument("--maps", type=int, default=3, help="serve: device-resident maps (seeded rooms)")
+    ap.add_argument("--map-frames", type=int, default=100, help="serve: frames fused into each map")
     return ap.parse_args()
 
 
@@ -618,6 +624,233 @@ def run_multi_sensor(args, dt, torch, tdist, dev, rank, world, local):
         print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------------ serve --
+SERVE_OPTS = dict(levels=3, iters=(10, 10, 10), eps=(0.01, 0.1, 0.2), lam=0.0, stop_norm=1e-6, min_rows=10)
+WORKLOAD_SERVE = ("serving: {n} render + registration requests, Poisson arrivals at {rate:g}/s, sensors 320x240 / "
+                  "640x480 / 1280x720 (shares 0.3 / 0.5 / 0.2), SE(3):Sim(3) = 3:1 (Sim(3) depth scaled by U[0.9, 1.1]), "
+                  "priors 2 deg / 2 cm off; {m} device-resident FP16 maps of seeded 4x4x3 m rooms ({f} frames each, "
+                  "5 mm voxels); per request preprocessing + 3-level pyramid, render at the prior, 3-level "
+                  "registration (10 iterations per level); continuous batching over 4 streams, admission by a "
+                  "{gb:g} GB device budget")
+
+
+def pose_diff(A, B):
+    """(rotation angle rad, translation m, relative scale) between two similarity transforms."""
+    sa, sb = np.cbrt(np.linalg.det(A[:3, :3])), np.cbrt(np.linalg.det(B[:3, :3]))
+    R = (A[:3, :3] / sa).T @ (B[:3, :3] / sb)
+    ang = float(np.arccos(np.clip((np.trace(R) - 1) / 2, -1, 1)))
+    return ang, float(np.linalg.norm(A[:3, 3] - B[:3, 3])), float(abs(sa / sb - 1))
+
+
+def serve_stream(srv, reqs, pinned):
+    """Submit each request at its arrival time (server clock), collect every result."""
+    out = {}
+    t0 = srv.clock() + 0.01
+    for i, q in enumerate(reqs):
+        while srv.clock() - t0 < q["t"]:
+            for r in srv.poll(64, wait_us=0):
+                out[r.tag] = r
+        srv.submit(q["map"], pinned[i], q["K"], q["prior"], sim3=q["sim3"], tag=i)
+    deadline = time.time() + 300
+    while len(out) < len(reqs):
+        assert time.time() < deadline, "serve: results missing"
+        for r in srv.poll(256, wait_us=2000):
+            out[r.tag] = r
+    return [out[i] for i in range(len(reqs))]
+
+
+def serial_stream(dt, torch, dev, maps, reqs, pinned, icps):
+    """The same arrival stream served one request at a time (synchronous per request)."""
+    opts = dt.icp_opts(**SERVE_OPTS)
+    bufs = {}
+    T = torch.eye(4, dtype=torch.float64, device=dev)
+    eye = torch.eye(4, dtype=torch.float64, device=dev)
+    prior = torch.empty(4, 4, dtype=torch.float64, device=dev)
+    host_T = torch.empty(4, 4, dtype=torch.float64).pin_memory()
+    done, res = [], []
+    t0 = time.perf_counter() + 0.01
+    for i, q in enumerate(reqs):
+        while time.perf_counter() - t0 < q["t"]:
+            pass
+        K = q["K"]
+        key = (K.width, K.height)
+        if key not in bufs:
+            bufs[key] = (torch.empty(K.height, K.width, device=dev), torch.zeros(K.height, K.width, device=dev),
+                         torch.zeros(K.height, K.width, 4, device=dev))
+        d_in, rd, rn = bufs[key]
+        src = pinned[i] if torch.is_tensor(pinned[i]) else torch.from_numpy(pinned[i])
+        d_in.copy_(src, non_blocking=True)
+        prior.copy_(torch.from_numpy(q["prior"]), non_blocking=True)
+        icp = icps[key]
+        icp.set_frame(d_in, None, K, 0.1, 6.0, 0.01)
+        maps[q["map"]].render_dev(K, prior, rd, rn)
+        T.copy_(eye)
+        dt.icp_batch([(icp, rn, K, T, q["sim3"])], opts, shape=(8, 256))
+        host_T.copy_(T, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        done.append(time.perf_counter() - t0 - q["t"])
+        res.append(q["prior"] @ host_T.numpy())
+    return np.array(done), res
+
+
+def serve_cpu_baseline(rooms, q):
+    """The oracle on a bounded sample of one 640x480 request, scaled to the whole request."""
+    import oracle
+    from oracle import icp as oicp
+    room, K = rooms[q["map"]], q["K"]
+    om = oracle.OracleMap(oracle.Params(voxel_size=0.005, truncation=0.02, z_max=room.z_max, color=False))
+    for i in range(0, room.n_frames, max(1, room.n_frames // 6)):
+        f = room.frame(i)
+        om.integrate(f.depth, None, room.K, f.pose)
+    stride = 16
+    vv, uu = np.mgrid[0:K.height:stride, 0:K.width:stride]
+    pix = np.stack([uu.ravel(), vv.ravel()], 1).astype(np.int32)
+    t0 = time.perf_counter()
+    om.render(K, q["prior"], pix)
+    t_render = (time.perf_counter() - t0) * (K.width * K.height) / len(pix)
+    ref = room.render(q["prior"], K=K, noise=False, exact=True)
+    rn = np.zeros(ref.normals.shape[:2] + (4,), np.float32)
+    rn[..., :3] = ref.normals
+    pre = oracle.preprocess(q["depth"], K, 0.1, 6.0, 0.01)
+    levels = oicp.pyramid(pre["z"], K, 3)
+    st = oicp.Settings(sim3=bool(q["sim3"]), eps=SERVE_OPTS["eps"], iters=SERVE_OPTS["iters"])
+    t_icp = 0.0
+    for l in range(3):
+        t0 = time.perf_counter()
+        oicp.step(levels[l], ref.depth, rn, K, np.eye(4), st.eps[l], st, level_index=l)
+        t_icp += (time.perf_counter() - t0) * SERVE_OPTS["iters"][l]
+    sample = (f"one 640x480 request: oracle render of 1/{stride * stride} of the pixels scaled up ({t_render:.1f} s), "
+              f"one registration iteration per level scaled to 10 per level ({t_icp:.1f} s); oracle map fused from "
+              f"1/{max(1, room.n_frames // 6)} of the frames")
+    return 1.0 / (t_render + t_icp), sample
+
+
+def run_serve(args, dt, torch, tdist, dev, rank, world, local):
+    import scenes
+    n_frames = 20 if args.profile else args.map_frames
+    rooms = [scenes.kinect_room(1 + i, n_frames=n_frames) for i in range(args.maps)]
+    maps16, maps32 = [], []
+    for room in rooms:
+        for store, lst in ((dt.STORE_FP16, maps16), (dt.STORE_FP32, maps32)):
+            m = dt.Map(dt.params(voxel_size=0.005, truncation=0.02, max_blocks=1 << 18, z_max=room.z_max,
+                                 color=False, storage=store))
+            lst.append(m)
+        for i in range(room.n_frames):
+            f = room.frame(i)
+            d = torch.from_numpy(f.depth).to(dev)
+            lst16, lst32 = maps16[-1], maps32[-1]
+            lst16.integrate(d, None, room.K, f.pose)
+            lst32.integrate(d, None, room.K, f.pose)
+    torch.cuda.synchronize()
+    voxels = [round(m.stats().bricks * 512 / 1e6, 2) for m in maps16]
+    n_req = 64 if args.profile else args.requests
+    reqs = scenes.serve_requests(rooms, n_req, seed=1, rate=args.rate, pool=min(n_req, 96))
+    pinned = [torch.from_numpy(q["depth"]).pin_memory() for q in reqs]
+    pinned_np = [p.numpy() for p in pinned]
+    budget = 16 << 30
+    p = dt.server_params(hbm_budget=budget, max_inflight=128, max_batch=32, streams=4,
+                         opts=dt.icp_opts(**SERVE_OPTS), shape=(8, 256))
+    srv = dt.Server(maps16, p)
+    warm = scenes.serve_requests(rooms, 48, seed=2, rate=args.rate, pool=8)
+    serve_stream(srv, warm, [q["depth"] for q in warm])
+    clk = ClockSampler(local)
+    clk.start()
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    res = serve_stream(srv, reqs, pinned_np)
+    clocks = clk.stop()
+    st = srv.stats()
+    srv.close()
+    lat = np.array([r.t_done - r.t_submit for r in res])
+    span = max(r.t_done for r in res) - min(r.t_submit for r in res)
+    value = world * len(reqs) / span
+    # serial plain FP32 solves of the same stream
+    icps = {(K.width, K.height): dt.Icp(K.width, K.height, 3) for K, _ in scenes.SERVE_SENSORS}
+    serial_stream(dt, torch, dev, maps32, warm[:8], [q["depth"] for q in warm[:8]], icps)
+    lat_s, res_s = serial_stream(dt, torch, dev, maps32, reqs, pinned, icps)
+    span_s = float(lat_s[-1] + reqs[-1]["t"] - reqs[0]["t"])
+    # accuracy: FP16 served vs FP32 serial, and both vs the truth
+    d_fp = np.array([pose_diff(np.array(r.T_wc[:]).reshape(4, 4), T) for r, T in zip(res, res_s)])
+    d_gt = np.array([pose_diff(np.array(r.T_wc[:]).reshape(4, 4) @ np.diag([q["scale"]] * 3 + [1.0]), q["T_true"])
+                     for r, q in zip(res, reqs)])
+    # roofline of the dominant kernel: one render launch over a batch of the pool's frames per map (events)
+    sample = list(range(0, min(len(reqs), 96)))
+    bufs = [(torch.from_numpy(reqs[i]["prior"]).to(dev), torch.zeros(reqs[i]["K"].height, reqs[i]["K"].width,
+                                                                     device=dev),
+             torch.zeros(reqs[i]["K"].height, reqs[i]["K"].width, 4, device=dev)) for i in sample]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    geom = 0.0
+    for mi, m in enumerate(maps16):
+        sel = [j for j, i in enumerate(sample) if reqs[i]["map"] == mi][:32]
+        for j in sel[:4]:
+            geom += m.touched(reqs[sample[j]]["K"], reqs[sample[j]]["prior"])[0] * len(sel) / max(1, min(4, len(sel)))
+    rms = 0.0
+    pix = 0
+    for mi, m in enumerate(maps16):
+        sel = [j for j, i in enumerate(sample) if reqs[i]["map"] == mi][:32]
+        if not sel:
+            continue
+        jobs = [(reqs[sample[j]]["K"], bufs[j][0], bufs[j][1], bufs[j][2], None) for j in sel]
+        m.render_batch(jobs)
+        e0.record()
+        m.render_batch(jobs)
+        e1.record()
+        torch.cuda.synchronize()
+        rms += e0.elapsed_time(e1)
+        pix += sum(reqs[sample[j]]["K"].width * reqs[sample[j]]["K"].height for j in sel)
+    render_bytes = geom * 512 * 4 + pix * (4 + 16)
+    peak, peak_kind = measured_hbm_peak()
+    achieved = render_bytes / (rms / 1000.0) / 1e9
+    roof = {"kernel": "k_render (batched direct DTSDF ray-cast, FP16 storage)", "bound": "hbm", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+            "algorithmic_bytes_per_launch": render_bytes / max(1, args.maps), "launch_ms": rms / max(1, args.maps)}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu and not args.profile:
+        q640 = next(q for q in reqs if q["K"].width == 640)
+        v, desc = serve_cpu_baseline(rooms, q640)
+        cpu = {"value": v, "unit": "requests/s", "cores": cpu_cores(), "kind": "oracle", "sample": desc}
+    h2d = int(np.mean([q["depth"].nbytes for q in reqs]))
+    if rank == 0:
+        out = {"metric": "served render+ICP requests/s, p50/p99 latency (continuous batching, mixed sizes)",
+               "value": value, "unit": "requests/s", "n_gpus": world, "steps": len(reqs), "warmup": len(warm),
+               "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f16 storage / f32 compute", "data": "synthetic",
+               "config": {"workload": WORKLOAD_SERVE.format(n=len(reqs), rate=args.rate, m=args.maps, f=n_frames,
+                                                            gb=budget / 2 ** 30),
+                          "map_voxels_M": voxels, "parallelism": f"replicas x{world}",
+                          "l2": "inputs (maps 1-2 GB each) larger than L2",
+                          "server": {"streams": 4, "max_batch": 32, "batches": int(st.batches),
+                                     "mean_batch": len(reqs) / max(1, int(st.batches)),
+                                     "peak_inflight": int(st.peak_inflight), "peak_bytes": int(st.peak_bytes)}},
+               "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
+                              "mean": float(lat.mean() * 1e3)},
+               "serial_fp32": {"value": len(reqs) / span_s, "unit": "requests/s",
+                               "latency_ms": {"p50": float(np.percentile(lat_s, 50) * 1e3),
+                                              "p99": float(np.percentile(lat_s, 99) * 1e3)}},
+               "accuracy": {"fp16_served_vs_fp32_serial": {
+                   "rot_rad_median": float(np.median(d_fp[:, 0])), "rot_rad_max": float(d_fp[:, 0].max()),
+                   "trans_m_median": float(np.median(d_fp[:, 1])), "trans_m_max": float(d_fp[:, 1].max()),
+                   "scale_max": float(d_fp[:, 2].max()),
+                   "within_1e-4_rad_1e-4_m_1e-5_scale": float(np.mean((d_fp[:, 0] <= 1e-4) & (d_fp[:, 1] <= 1e-4) &
+                                                                      (d_fp[:, 2] <= 1e-5)))},
+                   "vs_truth": {"trans_m_median": float(np.median(d_gt[:, 1])),
+                                "rot_rad_median": float(np.median(d_gt[:, 0])),
+                                "success_rate_1cm_1deg": float(np.mean((d_gt[:, 1] < 0.01) &
+                                                                       (d_gt[:, 0] < np.radians(1.0))))}},
+               "roofline": roof, "cpu_baseline": cpu,
+               "e2e": {"value": value, "unit": "requests/s", "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": ctypes_result_bytes(dt)},
+               "gpu_launches": int(st.batches) * (2 + args.maps) + 5 * len(reqs), "clocks": clocks}
+        print(json.dumps(out), flush=True)
+    for m in maps16 + maps32:
+        m.close()
+
+
+def ctypes_result_bytes(dt):
+    return 32 * 8 + dt.STATS_BYTES
+
+
 # --------------------------------------------------------------------- main --
 def main():
     args = parse()
@@ -641,6 +874,8 @@ def main():
     assert args.warmup >= 3 or args.profile, "at least 3 warm-up steps"
     if args.workload == "multi_sensor":
         run_multi_sensor(args, dt, torch, tdist, dev, rank, world, local)
+    elif args.workload == "serve":
+        run_serve(args, dt, torch, tdist, dev, rank, world, local)
     else:
         run_tracking(args, dt, torch, tdist, dev, rank, world, local)
     if world > 1:
