@@ -183,8 +183,13 @@ __device__ __forceinline__ void atomic_min_float(float* addr, float v) {
 constexpr uint32_t OCC_BITS_LOG2 = 23;
 constexpr uint32_t OCC_WORDS = 1u << (OCC_BITS_LOG2 - 5);
 __host__ __device__ __forceinline__ uint32_t occ_bit(int bx, int by, int bz, int level) {
-  const unsigned long long k = pack_block(bx, by, bz) ^ (level ? 0x5bd1e9955bd1e995ull : 0ull);
-  return hash_slot(k, (1u << OCC_BITS_LOG2) - 1u);
+  // 32-bit multiplicative hash of the coordinates (cheap enough to test at every cell a ray enters)
+  uint32_t h = ((uint32_t)bx * 0x8da6b343u) ^ ((uint32_t)by * 0xd8163841u) ^ ((uint32_t)bz * 0xcb1ab31fu) ^
+               (level ? 0x5bd1e995u : 0u);
+  h ^= h >> 16;
+  h *= 0x7feb352du;
+  h ^= h >> 15;
+  return h & ((1u << OCC_BITS_LOG2) - 1u);
 }
 __device__ __forceinline__ void occ_set(const MapView& m, int bx, int by, int bz) {
   const uint32_t a = occ_bit(bx, by, bz, 0), b = occ_bit(bx >> 2, by >> 2, bz >> 2, 1);

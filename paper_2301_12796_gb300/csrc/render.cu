@@ -273,27 +273,32 @@ __device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, cons
 
 // Sign of Phi from the present directions' trilinear values (Phi is their convex combination).
 // Returns 0 undefined, 1 positive, -1 non-positive, 2 undecided (needs the full combination).
+// npres receives the number of present directions: with one present direction that faces
+// the ray (return value 1 or -1), Phi is that direction's value lo itself.
 template <int STORE, bool COUNT>
 __device__ __forceinline__ int sign_fast(const MapView& m, Cell& c, const float g[3], const float r[3], float& lo,
-                                         uint8_t* touched) {
+                                         int& npres, uint8_t* touched) {
   const float f0 = floorf(g[0]), f1 = floorf(g[1]), f2 = floorf(g[2]);
   const int g0 = (int)f0, g1 = (int)f1, g2 = (int)f2;
   const float fx = g[0] - f0, fy = g[1] - f1, fz = g[2] - f2;
   const int lofs = pad_index(g0 - 8 * c.cx, g1 - 8 * c.cy, g2 - 8 * c.cz);
   float mn = 2.f, mx = -2.f;
   bool any = false, facing = false;
+  int np = 0;
 #pragma unroll 1
   for (uint32_t mm = c.cmask; mm; mm &= mm - 1) {
     const int D = __ffs(mm) - 1;
     float phiD, WD;
     if (!interp<STORE, COUNT>(m, (size_t)c.slot[D * RT_N] * PVOX + lofs, fx, fy, fz, phiD, WD, touched)) continue;
     any = true;
+    ++np;
     mn = fminf(mn, phiD);
     mx = fmaxf(mx, phiD);
     const float vr = (D & 1) ? r[D >> 1] : -r[D >> 1];
     facing |= vr > 0.0f;
   }
   lo = mn;
+  npres = np;
   if (!any) return 0;
   if (!facing) return 2;
   if (mn > 0.0f) return 1;
@@ -335,7 +340,7 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
   bool alive = true;
   int state = S_DONE;
   int jb = 0, pix = 0, it = 0, k = 0, k1 = 0;
-  float r[3] = {0.f, 0.f, 0.f}, o[3] = {0.f, 0.f, 0.f}, rl = 1.f;
+  float r[3] = {0.f, 0.f, 0.f}, o[3] = {0.f, 0.f, 0.f}, ri[3] = {0.f, 0.f, 0.f}, rl = 1.f;
   bool prev_def = false;
   float prev_phi = 0.f;
   int hit_k = -1;
@@ -385,6 +390,8 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
             o[0] = T.t[0];
             o[1] = T.t[1];
             o[2] = T.t[2];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) ri[q] = r[q] != 0.f ? 1.0f / r[q] : 0.f;
             k1 = (int)floorf(m.zmax * rl / step);
             k = (int)ceilf(m.zmin * rl / step);
             state = S_MARCH;
@@ -446,16 +453,16 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
             if (r[q] > 0.f)
-              tex = fminf(tex, (org[q] + (cc[q] + 1) * cs - o[q]) / r[q]);
+              tex = fminf(tex, (org[q] + (cc[q] + 1) * cs - o[q]) * ri[q]);
             else if (r[q] < 0.f)
-              tex = fminf(tex, (org[q] + cc[q] * cs - o[q]) / r[q]);
+              tex = fminf(tex, (org[q] + cc[q] * cs - o[q]) * ri[q]);
           }
           if (COUNT) {
             ++n_cells;
             ++n_samples;
           }
           prev_def = false;
-          k = max(k + 1, (int)ceilf(tex / step));
+          k = max(k + 1, (int)ceilf(tex / step - 1e-3f));
           continue;
         }
       }
@@ -476,14 +483,14 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           if (r[q] > 0.f)
-            tex = fminf(tex, (org[q] + (cc[q] + 1) * bsz - o[q]) / r[q]);
+            tex = fminf(tex, (org[q] + (cc[q] + 1) * bsz - o[q]) * ri[q]);
           else if (r[q] < 0.f)
-            tex = fminf(tex, (org[q] + cc[q] * bsz - o[q]) / r[q]);
+            tex = fminf(tex, (org[q] + cc[q] * bsz - o[q]) * ri[q]);
         }
         if (empty) {
           if (COUNT) ++n_samples;
           prev_def = false;
-          k = max(k + 1, (int)ceilf(tex / step));
+          k = max(k + 1, (int)ceilf(tex / step - 1e-3f));
           continue;
         }
         cell.jumped = true;
@@ -504,10 +511,17 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
     C.defined = 0;
     C.wsum = 0.f;
     if (cell.cmask) {
-      bool full = state >= S_ENDS_A;
+      // the bracket ends need Phi's value: from the sign test when one facing direction is
+      // present, else from the full combination; the outputs always need the full combination
+      bool full = state >= S_OUT;
       if (!full) {
-        sg = sign_fast<STORE, COUNT>(m, cell, g, r, val, touched);
-        full = sg == 2;
+        int npres = 0;
+        sg = sign_fast<STORE, COUNT>(m, cell, g, r, val, npres, touched);
+        full = sg == 2 || (state >= S_ENDS_A && npres > 1);
+        if (!full && state >= S_ENDS_A) {
+          C.defined = sg != 0;
+          C.phi = val;
+        }
       }
       if (full) {
         if (COUNT && state == S_MARCH) ++n_full;
