@@ -137,15 +137,27 @@ DTSDF_API dtsdf_status dtsdf_render_dev(dtsdf_map map, const dtsdf_intrinsics* K
 
 /* Launch shape of the map's renders (no counterpart in the paper: scheduling only; every
  * shape computes the same samples, decisions and outputs). ctas: CTAs of the persistent
- * render grid, 0 = one wave of resident CTAs. lane_refill: 1 = a lane whose ray is finished
- * takes the next ray at once, 0 = a warp takes the next 8x4 tile of rays when all its lanes
- * have finished. Defaults {0, 0}. DTSDF_ERR_INVALID_ARG for ctas < 0 or lane_refill not 0/1. */
+ * render grid, 0 = one wave of resident CTAs. tile_w: width of the pixel tiles of 32 rays
+ * that the work is handed out in, 1, 2, 4, 8, 16 or 32 (0 = 4), the height being 32 / tile_w; a
+ * tile's rays go to the lanes of a warp row by row. refill: lanes per refill group, 1, 2, 4,
+ * 8, 16 or 32 (0 = 32): a group of `refill` consecutive lanes takes its next `refill` rays
+ * once all of its lanes have finished (32: the warp takes a whole tile; 1: a lane takes a ray
+ * as soon as it is free). Defaults {0, 0, 0}. DTSDF_ERR_INVALID_ARG for other values. */
 typedef struct {
   int32_t ctas;
-  int32_t lane_refill;
+  int32_t refill;
+  int32_t tile_w;
 } dtsdf_render_opts;
 
 DTSDF_API dtsdf_status dtsdf_set_render_opts(dtsdf_map map, const dtsdf_render_opts* opts);
+
+/* Autotuner of the render launch shape (no counterpart in the paper): times a render at T_wc
+ * (intrinsics K, outputs `out`, as dtsdf_render) with tile widths 2 to 32 and refill groups
+ * of 8, 16 or 32 lanes (ctas 0), keeps the fastest as the map's shape and returns it in *best
+ * and its time in *best_ms (host, may be NULL). Synchronous. */
+DTSDF_API dtsdf_status dtsdf_render_tune(dtsdf_map map, const dtsdf_intrinsics* K, const double T_wc[16],
+                                         const dtsdf_render_out* out, dtsdf_render_opts* best, float* best_ms,
+                                         void* stream);
 
 /* Instrumented render at T_wc that counts the distinct bricks the march reads: geometry
  * bricks (sdf + weight) and colour bricks. Defines the algorithmic bytes of a render for

@@ -47,7 +47,7 @@ class RenderOut(ctypes.Structure):
 
 
 class RenderOpts(ctypes.Structure):
-    _fields_ = [("ctas", c_int32), ("lane_refill", c_int32)]
+    _fields_ = [("ctas", c_int32), ("refill", c_int32), ("tile_w", c_int32)]
 
 
 class IcpProblem(ctypes.Structure):
@@ -119,6 +119,8 @@ SIGNATURES = {
     "dtsdf_render": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), P], c_int32),
     "dtsdf_render_dev": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), P], c_int32),
     "dtsdf_set_render_opts": ([P, ctypes.POINTER(RenderOpts)], c_int32),
+    "dtsdf_render_tune": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), ctypes.POINTER(RenderOpts),
+                           ctypes.POINTER(ctypes.c_float), P], c_int32),
     "dtsdf_render_touched": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64),
                               P, P], c_int32),
     "dtsdf_pose_compose": ([P, c_int32, P, P, P], c_int32),
@@ -256,11 +258,23 @@ class Map:
                                RenderOut(depth.data_ptr(), normals.data_ptr(), None if color is None else color.data_ptr()))
         check(lib().dtsdf_render_batch(self._h, arr, len(jobs), _stream_ptr(stream)), "dtsdf_render_batch")
 
-    def set_render_opts(self, ctas: int = 0, lane_refill: bool = False):
-        """Launch shape of this map's renders: persistent CTAs (0 = one resident wave) and the
-        refill policy of finished lanes. Every shape gives the same outputs."""
-        o = RenderOpts(int(ctas), int(bool(lane_refill)))
+    def set_render_opts(self, ctas: int = 0, refill: int = 0, tile_w: int = 0):
+        """Launch shape of this map's renders: persistent CTAs (0 = one resident wave), lanes per
+        refill group (1, 2, 4, 8, 16, 32; 0 = 32) and the width of the 32-ray pixel tiles (1, 2, 4,
+        8, 16, 32; 0 = 4). Every shape gives the same outputs."""
+        o = RenderOpts(int(ctas), int(refill), int(tile_w))
         check(lib().dtsdf_set_render_opts(self._h, ctypes.byref(o)), "dtsdf_set_render_opts")
+
+    def tune_render(self, K, T_wc, depth, normals, color=None, stream=None):
+        """Time every render launch shape at T_wc, keep the fastest; returns ((ctas, refill,
+        tile_w), ms)."""
+        out = RenderOut(depth.data_ptr(), normals.data_ptr(), None if color is None else color.data_ptr())
+        Ki = intrinsics(K)
+        best = RenderOpts()
+        ms = ctypes.c_float()
+        check(lib().dtsdf_render_tune(self._h, ctypes.byref(Ki), pose_buf(T_wc), ctypes.byref(out), ctypes.byref(best),
+                                      ctypes.byref(ms), _stream_ptr(stream)), "dtsdf_render_tune")
+        return (best.ctas, best.refill, best.tile_w), ms.value
 
     def touched(self, K, T_wc, stream=None, counters=False):
         """(geometry bricks, colour bricks) read by one render at T_wc; with counters=True also

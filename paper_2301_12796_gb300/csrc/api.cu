@@ -368,10 +368,60 @@ dtsdf_status dtsdf_render_dev(dtsdf_map m, const dtsdf_intrinsics* K, const doub
 }
 
 dtsdf_status dtsdf_set_render_opts(dtsdf_map m, const dtsdf_render_opts* o) {
-  if (!m || !o || o->ctas < 0 || (o->lane_refill != 0 && o->lane_refill != 1))
+  const int g = o ? o->refill : 0, tw = o ? o->tile_w : 0;
+  if (!m || !o || o->ctas < 0 || !(g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32) ||
+      !(tw == 0 || tw == 1 || tw == 2 || tw == 4 || tw == 8 || tw == 16 || tw == 32))
     return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
   m->shape.ctas = o->ctas;
-  m->shape.lane_refill = o->lane_refill;
+  m->shape.refill = g ? g : 32;
+  m->shape.tile_w = tw ? tw : 4;
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_render_tune(dtsdf_map m, const dtsdf_intrinsics* K, const double T_wc[16],
+                               const dtsdf_render_out* out, dtsdf_render_opts* best, float* best_ms, void* stream) {
+  if (!m || !intr_ok(K) || !pose_ok(T_wc) || !out || !out->depth || !out->normals || !best)
+    return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  cudaError_t e = cudaEventCreate(&e1);
+  const RenderShape keep = m->shape;
+  RenderShape bs = keep;
+  float bt = 3.4e38f;
+  const int widths[5] = {2, 4, 8, 16, 32}, groups[3] = {8, 16, 32};
+  const Pose32 T = to_pose32(T_wc);
+  for (int wi = 0; wi < 5 && e == cudaSuccess; ++wi)
+    for (int gi = 0; gi < 3 && e == cudaSuccess; ++gi) {
+      m->shape.ctas = 0;
+      m->shape.tile_w = widths[wi];
+      m->shape.refill = groups[gi];
+      float best_rep = 3.4e38f;
+      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess && render_launch(m, *K, T, nullptr, out, s, nullptr) != DTSDF_OK) e = cudaErrorUnknown;
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && rep > 0 && ms < best_rep) best_rep = ms;  // the first run warms up
+      }
+      if (e == cudaSuccess && best_rep < bt) {
+        bt = best_rep;
+        bs = m->shape;
+      }
+    }
+  cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    m->shape = keep;
+    return cuda_fail(e, "dtsdf_render_tune");
+  }
+  m->shape = bs;
+  best->ctas = bs.ctas;
+  best->refill = bs.refill;
+  best->tile_w = bs.tile_w;
+  if (best_ms) *best_ms = bt;
   return DTSDF_OK;
 }
 

@@ -71,15 +71,17 @@ struct RenderBatch {
   unsigned* queue;
   uint8_t* touched;  // instrumentation build only (brick flags + counters), else null
   int max_samples;
-  int lane_refill;   // 1: a finished lane takes the next ray; 0: a warp takes a tile when all lanes finish
+  int refill;        // lanes per refill group (1 .. 32): a group takes new rays when all its lanes finish
+  int tile_w;        // pixel tile of 32 rays: tile_w x (32 / tile_w)
 };
 
-// Launch shape of a render: persistent CTAs (0 = one wave of resident CTAs) and the refill
-// policy of finished lanes (1: take the next ray at once; 0: the warp takes a new tile when
-// all its lanes have finished).
+// Launch shape of a render: persistent CTAs (0 = one wave of resident CTAs), the lanes per
+// refill group (a group of consecutive lanes takes new rays when all of them have finished)
+// and the width of the 32-ray pixel tiles (1, 2, 4, 8, 16 or 32).
 struct RenderShape {
   int ctas = 0;
-  int lane_refill = 0;
+  int refill = 32;
+  int tile_w = 4;
 };
 
 // Render njobs (1..MAX_RENDER_JOBS) frames in one persistent launch.

@@ -311,9 +311,8 @@ __device__ __forceinline__ int sign_fast(const MapView& m, Cell& c, const float 
 // the output evaluations (OUT) all evaluate the field at one call site of the sign test
 // and one of the full combination, so lanes in different phases stay converged. A lane
 // whose ray is finished (DONE) takes the next ray from the launch's work counter at the
-// top of the loop, so a warp stays full until the work runs out: rays of very different
-// lengths (grazing rays cross long stretches of allocated band) do not hold a warp, or a
-// CTA, on one slow lane.
+// top of the loop once its refill group has finished. Work items are the pixels of tiles of
+// 32 rays (tile_w x 32 / tile_w pixels), handed out tile after tile.
 enum { S_MARCH = 0, S_SCAN = 1, S_ENDS_A = 2, S_ENDS_B = 3, S_OUT = 4, S_DONE = 5 };
 
 template <int STORE, bool COLOR, bool COUNT, int NJ>
@@ -353,13 +352,15 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
   float4 out_c = make_float4(0.f, 0.f, 0.f, 0.f);
 
   for (;;) {
-    // ---- lanes without a ray take the next work items (warp-aggregated atomic)
-    const bool need = alive && state == S_DONE;
+    // ---- lanes without a ray take the next work items (warp-aggregated atomic). A group of
+    // a.refill consecutive lanes takes new rays once all of its lanes have finished: 32 keeps
+    // the warp on one 8x4 tile (coherent, but lanes wait for the slowest), smaller groups take
+    // rows of a tile, 1 lets every lane take a ray as soon as it is free
+    const unsigned busym = __ballot_sync(0xffffffffu, alive && state != S_DONE);
+    const unsigned gmask = a.refill >= 32 ? 0xffffffffu : (((1u << a.refill) - 1u) << (lane & ~(a.refill - 1)));
+    const bool need = alive && state == S_DONE && (busym & gmask) == 0;
     const unsigned nm = __ballot_sync(0xffffffffu, need);
-    // lane refill: any finished lane takes a new ray; warp refill: the warp takes a new tile
-    // of 32 rays once every lane has finished (coherent, but lanes wait for the slowest)
-    const bool busy = __any_sync(0xffffffffu, alive && state != S_DONE);
-    if (nm && (a.lane_refill || !busy)) {
+    if (nm) {
       const int leader = __ffs(nm) - 1;
       unsigned base = 0;
       if (lane == leader) base = atomicAdd(a.queue, (unsigned)__popc(nm));
@@ -375,8 +376,8 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
           const RenderJob& J = a.job[jb];
           const int loc = (int)(item - (unsigned)J.start);
           const int tile = loc >> 5, w = loc & 31;
-          const int u = (tile % J.tiles_x) * 8 + (w & 7);
-          const int v = (tile / J.tiles_x) * 4 + (w >> 3);
+          const int u = (tile % J.tiles_x) * a.tile_w + (w & (a.tile_w - 1));
+          const int v = (tile / J.tiles_x) * (32 / a.tile_w) + (w / a.tile_w);
           if (u < J.K.W && v < J.K.H) {
             pix = v * J.K.W + u;
             const Pose32& T = s_pose[jb];
@@ -663,18 +664,20 @@ void dispatch_render(const MapView& m, const RenderBatch<NJ>& a, bool col, int c
 
 template <int NJ>
 void fill_batch(RenderBatch<NJ>& a, const RenderJob* jobs, int njobs, unsigned* queue, uint8_t* touched,
-                int lane_refill) {
+                int refill, int tile_w) {
   a.njobs = njobs;
   a.queue = queue;
   a.touched = touched;
   a.max_samples = 1 << 17;
-  a.lane_refill = lane_refill;
+  a.refill = refill;
+  a.tile_w = tile_w;
+  const int tile_h = 32 / tile_w;
   int start = 0;
   for (int i = 0; i < njobs; ++i) {
     a.job[i] = jobs[i];
-    a.job[i].tiles_x = (jobs[i].K.W + 7) / 8;
+    a.job[i].tiles_x = (jobs[i].K.W + tile_w - 1) / tile_w;
     a.job[i].start = start;
-    start += a.job[i].tiles_x * ((jobs[i].K.H + 3) / 4) * 32;
+    start += a.job[i].tiles_x * ((jobs[i].K.H + tile_h - 1) / tile_h) * 32;
   }
   a.total = start;
 }
@@ -683,17 +686,17 @@ void fill_batch(RenderBatch<NJ>& a, const RenderJob* jobs, int njobs, unsigned* 
 
 void launch_render_jobs(const MapView& m, const RenderJob* jobs, int njobs, unsigned* queue, cudaStream_t s,
                         uint8_t* touched, const RenderShape& sh) {
-  const int ctas = sh.ctas, lane_refill = sh.lane_refill;
+  const int ctas = sh.ctas, refill = sh.refill, tile_w = sh.tile_w;
   bool col = false;
   for (int i = 0; i < njobs; ++i) col |= jobs[i].color != nullptr;
   col &= m.color != 0;
   if (njobs == 1) {
     RenderBatch<1> a;
-    fill_batch(a, jobs, njobs, queue, touched, lane_refill);
+    fill_batch(a, jobs, njobs, queue, touched, refill, tile_w);
     dispatch_render(m, a, col, ctas, s);
   } else {
     RenderBatch<MAX_RENDER_JOBS> a;
-    fill_batch(a, jobs, njobs, queue, touched, lane_refill);
+    fill_batch(a, jobs, njobs, queue, touched, refill, tile_w);
     dispatch_render(m, a, col, ctas, s);
   }
 }

@@ -200,3 +200,34 @@ def test_batch_captured_in_a_cuda_graph(probs):
         got = [it[3] for it in items] + [d for d, _ in outs]
         for a, b in zip(got, eager):
             assert torch.equal(a, b)
+
+
+def test_render_launch_shapes_give_identical_outputs():
+    """Tile width and refill group only schedule the rays: every shape gives the same bits,
+    and the autotuner keeps one of them as the map's shape."""
+    s, gm = _tiny_map()
+    K = s.K
+    T = s.poses[4] @ scenes.perturbation(np.random.default_rng(7), 1.0, 0.005)
+    def render():
+        d = torch.zeros(K.height, K.width, device=DEV)
+        n = torch.zeros(K.height, K.width, 4, device=DEV)
+        c = torch.zeros(K.height, K.width, 4, device=DEV)
+        gm.render(K, T, d, n, c)
+        torch.cuda.synchronize()
+        return d, n, c
+    ref = render()
+    assert (ref[0] > 0).float().mean() > 0.5
+    for ctas, refill, tile_w in [(0, 32, 8), (0, 32, 2), (0, 16, 16), (0, 8, 32), (0, 1, 1), (7, 32, 4)]:
+        gm.set_render_opts(ctas, refill, tile_w)
+        got = render()
+        for a, b in zip(got, ref):
+            assert torch.equal(a, b), (ctas, refill, tile_w)
+    d, n, c = render()
+    (ctas, refill, tile_w), ms = gm.tune_render(K, T, d, n, c)
+    assert refill in (8, 16, 32) and tile_w in (2, 4, 8, 16, 32) and ms > 0
+    for a, b in zip(render(), ref):
+        assert torch.equal(a, b)
+    with pytest.raises(dt.DtsdfError):
+        gm.set_render_opts(0, 3, 8)
+    with pytest.raises(dt.DtsdfError):
+        gm.set_render_opts(0, 32, 12)
