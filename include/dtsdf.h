@@ -127,7 +127,10 @@ DTSDF_API dtsdf_status dtsdf_integrate_dev(dtsdf_map map, const dtsdf_frame* fra
 /* Ray-cast depth, normals and colour at pose T_wc with intrinsics K (Sec. 4): per pixel,
  * march the combined SDF of Eq. combine_weight (fallback Eq. combine_tsdf_weight) along
  * the ray from z_min to z_max, find the first positive-to-negative crossing between
- * consecutive samples of the h/2 grid and refine it. Asynchronous. */
+ * consecutive samples of the h/2 grid and refine it. A pre-pass records per tile of 32 rays
+ * the depth range of the allocated blocks in view, and each ray marches only that range
+ * (outside it no sample can be defined). Asynchronous; the pre-pass scratch (8 bytes per ray
+ * tile) is stream-ordered memory from a pool the map keeps cached. */
 DTSDF_API dtsdf_status dtsdf_render(dtsdf_map map, const dtsdf_intrinsics* K, const double T_wc[16],
                           const dtsdf_render_out* out, void* stream);
 
@@ -333,7 +336,9 @@ typedef struct {
 
 /* Ray-cast n frames of any sizes (Sec. 4, as dtsdf_render) in one persistent launch per 64
  * frames: the pixels of all frames form one work list that the CTAs take in 8x4 tiles, so
- * uneven frames share the GPU without a tail per frame. Asynchronous, allocates nothing. */
+ * uneven frames share the GPU without a tail per frame. Asynchronous; its scratch (as for
+ * dtsdf_render) is stream-ordered memory from the map's pool, so the call can be captured in a
+ * CUDA graph. */
 DTSDF_API dtsdf_status dtsdf_render_batch(dtsdf_map map, const dtsdf_render_job* jobs, int32_t n, void* stream);
 
 /* ------------------------------------------------------------- serving ---- */

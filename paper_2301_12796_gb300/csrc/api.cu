@@ -111,6 +111,8 @@ struct dtsdf_map_s {
   unsigned* render_q = nullptr;
   std::atomic<uint32_t> render_q_next{0};
   RenderShape shape;
+  // stream-ordered scratch of render launches (per-tile depth ranges), kept cached in the pool
+  cudaMemPool_t pool = nullptr;
 };
 
 constexpr uint32_t RENDER_Q_SLOTS = 1024;
@@ -137,6 +139,7 @@ static void map_free(dtsdf_map m) {
   cudaFree(m->N);
   if (m->err_host) cudaFreeHost(m->err_host);
   if (m->err_event) cudaEventDestroy(m->err_event);
+  if (m->pool) cudaMemPoolDestroy(m->pool);
   delete m;
 }
 
@@ -157,8 +160,7 @@ static dtsdf_status render_launch(dtsdf_map m, const dtsdf_intrinsics& K, const 
   J.depth = out->depth;
   J.normals = (float4*)out->normals;
   J.color = (float4*)out->color;
-  launch_render_jobs(m->v, &J, 1, q, s, touched, m->shape);
-  CK_LAUNCH("render");
+  CK(launch_render_jobs(m->v, &J, 1, q, s, touched, m->shape, m->pool));
   return DTSDF_OK;
 }
 
@@ -236,6 +238,18 @@ dtsdf_status dtsdf_create(const dtsdf_params* params, void* stream, dtsdf_map* o
   ALLOC(m->render_q, sizeof(unsigned) * RENDER_Q_SLOTS);
 #undef ALLOC
   if (e == cudaSuccess) e = cudaMallocHost((void**)&m->err_host, sizeof(uint32_t));
+  if (e == cudaSuccess) {
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    cudaMemPoolProps pp;
+    memset(&pp, 0, sizeof(pp));
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = dev;
+    if (e == cudaSuccess) e = cudaMemPoolCreate(&m->pool, &pp);
+    uint64_t keep = ~0ull;  // keep freed scratch cached for the next render
+    if (e == cudaSuccess) e = cudaMemPoolSetAttribute(m->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->err_event, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     map_free(m);
@@ -452,8 +466,7 @@ dtsdf_status dtsdf_render_touched(dtsdf_map m, const dtsdf_intrinsics* K, const 
       J.depth = depth;
       J.normals = nrm;
       J.color = col;
-      launch_render_jobs(m->v, &J, 1, q, s, flags, m->shape);
-      e = cudaGetLastError();
+      e = launch_render_jobs(m->v, &J, 1, q, s, flags, m->shape, m->pool);
     }
   }
   uint8_t* host = nullptr;
@@ -945,8 +958,7 @@ dtsdf_status dtsdf_render_batch(dtsdf_map m, const dtsdf_render_job* jobs, int32
     }
     unsigned* q = render_slot(m);
     CK(cudaMemsetAsync(q, 0, sizeof(unsigned), s));
-    launch_render_jobs(m->v, J, k, q, s, nullptr, m->shape);
-    CK_LAUNCH("render_batch");
+    CK(launch_render_jobs(m->v, J, k, q, s, nullptr, m->shape, m->pool));
   }
   return DTSDF_OK;
 }

@@ -73,6 +73,10 @@ struct RenderBatch {
   int max_samples;
   int refill;        // lanes per refill group (1 .. 32): a group takes new rays when all its lanes finish
   int tile_w;        // pixel tile of 32 rays: tile_w x (32 / tile_w)
+  // camera-depth range per ray tile (bit patterns of non-negative floats) of the allocated
+  // blocks whose box covers one of the tile's pixels; zlo = 0xFFFFFFFF: no block. Null: none.
+  const uint32_t* zlo;
+  const uint32_t* zhi;
 };
 
 // Launch shape of a render: persistent CTAs (0 = one wave of resident CTAs), the lanes per
@@ -84,9 +88,11 @@ struct RenderShape {
   int tile_w = 4;
 };
 
-// Render njobs (1..MAX_RENDER_JOBS) frames in one persistent launch.
-void launch_render_jobs(const MapView& m, const RenderJob* jobs, int njobs, unsigned* queue, cudaStream_t s,
-                        uint8_t* touched, const RenderShape& shape);
+// Render njobs (1..MAX_RENDER_JOBS) frames in one persistent launch. With a memory pool, a
+// pre-pass first records per ray tile the depth range of the allocated blocks in view
+// (stream-ordered scratch from `pool`), so rays start and end their march there.
+cudaError_t launch_render_jobs(const MapView& m, const RenderJob* jobs, int njobs, unsigned* queue, cudaStream_t s,
+                               uint8_t* touched, const RenderShape& shape, cudaMemPool_t pool);
 void launch_frame_pyramid(const float4* P, const uint8_t* rgb, int levels, const Intr* K, float* const* depth,
                           float* const* inten, cudaStream_t s);
 void launch_keyframe_pyramid(const uint8_t* rgb, int levels, const Intr* K, float* const* tmpI, float4* const* kf,

@@ -380,6 +380,8 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
           const int v = (tile / J.tiles_x) * (32 / a.tile_w) + (w / a.tile_w);
           if (u < J.K.W && v < J.K.H) {
             pix = v * J.K.W + u;
+            int zt = -1;
+            if (a.zlo) zt = (J.start >> 5) + tile;
             const Pose32& T = s_pose[jb];
             // unit ray in camera and world frame
             const float rc0 = (u - J.K.cx) / J.K.fx, rc1 = (v - J.K.cy) / J.K.fy;
@@ -395,6 +397,17 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
             for (int q = 0; q < 3; ++q) ri[q] = r[q] != 0.f ? 1.0f / r[q] : 0.f;
             k1 = (int)floorf(m.zmax * rl / step);
             k = (int)ceilf(m.zmin * rl / step);
+            if (zt >= 0) {
+              // no sample outside the tile's block depth range lies in a cell with an active
+              // direction: start and end the march there (one sample of margin on each side)
+              const uint32_t lo = a.zlo[zt], hi = a.zhi[zt];
+              if (lo == 0xFFFFFFFFu) {
+                k1 = k - 1;
+              } else {
+                k = max(k, (int)floorf(__uint_as_float(lo) * rl / step) - 1);
+                k1 = min(k1, (int)ceilf(__uint_as_float(hi) * rl / step) + 1);
+              }
+            }
             state = S_MARCH;
             it = 0;
             prev_def = false;
@@ -614,6 +627,79 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
   }
 }
 
+// Depth ranges of the ray tiles: every allocated block with a direction holding weighted voxels
+// (brick bound < inf) projects the 8 corners of its cell box [8 b, 8 b + 8) h into each frame;
+// the ray tiles covering its pixel bounding box (grown by half a pixel) take the minimum and
+// maximum camera depth of its corners. A box reaching behind the camera covers the whole frame
+// from depth 0. Floats are non-negative, so their bit patterns order like unsigned integers.
+template <int NJ>
+__global__ void __launch_bounds__(256) k_tile_range(MapView m, RenderBatch<NJ> a, uint32_t* zlo, uint32_t* zhi) {
+  __shared__ Pose32 s_pose[NJ];
+  for (int jb = threadIdx.x; jb < a.njobs; jb += blockDim.x)
+    s_pose[jb] = a.job[jb].Tdev ? pose_from_device(a.job[jb].Tdev) : a.job[jb].T;
+  __syncthreads();
+  const uint32_t ndir = min(*((volatile uint32_t*)(m.counters + C_DIR)), m.dir_cap);
+  const float bs = 8.0f * m.h;
+  const int th = 32 / a.tile_w;
+  for (uint32_t d = blockIdx.x * blockDim.x + threadIdx.x; d < ndir; d += gridDim.x * blockDim.x) {
+    const uint32_t mask = (uint32_t)__ldg(m.dir_slots + (size_t)d * 8 + SLOT_MASK);
+    bool act = false;
+    for (uint32_t mm = mask; mm; mm &= mm - 1) {
+      const int sl = __ldg(m.dir_slots + (size_t)d * 8 + (__ffs(mm) - 1));
+      act |= sl >= 0 && __ldg(m.bound + sl) < INFINITY;
+    }
+    if (!act) continue;
+    const float x0 = m.ox + (float)__ldg(m.dir_coord + 4 * d) * bs;
+    const float y0 = m.oy + (float)__ldg(m.dir_coord + 4 * d + 1) * bs;
+    const float z0 = m.oz + (float)__ldg(m.dir_coord + 4 * d + 2) * bs;
+    for (int jb = 0; jb < a.njobs; ++jb) {
+      const Pose32& T = s_pose[jb];
+      const RenderJob& J = a.job[jb];
+      float zmin = 3.4e38f, zmax = 0.0f, umin = 3.4e38f, umax = -3.4e38f, vmin = 3.4e38f, vmax = -3.4e38f;
+      bool behind = false;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float px = x0 + ((c & 1) ? bs : 0.f) - T.t[0];
+        const float py = y0 + ((c & 2) ? bs : 0.f) - T.t[1];
+        const float pz = z0 + ((c & 4) ? bs : 0.f) - T.t[2];
+        const float xc = T.R[0] * px + T.R[3] * py + T.R[6] * pz;
+        const float yc = T.R[1] * px + T.R[4] * py + T.R[7] * pz;
+        const float zc = T.R[2] * px + T.R[5] * py + T.R[8] * pz;
+        zmin = fminf(zmin, zc);
+        zmax = fmaxf(zmax, zc);
+        if (zc < 1e-4f) {
+          behind = true;
+        } else {
+          const float u = J.K.fx * xc / zc + J.K.cx, v = J.K.fy * yc / zc + J.K.cy;
+          umin = fminf(umin, u);
+          umax = fmaxf(umax, u);
+          vmin = fminf(vmin, v);
+          vmax = fmaxf(vmax, v);
+        }
+      }
+      if (zmax < 1e-4f || zmin > m.zmax || zmax < m.zmin) continue;
+      int u0 = 0, u1 = J.K.W - 1, v0 = 0, v1 = J.K.H - 1;
+      if (behind) {
+        zmin = 0.0f;
+      } else {
+        u0 = max(u0, (int)floorf(umin - 0.5f));
+        u1 = min(u1, (int)ceilf(umax + 0.5f));
+        v0 = max(v0, (int)floorf(vmin - 0.5f));
+        v1 = min(v1, (int)ceilf(vmax + 0.5f));
+        if (u0 > u1 || v0 > v1) continue;
+      }
+      const uint32_t lo = __float_as_uint(fmaxf(zmin, 0.0f)), hi = __float_as_uint(zmax);
+      const int base = J.start >> 5;
+      for (int ty = v0 / th; ty <= v1 / th; ++ty)
+        for (int tx = u0 / a.tile_w; tx <= u1 / a.tile_w; ++tx) {
+          const int i = base + ty * J.tiles_x + tx;
+          atomicMin(zlo + i, lo);
+          atomicMax(zhi + i, hi);
+        }
+    }
+  }
+}
+
 namespace {
 
 // CTAs of the persistent render grid that fit on the device at once (per kernel instance).
@@ -684,8 +770,41 @@ void fill_batch(RenderBatch<NJ>& a, const RenderJob* jobs, int njobs, unsigned* 
 
 }  // namespace
 
-void launch_render_jobs(const MapView& m, const RenderJob* jobs, int njobs, unsigned* queue, cudaStream_t s,
-                        uint8_t* touched, const RenderShape& sh) {
+// Depth-range pre-pass into stream-ordered scratch from the pool, then the render. The
+// scratch is freed on the stream after the render, so concurrent launches never share it.
+template <int NJ>
+cudaError_t range_and_render(const MapView& m, RenderBatch<NJ>& a, bool col, int ctas, cudaStream_t s,
+                             cudaMemPool_t pool) {
+  uint32_t* buf = nullptr;
+  const size_t ntiles = (size_t)a.total / 32;
+  a.zlo = a.zhi = nullptr;
+  if (pool && ntiles) {
+    cudaError_t e = cudaMallocFromPoolAsync((void**)&buf, 2 * ntiles * sizeof(uint32_t), pool, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(buf, 0xFF, ntiles * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(buf + ntiles, 0, ntiles * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    static thread_local int sms = 0;
+    if (!sms) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 132;
+    }
+    k_tile_range<NJ><<<sms * 4, 256, 0, s>>>(m, a, buf, buf + ntiles);
+    a.zlo = buf;
+    a.zhi = buf + ntiles;
+  }
+  dispatch_render(m, a, col, ctas, s);
+  cudaError_t e = cudaGetLastError();
+  if (buf) {
+    const cudaError_t f = cudaFreeAsync(buf, s);
+    if (e == cudaSuccess) e = f;
+  }
+  return e;
+}
+
+cudaError_t launch_render_jobs(const MapView& m, const RenderJob* jobs, int njobs, unsigned* queue, cudaStream_t s,
+                               uint8_t* touched, const RenderShape& sh, cudaMemPool_t pool) {
   const int ctas = sh.ctas, refill = sh.refill, tile_w = sh.tile_w;
   bool col = false;
   for (int i = 0; i < njobs; ++i) col |= jobs[i].color != nullptr;
@@ -693,12 +812,11 @@ void launch_render_jobs(const MapView& m, const RenderJob* jobs, int njobs, unsi
   if (njobs == 1) {
     RenderBatch<1> a;
     fill_batch(a, jobs, njobs, queue, touched, refill, tile_w);
-    dispatch_render(m, a, col, ctas, s);
-  } else {
-    RenderBatch<MAX_RENDER_JOBS> a;
-    fill_batch(a, jobs, njobs, queue, touched, refill, tile_w);
-    dispatch_render(m, a, col, ctas, s);
+    return range_and_render(m, a, col, ctas, s, pool);
   }
+  RenderBatch<MAX_RENDER_JOBS> a;
+  fill_batch(a, jobs, njobs, queue, touched, refill, tile_w);
+  return range_and_render(m, a, col, ctas, s, pool);
 }
 
 }  // namespace dtsdf
