@@ -127,6 +127,23 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "of fallback"
 
 
+# ------------------------------------------------------------ replicas ---
+def max_over_ranks(ms: float, tdist, world: int, dev) -> float:
+    """The slowest rank's time: every rank runs its own replica of the workload (the path has
+    no exchange step), and the job's time is the maximum over ranks."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank: float, total_ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / (total_ms / 1000.0)
+
+
 # ---------------------------------------------------------------- workload ---
 def make_workload(n_frames: int):
     import scenes
@@ -336,13 +353,9 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
     clocks = clk.stop()
     ph = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])] for e in evs])
     step_ms = ph.sum(1)
-    total_ms = float(step_ms.sum())
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(step_ms.sum()), tdist, world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1000.0)
+    value = job_throughput(world, args.steps, total_ms)
     launches = tr.launches
     # pose error of the tracked frames against ground truth (sanity, not a parity claim)
     est = tr.est.cpu().numpy()
@@ -557,13 +570,9 @@ def run_multi_sensor(args, dt, torch, tdist, dev, rank, world, local):
     if world > 1:
         tdist.barrier()
     clocks = clk.stop()
-    total_ms = float(sum(a.elapsed_time(b) for a, b in evs))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(a.elapsed_time(b) for a, b in evs)), tdist, world, dev)
     n = ms.n
-    value = world * n * args.steps / (total_ms / 1000.0)
+    value = job_throughput(world, n * args.steps, total_ms)
     rot, tr, sc = ms.errors()
     # e2e through host buffers: sensor-B depth frames from pinned memory, poses read back
     e2e = None
