@@ -6,8 +6,8 @@
 // (and photometric row) in registers, accumulates w J J^T (upper triangle), w J r, w r^2
 // and the row counts in FP32, reduces them by warp shuffles and across warps in a fixed
 // order, and stores one partial per CTA. The last CTA to finish (atomic ticket) adds the
-// partials in FP64 in CTA order - so the result is bitwise reproducible - then one
-// thread solves H xi = -g by FP64 Cholesky and applies dT <- exp(xi) dT on the device.
+// partials in FP64 in a fixed order - so the result is bitwise reproducible - then one
+// warp solves H xi = -g by FP64 Cholesky and applies dT <- exp(xi) dT on the device.
 #include <math.h>
 
 #include <cooperative_groups.h>
@@ -89,7 +89,10 @@ __device__ void mat4_mul(const double* A, const double* B, double* C) {
 //   V = A I + B omega^ + C omega^2, A = int_0^1 e^{s sigma} ds,
 //   B = (1/th) int_0^1 e^{s sigma} sin(s th) ds, C = (1/th^2) (A - int_0^1 e^{s sigma} cos(s th) ds),
 // with series where th or sigma vanish.
-__host__ __device__ void exp_sim3(const double* xi, int dim, double* T) {
+// The transcendental values sin(th), cos(th), e^sigma and e^sigma - 1 (th = |omega|) are
+// passed in, so that a warp can evaluate them in parallel lanes.
+__host__ __device__ void exp_sim3_from(const double* xi, int dim, double sin_th, double cos_th, double es, double em1,
+                                       double* T) {
   const double nu0 = xi[0], nu1 = xi[1], nu2 = xi[2];
   const double w0 = xi[3], w1 = xi[4], w2 = xi[5];
   const double sg = dim == 7 ? xi[6] : 0.0;
@@ -100,11 +103,10 @@ __host__ __device__ void exp_sim3(const double* xi, int dim, double* T) {
     a = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
     b = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
   } else {
-    a = sin(th) / th;
-    b = (1.0 - cos(th)) / th2;
+    a = sin_th / th;
+    b = (1.0 - cos_th) / th2;
   }
-  const double es = exp(sg);
-  const double A = sg != 0.0 ? expm1(sg) / sg : 1.0;
+  const double A = sg != 0.0 ? em1 / sg : 1.0;
   double B, C;
   if (th < 1e-4) {
     // expansions of the integrals in th (exact in sigma), leading orders
@@ -130,8 +132,8 @@ __host__ __device__ void exp_sim3(const double* xi, int dim, double* T) {
     C = I2;
   } else {
     const double D = sg * sg + th2;
-    const double Is = (es * (sg * sin(th) - th * cos(th)) + th) / D;
-    const double Ic = (es * (sg * cos(th) + th * sin(th)) - sg) / D;
+    const double Is = (es * (sg * sin_th - th * cos_th) + th) / D;
+    const double Ic = (es * (sg * cos_th + th * sin_th) - sg) / D;
     B = Is / th;
     C = (A - Ic) / th2;
   }
@@ -154,6 +156,12 @@ __host__ __device__ void exp_sim3(const double* xi, int dim, double* T) {
   T[15] = 1.0;
 }
 
+__host__ __device__ void exp_sim3(const double* xi, int dim, double* T) {
+  const double th = sqrt(xi[3] * xi[3] + xi[4] * xi[4] + xi[5] * xi[5]);
+  const double sg = dim == 7 ? xi[6] : 0.0;
+  exp_sim3_from(xi, dim, sin(th), cos(th), exp(sg), expm1(sg), T);
+}
+
 __global__ void k_exp(int dim, const double* xi, double* T) { exp_sim3(xi, dim, T); }
 
 // Solve and update of one Gauss-Newton iteration from the FP64 sums (layout of Acc<DIM>:
@@ -163,87 +171,135 @@ __global__ void k_exp(int dim, const double* xi, double* T) { exp_sim3(xi, dim, 
 // min_rows rows, is a degenerate system), then pose <- exp(xi) pose (Eq. deltaT_update).
 // Records the iteration in *st. Returns true when the level is finished (converged:
 // ||xi|| < stop_norm, or degenerate: pose unchanged).
+// Run by the 32 lanes of one warp (every lane calls it with the same sums; FP64
+// throughout). The FP64 units are few, so what bounds this step is the length of its
+// dependent chains: the Cholesky factor is formed column by column with the trailing update
+// spread over the lanes, the triangular solves column-oriented, the sine, cosine and
+// exponentials of the exponential map in separate lanes and the pose product one entry per
+// lane. Every lane returns the same level decision.
 template <int DIM>
-__device__ bool icp_solve_update(const double* sum, int dsolve, double* pose, dtsdf_icp_stats* st, int min_rows,
-                                 double stop_norm) {
+__device__ bool icp_solve_update_warp(const double* sum, int dsolve, double* pose, dtsdf_icp_stats* st,
+                                      int min_rows, double stop_norm) {
   constexpr int NH = DIM * (DIM + 1) / 2;
   constexpr int N = NH + DIM + 3;
-  double H[7][7], g[7];
-  {
-    int k = 0;
-    for (int i = 0; i < DIM; ++i)
-      for (int j = i; j < DIM; ++j) {
-        H[i][j] = H[j][i] = sum[k++];
-      }
-    for (int i = 0; i < DIM; ++i) g[i] = sum[NH + i];
-  }
+  __shared__ double sL[7][8];
+  __shared__ double sb[8];
+  __shared__ double sE[16];
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
   const int D = dsolve;
-  for (int i = 0; i < 49; ++i) st->H[i] = 0.0;
-  for (int i = 0; i < D; ++i)
-    for (int j = 0; j < D; ++j) st->H[7 * i + j] = H[i][j];
-  for (int i = 0; i < 7; ++i) {
-    st->g[i] = i < D ? g[i] : 0.0;
-    st->xi[i] = 0.0;
+  for (int k = lane; k < NH; k += 32) {
+    int i = 0, r = k;  // entry k of the row-major upper triangle
+    while (r >= DIM - i) {
+      r -= DIM - i;
+      ++i;
+    }
+    sL[i][i + r] = sL[i + r][i] = sum[k];
   }
-  st->error = sum[NH + DIM];
-  st->rows_photo = (int64_t)sum[N - 1];
-  st->rows = (int64_t)sum[N - 2] + st->rows_photo;
-  st->dim = D;
-  st->iterations += 1;
-  st->step_norm = 0.0;
-  st->converged = 0;
-  // Cholesky H = L L^T; a pivot below 1e-10 max diag(H) is a degenerate system
-  double dmax = 0.0;
-  for (int i = 0; i < D; ++i) dmax = fmax(dmax, H[i][i]);
-  bool ok = st->rows >= min_rows && dmax > 0.0;
-  double L[7][7];
+  __syncwarp();
+  for (int k = lane; k < 49; k += 32) {
+    const int i = k / 7, j = k % 7;
+    st->H[k] = (i < D && j < D) ? sL[i][j] : 0.0;
+  }
+  if (lane < 7) {
+    st->g[lane] = lane < D ? sum[NH + lane] : 0.0;
+    st->xi[lane] = 0.0;
+  }
+  const int64_t rows_photo = (int64_t)sum[N - 1];
+  const int64_t rows = (int64_t)sum[N - 2] + rows_photo;
+  if (lane == 0) {
+    st->error = sum[NH + DIM];
+    st->rows_photo = rows_photo;
+    st->rows = rows;
+    st->dim = D;
+    st->iterations += 1;
+    st->step_norm = 0.0;
+    st->converged = 0;
+  }
+  double dmax = lane < D ? sL[lane][lane] : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(FULL, dmax, o));
+  // Cholesky H = L L^T (lower triangle of sL), a pivot below 1e-10 max diag(H): degenerate
+  bool ok = rows >= min_rows && dmax > 0.0;
   for (int j = 0; j < D && ok; ++j) {
-    double s = H[j][j];
-    for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+    const double s = sL[j][j];
     if (!(s > 1e-10 * dmax)) {
       ok = false;
       break;
     }
-    L[j][j] = sqrt(s);
-    for (int i = j + 1; i < D; ++i) {
-      double t = H[i][j];
-      for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
-      L[i][j] = t / L[j][j];
+    const double ljj = sqrt(s), inv = 1.0 / ljj;
+    __syncwarp();
+    if (lane == j) sL[j][j] = ljj;
+    if (lane > j && lane < D) sL[lane][j] = sL[lane][j] * inv;
+    __syncwarp();
+    const int m = D - 1 - j;  // trailing lower triangle, rows and columns j + 1 .. D - 1
+    for (int p = lane; p < m * (m + 1) / 2; p += 32) {
+      int ii = 0, kk = p;
+      while (kk > ii) {
+        kk -= ii + 1;
+        ++ii;
+      }
+      const int i = j + 1 + ii, k = j + 1 + kk;
+      sL[i][k] -= sL[i][j] * sL[k][j];
     }
+    __syncwarp();
   }
   if (!ok) {
-    st->status = DTSDF_ERR_DEGENERATE;
+    if (lane == 0) st->status = DTSDF_ERR_DEGENERATE;
+    __syncwarp();
     return true;
   }
-  double y[7], xi[7];
+  // L y = -g, then L^T xi = y (column-oriented; sb holds the right-hand side, then xi)
+  if (lane < D) sb[lane] = -sum[NH + lane];
+  __syncwarp();
   for (int i = 0; i < D; ++i) {
-    double t = -g[i];
-    for (int k = 0; k < i; ++k) t -= L[i][k] * y[k];
-    y[i] = t / L[i][i];
+    const double y = sb[i] / sL[i][i];
+    __syncwarp();
+    if (lane == i) sb[i] = y;
+    if (lane > i && lane < D) sb[lane] -= sL[lane][i] * y;
+    __syncwarp();
   }
   for (int i = D - 1; i >= 0; --i) {
-    double t = y[i];
-    for (int k = i + 1; k < D; ++k) t -= L[k][i] * xi[k];
-    xi[i] = t / L[i][i];
+    const double x = sb[i] / sL[i][i];
+    __syncwarp();
+    if (lane == i) sb[i] = x;
+    if (lane < i) sb[lane] -= sL[i][lane] * x;
+    __syncwarp();
   }
+  double xi[7];
   double nrm = 0.0;
-  for (int i = 0; i < D; ++i) {
-    st->xi[i] = xi[i];
+  for (int i = 0; i < 7; ++i) {
+    xi[i] = i < D ? sb[i] : 0.0;
     nrm += xi[i] * xi[i];
   }
   nrm = sqrt(nrm);
-  double E[16], T0[16], T1[16];
-  exp_sim3(xi, D, E);
-  for (int i = 0; i < 16; ++i) T0[i] = pose[i];
-  mat4_mul(E, T0, T1);
-  for (int i = 0; i < 16; ++i) pose[i] = T1[i];
-  st->status = 0;
-  st->step_norm = nrm;
-  if (nrm < stop_norm) {
-    st->converged = 1;
-    return true;
+  // exponential map: transcendental values in lanes 1-4, the rest in lane 0
+  const double th = sqrt(xi[3] * xi[3] + xi[4] * xi[4] + xi[5] * xi[5]);
+  const double sg = D == 7 ? xi[6] : 0.0;
+  double f = 0.0;
+  if (lane == 1) f = sin(th);
+  if (lane == 2) f = cos(th);
+  if (lane == 3) f = exp(sg);
+  if (lane == 4) f = expm1(sg);
+  const double s_th = __shfl_sync(FULL, f, 1), c_th = __shfl_sync(FULL, f, 2);
+  const double es = __shfl_sync(FULL, f, 3), em1 = __shfl_sync(FULL, f, 4);
+  if (lane == 0) exp_sim3_from(xi, D, s_th, c_th, es, em1, sE);
+  __syncwarp();
+  double t = 0.0;
+  if (lane < 16) {
+    const int i = lane >> 2, j = lane & 3;
+    for (int k = 0; k < 4; ++k) t += sE[4 * i + k] * pose[4 * k + j];
   }
-  return false;
+  __syncwarp();
+  if (lane < 16) pose[lane] = t;
+  if (lane < D) st->xi[lane] = xi[lane];
+  if (lane == 0) {
+    st->status = 0;
+    st->step_norm = nrm;
+    st->converged = nrm < stop_norm;
+  }
+  __syncwarp();
+  return nrm < stop_norm;
 }
 
 // ---------------------------------------------------------- reduction -----
@@ -467,16 +523,40 @@ __global__ void __launch_bounds__(ICP_THREADS) k_icp(IcpArgs a) {
   __syncthreads();
   if (!s_last) return;
 
-  // ---- last CTA: FP64 sum of the partials in CTA order, then solve on one thread
+  // ---- last CTA: FP64 sum of the partials in a fixed order - PARTS consecutive ranges of
+  // CTAs, each summed in CTA order by its own thread, then the range sums in order (short
+  // dependent chains of FP64 additions) - then the solve by one warp
+  constexpr int PARTS = ICP_THREADS / A::N;
+  __shared__ double s_psum[PARTS][A::N];
+  {
+    const int G = (int)gridDim.x, chunk = (G + PARTS - 1) / PARTS;
+    const int slot = threadIdx.x % A::N, part = threadIdx.x / A::N;
+    if (part < PARTS) {
+      const int b0 = part * chunk, b1 = min(G, b0 + chunk);
+      double s = 0.0;
+      int b = b0;
+      for (; b + 16 <= b1; b += 16) {
+        float v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = __ldcg(a.partials + (b + q) * A::N + slot);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) s += (double)v[q];
+      }
+      for (; b < b1; ++b) s += (double)__ldcg(a.partials + b * A::N + slot);
+      s_psum[part][slot] = s;
+    }
+  }
+  __syncthreads();
   if (threadIdx.x < A::N) {
     double s = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) s += (double)__ldcg(a.partials + b * A::N + threadIdx.x);
+    for (int q = 0; q < PARTS; ++q) s += s_psum[q][threadIdx.x];
     s_sum[threadIdx.x] = s;
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  *a.ticket = 0u;
-  if (icp_solve_update<DIM>(s_sum, DIM, a.pose, a.stats, a.min_rows, a.stop_norm)) *a.stop = 1;
+  if (threadIdx.x >= 32) return;
+  if (threadIdx.x == 0) *a.ticket = 0u;
+  const bool stop = icp_solve_update_warp<DIM>(s_sum, DIM, a.pose, a.stats, a.min_rows, a.stop_norm);
+  if (threadIdx.x == 0 && stop) *a.stop = 1;
 }
 
 // ------------------------------------------------------------- batched ----
@@ -564,10 +644,10 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS) k_icp_batch(const __grid_co
           s_sum[tid] = sm;
         }
         __syncthreads();
-        if (tid == 0) {
-          const bool stop = icp_solve_update<7>(s_sum, dsolve, s_cur, &s_st, a.min_rows, a.stop_norm);
-          for (int i = 0; i < 16; ++i) s_pose[b][i] = s_cur[i];
-          s_done[b] = stop ? 1 : 0;
+        if (tid < 32) {
+          const bool stop = icp_solve_update_warp<7>(s_sum, dsolve, s_cur, &s_st, a.min_rows, a.stop_norm);
+          if (tid < 16) s_pose[b][tid] = s_cur[tid];
+          if (tid == 0) s_done[b] = stop ? 1 : 0;
         }
       }
       cl.sync();  // the estimate and the level decision are published
