@@ -157,7 +157,7 @@ def opts_kinect(dt):
                        lam=0.1, z_min=0.1, stop_norm=1e-6, min_rows=10)
 
 
-LAUNCHES = {"render": 2, "set_frame": 6, "set_keyframe": 6, "compose": 1, "solve": 19, "integrate": 7}
+LAUNCHES = {"render": 2, "set_frame": 6, "set_keyframe": 6, "compose": 1, "solve": 19, "integrate": 8}
 
 
 class Tracker:

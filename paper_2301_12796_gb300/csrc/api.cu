@@ -101,6 +101,7 @@ struct dtsdf_map_s {
   // frame scratch
   float4* P = nullptr;
   float4* N = nullptr;
+  uint8_t* J = nullptr;  // per-pixel carving flags
   size_t ws_pixels = 0;
   // error flag mirror (pinned) and the event of its last copy
   uint32_t* err_host = nullptr;
@@ -137,6 +138,7 @@ static void map_free(dtsdf_map m) {
   cudaFree(m->render_q);
   cudaFree(m->P);
   cudaFree(m->N);
+  cudaFree(m->J);
   if (m->err_host) cudaFreeHost(m->err_host);
   if (m->err_event) cudaEventDestroy(m->err_event);
   if (m->pool) cudaMemPoolDestroy(m->pool);
@@ -308,10 +310,13 @@ static dtsdf_status ensure_ws(dtsdf_map m, size_t npix) {
   if (m->ws_pixels >= npix) return DTSDF_OK;
   cudaFree(m->P);
   cudaFree(m->N);
+  cudaFree(m->J);
   m->P = m->N = nullptr;
+  m->J = nullptr;
   m->ws_pixels = 0;
   CK(cudaMalloc((void**)&m->P, sizeof(float4) * npix));
   CK(cudaMalloc((void**)&m->N, sizeof(float4) * npix));
+  CK(cudaMalloc((void**)&m->J, npix));
   m->ws_pixels = npix;
   return DTSDF_OK;
 }
@@ -344,7 +349,7 @@ static dtsdf_status integrate_impl(dtsdf_map m, const dtsdf_frame* f, const doub
     launch_alloc(m->v, m->P, m->N, (int)npix, T, T_dev, num_sms(), s);
     CK_LAUNCH("alloc");
   }
-  launch_fuse(m->v, K, T, T_dev, m->P, m->N, m->p.color ? f->rgb : nullptr, num_sms(), s);
+  launch_fuse(m->v, K, T, T_dev, m->P, m->N, m->p.color ? f->rgb : nullptr, m->J, num_sms(), s);
   CK_LAUNCH("fuse");
   if (!m->err_pending) {
     CK(cudaMemcpyAsync(m->err_host, m->v.counters + C_ERR, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));

@@ -38,7 +38,7 @@ void launch_dense_fill(const MapView& m, int nb, cudaStream_t s);
 void launch_pool_init(const MapView& m, int with_color, int num_sms, cudaStream_t s);
 // Fusion of one frame followed by the apron refresh of the bricks near the changed ones.
 void launch_fuse(const MapView& m, const Intr& K, const Pose32& T, const double* Tdev, const float4* P,
-                 const float4* N, const uint8_t* rgb, int num_sms, cudaStream_t s);
+                 const float4* N, const uint8_t* rgb, uint8_t* J, int num_sms, cudaStream_t s);
 // Apron refresh and bound of every brick (after an import).
 void launch_apron_refresh_all(const MapView& m, int num_sms, cudaStream_t s);
 void launch_pose_compose(const double* A, int invert_a, const double* B, double* C, cudaStream_t s);

@@ -278,6 +278,7 @@ __global__ void k_pool_init(MapView m, int with_color) {
 
 // ------------------------------------------------------------------ fusion
 struct FuseFrame {
+  const uint8_t* J;    // per pixel: a valid depth within the carving radius differs by more than tau
   Intr K;
   Pose32 T;            // camera -> world (unless Tdev is given)
   const double* Tdev;  // camera -> world in device memory, or null
@@ -305,6 +306,31 @@ __device__ __forceinline__ void store_geom(const MapView& m, size_t i, float sdf
     m.geom16[i] = pack_geom16(sdf, w);
   else
     m.geom[i] = make_float2(sdf, w);
+}
+
+// Carving test of every pixel with a back-projected point: 1 if a valid pixel within the
+// carving radius has a depth differing from it by more than tau (Sec. 3, free-space carving
+// only where no depth discontinuity is near).
+__global__ void k_carve_flags(const float4* __restrict__ P, Intr K, int rad, float tau, uint8_t* __restrict__ J) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y * blockDim.y + threadIdx.y;
+  if (u >= K.W || v >= K.H) return;
+  const float4 p = P[v * K.W + u];
+  bool jump = false;
+  if (p.w > 0) {
+    for (int dv = -rad; dv <= rad && !jump; ++dv)
+      for (int du = -rad; du <= rad; ++du) {
+        const int uu = u + du, vv = v + dv;
+        if (uu < 0 || vv < 0 || uu >= K.W || vv >= K.H) continue;
+        const float4 q = P[vv * K.W + uu];
+        if (!(q.w > 0)) continue;
+        if (fabsf(rsub(q.z, p.z)) > tau) {
+          jump = true;
+          break;
+        }
+      }
+  }
+  J[v * K.W + u] = jump ? 1 : 0;
 }
 
 // Conservative frustum test of block (bx, by, bz): its bounding sphere, grown by `margin`,
@@ -407,20 +433,9 @@ __global__ void __launch_bounds__(256) k_fuse(MapView m, FuseFrame f) {
       const size_t gi = (size_t)b * PVOX + pad_index(i, j, k);  // geometry (padded brick)
       const size_t ci = (size_t)b * BVOX + vi;                  // colour
       if (draw > m.tau) {
-        // free-space carving, unless a depth jump > tau lies within the carving radius
-        bool jump = false;
-        for (int dv = -m.carve_r; dv <= m.carve_r && !jump; ++dv)
-          for (int du = -m.carve_r; du <= m.carve_r; ++du) {
-            const int uu = u + du, vv = v + dv;
-            if (uu < 0 || vv < 0 || uu >= f.K.W || vv >= f.K.H) continue;
-            const float4 q = __ldg(f.P + vv * f.K.W + uu);
-            if (!(q.w > 0)) continue;
-            if (fabsf(rsub(q.z, P.z)) > m.tau) {
-              jump = true;
-              break;
-            }
-          }
-        if (jump) continue;
+        // free-space carving, unless a depth jump > tau lies within the carving radius of the
+        // pixel (a property of the pixel alone, flagged once per frame by k_carve_flags)
+        if (__ldg(f.J + pi)) continue;
         const float2 g = load_geom<STORE>(m, gi);
         const float wn = g.y + m.wcarve;
         const float nsdf = (g.y * g.x + m.wcarve) / wn;
@@ -683,8 +698,13 @@ void launch_pool_init(const MapView& m, int with_color, int num_sms, cudaStream_
 }
 
 void launch_fuse(const MapView& m, const Intr& K, const Pose32& T, const double* Tdev, const float4* P,
-                 const float4* N, const uint8_t* rgb, int num_sms, cudaStream_t s) {
+                 const float4* N, const uint8_t* rgb, uint8_t* J, int num_sms, cudaStream_t s) {
+  {
+    dim3 blk(32, 8), grd((K.W + 31) / 32, (K.H + 7) / 8);
+    k_carve_flags<<<grd, blk, 0, s>>>(P, K, m.carve_r, m.tau, J);
+  }
   FuseFrame f;
+  f.J = J;
   f.K = K;
   f.T = T;
   f.Tdev = Tdev;
