@@ -196,9 +196,13 @@ __device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, cons
     const float wf = WD * fmaxf(vr, 0.0f);
     fw += wf;
     facc += wf * phiD;
-    // axis a: the cube shifted by +h reuses the base cube's corners with bit a set, and its
-    // corners with bit a set lie one voxel beyond the base cube; the cube shifted by -h reuses
-    // the base corners without bit a, and its corners without bit a lie one voxel before it
+    // axis a: phi(+h) - phi(-h) is the trilinear interpolation, with the sample's fractions,
+    // of the voxel differences v(c + e_a) - v(c - e_a) at the 8 corners c (the interpolation
+    // is linear in the values). Differencing first keeps the gradient accurate in single
+    // precision where the field is nearly flat (nearby values subtract exactly), and a flat
+    // field still gives exactly zero. For corners with bit a set, c + e_a lies one voxel
+    // beyond the base cube and c - e_a is the base corner without bit a; for the others,
+    // c + e_a is the base corner with bit a and c - e_a lies one voxel before the cube.
     bool gok = true;
     float gr[3];
 #pragma unroll
@@ -209,14 +213,13 @@ __device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, cons
 #pragma unroll
       for (int q = 0; q < 8; ++q)
         t[q] = ld_geom<STORE, COUNT>(m, (q & bit) ? base + S + coff(q) : base - S + coff(q), touched);
-      float vp[8], vn[8];
+      float dv[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         gok &= t[q].y > 0.0f;
-        vp[q] = (q & bit) ? t[q].x : s[q | bit];
-        vn[q] = (q & bit) ? s[q & ~bit] : t[q].x;
+        dv[q] = (q & bit) ? t[q].x - s[q & ~bit] : s[q | bit] - t[q].x;
       }
-      gr[a] = (tri(vp, fx, fy, fz) - tri(vn, fx, fy, fz)) * inv2h;
+      gr[a] = tri(dv, fx, fy, fz) * inv2h;
     }
     if (!gok) continue;
     const float gn = sqrtf(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
