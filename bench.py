@@ -41,6 +41,23 @@ WORKLOAD_MS = ("multi-sensor Sim(3): map of the 4x4x3 m room from 300 sensor-A f
                "(3 levels x 20 iterations), the step captured in a CUDA graph")
 FALLBACK_HBM_GBS = 6800.0
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_render launch of the
+# default workload (FP32 storage with colour, first timed render), from one ncu capture of
+# ``bench.py --steps 2 --warmup 3 --no-e2e --no-cpu`` (profiles/k_render_kinect640.md). It
+# belongs to the kernel sources it was taken with: reported only while their hash matches.
+RENDER_TRAFFIC = {"bytes": 281623040 + 15153664, "sources_sha1_16": "76cdaec48660ab86",
+                  "files": ("render.cu", "common.cuh", "internal.h")}
+
+
+def render_traffic():
+    """Measured DRAM bytes per render launch, or None once the kernel sources have changed."""
+    import hashlib
+    h = hashlib.sha1()
+    for f in RENDER_TRAFFIC["files"]:
+        with open(os.path.join(ROOT, "paper_2301_12796_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return RENDER_TRAFFIC["bytes"] if h.hexdigest()[:16] == RENDER_TRAFFIC["sources_sha1_16"] else None
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -387,7 +404,8 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
     peak, peak_kind = measured_hbm_peak()
     achieved = render_bytes / (render_ms / 1000.0) / 1e9
     roof = {"kernel": "k_render (direct DTSDF ray-cast)", "bound": "hbm", "achieved": achieved, "peak": peak,
-            "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+            "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+            "traffic": render_traffic() if storage == 0 and not args.profile else None,
             "algorithmic_bytes_per_launch": render_bytes, "geom_bricks": geom_b, "color_bricks": col_b,
             "launch_ms": render_ms}
     cpu = None
