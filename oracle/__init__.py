@@ -6,7 +6,8 @@ It shares no code, headers, tables or constants with the CUDA library and never
 imports it; the two meet only through the seeded inputs of ``scenes``.
 
 * ``dtsdf_oracle.c`` (plain C, double precision): preprocessing, block
-  allocation, voxel-projection fusion and ray-cast rendering (Sec. 3, 4, 7).
+  allocation, voxel-projection fusion and ray-cast rendering (Sec. 3, 4, 7), and
+  the view-dependent combined TSDF with its regular ray-cast (Sec. 4, Sec. 7).
 * ``icp.py`` (numpy, double precision): pyramid, projective association,
   point-to-plane residuals and Jacobians in SE(3) and Sim(3), photometric
   frame-to-keyframe rows, normal equations, Cholesky solve and the exponential
@@ -40,6 +41,8 @@ PARITY = {
     "segment_blocks": "pinned: brute-force slab test (tests/test_oracle_alloc.py)",
     "integrate": "pinned: per-voxel closed form on planes, running-average identity (tests/test_oracle_fusion.py)",
     "render": "pinned: analytic plane, sphere bound, thin-sheet lemma (tests/test_oracle_render.py)",
+    "combine": "pinned: one direction's values kept, identical directions kept, hand-evaluated weights, analytic "
+               "plane render (tests/test_oracle_combined.py)",
     "icp": "pinned: finite differences, exact recovery of known SE(3)/Sim(3) (tests/test_oracle_icp.py)",
     "exp": "pinned: Rodrigues closed form, group identities (tests/test_oracle_icp.py)",
 }
@@ -82,6 +85,14 @@ def _load():
             L.om_eval.restype = I
             L.om_render.argtypes = [P, P, I, I, F, F, F, F, P, ctypes.c_long, P, P, P, P]
             L.om_render.restype = I
+            L.om_combine.argtypes = [P, P]
+            L.om_combine.restype = I
+            L.om_render_combined.argtypes = [P, P, I, I, F, F, F, F, P, ctypes.c_long, P, P, P, P]
+            L.om_render_combined.restype = I
+            L.om_comb_voxel.argtypes = [P, I, I, I, P, P]
+            L.om_comb_voxel.restype = I
+            L.om_set_brick.argtypes = [P, I, I, I, I, P]
+            L.om_set_brick.restype = I
             _lib = L
     return _lib
 
@@ -185,14 +196,39 @@ class OracleMap:
         rc = self._L.om_brick_data(self._h, int(bx), int(by), int(bz), int(D), _p(out))
         return None if rc != 0 else out
 
+    def set_brick(self, bx, by, bz, D, vox):
+        """Write a brick (512 x 6: sdf, w, r, g, b, wc), allocating it if needed (tests)."""
+        v = np.ascontiguousarray(vox, np.float64).reshape(512, 6)
+        if self._L.om_set_brick(self._h, int(bx), int(by), int(bz), int(D), _p(v)) != 0:
+            raise MemoryError("oracle set_brick failed")
+
     def eval(self, x, r):
         info = np.zeros(9, np.float64)
         ok = self._L.om_eval(self._h, _p(np.ascontiguousarray(x, np.float64)),
                              _p(np.ascontiguousarray(r, np.float64)), _p(info))
         return bool(ok), info
 
+    def combine(self, centre):
+        """View-dependent combined TSDF of every allocated block for the camera centre (Sec. 4, Sec. 7)."""
+        if self._L.om_combine(self._h, _p(np.ascontiguousarray(centre, np.float64))) != 0:
+            raise MemoryError("oracle combine failed")
+
+    def comb_voxel(self, x, y, z, centre):
+        """(defined, phi, rgb, colour ok) of the combined value of voxel (x, y, z)."""
+        info = np.zeros(5, np.float64)
+        ok = self._L.om_comb_voxel(self._h, int(x), int(y), int(z), _p(np.ascontiguousarray(centre, np.float64)),
+                                   _p(info))
+        return bool(ok), info[0], info[1:4], bool(info[4])
+
+    def render_combined(self, K, T_wc, pixels: np.ndarray | None = None):
+        """Ray-cast of the combined TSDF of the last combine(); outputs as render()."""
+        return self._render(self._L.om_render_combined, K, T_wc, pixels)
+
     def render(self, K, T_wc, pixels: np.ndarray | None = None):
         """Ray-cast depth (0 = miss), camera-frame normals, colour, colour validity."""
+        return self._render(self._L.om_render, K, T_wc, pixels)
+
+    def _render(self, fn, K, T_wc, pixels):
         T = np.ascontiguousarray(T_wc, np.float64)
         if pixels is None:
             n = K.width * K.height
@@ -204,8 +240,10 @@ class OracleMap:
         normal = np.zeros((n, 3), np.float64)
         color = np.zeros((n, 3), np.float64)
         cok = np.zeros(n, np.uint8)
-        self._L.om_render(self._h, _p(T), K.width, K.height, K.fx, K.fy, K.cx, K.cy, _p(pix), n,
-                          _p(depth), _p(normal), _p(color), _p(cok))
+        rc = fn(self._h, _p(T), K.width, K.height, K.fx, K.fy, K.cx, K.cy, _p(pix), n, _p(depth), _p(normal),
+                _p(color), _p(cok))
+        if rc != 0:
+            raise RuntimeError("oracle render failed (combined: call combine() first)")
         if pixels is None:
             return (depth.reshape(K.height, K.width), normal.reshape(K.height, K.width, 3),
                     color.reshape(K.height, K.width, 3), cok.reshape(K.height, K.width))

@@ -76,6 +76,12 @@ typedef struct {
   int32_t* first_frame;
   size_t nbricks, brick_cap;
   int frames;
+  /* view-dependent combined TSDF (om_combine): one entry per allocated block */
+  uint64_t* ckeys;   /* block key -> combined block index, open addressing */
+  int32_t* cvals;
+  size_t ccap, nblocks;
+  double* comb;      /* per block, 512 voxels x 5: phi, defined, r, g, b */
+  uint8_t* comb_col; /* per block, 512 colour flags */
 } omap;
 
 #define EMPTY_KEY 0xFFFFFFFFFFFFFFFFull
@@ -212,6 +218,10 @@ void om_free(omap* m) {
   free(m->vox);
   free(m->coord);
   free(m->first_frame);
+  free(m->ckeys);
+  free(m->cvals);
+  free(m->comb);
+  free(m->comb_col);
   free(m);
 }
 
@@ -893,6 +903,367 @@ int om_render(const omap* m, const double* T_wc, int W, int H, float fx, float f
     if (color)
       for (int a = 0; a < 3; ++a) color[3 * i + a] = cok ? col[a] : 0.0;
     if (color_ok) color_ok[i] = (uint8_t)cok;
+  }
+  return 0;
+}
+
+/* ====================================================== combined TSDF (Sec. 4, Sec. 7) */
+/*
+ * View-dependent combined TSDF. Sec. 4: the combined SDF can be pre-computed for every voxel of
+ * the view frustum and then ray-cast like a regular TSDF from the pose of the combination.
+ * Sec. 7: the lookups are at integer voxel positions, so no trilinear interpolation is needed
+ * and a direction's gradient comes from its 6 neighbouring voxels. Readings:
+ *   combined value at voxel v for the camera centre c: every direction D with W^D(v) > 0
+ *   takes part; its gradient is the central difference of its 6 axis neighbours (all with
+ *   weight > 0, norm > 1e-12); the view ray is r = (x_v - c) / |x_v - c|; the weights are
+ *   those of Eq. combine_weight, with the fallback of Eq. combine_tsdf_weight when they all
+ *   vanish; otherwise the voxel is undefined. The colour is the combination of the colours of
+ *   the directions with a combination weight and a colour weight > 0 (none after the fallback).
+ *   Here every allocated block is combined (the kernels combine the blocks of the padded view
+ *   frustum, which hold every voxel a ray of that view reads).
+ *   ray-cast: the rules of the direct render (samples at t = k h/2, the first pair of
+ *   consecutive defined samples with Phi > 0 >= Phi, one scan of 4 sub-steps and linear
+ *   interpolation, outputs at the first grid sample behind the crossing, else in front of
+ *   it, else at the root) with Phi the trilinear interpolation of the combined values
+ *   (defined if all 8 corners are), the normal the central difference of that field at +-h
+ *   (defined if the 6 offset samples are, norm > 1e-12) and the colour the trilinear
+ *   interpolation of the combined colours (where all 8 corners have one).
+ */
+
+static int floor8(int x) { return x >= 0 ? x / 8 : -((-x + 7) / 8); }
+
+static const ovox* vox_at(const omap* m, int D, int x, int y, int z) {
+  const int bx = floor8(x), by = floor8(y), bz = floor8(z);
+  const int32_t br = hash_find(m, bx, by, bz, D);
+  if (br < 0) return NULL;
+  return m->vox + (size_t)br * BVOX + ((z - 8 * bz) * 8 + (y - 8 * by)) * 8 + (x - 8 * bx);
+}
+
+static uint64_t block_key(int bx, int by, int bz) { return pack_key(bx, by, bz, 0); }
+
+static int32_t cblock_find(const omap* m, int bx, int by, int bz) {
+  if (!m->ckeys) return -1;
+  const uint64_t k = block_key(bx, by, bz);
+  size_t i = mix64(k) & (m->ccap - 1);
+  for (;;) {
+    if (m->ckeys[i] == k) return m->cvals[i];
+    if (m->ckeys[i] == EMPTY_KEY) return -1;
+    i = (i + 1) & (m->ccap - 1);
+  }
+}
+
+/* combined value of voxel (x, y, z) for the camera centre c; returns 1 if defined */
+static int comb_voxel(const omap* m, int x, int y, int z, const double* c, double* phi, double* col, int* col_ok) {
+  const double xw[3] = {m->origin[0] + x * m->h, m->origin[1] + y * m->h, m->origin[2] + z * m->h};
+  double r[3] = {xw[0] - c[0], xw[1] - c[1], xw[2] - c[2]};
+  const double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  for (int a = 0; a < 3; ++a) r[a] /= rn;
+  double ws = 0, acc = 0, wf = 0, af = 0, cw = 0, cacc[3] = {0, 0, 0};
+  int any = 0;
+  for (int D = 0; D < ND; ++D) {
+    const ovox* v0 = vox_at(m, D, x, y, z);
+    if (!v0 || !(v0->w > 0)) continue;
+    any = 1;
+    double ff = -(VDIR[D][0] * r[0] + VDIR[D][1] * r[1] + VDIR[D][2] * r[2]);
+    if (ff < 0) ff = 0;
+    const double w_f = v0->w * ff;
+    if (w_f > 0) {
+      wf += w_f;
+      af += w_f * v0->sdf;
+    }
+    double g[3];
+    int ok = 1;
+    for (int a = 0; a < 3 && ok; ++a) {
+      const int e[3] = {a == 0, a == 1, a == 2};
+      const ovox* p = vox_at(m, D, x + e[0], y + e[1], z + e[2]);
+      const ovox* q = vox_at(m, D, x - e[0], y - e[1], z - e[2]);
+      if (!p || !q || !(p->w > 0) || !(q->w > 0)) {
+        ok = 0;
+        break;
+      }
+      g[a] = (p->sdf - q->sdf) / (2.0 * m->h);
+    }
+    if (!ok) continue;
+    const double nrm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    if (!(nrm > 1e-12)) continue;
+    const double n[3] = {g[0] / nrm, g[1] / nrm, g[2] / nrm};
+    const double cosv = (D & 1) ? -n[D >> 1] : n[D >> 1];
+    double facing = -(n[0] * r[0] + n[1] * r[1] + n[2] * r[2]);
+    if (facing < 0) facing = 0;
+    const double wc = om_w_dir(cosv, m->theta) * facing * v0->w;
+    if (!(wc > 0)) continue;
+    ws += wc;
+    acc += wc * v0->sdf;
+    if (v0->wc > 0) {
+      cw += wc;
+      cacc[0] += wc * v0->r;
+      cacc[1] += wc * v0->g;
+      cacc[2] += wc * v0->b;
+    }
+  }
+  *col_ok = 0;
+  if (!any) return 0;
+  if (ws > 0) {
+    *phi = acc / ws;
+    if (cw > 0) {
+      for (int a = 0; a < 3; ++a) col[a] = cacc[a] / cw;
+      *col_ok = 1;
+    }
+    return 1;
+  }
+  if (wf > 0) {
+    *phi = af / wf;
+    return 1;
+  }
+  return 0;
+}
+
+/* Combine every allocated block for the camera centre c (replaces an earlier combination). */
+int om_combine(omap* m, const double* c) {
+  free(m->ckeys);
+  free(m->cvals);
+  free(m->comb);
+  free(m->comb_col);
+  m->ckeys = NULL;
+  m->cvals = NULL;
+  m->comb = NULL;
+  m->comb_col = NULL;
+  /* distinct blocks */
+  size_t cap = 64;
+  while (cap < 4 * m->nbricks + 64) cap <<= 1;
+  m->ccap = cap;
+  m->ckeys = (uint64_t*)malloc(cap * sizeof(uint64_t));
+  m->cvals = (int32_t*)malloc(cap * sizeof(int32_t));
+  int32_t* bl = (int32_t*)malloc(3 * (m->nbricks + 1) * sizeof(int32_t));
+  if (!m->ckeys || !m->cvals || !bl) return -1;
+  memset(m->ckeys, 0xFF, cap * sizeof(uint64_t));
+  size_t nb = 0;
+  for (size_t b = 0; b < m->nbricks; ++b) {
+    const int bx = m->coord[4 * b], by = m->coord[4 * b + 1], bz = m->coord[4 * b + 2];
+    const uint64_t k = block_key(bx, by, bz);
+    size_t i = mix64(k) & (cap - 1);
+    while (m->ckeys[i] != EMPTY_KEY && m->ckeys[i] != k) i = (i + 1) & (cap - 1);
+    if (m->ckeys[i] == k) continue;
+    m->ckeys[i] = k;
+    m->cvals[i] = (int32_t)nb;
+    bl[3 * nb] = bx;
+    bl[3 * nb + 1] = by;
+    bl[3 * nb + 2] = bz;
+    ++nb;
+  }
+  m->nblocks = nb;
+  m->comb = (double*)malloc(nb * BVOX * 5 * sizeof(double));
+  m->comb_col = (uint8_t*)malloc(nb * BVOX);
+  if (!m->comb || !m->comb_col) {
+    free(bl);
+    return -1;
+  }
+#pragma omp parallel for schedule(dynamic, 4)
+  for (long b = 0; b < (long)nb; ++b) {
+    for (int vi = 0; vi < BVOX; ++vi) {
+      const int x = 8 * bl[3 * b] + (vi & 7), y = 8 * bl[3 * b + 1] + ((vi >> 3) & 7), z = 8 * bl[3 * b + 2] + (vi >> 6);
+      double phi = 0, col[3] = {0, 0, 0};
+      int cok = 0;
+      const int def = comb_voxel(m, x, y, z, c, &phi, col, &cok);
+      double* o = m->comb + ((size_t)b * BVOX + vi) * 5;
+      o[0] = def ? phi : 0.0;
+      o[1] = def;
+      o[2] = col[0];
+      o[3] = col[1];
+      o[4] = col[2];
+      m->comb_col[(size_t)b * BVOX + vi] = (uint8_t)(def && cok);
+    }
+  }
+  free(bl);
+  return 0;
+}
+
+/* combined voxel (x, y, z) of the last om_combine, NULL if undefined */
+static const double* cvox(const omap* m, int x, int y, int z, int* col_ok) {
+  const int bx = floor8(x), by = floor8(y), bz = floor8(z);
+  const int32_t cb = cblock_find(m, bx, by, bz);
+  if (cb < 0) return NULL;
+  const size_t vi = (size_t)cb * BVOX + ((z - 8 * bz) * 8 + (y - 8 * by)) * 8 + (x - 8 * bx);
+  const double* o = m->comb + vi * 5;
+  if (!(o[1] > 0)) return NULL;
+  *col_ok = m->comb_col[vi];
+  return o;
+}
+
+/* trilinear combined field at voxel coordinate g; returns 1 if all 8 corners are defined */
+static int comb_tri(const omap* m, const double* g, double* phi, double* col, int* col_ok) {
+  double fl[3], fr[3];
+  int b[3];
+  for (int a = 0; a < 3; ++a) {
+    fl[a] = floor(g[a]);
+    fr[a] = g[a] - fl[a];
+    b[a] = (int)fl[a];
+  }
+  double acc = 0, cacc[3] = {0, 0, 0};
+  int all_col = 1;
+  for (int q = 0; q < 8; ++q) {
+    const int o[3] = {q & 1, (q >> 1) & 1, (q >> 2) & 1};
+    double wt = 1.0;
+    for (int a = 0; a < 3; ++a) wt *= o[a] ? fr[a] : 1.0 - fr[a];
+    int cok = 0;
+    const double* v = cvox(m, b[0] + o[0], b[1] + o[1], b[2] + o[2], &cok);
+    if (!v) return 0;
+    acc += wt * v[0];
+    all_col &= cok;
+    for (int a = 0; a < 3; ++a) cacc[a] += wt * v[2 + a];
+  }
+  *phi = acc;
+  if (col) {
+    *col_ok = all_col;
+    for (int a = 0; a < 3; ++a) col[a] = cacc[a];
+  }
+  return 1;
+}
+
+/* combined field at world point x: value, normal (world, 1 if defined) and colour */
+typedef struct {
+  double phi, n[3], col[3];
+  int has_n, col_ok;
+} csample;
+
+static int comb_eval(const omap* m, const double* x, csample* s) {
+  double g[3];
+  for (int a = 0; a < 3; ++a) g[a] = (x[a] - m->origin[a]) / m->h;
+  if (!comb_tri(m, g, &s->phi, s->col, &s->col_ok)) return 0;
+  s->has_n = 0;
+  double gr[3];
+  for (int a = 0; a < 3; ++a) {
+    double gp[3] = {g[0], g[1], g[2]}, gm[3] = {g[0], g[1], g[2]};
+    gp[a] += 1.0;
+    gm[a] -= 1.0;
+    double fp, fm;
+    if (!comb_tri(m, gp, &fp, NULL, NULL) || !comb_tri(m, gm, &fm, NULL, NULL)) return 1;
+    gr[a] = (fp - fm) / (2.0 * m->h);
+  }
+  const double nrm = sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+  if (!(nrm > 1e-12)) return 1;
+  for (int a = 0; a < 3; ++a) s->n[a] = gr[a] / nrm;
+  s->has_n = 1;
+  return 1;
+}
+
+static int render_pixel_comb(const omap* m, const double* T, double fx, double fy, double cx, double cy, int u, int v,
+                             double* depth, double* ncam, double* col, int* col_ok) {
+  double rc[3] = {((double)u - cx) / fx, ((double)v - cy) / fy, 1.0};
+  double rl = sqrt(rc[0] * rc[0] + rc[1] * rc[1] + rc[2] * rc[2]);
+  double r[3], o[3] = {T[3], T[7], T[11]};
+  for (int a = 0; a < 3; ++a) r[a] = (T[4 * a] * rc[0] + T[4 * a + 1] * rc[1] + T[4 * a + 2] * rc[2]) / rl;
+  const double step = 0.5 * m->h;
+  const long k0 = (long)ceil(m->zmin * rl / step), k1 = (long)floor(m->zmax * rl / step);
+  int prev_def = 0;
+  double prev_phi = 0, prev_t = 0;
+  for (long k = k0; k <= k1; ++k) {
+    const double t = k * step;
+    const double x[3] = {o[0] + t * r[0], o[1] + t * r[1], o[2] + t * r[2]};
+    csample cs;
+    if (!comb_eval(m, x, &cs)) {
+      prev_def = 0;
+      continue;
+    }
+    if (prev_def && prev_phi > 0 && cs.phi <= 0) {
+      /* one regular scan of 4 sub-steps, then linear interpolation (as the direct render) */
+      double lo = prev_t, hi = t, prev = lo;
+      const double dt = (hi - lo) / 4.0;
+      for (int j = 1; j < 4; ++j) {
+        const double tj = lo + j * dt;
+        const double xj[3] = {o[0] + tj * r[0], o[1] + tj * r[1], o[2] + tj * r[2]};
+        csample cj;
+        if (comb_eval(m, xj, &cj) && cj.phi <= 0) {
+          hi = tj;
+          break;
+        }
+        prev = tj;
+      }
+      lo = prev;
+      double ts;
+      {
+        const double xa[3] = {o[0] + lo * r[0], o[1] + lo * r[1], o[2] + lo * r[2]};
+        const double xb[3] = {o[0] + hi * r[0], o[1] + hi * r[1], o[2] + hi * r[2]};
+        csample ca, cb;
+        const int da = comb_eval(m, xa, &ca) && ca.phi > 0;
+        const int db = comb_eval(m, xb, &cb) && cb.phi <= 0;
+        ts = (da && db) ? lo + (hi - lo) * ca.phi / (ca.phi - cb.phi) : 0.5 * (lo + hi);
+      }
+      const double ends[3] = {t, prev_t, ts};
+      csample ch;
+      int have = 0;
+      for (int e = 0; e < 3 && !have; ++e) {
+        const double xs[3] = {o[0] + ends[e] * r[0], o[1] + ends[e] * r[1], o[2] + ends[e] * r[2]};
+        have = comb_eval(m, xs, &ch) && ch.has_n;
+      }
+      if (!have) return 0;
+      *depth = ts / rl;
+      for (int a = 0; a < 3; ++a) ncam[a] = T[a] * ch.n[0] + T[4 + a] * ch.n[1] + T[8 + a] * ch.n[2];
+      *col_ok = ch.col_ok;
+      if (ch.col_ok)
+        for (int a = 0; a < 3; ++a) col[a] = ch.col[a];
+      return 1;
+    }
+    prev_def = 1;
+    prev_phi = cs.phi;
+    prev_t = t;
+  }
+  return 0;
+}
+
+/* Ray-cast the combined TSDF of the last om_combine (outputs as om_render). */
+int om_render_combined(const omap* m, const double* T_wc, int W, int H, float fx, float fy, float cx, float cy,
+                       const int32_t* pix, long npix, double* depth, double* normal, double* color,
+                       uint8_t* color_ok) {
+  if (!m->comb) return -1;
+  long n = pix ? npix : (long)W * H;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (long i = 0; i < n; ++i) {
+    int u = pix ? pix[2 * i] : (int)(i % W);
+    int v = pix ? pix[2 * i + 1] : (int)(i / W);
+    double d = 0, nc[3] = {0, 0, 0}, col[3] = {0, 0, 0};
+    int cok = 0;
+    if (!render_pixel_comb(m, T_wc, fx, fy, cx, cy, u, v, &d, nc, col, &cok)) {
+      d = 0;
+      nc[0] = nc[1] = nc[2] = 0;
+      cok = 0;
+    }
+    depth[i] = d;
+    if (normal)
+      for (int a = 0; a < 3; ++a) normal[3 * i + a] = nc[a];
+    if (color)
+      for (int a = 0; a < 3; ++a) color[3 * i + a] = cok ? col[a] : 0.0;
+    if (color_ok) color_ok[i] = (uint8_t)cok;
+  }
+  return 0;
+}
+
+/* Exposed for tests: combined value of voxel (x, y, z) for camera centre c; info = phi, r, g, b, colour ok. */
+int om_comb_voxel(const omap* m, int x, int y, int z, const double* c, double* info) {
+  double phi = 0, col[3] = {0, 0, 0};
+  int cok = 0;
+  const int def = comb_voxel(m, x, y, z, c, &phi, col, &cok);
+  info[0] = phi;
+  info[1] = col[0];
+  info[2] = col[1];
+  info[3] = col[2];
+  info[4] = cok;
+  return def;
+}
+
+/* Test support: allocate brick (bx, by, bz, D) if needed and overwrite its 512 voxels with
+ * vox (512 x 6: sdf, w, r, g, b, wc; voxel index i + 8 j + 64 k). Returns 0 on success. */
+int om_set_brick(omap* m, int bx, int by, int bz, int D, const double* vox) {
+  const int32_t b = brick_alloc(m, bx, by, bz, D, m->frames);
+  if (b < 0) return -1;
+  for (int vi = 0; vi < BVOX; ++vi) {
+    ovox* o = m->vox + (size_t)b * BVOX + vi;
+    o->sdf = vox[6 * vi];
+    o->w = vox[6 * vi + 1];
+    o->r = vox[6 * vi + 2];
+    o->g = vox[6 * vi + 3];
+    o->b = vox[6 * vi + 4];
+    o->wc = vox[6 * vi + 5];
   }
   return 0;
 }
