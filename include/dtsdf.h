@@ -138,6 +138,29 @@ DTSDF_API dtsdf_status dtsdf_render(dtsdf_map map, const dtsdf_intrinsics* K, co
 DTSDF_API dtsdf_status dtsdf_render_dev(dtsdf_map map, const dtsdf_intrinsics* K, const double* T_wc_dev,
                                         const dtsdf_render_out* out, void* stream);
 
+/* Render from the view-dependent combined TSDF (Sec. 4; Sec. 7: combination at integer voxel
+ * positions): the combined value of every voxel of the blocks in the view frustum grown by 1/8
+ * of the image on each side is formed with the weights of Eq. combine_weight (6-neighbour
+ * gradients, view ray from the camera centre of the combination pose; fallback of
+ * Eq. combine_tsdf_weight), and the result is ray-cast like a regular TSDF with the rules of
+ * dtsdf_render (sample grid, first crossing, refinement, outputs), the normal from the central
+ * differences of the trilinear combined field. Conditional combination (Sec. 4): the whole
+ * frustum is recombined at this pose while fewer than 5 combined renders were made, after more
+ * than 50 without recombination, or when the pose moved by more than 0.05 m or turned by more
+ * than 0.05 pi/2 since the last combination; otherwise only blocks that received bricks since
+ * the previous call are combined (at the last combination pose) and the render uses the stored
+ * field. The decision is taken on the device. The first call allocates the combined field:
+ * per directory entry 729 voxels x 8 B (+ 16 B with colour). Asynchronous. */
+DTSDF_API dtsdf_status dtsdf_render_combined(dtsdf_map map, const dtsdf_intrinsics* K, const double T_wc[16],
+                                             const dtsdf_render_out* out, void* stream);
+
+/* Same with the pose read from device memory (16 doubles, row-major). */
+DTSDF_API dtsdf_status dtsdf_render_combined_dev(dtsdf_map map, const dtsdf_intrinsics* K, const double* T_wc_dev,
+                                                 const dtsdf_render_out* out, void* stream);
+
+/* The next combined render recombines the whole frustum at its pose. */
+DTSDF_API dtsdf_status dtsdf_combined_reset(dtsdf_map map);
+
 /* Launch shape of the map's renders (no counterpart in the paper: scheduling only; every
  * shape computes the same samples, decisions and outputs). ctas: CTAs of the persistent
  * render grid, 0 = one wave of resident CTAs. tile_w: width of the pixel tiles of 32 rays

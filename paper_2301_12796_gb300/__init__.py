@@ -118,6 +118,9 @@ SIGNATURES = {
     "dtsdf_integrate_dev": ([P, ctypes.POINTER(Frame), P, P], c_int32),
     "dtsdf_render": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), P], c_int32),
     "dtsdf_render_dev": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), P], c_int32),
+    "dtsdf_render_combined": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), P], c_int32),
+    "dtsdf_render_combined_dev": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), P], c_int32),
+    "dtsdf_combined_reset": ([P], c_int32),
     "dtsdf_set_render_opts": ([P, ctypes.POINTER(RenderOpts)], c_int32),
     "dtsdf_render_tune": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), ctypes.POINTER(RenderOpts),
                            ctypes.POINTER(ctypes.c_float), P], c_int32),
@@ -248,6 +251,24 @@ class Map:
         Ki = intrinsics(K)
         check(lib().dtsdf_render_dev(self._h, ctypes.byref(Ki), T_dev.data_ptr(), ctypes.byref(out),
                                      _stream_ptr(stream)), "dtsdf_render_dev")
+
+    def render_combined(self, K, T_wc, depth, normals, color=None, stream=None):
+        """Render from the view-dependent combined TSDF with conditional combination (host pose)."""
+        out = RenderOut(depth.data_ptr(), normals.data_ptr(), None if color is None else color.data_ptr())
+        Ki = intrinsics(K)
+        check(lib().dtsdf_render_combined(self._h, ctypes.byref(Ki), pose_buf(T_wc), ctypes.byref(out),
+                                          _stream_ptr(stream)), "dtsdf_render_combined")
+
+    def render_combined_dev(self, K, T_dev, depth, normals, color=None, stream=None):
+        """Same with the pose in the float64 CUDA tensor T_dev [4, 4]."""
+        out = RenderOut(depth.data_ptr(), normals.data_ptr(), None if color is None else color.data_ptr())
+        Ki = intrinsics(K)
+        check(lib().dtsdf_render_combined_dev(self._h, ctypes.byref(Ki), T_dev.data_ptr(), ctypes.byref(out),
+                                              _stream_ptr(stream)), "dtsdf_render_combined_dev")
+
+    def combined_reset(self):
+        """The next combined render recombines the whole frustum at its pose."""
+        check(lib().dtsdf_combined_reset(self._h), "dtsdf_combined_reset")
 
     def render_batch(self, jobs, stream=None):
         """Render several frames in one launch. jobs: list of (K, T_dev float64 [4, 4] CUDA tensor,

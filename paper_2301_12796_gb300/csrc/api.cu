@@ -1,6 +1,7 @@
 // C ABI of libdtsdf: argument checking, device memory ownership, stream ordering and
 // status codes around the kernels of map.cu, render.cu and icp.cu.
 #include <math.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -114,6 +115,9 @@ struct dtsdf_map_s {
   RenderShape shape;
   // stream-ordered scratch of render launches (per-tile depth ranges), kept cached in the pool
   cudaMemPool_t pool = nullptr;
+  // combined TSDF (allocated by the first combined render)
+  CombState* comb_state = nullptr;
+  bool comb_force = false;
 };
 
 constexpr uint32_t RENDER_Q_SLOTS = 1024;
@@ -142,6 +146,10 @@ static void map_free(dtsdf_map m) {
   if (m->err_host) cudaFreeHost(m->err_host);
   if (m->err_event) cudaEventDestroy(m->err_event);
   if (m->pool) cudaMemPoolDestroy(m->pool);
+  cudaFree(m->v.comb);
+  cudaFree(m->v.comb_col);
+  cudaFree(m->v.comb_gen);
+  cudaFree(m->comb_state);
   delete m;
 }
 
@@ -384,6 +392,76 @@ dtsdf_status dtsdf_render_dev(dtsdf_map m, const dtsdf_intrinsics* K, const doub
   Pose32 T;
   memset(&T, 0, sizeof(T));
   return render_launch(m, *K, T, T_wc_dev, out, (cudaStream_t)stream, nullptr);
+}
+
+static dtsdf_status ensure_combined(dtsdf_map m, cudaStream_t s) {
+  if (m->comb_state) return DTSDF_OK;
+  const size_t nd = m->v.dir_cap;
+  float2* comb = nullptr;
+  float4* col = nullptr;
+  uint32_t* gen = nullptr;
+  CombState* st = nullptr;
+  cudaError_t e = cudaMalloc((void**)&comb, sizeof(float2) * CVOX * nd);
+  if (e == cudaSuccess && m->p.color) e = cudaMalloc((void**)&col, sizeof(float4) * CVOX * nd);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&gen, sizeof(uint32_t) * nd);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&st, sizeof(CombState));
+  if (e == cudaSuccess) e = cudaMemsetAsync(gen, 0xFF, sizeof(uint32_t) * nd, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(CombState), s);
+  if (e != cudaSuccess) {
+    cudaFree(comb);
+    cudaFree(col);
+    cudaFree(gen);
+    cudaFree(st);
+    return cuda_fail(e, "combined TSDF allocation");
+  }
+  m->v.comb = comb;
+  m->v.comb_col = col;
+  m->v.comb_gen = gen;
+  m->v.comb_cur = (const uint32_t*)((const char*)st + offsetof(CombState, gen));
+  m->comb_state = st;
+  return DTSDF_OK;
+}
+
+static dtsdf_status render_combined_impl(dtsdf_map m, const dtsdf_intrinsics* K, const double* T_host,
+                                         const double* T_dev, const dtsdf_render_out* out, void* stream) {
+  if (!m || !intr_ok(K) || (T_host ? !pose_ok(T_host) : !T_dev) || !out || !out->depth || !out->normals)
+    return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  dtsdf_status st = ensure_combined(m, s);
+  if (st != DTSDF_OK) return st;
+  launch_combine(m->v, m->comb_state, to_intr(*K), T_dev, T_host, m->comb_force ? 1 : 0, num_sms(), s);
+  CK_LAUNCH("combine");
+  m->comb_force = false;
+  RenderJob J;
+  memset(&J, 0, sizeof(J));
+  J.K = to_intr(*K);
+  J.Tdev = T_dev;
+  if (T_host) J.T = to_pose32(T_host);
+  J.depth = out->depth;
+  J.normals = (float4*)out->normals;
+  J.color = (float4*)out->color;
+  unsigned* q = render_slot(m);
+  CK(cudaMemsetAsync(q, 0, sizeof(unsigned), s));
+  CK(launch_render_jobs(m->v, &J, 1, q, s, nullptr, m->shape, m->pool, true));
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_render_combined(dtsdf_map m, const dtsdf_intrinsics* K, const double T_wc[16],
+                                   const dtsdf_render_out* out, void* stream) {
+  if (!T_wc) return fail(DTSDF_ERR_INVALID_ARG, "null pose");
+  return render_combined_impl(m, K, T_wc, nullptr, out, stream);
+}
+
+dtsdf_status dtsdf_render_combined_dev(dtsdf_map m, const dtsdf_intrinsics* K, const double* T_wc_dev,
+                                       const dtsdf_render_out* out, void* stream) {
+  if (!T_wc_dev) return fail(DTSDF_ERR_INVALID_ARG, "null pose");
+  return render_combined_impl(m, K, nullptr, T_wc_dev, out, stream);
+}
+
+dtsdf_status dtsdf_combined_reset(dtsdf_map m) {
+  if (!m) return fail(DTSDF_ERR_INVALID_ARG, "null map");
+  m->comb_force = true;
+  return DTSDF_OK;
 }
 
 dtsdf_status dtsdf_set_render_opts(dtsdf_map m, const dtsdf_render_opts* o) {

@@ -26,6 +26,12 @@ constexpr int PVOX = PAD * PAD * PAD;   // 1331 voxels per padded geometry brick
 __host__ __device__ __forceinline__ int pad_index(int x, int y, int z) {
   return ((z + 1) * PAD + (y + 1)) * PAD + (x + 1);
 }
+// Combined bricks hold local coordinates [0, 8]^3 (the trilinear corners of every sample whose
+// base voxel lies in the block). STORE_COMBINED selects the ray-cast of the combined field.
+constexpr int CEDGE = 9;
+constexpr int CVOX = CEDGE * CEDGE * CEDGE;
+constexpr int STORE_COMBINED = 2;
+__host__ __device__ __forceinline__ int comb_index(int x, int y, int z) { return (z * CEDGE + y) * CEDGE + x; }
 constexpr unsigned long long EMPTY_KEY = ~0ull;
 constexpr int MAX_PROBE = 256;  // linear-probe bound; the table is kept at most half full
 constexpr int SLOT_MASK = 6;    // dir_slots[d * 8 + 6]: bitmask of allocated directions
@@ -144,6 +150,12 @@ struct MapView {
   float* bound;        // per brick: minimum sdf over local voxels [0, 8]^3 with weight > 0 (+inf if none)
   uint32_t* stamp;     // per brick: last frame whose fusion or allocation changed its voxels
   uint32_t frame;      // id of the frame being fused
+  // view-dependent combined TSDF (allocated on first use): per directory entry the combined
+  // values of local voxels [0, 8]^3 (CVOX), x fastest, and the generation they belong to
+  float2* comb;        // (phi, 1 if defined else 0)
+  float4* comb_col;    // (r, g, b, 1 if defined else 0), colour maps only
+  uint32_t* comb_gen;  // per directory entry
+  const uint32_t* comb_cur;  // device word: the current generation
   uint32_t* occ;       // occupancy filters: 2 x OCC_WORDS words (blocks, then 4^3-block super-cells)
   uint32_t pool_cap;
   uint32_t* counters;

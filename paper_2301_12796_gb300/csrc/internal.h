@@ -88,11 +88,31 @@ struct RenderShape {
   int tile_w = 4;
 };
 
+// Combined TSDF: device state of the conditional combination (combined.cu).
+struct CombState {
+  double pose[16];     // camera -> world pose of the current combination
+  uint32_t gen;        // generation of the current combination (comb_gen of its blocks)
+  uint32_t frames;     // combined renders so far
+  uint32_t since;      // combined renders since the last full combination
+  uint32_t full;       // this call recombines every block in view
+  uint32_t pool_mark;  // brick count at the previous call
+  uint32_t pool_from;  // bricks from this index on were allocated since the previous call
+};
+struct Pose64 {
+  double T[16];
+};
+struct CombFrame {
+  float pl[4][3];  // inward unit normals of the padded frustum's side planes (camera frame)
+};
+// Conditional combination and the combine pass for a render at T (device pose, else host).
+void launch_combine(const MapView& m, CombState* st, const Intr& K, const double* Tdev, const double* Thost, int force,
+                    int num_sms, cudaStream_t s);
+
 // Render njobs (1..MAX_RENDER_JOBS) frames in one persistent launch. With a memory pool, a
 // pre-pass first records per ray tile the depth range of the allocated blocks in view
 // (stream-ordered scratch from `pool`), so rays start and end their march there.
 cudaError_t launch_render_jobs(const MapView& m, const RenderJob* jobs, int njobs, unsigned* queue, cudaStream_t s,
-                               uint8_t* touched, const RenderShape& shape, cudaMemPool_t pool);
+                               uint8_t* touched, const RenderShape& shape, cudaMemPool_t pool, bool combined = false);
 void launch_frame_pyramid(const float4* P, const uint8_t* rgb, int levels, const Intr* K, float* const* depth,
                           float* const* inten, cudaStream_t s);
 void launch_keyframe_pyramid(const uint8_t* rgb, int levels, const Intr* K, float* const* tmpI, float4* const* kf,

@@ -309,6 +309,130 @@ __device__ __forceinline__ int sign_fast(const MapView& m, Cell& c, const float 
   return 2;
 }
 
+// ------------------------------------------------------ combined-TSDF mode
+// The same march over the view-dependent combined TSDF (combined.cu): a block cell is present
+// when its combined brick belongs to the current combination; the field at a sample is the
+// trilinear interpolation of the combined values (all 8 corners defined), so the sign test
+// is exact and the bracket ends take its value; the outputs add the normal (central
+// differences of that field at +-h, corner differences first) and the trilinear colour.
+__device__ __forceinline__ void cell_enter_comb(const MapView& m, Cell& c, int x, int y, int z, uint32_t gen) {
+  c.cx = x;
+  c.cy = y;
+  c.cz = z;
+  c.jumped = false;
+  c.positive = false;
+  const int d = val_dir(probe_block(m.keys, m.vals, m.hmask, x, y, z));
+  const bool ok = d >= 0 && __ldg(m.comb_gen + d) == gen;
+  c.slot[0] = ok ? d : -1;
+  c.cmask = ok ? 1u : 0u;
+}
+
+__host__ __device__ __forceinline__ constexpr int ccoff(int q) {
+  return (q & 1) + CEDGE * ((q >> 1) & 1) + CEDGE * CEDGE * (q >> 2);
+}
+
+// combined value at local voxel (lx, ly, lz) of the cell, -1 <= l <= 9 (beyond [0, 8] through
+// the neighbouring block); false where undefined
+__device__ __forceinline__ bool comb_at(const MapView& m, const Cell& c, int lx, int ly, int lz, uint32_t gen,
+                                        float& v) {
+  if ((unsigned)lx <= 8u && (unsigned)ly <= 8u && (unsigned)lz <= 8u) {
+    const float2 e = __ldg(m.comb + (size_t)c.slot[0] * CVOX + comb_index(lx, ly, lz));
+    v = e.x;
+    return e.y > 0.0f;
+  }
+  const int ex = lx >> 3, ey = ly >> 3, ez = lz >> 3;
+  const int d = val_dir(probe_block(m.keys, m.vals, m.hmask, c.cx + ex, c.cy + ey, c.cz + ez));
+  if (d < 0 || __ldg(m.comb_gen + d) != gen) return false;
+  const float2 e = __ldg(m.comb + (size_t)d * CVOX + comb_index(lx & 7, ly & 7, lz & 7));
+  v = e.x;
+  return e.y > 0.0f;
+}
+
+__device__ __forceinline__ int sign_comb(const MapView& m, const Cell& c, const float g[3], float& val, int& npres) {
+  const float f0 = floorf(g[0]), f1 = floorf(g[1]), f2 = floorf(g[2]);
+  const float fx = g[0] - f0, fy = g[1] - f1, fz = g[2] - f2;
+  const size_t base = (size_t)c.slot[0] * CVOX +
+                      comb_index((int)f0 - 8 * c.cx, (int)f1 - 8 * c.cy, (int)f2 - 8 * c.cz);
+  float2 v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = __ldg(m.comb + base + ccoff(q));
+  bool ok = true;
+  float s[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    ok &= v[q].y > 0.0f;
+    s[q] = v[q].x;
+  }
+  npres = ok ? 1 : 0;
+  if (!ok) return 0;
+  val = tri(s, fx, fy, fz);
+  return val > 0.0f ? 1 : -1;
+}
+
+template <bool COLOR>
+__device__ __forceinline__ Combined full_comb(const MapView& m, const Cell& c, const float g[3], bool want_color,
+                                              uint32_t gen) {
+  Combined out;
+  out.defined = 0;
+  out.phi = 0.f;
+  out.wsum = 0.f;
+  out.n[0] = out.n[1] = out.n[2] = 0.f;
+  out.rgb[0] = out.rgb[1] = out.rgb[2] = 0.f;
+  out.cw = 0.f;
+  int np = 0;
+  float val = 0.f;
+  if (sign_comb(m, c, g, val, np) == 0) return out;
+  out.defined = 1;
+  out.phi = val;
+  const float f0 = floorf(g[0]), f1 = floorf(g[1]), f2 = floorf(g[2]);
+  const float fx = g[0] - f0, fy = g[1] - f1, fz = g[2] - f2;
+  const int l0 = (int)f0 - 8 * c.cx, l1 = (int)f1 - 8 * c.cy, l2 = (int)f2 - 8 * c.cz;
+  float gr[3];
+  bool gok = true;
+#pragma unroll 1
+  for (int a = 0; a < 3 && gok; ++a) {
+    float dv[8];
+    for (int q = 0; q < 8 && gok; ++q) {
+      const int x = l0 + (q & 1), y = l1 + ((q >> 1) & 1), z = l2 + (q >> 2);
+      float vp = 0.f, vm = 0.f;
+      gok = comb_at(m, c, x + (a == 0), y + (a == 1), z + (a == 2), gen, vp) &&
+            comb_at(m, c, x - (a == 0), y - (a == 1), z - (a == 2), gen, vm);
+      dv[q] = vp - vm;
+    }
+    if (gok) gr[a] = tri(dv, fx, fy, fz) * (0.5f / m.h);
+  }
+  if (gok) {
+    const float gn = sqrtf(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+    if (gn > 1e-12f) {
+      out.wsum = 1.0f;
+      out.n[0] = gr[0] / gn;
+      out.n[1] = gr[1] / gn;
+      out.n[2] = gr[2] / gn;
+    }
+  }
+  if (COLOR && want_color) {
+    const size_t base = (size_t)c.slot[0] * CVOX + comb_index(l0, l1, l2);
+    float cr = 0.f, cg = 0.f, cb = 0.f;
+    bool cok = true;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 cv = __ldg(m.comb_col + base + ccoff(q));
+      cok &= cv.w > 0.0f;
+      const float wq = corner_w(q, fx, fy, fz);
+      cr += wq * cv.x;
+      cg += wq * cv.y;
+      cb += wq * cv.z;
+    }
+    if (cok) {
+      out.cw = 1.0f;
+      out.rgb[0] = cr;
+      out.rgb[1] = cg;
+      out.rgb[2] = cb;
+    }
+  }
+  return out;
+}
+
 // One loop, one state machine per lane: marching (MARCH), the regular sub-step scan
 // of the refinement (SCAN), the full evaluations at the final bracket ends (ENDS_A/B) and
 // the output evaluations (OUT) all evaluate the field at one call site of the sign test
@@ -333,6 +457,7 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
 
   Cell cell;
   cell.slot = s_slot + tid;
+  const uint32_t cgen = STORE == STORE_COMBINED ? __ldg(m.comb_cur) : 0u;
   const float org[3] = {m.ox, m.oy, m.oz};
   const float inv_h = 1.0f / m.h;
   const float step = 0.5f * m.h;
@@ -483,7 +608,10 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
           continue;
         }
       }
-      cell_enter(m, cell, cx, cy, cz);
+      if constexpr (STORE == STORE_COMBINED)
+        cell_enter_comb(m, cell, cx, cy, cz, cgen);
+      else
+        cell_enter(m, cell, cx, cy, cz);
       if (COUNT && state == S_MARCH) {
         ++n_cells;
         n_acells += cell.cmask != 0;
@@ -533,7 +661,10 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
       bool full = state >= S_OUT;
       if (!full) {
         int npres = 0;
-        sg = sign_fast<STORE, COUNT>(m, cell, g, r, val, npres, touched);
+        if constexpr (STORE == STORE_COMBINED)
+          sg = sign_comb(m, cell, g, val, npres);
+        else
+          sg = sign_fast<STORE, COUNT>(m, cell, g, r, val, npres, touched);
         full = sg == 2 || (state >= S_ENDS_A && npres > 1);
         if (!full && state >= S_ENDS_A) {
           C.defined = sg != 0;
@@ -542,7 +673,10 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
       }
       if (full) {
         if (COUNT && state == S_MARCH) ++n_full;
-        C = combine_full<STORE, COLOR, COUNT>(m, cell, g, r, touched, state == S_OUT);
+        if constexpr (STORE == STORE_COMBINED)
+          C = full_comb<COLOR>(m, cell, g, state == S_OUT, cgen);
+        else
+          C = combine_full<STORE, COLOR, COUNT>(m, cell, g, r, touched, state == S_OUT);
         sg = C.defined ? (C.phi > 0.f ? 1 : -1) : 0;
         val = C.phi;
       }
@@ -732,7 +866,15 @@ void launch_k_render(const MapView& m, const RenderBatch<NJ>& a, int ctas, cudaS
 }
 
 template <int NJ>
-void dispatch_render(const MapView& m, const RenderBatch<NJ>& a, bool col, int ctas, cudaStream_t s) {
+void dispatch_render(const MapView& m, const RenderBatch<NJ>& a, bool col, int ctas, cudaStream_t s,
+                     bool combined) {
+  if (combined) {
+    if (col && m.comb_col)
+      launch_k_render<STORE_COMBINED, true, false, NJ>(m, a, ctas, s);
+    else
+      launch_k_render<STORE_COMBINED, false, false, NJ>(m, a, ctas, s);
+    return;
+  }
   const bool cnt = a.touched != nullptr;
 #define DTSDF_RENDER(ST, CO, CN) launch_k_render<ST, CO, CN, NJ>(m, a, ctas, s)
   if (cnt) {
@@ -777,7 +919,7 @@ void fill_batch(RenderBatch<NJ>& a, const RenderJob* jobs, int njobs, unsigned* 
 // scratch is freed on the stream after the render, so concurrent launches never share it.
 template <int NJ>
 cudaError_t range_and_render(const MapView& m, RenderBatch<NJ>& a, bool col, int ctas, cudaStream_t s,
-                             cudaMemPool_t pool) {
+                             cudaMemPool_t pool, bool combined) {
   uint32_t* buf = nullptr;
   const size_t ntiles = (size_t)a.total / 32;
   a.zlo = a.zhi = nullptr;
@@ -797,7 +939,7 @@ cudaError_t range_and_render(const MapView& m, RenderBatch<NJ>& a, bool col, int
     a.zlo = buf;
     a.zhi = buf + ntiles;
   }
-  dispatch_render(m, a, col, ctas, s);
+  dispatch_render(m, a, col, ctas, s, combined);
   cudaError_t e = cudaGetLastError();
   if (buf) {
     const cudaError_t f = cudaFreeAsync(buf, s);
@@ -807,7 +949,7 @@ cudaError_t range_and_render(const MapView& m, RenderBatch<NJ>& a, bool col, int
 }
 
 cudaError_t launch_render_jobs(const MapView& m, const RenderJob* jobs, int njobs, unsigned* queue, cudaStream_t s,
-                               uint8_t* touched, const RenderShape& sh, cudaMemPool_t pool) {
+                               uint8_t* touched, const RenderShape& sh, cudaMemPool_t pool, bool combined) {
   const int ctas = sh.ctas, refill = sh.refill, tile_w = sh.tile_w;
   bool col = false;
   for (int i = 0; i < njobs; ++i) col |= jobs[i].color != nullptr;
@@ -815,11 +957,11 @@ cudaError_t launch_render_jobs(const MapView& m, const RenderJob* jobs, int njob
   if (njobs == 1) {
     RenderBatch<1> a;
     fill_batch(a, jobs, njobs, queue, touched, refill, tile_w);
-    return range_and_render(m, a, col, ctas, s, pool);
+    return range_and_render(m, a, col, ctas, s, pool, combined);
   }
   RenderBatch<MAX_RENDER_JOBS> a;
   fill_batch(a, jobs, njobs, queue, touched, refill, tile_w);
-  return range_and_render(m, a, col, ctas, s, pool);
+  return range_and_render(m, a, col, ctas, s, pool, combined);
 }
 
 }  // namespace dtsdf

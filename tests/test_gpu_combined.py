@@ -1,0 +1,123 @@
+"""Combined-TSDF render mode (dtsdf_render_combined) against the FP64 oracle's combination and
+ray-cast, on the oracle's own map loaded into the device map: the tiny dense room at several
+poses, the Kinect-shaped room at full size on sampled rays, and the conditional combination
+(the stored field is reused after a small motion and recomputed after a large one).
+
+Tolerances as for the direct render: hit mask >= 99.9 %, depth <= 1e-4 m and normals
+<= 1e-3 rad on >= 99.9 % of the pixels both sides hit, colour <= 0.5 of 255."""
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+torch = pytest.importorskip("torch")
+import paper_2301_12796_gb300 as dt  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def device_copy(om, **kw):
+    ob = om.bricks()
+    vox = np.stack([om.brick(*b[:4]) for b in ob]).astype(np.float32)
+    gm = dt.Map(dt.params(max_blocks=len(ob) + 64, **kw))
+    gm.import_bricks(ob[:, :4], vox)
+    return gm
+
+
+def render_comb(gm, K, T):
+    d = torch.zeros(K.height, K.width, device=DEV)
+    n = torch.zeros(K.height, K.width, 4, device=DEV)
+    c = torch.zeros(K.height, K.width, 4, device=DEV)
+    gm.render_combined(K, T, d, n, c)
+    torch.cuda.synchronize()
+    return d.cpu().numpy(), n.cpu().numpy(), c.cpu().numpy()
+
+
+def compare(g, o, pix=None):
+    dg, ng, cg = g
+    do, no, co, cok = o
+    if pix is not None:
+        dg, ng, cg = dg[pix[:, 1], pix[:, 0]], ng[pix[:, 1], pix[:, 0]], cg[pix[:, 1], pix[:, 0]]
+    hg, ho = dg > 0, do > 0
+    both = hg & ho
+    derr = np.abs(dg[both] - do[both])
+    nerr = np.arccos(np.clip(np.sum(ng[both][..., :3] * no[both], -1), -1, 1))
+    cb = both & (cg[..., 3] > 0) & (cok > 0)
+    cerr = np.abs(cg[cb][..., :3] - co[cb]).max() if cb.any() else 0.0
+    return float(np.mean(hg == ho)), derr, nerr, cerr, int(both.sum())
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    s = scenes.tiny_scene(1)
+    kw = dict(voxel_size=0.01, truncation=0.04, dense_dim=64, color=True)
+    om = oracle.OracleMap(oracle.Params(**kw))
+    for i in range(10):
+        f = s.frame(i)
+        om.integrate(f.depth, f.rgb, s.K, f.pose)
+    return s, om, kw
+
+
+@pytest.mark.parametrize("fi", [0, 4, 8])
+def test_combined_render_matches_oracle(tiny, fi):
+    s, om, kw = tiny
+    gm = device_copy(om, **kw)
+    T = s.poses[fi] @ scenes.perturbation(np.random.default_rng(fi), 1.0, 0.005)
+    g = render_comb(gm, s.K, T)  # first call: boot-up, the whole frustum is combined at T
+    om.combine(T[:3, 3])
+    agree, derr, nerr, cerr, n = compare(g, om.render_combined(s.K, T))
+    print(f"combined fi={fi}: mask {agree:.5f} depth max {derr.max():.2e} normals {np.mean(nerr <= 1e-3):.5f}")
+    assert n > 5000
+    assert agree >= 0.999
+    assert np.mean(derr <= 1e-4) >= 0.999 and np.median(derr) < 1e-6
+    assert np.mean(nerr <= 1e-3) >= 0.999
+    assert cerr <= 0.5
+
+
+def test_conditional_combination_reuses_and_recomputes(tiny):
+    s, om, kw = tiny
+    gm = device_copy(om, **kw)
+    K = s.K
+    T1 = s.poses[3]
+    for _ in range(5):  # boot-up: five recombinations at T1
+        render_comb(gm, K, T1)
+    T2 = T1 @ scenes.perturbation(np.random.default_rng(2), 1.0, 0.01)  # small motion: field kept
+    g2 = render_comb(gm, K, T2)
+    om.combine(T1[:3, 3])
+    agree, derr, nerr, _, _ = compare(g2, om.render_combined(K, T2))
+    assert agree >= 0.999 and np.mean(derr <= 1e-4) >= 0.999 and np.mean(nerr <= 1e-3) >= 0.999
+    T3 = s.poses[7]  # large motion: recombined at T3
+    g3 = render_comb(gm, K, T3)
+    om.combine(T3[:3, 3])
+    agree, derr, nerr, _, _ = compare(g3, om.render_combined(K, T3))
+    assert agree >= 0.999 and np.mean(derr <= 1e-4) >= 0.999 and np.mean(nerr <= 1e-3) >= 0.999
+    # a reset forces the recombination at the next pose even for a small motion
+    gm.combined_reset()
+    T4 = T3 @ scenes.perturbation(np.random.default_rng(4), 0.5, 0.005)
+    g4 = render_comb(gm, K, T4)
+    om.combine(T4[:3, 3])
+    agree, derr, _, _, _ = compare(g4, om.render_combined(K, T4))
+    assert agree >= 0.999 and np.mean(derr <= 1e-4) >= 0.999
+
+
+def test_combined_render_full_size_sampled():
+    s = scenes.kinect_room(1)
+    kw = dict(voxel_size=0.005, truncation=0.02, color=True, z_max=s.z_max)
+    om = oracle.OracleMap(oracle.Params(**kw))
+    for i in range(0, 300, 20):
+        f = s.frame(i)
+        om.integrate(f.depth, f.rgb, s.K, f.pose)
+    gm = device_copy(om, **kw)
+    K, T = s.K, s.poses[150]
+    g = render_comb(gm, K, T)
+    om.combine(T[:3, 3])
+    vv, uu = np.mgrid[0:K.height:4, 0:K.width:4]
+    pix = np.stack([uu.ravel(), vv.ravel()], 1).astype(np.int32)
+    agree, derr, nerr, cerr, n = compare(g, om.render_combined(K, T, pix), pix)
+    print(f"combined full size: mask {agree:.5f} depth<=1e-4 {np.mean(derr <= 1e-4):.5f} "
+          f"normals {np.mean(nerr <= 1e-3):.5f} colour {cerr:.3f}")
+    assert n > 10000 and agree >= 0.999
+    assert np.mean(derr <= 1e-4) >= 0.999
+    assert np.mean(nerr <= 1e-3) >= 0.995
