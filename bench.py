@@ -74,6 +74,9 @@ def parse():
                          "registration of 1280x720 second-sensor frames against the 640x480 map; serve: "
                          "a Poisson stream of render + registration requests of mixed sizes served by the "
                          "continuous-batching server over FP16 maps, against serial FP32 solves")
+    ap.add_argument("--render-mode", default="direct", choices=["direct", "combined"],
+                    help="tracking: direct ray-cast of the six directions (default) or the ray-cast of the "
+                         "view-dependent combined TSDF with conditional combination")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
                     help="map storage: FP32 sdf/weight/colour, or FP16 sdf + half weight + u8 colour")
     ap.add_argument("--problems", type=int, default=64, help="multi_sensor: registration problems per step")
@@ -180,8 +183,9 @@ LAUNCHES = {"render": 2, "set_frame": 6, "set_keyframe": 6, "compose": 1, "solve
 class Tracker:
     """Device-resident tracking loop over the frames (map, ICP context, buffers, poses)."""
 
-    def __init__(self, dt, torch, s, frames, dev, map_frames, storage=0):
+    def __init__(self, dt, torch, s, frames, dev, map_frames, storage=0, combined=False):
         self.dt, self.torch, self.s, self.dev = dt, torch, s, dev
+        self.combined = combined
         K = s.K
         self.K = K
         self.map = dt.Map(dt.params(voxel_size=0.005, truncation=0.02, max_blocks=1 << 19, z_max=s.z_max, color=True,
@@ -215,12 +219,15 @@ class Tracker:
         ref = self.est[f - 1]
         if ev:
             ev[0].record()
-        self.map.render_dev(K, ref, self.ref_d, self.ref_n, self.ref_c)
+        if self.combined:
+            self.map.render_combined_dev(K, ref, self.ref_d, self.ref_n, self.ref_c)
+        else:
+            self.map.render_dev(K, ref, self.ref_d, self.ref_n, self.ref_c)
         if ev:
             ev[1].record()
         self.icp.set_frame(self.depth[f], self.rgb[f], K, 0.1, self.s.z_max, 0.01)
         kf = 10 * ((f - 1) // 10)
-        n = LAUNCHES["render"] + LAUNCHES["set_frame"]
+        n = LAUNCHES["render"] + (2 if self.combined else 0) + LAUNCHES["set_frame"]
         if kf != self.kf:
             self.icp.set_keyframe(self.rgb[kf], K)
             self.kf = kf
@@ -335,7 +342,8 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
     storage = 1 if args.storage == "fp16" else 0
     n_frames = 60 if args.profile else args.frames
     s, frames = make_workload(n_frames)
-    tr = Tracker(dt, torch, s, frames, dev, range(n_frames), storage)
+    combined = args.render_mode == "combined"
+    tr = Tracker(dt, torch, s, frames, dev, range(n_frames), storage, combined)
     st = tr.map.stats()
     l2 = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MB > L2
     for i in range(args.warmup):
@@ -401,9 +409,40 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
                "steps": n_e2e}
     # ---------------- roofline of the dominant kernel
     render_ms = float(ph[:, 0].mean())
+    comb = None
+    if combined:
+        # the combine pass alone, forced over the padded frustum (L2 flushed before each run)
+        pose = tr.est[1 + args.warmup % (tr.n - 1)]
+        tr.map.combine_dev(s.K, pose, force=True)
+        torch.cuda.synchronize()
+        blocks, cbricks = tr.map.combined_blocks()
+        ts = []
+        for _ in range(5):
+            flush_l2(l2)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            tr.map.combine_dev(s.K, pose, force=True)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        comb_ms = float(np.mean(ts))
+        gvb, cvb = voxel_bytes(storage)
+        comb_bytes = cbricks * 512 * (gvb + cvb) + blocks * 729 * (8 + 16)
+        comb = {"blocks": int(blocks), "bricks": int(cbricks), "full_combine_ms": comb_ms,
+                "algorithmic_bytes": float(comb_bytes)}
     peak, peak_kind = measured_hbm_peak()
     achieved = render_bytes / (render_ms / 1000.0) / 1e9
-    roof = {"kernel": "k_render (direct DTSDF ray-cast)", "bound": "hbm", "achieved": achieved, "peak": peak,
+    if comb is not None:
+        a_c = comb["algorithmic_bytes"] / (comb["full_combine_ms"] / 1000.0) / 1e9
+        roof = {"kernel": "k_combine (view-dependent combined TSDF, whole padded frustum)", "bound": "hbm",
+                "achieved": a_c, "peak": peak, "unit": "GB/s", "frac": a_c / peak, "peak_kind": peak_kind,
+                "traffic": None, "algorithmic_bytes_per_launch": comb["algorithmic_bytes"],
+                "launch_ms": comb["full_combine_ms"],
+                "bytes_definition": "source (block, direction) bricks' core voxels (geometry + colour) read once, "
+                                    "729 combined voxels x 24 B written per block"}
+    else:
+        roof = None
+    roof = roof or {"kernel": "k_render (direct DTSDF ray-cast)", "bound": "hbm", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
             "traffic": render_traffic() if storage == 0 and not args.profile else None,
             "algorithmic_bytes_per_launch": render_bytes, "geom_bricks": geom_b, "color_bricks": col_b,
@@ -418,7 +457,8 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": WORKLOAD if not storage else WORKLOAD_FP16, "resolution": "640x480",
-                          "storage": args.storage, "map_frames": n_frames,
+                          "storage": args.storage, "map_frames": n_frames, "render_mode": args.render_mode,
+                          "combined": comb,
                           "map_bricks": int(st.bricks), "map_voxels_per_direction_M": [round(x * 512 / 1e6, 2)
                                                                                       for x in st.bricks_per_dir],
                           "l2": "flushed between steps (512 MB write outside the timed events)",

@@ -161,6 +161,18 @@ DTSDF_API dtsdf_status dtsdf_render_combined_dev(dtsdf_map map, const dtsdf_intr
 /* The next combined render recombines the whole frustum at its pose. */
 DTSDF_API dtsdf_status dtsdf_combined_reset(dtsdf_map map);
 
+/* The combination step of dtsdf_render_combined alone (conditional as there, or the whole
+ * padded frustum at T_wc when force != 0), for callers that precompute the combined TSDF
+ * ahead of their renders. Asynchronous. */
+DTSDF_API dtsdf_status dtsdf_combine(dtsdf_map map, const dtsdf_intrinsics* K, const double T_wc[16], int32_t force,
+                                     void* stream);
+DTSDF_API dtsdf_status dtsdf_combine_dev(dtsdf_map map, const dtsdf_intrinsics* K, const double* T_wc_dev,
+                                         int32_t force, void* stream);
+
+/* Blocks of the current combination and the (block, direction) bricks they hold (host
+ * outputs); 0 before the first combination. Synchronous. */
+DTSDF_API dtsdf_status dtsdf_combined_blocks(dtsdf_map map, int64_t* blocks, int64_t* bricks, void* stream);
+
 /* Launch shape of the map's renders (no counterpart in the paper: scheduling only; every
  * shape computes the same samples, decisions and outputs). ctas: CTAs of the persistent
  * render grid, 0 = one wave of resident CTAs. tile_w: width of the pixel tiles of 32 rays

@@ -121,6 +121,9 @@ SIGNATURES = {
     "dtsdf_render_combined": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), P], c_int32),
     "dtsdf_render_combined_dev": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), P], c_int32),
     "dtsdf_combined_reset": ([P], c_int32),
+    "dtsdf_combine": ([P, ctypes.POINTER(Intrinsics), P, c_int32, P], c_int32),
+    "dtsdf_combine_dev": ([P, ctypes.POINTER(Intrinsics), P, c_int32, P], c_int32),
+    "dtsdf_combined_blocks": ([P, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64), P], c_int32),
     "dtsdf_set_render_opts": ([P, ctypes.POINTER(RenderOpts)], c_int32),
     "dtsdf_render_tune": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), ctypes.POINTER(RenderOpts),
                            ctypes.POINTER(ctypes.c_float), P], c_int32),
@@ -265,6 +268,24 @@ class Map:
         Ki = intrinsics(K)
         check(lib().dtsdf_render_combined_dev(self._h, ctypes.byref(Ki), T_dev.data_ptr(), ctypes.byref(out),
                                               _stream_ptr(stream)), "dtsdf_render_combined_dev")
+
+    def combine(self, K, T_wc, force=False, stream=None):
+        """The combination step alone (host pose); force recombines the whole padded frustum."""
+        Ki = intrinsics(K)
+        check(lib().dtsdf_combine(self._h, ctypes.byref(Ki), pose_buf(T_wc), int(bool(force)), _stream_ptr(stream)),
+              "dtsdf_combine")
+
+    def combine_dev(self, K, T_dev, force=False, stream=None):
+        Ki = intrinsics(K)
+        check(lib().dtsdf_combine_dev(self._h, ctypes.byref(Ki), T_dev.data_ptr(), int(bool(force)),
+                                      _stream_ptr(stream)), "dtsdf_combine_dev")
+
+    def combined_blocks(self, stream=None):
+        """(blocks, bricks) of the current combination."""
+        b, k = c_int64(), c_int64()
+        check(lib().dtsdf_combined_blocks(self._h, ctypes.byref(b), ctypes.byref(k), _stream_ptr(stream)),
+              "dtsdf_combined_blocks")
+        return b.value, k.value
 
     def combined_reset(self):
         """The next combined render recombines the whole frustum at its pose."""

@@ -458,6 +458,54 @@ dtsdf_status dtsdf_render_combined_dev(dtsdf_map m, const dtsdf_intrinsics* K, c
   return render_combined_impl(m, K, nullptr, T_wc_dev, out, stream);
 }
 
+static dtsdf_status combine_impl(dtsdf_map m, const dtsdf_intrinsics* K, const double* T_host, const double* T_dev,
+                                 int32_t force, void* stream) {
+  if (!m || !intr_ok(K) || (T_host ? !pose_ok(T_host) : !T_dev)) return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  dtsdf_status st = ensure_combined(m, s);
+  if (st != DTSDF_OK) return st;
+  launch_combine(m->v, m->comb_state, to_intr(*K), T_dev, T_host, (force || m->comb_force) ? 1 : 0, num_sms(), s);
+  CK_LAUNCH("combine");
+  m->comb_force = false;
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_combine(dtsdf_map m, const dtsdf_intrinsics* K, const double T_wc[16], int32_t force,
+                           void* stream) {
+  if (!T_wc) return fail(DTSDF_ERR_INVALID_ARG, "null pose");
+  return combine_impl(m, K, T_wc, nullptr, force, stream);
+}
+
+dtsdf_status dtsdf_combine_dev(dtsdf_map m, const dtsdf_intrinsics* K, const double* T_wc_dev, int32_t force,
+                               void* stream) {
+  if (!T_wc_dev) return fail(DTSDF_ERR_INVALID_ARG, "null pose");
+  return combine_impl(m, K, nullptr, T_wc_dev, force, stream);
+}
+
+dtsdf_status dtsdf_combined_blocks(dtsdf_map m, int64_t* blocks, int64_t* bricks, void* stream) {
+  if (!m || !blocks || !bricks) return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  *blocks = *bricks = 0;
+  if (!m->comb_state) return DTSDF_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t cnt[C_COUNT];
+  CombState st;
+  CK(cudaMemcpyAsync(cnt, m->v.counters, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&st, m->comb_state, sizeof(st), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const uint32_t nd = cnt[C_DIR] < m->v.dir_cap ? cnt[C_DIR] : m->v.dir_cap;
+  if (!nd) return DTSDF_OK;
+  std::vector<uint32_t> gen(nd);
+  std::vector<int32_t> slots(8 * (size_t)nd);
+  CK(cudaMemcpy(gen.data(), m->v.comb_gen, sizeof(uint32_t) * nd, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(slots.data(), m->v.dir_slots, sizeof(int32_t) * 8 * nd, cudaMemcpyDeviceToHost));
+  for (uint32_t d = 0; d < nd; ++d) {
+    if (gen[d] != st.gen) continue;
+    *blocks += 1;
+    *bricks += __builtin_popcount((uint32_t)slots[8 * (size_t)d + SLOT_MASK]);
+  }
+  return DTSDF_OK;
+}
+
 dtsdf_status dtsdf_combined_reset(dtsdf_map m) {
   if (!m) return fail(DTSDF_ERR_INVALID_ARG, "null map");
   m->comb_force = true;
