@@ -45,7 +45,7 @@ FALLBACK_HBM_GBS = 6800.0
 # default workload (FP32 storage with colour, first timed render), from one ncu capture of
 # ``bench.py --steps 2 --warmup 3 --no-e2e --no-cpu`` (profiles/k_render_kinect640.md). It
 # belongs to the kernel sources it was taken with: reported only while their hash matches.
-RENDER_TRAFFIC = {"bytes": 281623040 + 15153664, "sources_sha1_16": "76cdaec48660ab86",
+RENDER_TRAFFIC = {"bytes": 281753856 + 15643392, "sources_sha1_16": "e1e4d1278955c2e8",
                   "files": ("render.cu", "common.cuh", "internal.h")}
 
 
@@ -183,12 +183,12 @@ LAUNCHES = {"render": 2, "set_frame": 6, "set_keyframe": 6, "compose": 1, "solve
 class Tracker:
     """Device-resident tracking loop over the frames (map, ICP context, buffers, poses)."""
 
-    def __init__(self, dt, torch, s, frames, dev, map_frames, storage=0, combined=False):
+    def __init__(self, dt, torch, s, frames, dev, map_frames, storage=0, combined=False, max_blocks=1 << 19):
         self.dt, self.torch, self.s, self.dev = dt, torch, s, dev
         self.combined = combined
         K = s.K
         self.K = K
-        self.map = dt.Map(dt.params(voxel_size=0.005, truncation=0.02, max_blocks=1 << 19, z_max=s.z_max, color=True,
+        self.map = dt.Map(dt.params(voxel_size=0.005, truncation=0.02, max_blocks=max_blocks, z_max=s.z_max, color=True,
                                     storage=storage))
         self.icp = dt.Icp(K.width, K.height, 3)
         self.opts = opts_kinect(dt)
@@ -343,7 +343,9 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
     n_frames = 60 if args.profile else args.frames
     s, frames = make_workload(n_frames)
     combined = args.render_mode == "combined"
-    tr = Tracker(dt, torch, s, frames, dev, range(n_frames), storage, combined)
+    # the profiling case keeps the device footprint to a few GB (60-frame map: 121k bricks)
+    tr = Tracker(dt, torch, s, frames, dev, range(n_frames), storage, combined,
+                 max_blocks=(1 << 17) if args.profile else (1 << 19))
     st = tr.map.stats()
     l2 = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MB > L2
     for i in range(args.warmup):
