@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--frames", type=int, default=300)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="tracking: skip the compact serving measurement")
     ap.add_argument("--profile", action="store_true", help="small run for ncu: map of 60 frames, few steps")
     ap.add_argument("--workload", default="tracking", choices=["tracking", "multi_sensor", "serve"],
                     help="tracking: Kinect-shaped tracking frames (default); multi_sensor: batched Sim(3) "
@@ -449,6 +450,9 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
             "traffic": render_traffic() if storage == 0 and not args.profile else None,
             "algorithmic_bytes_per_launch": render_bytes, "geom_bricks": geom_b, "color_bricks": col_b,
             "launch_ms": render_ms}
+    serve = None
+    if not args.profile and not args.no_serve:
+        serve = serve_summary(dt, torch, dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and not args.profile:
         ob = OracleBench(s, frames)
@@ -470,7 +474,8 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
                           "rays_per_s": world * npix * args.steps / (total_ms / 1000.0),
                           "march_counts_per_frame": march,
                           "wall_s_timed_loop": t_wall, "median_translation_error_m": terr},
-               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+               "serve": serve, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "clocks": clocks}
         print(json.dumps(out), flush=True)
 
 
@@ -830,10 +835,12 @@ def run_serve(args, dt, torch, tdist, dev, rank, world, local):
     res = serve_stream(srv, reqs, pinned_np)
     clocks = clk.stop()
     st = srv.stats()
-    srv.close()
     lat = np.array([r.t_done - r.t_submit for r in res])
     span = max(r.t_done for r in res) - min(r.t_submit for r in res)
     value = world * len(reqs) / span
+    # latency below capacity: the same kind of stream at a tenth of the offered rate
+    low = serve_requests_low(srv, rooms, max(32, n_req // 4), args.rate / 10.0)
+    srv.close()
     # serial plain FP32 solves of the same stream
     icps = {(K.width, K.height): dt.Icp(K.width, K.height, 3) for K, _ in scenes.SERVE_SENSORS}
     serial_stream(dt, torch, dev, maps32, warm[:8], [q["depth"] for q in warm[:8]], icps)
@@ -894,6 +901,7 @@ def run_serve(args, dt, torch, tdist, dev, rank, world, local):
                                      "peak_inflight": int(st.peak_inflight), "peak_bytes": int(st.peak_bytes)}},
                "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
                               "mean": float(lat.mean() * 1e3)},
+               "latency_below_capacity": low,
                "serial_fp32": {"value": len(reqs) / span_s, "unit": "requests/s",
                                "latency_ms": {"p50": float(np.percentile(lat_s, 50) * 1e3),
                                               "p99": float(np.percentile(lat_s, 99) * 1e3)}},
@@ -914,6 +922,53 @@ def run_serve(args, dt, torch, tdist, dev, rank, world, local):
         print(json.dumps(out), flush=True)
     for m in maps16 + maps32:
         m.close()
+
+
+def serve_requests_low(srv, rooms, n, rate):
+    """p50/p99 latency and throughput of a stream offered at `rate` (below capacity)."""
+    import scenes
+    reqs = scenes.serve_requests(rooms, n, seed=3, rate=rate, pool=min(n, 48))
+    res = serve_stream(srv, reqs, [q["depth"] for q in reqs])
+    lat = np.array([r.t_done - r.t_submit for r in res])
+    return {"requests": n, "offered_per_s": rate, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_batch": float(np.mean([r.batch_size for r in res]))}
+
+
+def serve_summary(dt, torch, dev, n_req=256, rate=2000.0, n_maps=2, n_frames=40):
+    """Compact serving measurement for the tracking line: the continuous-batching server over
+    FP16 maps of seeded rooms, a Poisson stream of mixed-size SE(3)/Sim(3) requests at `rate`,
+    and a stream at a tenth of that rate."""
+    import scenes
+    rooms = [scenes.kinect_room(1 + i, n_frames=n_frames) for i in range(n_maps)]
+    maps = []
+    for room in rooms:
+        m = dt.Map(dt.params(voxel_size=0.005, truncation=0.02, max_blocks=1 << 18, z_max=room.z_max, color=False,
+                             storage=dt.STORE_FP16))
+        for i in range(room.n_frames):
+            f = room.frame(i)
+            m.integrate(torch.from_numpy(f.depth).to(dev), None, room.K, f.pose)
+        maps.append(m)
+    torch.cuda.synchronize()
+    reqs = scenes.serve_requests(rooms, n_req, seed=1, rate=rate, pool=min(n_req, 64))
+    pinned = [torch.from_numpy(q["depth"]).pin_memory().numpy() for q in reqs]
+    p = dt.server_params(hbm_budget=8 << 30, max_inflight=128, max_batch=32, streams=4,
+                         opts=dt.icp_opts(**SERVE_OPTS), shape=(8, 256))
+    srv = dt.Server(maps, p)
+    warm = scenes.serve_requests(rooms, 32, seed=2, rate=rate, pool=8)
+    serve_stream(srv, warm, [q["depth"] for q in warm])
+    res = serve_stream(srv, reqs, pinned)
+    lat = np.array([r.t_done - r.t_submit for r in res])
+    span = max(r.t_done for r in res) - min(r.t_submit for r in res)
+    low = serve_requests_low(srv, rooms, 128, rate / 10.0)
+    srv.close()
+    for m in maps:
+        m.close()
+    return {"workload": f"{n_req} requests, Poisson {rate:g}/s, 320x240 / 640x480 / 1280x720 (0.3 / 0.5 / 0.2), "
+                        f"SE(3):Sim(3) 3:1, {n_maps} FP16 room maps of {n_frames} frames (bench.py --workload serve: "
+                        f"512 requests, 3 maps of 100 frames, against serial FP32)",
+            "requests_per_s": len(reqs) / span, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "below_capacity": low}
 
 
 def ctypes_result_bytes(dt):
