@@ -212,6 +212,7 @@ dtsdf_status dtsdf_create(const dtsdf_params* params, void* stream, dtsdf_map* o
   v.zmax = p.z_max;
   v.dsup = p.delta_sup;
   v.costh = (float)cos((double)p.theta);
+  v.sinth = (float)sin((double)p.theta);
   v.ox = p.dense_origin[0];
   v.oy = p.dense_origin[1];
   v.oz = p.dense_origin[2];

@@ -18,8 +18,12 @@
 
 namespace dtsdf {
 
-__device__ __forceinline__ float w_dir_c(float c, float theta) {
-  const float alpha = acosf(fminf(fmaxf(c, -1.0f), 1.0f));
+// Eq. direction_weight as read; the clamped ranges (angle <= pi/2 - theta: 1, >= theta: 0)
+// are decided on the cosine (cos_hi = sin theta, cos_lo = cos theta) without the arc cosine.
+__device__ __forceinline__ float w_dir_c(float c, float theta, float cos_lo, float cos_hi) {
+  if (c >= cos_hi) return 1.0f;
+  if (c <= cos_lo) return 0.0f;
+  const float alpha = acosf(c);
   return fminf(fmaxf((theta - alpha) / (2.0f * theta - 1.57079632679489662f), 0.0f), 1.0f);
 }
 
@@ -78,6 +82,7 @@ __global__ void __launch_bounds__(256) k_combine(MapView m, const CombState* st,
   __syncthreads();
   const uint32_t ndir = min(*((volatile uint32_t*)(m.counters + C_DIR)), m.dir_cap);
   const float h = m.h;
+  const float cos_lo = m.costh, cos_hi = m.sinth;
   for (uint32_t d = blockIdx.x; d < ndir; d += gridDim.x) {
     const uint32_t mask = (uint32_t)m.dir_slots[(size_t)d * 8 + SLOT_MASK];
     bool take = mask != 0;
@@ -124,10 +129,10 @@ __global__ void __launch_bounds__(256) k_combine(MapView m, const CombState* st,
       float r0 = m.ox + (float)(8 * bx + x) * h - s_c[0];
       float r1 = m.oy + (float)(8 * by + y) * h - s_c[1];
       float r2 = m.oz + (float)(8 * bz + z) * h - s_c[2];
-      const float rn = sqrtf(r0 * r0 + r1 * r1 + r2 * r2);
-      r0 /= rn;
-      r1 /= rn;
-      r2 /= rn;
+      const float rinv = 1.0f / sqrtf(r0 * r0 + r1 * r1 + r2 * r2);
+      r0 *= rinv;
+      r1 *= rinv;
+      r2 *= rinv;
       float ws = 0.f, acc = 0.f, wf = 0.f, af = 0.f, cw = 0.f, cr = 0.f, cg = 0.f, cb = 0.f;
       bool any = false;
 #pragma unroll 1
@@ -153,8 +158,10 @@ __global__ void __launch_bounds__(256) k_combine(MapView m, const CombState* st,
         const float gn = sqrtf(g0 * g0 + g1 * g1 + g2 * g2);
         if (!(gn > 1e-12f)) continue;
         const float n0 = g0 / gn, n1 = g1 / gn, n2 = g2 / gn;
+        const float facing = -(n0 * r0 + n1 * r1 + n2 * r2);
+        if (!(facing > 0.0f)) continue;  // the weight of Eq. combine_weight vanishes
         const float cosv = (D == 0) ? n0 : (D == 1) ? -n0 : (D == 2) ? n1 : (D == 3) ? -n1 : (D == 4) ? n2 : -n2;
-        const float wc = w_dir_c(cosv, m.theta) * fmaxf(-(n0 * r0 + n1 * r1 + n2 * r2), 0.0f) * v0.y;
+        const float wc = w_dir_c(cosv, m.theta, cos_lo, cos_hi) * facing * v0.y;
         if (!(wc > 0.0f)) continue;
         ws += wc;
         acc += wc * v0.x;
@@ -208,12 +215,18 @@ void launch_combine(const MapView& m, CombState* st, const Intr& K, const double
   set(2, 0.f, K.fy, K.cy + 0.5f + pv);
   set(3, 0.f, -K.fy, (float)K.H - 0.5f + pv - K.cy);
   const bool col = m.color && m.comb_col;
+  // one wave of resident CTAs walks the directory
+  auto go = [&](auto kern) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 4;
+    kern<<<num_sms * per_sm, 256, 0, s>>>(m, st, f);
+  };
   if (m.storage == DTSDF_STORE_FP16) {
-    if (col) k_combine<DTSDF_STORE_FP16, true><<<num_sms * 8, 256, 0, s>>>(m, st, f);
-    else k_combine<DTSDF_STORE_FP16, false><<<num_sms * 8, 256, 0, s>>>(m, st, f);
+    if (col) go(k_combine<DTSDF_STORE_FP16, true>);
+    else go(k_combine<DTSDF_STORE_FP16, false>);
   } else {
-    if (col) k_combine<DTSDF_STORE_FP32, true><<<num_sms * 8, 256, 0, s>>>(m, st, f);
-    else k_combine<DTSDF_STORE_FP32, false><<<num_sms * 8, 256, 0, s>>>(m, st, f);
+    if (col) go(k_combine<DTSDF_STORE_FP32, true>);
+    else go(k_combine<DTSDF_STORE_FP32, false>);
   }
 }
 

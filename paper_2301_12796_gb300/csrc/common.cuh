@@ -129,7 +129,7 @@ __host__ __device__ __forceinline__ uint32_t hash_slot(unsigned long long k, uin
 
 // Device view of a map, passed by value to kernels.
 struct MapView {
-  float h, tau, theta, wmax, wcarve, zmin, zmax, dsup, costh;
+  float h, tau, theta, wmax, wcarve, zmin, zmax, dsup, costh, sinth;
   float ox, oy, oz;
   int carve_r, dense_dim, color, storage;
   // hash: block coordinate -> directory index

@@ -128,8 +128,12 @@ __device__ __forceinline__ bool interp(const MapView& m, size_t base, float fx, 
   return ok;
 }
 
-__device__ __forceinline__ float w_dir_r(float c, float theta) {
-  const float alpha = acosf(fminf(fmaxf(c, -1.0f), 1.0f));
+// Eq. direction_weight as read; the clamped ranges (angle <= pi/2 - theta: 1, >= theta: 0) are
+// decided on the cosine (sin theta, cos theta) without the arc cosine.
+__device__ __forceinline__ float w_dir_r(float c, float theta, float cos_lo, float cos_hi) {
+  if (c >= cos_hi) return 1.0f;
+  if (c <= cos_lo) return 0.0f;
+  const float alpha = acosf(c);
   return fminf(fmaxf((theta - alpha) / (2.0f * theta - 1.57079632679489662f), 0.0f), 1.0f);
 }
 
@@ -225,9 +229,10 @@ __device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, cons
     const float gn = sqrtf(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
     if (!(gn > 1e-12f)) continue;
     const float n0 = gr[0] / gn, n1 = gr[1] / gn, n2 = gr[2] / gn;
+    const float facing = -(n0 * r[0] + n1 * r[1] + n2 * r[2]);
+    if (!(facing > 0.0f)) continue;  // the weight of Eq. combine_weight vanishes
     const float cosv = (D == 0) ? n0 : (D == 1) ? -n0 : (D == 2) ? n1 : (D == 3) ? -n1 : (D == 4) ? n2 : -n2;
-    const float facing = fmaxf(-(n0 * r[0] + n1 * r[1] + n2 * r[2]), 0.0f);
-    const float wc = w_dir_r(cosv, m.theta) * facing * WD;
+    const float wc = w_dir_r(cosv, m.theta, m.costh, m.sinth) * facing * WD;
     if (!(wc > 0.0f)) continue;
     out.wsum += wc;
     acc += wc * phiD;
