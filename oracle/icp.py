@@ -316,6 +316,8 @@ class Settings:
     z_min: float = 0.1
     stop: float = 1e-6
     min_rows: int = 10
+    lm: bool = False  # Levenberg-Marquardt with Madsen's damping update instead of Gauss-Newton
+    lm_tau: float = 1e-3  # initial damping mu = lm_tau * max diag(H) of a level's first evaluation
 
 
 def step(level: Level, ref_depth32, ref_normals32, K_ref, dT, eps, settings: Settings, photo=None,
@@ -336,11 +338,69 @@ def step(level: Level, ref_depth32, ref_normals32, K_ref, dT, eps, settings: Set
     return exp(xi) @ dT, H, g, E, n, xi, True
 
 
+def lm_level(level: Level, ref_depth32, ref_normals32, K_ref, dT, eps, settings: Settings, iters: int, photo,
+             level_index: int, log: list):
+    """One pyramid level of Levenberg-Marquardt (Sec. 7: the implementation solves with LM and
+    Madsen's damping update). Each iteration evaluates the rows at the current pose; the first
+    evaluation is accepted and sets mu = tau max diag(H) (tau = settings.lm_tau, 1e-3), nu = 2; later ones are accepted when
+    the gain ratio rho = (E_acc - E) / (predicted decrease) is positive (mu <- mu max(1/3,
+    1 - (2 rho - 1)^3), nu <- 2), otherwise the pose returns to the accepted one and mu <- mu nu,
+    nu <- 2 nu. The step solves (H_acc + mu I) xi = -g_acc; its predicted decrease of E is
+    xi^T H_acc xi + 2 mu xi^T xi (E(xi) ~ E + 2 g^T xi + xi^T H xi in the convention without the
+    factor 2); the pose becomes exp(xi) dT_acc. The level stops at ||xi|| < stop."""
+    acc = None
+    mu = nu = pred = 0.0
+    for it in range(iters):
+        rows = [geometric_rows(level, ref_depth32, ref_normals32, K_ref, dT, eps, settings.z_min, settings.sim3)]
+        if photo is not None:
+            kf_I, K_kf, T_rs = photo
+            rows.append(photometric_rows(level, kf_I, K_kf, T_rs, dT, settings.photo_thr[level_index], settings.lam,
+                                         settings.z_min, settings.sim3))
+        H, g, E, n = normal_equations(rows)
+        if n < settings.min_rows:
+            log.append(dict(level=level_index, it=it, E=E, n=n, step=0.0, ok=False))
+            break
+        if acc is None:
+            mu, nu = settings.lm_tau * float(np.max(np.diag(H))), 2.0
+            acc = (dT, H, g, E)
+            accepted, rho = True, None
+        else:
+            rho = (acc[3] - E) / pred
+            accepted = rho > 0
+            if accepted:
+                mu *= max(1.0 / 3.0, 1.0 - (2.0 * rho - 1.0) ** 3)
+                nu = 2.0
+                acc = (dT, H, g, E)
+            else:
+                mu *= nu
+                nu *= 2.0
+                dT = acc[0]
+        Ha, ga = acc[1], acc[2]
+        xi, ok = solve(Ha + mu * np.eye(Ha.shape[0]), ga)
+        if not ok:
+            log.append(dict(level=level_index, it=it, E=E, n=n, step=0.0, ok=False, accepted=accepted))
+            break
+        pred = float(xi @ Ha @ xi + 2.0 * mu * (xi @ xi))
+        dT = exp(xi) @ acc[0]
+        log.append(dict(level=level_index, it=it, E=E, n=n, step=float(np.linalg.norm(xi)), ok=True,
+                        accepted=accepted, mu=mu, rho=rho, pred=pred))
+        if np.linalg.norm(xi) < settings.stop:
+            break
+    return dT
+
+
 def track(levels: list[Level], ref_depth32, ref_normals32, K_ref, dT0, settings: Settings, photo_levels=None):
     """Coarse-to-fine schedule: levels from coarsest to finest, iters[l] each,
-    stopping a level when ||xi|| < settings.stop. photo_levels[l] = (kf_I, K_kf, T_rs)."""
+    stopping a level when ||xi|| < settings.stop. photo_levels[l] = (kf_I, K_kf, T_rs).
+    settings.lm selects Levenberg-Marquardt (lm_level) instead of Gauss-Newton."""
     dT = np.array(dT0, np.float64)
     log = []
+    if settings.lm:
+        for l in reversed(range(len(levels))):
+            photo = None if photo_levels is None else photo_levels[l]
+            dT = lm_level(levels[l], ref_depth32, ref_normals32, K_ref, dT, settings.eps[l], settings,
+                          settings.iters[l], photo, l, log)
+        return dT, log
     for l in reversed(range(len(levels))):
         for it in range(settings.iters[l]):
             photo = None if photo_levels is None else photo_levels[l]

@@ -192,3 +192,88 @@ def test_pyramid_single_and_double_precision_agree():
             exp = c.mean() if c.size else 0.0
             assert d64[v, u] == pytest.approx(exp, rel=1e-15)
             assert d32[v, u] == pytest.approx(exp, rel=1e-6)
+
+
+# ------------------------------------------- Levenberg-Marquardt (Sec. 7) ----
+
+def _lm_problem(deg, m, seed):
+    s, K, T_ref, T_cur, rd, rn, cur = _ref_and_current(deg, m, seed=seed)
+    return icp.pyramid(cur.depth, K, 3), rd, rn, K, np.linalg.inv(T_ref) @ T_cur
+
+
+@pytest.mark.parametrize("deg,m", [(2, 0.02), (5, 0.10)])
+def test_lm_exact_recovery(deg, m):
+    """LM reaches the true motion of noiseless planes (as Gauss-Newton does)."""
+    levels, rd, rn, K, true = _lm_problem(deg, m, deg)
+    st = icp.Settings(eps=(0.02, 0.2, 0.3), iters=(30, 15, 15), lm=True)
+    dT, log = icp.track(levels, rd, rn, K, np.eye(4), st)
+    E = np.linalg.inv(true) @ dT
+    ang = np.arccos(np.clip((np.trace(E[:3, :3]) - 1) / 2, -1, 1))
+    assert ang < 1e-6 and np.linalg.norm(E[:3, 3]) < 1e-6
+    # a rejected evaluation never becomes the accepted one: accepted errors strictly decrease
+    for lvl in range(3):
+        acc = [e["E"] for e in log if e["level"] == lvl and e.get("accepted")]
+        assert all(b < a for a, b in zip(acc, acc[1:]))
+
+
+def test_lm_without_damping_is_gauss_newton():
+    """mu = 0 (tau = 0) turns the damped system into the Gauss-Newton one: while every step is
+    accepted the two schedules take identical steps."""
+    levels, rd, rn, K, true = _lm_problem(2, 0.02, 3)
+    gn = icp.Settings(eps=(0.02, 0.2, 0.3), iters=(3, 3, 3), stop=0.0)
+    lm = icp.Settings(eps=(0.02, 0.2, 0.3), iters=(3, 3, 3), stop=0.0, lm=True, lm_tau=0.0)
+    Tg, lg = icp.track(levels, rd, rn, K, np.eye(4), gn)
+    Tl, ll = icp.track(levels, rd, rn, K, np.eye(4), lm)
+    assert all(e["accepted"] for e in ll)
+    assert np.array_equal(Tg, Tl)
+    assert [e["E"] for e in lg] == [e["E"] for e in ll]
+
+
+@pytest.mark.parametrize("tau", [1e-3, 1.0])
+def test_lm_predicted_decrease_matches_near_linear_error(tau):
+    """For a small motion the residuals are nearly linear in xi, so the quadratic model is
+    nearly exact and the gain ratio of the first step is ~1. The predicted decrease must carry
+    both xi^T H xi and the damping term 2 mu xi^T xi: with tau = 1 the damping term is a large
+    part of it, and dropping it (or the factor 2 of g in E(xi)) moves rho far from 1."""
+    levels, rd, rn, K, true = _lm_problem(0.2, 0.002, 5)
+    # the full-resolution level alone: its points lie on the planes (no 2x2 means across creases)
+    st = icp.Settings(eps=(0.02,), iters=(2,), stop=0.0, lm=True, lm_tau=tau)
+    dT, log = icp.track(levels[:1], rd, rn, K, np.eye(4), st)
+    first, second = log[0], log[1]
+    assert abs(second["rho"] - 1.0) < 1e-3, second
+    # Madsen's update for rho ~ 1: mu shrinks by the floor factor 1/3
+    assert second["mu"] == pytest.approx(first["mu"] / 3.0, rel=1e-12)
+
+
+def test_lm_rejections_grow_the_damping():
+    """An evaluation with a larger error than the accepted one is rejected and mu grows by nu,
+    which doubles on each further rejection (x2, x4, x8 ...) and returns to 2 on acceptance.
+    Sensor noise makes the error stall near the optimum, where rejections occur."""
+    import oracle
+    s = scenes.planes_scene()
+    rng = np.random.default_rng(2)
+    T_ref = s.poses[0]
+    cur = s.render(T_ref @ scenes.perturbation(rng, 2, 0.02), noise=True)
+    ref = s.render(T_ref, noise=False, exact=True)
+    rn = np.zeros(ref.normals.shape[:2] + (4,), np.float32)
+    rn[..., :3] = ref.normals
+    lv = icp.pyramid(oracle.preprocess(cur.depth, s.K, 0.1, 6.0, 0.02)["z"], s.K, 3)
+    st = icp.Settings(eps=(0.02, 0.2, 0.3), iters=(10, 5, 4), lm=True)
+    dT, log = icp.track(lv, ref.depth, rn, s.K, np.eye(4), st)
+    log = [e for e in log if "mu" in e]
+    assert sum(not e["accepted"] for e in log) >= 2
+    nu = 2.0
+    for a, b in zip(log, log[1:]):
+        if b["level"] != a["level"]:
+            nu = 2.0
+            continue
+        if b["accepted"]:
+            r = b["rho"]
+            assert r > 0 and b["mu"] == pytest.approx(a["mu"] * max(1 / 3, 1 - (2 * r - 1) ** 3), rel=1e-12)
+            nu = 2.0
+        else:
+            assert b["rho"] <= 0 and b["mu"] == pytest.approx(a["mu"] * nu, rel=1e-12)
+            nu *= 2.0
+    for lvl in range(3):
+        acc = [e["E"] for e in log if e["level"] == lvl and e["accepted"]]
+        assert all(y < x for x, y in zip(acc, acc[1:]))
