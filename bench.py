@@ -80,6 +80,10 @@ def parse():
                          "view-dependent combined TSDF with conditional combination")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
                     help="map storage: FP32 sdf/weight/colour, or FP16 sdf + half weight + u8 colour")
+    ap.add_argument("--solver", default="gn", choices=["gn", "lm"],
+                    help="tracking: Gauss-Newton or Levenberg-Marquardt (Madsen damping) per level")
+    ap.add_argument("--photo", default="f2kf", choices=["f2kf", "f2f"],
+                    help="tracking: photometric term against a keyframe every 10 frames, or the previous frame")
     ap.add_argument("--problems", type=int, default=64, help="multi_sensor: registration problems per step")
     ap.add_argument("--requests", type=int, default=512, help="serve: requests in the arrival stream")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrival rate, requests/s")
@@ -173,9 +177,9 @@ def make_workload(n_frames: int):
     return s, frames
 
 
-def opts_kinect(dt):
+def opts_kinect(dt, solver="gn"):
     return dt.icp_opts(levels=3, iters=(10, 5, 4), eps=(0.005, 0.05, 0.05), photo_thr=(0.05, 0.175, 0.175),
-                       lam=0.1, z_min=0.1, stop_norm=1e-6, min_rows=10)
+                       lam=0.1, z_min=0.1, stop_norm=1e-6, min_rows=10, lm=solver == "lm")
 
 
 LAUNCHES = {"render": 2, "set_frame": 6, "set_keyframe": 6, "compose": 1, "solve": 19, "integrate": 8}
@@ -184,15 +188,17 @@ LAUNCHES = {"render": 2, "set_frame": 6, "set_keyframe": 6, "compose": 1, "solve
 class Tracker:
     """Device-resident tracking loop over the frames (map, ICP context, buffers, poses)."""
 
-    def __init__(self, dt, torch, s, frames, dev, map_frames, storage=0, combined=False, max_blocks=1 << 19):
+    def __init__(self, dt, torch, s, frames, dev, map_frames, storage=0, combined=False, max_blocks=1 << 19,
+                 solver="gn", photo="f2kf"):
         self.dt, self.torch, self.s, self.dev = dt, torch, s, dev
         self.combined = combined
+        self.photo = photo  # "f2kf": keyframe every 10 frames; "f2f": the previous frame, T_rs = I
         K = s.K
         self.K = K
         self.map = dt.Map(dt.params(voxel_size=0.005, truncation=0.02, max_blocks=max_blocks, z_max=s.z_max, color=True,
                                     storage=storage))
         self.icp = dt.Icp(K.width, K.height, 3)
-        self.opts = opts_kinect(dt)
+        self.opts = opts_kinect(dt, solver)
         H, W = K.height, K.width
         self.depth = [torch.from_numpy(f.depth).to(dev) for f in frames]
         self.rgb = [torch.from_numpy(f.rgb).to(dev) for f in frames]
@@ -227,15 +233,20 @@ class Tracker:
         if ev:
             ev[1].record()
         self.icp.set_frame(self.depth[f], self.rgb[f], K, 0.1, self.s.z_max, 0.01)
-        kf = 10 * ((f - 1) // 10)
+        kf = f - 1 if self.photo == "f2f" else 10 * ((f - 1) // 10)
         n = LAUNCHES["render"] + (2 if self.combined else 0) + LAUNCHES["set_frame"]
         if kf != self.kf:
             self.icp.set_keyframe(self.rgb[kf], K)
             self.kf = kf
             n += LAUNCHES["set_keyframe"]
-        dt.pose_compose(self.est[kf], ref, self.T_rs, invert_a=True)
+        if self.photo == "f2f":
+            T_rs = self.eye  # the render camera is the previous frame's camera
+            n -= LAUNCHES["compose"]
+        else:
+            dt.pose_compose(self.est[kf], ref, self.T_rs, invert_a=True)
+            T_rs = self.T_rs
         self.dT.copy_(self.eye)
-        self.icp.solve(self.ref_d, self.ref_n, K, self.dT, self.opts, T_rs_dev=self.T_rs)
+        self.icp.solve(self.ref_d, self.ref_n, K, self.dT, self.opts, T_rs_dev=T_rs)
         dt.pose_compose(ref, self.dT, self.est[f])
         if ev:
             ev[2].record()
@@ -346,7 +357,7 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
     combined = args.render_mode == "combined"
     # the profiling case keeps the device footprint to a few GB (60-frame map: 121k bricks)
     tr = Tracker(dt, torch, s, frames, dev, range(n_frames), storage, combined,
-                 max_blocks=(1 << 17) if args.profile else (1 << 19))
+                 max_blocks=(1 << 17) if args.profile else (1 << 19), solver=args.solver, photo=args.photo)
     st = tr.map.stats()
     l2 = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MB > L2
     for i in range(args.warmup):
@@ -464,6 +475,7 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": WORKLOAD if not storage else WORKLOAD_FP16, "resolution": "640x480",
                           "storage": args.storage, "map_frames": n_frames, "render_mode": args.render_mode,
+                          "solver": args.solver, "photometric": args.photo,
                           "combined": comb,
                           "map_bricks": int(st.bricks), "map_voxels_per_direction_M": [round(x * 512 / 1e6, 2)
                                                                                       for x in st.bricks_per_dir],

@@ -239,6 +239,12 @@ typedef struct {
   double stop_norm;     /* stop a level when ||xi|| < stop_norm (Sec. 8: 1e-6) */
   int32_t min_rows;     /* fewer rows than this -> DTSDF_ERR_DEGENERATE */
   int32_t kahan;        /* 1: Kahan-compensated FP32 accumulation of the per-pixel sums */
+  int32_t lm;           /* 1: Levenberg-Marquardt with Madsen's damping update (Sec. 7) instead of
+                         * Gauss-Newton; dtsdf_icp_solve only (one LM state per level: the first
+                         * evaluation is accepted, mu = 1e-3 max diag(H), nu = 2; a step whose gain
+                         * ratio is not positive is undone and mu grows by nu, nu doubles). The
+                         * single-step, batch, server and no-alloc entry points need 0 here
+                         * (DTSDF_ERR_INVALID_ARG otherwise). */
 } dtsdf_icp_opts;
 
 /* Result of one Gauss-Newton iteration. H (row-major, dim x dim in the top-left of 7x7
@@ -455,6 +461,70 @@ DTSDF_API double dtsdf_server_clock(dtsdf_server s);
 /* Finish every submitted request, stop the worker and free the server's memory. Results not
  * yet polled are dropped. */
 DTSDF_API dtsdf_status dtsdf_server_destroy(dtsdf_server s);
+
+/* ------------------------------------------------------------ input filters ---- */
+
+/* Bilateral input filters (Sec. 8 settings: depth sigma_d = 5.0 px, sigma_r = 0.025 m, radius 5;
+ * normals sigma_d = 2.5 px, sigma_r = 5.0, radius 5). The paper gives no formula; the filters
+ * are the usual ones. Depth: after the outlier filter, each survivor becomes the mean of the
+ * survivors in its (2r+1)^2 window weighted by exp(-(du^2+dv^2)/(2 sigma_d^2)) *
+ * exp(-(z_j - z_i)^2/(2 sigma_r^2)), then is back-projected. Normals: after the normal
+ * estimate, each normal becomes the normalised weighted sum of the window's normals with the
+ * range term exp(-a^2/(2 sigma_r^2)), a the angle between the normals in DEGREES. radius 0 turns
+ * a filter off (the default of a new map or ICP context). Radii 0..8; sigmas > 0 where used. */
+typedef struct {
+  int32_t depth_radius;
+  float depth_sigma_d;   /* pixels */
+  float depth_sigma_r;   /* metres */
+  int32_t normal_radius;
+  float normal_sigma_d;  /* pixels */
+  float normal_sigma_r;  /* degrees */
+} dtsdf_filter_opts;
+
+/* Filters applied by the map's fusion preprocessing (NULL: both off). Takes effect at the next
+ * dtsdf_integrate*. */
+DTSDF_API dtsdf_status dtsdf_set_filters(dtsdf_map map, const dtsdf_filter_opts* f);
+
+/* Filters applied by dtsdf_icp_set_frame (only the depth filter changes what ICP uses: the
+ * pyramid is built from the filtered depth). NULL: both off. */
+DTSDF_API dtsdf_status dtsdf_icp_set_filters(dtsdf_icp icp, const dtsdf_filter_opts* f);
+
+/* Preprocessing of one frame as fusion runs it (Sec. 7): outlier filter, optional bilateral
+ * depth filter, normals, optional bilateral normal filter (f may be NULL). points and normals:
+ * device float4 arrays of width x height, (x, y, z, 1) / (nx, ny, nz, 1) in the camera frame where
+ * present, zeros elsewhere. Asynchronous; allocates stream-ordered scratch when a filter is on. */
+DTSDF_API dtsdf_status dtsdf_preprocess(const dtsdf_frame* frame, float z_min, float z_max, float delta_sup,
+                                        const dtsdf_filter_opts* f, float* points, float* normals, void* stream);
+
+/* Post-fusion error (Sec. 9): sum of |rendered - measured| over the n pixels where both depths
+ * are positive, and that pixel count, as out_dev[0], out_dev[1] (device, 2 doubles; the MAE is
+ * their ratio). rendered, measured: device float32 (may be NULL when n = 0). FP64 sums in a
+ * fixed order (deterministic).
+ * Asynchronous; uses 4 KB of stream-ordered scratch. */
+DTSDF_API dtsdf_status dtsdf_depth_mae(const float* rendered, const float* measured, int64_t n, double* out_dev,
+                                       void* stream);
+
+/* ------------------------------------------------------ multi-sensor scale ---- */
+
+/* Multi-sensor scale anchoring (Sec. 6, Eq. scale_anchor). n frames in time order (host
+ * arrays): log_scale_est[k] = log of the scale of frame k's Sim(3) estimate against the model,
+ * sensor[k] = its sensor. The anchor sensor's scale is held at exp(anchor_log_scale); a drift of
+ * the model's scale shows as a common offset of every sensor's estimate, which the anchor
+ * sensor's estimate measures. Output: anchor_log_scale for the anchor's frames; for the others
+ * est[k] - (est[j] - anchor_log_scale), j the anchor's latest frame before k (est[k] itself
+ * before the anchor's first frame). With anchor_log_scale = 0 this is the paper's
+ * s_i = s^_i - s^_0 in the log domain. log_scale_out may alias log_scale_est. Host arithmetic
+ * only: no device is used. DTSDF_ERR_INVALID_ARG for null arrays or n < 0. */
+DTSDF_API dtsdf_status dtsdf_scale_anchor(const double* log_scale_est, const int32_t* sensor, int64_t n,
+                                          int32_t anchor_sensor, double anchor_log_scale, double* log_scale_out);
+
+/* depth_out[i] = scale * depth_in[i] (float32, device, n pixels; invalid 0 stays 0): a sensor's
+ * depth brought to the model's metric before fusion (Sec. 6: with the scale known, the images
+ * are scaled and SE(3) poses serve the rest of the pipeline). depth_out may equal depth_in.
+ * Asynchronous on `stream`. DTSDF_ERR_INVALID_ARG for null pointers, n < 0 or a scale that is
+ * not finite and positive. */
+DTSDF_API dtsdf_status dtsdf_depth_scale(const float* depth_in, float* depth_out, int64_t n, float scale,
+                                         void* stream);
 
 /* Exponential map of se(3) (sim3 = 0, xi[6]) or sim(3) (sim3 = 1, xi[7]) evaluated by the
  * library's device code (the closed form of the matrix exponential of the 4x4 generator);

@@ -410,3 +410,27 @@ def track(levels: list[Level], ref_depth32, ref_normals32, K_ref, dT0, settings:
             if not ok or np.linalg.norm(xi) < settings.stop:
                 break
     return dT, log
+
+
+# ------------------------------------------------- multi-sensor scale ----
+
+def scale_anchor(log_scale_est, sensor, anchor: int = 0, anchor_value: float = 0.0) -> np.ndarray:
+    """Sec. 6, Eq. scale_anchor, in the log domain (the printed equation equates a ratio of
+    exponentials with a difference of logs; the difference of log scales is taken). Frames in
+    time order; log_scale_est[k] is the log scale of frame k's Sim(3) estimate against the model.
+    Scale drift of the model is common to all sensors, so the anchor sensor - whose scale is held
+    at exp(anchor_value) - measures it: a frame of another sensor is compensated by the anchor's
+    latest estimate, s_k = s^_k - (s^_anchor - anchor_value); the anchor's own frames get
+    anchor_value; frames before the anchor's first estimate are left as estimated."""
+    est = np.asarray(log_scale_est, np.float64)
+    out = np.empty_like(est)
+    latest = None
+    for k in range(est.shape[0]):
+        if int(sensor[k]) == anchor:
+            latest = est[k]
+            out[k] = anchor_value
+        elif latest is None:
+            out[k] = est[k]
+        else:
+            out[k] = est[k] - (latest - anchor_value)
+    return out

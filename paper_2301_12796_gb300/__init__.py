@@ -50,6 +50,19 @@ class RenderOpts(ctypes.Structure):
     _fields_ = [("ctas", c_int32), ("refill", c_int32), ("tile_w", c_int32)]
 
 
+class FilterOpts(ctypes.Structure):
+    _fields_ = [("depth_radius", c_int32), ("depth_sigma_d", c_float), ("depth_sigma_r", c_float),
+                ("normal_radius", c_int32), ("normal_sigma_d", c_float), ("normal_sigma_r", c_float)]
+
+
+def filter_opts(depth=True, normals=True, depth_radius=5, depth_sigma_d=5.0, depth_sigma_r=0.025, normal_radius=5,
+                normal_sigma_d=2.5, normal_sigma_r=5.0) -> FilterOpts:
+    """Bilateral input filters with the Sec. 8 settings by default; a filter that is not wanted
+    gets radius 0."""
+    return FilterOpts(depth_radius if depth else 0, depth_sigma_d, depth_sigma_r, normal_radius if normals else 0,
+                      normal_sigma_d, normal_sigma_r)
+
+
 class IcpProblem(ctypes.Structure):
     _fields_ = [("icp", c_void_p), ("ref", RenderOut), ("K_ref", Intrinsics), ("T_rel_dev", c_void_p),
                 ("stats_dev", c_void_p), ("sim3", c_int32)]
@@ -71,7 +84,7 @@ class MapStats(ctypes.Structure):
 class IcpOpts(ctypes.Structure):
     _fields_ = [("levels", c_int32), ("iters", c_int32 * 4), ("eps", c_float * 4), ("photo_thr", c_float * 4),
                 ("lambda_", c_float), ("z_min", c_float), ("stop_norm", c_double), ("min_rows", c_int32),
-                ("kahan", c_int32)]
+                ("kahan", c_int32), ("lm", c_int32)]
 
 
 class IcpStats(ctypes.Structure):
@@ -158,6 +171,13 @@ SIGNATURES = {
     "dtsdf_server_clock": ([P], c_double),
     "dtsdf_server_destroy": ([P], c_int32),
     "dtsdf_exp": ([c_int32, P, P], c_int32),
+    "dtsdf_set_filters": ([P, ctypes.POINTER(FilterOpts)], c_int32),
+    "dtsdf_icp_set_filters": ([P, ctypes.POINTER(FilterOpts)], c_int32),
+    "dtsdf_preprocess": ([ctypes.POINTER(Frame), c_float, c_float, c_float, ctypes.POINTER(FilterOpts), P, P, P],
+                         c_int32),
+    "dtsdf_depth_mae": ([P, P, c_int64, P, P], c_int32),
+    "dtsdf_scale_anchor": ([P, P, c_int64, c_int32, c_double, P], c_int32),
+    "dtsdf_depth_scale": ([P, P, c_int64, c_float, P], c_int32),
     "dtsdf_last_error": ([], ctypes.c_char_p),
     "dtsdf_version": ([], ctypes.c_char_p),
 }
@@ -300,6 +320,10 @@ class Map:
                                RenderOut(depth.data_ptr(), normals.data_ptr(), None if color is None else color.data_ptr()))
         check(lib().dtsdf_render_batch(self._h, arr, len(jobs), _stream_ptr(stream)), "dtsdf_render_batch")
 
+    def set_filters(self, f: FilterOpts | None):
+        """Bilateral input filters of this map's fusion (None: off)."""
+        check(lib().dtsdf_set_filters(self._h, None if f is None else ctypes.byref(f)), "dtsdf_set_filters")
+
     def set_render_opts(self, ctas: int = 0, refill: int = 0, tile_w: int = 0):
         """Launch shape of this map's renders: persistent CTAs (0 = one resident wave), lanes per
         refill group (1, 2, 4, 8, 16, 32; 0 = 32) and the width of the 32-ray pixel tiles (1, 2, 4,
@@ -361,12 +385,12 @@ Map.import_bricks = _import
 
 
 def icp_opts(levels=3, iters=(10, 5, 4), eps=(0.005, 0.05, 0.05), photo_thr=(0.05, 0.175, 0.175), lam=0.1,
-             z_min=0.1, stop_norm=1e-6, min_rows=10, kahan=False) -> IcpOpts:
+             z_min=0.1, stop_norm=1e-6, min_rows=10, kahan=False, lm=False) -> IcpOpts:
     it = list(iters) + [0] * (4 - len(iters))
     ep = list(eps) + [0.05] * (4 - len(eps))
     th = list(photo_thr) + [0.175] * (4 - len(photo_thr))
     return IcpOpts(levels, (c_int32 * 4)(*it), (c_float * 4)(*ep), (c_float * 4)(*th), lam, z_min, stop_norm,
-                   min_rows, int(kahan))
+                   min_rows, int(kahan), int(lm))
 
 
 class Icp:
@@ -388,6 +412,10 @@ class Icp:
         f = Frame(depth.data_ptr(), None if rgb is None else rgb.data_ptr(), intrinsics(K))
         check(lib().dtsdf_icp_set_frame(self._h, ctypes.byref(f), z_min, z_max, delta_sup, _stream_ptr(stream)),
               "dtsdf_icp_set_frame")
+
+    def set_filters(self, f: FilterOpts | None):
+        """Bilateral input filters of set_frame (None: off)."""
+        check(lib().dtsdf_icp_set_filters(self._h, None if f is None else ctypes.byref(f)), "dtsdf_icp_set_filters")
 
     def set_keyframe(self, rgb, K, stream=None):
         f = Frame(None, rgb.data_ptr(), intrinsics(K))
@@ -465,6 +493,52 @@ def pose_compose(A_dev, B_dev, C_dev, invert_a=False, stream=None):
     """C = A B (or A^-1 B) on the device for float64 CUDA tensors [4, 4]."""
     check(lib().dtsdf_pose_compose(A_dev.data_ptr(), int(invert_a), B_dev.data_ptr(), C_dev.data_ptr(),
                                    _stream_ptr(stream)), "dtsdf_pose_compose")
+
+
+def preprocess(depth, K, z_min, z_max, delta_sup, f: FilterOpts | None = None, points=None, normals=None,
+               stream=None):
+    """Fusion's preprocessing of a float32 CUDA depth image [H, W] (dtsdf_preprocess); returns the
+    (points, normals) float32 CUDA tensors [H, W, 4] (w = 1 where present)."""
+    import torch
+    H, W = depth.shape
+    points = torch.empty(H, W, 4, dtype=torch.float32, device=depth.device) if points is None else points
+    normals = torch.empty(H, W, 4, dtype=torch.float32, device=depth.device) if normals is None else normals
+    fr = Frame(depth.data_ptr(), None, intrinsics(K))
+    check(lib().dtsdf_preprocess(ctypes.byref(fr), z_min, z_max, delta_sup, None if f is None else ctypes.byref(f),
+                                 points.data_ptr(), normals.data_ptr(), _stream_ptr(stream)), "dtsdf_preprocess")
+    return points, normals
+
+
+def depth_mae(rendered, measured, out=None, stream=None):
+    """(sum |rendered - measured|, count) over pixels where both are positive, as a float64 CUDA
+    tensor [2] (dtsdf_depth_mae); MAE = out[0] / out[1]."""
+    import torch
+    if rendered.numel() != measured.numel():
+        raise ValueError("rendered / measured: equal sizes")
+    out = torch.empty(2, dtype=torch.float64, device=rendered.device) if out is None else out
+    check(lib().dtsdf_depth_mae(rendered.data_ptr(), measured.data_ptr(), rendered.numel(), out.data_ptr(),
+                                _stream_ptr(stream)), "dtsdf_depth_mae")
+    return out
+
+
+def scale_anchor(log_scale_est, sensor, anchor=0, anchor_log_scale=0.0) -> np.ndarray:
+    """Anchored log scales of frames in time order (dtsdf_scale_anchor; host arithmetic)."""
+    e = np.ascontiguousarray(log_scale_est, np.float64)
+    s = np.ascontiguousarray(sensor, np.int32)
+    if e.shape != s.shape or e.ndim != 1:
+        raise ValueError("log_scale_est and sensor: equal 1-D shapes")
+    out = np.empty_like(e)
+    check(lib().dtsdf_scale_anchor(e.ctypes.data, s.ctypes.data, e.shape[0], int(anchor), float(anchor_log_scale),
+                                   out.ctypes.data), "dtsdf_scale_anchor")
+    return out
+
+
+def depth_scale(depth_in, depth_out, scale: float, stream=None):
+    """depth_out = scale * depth_in on the device (float32 CUDA tensors of equal size)."""
+    if depth_in.numel() != depth_out.numel() or depth_in.dtype != depth_out.dtype:
+        raise ValueError("depth_in / depth_out: equal float32 sizes")
+    check(lib().dtsdf_depth_scale(depth_in.data_ptr(), depth_out.data_ptr(), depth_in.numel(), float(scale),
+                                  _stream_ptr(stream)), "dtsdf_depth_scale")
 
 
 def exp(xi) -> np.ndarray:

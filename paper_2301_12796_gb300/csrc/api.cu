@@ -103,6 +103,8 @@ struct dtsdf_map_s {
   float4* P = nullptr;
   float4* N = nullptr;
   uint8_t* J = nullptr;  // per-pixel carving flags
+  float4* F = nullptr;   // scratch image of the bilateral filters
+  FilterOpts filt{};     // bilateral input filters (radius 0: off)
   size_t ws_pixels = 0;
   // error flag mirror (pinned) and the event of its last copy
   uint32_t* err_host = nullptr;
@@ -143,6 +145,7 @@ static void map_free(dtsdf_map m) {
   cudaFree(m->P);
   cudaFree(m->N);
   cudaFree(m->J);
+  cudaFree(m->F);
   if (m->err_host) cudaFreeHost(m->err_host);
   if (m->err_event) cudaEventDestroy(m->err_event);
   if (m->pool) cudaMemPoolDestroy(m->pool);
@@ -320,12 +323,14 @@ static dtsdf_status ensure_ws(dtsdf_map m, size_t npix) {
   cudaFree(m->P);
   cudaFree(m->N);
   cudaFree(m->J);
-  m->P = m->N = nullptr;
+  cudaFree(m->F);
+  m->P = m->N = m->F = nullptr;
   m->J = nullptr;
   m->ws_pixels = 0;
   CK(cudaMalloc((void**)&m->P, sizeof(float4) * npix));
   CK(cudaMalloc((void**)&m->N, sizeof(float4) * npix));
   CK(cudaMalloc((void**)&m->J, npix));
+  CK(cudaMalloc((void**)&m->F, sizeof(float4) * npix));
   m->ws_pixels = npix;
   return DTSDF_OK;
 }
@@ -349,7 +354,7 @@ static dtsdf_status integrate_impl(dtsdf_map m, const dtsdf_frame* f, const doub
   memset(&T, 0, sizeof(T));
   if (T_wc) T = to_pose32(T_wc);
   m->v.frame = (uint32_t)m->frames;
-  launch_preprocess(f->depth, K, m->v.zmin, m->v.zmax, m->v.dsup, m->P, m->N, s);
+  launch_preprocess(f->depth, K, m->v.zmin, m->v.zmax, m->v.dsup, m->P, m->N, s, &m->filt, m->F);
   CK_LAUNCH("preprocess");
   if (m->p.dense_dim <= 0) {
     CK(cudaMemsetAsync(m->v.counters + C_WORK, 0, sizeof(uint32_t), s));
@@ -733,12 +738,15 @@ struct dtsdf_icp_s {
   float4* kf[4] = {nullptr, nullptr, nullptr, nullptr};
   float4* P = nullptr;
   float4* N = nullptr;
+  float4* F = nullptr;  // scratch image of the bilateral depth filter
+  FilterOpts filt{};
   float* partials = nullptr;
   int grid = 0;
   double* pose = nullptr;
   dtsdf_icp_stats* stats = nullptr;
   uint32_t* ticket = nullptr;
   int32_t* stop = nullptr;
+  LmState* lm = nullptr;
   double* host_pose = nullptr;
   dtsdf_icp_stats* host_stats = nullptr;
 };
@@ -753,11 +761,13 @@ static void icp_free(dtsdf_icp c) {
   }
   cudaFree(c->P);
   cudaFree(c->N);
+  cudaFree(c->F);
   cudaFree(c->partials);
   cudaFree(c->pose);
   cudaFree(c->stats);
   cudaFree(c->ticket);
   cudaFree(c->stop);
+  cudaFree(c->lm);
   if (c->host_pose) cudaFreeHost(c->host_pose);
   if (c->host_stats) cudaFreeHost(c->host_stats);
   delete c;
@@ -800,11 +810,13 @@ dtsdf_status dtsdf_icp_create(int32_t max_width, int32_t max_height, int32_t lev
   c->grid = num_sms() * 2;
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->P, sizeof(float4) * n0);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->N, sizeof(float4) * n0);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->F, sizeof(float4) * n0);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->partials, sizeof(float) * 64 * c->grid);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->pose, sizeof(double) * 16);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->stats, sizeof(dtsdf_icp_stats));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->ticket, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->stop, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->lm, sizeof(LmState));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->host_pose, sizeof(double) * 16);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->host_stats, sizeof(dtsdf_icp_stats));
   if (e == cudaSuccess) e = cudaMemset(c->ticket, 0, sizeof(uint32_t));
@@ -833,7 +845,7 @@ dtsdf_status dtsdf_icp_set_frame(dtsdf_icp c, const dtsdf_frame* f, float z_min,
   cudaStream_t s = (cudaStream_t)stream;
   const Intr K0 = to_intr(f->K);
   for (int l = 0; l < c->levels; ++l) c->K[l] = level_intr(K0, l);
-  launch_preprocess(f->depth, K0, z_min, z_max, delta_sup, c->P, c->N, s);
+  launch_preprocess(f->depth, K0, z_min, z_max, delta_sup, c->P, c->N, s, &c->filt, c->F);
   launch_frame_pyramid(c->P, f->rgb, c->levels, c->K, c->depth, c->inten, s);
   CK_LAUNCH("icp_set_frame");
   c->has_frame = true;
@@ -852,8 +864,9 @@ dtsdf_status dtsdf_icp_set_keyframe(dtsdf_icp c, const dtsdf_frame* f, void* str
   return DTSDF_OK;
 }
 
-static bool opts_ok(const dtsdf_icp_opts* o, int levels) {
-  if (!o || o->levels < 1 || o->levels > levels || !(o->z_min > 0) || !(o->stop_norm >= 0) || o->min_rows < 0)
+static bool opts_ok(const dtsdf_icp_opts* o, int levels, bool allow_lm = false) {
+  if (!o || o->levels < 1 || o->levels > levels || !(o->z_min > 0) || !(o->stop_norm >= 0) || o->min_rows < 0 ||
+      !(o->lm == 0 || (allow_lm && o->lm == 1)))
     return false;
   for (int l = 0; l < o->levels; ++l)
     if (o->iters[l] < 0 || o->iters[l] > 1000 || !(o->eps[l] > 0) || !(o->photo_thr[l] >= 0)) return false;
@@ -891,6 +904,7 @@ static void fill_launch(dtsdf_icp c, IcpLaunch& L, const dtsdf_render_out* ref, 
   L.min_rows = o->min_rows;
   L.stop_norm = o->stop_norm;
   L.kahan = o->kahan;
+  L.lm = nullptr;
 }
 
 static dtsdf_status icp_step_impl(dtsdf_icp c, const dtsdf_render_out* ref, const dtsdf_intrinsics* K_ref, int level,
@@ -933,7 +947,7 @@ dtsdf_status dtsdf_icp_sim3_step(dtsdf_icp c, const dtsdf_render_out* ref, const
 dtsdf_status dtsdf_icp_solve(dtsdf_icp c, const dtsdf_render_out* ref, const dtsdf_intrinsics* K_ref, int32_t sim3,
                              double* T_rel_dev, const double* T_rs_dev, const dtsdf_icp_opts* o,
                              dtsdf_icp_stats* stats_dev, void* stream) {
-  if (!c || !ref || !ref->normals || !intr_ok(K_ref) || !T_rel_dev || !opts_ok(o, c->levels) || !c->has_frame ||
+  if (!c || !ref || !ref->normals || !intr_ok(K_ref) || !T_rel_dev || !opts_ok(o, c->levels, true) || !c->has_frame ||
       (sim3 != 0 && sim3 != 1))
     return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
   cudaStream_t s = (cudaStream_t)stream;
@@ -941,9 +955,11 @@ dtsdf_status dtsdf_icp_solve(dtsdf_icp c, const dtsdf_render_out* ref, const dts
   CK(cudaMemsetAsync(c->stats, 0, sizeof(dtsdf_icp_stats), s));
   for (int l = o->levels - 1; l >= 0; --l) {
     CK(cudaMemsetAsync(c->stop, 0, sizeof(int32_t), s));
+    if (o->lm) CK(cudaMemsetAsync(c->lm, 0, sizeof(LmState), s));
     IcpLaunch L;
     bool photo = false;
     fill_launch(c, L, ref, K_ref, l, nullptr, T_rs_dev, o, photo);
+    if (o->lm) L.lm = c->lm;
     for (int it = 0; it < o->iters[l]; ++it) launch_icp(L, sim3, photo, c->grid, s);
     CK_LAUNCH("icp_solve");
   }
@@ -1092,6 +1108,94 @@ dtsdf_status dtsdf_render_batch(dtsdf_map m, const dtsdf_render_job* jobs, int32
     CK(cudaMemsetAsync(q, 0, sizeof(unsigned), s));
     CK(launch_render_jobs(m->v, J, k, q, s, nullptr, m->shape, m->pool));
   }
+  return DTSDF_OK;
+}
+
+static bool filters_ok(const dtsdf_filter_opts* f) {
+  if (!f) return true;
+  if (f->depth_radius < 0 || f->depth_radius > 8 || f->normal_radius < 0 || f->normal_radius > 8) return false;
+  if (f->depth_radius > 0 && !(f->depth_sigma_d > 0 && f->depth_sigma_r > 0)) return false;
+  if (f->normal_radius > 0 && !(f->normal_sigma_d > 0 && f->normal_sigma_r > 0)) return false;
+  return true;
+}
+
+static FilterOpts to_filter(const dtsdf_filter_opts* f) {
+  FilterOpts o{};
+  if (f) {
+    o.depth_radius = f->depth_radius;
+    o.depth_sigma_d = f->depth_sigma_d;
+    o.depth_sigma_r = f->depth_sigma_r;
+    o.normal_radius = f->normal_radius;
+    o.normal_sigma_d = f->normal_sigma_d;
+    o.normal_sigma_r = f->normal_sigma_r;
+  }
+  return o;
+}
+
+dtsdf_status dtsdf_set_filters(dtsdf_map m, const dtsdf_filter_opts* f) {
+  if (!m || !filters_ok(f)) return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  m->filt = to_filter(f);
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_icp_set_filters(dtsdf_icp c, const dtsdf_filter_opts* f) {
+  if (!c || !filters_ok(f)) return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  c->filt = to_filter(f);
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_preprocess(const dtsdf_frame* fr, float z_min, float z_max, float delta_sup,
+                              const dtsdf_filter_opts* f, float* points, float* normals, void* stream) {
+  if (!fr || !fr->depth || !intr_ok(&fr->K) || !points || !normals || !(z_min > 0) || !(z_max > z_min) ||
+      !(delta_sup > 0) || !filters_ok(f))
+    return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Intr K = to_intr(fr->K);
+  const FilterOpts o = to_filter(f);
+  float4* tmp = nullptr;
+  if (o.depth_radius > 0 || o.normal_radius > 0)
+    CK(cudaMallocAsync((void**)&tmp, sizeof(float4) * (size_t)K.W * K.H, s));
+  launch_preprocess(fr->depth, K, z_min, z_max, delta_sup, (float4*)points, (float4*)normals, s, &o, tmp);
+  cudaError_t e = cudaGetLastError();
+  if (tmp) cudaFreeAsync(tmp, s);
+  if (e != cudaSuccess) return cuda_fail(e, "dtsdf_preprocess");
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_depth_mae(const float* rendered, const float* measured, int64_t n, double* out_dev, void* stream) {
+  if (!out_dev || n < 0 || (n > 0 && (!rendered || !measured))) return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  double* part = nullptr;
+  CK(cudaMallocAsync((void**)&part, sizeof(double) * MAE_PARTIAL_DOUBLES, s));
+  launch_mae(rendered, measured, n, part, out_dev, s);
+  cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(part, s);
+  if (e != cudaSuccess) return cuda_fail(e, "dtsdf_depth_mae");
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_scale_anchor(const double* est, const int32_t* sensor, int64_t n, int32_t anchor,
+                                double anchor_log_scale, double* out) {
+  if (n < 0 || (n > 0 && (!est || !sensor || !out))) return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  bool have = false;
+  double latest = 0.0;
+  for (int64_t k = 0; k < n; ++k) {
+    const double e = est[k];
+    if (sensor[k] == anchor) {
+      latest = e;
+      have = true;
+      out[k] = anchor_log_scale;
+    } else {
+      out[k] = have ? e - (latest - anchor_log_scale) : e;
+    }
+  }
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_depth_scale(const float* in, float* out, int64_t n, float scale, void* stream) {
+  if (!in || !out || n < 0 || !(scale > 0.0f) || !(scale < INFINITY)) return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  launch_depth_scale(in, out, n, scale, (cudaStream_t)stream);
+  CK_LAUNCH("depth_scale");
   return DTSDF_OK;
 }
 

@@ -177,13 +177,20 @@ __global__ void k_exp(int dim, const double* xi, double* T) { exp_sim3(xi, dim, 
 // spread over the lanes, the triangular solves column-oriented, the sine, cosine and
 // exponentials of the exponential map in separate lanes and the pose product one entry per
 // lane. Every lane returns the same level decision.
+// With lm (Levenberg-Marquardt, Sec. 7, with Madsen's damping update): the first evaluation of a
+// level is accepted and sets mu = 1e-3 max diag(H), nu = 2; a later one is accepted when the gain
+// ratio rho = (E_acc - E) / (predicted decrease) is positive (mu <- mu max(1/3, 1 - (2 rho - 1)^3),
+// nu <- 2), otherwise the pose returns to the accepted one (mu <- mu nu, nu <- 2 nu). The step
+// solves (H_acc + mu I) xi = -g_acc, its predicted decrease of E is xi^T H_acc xi + 2 mu xi^T xi
+// (E(xi) ~ E + 2 g^T xi + xi^T H xi without the factor 2), and pose <- exp(xi) pose_acc.
 template <int DIM>
 __device__ bool icp_solve_update_warp(const double* sum, int dsolve, double* pose, dtsdf_icp_stats* st,
-                                      int min_rows, double stop_norm) {
+                                      int min_rows, double stop_norm, LmState* lm = nullptr) {
   constexpr int NH = DIM * (DIM + 1) / 2;
   constexpr int N = NH + DIM + 3;
   __shared__ double sL[7][8];
   __shared__ double sb[8];
+  __shared__ double sgv[8];
   __shared__ double sE[16];
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -219,8 +226,66 @@ __device__ bool icp_solve_update_warp(const double* sum, int dsolve, double* pos
   double dmax = lane < D ? sL[lane][lane] : 0.0;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(FULL, dmax, o));
-  // Cholesky H = L L^T (lower triangle of sL), a pivot below 1e-10 max diag(H): degenerate
+  if (lane < D) sgv[lane] = sum[NH + lane];
   bool ok = rows >= min_rows && dmax > 0.0;
+  double mu = 0.0;
+  if (lm && ok) {
+    int accept = 1;
+    if (lane == 0) {
+      const double E = sum[NH + DIM];
+      if (!lm->have) {
+        lm->mu = 1e-3 * dmax;
+        lm->nu = 2.0;
+      } else {
+        const double rho = (lm->E - E) / lm->pred;
+        accept = rho > 0.0;
+        if (accept) {
+          const double c = 2.0 * rho - 1.0;
+          lm->mu *= fmax(1.0 / 3.0, 1.0 - c * c * c);
+          lm->nu = 2.0;
+        } else {
+          lm->mu *= lm->nu;
+          lm->nu *= 2.0;
+        }
+      }
+      if (accept) {
+        lm->E = E;
+        lm->have = 1;
+      }
+    }
+    accept = __shfl_sync(FULL, accept, 0);
+    __syncwarp();
+    mu = lm->mu;
+    // the accepted system and pose: this evaluation's, or the stored ones
+    for (int k = lane; k < 49; k += 32) {
+      const int i = k / 7, j = k % 7;
+      if (i < D && j < D) {
+        if (accept)
+          lm->H[k] = sL[i][j];
+        else
+          sL[i][j] = lm->H[k];
+      }
+    }
+    if (lane < D) {
+      if (accept)
+        lm->g[lane] = sgv[lane];
+      else
+        sgv[lane] = lm->g[lane];
+    }
+    if (lane < 16) {
+      if (accept)
+        lm->pose[lane] = pose[lane];
+      else
+        pose[lane] = lm->pose[lane];
+    }
+    __syncwarp();
+    if (lane < D) sL[lane][lane] += mu;
+    __syncwarp();
+    dmax = lane < D ? sL[lane][lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(FULL, dmax, o));
+  }
+  // Cholesky H = L L^T (lower triangle of sL), a pivot below 1e-10 max diag(H): degenerate
   for (int j = 0; j < D && ok; ++j) {
     const double s = sL[j][j];
     if (!(s > 1e-10 * dmax)) {
@@ -250,7 +315,7 @@ __device__ bool icp_solve_update_warp(const double* sum, int dsolve, double* pos
     return true;
   }
   // L y = -g, then L^T xi = y (column-oriented; sb holds the right-hand side, then xi)
-  if (lane < D) sb[lane] = -sum[NH + lane];
+  if (lane < D) sb[lane] = -sgv[lane];
   __syncwarp();
   for (int i = 0; i < D; ++i) {
     const double y = sb[i] / sL[i][i];
@@ -273,6 +338,12 @@ __device__ bool icp_solve_update_warp(const double* sum, int dsolve, double* pos
     nrm += xi[i] * xi[i];
   }
   nrm = sqrt(nrm);
+  if (lm && lane == 0) {  // predicted decrease of E for the next gain ratio
+    double q = 0.0;
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j < D; ++j) q += xi[i] * lm->H[7 * i + j] * xi[j];
+    lm->pred = q + 2.0 * mu * (nrm * nrm);
+  }
   // exponential map: transcendental values in lanes 1-4, the rest in lane 0
   const double th = sqrt(xi[3] * xi[3] + xi[4] * xi[4] + xi[5] * xi[5]);
   const double sg = D == 7 ? xi[6] : 0.0;
@@ -323,6 +394,7 @@ struct IcpArgs {
   float thr, lambda;
   // state
   double* pose;
+  LmState* lm;
   float* partials;
   uint32_t* ticket;
   int32_t* stop;
@@ -555,7 +627,7 @@ __global__ void __launch_bounds__(ICP_THREADS) k_icp(IcpArgs a) {
   __syncthreads();
   if (threadIdx.x >= 32) return;
   if (threadIdx.x == 0) *a.ticket = 0u;
-  const bool stop = icp_solve_update_warp<DIM>(s_sum, DIM, a.pose, a.stats, a.min_rows, a.stop_norm);
+  const bool stop = icp_solve_update_warp<DIM>(s_sum, DIM, a.pose, a.stats, a.min_rows, a.stop_norm, a.lm);
   if (threadIdx.x == 0 && stop) *a.stop = 1;
 }
 
@@ -751,6 +823,7 @@ void launch_icp(const IcpLaunch& L, int sim3, bool photo, int grid, cudaStream_t
   a.thr = L.thr;
   a.lambda = L.lambda;
   a.pose = L.pose;
+  a.lm = L.lm;
   a.partials = L.partials;
   a.ticket = L.ticket;
   a.stop = L.stop;

@@ -5,6 +5,15 @@
 
 namespace dtsdf {
 
+// Levenberg-Marquardt state of one pyramid level (device memory; zero = no evaluation yet).
+struct LmState {
+  double mu, nu, E, pred;
+  double pose[16];  // accepted pose
+  double H[49];     // accepted system (row-major 7x7) and right-hand side
+  double g[7];
+  int have;
+};
+
 struct IcpLaunch {
   const float* depth;
   const float* inten;
@@ -25,13 +34,24 @@ struct IcpLaunch {
   int min_rows;
   double stop_norm;
   int kahan;
+  LmState* lm = nullptr;  // Levenberg-Marquardt state, or null for Gauss-Newton
 };
 
 // Record a message for dtsdf_last_error() and return the status.
 dtsdf_status set_error(dtsdf_status s, const char* msg);
 
+// Bilateral input filters (radius 0 = off); layout of dtsdf_filter_opts.
+struct FilterOpts {
+  int depth_radius;
+  float depth_sigma_d, depth_sigma_r;
+  int normal_radius;
+  float normal_sigma_d, normal_sigma_r;
+};
+
+// Outlier filter and normals; with f (and a scratch image tmp of W x H float4) the bilateral depth
+// filter runs between them and the bilateral normal filter after them.
 void launch_preprocess(const float* depth, const Intr& K, float zmin, float zmax, float dsup, float4* P, float4* N,
-                       cudaStream_t s);
+                       cudaStream_t s, const FilterOpts* f = nullptr, float4* tmp = nullptr);
 void launch_alloc(const MapView& m, const float4* P, const float4* N, int npix, const Pose32& T, const double* Tdev,
                   int num_sms, cudaStream_t s);
 void launch_dense_fill(const MapView& m, int nb, cudaStream_t s);
@@ -42,6 +62,9 @@ void launch_fuse(const MapView& m, const Intr& K, const Pose32& T, const double*
 // Apron refresh and bound of every brick (after an import).
 void launch_apron_refresh_all(const MapView& m, int num_sms, cudaStream_t s);
 void launch_pose_compose(const double* A, int invert_a, const double* B, double* C, cudaStream_t s);
+constexpr int MAE_PARTIAL_DOUBLES = 2 * 256;
+void launch_mae(const float* a, const float* b, int64_t n, double* part, double* out, cudaStream_t s);
+void launch_depth_scale(const float* in, float* out, int64_t n, float scale, cudaStream_t s);
 void launch_import(const MapView& m, const int32_t* coords, const float* vox, int64_t n, bool allocate, int num_sms,
                    cudaStream_t s);
 void launch_export(const MapView& m, int64_t cap, int32_t* coords, float* vox, int num_sms, cudaStream_t s);

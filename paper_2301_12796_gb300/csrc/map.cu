@@ -86,6 +86,123 @@ __global__ void k_normals(const float4* __restrict__ P, Intr K, float4* __restri
   N[i] = out;
 }
 
+// Bilateral depth filter (Sec. 8 settings): for a survivor of the outlier filter, the mean of the
+// survivors in the (2r+1)^2 window weighted by exp(-(du^2 + dv^2) / (2 sd^2)) in pixels times
+// exp(-(z_j - z_i)^2 / (2 sr^2)) in depth; the result is back-projected again. Non-survivors
+// stay empty. Fixed tap order (dv, then du), FP32.
+__global__ void k_bilateral_depth(const float4* __restrict__ Pin, Intr K, int r, float sd, float sr,
+                                  float4* __restrict__ Pout) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y * blockDim.y + threadIdx.y;
+  if (u >= K.W || v >= K.H) return;
+  const int i = v * K.W + u;
+  const float4 c = Pin[i];
+  float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (c.w > 0.f) {
+    const float ks = -0.5f / (sd * sd), kr = -0.5f / (sr * sr);
+    float num = 0.f, den = 0.f;
+    for (int dv = -r; dv <= r; ++dv) {
+      const int vv = v + dv;
+      if (vv < 0 || vv >= K.H) continue;
+      for (int du = -r; du <= r; ++du) {
+        const int uu = u + du;
+        if (uu < 0 || uu >= K.W) continue;
+        const float4 q = Pin[vv * K.W + uu];
+        if (!(q.w > 0.f)) continue;
+        const float dz = q.z - c.z;
+        const float w = expf(ks * (float)(du * du + dv * dv) + kr * dz * dz);
+        num += w * q.z;
+        den += w;
+      }
+    }
+    const float z = num / den;  // den >= 1 (the centre tap)
+    const float a = rdiv(rsub((float)u, K.cx), K.fx);
+    const float b = rdiv(rsub((float)v, K.cy), K.fy);
+    out = make_float4(rmul(z, a), rmul(z, b), z, 1.0f);
+  }
+  Pout[i] = out;
+}
+
+// Bilateral normal filter (Sec. 8 settings): for a pixel with a normal, the normalised sum of the
+// normals in the (2r+1)^2 window weighted by exp(-(du^2 + dv^2) / (2 sd^2)) in pixels times
+// exp(-a^2 / (2 sr^2)), a the angle between the two normals in degrees. Fixed tap order, FP32.
+__global__ void k_bilateral_normals(const float4* __restrict__ Nin, Intr K, int r, float sd, float sr_deg,
+                                    float4* __restrict__ Nout) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y * blockDim.y + threadIdx.y;
+  if (u >= K.W || v >= K.H) return;
+  const int i = v * K.W + u;
+  const float4 c = Nin[i];
+  float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (c.w > 0.f) {
+    const float ks = -0.5f / (sd * sd), kr = -0.5f / (sr_deg * sr_deg);
+    const float deg = 57.29577951308232f;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    for (int dv = -r; dv <= r; ++dv) {
+      const int vv = v + dv;
+      if (vv < 0 || vv >= K.H) continue;
+      for (int du = -r; du <= r; ++du) {
+        const int uu = u + du;
+        if (uu < 0 || uu >= K.W) continue;
+        const float4 q = Nin[vv * K.W + uu];
+        if (!(q.w > 0.f)) continue;
+        const float d = fminf(1.f, fmaxf(-1.f, c.x * q.x + c.y * q.y + c.z * q.z));
+        const float a = acosf(d) * deg;
+        const float w = expf(ks * (float)(du * du + dv * dv) + kr * a * a);
+        s0 += w * q.x;
+        s1 += w * q.y;
+        s2 += w * q.z;
+      }
+    }
+    const float len = sqrtf(s0 * s0 + s1 * s1 + s2 * s2);
+    if (len > 0.f) out = make_float4(s0 / len, s1 / len, s2 / len, 1.0f);
+  }
+  Nout[i] = out;
+}
+
+// Post-fusion error (Sec. 9): per CTA, the sum of |rendered - measured| and the count over the
+// pixels where both depths are positive, in FP64; the CTA partials are summed in a fixed order by
+// k_mae_final, so the result does not depend on scheduling.
+constexpr int MAE_CTAS = 256;
+__global__ void __launch_bounds__(256) k_mae_partial(const float* __restrict__ a, const float* __restrict__ b,
+                                                     int64_t n, double* __restrict__ part) {
+  __shared__ double ss[256];
+  __shared__ double sc[256];
+  double s = 0.0, c = 0.0;
+  for (int64_t i = blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)MAE_CTAS * 256) {
+    const float x = a[i], y = b[i];
+    if (x > 0.f && y > 0.f) {
+      s += fabs((double)x - (double)y);
+      c += 1.0;
+    }
+  }
+  ss[threadIdx.x] = s;
+  sc[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      ss[threadIdx.x] += ss[threadIdx.x + o];
+      sc[threadIdx.x] += sc[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = ss[0];
+    part[2 * blockIdx.x + 1] = sc[0];
+  }
+}
+
+__global__ void k_mae_final(const double* __restrict__ part, double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double s = 0.0, c = 0.0;
+  for (int k = 0; k < MAE_CTAS; ++k) {
+    s += part[2 * k];
+    c += part[2 * k + 1];
+  }
+  out[0] = s;
+  out[1] = c;
+}
+
 // ---------------------------------------------------------------- allocation
 // Record that block (bx, by, bz) needs the directions in `mask`.
 __device__ void request_block(const MapView& m, int bx, int by, int bz, uint32_t mask) {
@@ -634,6 +751,18 @@ __global__ void k_pose_compose(const double* A, int invert_a, const double* B, d
   for (int i = 0; i < 16; ++i) C[i] = out[i];
 }
 
+// depth brought to the model's metric: out = scale * in, 0 (invalid) stays 0
+__global__ void k_depth_scale(const float* __restrict__ in, float* __restrict__ out, int64_t n, float scale) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = __fmul_rn(in[i], scale);
+}
+
+void launch_depth_scale(const float* in, float* out, int64_t n, float scale, cudaStream_t s) {
+  if (n <= 0) return;
+  const int64_t blocks = (n + 255) / 256;
+  k_depth_scale<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(in, out, n, scale);
+}
+
 void launch_pose_compose(const double* A, int invert_a, const double* B, double* C, cudaStream_t s) {
   k_pose_compose<<<1, 1, 0, s>>>(A, invert_a, B, C);
 }
@@ -676,10 +805,26 @@ __global__ void k_export(MapView m, int64_t cap, int32_t* coords, float* vox) {
 
 // --------------------------------------------------------------- launchers
 void launch_preprocess(const float* depth, const Intr& K, float zmin, float zmax, float dsup, float4* P, float4* N,
-                       cudaStream_t s) {
+                       cudaStream_t s, const FilterOpts* f, float4* tmp) {
   dim3 blk(32, 8), grd((K.W + 31) / 32, (K.H + 7) / 8);
-  k_filter<<<grd, blk, 0, s>>>(depth, K, zmin, zmax, dsup, P);
-  k_normals<<<grd, blk, 0, s>>>(P, K, N);
+  const bool fd = f && f->depth_radius > 0 && tmp, fn = f && f->normal_radius > 0 && tmp;
+  if (fd) {
+    k_filter<<<grd, blk, 0, s>>>(depth, K, zmin, zmax, dsup, tmp);
+    k_bilateral_depth<<<grd, blk, 0, s>>>(tmp, K, f->depth_radius, f->depth_sigma_d, f->depth_sigma_r, P);
+  } else {
+    k_filter<<<grd, blk, 0, s>>>(depth, K, zmin, zmax, dsup, P);
+  }
+  if (fn) {
+    k_normals<<<grd, blk, 0, s>>>(P, K, tmp);
+    k_bilateral_normals<<<grd, blk, 0, s>>>(tmp, K, f->normal_radius, f->normal_sigma_d, f->normal_sigma_r, N);
+  } else {
+    k_normals<<<grd, blk, 0, s>>>(P, K, N);
+  }
+}
+
+void launch_mae(const float* a, const float* b, int64_t n, double* part, double* out, cudaStream_t s) {
+  k_mae_partial<<<MAE_CTAS, 256, 0, s>>>(a, b, n, part);
+  k_mae_final<<<1, 32, 0, s>>>(part, out);
 }
 
 void launch_alloc(const MapView& m, const float4* P, const float4* N, int npix, const Pose32& T, const double* Tdev,

@@ -438,7 +438,8 @@ void worker_main(dtsdf_server_s* s) {
 }
 
 bool opts_valid(const dtsdf_icp_opts& o) {
-  if (o.levels < 1 || o.levels > ICP_MAX_LEVELS || !(o.z_min > 0) || !(o.stop_norm >= 0) || o.min_rows < 0)
+  if (o.levels < 1 || o.levels > ICP_MAX_LEVELS || !(o.z_min > 0) || !(o.stop_norm >= 0) || o.min_rows < 0 ||
+      o.lm != 0)
     return false;
   for (int l = 0; l < o.levels; ++l)
     if (o.iters[l] < 0 || o.iters[l] > 1000 || !(o.eps[l] > 0)) return false;

@@ -49,8 +49,8 @@ def test_struct_layouts_match_header():
       printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(dtsdf_params), sizeof(dtsdf_intrinsics),
              sizeof(dtsdf_frame), sizeof(dtsdf_render_out), sizeof(dtsdf_map_stats_t),
              sizeof(dtsdf_icp_opts), sizeof(dtsdf_icp_stats));
-      printf("%zu %zu %zu\n", offsetof(dtsdf_icp_opts, stop_norm), offsetof(dtsdf_icp_stats, rows),
-             offsetof(dtsdf_params, max_blocks));
+      printf("%zu %zu %zu %zu\n", offsetof(dtsdf_icp_opts, stop_norm), offsetof(dtsdf_icp_stats, rows),
+             offsetof(dtsdf_params, max_blocks), offsetof(dtsdf_icp_opts, lm));
       printf("%zu %zu %zu %zu\n", sizeof(dtsdf_render_opts), sizeof(dtsdf_icp_problem), sizeof(dtsdf_batch_shape),
              sizeof(dtsdf_render_job));
       printf("%zu %zu %zu\n", offsetof(dtsdf_icp_problem, K_ref), offsetof(dtsdf_icp_problem, sim3),
@@ -72,7 +72,8 @@ def test_struct_layouts_match_header():
     offs = [int(x) for x in lines[1].split()]
     assert sizes == [ctypes.sizeof(x) for x in (dt.Params, dt.Intrinsics, dt.Frame, dt.RenderOut, dt.MapStats,
                                                 dt.IcpOpts, dt.IcpStats)]
-    assert offs == [dt.IcpOpts.stop_norm.offset, dt.IcpStats.rows.offset, dt.Params.max_blocks.offset]
+    assert offs == [dt.IcpOpts.stop_norm.offset, dt.IcpStats.rows.offset, dt.Params.max_blocks.offset,
+                    dt.IcpOpts.lm.offset]
     assert [int(x) for x in lines[2].split()] == [ctypes.sizeof(x) for x in (dt.RenderOpts, dt.IcpProblem,
                                                                              dt.BatchShape, dt.RenderJob)]
     assert [int(x) for x in lines[3].split()] == [dt.IcpProblem.K_ref.offset, dt.IcpProblem.sim3.offset,
@@ -105,11 +106,16 @@ def test_invalid_parameters_rejected_on_host(lib):
     assert lib.dtsdf_icp_batch(pr, 0, ctypes.byref(opts), ctypes.byref(dt.BatchShape(3, 256)), None) == \
         dt.ERR_INVALID_ARG
     assert lib.dtsdf_render_batch(None, None, 1, None) == dt.ERR_INVALID_ARG
+    # Levenberg-Marquardt is an option of the single-problem schedule only
+    lm = dt.icp_opts(lm=True)
+    assert lib.dtsdf_icp_batch(pr, 0, ctypes.byref(lm), None, None) == dt.ERR_INVALID_ARG
     # the server checks its parameters before allocating anything
     sp = dt.server_params(hbm_budget=0)
     maps = (ctypes.c_void_p * 1)(1)
     assert lib.dtsdf_server_create(maps, 1, ctypes.byref(sp), ctypes.byref(h)) == dt.ERR_INVALID_ARG
     sp = dt.server_params(streams=99)
+    assert lib.dtsdf_server_create(maps, 1, ctypes.byref(sp), ctypes.byref(h)) == dt.ERR_INVALID_ARG
+    sp = dt.server_params(opts=dt.icp_opts(lm=True))
     assert lib.dtsdf_server_create(maps, 1, ctypes.byref(sp), ctypes.byref(h)) == dt.ERR_INVALID_ARG
     sp = dt.server_params(shape=(3, 256))
     assert lib.dtsdf_server_create(maps, 1, ctypes.byref(sp), ctypes.byref(h)) == dt.ERR_INVALID_ARG

@@ -1,0 +1,124 @@
+"""Input preprocessing, bilateral filters and the post-fusion error through the C ABI
+(dtsdf_preprocess, dtsdf_set_filters, dtsdf_icp_set_filters, dtsdf_depth_mae) against the oracle.
+
+Tolerances: unfiltered preprocessing is bit-exact (both sides take it in single precision with
+the same operation order); filtered depth within 1e-5 relative (FP32 sums of up to 121 weighted
+taps against FP64) with identical presence masks; filtered normals within 1e-3 rad on 99.9 % of
+the pixels with a normal (a normal whose camera-facing decision flips at a grazing pixel differs
+by pi); the MAE sums within 1e-12 relative (FP64 on both sides, different summation order) and
+the counts exact."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import filters as OF
+import scenes
+import paper_2301_12796_gb300 as dt
+from paper_2301_12796_gb300 import build as B
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+ZMIN, ZMAX, DSUP = 0.1, 6.0, 0.02
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+    dt.lib()
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _frames():
+    s = scenes.tiny_scene(1)
+    return s, [s.frame(i) for i in range(10)]
+
+
+def test_unfiltered_preprocessing_is_bit_exact():
+    s, frames = _frames()
+    for f in frames[:3]:
+        P, N = dt.preprocess(cu(f.depth), s.K, ZMIN, ZMAX, DSUP)
+        torch.cuda.synchronize()
+        P, N = P.cpu().numpy(), N.cpu().numpy()
+        o = oracle.preprocess(f.depth, s.K, ZMIN, ZMAX, DSUP)
+        assert np.array_equal(P[..., 3] > 0, o["ok"] > 0)
+        assert np.array_equal(N[..., 3] > 0, o["nok"] > 0)
+        assert np.array_equal(P[..., :3], o["Pf"]) and np.array_equal(N[..., :3], o["nf"])
+
+
+def _angles(a, b):
+    return np.arccos(np.clip(np.sum(a * b, -1), -1.0, 1.0))
+
+
+@pytest.mark.parametrize("which", ["depth", "normals", "both"])
+def test_bilateral_filters_match_oracle(which):
+    s, frames = _frames()
+    f = dt.filter_opts(depth=which != "normals", normals=which != "depth")
+    for fr in frames[:3]:
+        P, N = dt.preprocess(cu(fr.depth), s.K, ZMIN, ZMAX, DSUP, f)
+        torch.cuda.synchronize()
+        P, N = P.cpu().numpy(), N.cpu().numpy()
+        z = oracle.preprocess(fr.depth, s.K, ZMIN, ZMAX, DSUP)["z"].astype(np.float64)
+        if f.depth_radius:
+            z = OF.bilateral_depth(z, 5, 5.0, 0.025)
+        valid = z > 0
+        assert np.array_equal(P[..., 3] > 0, valid)
+        np.testing.assert_allclose(P[..., 2][valid], z[valid], rtol=1e-5)
+        n, has = OF.normals(OF.backproject(z, s.K), valid)
+        if f.normal_radius:
+            n = OF.bilateral_normals(n, has, 5, 2.5, 5.0)
+        assert np.array_equal(N[..., 3] > 0, has)
+        ang = _angles(N[..., :3][has].astype(np.float64), n[has])
+        assert np.mean(ang <= 1e-3) >= 0.999, (which, np.mean(ang <= 1e-3), np.max(ang))
+
+
+def test_filters_in_fusion_and_icp():
+    """A map and an ICP context with both filters: the map's preprocessing is the filtered one
+    (its post-fusion error stays at the noise level) and ICP converges on the filtered pyramid."""
+    s, frames = _frames()
+    K = s.K
+    f = dt.filter_opts()
+    maes = {}
+    for name, filt in (("off", None), ("on", f)):
+        gm = dt.Map(dt.params(max_blocks=1 << 16, voxel_size=0.01, truncation=0.04, color=False))
+        gm.set_filters(filt)
+        for fr in frames:
+            gm.integrate(cu(fr.depth), None, K, fr.pose)
+        d = torch.zeros(K.height, K.width, device=DEV)
+        n = torch.zeros(K.height, K.width, 4, device=DEV)
+        tot = np.zeros(2)
+        for fr in frames:
+            gm.render(K, fr.pose, d, n)
+            out = dt.depth_mae(d, cu(fr.depth))
+            torch.cuda.synchronize()
+            tot += out.cpu().numpy()
+        maes[name] = tot[0] / tot[1]
+    assert maes["off"] < 2e-3 and maes["on"] < 2e-3, maes
+    ic = dt.Icp(K.width, K.height, 3)
+    ic.set_filters(f)
+    rd, rn = torch.zeros(K.height, K.width, device=DEV), torch.zeros(K.height, K.width, 4, device=DEV)
+    gm.render(K, frames[4].pose, rd, rn)
+    ic.set_frame(cu(frames[5].depth), None, K, ZMIN, ZMAX, DSUP)
+    T = torch.eye(4, dtype=torch.float64, device=DEV)
+    ic.solve(rd, rn, K, T, dt.icp_opts(levels=3, eps=(0.02, 0.05, 0.1), lam=0.0))
+    true = np.linalg.inv(frames[4].pose) @ frames[5].pose
+    E = np.linalg.inv(true) @ T.cpu().numpy()
+    assert np.linalg.norm(E[:3, 3]) < 3e-3
+
+
+def test_depth_mae_matches_oracle():
+    rng = np.random.default_rng(5)
+    for n in (0, 1, 1000, 307200, 1 << 21):
+        a = (1.0 + rng.random(n)).astype(np.float32)
+        b = (a + rng.normal(0, 0.01, n)).astype(np.float32)
+        a[rng.random(n) < 0.1] = 0
+        b[rng.random(n) < 0.1] = 0
+        out = dt.depth_mae(cu(a), cu(b))
+        torch.cuda.synchronize()
+        s, c = out.cpu().numpy()
+        so, co = OF.depth_mae(a, b)
+        assert int(c) == co
+        assert s == pytest.approx(so, rel=1e-12, abs=0.0)

@@ -251,17 +251,22 @@ def test_icp_normal_equations_match_oracle(sim3, level):
     assert np.allclose(T1, oicp.exp(xi) @ dT, atol=1e-6)
 
 
-def test_icp_photometric_rows_match_oracle():
+@pytest.mark.parametrize("mode", ["f2kf", "f2f"])
+def test_icp_photometric_rows_match_oracle(mode):
+    """Photometric rows against a keyframe (f2kf) and against the previous frame, whose camera is
+    the render camera (f2f: T_rs = I, Sec. 5)."""
     s = scenes.planes_scene()
     K = s.K
     T_ref = s.poses[0]
     rng = np.random.default_rng(21)
     T_kf = T_ref @ scenes.perturbation(rng, 3.0, 0.03)
+    if mode == "f2f":
+        T_kf = T_ref
     T_cur = T_ref @ scenes.perturbation(rng, 1.5, 0.015)
     cur = s.render(T_cur, noise=False)
     kf = s.render(T_kf, noise=False)
     rd, rn = _analytic_ref(s, T_ref, K)
-    T_rs = np.linalg.inv(T_kf) @ T_ref
+    T_rs = np.eye(4) if mode == "f2f" else np.linalg.inv(T_kf) @ T_ref
     dT = np.linalg.inv(T_ref) @ T_cur
     ic = dt.Icp(K.width, K.height, 3)
     ic.set_frame(cu(cur.depth), cu(cur.rgb), K, 0.1, 6.0, 0.02)
@@ -307,6 +312,41 @@ def test_icp_schedule_recovers_pose_like_oracle(sim3):
     # and both recover the true motion to the noise level
     true = np.linalg.inv(T_ref) @ T_cur
     assert np.linalg.norm(To[:3, 3] - true[:3, 3]) < 5e-3
+
+
+@pytest.mark.parametrize("sim3", [False, True])
+def test_icp_lm_schedule_matches_oracle(sim3):
+    """Levenberg-Marquardt (opts.lm = 1) against the oracle's LM schedule on a noisy frame whose
+    gain ratios stay far from 0 (accept / reject decisions are not near a tie): same pose
+    (1e-4 rad / 1e-4 m / 1e-5 relative scale), same number of evaluations, same rejections."""
+    s = scenes.planes_scene()
+    K = s.K
+    T_ref = s.poses[0]
+    rng = np.random.default_rng(5)
+    T_cur = T_ref @ scenes.perturbation(rng, 2.0, 0.02)
+    cur = s.render(T_cur, noise=True, depth_scale=1.04 if sim3 else 1.0)
+    rd, rn = _analytic_ref(s, T_ref, K)
+    ic = dt.Icp(K.width, K.height, 3)
+    ic.set_frame(cu(cur.depth), None, K, 0.1, 6.0, 0.02)
+    opts = dt.icp_opts(levels=3, iters=(10, 5, 4), eps=(0.02, 0.2, 0.3), lm=True)
+    Tdev = torch.eye(4, dtype=torch.float64, device=DEV)
+    stats = torch.zeros(dt.STATS_BYTES, dtype=torch.uint8, device=DEV)
+    ic.solve(cu(rd), cu(rn), K, Tdev, opts, sim3=sim3, stats_dev=stats)
+    Tg = Tdev.cpu().numpy()
+    st = dt.stats_from_device(stats)
+    pre = oracle.preprocess(cur.depth, K, 0.1, 6.0, 0.02)
+    levels = oicp.pyramid(pre["z"], K, 3)
+    so_ = oicp.Settings(sim3=sim3, eps=(0.02, 0.2, 0.3), iters=(10, 5, 4), lm=True)
+    To, log = oicp.track(levels, rd, rn, K, np.eye(4), so_)
+    evals = [e for e in log if "mu" in e]
+    assert any(not e["accepted"] for e in evals)
+    assert all(e["rho"] is None or abs(e["rho"]) > 0.1 for e in evals)
+    assert st.status == 0 and st.iterations == len(evals)
+    sg, so = np.cbrt(np.linalg.det(Tg[:3, :3])), np.cbrt(np.linalg.det(To[:3, :3]))
+    assert abs(sg / so - 1) <= 1e-5
+    Rg, Ro = Tg[:3, :3] / sg, To[:3, :3] / so
+    ang = np.arccos(np.clip((np.trace(Rg.T @ Ro) - 1) / 2, -1, 1))
+    assert ang <= 1e-4 and np.linalg.norm(Tg[:3, 3] - To[:3, 3]) <= 1e-4
 
 
 def test_icp_reduction_is_bitwise_deterministic():

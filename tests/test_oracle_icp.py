@@ -277,3 +277,62 @@ def test_lm_rejections_grow_the_damping():
     for lvl in range(3):
         acc = [e["E"] for e in log if e["level"] == lvl and e["accepted"]]
         assert all(y < x for x, y in zip(acc, acc[1:]))
+
+
+# ------------------------------------------ multi-sensor scale anchoring ----
+
+CYCLE = (1.0, 1.05, 0.975, 1.025, 0.95)  # Sec. 6: five sensors, five consecutive frames each
+
+
+def _cycle(n_cycles):
+    sensor = np.repeat(np.tile(np.arange(5), n_cycles), 5)
+    return sensor, np.log(np.array(CYCLE))[sensor]
+
+
+def test_scale_anchor_is_the_papers_difference():
+    """With a constant anchor estimate s^_0 and anchor value 0 the result is s^_i - s^_0 for every
+    other sensor (Eq. scale_anchor in the log domain)."""
+    sensor, true = _cycle(3)
+    s0 = 0.0123
+    est = np.where(sensor == 0, s0, true + 0.5)
+    out = icp.scale_anchor(est, sensor, 0, 0.0)
+    assert np.array_equal(out[sensor == 0], np.zeros(15))
+    np.testing.assert_allclose(out[sensor != 0], (true + 0.5 - s0)[sensor != 0], rtol=0, atol=1e-15)
+
+
+def test_scale_anchor_removes_common_drift():
+    """Estimates = true log scale + a drift common to all sensors. Drift constant over each
+    cycle cancels exactly; a linear drift leaves at most its change since the anchor's last frame
+    (20 frames for the last sensor of a cycle)."""
+    sensor, true = _cycle(4)
+    cyc = np.arange(sensor.shape[0]) // 25
+    est = true + 0.01 * cyc
+    out = icp.scale_anchor(est, sensor, 0, np.log(CYCLE[0]))
+    np.testing.assert_allclose(out, true, rtol=0, atol=1e-15)
+    rate = 1e-4
+    t = np.arange(sensor.shape[0])
+    out = icp.scale_anchor(true + rate * t, sensor, 0, 0.0)
+    last_anchor = np.array([max(j for j in range(k + 1) if sensor[j] == 0) for k in t])
+    np.testing.assert_allclose(out - true, rate * (t - last_anchor), rtol=0, atol=1e-14)
+    assert np.max(np.abs(out - true)) <= rate * 20 + 1e-14  # unanchored: rate * 99
+
+
+def test_scale_anchor_before_the_first_anchor_frame():
+    sensor = np.array([2, 3, 0, 2, 1])
+    est = np.array([0.1, 0.2, 0.05, 0.13, -0.04])
+    out = icp.scale_anchor(est, sensor, 0, 0.0)
+    assert out[0] == 0.1 and out[1] == 0.2 and out[2] == 0.0
+    assert out[3] == 0.13 - 0.05 and out[4] == -0.04 - 0.05
+
+
+def test_library_scale_anchor_matches_oracle():
+    """dtsdf_scale_anchor (host arithmetic in the library) equals the oracle bit for bit."""
+    from paper_2301_12796_gb300 import build as B
+    import paper_2301_12796_gb300 as dt
+    B.build()
+    rng = np.random.default_rng(4)
+    sensor = rng.integers(0, 5, size=400).astype(np.int32)
+    est = rng.normal(0, 0.05, size=400)
+    for anchor, val in ((0, 0.0), (3, 0.02)):
+        assert np.array_equal(dt.scale_anchor(est, sensor, anchor, val), icp.scale_anchor(est, sensor, anchor, val))
+    assert dt.scale_anchor(np.zeros(0), np.zeros(0, np.int32)).shape == (0,)
