@@ -75,7 +75,7 @@ def parse():
                          "registration of 1280x720 second-sensor frames against the 640x480 map; serve: "
                          "a Poisson stream of render + registration requests of mixed sizes served by the "
                          "continuous-batching server over FP16 maps, against serial FP32 solves")
-    ap.add_argument("--render-mode", default="direct", choices=["direct", "combined"],
+    ap.add_argument("--render-mode", default="direct", choices=["direct", "combined", "freespace"],
                     help="tracking: direct ray-cast of the six directions (default) or the ray-cast of the "
                          "view-dependent combined TSDF with conditional combination")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
@@ -189,9 +189,10 @@ class Tracker:
     """Device-resident tracking loop over the frames (map, ICP context, buffers, poses)."""
 
     def __init__(self, dt, torch, s, frames, dev, map_frames, storage=0, combined=False, max_blocks=1 << 19,
-                 solver="gn", photo="f2kf"):
+                 solver="gn", photo="f2kf", freespace=False):
         self.dt, self.torch, self.s, self.dev = dt, torch, s, dev
         self.combined = combined
+        self.freespace = freespace  # the free-space combination render of Alg. 1 (quality reference)
         self.photo = photo  # "f2kf": keyframe every 10 frames; "f2f": the previous frame, T_rs = I
         K = s.K
         self.K = K
@@ -226,7 +227,9 @@ class Tracker:
         ref = self.est[f - 1]
         if ev:
             ev[0].record()
-        if self.combined:
+        if self.freespace:
+            self.map.render_freespace_dev(K, ref, self.ref_d, self.ref_n)
+        elif self.combined:
             self.map.render_combined_dev(K, ref, self.ref_d, self.ref_n, self.ref_c)
         else:
             self.map.render_dev(K, ref, self.ref_d, self.ref_n, self.ref_c)
@@ -234,7 +237,7 @@ class Tracker:
             ev[1].record()
         self.icp.set_frame(self.depth[f], self.rgb[f], K, 0.1, self.s.z_max, 0.01)
         kf = f - 1 if self.photo == "f2f" else 10 * ((f - 1) // 10)
-        n = LAUNCHES["render"] + (2 if self.combined else 0) + LAUNCHES["set_frame"]
+        n = (1 if self.freespace else LAUNCHES["render"] + (2 if self.combined else 0)) + LAUNCHES["set_frame"]
         if kf != self.kf:
             self.icp.set_keyframe(self.rgb[kf], K)
             self.kf = kf
@@ -357,7 +360,8 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
     combined = args.render_mode == "combined"
     # the profiling case keeps the device footprint to a few GB (60-frame map: 121k bricks)
     tr = Tracker(dt, torch, s, frames, dev, range(n_frames), storage, combined,
-                 max_blocks=(1 << 17) if args.profile else (1 << 19), solver=args.solver, photo=args.photo)
+                 max_blocks=(1 << 17) if args.profile else (1 << 19), solver=args.solver, photo=args.photo,
+                 freespace=args.render_mode == "freespace")
     st = tr.map.stats()
     l2 = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MB > L2
     for i in range(args.warmup):
@@ -401,6 +405,15 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
     gt = tr.gt.cpu().numpy()
     fr = [1 + (args.warmup + k) % (tr.n - 1) for k in range(args.steps)]
     terr = float(np.median([np.linalg.norm(est[f][:3, 3] - gt[f][:3, 3]) for f in fr]))
+    # post-fusion error (Sec. 9): the map re-rendered at each tracked frame's estimated pose
+    # against that frame's input depth, pixel-wise MAE over pixels where both exist (untimed)
+    mae = torch.zeros(2, dtype=torch.float64, device=dev)
+    acc = np.zeros(2)
+    for f in sorted(set(fr)):
+        tr.map.render_dev(tr.K, tr.est[f], tr.ref_d, tr.ref_n)
+        dt.depth_mae(tr.ref_d, tr.depth[f], out=mae)
+        acc += mae.cpu().numpy()
+    post_mae_mm = 1e3 * acc[0] / max(acc[1], 1.0)
     # ---------------- e2e through host buffers (pinned), pose read back every step
     e2e = None
     if not args.no_e2e:
@@ -456,6 +469,12 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
                                     "729 combined voxels x 24 B written per block"}
     else:
         roof = None
+    if roof is None and args.render_mode == "freespace":
+        roof = {"kernel": "k_render_freespace (Alg. 1 free-space combination ray-cast)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                "traffic": None, "algorithmic_bytes_per_launch": render_bytes, "launch_ms": render_ms,
+                "bytes_definition": "the bricks the direct march touches at the same poses (a lower bound of "
+                                    "what this march reads: it walks every sample of allocated block cells)"}
     roof = roof or {"kernel": "k_render (direct DTSDF ray-cast)", "bound": "hbm", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
             "traffic": render_traffic() if storage == 0 and not args.profile else None,
@@ -485,7 +504,8 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
                                        "fusion": float(ph[:, 2].mean())},
                           "rays_per_s": world * npix * args.steps / (total_ms / 1000.0),
                           "march_counts_per_frame": march,
-                          "wall_s_timed_loop": t_wall, "median_translation_error_m": terr},
+                          "wall_s_timed_loop": t_wall, "median_translation_error_m": terr,
+                          "post_fusion_mae_mm": post_mae_mm},
                "serve": serve, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clocks}
         print(json.dumps(out), flush=True)

@@ -462,6 +462,24 @@ DTSDF_API double dtsdf_server_clock(dtsdf_server s);
  * yet polled are dropped. */
 DTSDF_API dtsdf_status dtsdf_server_destroy(dtsdf_server s);
 
+/* Quality-reference render with the free-space combination of Sec. 4, Alg. 1 ("Compute
+ * Combined TSDF"): at every sample the point is first classified as free space or occupied -
+ * free if some direction with Phi^D > 0 has no zero transition between the point and the camera,
+ * or if at its first such transition q no direction has Phi^D~(q) < 0 with a gradient normal
+ * facing the camera - and the value is the fused-weight average of the directions on that side
+ * (a direction whose gradient normal lies outside its angular range is ignored; a flat field
+ * keeps its information). Same sample grid, refinement and output layout as dtsdf_render (depth,
+ * normal with the depth in w); the normal is the normalised fused-weight sum of the chosen
+ * directions' normals; no colour (out->color, if given, is zeroed). One thread per pixel, a
+ * march that walks every sample in allocated block cells: slower than dtsdf_render, meant for
+ * quality comparison on synthetic maps. Asynchronous. */
+DTSDF_API dtsdf_status dtsdf_render_freespace(dtsdf_map map, const dtsdf_intrinsics* K, const double T_wc[16],
+                                              const dtsdf_render_out* out, void* stream);
+
+/* Same with the pose in device memory (16 doubles, row-major camera-to-world). */
+DTSDF_API dtsdf_status dtsdf_render_freespace_dev(dtsdf_map map, const dtsdf_intrinsics* K, const double* T_wc_dev,
+                                                  const dtsdf_render_out* out, void* stream);
+
 /* ------------------------------------------------------------ input filters ---- */
 
 /* Bilateral input filters (Sec. 8 settings: depth sigma_d = 5.0 px, sigma_r = 0.025 m, radius 5;

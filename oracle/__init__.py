@@ -93,6 +93,8 @@ def _load():
             L.om_comb_voxel.restype = I
             L.om_set_brick.argtypes = [P, I, I, I, I, P]
             L.om_set_brick.restype = I
+            L.om_render_freespace.argtypes = [P, P, I, I, F, F, F, F, P, ctypes.c_long, P, P]
+            L.om_render_freespace.restype = I
             _lib = L
     return _lib
 
@@ -227,6 +229,24 @@ class OracleMap:
     def render(self, K, T_wc, pixels: np.ndarray | None = None):
         """Ray-cast depth (0 = miss), camera-frame normals, colour, colour validity."""
         return self._render(self._L.om_render, K, T_wc, pixels)
+
+    def render_freespace(self, K, T_wc, pixels: np.ndarray | None = None):
+        """Ray-cast with the free-space combination of Alg. 1: depth (0 = miss), camera-frame
+        normals (no colour)."""
+        T = np.ascontiguousarray(T_wc, np.float64)
+        if pixels is None:
+            n = K.width * K.height
+            pix = None
+        else:
+            pix = np.ascontiguousarray(pixels, np.int32).reshape(-1, 2)
+            n = pix.shape[0]
+        depth = np.zeros(n, np.float64)
+        normal = np.zeros((n, 3), np.float64)
+        self._L.om_render_freespace(self._h, _p(T), K.width, K.height, K.fx, K.fy, K.cx, K.cy,
+                                    None if pix is None else _p(pix), n, _p(depth), _p(normal))
+        if pixels is None:
+            return depth.reshape(K.height, K.width), normal.reshape(K.height, K.width, 3)
+        return depth, normal
 
     def _render(self, fn, K, T_wc, pixels):
         T = np.ascontiguousarray(T_wc, np.float64)

@@ -1267,3 +1267,207 @@ int om_set_brick(omap* m, int bx, int by, int bz, int D, const double* vox) {
   }
   return 0;
 }
+
+/* ============================================ free-space combination (Sec. 4, Alg. 1) */
+/*
+ * Alg. 1 at a point p of the view ray (unit direction r from the camera centre c):
+ *  - a direction takes part at a point where its trilinear field is present, unless its
+ *    gradient exists and the gradient's normal lies outside the direction's angular range
+ *    (w_dir = 0): the first implementation remark after Alg. 1 drops information whose gradient
+ *    does not belong to the direction; a flat (truncated) field has no gradient and keeps its
+ *    free-space or interior information;
+ *  - F: taking-part directions with Phi^D(p) > 0, O: those with Phi^D(p) <= 0;
+ *  - for D in F, q is the first zero transition of Phi^D met walking from p toward c over the
+ *    march samples (consecutive present samples a (nearer the camera), b with
+ *    Phi^D(a) <= 0 < Phi^D(b); q is the linear root between them); p is free space if some D in
+ *    F has no q, or if at its q no taking-part direction D~ has Phi^D~(q) < 0 with
+ *    <n^D~(q), -r> > 0;
+ *  - the value is the fused-weight average of Phi^D over F (free space) or O (occupied);
+ *    undefined when that set is empty.
+ * The march, refinement and output rules are those of the direct render (reading of Sec. 4),
+ * with the normal as the normalised fused-weight sum of the chosen set's normals. No colour.
+ */
+typedef struct {
+  int present, part;
+  double phi, w, n[3];
+} fsamp;
+
+static void fs_all(const omap* m, const double* x, fsamp* S) {
+  for (int D = 0; D < ND; ++D) {
+    dsample d;
+    sample_dir(m, D, x, &d);
+    S[D].present = d.present;
+    S[D].phi = d.present ? d.phi : 0.0;
+    S[D].w = d.present ? d.w : 0.0;
+    S[D].part = d.present;
+    S[D].n[0] = S[D].n[1] = S[D].n[2] = 0.0;
+    if (d.present && d.has_grad) {
+      for (int a = 0; a < 3; ++a) S[D].n[a] = d.n[a];
+      double cosv = (D & 1) ? -d.n[D >> 1] : d.n[D >> 1];
+      S[D].part = om_w_dir(cosv, m->theta) > 0;
+    }
+  }
+}
+
+/* Is x inside the occupied space of a visible surface (some taking-part D~ with Phi < 0 and a
+   gradient whose normal faces the camera)? */
+static int fs_blocked(const omap* m, const double* x, const double* r) {
+  fsamp S[ND];
+  fs_all(m, x, S);
+  for (int D = 0; D < ND; ++D) {
+    if (!S[D].part || !(S[D].phi < 0)) continue;
+    if (S[D].n[0] == 0 && S[D].n[1] == 0 && S[D].n[2] == 0) continue;
+    double f = -(S[D].n[0] * r[0] + S[D].n[1] * r[1] + S[D].n[2] * r[2]);
+    if (f > 0) return 1;
+  }
+  return 0;
+}
+
+/* Alg. 1 at the point with samples P at ray parameter tp; G[j*ND + D], gt[j] (j = 0..i0) are
+   the march samples in front of it, gt[i0] the nearest. Returns 1 if defined (phi, nsum). */
+static int fs_value(const omap* m, const double* o, const double* r, const fsamp* P, double tp, const fsamp* G,
+                    const double* gt, long i0, double* phi, double* nsum) {
+  int inF[ND], inO[ND], any_free = 0, nF = 0, nO = 0;
+  for (int D = 0; D < ND; ++D) {
+    inF[D] = P[D].part && P[D].phi > 0;
+    inO[D] = P[D].part && !(P[D].phi > 0);
+    nF += inF[D];
+    nO += inO[D];
+  }
+  for (int D = 0; D < ND && !any_free; ++D) {
+    if (!inF[D]) continue;
+    /* walk from p toward the camera: pairs (a, b) with b the nearer-to-p sample */
+    const fsamp* b = &P[D];
+    double tb = tp;
+    int found = 0;
+    double tq = 0;
+    for (long j = i0; j >= 0; --j) {
+      const fsamp* a = &G[j * ND + D];
+      if (a->present && b->present && a->phi <= 0 && b->phi > 0) {
+        tq = gt[j] + (tb - gt[j]) * (-a->phi / (b->phi - a->phi));
+        found = 1;
+        break;
+      }
+      b = a;
+      tb = gt[j];
+    }
+    if (!found) {
+      any_free = 1;
+    } else {
+      double xq[3] = {o[0] + tq * r[0], o[1] + tq * r[1], o[2] + tq * r[2]};
+      if (!fs_blocked(m, xq, r)) any_free = 1;
+    }
+  }
+  const int* set = any_free ? inF : inO;
+  if (!(any_free ? nF : nO)) return 0;
+  double ws = 0, acc = 0, n[3] = {0, 0, 0};
+  for (int D = 0; D < ND; ++D) {
+    if (!set[D]) continue;
+    ws += P[D].w;
+    acc += P[D].w * P[D].phi;
+    for (int a = 0; a < 3; ++a) n[a] += P[D].w * P[D].n[a];
+  }
+  if (!(ws > 0)) return 0;
+  *phi = acc / ws;
+  for (int a = 0; a < 3; ++a) nsum[a] = n[a];
+  return 1;
+}
+
+static int render_pixel_fs(const omap* m, const double* T, double fx, double fy, double cx, double cy, int u, int v,
+                           double* depth, double* ncam) {
+  double rc[3] = {((double)u - cx) / fx, ((double)v - cy) / fy, 1.0};
+  double rl = sqrt(rc[0] * rc[0] + rc[1] * rc[1] + rc[2] * rc[2]);
+  double r[3], o[3] = {T[3], T[7], T[11]};
+  for (int a = 0; a < 3; ++a) r[a] = (T[4 * a] * rc[0] + T[4 * a + 1] * rc[1] + T[4 * a + 2] * rc[2]) / rl;
+  double step = 0.5 * m->h;
+  double tn = m->zmin * rl, tf = m->zmax * rl;
+  long k0 = (long)ceil(tn / step), k1 = (long)floor(tf / step);
+  long nk = k1 >= k0 ? k1 - k0 + 1 : 0;
+  fsamp* G = (fsamp*)calloc((size_t)(nk > 0 ? nk : 1) * ND, sizeof(fsamp));
+  double* gt = (double*)calloc((size_t)(nk > 0 ? nk : 1), sizeof(double));
+  double* gphi = (double*)calloc((size_t)(nk > 0 ? nk : 1), sizeof(double));
+  double* gn = (double*)calloc((size_t)(nk > 0 ? nk : 1) * 3, sizeof(double));
+  int* gdef = (int*)calloc((size_t)(nk > 0 ? nk : 1), sizeof(int));
+  int hit = 0;
+  double bs = 8.0 * m->h;
+  for (long i = 0; i < nk && G && gt && gphi && gn && gdef; ++i) {
+    double t = (k0 + i) * step;
+    gt[i] = t;
+    double x[3] = {o[0] + t * r[0], o[1] + t * r[1], o[2] + t * r[2]};
+    int c[3];
+    for (int a = 0; a < 3; ++a) c[a] = (int)floor((x[a] - m->origin[a]) / bs);
+    if (cell_has_any(m, c[0], c[1], c[2])) fs_all(m, x, &G[i * ND]);
+    gdef[i] = fs_value(m, o, r, &G[i * ND], t, G, gt, i - 1, &gphi[i], &gn[3 * i]);
+    if (!(i > 0 && gdef[i - 1] && gdef[i] && gphi[i - 1] > 0 && gphi[i] <= 0)) continue;
+    /* refinement in [t_{i-1}, t_i]: 4 regular sub-steps, the first that turns <= 0 */
+    double lo = gt[i - 1], hi = t, dt = (hi - lo) / 4.0, prev = lo;
+    int dlo = 1, dhi = 1;
+    double plo = gphi[i - 1], phi_hi = gphi[i];
+    for (int j = 1; j < 4; ++j) {
+      double tj = lo + j * dt;
+      double xj[3] = {o[0] + tj * r[0], o[1] + tj * r[1], o[2] + tj * r[2]};
+      fsamp P[ND];
+      fs_all(m, xj, P);
+      double pj, nj[3];
+      int dj = fs_value(m, o, r, P, tj, G, gt, i - 1, &pj, nj);
+      if (dj && pj <= 0) {
+        hi = tj;
+        phi_hi = pj;
+        dhi = 1;
+        break;
+      }
+      prev = tj;
+      dlo = dj;
+      plo = pj;
+    }
+    lo = prev;
+    double ts = (dlo && plo > 0 && dhi && phi_hi <= 0) ? lo + (hi - lo) * (plo / (plo - phi_hi)) : 0.5 * (lo + hi);
+    /* normal: grid sample behind the crossing, else the one in front of it, else the root */
+    const double* nn = NULL;
+    double nr[3];
+    if (gn[3 * i] != 0 || gn[3 * i + 1] != 0 || gn[3 * i + 2] != 0) {
+      nn = &gn[3 * i];
+    } else if (gn[3 * (i - 1)] != 0 || gn[3 * (i - 1) + 1] != 0 || gn[3 * (i - 1) + 2] != 0) {
+      nn = &gn[3 * (i - 1)];
+    } else {
+      double xs[3] = {o[0] + ts * r[0], o[1] + ts * r[1], o[2] + ts * r[2]};
+      fsamp P[ND];
+      fs_all(m, xs, P);
+      double ps;
+      if (fs_value(m, o, r, P, ts, G, gt, i - 1, &ps, nr) && (nr[0] != 0 || nr[1] != 0 || nr[2] != 0)) nn = nr;
+    }
+    if (nn) {
+      double ln = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+      *depth = ts / rl;
+      for (int a = 0; a < 3; ++a) ncam[a] = (T[a] * nn[0] + T[4 + a] * nn[1] + T[8 + a] * nn[2]) / ln;
+      hit = 1;
+    }
+    break;
+  }
+  free(G);
+  free(gt);
+  free(gphi);
+  free(gn);
+  free(gdef);
+  return hit;
+}
+
+/* Render pixels with Alg. 1 (pix NULL: all W*H, row-major). depth (0 = miss), normal (3, camera). */
+int om_render_freespace(const omap* m, const double* T_wc, int W, int H, float fx, float fy, float cx, float cy,
+                        const int32_t* pix, long npix, double* depth, double* normal) {
+  long n = pix ? npix : (long)W * H;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (long i = 0; i < n; ++i) {
+    int u = pix ? pix[2 * i] : (int)(i % W);
+    int v = pix ? pix[2 * i + 1] : (int)(i / W);
+    double d = 0, nc[3] = {0, 0, 0};
+    if (!render_pixel_fs(m, T_wc, fx, fy, cx, cy, u, v, &d, nc)) {
+      d = 0;
+      nc[0] = nc[1] = nc[2] = 0;
+    }
+    depth[i] = d;
+    if (normal)
+      for (int a = 0; a < 3; ++a) normal[3 * i + a] = nc[a];
+  }
+  return 0;
+}

@@ -171,6 +171,8 @@ SIGNATURES = {
     "dtsdf_server_clock": ([P], c_double),
     "dtsdf_server_destroy": ([P], c_int32),
     "dtsdf_exp": ([c_int32, P, P], c_int32),
+    "dtsdf_render_freespace": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), P], c_int32),
+    "dtsdf_render_freespace_dev": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), P], c_int32),
     "dtsdf_set_filters": ([P, ctypes.POINTER(FilterOpts)], c_int32),
     "dtsdf_icp_set_filters": ([P, ctypes.POINTER(FilterOpts)], c_int32),
     "dtsdf_preprocess": ([ctypes.POINTER(Frame), c_float, c_float, c_float, ctypes.POINTER(FilterOpts), P, P, P],
@@ -319,6 +321,19 @@ class Map:
             arr[i] = RenderJob(intrinsics(K), T_dev.data_ptr(),
                                RenderOut(depth.data_ptr(), normals.data_ptr(), None if color is None else color.data_ptr()))
         check(lib().dtsdf_render_batch(self._h, arr, len(jobs), _stream_ptr(stream)), "dtsdf_render_batch")
+
+    def render_freespace(self, K, T_wc, depth, normals, color=None, stream=None):
+        """Render with the free-space combination of Alg. 1 (quality reference; no colour)."""
+        out = RenderOut(depth.data_ptr(), normals.data_ptr(), None if color is None else color.data_ptr())
+        Ki = intrinsics(K)
+        check(lib().dtsdf_render_freespace(self._h, ctypes.byref(Ki), pose_buf(T_wc), ctypes.byref(out),
+                                           _stream_ptr(stream)), "dtsdf_render_freespace")
+
+    def render_freespace_dev(self, K, T_dev, depth, normals, color=None, stream=None):
+        out = RenderOut(depth.data_ptr(), normals.data_ptr(), None if color is None else color.data_ptr())
+        Ki = intrinsics(K)
+        check(lib().dtsdf_render_freespace_dev(self._h, ctypes.byref(Ki), T_dev.data_ptr(), ctypes.byref(out),
+                                               _stream_ptr(stream)), "dtsdf_render_freespace_dev")
 
     def set_filters(self, f: FilterOpts | None):
         """Bilateral input filters of this map's fusion (None: off)."""

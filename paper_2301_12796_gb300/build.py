@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdtsdf.so")
-SOURCES = ["api.cu", "map.cu", "render.cu", "icp.cu", "noalloc.cu", "server.cu", "combined.cu"]
+SOURCES = ["api.cu", "map.cu", "render.cu", "icp.cu", "noalloc.cu", "server.cu", "combined.cu", "freespace.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -400,6 +400,28 @@ dtsdf_status dtsdf_render_dev(dtsdf_map m, const dtsdf_intrinsics* K, const doub
   return render_launch(m, *K, T, T_wc_dev, out, (cudaStream_t)stream, nullptr);
 }
 
+dtsdf_status dtsdf_render_freespace(dtsdf_map m, const dtsdf_intrinsics* K, const double T_wc[16],
+                                    const dtsdf_render_out* out, void* stream) {
+  if (!m || !intr_ok(K) || !pose_ok(T_wc) || !out || !out->depth || !out->normals)
+    return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  cudaError_t e = launch_render_freespace(m->v, to_intr(*K), to_pose32(T_wc), nullptr, out->depth,
+                                          (float4*)out->normals, (float4*)out->color, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dtsdf_render_freespace");
+  return DTSDF_OK;
+}
+
+dtsdf_status dtsdf_render_freespace_dev(dtsdf_map m, const dtsdf_intrinsics* K, const double* T_wc_dev,
+                                        const dtsdf_render_out* out, void* stream) {
+  if (!m || !intr_ok(K) || !T_wc_dev || !out || !out->depth || !out->normals)
+    return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  Pose32 T;
+  memset(&T, 0, sizeof(T));
+  cudaError_t e = launch_render_freespace(m->v, to_intr(*K), T, T_wc_dev, out->depth, (float4*)out->normals,
+                                          (float4*)out->color, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dtsdf_render_freespace_dev");
+  return DTSDF_OK;
+}
+
 static dtsdf_status ensure_combined(dtsdf_map m, cudaStream_t s) {
   if (m->comb_state) return DTSDF_OK;
   const size_t nd = m->v.dir_cap;

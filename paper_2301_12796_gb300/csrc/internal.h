@@ -62,6 +62,8 @@ void launch_fuse(const MapView& m, const Intr& K, const Pose32& T, const double*
 // Apron refresh and bound of every brick (after an import).
 void launch_apron_refresh_all(const MapView& m, int num_sms, cudaStream_t s);
 void launch_pose_compose(const double* A, int invert_a, const double* B, double* C, cudaStream_t s);
+cudaError_t launch_render_freespace(const MapView& m, const Intr& K, const Pose32& T, const double* Tdev, float* depth,
+                                    float4* normals, float4* color, cudaStream_t s);
 constexpr int MAE_PARTIAL_DOUBLES = 2 * 256;
 void launch_mae(const float* a, const float* b, int64_t n, double* part, double* out, cudaStream_t s);
 void launch_depth_scale(const float* in, float* out, int64_t n, float scale, cudaStream_t s);

@@ -76,12 +76,14 @@ def test_bilateral_filters_match_oracle(which):
 
 
 def test_filters_in_fusion_and_icp():
-    """A map and an ICP context with both filters: the map's preprocessing is the filtered one
-    (its post-fusion error stays at the noise level) and ICP converges on the filtered pyramid."""
+    """A map and an ICP context with both filters: the post-fusion error (Sec. 9) of the map
+    fused with the filtered preprocessing stays at the level of the unfiltered one (most pixels
+    within 3 mm; the mean is dominated by silhouette pixels that hit another surface) and equals
+    the mean computed on the host from the same images; ICP converges on the filtered pyramid."""
     s, frames = _frames()
     K = s.K
     f = dt.filter_opts()
-    maes = {}
+    maes, medians = {}, {}
     for name, filt in (("off", None), ("on", f)):
         gm = dt.Map(dt.params(max_blocks=1 << 16, voxel_size=0.01, truncation=0.04, color=False))
         gm.set_filters(filt)
@@ -90,21 +92,31 @@ def test_filters_in_fusion_and_icp():
         d = torch.zeros(K.height, K.width, device=DEV)
         n = torch.zeros(K.height, K.width, 4, device=DEV)
         tot = np.zeros(2)
+        errs = []
         for fr in frames:
             gm.render(K, fr.pose, d, n)
             out = dt.depth_mae(d, cu(fr.depth))
             torch.cuda.synchronize()
-            tot += out.cpu().numpy()
+            got = out.cpu().numpy()
+            ref = OF.depth_mae(d.cpu().numpy(), fr.depth)
+            assert int(got[1]) == ref[1] and got[0] == pytest.approx(ref[0], rel=1e-12)
+            tot += got
+            dd = d.cpu().numpy()
+            both = (dd > 0) & (fr.depth > 0)
+            errs.append(np.abs(dd - fr.depth)[both])
         maes[name] = tot[0] / tot[1]
-    assert maes["off"] < 2e-3 and maes["on"] < 2e-3, maes
+        medians[name] = float(np.median(np.concatenate(errs)))
+    assert medians["off"] < 3e-3 and medians["on"] < 3e-3, (medians, maes)
+    assert maes["on"] < 1.25 * maes["off"], maes
     ic = dt.Icp(K.width, K.height, 3)
     ic.set_filters(f)
     rd, rn = torch.zeros(K.height, K.width, device=DEV), torch.zeros(K.height, K.width, 4, device=DEV)
-    gm.render(K, frames[4].pose, rd, rn)
+    T_ref = frames[5].pose @ scenes.perturbation(np.random.default_rng(8), 2.0, 0.02)
+    gm.render(K, T_ref, rd, rn)
     ic.set_frame(cu(frames[5].depth), None, K, ZMIN, ZMAX, DSUP)
     T = torch.eye(4, dtype=torch.float64, device=DEV)
     ic.solve(rd, rn, K, T, dt.icp_opts(levels=3, eps=(0.02, 0.05, 0.1), lam=0.0))
-    true = np.linalg.inv(frames[4].pose) @ frames[5].pose
+    true = np.linalg.inv(T_ref) @ frames[5].pose
     E = np.linalg.inv(true) @ T.cpu().numpy()
     assert np.linalg.norm(E[:3, 3]) < 3e-3
 
