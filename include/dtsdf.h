@@ -93,7 +93,7 @@ typedef struct {
 
 /* Map statistics (dtsdf_map_stats synchronises the stream). */
 typedef struct {
-  int64_t bricks;          /* allocated (block, direction) bricks */
+  int64_t bricks;          /* allocated (block, direction) bricks (recycled ones not counted) */
   int64_t blocks;          /* distinct allocated block coordinates */
   int64_t bricks_per_dir[6];
   int64_t capacity;        /* max_blocks */
@@ -215,8 +215,10 @@ DTSDF_API dtsdf_status dtsdf_pose_compose(const double* A_dev, int32_t invert_a,
 DTSDF_API dtsdf_status dtsdf_map_stats(dtsdf_map map, dtsdf_map_stats_t* stats, void* stream);
 
 /* Copy the map to host memory: coords (n x 4 int32: bx, by, bz, D) and voxels
- * (n x 512 x 6 float: sdf, w, r, g, b, wc, voxel index i + 8 j + 64 k). At most `cap`
- * bricks are written; *n_out receives the total count. Synchronous. */
+ * (n x 512 x 6 float: sdf, w, r, g, b, wc, voxel index i + 8 j + 64 k), one entry per pool
+ * brick. At most `cap` bricks are written; *n_out receives the pool count. Entries of bricks
+ * that dtsdf_recycle returned to the pool (and that were not handed out again) have D = -1;
+ * dtsdf_map_import rejects them. Synchronous. */
 DTSDF_API dtsdf_status dtsdf_map_export(dtsdf_map map, int32_t* coords, float* voxels, int64_t cap, int64_t* n_out,
                               void* stream);
 
@@ -461,6 +463,18 @@ DTSDF_API double dtsdf_server_clock(dtsdf_server s);
 /* Finish every submitted request, stop the worker and free the server's memory. Results not
  * yet polled are dropped. */
 DTSDF_API dtsdf_status dtsdf_server_destroy(dtsdf_server s);
+
+/* Voxel recycling (Sec. 3: bricks that repeated carving turned into free space go back to the
+ * pool). Every brick of a hash map whose core voxels with weight > 0 all have sdf >= free_sdf
+ * (0 < free_sdf <= 1; e.g. 0.75: at least 3/4 of the truncation range in front of any surface)
+ * is detached: its slot leaves the block's directory entry and hash mask, its copies in the
+ * neighbours' aprons and its own voxels return to the empty value (sdf 1, weight 0), and the
+ * allocator hands it out again before growing the pool. Stream-ordered with the map's other
+ * work: run it on the map's stream between frames (or on another stream after an event), never
+ * concurrently with dtsdf_integrate* or a render of the same map. recycled (host, or NULL)
+ * receives the number of bricks detached; then the call waits for the stream. Dense maps:
+ * DTSDF_ERR_INVALID_ARG. */
+DTSDF_API dtsdf_status dtsdf_recycle(dtsdf_map map, float free_sdf, int64_t* recycled, void* stream);
 
 /* Quality-reference render with the free-space combination of Sec. 4, Alg. 1 ("Compute
  * Combined TSDF"): at every sample the point is first classified as free space or occupied -

@@ -43,6 +43,12 @@ PARITY = {
     "render": "pinned: analytic plane, sphere bound, thin-sheet lemma (tests/test_oracle_render.py)",
     "combine": "pinned: one direction's values kept, identical directions kept, hand-evaluated weights, analytic "
                "plane render (tests/test_oracle_combined.py)",
+    "render_freespace": "pinned: analytic plane, thin-plate lemma, sphere bound, agreement with the direct render "
+                        "(tests/test_oracle_freespace.py)",
+    "filters": "pinned: constant / ramp / step invariants, scipy Gaussian correlation without range term, plane "
+               "normals, MAE closed form (tests/test_oracle_filters.py)",
+    "recycle": "pinned: brute-force criterion on every brick, fusion after recycling equal to fusion of a map "
+               "that never held the removed bricks (tests/test_oracle_recycle.py)",
     "icp": "pinned: finite differences, exact recovery of known SE(3)/Sim(3) (tests/test_oracle_icp.py)",
     "exp": "pinned: Rodrigues closed form, group identities (tests/test_oracle_icp.py)",
 }
@@ -95,6 +101,8 @@ def _load():
             L.om_set_brick.restype = I
             L.om_render_freespace.argtypes = [P, P, I, I, F, F, F, F, P, ctypes.c_long, P, P]
             L.om_render_freespace.restype = I
+            L.om_recycle.argtypes = [P, D]
+            L.om_recycle.restype = ctypes.c_int64
             _lib = L
     return _lib
 
@@ -180,6 +188,10 @@ class OracleMap:
         rc = self._L.om_integrate(self._h, _p(d), _p(c), d.shape[1], d.shape[0], K.fx, K.fy, K.cx, K.cy, _p(T))
         if rc != 0:
             raise MemoryError("oracle integrate failed")
+
+    def recycle(self, free_sdf: float = 0.75) -> int:
+        """Remove the bricks whose weighted voxels all have sdf >= free_sdf (Sec. 3 recycling)."""
+        return int(self._L.om_recycle(self._h, float(np.float32(free_sdf))))
 
     def num_bricks(self) -> int:
         return int(self._L.om_num_bricks(self._h))

@@ -1471,3 +1471,37 @@ int om_render_freespace(const omap* m, const double* T_wc, int W, int H, float f
   }
   return 0;
 }
+
+/* ====================================================== voxel recycling (Sec. 3) */
+/*
+ * Bricks that repeated carving turned into free space return to the pool: a brick is removed
+ * when every voxel with weight > 0 has sdf >= free_sdf. The remaining bricks keep their order
+ * and the hash is rebuilt; a later observation allocates a removed brick afresh (empty voxels).
+ * Returns the number of bricks removed.
+ */
+int64_t om_recycle(omap* m, double free_sdf) {
+  size_t w = 0;
+  int64_t removed = 0;
+  for (size_t b = 0; b < m->nbricks; ++b) {
+    const ovox* v = m->vox + b * BVOX;
+    int keep = 0;
+    for (int i = 0; i < BVOX && !keep; ++i)
+      if (v[i].w > 0 && !(v[i].sdf >= free_sdf)) keep = 1;
+    if (!keep) {
+      ++removed;
+      continue;
+    }
+    if (w != b) {
+      memmove(m->vox + w * BVOX, v, BVOX * sizeof(ovox));
+      for (int a = 0; a < 4; ++a) m->coord[4 * w + a] = m->coord[4 * b + a];
+      m->first_frame[w] = m->first_frame[b];
+    }
+    ++w;
+  }
+  m->nbricks = w;
+  memset(m->keys, 0xFF, m->cap * sizeof(uint64_t));
+  m->count = 0;
+  for (size_t b = 0; b < w; ++b)
+    hash_put(m, pack_key(m->coord[4 * b], m->coord[4 * b + 1], m->coord[4 * b + 2], m->coord[4 * b + 3]), (int32_t)b);
+  return removed;
+}

@@ -171,6 +171,7 @@ SIGNATURES = {
     "dtsdf_server_clock": ([P], c_double),
     "dtsdf_server_destroy": ([P], c_int32),
     "dtsdf_exp": ([c_int32, P, P], c_int32),
+    "dtsdf_recycle": ([P, c_float, ctypes.POINTER(c_int64), P], c_int32),
     "dtsdf_render_freespace": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), P], c_int32),
     "dtsdf_render_freespace_dev": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), P], c_int32),
     "dtsdf_set_filters": ([P, ctypes.POINTER(FilterOpts)], c_int32),
@@ -375,8 +376,16 @@ class Map:
         check(lib().dtsdf_map_stats(self._h, ctypes.byref(st), _stream_ptr(stream)), "dtsdf_map_stats")
         return st
 
+    def recycle(self, free_sdf: float = 0.75, stream=None) -> int:
+        """Return the bricks whose weighted voxels are all >= free_sdf to the pool (dtsdf_recycle);
+        returns how many were detached."""
+        n = c_int64()
+        check(lib().dtsdf_recycle(self._h, float(free_sdf), ctypes.byref(n), _stream_ptr(stream)), "dtsdf_recycle")
+        return int(n.value)
+
     def export(self, stream=None):
-        """(coords int32 [n, 4] = bx, by, bz, D; voxels float32 [n, 512, 6] = sdf, w, r, g, b, wc)."""
+        """(coords int32 [n, 4] = bx, by, bz, D; voxels float32 [n, 512, 6] = sdf, w, r, g, b, wc) of the
+        live bricks (pool entries of recycled bricks are left out)."""
         n = c_int64()
         check(lib().dtsdf_map_export(self._h, None, None, 0, ctypes.byref(n), _stream_ptr(stream)), "export")
         coords = np.zeros((n.value, 4), np.int32)
@@ -384,6 +393,9 @@ class Map:
         if n.value:
             check(lib().dtsdf_map_export(self._h, coords.ctypes.data_as(c_void_p), vox.ctypes.data_as(c_void_p),
                                          n.value, ctypes.byref(n), _stream_ptr(stream)), "export")
+        live = coords[:, 3] >= 0
+        if not live.all():
+            coords, vox = coords[live], vox[live]
         return coords, vox
 
 

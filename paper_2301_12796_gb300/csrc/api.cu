@@ -136,6 +136,7 @@ static void map_free(dtsdf_map m) {
   cudaFree(m->v.col);
   cudaFree(m->v.col8);
   cudaFree(m->v.brick_dir);
+  cudaFree(m->v.free_ring);
   cudaFree(m->v.bound);
   cudaFree(m->v.stamp);
   cudaFree(m->v.occ);
@@ -248,6 +249,7 @@ dtsdf_status dtsdf_create(const dtsdf_params* params, void* stream, dtsdf_map* o
   ALLOC(v.stamp, sizeof(uint32_t) * (size_t)bricks);
   ALLOC(v.occ, sizeof(uint32_t) * 2 * (size_t)OCC_WORDS);
   ALLOC(v.counters, sizeof(uint32_t) * C_COUNT);
+  if (p.dense_dim <= 0) ALLOC(v.free_ring, sizeof(int32_t) * (size_t)bricks);
   ALLOC(v.work, sizeof(int32_t) * (size_t)v.work_cap);
   ALLOC(m->render_q, sizeof(unsigned) * RENDER_Q_SLOTS);
 #undef ALLOC
@@ -360,6 +362,8 @@ static dtsdf_status integrate_impl(dtsdf_map m, const dtsdf_frame* f, const doub
     CK(cudaMemsetAsync(m->v.counters + C_WORK, 0, sizeof(uint32_t), s));
     CK(cudaMemcpyAsync(m->v.counters + C_POOL_BEFORE, m->v.counters + C_POOL, sizeof(uint32_t),
                        cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(m->v.counters + C_FREE_BEFORE, m->v.counters + C_FREE_TAKEN, sizeof(uint32_t),
+                       cudaMemcpyDeviceToDevice, s));
     launch_alloc(m->v, m->P, m->N, (int)npix, T, T_dev, num_sms(), s);
     CK_LAUNCH("alloc");
   }
@@ -398,6 +402,28 @@ dtsdf_status dtsdf_render_dev(dtsdf_map m, const dtsdf_intrinsics* K, const doub
   Pose32 T;
   memset(&T, 0, sizeof(T));
   return render_launch(m, *K, T, T_wc_dev, out, (cudaStream_t)stream, nullptr);
+}
+
+dtsdf_status dtsdf_recycle(dtsdf_map m, float free_sdf, int64_t* recycled, void* stream) {
+  if (!m || m->p.dense_dim > 0 || !(free_sdf > 0.0f) || !(free_sdf <= 1.0f))
+    return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t* list = nullptr;
+  CK(cudaMallocAsync((void**)&list, sizeof(int32_t) * ((size_t)m->v.pool_cap + 1), s));
+  uint32_t* nlist = (uint32_t*)(list + m->v.pool_cap);
+  cudaError_t e = cudaMemsetAsync(nlist, 0, sizeof(uint32_t), s);
+  if (e == cudaSuccess) {
+    launch_recycle(m->v, free_sdf, list, nlist, num_sms(), s);
+    e = cudaGetLastError();
+  }
+  uint32_t n = 0;
+  if (e == cudaSuccess && recycled) e = cudaMemcpyAsync(&n, nlist, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(list, s);
+  if (e == cudaSuccess && recycled) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "dtsdf_recycle");
+  if (recycled) *recycled = n;
+  m->comb_force = true;  // detached bricks change the combination of their blocks
+  return DTSDF_OK;
 }
 
 dtsdf_status dtsdf_render_freespace(dtsdf_map m, const dtsdf_intrinsics* K, const double T_wc[16],
@@ -668,7 +694,7 @@ dtsdf_status dtsdf_map_stats(dtsdf_map m, dtsdf_map_stats_t* st, void* stream) {
   CK(cudaStreamSynchronize(s));
   memset(st, 0, sizeof(*st));
   const uint32_t nb = c[C_POOL] < m->v.pool_cap ? c[C_POOL] : m->v.pool_cap;
-  st->bricks = nb;
+  st->bricks = (int64_t)nb - (int64_t)(c[C_FREE_N] - c[C_FREE_TAKEN]);
   st->blocks = c[C_DIR] < m->v.dir_cap ? c[C_DIR] : m->v.dir_cap;
   st->capacity = m->v.pool_cap;
   st->error_flags = c[C_ERR];
@@ -681,7 +707,8 @@ dtsdf_status dtsdf_map_stats(dtsdf_map m, dtsdf_map_stats_t* st, void* stream) {
       delete[] bd;
       return cuda_fail(e, "map_stats");
     }
-    for (uint32_t i = 0; i < nb; ++i) st->bricks_per_dir[bd[i] & 7]++;
+    for (uint32_t i = 0; i < nb; ++i)
+      if (bd[i] >= 0) st->bricks_per_dir[bd[i] & 7]++;
     delete[] bd;
   }
   return DTSDF_OK;

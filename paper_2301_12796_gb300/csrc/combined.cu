@@ -36,11 +36,15 @@ __device__ __forceinline__ float2 src_geom(const MapView& m, size_t i) {
 // Conditional combination (Sec. 4): recombine while fewer than 5 frames were rendered, after
 // more than 50 frames without an update, or when the camera moved by more than 0.05 m or
 // turned by more than 0.05 pi/2 since the last combination; otherwise only the blocks that
-// received bricks since then are combined, at the last combination pose.
-__global__ void k_comb_policy(CombState* st, const double* Tdev, Pose64 Tv, const uint32_t* pool_count, int force) {
+// received bricks since then are combined, at the last combination pose. Recycled bricks handed
+// out again keep old pool indices, so a change of the recycled-brick count also recombines all.
+__global__ void k_comb_policy(CombState* st, const double* Tdev, Pose64 Tv, const uint32_t* counters, int force) {
   double T[16];
   for (int i = 0; i < 16; ++i) T[i] = Tdev ? Tdev[i] : Tv.T[i];
-  bool full = force || st->frames < 5 || st->since > 50;
+  const uint32_t taken = counters[C_FREE_TAKEN];
+  bool full = force || st->frames < 5 || st->since > 50 || taken != st->taken_mark;
+  st->taken_mark = taken;
+  const uint32_t* pool_count = counters + C_POOL;
   if (!full) {
     const double* L = st->pose;
     const double dx = T[3] - L[3], dy = T[7] - L[7], dz = T[11] - L[11];
@@ -200,7 +204,7 @@ void launch_combine(const MapView& m, CombState* st, const Intr& K, const double
                     int num_sms, cudaStream_t s) {
   Pose64 Tv;
   for (int i = 0; i < 16; ++i) Tv.T[i] = Thost ? Thost[i] : 0.0;
-  k_comb_policy<<<1, 1, 0, s>>>(st, Tdev, Tv, m.counters + C_POOL, force);
+  k_comb_policy<<<1, 1, 0, s>>>(st, Tdev, Tv, m.counters, force);
   CombFrame f;
   // inward unit normals of the four side planes of the image grown by 1/8 of its size
   const float pu = 0.125f * (float)K.W, pv = 0.125f * (float)K.H;

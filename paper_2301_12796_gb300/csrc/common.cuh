@@ -50,7 +50,20 @@ __host__ __device__ __forceinline__ int val_dir(uint32_t v) { return v == VAL_EM
 __host__ __device__ __forceinline__ uint32_t val_mask(uint32_t v) { return v == VAL_EMPTY ? 0u : v >> 26; }
 
 // device counters
-enum { C_DIR = 0, C_POOL = 1, C_WORK = 2, C_ERR = 3, C_DIR_BEFORE = 4, C_POOL_BEFORE = 5, C_COUNT = 8 };
+// C_FREE_N / C_FREE_TAKEN: bricks pushed to / taken from the ring of recycled bricks (both only
+// grow; ring position = count mod pool_cap); C_FREE_BEFORE: C_FREE_TAKEN before this frame.
+enum {
+  C_DIR = 0,
+  C_POOL = 1,
+  C_WORK = 2,
+  C_ERR = 3,
+  C_DIR_BEFORE = 4,
+  C_POOL_BEFORE = 5,
+  C_FREE_N = 6,
+  C_FREE_TAKEN = 7,
+  C_FREE_BEFORE = 8,
+  C_COUNT = 10
+};
 
 __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
@@ -158,6 +171,7 @@ struct MapView {
   const uint32_t* comb_cur;  // device word: the current generation
   uint32_t* occ;       // occupancy filters: 2 x OCC_WORDS words (blocks, then 4^3-block super-cells)
   uint32_t pool_cap;
+  int32_t* free_ring;  // recycled bricks (hash maps), pool_cap entries
   uint32_t* counters;
   int32_t* work;
   uint32_t work_cap;

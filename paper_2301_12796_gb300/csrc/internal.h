@@ -62,6 +62,7 @@ void launch_fuse(const MapView& m, const Intr& K, const Pose32& T, const double*
 // Apron refresh and bound of every brick (after an import).
 void launch_apron_refresh_all(const MapView& m, int num_sms, cudaStream_t s);
 void launch_pose_compose(const double* A, int invert_a, const double* B, double* C, cudaStream_t s);
+void launch_recycle(const MapView& m, float free_sdf, int32_t* list, uint32_t* nlist, int num_sms, cudaStream_t s);
 cudaError_t launch_render_freespace(const MapView& m, const Intr& K, const Pose32& T, const double* Tdev, float* depth,
                                     float4* normals, float4* color, cudaStream_t s);
 constexpr int MAE_PARTIAL_DOUBLES = 2 * 256;
@@ -122,6 +123,7 @@ struct CombState {
   uint32_t full;       // this call recombines every block in view
   uint32_t pool_mark;  // brick count at the previous call
   uint32_t pool_from;  // bricks from this index on were allocated since the previous call
+  uint32_t taken_mark; // recycled bricks handed out again, at the previous call
 };
 struct Pose64 {
   double T[16];

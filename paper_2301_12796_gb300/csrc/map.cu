@@ -330,10 +330,18 @@ __global__ void k_alloc_assign(MapView m) {
     uint32_t have = (uint32_t)slots[SLOT_MASK];
     for (int D = 0; D < ND; ++D) {
       if (!(want & (1u << D)) || (have & (1u << D))) continue;
-      const uint32_t s = atomicAdd(m.counters + C_POOL, 1u);
-      if (s >= m.pool_cap) {
-        atomicOr(m.counters + C_ERR, ERR_POOL_FULL);
-        continue;
+      // a recycled brick first (the ring holds C_FREE_N - C_FREE_TAKEN of them; a take past
+      // the end falls back to the pool and the count is clamped after this kernel)
+      uint32_t s;
+      const uint32_t t = m.free_ring ? atomicAdd(m.counters + C_FREE_TAKEN, 1u) : 0xFFFFFFFFu;
+      if (m.free_ring && t < *((volatile uint32_t*)(m.counters + C_FREE_N))) {
+        s = (uint32_t)m.free_ring[t % m.pool_cap];
+      } else {
+        s = atomicAdd(m.counters + C_POOL, 1u);
+        if (s >= m.pool_cap) {
+          atomicOr(m.counters + C_ERR, ERR_POOL_FULL);
+          continue;
+        }
       }
       m.brick_dir[s] = d * 8 + D;
       // a new brick's apron may already hold data: no bound until it is recomputed
@@ -346,6 +354,12 @@ __global__ void k_alloc_assign(MapView m) {
     slots[SLOT_MASK] = (int32_t)have;
     *((volatile uint32_t*)(m.vals + i)) = pack_val(d, have);
   }
+}
+
+// Takes past the ring's end fell back to the pool: bring the taken count back to the end.
+__global__ void k_free_clamp(uint32_t* counters) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && counters[C_FREE_TAKEN] > counters[C_FREE_N])
+    counters[C_FREE_TAKEN] = counters[C_FREE_N];
 }
 
 // Dense mode: every (block, direction) of an n^3-block grid, directory index = linear block
@@ -521,6 +535,7 @@ __global__ void __launch_bounds__(256) k_fuse(MapView m, FuseFrame f) {
   const float h = m.h;
   for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
     const int bd = __ldg(m.brick_dir + b);
+    if (bd < 0) continue;  // a recycled brick in the free ring
     const int d = bd >> 3, D = bd & 7;
     const int bx = __ldg(m.dir_coord + 4 * d), by = __ldg(m.dir_coord + 4 * d + 1),
               bz = __ldg(m.dir_coord + 4 * d + 2);
@@ -643,8 +658,14 @@ __global__ void __launch_bounds__(256) k_apron_pull(MapView m, int all) {
   __shared__ int s_nb[27];
   const uint32_t nb = min(*((volatile uint32_t*)(m.counters + C_POOL)), m.pool_cap);
   const uint32_t b0 = all ? 0u : min(*((volatile uint32_t*)(m.counters + C_POOL_BEFORE)), nb);
-  for (uint32_t b = b0 + blockIdx.x; b < nb; b += gridDim.x) {
+  // recycled bricks handed out again this frame: ring positions [C_FREE_BEFORE, C_FREE_TAKEN)
+  const uint32_t r0 = all || !m.free_ring ? 0u : *((volatile uint32_t*)(m.counters + C_FREE_BEFORE));
+  const uint32_t r1 = all || !m.free_ring ? 0u : *((volatile uint32_t*)(m.counters + C_FREE_TAKEN));
+  const uint32_t nitems = (nb - b0) + (r1 > r0 ? r1 - r0 : 0u);
+  for (uint32_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const uint32_t b = it < nb - b0 ? b0 + it : (uint32_t)m.free_ring[(r0 + (it - (nb - b0))) % m.pool_cap];
     const int bd = m.brick_dir[b];
+    if (bd < 0) continue;
     const int d = bd >> 3, D = bd & 7;
     const int bx = m.dir_coord[4 * d], by = m.dir_coord[4 * d + 1], bz = m.dir_coord[4 * d + 2];
     if (threadIdx.x < 27) {
@@ -678,7 +699,7 @@ template <int STORE>
 __global__ void __launch_bounds__(256) k_bounds_exact(MapView m) {
   const uint32_t nb = min(*((volatile uint32_t*)(m.counters + C_POOL)), m.pool_cap);
   for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x)
-    if (m.stamp[b] == m.frame) exact_bound<STORE>(m, b);
+    if (m.stamp[b] == m.frame && m.brick_dir[b] >= 0) exact_bound<STORE>(m, b);
 }
 
 // ------------------------------------------------------------------ import
@@ -773,8 +794,10 @@ __global__ void k_export(MapView m, int64_t cap, int32_t* coords, float* vox) {
   for (uint32_t b = blockIdx.x; b < nb && b < cap; b += gridDim.x) {
     const int bd = m.brick_dir[b];
     const int d = bd >> 3;
-    if (threadIdx.x < 4)
-      coords[4 * (size_t)b + threadIdx.x] = threadIdx.x < 3 ? m.dir_coord[4 * d + threadIdx.x] : (bd & 7);
+    if (threadIdx.x < 4) {  // a recycled brick: (0, 0, 0, -1)
+      coords[4 * (size_t)b + threadIdx.x] =
+          bd < 0 ? (threadIdx.x < 3 ? 0 : -1) : (threadIdx.x < 3 ? m.dir_coord[4 * d + threadIdx.x] : (bd & 7));
+    }
     for (int vi = threadIdx.x; vi < BVOX; vi += blockDim.x) {
       const size_t ci = (size_t)b * BVOX + vi;
       const size_t gi = (size_t)b * PVOX + pad_index(vi & 7, (vi >> 3) & 7, vi >> 6);
@@ -831,6 +854,109 @@ void launch_alloc(const MapView& m, const float4* P, const float4* N, int npix, 
                   int num_sms, cudaStream_t s) {
   k_alloc_request<<<(npix + 255) / 256, 256, 0, s>>>(m, P, N, npix, T, Tdev);
   k_alloc_assign<<<num_sms * 2, 256, 0, s>>>(m);
+  if (m.free_ring) k_free_clamp<<<1, 32, 0, s>>>(m.counters);
+}
+
+// ------------------------------------------------------------------ recycling
+// A brick is recycled when every core voxel with weight > 0 has sdf >= free_sdf: repeated
+// carving (running averages toward 1) left only free space in it (Sec. 3). The list of such
+// bricks is built first; then each is detached: its slot leaves the directory and the hash
+// mask, its copies in the 26 neighbours' aprons return to the empty value (1, 0), its voxels
+// are reset and it is pushed to the free ring for the allocator.
+template <int STORE>
+__global__ void __launch_bounds__(256) k_recycle_mark(MapView m, float free_sdf, int32_t* list, uint32_t* nlist) {
+  const uint32_t nb = min(*((volatile uint32_t*)(m.counters + C_POOL)), m.pool_cap);
+  for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    if (m.brick_dir[b] < 0) continue;
+    bool free_only = true;
+    for (int vi = threadIdx.x; vi < BVOX; vi += blockDim.x) {
+      const size_t gi = (size_t)b * PVOX + pad_index(vi & 7, (vi >> 3) & 7, vi >> 6);
+      const float2 g = STORE == DTSDF_STORE_FP16 ? unpack_geom16(m.geom16[gi]) : m.geom[gi];
+      if (g.y > 0.0f && !(g.x >= free_sdf)) free_only = false;
+    }
+    free_only = __syncthreads_and(free_only);
+    if (free_only && threadIdx.x == 0) list[atomicAdd(nlist, 1u)] = (int32_t)b;
+  }
+}
+
+template <int STORE>
+__global__ void __launch_bounds__(256) k_recycle_apply(MapView m, const int32_t* list, const uint32_t* nlist) {
+  __shared__ int s_nb[27];
+  const uint32_t n = *nlist;
+  for (uint32_t it = blockIdx.x; it < n; it += gridDim.x) {
+    const int b = list[it];
+    const int bd = m.brick_dir[b];
+    const int d = bd >> 3, D = bd & 7;
+    const int bx = m.dir_coord[4 * d], by = m.dir_coord[4 * d + 1], bz = m.dir_coord[4 * d + 2];
+    if (threadIdx.x < 27) {
+      const int q = threadIdx.x;
+      int sl = -1;
+      if (q != 13) {
+        const int dd = hash_find(m, bx + q % 3 - 1, by + (q / 3) % 3 - 1, bz + q / 9 - 1);
+        sl = dd >= 0 ? m.dir_slots[(size_t)dd * 8 + D] : -1;
+      }
+      s_nb[q] = sl;
+    }
+    __syncthreads();
+    // the neighbours' apron positions that mirror this brick's voxels (as the apron push writes them)
+    for (int vi = threadIdx.x; vi < PVOX; vi += blockDim.x) {
+      const int x = vi % PAD - 1, y = (vi / PAD) % PAD - 1, z = vi / (PAD * PAD) - 1;
+      const int ex = x >> 3, ey = y >> 3, ez = z >> 3;
+      if ((ex | ey | ez) == 0) continue;
+      const int sl = s_nb[(1 - ez) * 9 + (1 - ey) * 3 + (1 - ex)];
+      if (sl < 0) continue;
+      if (STORE == DTSDF_STORE_FP16)
+        m.geom16[(size_t)sl * PVOX + vi] = pack_geom16(1.0f, 0.0f);
+      else
+        m.geom[(size_t)sl * PVOX + vi] = make_float2(1.0f, 0.0f);
+    }
+    // the brick itself, core and apron, and its colour
+    for (int vi = threadIdx.x; vi < PVOX; vi += blockDim.x) {
+      if (STORE == DTSDF_STORE_FP16)
+        m.geom16[(size_t)b * PVOX + vi] = pack_geom16(1.0f, 0.0f);
+      else
+        m.geom[(size_t)b * PVOX + vi] = make_float2(1.0f, 0.0f);
+    }
+    if (m.color) {
+      for (int vi = threadIdx.x; vi < BVOX; vi += blockDim.x) {
+        if (STORE == DTSDF_STORE_FP16)
+          m.col8[(size_t)b * BVOX + vi] = 0u;
+        else
+          m.col[(size_t)b * BVOX + vi] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    if (threadIdx.x == 0) {
+      // leave the directory and the hash mask
+      m.dir_slots[(size_t)d * 8 + D] = -1;
+      atomicAnd((unsigned*)(m.dir_slots + (size_t)d * 8 + SLOT_MASK), ~(1u << D));
+      const unsigned long long k = pack_block(bx, by, bz);
+      uint32_t i = hash_slot(k, m.hmask);
+      for (int p = 0; p < MAX_PROBE; ++p) {
+        const unsigned long long kk = m.keys[i];
+        if (kk == k) {
+          atomicAnd(m.vals + i, ~(1u << (26 + D)));
+          break;
+        }
+        if (kk == EMPTY_KEY) break;
+        i = (i + 1) & m.hmask;
+      }
+      m.bound[b] = INFINITY;
+      m.brick_dir[b] = -1;
+      const uint32_t pos = atomicAdd(m.counters + C_FREE_N, 1u);
+      m.free_ring[pos % m.pool_cap] = b;
+    }
+    __syncthreads();
+  }
+}
+
+void launch_recycle(const MapView& m, float free_sdf, int32_t* list, uint32_t* nlist, int num_sms, cudaStream_t s) {
+  if (m.storage == DTSDF_STORE_FP16) {
+    k_recycle_mark<DTSDF_STORE_FP16><<<num_sms * 8, 256, 0, s>>>(m, free_sdf, list, nlist);
+    k_recycle_apply<DTSDF_STORE_FP16><<<num_sms * 4, 256, 0, s>>>(m, list, nlist);
+  } else {
+    k_recycle_mark<DTSDF_STORE_FP32><<<num_sms * 8, 256, 0, s>>>(m, free_sdf, list, nlist);
+    k_recycle_apply<DTSDF_STORE_FP32><<<num_sms * 4, 256, 0, s>>>(m, list, nlist);
+  }
 }
 
 void launch_dense_fill(const MapView& m, int nb, cudaStream_t s) {
@@ -891,6 +1017,7 @@ void launch_import(const MapView& m, const int32_t* coords, const float* vox, in
   if (allocate && n > 0) {
     k_import_request<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m, coords, n);
     k_alloc_assign<<<num_sms * 2, 256, 0, s>>>(m);
+    if (m.free_ring) k_free_clamp<<<1, 32, 0, s>>>(m.counters);
   }
   if (n > 0) k_import_write<<<num_sms * 4, 256, 0, s>>>(m, coords, vox, n);
 }
