@@ -45,7 +45,7 @@ FALLBACK_HBM_GBS = 6800.0
 # default workload (FP32 storage with colour, first timed render), from one ncu capture of
 # ``bench.py --steps 2 --warmup 3 --no-e2e --no-cpu`` (profiles/k_render_kinect640.md). It
 # belongs to the kernel sources it was taken with: reported only while their hash matches.
-RENDER_TRAFFIC = {"bytes": 281753856 + 15643392, "sources_sha1_16": "e1e4d1278955c2e8",
+RENDER_TRAFFIC = {"bytes": 281167616 + 15277824, "sources_sha1_16": "3a3ec4d5541e58e9",
                   "files": ("render.cu", "common.cuh", "internal.h")}
 
 
@@ -62,8 +62,8 @@ def render_traffic():
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames", type=int, default=300)
     ap.add_argument("--no-e2e", action="store_true")
@@ -182,7 +182,7 @@ def opts_kinect(dt, solver="gn"):
                        lam=0.1, z_min=0.1, stop_norm=1e-6, min_rows=10, lm=solver == "lm")
 
 
-LAUNCHES = {"render": 2, "set_frame": 6, "set_keyframe": 6, "compose": 1, "solve": 19, "integrate": 8}
+LAUNCHES = {"render": 2, "set_frame": 6, "set_keyframe": 6, "compose": 1, "solve": 19, "integrate": 9}
 
 
 class Tracker:
@@ -503,6 +503,8 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
                           "phase_ms": {"render": render_ms, "preprocess_pyramid_icp": float(ph[:, 1].mean()),
                                        "fusion": float(ph[:, 2].mean())},
                           "rays_per_s": world * npix * args.steps / (total_ms / 1000.0),
+                          "frame_ms_p50": float(np.percentile(step_ms, 50)),
+                          "frame_ms_p99": float(np.percentile(step_ms, 99)),
                           "march_counts_per_frame": march,
                           "wall_s_timed_loop": t_wall, "median_translation_error_m": terr,
                           "post_fusion_mae_mm": post_mae_mm},
