@@ -24,7 +24,7 @@ namespace dtsdf {
 
 constexpr int RT_N = 128;  // threads per CTA of the persistent render grid
 #ifndef DTSDF_RENDER_MINB
-#define DTSDF_RENDER_MINB 4   // resident CTAs per SM the register allocation is sized for
+#define DTSDF_RENDER_MINB 3   // resident CTAs per SM the register allocation is sized for (159 registers, no spills)
 #endif
 
 // Out-of-line hash probe over explicit pointers (keeps callers' state in registers).
