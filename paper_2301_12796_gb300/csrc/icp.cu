@@ -91,24 +91,31 @@ __device__ void mat4_mul(const double* A, const double* B, double* C) {
 // with series where th or sigma vanish.
 // The transcendental values sin(th), cos(th), e^sigma and e^sigma - 1 (th = |omega|) are
 // passed in, so that a warp can evaluate them in parallel lanes.
-__host__ __device__ void exp_sim3_from(const double* xi, int dim, double sin_th, double cos_th, double es, double em1,
-                                       double* T) {
+// Evaluated by one warp, as the solve uses it: every lane forms the scalar
+// coefficients (identical values; reciprocals instead of repeated divisions: GB300's FP64 rate is
+// low, so the dependent FP64 chain is the solve's latency), lanes 0-11 one entry each of the top
+// 3x4 block of T, lanes 12-15 the last row. T: shared or global, written by lanes 0-15.
+__device__ void exp_sim3_warp(const double* xi, int dim, double sin_th, double cos_th, double es, double em1,
+                              double* T, int lane) {
   const double nu0 = xi[0], nu1 = xi[1], nu2 = xi[2];
   const double w0 = xi[3], w1 = xi[4], w2 = xi[5];
   const double sg = dim == 7 ? xi[6] : 0.0;
   const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
   const double th = sqrt(th2);
-  double a, b;  // Rodrigues coefficients sin(th)/th, (1 - cos th)/th^2
-  if (th < 1e-4) {
-    a = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
-    b = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+  const bool small = th < 1e-4;
+  const double inv_th = small ? 0.0 : 1.0 / th;
+  const double inv_th2 = inv_th * inv_th;
+  double a, b;  // sin(th)/th, (1 - cos th)/th^2
+  if (small) {
+    a = 1.0 - th2 * (1.0 / 6.0) + th2 * th2 * (1.0 / 120.0);
+    b = 0.5 - th2 * (1.0 / 24.0) + th2 * th2 * (1.0 / 720.0);
   } else {
-    a = sin_th / th;
-    b = (1.0 - cos_th) / th2;
+    a = sin_th * inv_th;
+    b = (1.0 - cos_th) * inv_th2;
   }
   const double A = sg != 0.0 ? em1 / sg : 1.0;
   double B, C;
-  if (th < 1e-4) {
+  if (small) {
     // expansions of the integrals in th (exact in sigma), leading orders
     double I1, I2, I3;  // int s e^{s sg}, int s^2 e^{s sg} / 2, int s^3 e^{s sg} / 6 over [0, 1]
     if (fabs(sg) < 1e-2) {
@@ -131,38 +138,45 @@ __host__ __device__ void exp_sim3_from(const double* xi, int dim, double sin_th,
     B = I1 - th2 * I3;
     C = I2;
   } else {
-    const double D = sg * sg + th2;
-    const double Is = (es * (sg * sin_th - th * cos_th) + th) / D;
-    const double Ic = (es * (sg * cos_th + th * sin_th) - sg) / D;
-    B = Is / th;
-    C = (A - Ic) / th2;
+    const double inv_D = sg != 0.0 ? 1.0 / (sg * sg + th2) : inv_th2;
+    const double Is = (es * (sg * sin_th - th * cos_th) + th) * inv_D;
+    const double Ic = (es * (sg * cos_th + th * sin_th) - sg) * inv_D;
+    B = Is * inv_th;
+    C = (A - Ic) * inv_th2;
   }
-  // omega^ and omega^2
-  const double W[9] = {0, -w2, w1, w2, 0, -w0, -w1, w0, 0};
-  double W2[9];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) W2[3 * i + j] = W[3 * i] * W[j] + W[3 * i + 1] * W[3 + j] + W[3 * i + 2] * W[6 + j];
-  for (int i = 0; i < 3; ++i) {
-    for (int j = 0; j < 3; ++j) {
-      const double id = i == j ? 1.0 : 0.0;
-      T[4 * i + j] = es * (id + a * W[3 * i + j] + b * W2[3 * i + j]);
-    }
-    const double V0 = A * (i == 0) + B * W[3 * i] + C * W2[3 * i];
-    const double V1 = A * (i == 1) + B * W[3 * i + 1] + C * W2[3 * i + 1];
-    const double V2 = A * (i == 2) + B * W[3 * i + 2] + C * W2[3 * i + 2];
+  if (lane >= 16) return;
+  if (lane >= 12) {
+    T[lane] = lane == 15 ? 1.0 : 0.0;
+    return;
+  }
+  const int i = lane >> 2, j = lane & 3;
+  // row i of omega^ and of omega^2 (omega^ = [[0,-w2,w1],[w2,0,-w0],[-w1,w0,0]])
+  const double r0 = i == 0 ? 0.0 : (i == 1 ? w2 : -w1);
+  const double r1 = i == 0 ? -w2 : (i == 1 ? 0.0 : w0);
+  const double r2 = i == 0 ? w1 : (i == 1 ? -w0 : 0.0);
+  const double q0 = r1 * w2 - r2 * w1;  // (omega^2)_{i,0} = row_i . column 0 = (0, w2, -w1)
+  const double q1 = -r0 * w2 + r2 * w0; // column 1 = (-w2, 0, w0)
+  const double q2 = r0 * w1 - r1 * w0;  // column 2 = (w1, -w0, 0)
+  if (j < 3) {
+    const double wij = j == 0 ? r0 : (j == 1 ? r1 : r2);
+    const double qij = j == 0 ? q0 : (j == 1 ? q1 : q2);
+    T[4 * i + j] = es * ((i == j ? 1.0 : 0.0) + a * wij + b * qij);
+  } else {
+    const double V0 = A * (i == 0) + B * r0 + C * q0;
+    const double V1 = A * (i == 1) + B * r1 + C * q1;
+    const double V2 = A * (i == 2) + B * r2 + C * q2;
     T[4 * i + 3] = V0 * nu0 + V1 * nu1 + V2 * nu2;
   }
-  T[12] = T[13] = T[14] = 0.0;
-  T[15] = 1.0;
 }
 
-__host__ __device__ void exp_sim3(const double* xi, int dim, double* T) {
+__global__ void k_exp(int dim, const double* xi, double* T) {
+  const int lane = threadIdx.x & 31;
   const double th = sqrt(xi[3] * xi[3] + xi[4] * xi[4] + xi[5] * xi[5]);
   const double sg = dim == 7 ? xi[6] : 0.0;
-  exp_sim3_from(xi, dim, sin(th), cos(th), exp(sg), expm1(sg), T);
+  double s_th, c_th;
+  sincos(th, &s_th, &c_th);
+  exp_sim3_warp(xi, dim, s_th, c_th, exp(sg), expm1(sg), T, lane);
 }
-
-__global__ void k_exp(int dim, const double* xi, double* T) { exp_sim3(xi, dim, T); }
 
 // Solve and update of one Gauss-Newton iteration from the FP64 sums (layout of Acc<DIM>:
 // upper triangle of H, g, E, geometric rows, photometric rows) for the leading dsolve
@@ -189,6 +203,7 @@ __device__ bool icp_solve_update_warp(const double* sum, int dsolve, double* pos
   constexpr int NH = DIM * (DIM + 1) / 2;
   constexpr int N = NH + DIM + 3;
   __shared__ double sL[7][8];
+  __shared__ double sInv[8];  // 1 / L_jj
   __shared__ double sb[8];
   __shared__ double sgv[8];
   __shared__ double sE[16];
@@ -294,7 +309,10 @@ __device__ bool icp_solve_update_warp(const double* sum, int dsolve, double* pos
     }
     const double ljj = sqrt(s), inv = 1.0 / ljj;
     __syncwarp();
-    if (lane == j) sL[j][j] = ljj;
+    if (lane == j) {
+      sL[j][j] = ljj;
+      sInv[j] = inv;
+    }
     if (lane > j && lane < D) sL[lane][j] = sL[lane][j] * inv;
     __syncwarp();
     const int m = D - 1 - j;  // trailing lower triangle, rows and columns j + 1 .. D - 1
@@ -318,14 +336,14 @@ __device__ bool icp_solve_update_warp(const double* sum, int dsolve, double* pos
   if (lane < D) sb[lane] = -sgv[lane];
   __syncwarp();
   for (int i = 0; i < D; ++i) {
-    const double y = sb[i] / sL[i][i];
+    const double y = sb[i] * sInv[i];
     __syncwarp();
     if (lane == i) sb[i] = y;
     if (lane > i && lane < D) sb[lane] -= sL[lane][i] * y;
     __syncwarp();
   }
   for (int i = D - 1; i >= 0; --i) {
-    const double x = sb[i] / sL[i][i];
+    const double x = sb[i] * sInv[i];
     __syncwarp();
     if (lane == i) sb[i] = x;
     if (lane < i) sb[lane] -= sL[i][lane] * x;
@@ -344,17 +362,17 @@ __device__ bool icp_solve_update_warp(const double* sum, int dsolve, double* pos
       for (int j = 0; j < D; ++j) q += xi[i] * lm->H[7 * i + j] * xi[j];
     lm->pred = q + 2.0 * mu * (nrm * nrm);
   }
-  // exponential map: transcendental values in lanes 1-4, the rest in lane 0
+  // exponential map: sin and cos in lane 1, e^sigma and e^sigma - 1 in lanes 3 and 4 (Sim(3)
+  // only; 1 and 0 for SE(3)), then the entries of exp(xi) over lanes 0-15
   const double th = sqrt(xi[3] * xi[3] + xi[4] * xi[4] + xi[5] * xi[5]);
   const double sg = D == 7 ? xi[6] : 0.0;
-  double f = 0.0;
-  if (lane == 1) f = sin(th);
-  if (lane == 2) f = cos(th);
-  if (lane == 3) f = exp(sg);
-  if (lane == 4) f = expm1(sg);
-  const double s_th = __shfl_sync(FULL, f, 1), c_th = __shfl_sync(FULL, f, 2);
-  const double es = __shfl_sync(FULL, f, 3), em1 = __shfl_sync(FULL, f, 4);
-  if (lane == 0) exp_sim3_from(xi, D, s_th, c_th, es, em1, sE);
+  double fs = 0.0, fc = 1.0, fe = 1.0, fm = 0.0;
+  if (lane == 1) sincos(th, &fs, &fc);
+  if (D == 7 && lane == 3) fe = exp(sg);
+  if (D == 7 && lane == 4) fm = expm1(sg);
+  const double s_th = __shfl_sync(FULL, fs, 1), c_th = __shfl_sync(FULL, fc, 1);
+  const double es = __shfl_sync(FULL, fe, 3), em1 = __shfl_sync(FULL, fm, 4);
+  exp_sim3_warp(xi, D, s_th, c_th, es, em1, sE, lane);
   __syncwarp();
   double t = 0.0;
   if (lane < 16) {
@@ -500,22 +518,33 @@ __global__ void __launch_bounds__(ICP_THREADS) k_icp(IcpArgs a) {
   __shared__ float s_red[ICP_THREADS / 32][A::N];
   __shared__ double s_sum[A::N];
   __shared__ int s_last;
+  __shared__ float s_pose[24];
   if (*((volatile int32_t*)a.stop)) return;  // level finished (converged or degenerate)
 
-  // current estimate: x = p + ((A p) + t), A = sR - I (single precision, rounded)
+  // current estimate: x = p + ((A p) + t), A = sR - I (single precision, rounded); the FP64 pose
+  // is rounded once per CTA (the FP64 rate is low), then read by every thread
+  if (threadIdx.x < 12) {
+    const int i = threadIdx.x >> 2, j = threadIdx.x & 3;
+    const double v = a.pose[4 * i + j];
+    s_pose[threadIdx.x] = (float)(j == 3 ? v : v - (i == j ? 1.0 : 0.0));
+  } else if (PHOTO && a.Trs_dev && threadIdx.x < 24) {
+    const int k = threadIdx.x - 12, i = k >> 2, j = k & 3;
+    s_pose[threadIdx.x] = __double2float_rn(a.Trs_dev[4 * i + j]);
+  }
+  __syncthreads();
   float Am[9], tv[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
 #pragma unroll
-    for (int j = 0; j < 3; ++j) Am[3 * i + j] = (float)(a.pose[4 * i + j] - (i == j ? 1.0 : 0.0));
-    tv[i] = (float)a.pose[4 * i + 3];
+    for (int j = 0; j < 3; ++j) Am[3 * i + j] = s_pose[4 * i + j];
+    tv[i] = s_pose[4 * i + 3];
   }
   if (PHOTO && a.Trs_dev) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
 #pragma unroll
-      for (int j = 0; j < 3; ++j) a.Rrs[3 * i + j] = __double2float_rn(a.Trs_dev[4 * i + j]);
-      a.trs[i] = __double2float_rn(a.Trs_dev[4 * i + 3]);
+      for (int j = 0; j < 3; ++j) a.Rrs[3 * i + j] = s_pose[12 + 4 * i + j];
+      a.trs[i] = s_pose[12 + 4 * i + 3];
     }
   }
   A acc;
@@ -595,9 +624,11 @@ __global__ void __launch_bounds__(ICP_THREADS) k_icp(IcpArgs a) {
   __syncthreads();
   if (!s_last) return;
 
-  // ---- last CTA: FP64 sum of the partials in a fixed order - PARTS consecutive ranges of
-  // CTAs, each summed in CTA order by its own thread, then the range sums in order (short
-  // dependent chains of FP64 additions) - then the solve by one warp
+  // ---- last CTA: sum of the partials in a fixed order - PARTS consecutive ranges of CTAs,
+  // each summed in CTA order by its own thread, then the range sums in order - then the solve
+  // by one warp. A range is summed in double-single arithmetic (FP32 value + FP32 sum of the
+  // exact rounding errors of the additions, Knuth's TwoSum: about 48 bits, far below the FP32
+  // partials' own error) because GB300's FP64 rate is low; the range sums are added in FP64.
   constexpr int PARTS = ICP_THREADS / A::N;
   __shared__ double s_psum[PARTS][A::N];
   {
@@ -605,17 +636,30 @@ __global__ void __launch_bounds__(ICP_THREADS) k_icp(IcpArgs a) {
     const int slot = threadIdx.x % A::N, part = threadIdx.x / A::N;
     if (part < PARTS) {
       const int b0 = part * chunk, b1 = min(G, b0 + chunk);
-      double s = 0.0;
+      float hi = 0.0f, lo = 0.0f;
       int b = b0;
       for (; b + 16 <= b1; b += 16) {
         float v[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) v[q] = __ldcg(a.partials + (b + q) * A::N + slot);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) s += (double)v[q];
+        for (int q = 0; q < 16; ++q) {
+          const float t = __fadd_rn(hi, v[q]);
+          const float bp = __fsub_rn(t, hi);
+          const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(v[q], bp));
+          hi = t;
+          lo = __fadd_rn(lo, e);
+        }
       }
-      for (; b < b1; ++b) s += (double)__ldcg(a.partials + b * A::N + slot);
-      s_psum[part][slot] = s;
+      for (; b < b1; ++b) {
+        const float x = __ldcg(a.partials + b * A::N + slot);
+        const float t = __fadd_rn(hi, x);
+        const float bp = __fsub_rn(t, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+        hi = t;
+        lo = __fadd_rn(lo, e);
+      }
+      s_psum[part][slot] = (double)hi + (double)lo;
     }
   }
   __syncthreads();
@@ -848,6 +892,6 @@ void launch_icp(const IcpLaunch& L, int sim3, bool photo, int grid, cudaStream_t
 #undef DTSDF_ICP
 }
 
-void launch_exp(int dim, const double* xi, double* T, cudaStream_t s) { k_exp<<<1, 1, 0, s>>>(dim, xi, T); }
+void launch_exp(int dim, const double* xi, double* T, cudaStream_t s) { k_exp<<<1, 32, 0, s>>>(dim, xi, T); }
 
 }  // namespace dtsdf

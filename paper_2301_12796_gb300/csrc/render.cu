@@ -107,27 +107,6 @@ __device__ __forceinline__ float tri(const float* v, float fx, float fy, float f
   return lerp_rn(lerp_rn(s00, s10, fy), lerp_rn(s01, s11, fy), fz);
 }
 
-// Trilinear sdf and weight of one direction at the sample whose base voxel has index `base`
-// in its padded brick; false unless all 8 corners have weight > 0.
-template <int STORE, bool COUNT>
-__device__ __forceinline__ bool interp(const MapView& m, size_t base, float fx, float fy, float fz, float& phi,
-                                       float& W, uint8_t* touched) {
-  float2 v[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = ld_geom<STORE, COUNT>(m, base + coff(q), touched);
-  bool ok = true;
-  float s[8], w[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    ok &= v[q].y > 0.0f;
-    s[q] = v[q].x;
-    w[q] = v[q].y;
-  }
-  phi = tri(s, fx, fy, fz);
-  W = tri(w, fx, fy, fz);
-  return ok;
-}
-
 // Eq. direction_weight as read; the clamped ranges (angle <= pi/2 - theta: 1, >= theta: 0) are
 // decided on the cosine (sin theta, cos theta) without the arc cosine.
 __device__ __forceinline__ float w_dir_r(float c, float theta, float cos_lo, float cos_hi) {
@@ -293,17 +272,43 @@ __device__ __forceinline__ int sign_fast(const MapView& m, Cell& c, const float 
   float mn = 2.f, mx = -2.f;
   bool any = false, facing = false;
   int np = 0;
+  // two directions per step: their 16 corner loads are in flight together
 #pragma unroll 1
-  for (uint32_t mm = c.cmask; mm; mm &= mm - 1) {
-    const int D = __ffs(mm) - 1;
-    float phiD, WD;
-    if (!interp<STORE, COUNT>(m, (size_t)c.slot[D * RT_N] * PVOX + lofs, fx, fy, fz, phiD, WD, touched)) continue;
-    any = true;
-    ++np;
-    mn = fminf(mn, phiD);
-    mx = fmaxf(mx, phiD);
-    const float vr = (D & 1) ? r[D >> 1] : -r[D >> 1];
-    facing |= vr > 0.0f;
+  for (uint32_t mm = c.cmask; mm;) {
+    const int D0 = __ffs(mm) - 1;
+    mm &= mm - 1;
+    const int D1 = mm ? __ffs(mm) - 1 : -1;
+    if (mm) mm &= mm - 1;
+    float2 v0[8], v1[8];
+    const size_t b0 = (size_t)c.slot[D0 * RT_N] * PVOX + lofs;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v0[q] = ld_geom<STORE, COUNT>(m, b0 + coff(q), touched);
+    if (D1 >= 0) {
+      const size_t b1 = (size_t)c.slot[D1 * RT_N] * PVOX + lofs;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v1[q] = ld_geom<STORE, COUNT>(m, b1 + coff(q), touched);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int D = k ? D1 : D0;
+      if (D < 0) break;
+      const float2* v = k ? v1 : v0;
+      bool ok = true;
+      float s[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        ok &= v[q].y > 0.0f;
+        s[q] = v[q].x;
+      }
+      if (!ok) continue;
+      const float phiD = tri(s, fx, fy, fz);
+      any = true;
+      ++np;
+      mn = fminf(mn, phiD);
+      mx = fmaxf(mx, phiD);
+      const float vr = (D & 1) ? r[D >> 1] : -r[D >> 1];
+      facing |= vr > 0.0f;
+    }
   }
   lo = mn;
   npres = np;
