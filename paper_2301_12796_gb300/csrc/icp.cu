@@ -16,7 +16,7 @@
 
 namespace dtsdf {
 
-constexpr int ICP_THREADS = 256;
+constexpr int ICP_THREADS = ICP_CTA_THREADS;
 
 // ------------------------------------------------------------- pyramid ----
 __global__ void k_extract_depth(const float4* __restrict__ P, int n, float* __restrict__ d) {

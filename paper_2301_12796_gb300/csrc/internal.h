@@ -144,6 +144,7 @@ void launch_frame_pyramid(const float4* P, const uint8_t* rgb, int levels, const
                           float* const* inten, cudaStream_t s);
 void launch_keyframe_pyramid(const uint8_t* rgb, int levels, const Intr* K, float* const* tmpI, float4* const* kf,
                              cudaStream_t s);
+constexpr int ICP_CTA_THREADS = 256;  // threads per CTA of one ICP iteration
 void launch_icp(const IcpLaunch& L, int sim3, bool photo, int grid, cudaStream_t s);
 void launch_exp(int dim, const double* xi, double* T, cudaStream_t s);
 
