@@ -45,7 +45,7 @@ FALLBACK_HBM_GBS = 6800.0
 # default workload (FP32 storage with colour, first timed render), from one ncu capture of
 # ``bench.py --steps 2 --warmup 3 --no-e2e --no-cpu`` (profiles/k_render_kinect640.md). It
 # belongs to the kernel sources it was taken with: reported only while their hash matches.
-RENDER_TRAFFIC = {"bytes": 272807168 + 11704064, "sources_sha1_16": "5ca77edb7dd32503",
+RENDER_TRAFFIC = {"bytes": 272414720 + 11687424, "sources_sha1_16": "b8d9a7b899f1164f",
                   "files": ("render.cu", "common.cuh", "internal.h")}
 
 
