@@ -69,8 +69,7 @@ __global__ void k_comb_policy(CombState* st, const double* Tdev, Pose64 Tv, cons
 
 template <int STORE, bool COLOR>
 __global__ void __launch_bounds__(256) k_combine(MapView m, const CombState* st, CombFrame f) {
-  __shared__ int s_src[ND];
-  __shared__ int s_col[ND][8];
+  __shared__ int s_src[ND][8];
   __shared__ float s_c[3];
   __shared__ float s_R[9];
   __shared__ uint32_t s_full, s_gen, s_from;
@@ -111,20 +110,20 @@ __global__ void __launch_bounds__(256) k_combine(MapView m, const CombState* st,
       for (int q = 0; q < 4; ++q) take &= (f.pl[q][0] * cx + f.pl[q][1] * cy + f.pl[q][2] * cz) >= -rad;
     }
     if (!take) continue;  // uniform over the CTA
-    if (threadIdx.x < ND) s_src[threadIdx.x] = ((mask >> threadIdx.x) & 1u) ? m.dir_slots[(size_t)d * 8 + threadIdx.x] : -1;
-    if (COLOR && threadIdx.x < 8 * ND) {
-      // colour bricks of the blocks {0, 1}^3 from this one (colour bricks are not padded)
+    if (threadIdx.x < 8 * ND) {
+      // bricks of the blocks {0, 1}^3 from this one: voxel (x, y, z) of [0, 8]^3 belongs to block
+      // (x >> 3, y >> 3, z >> 3) and is combined from that block's directions (a voxel's data is
+      // its own block's), not only from the directions this block holds
       const int D = threadIdx.x >> 3, j = threadIdx.x & 7;
       int sl = -1;
-      if ((mask >> D) & 1u) {
-        if (j == 0) {
-          sl = m.dir_slots[(size_t)d * 8 + D];
-        } else {
-          const int dd = hash_find(m, bx + (j & 1), by + ((j >> 1) & 1), bz + (j >> 2));
-          sl = dd >= 0 ? m.dir_slots[(size_t)dd * 8 + D] : -1;
-        }
+      if (j == 0) {
+        if ((mask >> D) & 1u) sl = m.dir_slots[(size_t)d * 8 + D];
+      } else {
+        const int dd = hash_find(m, bx + (j & 1), by + ((j >> 1) & 1), bz + (j >> 2));
+        if (dd >= 0 && ((uint32_t)m.dir_slots[(size_t)dd * 8 + SLOT_MASK] >> D) & 1u)
+          sl = m.dir_slots[(size_t)dd * 8 + D];
       }
-      s_col[D][j] = sl;
+      s_src[D][j] = sl;
     }
     __syncthreads();
     const float inv2h = 0.5f / h;
@@ -140,10 +139,11 @@ __global__ void __launch_bounds__(256) k_combine(MapView m, const CombState* st,
       float ws = 0.f, acc = 0.f, wf = 0.f, af = 0.f, cw = 0.f, cr = 0.f, cg = 0.f, cb = 0.f;
       bool any = false;
 #pragma unroll 1
+      const int own = (x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2);
       for (int D = 0; D < ND; ++D) {
-        const int sl = s_src[D];
+        const int sl = s_src[D][own];
         if (sl < 0) continue;
-        const size_t base = (size_t)sl * PVOX + pad_index(x, y, z);
+        const size_t base = (size_t)sl * PVOX + pad_index(x & 7, y & 7, z & 7);
         const float2 v0 = src_geom<STORE>(m, base);
         if (!(v0.y > 0.0f)) continue;
         any = true;
@@ -170,10 +170,8 @@ __global__ void __launch_bounds__(256) k_combine(MapView m, const CombState* st,
         ws += wc;
         acc += wc * v0.x;
         if (COLOR) {
-          const int j = (x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2);
-          const int cs = s_col[D][j];
-          if (cs >= 0) {
-            const size_t ci = (size_t)cs * BVOX + ((z & 7) * 8 + (y & 7)) * 8 + (x & 7);
+          {
+            const size_t ci = (size_t)sl * BVOX + ((z & 7) * 8 + (y & 7)) * 8 + (x & 7);
             const float4 c = STORE == DTSDF_STORE_FP16 ? unpack_col8(__ldg(m.col8 + ci)) : __ldg(m.col + ci);
             if (c.w > 0.0f) {
               cw += wc;
