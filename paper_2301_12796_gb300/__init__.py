@@ -122,7 +122,7 @@ class ServerStats(ctypes.Structure):
                                        "peak_inflight", "bytes_in_use", "peak_bytes")]
 
 
-# exported symbols and their signatures (same order as include/dtsdf.h)
+# exported symbols and their signatures (every function include/dtsdf.h declares)
 P = c_void_p
 SIGNATURES = {
     "dtsdf_create": ([ctypes.POINTER(Params), P, ctypes.POINTER(P)], c_int32),
