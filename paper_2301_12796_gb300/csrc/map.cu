@@ -994,13 +994,15 @@ void launch_fuse(const MapView& m, const Intr& K, const Pose32& T, const double*
   set(2, 0.f, K.fy, K.cy + 0.5f);
   set(3, 0.f, -K.fy, (float)K.H - 0.5f - K.cy);
   const bool sparse = m.dense_dim <= 0;
+  // fusion: CTAs of 128 threads (4 voxels each), so that twice as many bricks are in flight per
+  // SM as with 256 (each brick's update is a chain of dependent gathers and barriers)
   if (m.storage == DTSDF_STORE_FP16) {
     if (sparse) k_apron_pull<DTSDF_STORE_FP16><<<num_sms * 4, 256, 0, s>>>(m, 0);
-    k_fuse<DTSDF_STORE_FP16><<<num_sms * 8, 256, 0, s>>>(m, f);
+    k_fuse<DTSDF_STORE_FP16><<<num_sms * 16, 128, 0, s>>>(m, f);
     k_bounds_exact<DTSDF_STORE_FP16><<<num_sms * 8, 256, 0, s>>>(m);
   } else {
     if (sparse) k_apron_pull<DTSDF_STORE_FP32><<<num_sms * 4, 256, 0, s>>>(m, 0);
-    k_fuse<DTSDF_STORE_FP32><<<num_sms * 8, 256, 0, s>>>(m, f);
+    k_fuse<DTSDF_STORE_FP32><<<num_sms * 16, 128, 0, s>>>(m, f);
     k_bounds_exact<DTSDF_STORE_FP32><<<num_sms * 8, 256, 0, s>>>(m);
   }
 }
