@@ -405,7 +405,7 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
     gt = tr.gt.cpu().numpy()
     fr = [1 + (args.warmup + k) % (tr.n - 1) for k in range(args.steps)]
     terr = float(np.median([np.linalg.norm(est[f][:3, 3] - gt[f][:3, 3]) for f in fr]))
-    # post-fusion error (Sec. 9): the map re-rendered at each tracked frame's estimated pose
+    # post-fusion error (Sec. 8.2): the map re-rendered at each tracked frame's estimated pose
     # against that frame's input depth, pixel-wise MAE over pixels where both exist (untimed)
     mae = torch.zeros(2, dtype=torch.float64, device=dev)
     acc = np.zeros(2)

@@ -528,7 +528,7 @@ DTSDF_API dtsdf_status dtsdf_icp_set_filters(dtsdf_icp icp, const dtsdf_filter_o
 DTSDF_API dtsdf_status dtsdf_preprocess(const dtsdf_frame* frame, float z_min, float z_max, float delta_sup,
                                         const dtsdf_filter_opts* f, float* points, float* normals, void* stream);
 
-/* Post-fusion error (Sec. 9): sum of |rendered - measured| over the n pixels where both depths
+/* Post-fusion error (Sec. 8.2): sum of |rendered - measured| over the n pixels where both depths
  * are positive, and that pixel count, as out_dev[0], out_dev[1] (device, 2 doubles; the MAE is
  * their ratio). rendered, measured: device float32 (may be NULL when n = 0). FP64 sums in a
  * fixed order (deterministic).

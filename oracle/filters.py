@@ -10,7 +10,7 @@ Passages followed:
   * Sec. 7: normals are the cross product of the central differences of the back-projected
     neighbours in x and y, turned toward the camera, present where the pixel and its four
     neighbours are.
-  * Sec. 9: the post-fusion error of a frame is the mean absolute difference between the depth
+  * Sec. 8.2: the post-fusion error of a frame is the mean absolute difference between the depth
     rendered at its estimated pose and its input depth, over the pixels where both exist.
 """
 from __future__ import annotations
@@ -92,7 +92,7 @@ def bilateral_normals(n: np.ndarray, has: np.ndarray, radius: int, sigma_d: floa
 
 
 def depth_mae(rendered: np.ndarray, measured: np.ndarray):
-    """Sec. 9 post-fusion error of one frame: (sum |rendered - measured|, count) over the pixels
+    """Sec. 8.2 post-fusion error of one frame: (sum |rendered - measured|, count) over the pixels
     where both depths are positive."""
     a = np.asarray(rendered, np.float64)
     b = np.asarray(measured, np.float64)

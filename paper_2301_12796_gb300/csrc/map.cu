@@ -160,7 +160,7 @@ __global__ void k_bilateral_normals(const float4* __restrict__ Nin, Intr K, int 
   Nout[i] = out;
 }
 
-// Post-fusion error (Sec. 9): per CTA, the sum of |rendered - measured| and the count over the
+// Post-fusion error (Sec. 8.2): per CTA, the sum of |rendered - measured| and the count over the
 // pixels where both depths are positive, in FP64; the CTA partials are summed in a fixed order by
 // k_mae_final, so the result does not depend on scheduling.
 constexpr int MAE_CTAS = 256;

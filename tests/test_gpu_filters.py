@@ -76,7 +76,7 @@ def test_bilateral_filters_match_oracle(which):
 
 
 def test_filters_in_fusion_and_icp():
-    """A map and an ICP context with both filters: the post-fusion error (Sec. 9) of the map
+    """A map and an ICP context with both filters: the post-fusion error (Sec. 8.2) of the map
     fused with the filtered preprocessing stays at the level of the unfiltered one (most pixels
     within 3 mm; the mean is dominated by silhouette pixels that hit another surface) and equals
     the mean computed on the host from the same images; ICP converges on the filtered pyramid."""
