@@ -121,6 +121,23 @@ def test_invalid_parameters_rejected_on_host(lib):
     assert lib.dtsdf_server_create(maps, 1, ctypes.byref(sp), ctypes.byref(h)) == dt.ERR_INVALID_ARG
     assert lib.dtsdf_server_create(None, 1, ctypes.byref(dt.server_params()), ctypes.byref(h)) == dt.ERR_INVALID_ARG
     assert lib.dtsdf_server_submit(None, None, None) == dt.ERR_INVALID_ARG
+    # the later entry points: argument checks before any CUDA call
+    assert lib.dtsdf_recycle(None, 0.75, None, None) == dt.ERR_INVALID_ARG
+    assert lib.dtsdf_render_freespace(None, None, None, None, None) == dt.ERR_INVALID_ARG
+    assert lib.dtsdf_set_filters(None, None) == dt.ERR_INVALID_ARG
+    assert lib.dtsdf_icp_set_filters(None, None) == dt.ERR_INVALID_ARG
+    assert lib.dtsdf_preprocess(None, 0.1, 6.0, 0.02, None, None, None, None) == dt.ERR_INVALID_ARG
+    fr = dt.Frame(1, None, dt.intrinsics(__import__("scenes").Intrinsics(8, 8, 6.0, 6.0, 3.5, 3.5)))
+    bad = dt.filter_opts(depth_radius=9)
+    assert lib.dtsdf_preprocess(ctypes.byref(fr), 0.1, 6.0, 0.02, ctypes.byref(bad), 1, 1, None) == dt.ERR_INVALID_ARG
+    bad = dt.filter_opts(normal_sigma_r=0.0)
+    assert lib.dtsdf_preprocess(ctypes.byref(fr), 0.1, 6.0, 0.02, ctypes.byref(bad), 1, 1, None) == dt.ERR_INVALID_ARG
+    assert lib.dtsdf_depth_mae(None, None, 4, None, None) == dt.ERR_INVALID_ARG
+    assert lib.dtsdf_depth_scale(None, None, 4, 1.0, None) == dt.ERR_INVALID_ARG
+    assert lib.dtsdf_depth_scale(1, 1, 4, -1.0, None) == dt.ERR_INVALID_ARG
+    assert lib.dtsdf_depth_scale(1, 1, 4, float("inf"), None) == dt.ERR_INVALID_ARG
+    assert lib.dtsdf_scale_anchor(None, None, 3, 0, 0.0, None) == dt.ERR_INVALID_ARG
+    assert lib.dtsdf_scale_anchor(None, None, 0, 0, 0.0, None) == dt.OK
 
 
 def test_product_path_has_no_cpu_fallback(tmp_path, monkeypatch):
