@@ -324,6 +324,22 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (model name, or the Arm implementer / part), else the
+    machine type."""
+    import platform
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+        for key in ("model name", "Model", "CPU part"):
+            for line in info:
+                if line.split(":")[0].strip() == key:
+                    val = line.split(":", 1)[1].strip()
+                    return f"{platform.machine()} {key}: {val}"
+    except OSError:
+        pass
+    return platform.machine()
+
+
 # ---------------------------------------------------------------- reference --
 def run_reference(args, rank, world):
     """The oracle as it stands, on the host cores, one bounded sample of a tracking frame per step."""
@@ -341,7 +357,7 @@ def run_reference(args, rank, world):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD},
-           "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cpu_cores(), "kind": "oracle",
+           "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cpu_cores(), "cpu": cpu_model(), "kind": "oracle",
                             "sample": ob.describe(parts)},
            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -504,7 +520,7 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu and not args.profile:
         ob = OracleBench(s, frames)
         v, parts = ob.step(stride=2)
-        cpu = {"value": v, "unit": "frames/s", "cores": cpu_cores(), "kind": "oracle", "sample": ob.describe(parts)}
+        cpu = {"value": v, "unit": "frames/s", "cores": cpu_cores(), "cpu": cpu_model(), "kind": "oracle", "sample": ob.describe(parts)}
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -725,7 +741,7 @@ def run_multi_sensor(args, dt, torch, tdist, dev, rank, world, local):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and not args.profile:
         v, sample_desc = ms_cpu_baseline(ms, n_frames)
-        cpu = {"value": v, "unit": "registrations/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample_desc}
+        cpu = {"value": v, "unit": "registrations/s", "cores": cpu_cores(), "cpu": cpu_model(), "kind": "oracle", "sample": sample_desc}
     if rank == 0:
         out = {"metric": "multi-sensor Sim(3) registrations/s (1280x720 vs 640x480 map)", "value": value,
                "unit": "registrations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -936,7 +952,7 @@ def run_serve(args, dt, torch, tdist, dev, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu and not args.profile:
         q640 = next(q for q in reqs if q["K"].width == 640)
         v, desc = serve_cpu_baseline(rooms, q640)
-        cpu = {"value": v, "unit": "requests/s", "cores": cpu_cores(), "kind": "oracle", "sample": desc}
+        cpu = {"value": v, "unit": "requests/s", "cores": cpu_cores(), "cpu": cpu_model(), "kind": "oracle", "sample": desc}
     h2d = int(np.mean([q["depth"].nbytes for q in reqs]))
     if rank == 0:
         out = {"metric": "served render+ICP requests/s, p50/p99 latency (continuous batching, mixed sizes)",
