@@ -336,3 +336,20 @@ def test_library_scale_anchor_matches_oracle():
     for anchor, val in ((0, 0.0), (3, 0.02)):
         assert np.array_equal(dt.scale_anchor(est, sensor, anchor, val), icp.scale_anchor(est, sensor, anchor, val))
     assert dt.scale_anchor(np.zeros(0), np.zeros(0, np.int32)).shape == (0,)
+
+
+def test_lm_recovers_depth_scale_in_sim3():
+    """Levenberg-Marquardt in Sim(3) reaches the same exact optimum as Gauss-Newton: the inverse
+    of a 1.0625 depth scale and the true motion."""
+    scale = 1.0625
+    s, K, T_ref, T_cur, rd, rn, cur = _ref_and_current(2, 0.02, seed=11, depth_scale=scale)
+    levels = icp.pyramid(cur.depth, K, 3)
+    st = icp.Settings(sim3=True, eps=(0.02, 0.2, 0.3), iters=(40, 20, 20), lm=True)
+    dT, log = icp.track(levels, rd, rn, K, np.eye(4), st)
+    true = np.linalg.inv(T_ref) @ T_cur
+    s_est = np.cbrt(np.linalg.det(dT[:3, :3]))
+    assert abs(s_est * scale - 1.0) < 1e-6
+    R = dT[:3, :3] / s_est
+    E = true[:3, :3].T @ R
+    assert np.arccos(np.clip((np.trace(E) - 1) / 2, -1, 1)) < 1e-6
+    assert np.linalg.norm(dT[:3, 3] - true[:3, 3]) < 1e-6
