@@ -13,9 +13,12 @@ imports it; the two meet only through the seeded inputs of ``scenes``.
   frame-to-keyframe rows, normal equations, Cholesky solve and the exponential
   map (Sec. 5, 5.2, 5.3, 6).
 
-Floating-point comparisons that decide an integer or a set are taken in single
-precision with the kernel's operation order (which pixel, which block, inlier or
-not); values are computed in double.
+Every value and every decision is computed in double precision. A decision whose
+quantity lies within a stated margin of its threshold (the difference a single-
+precision evaluation of the same quantity can make) is recorded as a tie: per pixel
+(preprocess), per allocated (block, D) key (alloc_tie), per voxel (brick_ties) and per
+ICP row (icp.Rows.tie). Comparisons with another implementation accept a difference
+only on the oracle's ties, and report how many there were.
 
 Parity status per function is listed in ``PARITY`` below. Every entry is pinned by
 a test under ``tests/`` against closed forms, brute force, library routines or
@@ -38,7 +41,8 @@ _lib = None
 PARITY = {
     "w_dir": "pinned: closed-form values, partition of unity (tests/test_oracle_weights.py)",
     "preprocess": "pinned: exact plane normals, filter counts by brute force (tests/test_oracle_fusion.py)",
-    "segment_blocks": "pinned: brute-force slab test (tests/test_oracle_alloc.py)",
+    "segment_blocks": "pinned: dense sampling of the segment and an independent half-open slab test "
+                      "(tests/test_oracle_alloc.py)",
     "integrate": "pinned: per-voxel closed form on planes, running-average identity (tests/test_oracle_fusion.py)",
     "render": "pinned: analytic plane, sphere bound, thin-sheet lemma (tests/test_oracle_render.py)",
     "combine": "pinned: one direction's values kept, identical directions kept, hand-evaluated weights, analytic "
@@ -79,9 +83,13 @@ def _load():
             L.om_bricks.argtypes = [P, P]
             L.om_brick_data.argtypes = [P, I, I, I, I, P]
             L.om_brick_data.restype = I
-            L.om_preprocess.argtypes = [P, I, I, F, F, F, F, F, F, F, P, P, P, P, P, P, P]
+            L.om_brick_ties.argtypes = [P, I, I, I, I, P]
+            L.om_brick_ties.restype = I
+            L.om_alloc_tie.argtypes = [P, I, I, I, I]
+            L.om_alloc_tie.restype = I
+            L.om_preprocess.argtypes = [P, I, I, F, F, F, F, F, F, F, P, P, P, P, P, P]
             L.om_preprocess.restype = I
-            L.om_segment_blocks.argtypes = [P, P, F, P, P, I]
+            L.om_segment_blocks.argtypes = [P, P, D, P, P, P, I]
             L.om_segment_blocks.restype = I
             L.om_w_dir.argtypes = [D, D]
             L.om_w_dir.restype = D
@@ -117,29 +125,32 @@ def w_dir(cos_angle: float, theta: float) -> float:
 
 
 def preprocess(depth: np.ndarray, K, z_min: float, z_max: float, delta_sup: float) -> dict:
-    """Depth outlier filter and cross-product normals (Sec. 7)."""
+    """Depth outlier filter and cross-product normals (Sec. 7), in double precision.
+    ok / nok: kept pixel / pixel with a normal; tie: the normal's orientation toward the
+    camera is within the tie margin; z: kept input depth; P, n: camera point and normal."""
     L = _load()
     d = np.ascontiguousarray(depth, np.float32)
     H, W = d.shape
-    out = dict(ok=np.zeros((H, W), np.uint8), nok=np.zeros((H, W), np.uint8), z=np.zeros((H, W), np.float32),
-               Pf=np.zeros((H, W, 3), np.float32), nf=np.zeros((H, W, 3), np.float32),
-               Pd=np.zeros((H, W, 3), np.float64), nd=np.zeros((H, W, 3), np.float64))
+    out = dict(ok=np.zeros((H, W), np.uint8), nok=np.zeros((H, W), np.uint8), tie=np.zeros((H, W), np.uint8),
+               z=np.zeros((H, W), np.float32), P=np.zeros((H, W, 3), np.float64),
+               n=np.zeros((H, W, 3), np.float64))
     rc = L.om_preprocess(_p(d), W, H, K.fx, K.fy, K.cx, K.cy, z_min, z_max, delta_sup,
-                         _p(out["ok"]), _p(out["nok"]), _p(out["z"]), _p(out["Pf"]), _p(out["nf"]),
-                         _p(out["Pd"]), _p(out["nd"]))
+                         _p(out["ok"]), _p(out["nok"]), _p(out["tie"]), _p(out["z"]), _p(out["P"]), _p(out["n"]))
     assert rc == 0
     return out
 
 
-def segment_blocks(a, b, block_size: float, origin=(0.0, 0.0, 0.0)) -> np.ndarray:
-    """Blocks crossed by segment a-b (single-precision 3D DDA, Sec. 7 allocation)."""
+def segment_blocks(a, b, block_size: float, origin=(0.0, 0.0, 0.0)):
+    """Blocks whose closed cube segment a-b meets (exact slab test, Sec. 7 allocation):
+    (cells n x 3, met n bool, tie n bool); a cell is listed when it is met or a tie."""
     L = _load()
-    A = np.ascontiguousarray(a, np.float32)
-    B = np.ascontiguousarray(b, np.float32)
-    O = np.ascontiguousarray(origin, np.float32)
-    cells = np.zeros((64, 3), np.int32)
-    n = L.om_segment_blocks(_p(A), _p(B), block_size, _p(O), _p(cells), 64)
-    return cells[: min(n, 64)].copy()
+    A = np.ascontiguousarray(a, np.float64)
+    B = np.ascontiguousarray(b, np.float64)
+    O = np.ascontiguousarray(origin, np.float64)
+    cells = np.zeros((256, 3), np.int32)
+    flags = np.zeros(256, np.uint8)
+    n = min(L.om_segment_blocks(_p(A), _p(B), float(block_size), _p(O), _p(cells), _p(flags), 256), 256)
+    return cells[:n].copy(), (flags[:n] & 1) > 0, (flags[:n] & 2) > 0
 
 
 class Params:
@@ -209,6 +220,16 @@ class OracleMap:
         out = np.zeros((512, 6), np.float64)
         rc = self._L.om_brick_data(self._h, int(bx), int(by), int(bz), int(D), _p(out))
         return None if rc != 0 else out
+
+    def brick_ties(self, bx, by, bz, D) -> np.ndarray | None:
+        """512 tie flags (bit 0: sdf and weight, bit 1: colour) of a brick's voxels."""
+        out = np.zeros(512, np.uint8)
+        rc = self._L.om_brick_ties(self._h, int(bx), int(by), int(bz), int(D), _p(out))
+        return None if rc != 0 else out
+
+    def alloc_tie(self, bx, by, bz, D) -> int:
+        """First frame whose allocation of (bx, by, bz, D) was a tie, -1 if none was."""
+        return int(self._L.om_alloc_tie(self._h, int(bx), int(by), int(bz), int(D)))
 
     def set_brick(self, bx, by, bz, D, vox):
         """Write a brick (512 x 6: sdf, w, r, g, b, wc), allocating it if needed (tests)."""

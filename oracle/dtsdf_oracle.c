@@ -3,13 +3,26 @@
  *
  * This file is a plain, slow, obviously correct restatement of what the paper
  * computes, used only by the tests, the smoke check and the CPU baseline of the
- * benchmark. It shares no code with the CUDA path. Values are computed in
- * double precision. Where a floating-point comparison decides an integer or a
- * set (which pixel a voxel projects to, which blocks a segment crosses, whether
- * a voxel lies in the truncation band, whether a pixel survives the outlier
- * filter), the decision is taken in single precision with a fixed operation
- * order and no contraction, because that is the precision of the kernel being
- * checked; the values that follow a decision are then computed in double.
+ * benchmark. It shares no code with the CUDA path. Every value and every decision
+ * (which pixel a voxel projects to, which blocks a segment crosses, whether a voxel
+ * lies in the truncation band, whether a normal belongs to a direction) is taken in
+ * double precision.
+ *
+ * A decision whose FP64 quantity lies within a stated margin of its threshold is a
+ * "tie": an implementation that computes the same quantity in single precision may
+ * take it the other way. The oracle records ties (per pixel, per allocated
+ * (block, D) key and per voxel) so that a comparison can check that every element on
+ * which two implementations disagree is a tie of the oracle. The margins bound the
+ * difference between an FP32 and an FP64 evaluation of the quantity:
+ *   TIE_N  2e-4    cosines between a pixel normal and an axis or the view ray: FP32
+ *                  normals are cross products of back-projected neighbours two pixels
+ *                  apart; at 3 m and f = 525 the points carry ~1e-6 m of rounding over
+ *                  a 1.1e-2 m baseline (~1e-4 rad)
+ *   TIE_X  1e-5 m  camera- and world-frame coordinates and distances (FP32 keeps ~1e-6 m
+ *                  at 8 m), plus TIE_N times the lever arm where a normal multiplies a
+ *                  distance
+ *   TIE_PX 2e-3    pixel coordinates of a projection (about 10x the FP32 rounding of
+ *                  f x / z at f = 910)
  *
  * Paper references (Splietker & Behnke, "Rendering the Directional TSDF for
  * Tracking and Multi-Sensor Registration with Point-To-Plane Scale ICP"):
@@ -30,18 +43,21 @@
  *   SDF sign          d = <x - p, n> / tau with n facing the camera (d > 0 in front)
  *   carving           d_raw > tau and no valid depth within 2 px differs by more
  *                     than tau: sdf <- running average with value 1, weight w_carve
+ *   allocation        every (block, D) whose closed 8h cube the segment
+ *                     [p - tau r, p + tau r] meets, for every D the normal belongs to
  *   presence          a direction counts at x only if all 8 trilinear corners
  *                     exist and have weight > 0; its gradient (central differences
  *                     of the trilinear field at +-h) only if the 6 offset samples
  *                     are present
  *   render march      samples at t = k * h/2 along the unit ray; the first pair of
- *                     consecutive defined samples with Phi > 0 >= Phi is the hit,
- *                     refined by one regular 4-step scan for the first sign change
- *                     and linear interpolation; the normal and colour are taken at
- *                     the first grid sample behind the crossing (else the sample in
- *                     front of it, else the root)
+ *                     consecutive defined samples with Phi > 0 >= Phi brackets the
+ *                     hit; the hit is the root of the continuous Phi(t) in that
+ *                     bracket, found by bisection to 1e-10 m (an undefined midpoint
+ *                     counts as free space); normal and colour are evaluated at the
+ *                     root; a miss if the combination weights vanish there
  *
- * Build: gcc -O2 -fPIC -shared -fopenmp -ffp-contract=off (see oracle/__init__.py).
+ * Build: gcc -O2 -fPIC -shared -fopenmp -ffp-contract=off (see oracle/__init__.py; no contraction,
+ * so that x86 and Arm builds give the same bits).
  */
 #include <math.h>
 #include <stdint.h>
@@ -51,8 +67,11 @@
 #define ND 6
 #define BLK 8
 #define BVOX 512
-/* smallest weight of an admitted update (keeps "weight > 0" a property of the decision) */
-#define W_FLOOR 1e-12
+#define TIE_N 2e-4
+#define TIE_X 1e-5
+#define TIE_PX 2e-3
+/* bisection of the crossing bracket ends when it is narrower than this (metres along the ray) */
+#define ROOT_TOL 1e-10
 
 /* Direction axis vectors v^D: X+, X-, Y+, Y-, Z+, Z- (Sec. 3). */
 static const double VDIR[ND][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
@@ -62,9 +81,8 @@ typedef struct {
 } ovox;
 
 typedef struct {
-  /* parameters: nominal single-precision values, widened for the FP64 path */
-  float hf, tauf, thetaf, wmaxf, wcarvef, zminf, zmaxf, dsupf, costhf, originf[3];
-  double h, tau, theta, wmax, wcarve, zmin, zmax, dsup, origin[3];
+  /* parameters: the nominal single-precision values the library takes, widened to double */
+  double h, tau, theta, wmax, wcarve, zmin, zmax, dsup, costh, origin[3];
   int carve_r, dense_dim, color;
   /* hash: (bx, by, bz, D) -> brick index, open addressing, linear probing */
   uint64_t* keys;
@@ -72,10 +90,15 @@ typedef struct {
   size_t cap, count;
   /* bricks */
   ovox* vox;
+  uint8_t* tie;   /* per voxel: 1 once a decision about its update was a tie */
   int32_t* coord; /* 4 per brick: bx, by, bz, D */
   int32_t* first_frame;
   size_t nbricks, brick_cap;
   int frames;
+  /* (block, D) keys whose allocation was a tie in some frame, with the first such frame */
+  uint64_t* tkeys;
+  int32_t* tvals;
+  size_t tcap, tcount;
   /* view-dependent combined TSDF (om_combine): one entry per allocated block */
   uint64_t* ckeys;   /* block key -> combined block index, open addressing */
   int32_t* cvals;
@@ -136,6 +159,53 @@ static int hash_grow(omap* m) {
   return 0;
 }
 
+void om_free(omap* m);
+
+/* Record a tie of the allocation of (bx, by, bz, D) in frame `frame` (keeps the first frame). */
+static int tie_key_put(omap* m, int bx, int by, int bz, int D, int frame) {
+  if ((m->tcount + 1) * 2 > m->tcap) {
+    size_t oc = m->tcap;
+    uint64_t* ok = m->tkeys;
+    int32_t* ov = m->tvals;
+    m->tcap = oc * 2;
+    m->tkeys = (uint64_t*)malloc(m->tcap * sizeof(uint64_t));
+    m->tvals = (int32_t*)malloc(m->tcap * sizeof(int32_t));
+    if (!m->tkeys || !m->tvals) return -1;
+    memset(m->tkeys, 0xFF, m->tcap * sizeof(uint64_t));
+    m->tcount = 0;
+    for (size_t i = 0; i < oc; ++i)
+      if (ok[i] != EMPTY_KEY) {
+        size_t j = mix64(ok[i]) & (m->tcap - 1);
+        while (m->tkeys[j] != EMPTY_KEY) j = (j + 1) & (m->tcap - 1);
+        m->tkeys[j] = ok[i];
+        m->tvals[j] = ov[i];
+        m->tcount++;
+      }
+    free(ok);
+    free(ov);
+  }
+  const uint64_t k = pack_key(bx, by, bz, D);
+  size_t i = mix64(k) & (m->tcap - 1);
+  while (m->tkeys[i] != EMPTY_KEY && m->tkeys[i] != k) i = (i + 1) & (m->tcap - 1);
+  if (m->tkeys[i] == EMPTY_KEY) {
+    m->tkeys[i] = k;
+    m->tvals[i] = frame;
+    m->tcount++;
+  }
+  return 0;
+}
+
+/* First frame in which the allocation of (bx, by, bz, D) was a tie, -1 if never. */
+static int32_t tie_key_find(const omap* m, int bx, int by, int bz, int D) {
+  const uint64_t k = pack_key(bx, by, bz, D);
+  size_t i = mix64(k) & (m->tcap - 1);
+  for (;;) {
+    if (m->tkeys[i] == k) return m->tvals[i];
+    if (m->tkeys[i] == EMPTY_KEY) return -1;
+    i = (i + 1) & (m->tcap - 1);
+  }
+}
+
 /* Allocate brick (bx, by, bz, D) if absent. Initial voxel: sdf 1, weights 0, colour 0. */
 static int32_t brick_alloc(omap* m, int bx, int by, int bz, int D, int frame) {
   int32_t b = hash_find(m, bx, by, bz, D);
@@ -143,10 +213,13 @@ static int32_t brick_alloc(omap* m, int bx, int by, int bz, int D, int frame) {
   if (m->nbricks == m->brick_cap) {
     size_t nc = m->brick_cap ? m->brick_cap * 2 : 1024;
     ovox* nv = (ovox*)realloc(m->vox, nc * BVOX * sizeof(ovox));
+    if (nv) m->vox = nv;
+    uint8_t* nt = (uint8_t*)realloc(m->tie, nc * BVOX);
+    if (nt) m->tie = nt;
     int32_t* ncd = (int32_t*)realloc(m->coord, nc * 4 * sizeof(int32_t));
+    if (ncd) m->coord = ncd;
     int32_t* nff = (int32_t*)realloc(m->first_frame, nc * sizeof(int32_t));
-    if (!nv || !ncd || !nff) return -1;
-    m->vox = nv;
+    if (!nv || !nt || !ncd || !nff) return -1;
     m->coord = ncd;
     m->first_frame = nff;
     m->brick_cap = nc;
@@ -158,6 +231,7 @@ static int32_t brick_alloc(omap* m, int bx, int by, int bz, int D, int frame) {
     v[i].sdf = 1.0;
     v[i].w = v[i].r = v[i].g = v[i].b = v[i].wc = 0.0;
   }
+  memset(m->tie + (size_t)b * BVOX, 0, BVOX);
   m->coord[4 * b] = bx;
   m->coord[4 * b + 1] = by;
   m->coord[4 * b + 2] = bz;
@@ -171,15 +245,6 @@ omap* om_create(float voxel_size, float truncation, float theta, float w_max, fl
                 float z_max, float delta_sup, int carve_radius, int dense_dim, const float* origin, int color) {
   omap* m = (omap*)calloc(1, sizeof(omap));
   if (!m) return NULL;
-  m->hf = voxel_size;
-  m->tauf = truncation;
-  m->thetaf = theta;
-  m->wmaxf = w_max;
-  m->wcarvef = w_carve;
-  m->zminf = z_min;
-  m->zmaxf = z_max;
-  m->dsupf = delta_sup;
-  m->costhf = (float)cos((double)theta);
   m->h = voxel_size;
   m->tau = truncation;
   m->theta = theta;
@@ -188,17 +253,23 @@ omap* om_create(float voxel_size, float truncation, float theta, float w_max, fl
   m->zmin = z_min;
   m->zmax = z_max;
   m->dsup = delta_sup;
+  m->costh = cos((double)theta);
   m->carve_r = carve_radius;
   m->dense_dim = dense_dim;
   m->color = color;
-  for (int a = 0; a < 3; ++a) {
-    m->originf[a] = origin ? origin[a] : 0.0f;
-    m->origin[a] = m->originf[a];
-  }
+  for (int a = 0; a < 3; ++a) m->origin[a] = origin ? (double)origin[a] : 0.0;
   m->cap = 1 << 12;
   m->keys = (uint64_t*)malloc(m->cap * sizeof(uint64_t));
   m->vals = (int32_t*)malloc(m->cap * sizeof(int32_t));
+  m->tcap = 1 << 10;
+  m->tkeys = (uint64_t*)malloc(m->tcap * sizeof(uint64_t));
+  m->tvals = (int32_t*)malloc(m->tcap * sizeof(int32_t));
+  if (!m->keys || !m->vals || !m->tkeys || !m->tvals) {
+    om_free(m);
+    return NULL;
+  }
   memset(m->keys, 0xFF, m->cap * sizeof(uint64_t));
+  memset(m->tkeys, 0xFF, m->tcap * sizeof(uint64_t));
   if (dense_dim > 0) {
     /* dense grid: every (block, D) of the dense_dim^3 voxel cube exists from the start */
     int nb = dense_dim / BLK;
@@ -206,7 +277,10 @@ omap* om_create(float voxel_size, float truncation, float theta, float w_max, fl
       for (int z = 0; z < nb; ++z)
         for (int y = 0; y < nb; ++y)
           for (int x = 0; x < nb; ++x)
-            if (brick_alloc(m, x, y, z, D, 0) < 0) return NULL;
+            if (brick_alloc(m, x, y, z, D, 0) < 0) {
+              om_free(m);
+              return NULL;
+            }
   }
   return m;
 }
@@ -216,8 +290,11 @@ void om_free(omap* m) {
   free(m->keys);
   free(m->vals);
   free(m->vox);
+  free(m->tie);
   free(m->coord);
   free(m->first_frame);
+  free(m->tkeys);
+  free(m->tvals);
   free(m->ckeys);
   free(m->cvals);
   free(m->comb);
@@ -251,6 +328,17 @@ int om_brick_data(const omap* m, int bx, int by, int bz, int D, double* out) {
   return 0;
 }
 
+/* Tie flags of one brick's 512 voxels (bit 0: sdf and weight, bit 1: colour). Returns -1 if absent. */
+int om_brick_ties(const omap* m, int bx, int by, int bz, int D, uint8_t* out) {
+  int32_t b = hash_find(m, bx, by, bz, D);
+  if (b < 0) return -1;
+  memcpy(out, m->tie + (size_t)b * BVOX, BVOX);
+  return 0;
+}
+
+/* First frame in which the allocation of (bx, by, bz, D) was a tie, -1 if it never was. */
+int om_alloc_tie(const omap* m, int bx, int by, int bz, int D) { return tie_key_find(m, bx, by, bz, D); }
+
 /* ===================================================== preprocessing (A0) == */
 /*
  * Depth outlier filter (Sec. 7): a pixel with depth in [z_min, z_max] is kept only
@@ -259,33 +347,35 @@ int om_brick_data(const omap* m, int bx, int by, int bz, int D, double* out) {
  * back-projected neighbours in x and y (Sec. 7), oriented toward the camera;
  * valid only where the centre and the 4 neighbours survived the filter.
  * Back-projection follows Eq. reprojection: (z (u - cx)/fx, z (v - cy)/fy, z).
+ * The filter compares differences of input depths, which are exact in either
+ * precision near the threshold (Sterbenz: the two depths are within a factor of two
+ * when they differ by about delta_sup >= 0.1 m / 2), so it has no ties. The
+ * orientation of a normal is a tie when <n, P> / |P| is within TIE_N of zero.
  */
 typedef struct {
   int W, H;
-  float fx, fy, cx, cy;
+  double fx, fy, cx, cy;
   float* z;      /* filtered depth */
   uint8_t* ok;   /* survived filter */
   uint8_t* nok;  /* has a normal */
-  float* Pf;     /* FP32 camera point (decisions) */
-  float* nf;     /* FP32 camera normal (decisions) */
-  double* Pd;    /* FP64 camera point */
-  double* nd;    /* FP64 camera normal */
+  uint8_t* tie;  /* the normal's orientation is a tie */
+  double* P;     /* camera point */
+  double* n;     /* camera normal */
 } oframe;
 
 static void frame_free(oframe* f) {
   free(f->z);
   free(f->ok);
   free(f->nok);
-  free(f->Pf);
-  free(f->nf);
-  free(f->Pd);
-  free(f->nd);
+  free(f->tie);
+  free(f->P);
+  free(f->n);
 }
 
-static int in_range(float z, float zmin, float zmax) { return z > 0.0f && z >= zmin && z <= zmax; }
+static int in_range(double z, double zmin, double zmax) { return z > 0.0 && z >= zmin && z <= zmax; }
 
-static int frame_prepare(oframe* f, const float* depth, int W, int H, float fx, float fy, float cx, float cy,
-                         float zmin, float zmax, float dsup) {
+static int frame_prepare(oframe* f, const float* depth, int W, int H, double fx, double fy, double cx, double cy,
+                         double zmin, double zmax, double dsup) {
   size_t n = (size_t)W * H;
   f->W = W;
   f->H = H;
@@ -296,15 +386,14 @@ static int frame_prepare(oframe* f, const float* depth, int W, int H, float fx, 
   f->z = (float*)calloc(n, sizeof(float));
   f->ok = (uint8_t*)calloc(n, 1);
   f->nok = (uint8_t*)calloc(n, 1);
-  f->Pf = (float*)calloc(3 * n, sizeof(float));
-  f->nf = (float*)calloc(3 * n, sizeof(float));
-  f->Pd = (double*)calloc(3 * n, sizeof(double));
-  f->nd = (double*)calloc(3 * n, sizeof(double));
-  if (!f->z || !f->ok || !f->nok || !f->Pf || !f->nf || !f->Pd || !f->nd) return -1;
+  f->tie = (uint8_t*)calloc(n, 1);
+  f->P = (double*)calloc(3 * n, sizeof(double));
+  f->n = (double*)calloc(3 * n, sizeof(double));
+  if (!f->z || !f->ok || !f->nok || !f->tie || !f->P || !f->n) return -1;
   for (int v = 0; v < H; ++v)
     for (int u = 0; u < W; ++u) {
       size_t i = (size_t)v * W + u;
-      float z = depth[i];
+      double z = depth[i];
       if (!in_range(z, zmin, zmax)) continue;
       int support = 0;
       for (int dv = -1; dv <= 1; ++dv)
@@ -312,22 +401,16 @@ static int frame_prepare(oframe* f, const float* depth, int W, int H, float fx, 
           if (!du && !dv) continue;
           int uu = u + du, vv = v + dv;
           if (uu < 0 || vv < 0 || uu >= W || vv >= H) continue;
-          float zn = depth[(size_t)vv * W + uu];
+          double zn = depth[(size_t)vv * W + uu];
           if (!in_range(zn, zmin, zmax)) continue;
-          if (fabsf(zn - z) <= dsup) support++;
+          if (fabs(zn - z) <= dsup) support++;
         }
       if (support >= 2) {
         f->ok[i] = 1;
-        f->z[i] = z;
-        float a = ((float)u - cx) / fx;
-        float b = ((float)v - cy) / fy;
-        f->Pf[3 * i] = z * a;
-        f->Pf[3 * i + 1] = z * b;
-        f->Pf[3 * i + 2] = z;
-        double zd = z;
-        f->Pd[3 * i] = zd * (((double)u - cx) / fx);
-        f->Pd[3 * i + 1] = zd * (((double)v - cy) / fy);
-        f->Pd[3 * i + 2] = zd;
+        f->z[i] = depth[i];
+        f->P[3 * i] = z * ((u - cx) / fx);
+        f->P[3 * i + 1] = z * ((v - cy) / fy);
+        f->P[3 * i + 2] = z;
       }
     }
   for (int v = 1; v < H - 1; ++v)
@@ -335,45 +418,32 @@ static int frame_prepare(oframe* f, const float* depth, int W, int H, float fx, 
       size_t i = (size_t)v * W + u;
       size_t il = i - 1, ir = i + 1, iu = i - W, idn = i + W;
       if (!f->ok[i] || !f->ok[il] || !f->ok[ir] || !f->ok[iu] || !f->ok[idn]) continue;
-      /* FP32 */
-      float dx[3], dy[3], nn[3];
+      double dx[3], dy[3], c[3];
       for (int a = 0; a < 3; ++a) {
-        dx[a] = f->Pf[3 * ir + a] - f->Pf[3 * il + a];
-        dy[a] = f->Pf[3 * idn + a] - f->Pf[3 * iu + a];
+        dx[a] = f->P[3 * ir + a] - f->P[3 * il + a];
+        dy[a] = f->P[3 * idn + a] - f->P[3 * iu + a];
       }
-      nn[0] = dx[1] * dy[2] - dx[2] * dy[1];
-      nn[1] = dx[2] * dy[0] - dx[0] * dy[2];
-      nn[2] = dx[0] * dy[1] - dx[1] * dy[0];
-      float len = sqrtf((nn[0] * nn[0] + nn[1] * nn[1]) + nn[2] * nn[2]);
-      if (!(len > 0.0f)) continue;
-      for (int a = 0; a < 3; ++a) nn[a] = nn[a] / len;
-      const float* P = f->Pf + 3 * i;
-      if ((nn[0] * P[0] + nn[1] * P[1]) + nn[2] * P[2] > 0.0f)
-        for (int a = 0; a < 3; ++a) nn[a] = -nn[a];
-      for (int a = 0; a < 3; ++a) f->nf[3 * i + a] = nn[a];
-      /* FP64 */
-      double ddx[3], ddy[3], nd[3];
-      for (int a = 0; a < 3; ++a) {
-        ddx[a] = f->Pd[3 * ir + a] - f->Pd[3 * il + a];
-        ddy[a] = f->Pd[3 * idn + a] - f->Pd[3 * iu + a];
-      }
-      nd[0] = ddx[1] * ddy[2] - ddx[2] * ddy[1];
-      nd[1] = ddx[2] * ddy[0] - ddx[0] * ddy[2];
-      nd[2] = ddx[0] * ddy[1] - ddx[1] * ddy[0];
-      double dl = sqrt(nd[0] * nd[0] + nd[1] * nd[1] + nd[2] * nd[2]);
-      for (int a = 0; a < 3; ++a) f->nd[3 * i + a] = nd[a] / dl;
-      /* orient the FP64 normal to the side the FP32 decision chose (toward the camera) */
-      double dot = f->nd[3 * i] * nn[0] + f->nd[3 * i + 1] * nn[1] + f->nd[3 * i + 2] * nn[2];
-      if (dot < 0)
-        for (int a = 0; a < 3; ++a) f->nd[3 * i + a] = -f->nd[3 * i + a];
+      c[0] = dx[1] * dy[2] - dx[2] * dy[1];
+      c[1] = dx[2] * dy[0] - dx[0] * dy[2];
+      c[2] = dx[0] * dy[1] - dx[1] * dy[0];
+      double len = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+      if (!(len > 0.0)) continue;
+      for (int a = 0; a < 3; ++a) c[a] /= len;
+      const double* P = f->P + 3 * i;
+      const double s = c[0] * P[0] + c[1] * P[1] + c[2] * P[2];
+      if (s > 0.0)
+        for (int a = 0; a < 3; ++a) c[a] = -c[a];
+      const double pl = sqrt(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+      f->tie[i] = fabs(s) < TIE_N * pl;
+      for (int a = 0; a < 3; ++a) f->n[3 * i + a] = c[a];
       f->nok[i] = 1;
     }
   return 0;
 }
 
-/* Expose preprocessing: out_ok, out_nok (u8 [n]); Pf, nf (f32 [3n]); Pd, nd (f64 [3n]); z (f32 [n]). */
+/* Expose preprocessing: ok, nok, tie (u8 [n]); z (f32 [n]); P, n (f64 [3n]). */
 int om_preprocess(const float* depth, int W, int H, float fx, float fy, float cx, float cy, float zmin, float zmax,
-                  float dsup, uint8_t* ok, uint8_t* nok, float* zf, float* Pf, float* nf, double* Pd, double* nd) {
+                  float dsup, uint8_t* ok, uint8_t* nok, uint8_t* tie, float* zf, double* P, double* nrm) {
   oframe f;
   memset(&f, 0, sizeof(f));
   if (frame_prepare(&f, depth, W, H, fx, fy, cx, cy, zmin, zmax, dsup) != 0) {
@@ -383,113 +453,209 @@ int om_preprocess(const float* depth, int W, int H, float fx, float fy, float cx
   size_t n = (size_t)W * H;
   if (ok) memcpy(ok, f.ok, n);
   if (nok) memcpy(nok, f.nok, n);
+  if (tie) memcpy(tie, f.tie, n);
   if (zf) memcpy(zf, f.z, n * sizeof(float));
-  if (Pf) memcpy(Pf, f.Pf, 3 * n * sizeof(float));
-  if (nf) memcpy(nf, f.nf, 3 * n * sizeof(float));
-  if (Pd) memcpy(Pd, f.Pd, 3 * n * sizeof(double));
-  if (nd) memcpy(nd, f.nd, 3 * n * sizeof(double));
+  if (P) memcpy(P, f.P, 3 * n * sizeof(double));
+  if (nrm) memcpy(nrm, f.n, 3 * n * sizeof(double));
   frame_free(&f);
   return 0;
 }
 
 /* ======================================================== allocation (A1) == */
 /*
- * Blocks of 8^3 voxels (Sec. 7) are allocated for every (block, D) whose cube
- * the segment [p - tau r, p + tau r] crosses, for each direction D the pixel's
- * world normal belongs to (Eq. angular_threshold: <n, v^D> > cos(theta)).
- * The traversal is a 3D digital differential analyser (Amanatides & Woo) in
- * block units, single precision, ties broken x before y before z.
- * Returns the number of cells written to `cells` (x, y, z triples), at most max_cells.
+ * Blocks of 8^3 voxels (Sec. 7) are allocated for every (block, D) whose closed cube
+ * the segment [p - tau r, p + tau r] meets, for each direction D the pixel's world
+ * normal belongs to (Eq. angular_threshold: <n, v^D> > cos(theta)). The blocks are
+ * found by testing every block of the segment's bounding box with the exact slab test
+ * (the definition itself; an implementation may traverse them with a 3D DDA).
+ * A block is a tie when the segment meets the cube grown by TIE_X on every side but
+ * not the cube shrunk by TIE_X.
  */
-int om_segment_blocks(const float* a, const float* b, float block_size, const float* origin, int32_t* cells,
-                      int max_cells) {
-  float A[3], B[3], d[3], tmax[3], tdel[3];
-  int c[3], e[3], st[3];
+
+/* Does the segment a + s d, s in [0, 1], meet the closed box [lo, hi]? */
+static int seg_box(const double* a, const double* d, const double* lo, const double* hi) {
+  double t0 = 0.0, t1 = 1.0;
   for (int k = 0; k < 3; ++k) {
-    A[k] = (a[k] - origin[k]) / block_size;
-    B[k] = (b[k] - origin[k]) / block_size;
-    d[k] = B[k] - A[k];
-    c[k] = (int)floorf(A[k]);
-    e[k] = (int)floorf(B[k]);
-    if (d[k] > 0.0f) {
-      st[k] = 1;
-      tdel[k] = 1.0f / d[k];
-      tmax[k] = ((float)(c[k] + 1) - A[k]) / d[k];
-    } else if (d[k] < 0.0f) {
-      st[k] = -1;
-      tdel[k] = -1.0f / d[k];
-      tmax[k] = ((float)c[k] - A[k]) / d[k];
-    } else {
-      st[k] = 0;
-      tdel[k] = INFINITY;
-      tmax[k] = INFINITY;
+    if (d[k] == 0.0) {
+      if (a[k] < lo[k] || a[k] > hi[k]) return 0;
+      continue;
     }
+    double u0 = (lo[k] - a[k]) / d[k], u1 = (hi[k] - a[k]) / d[k];
+    if (u0 > u1) {
+      double x = u0;
+      u0 = u1;
+      u1 = x;
+    }
+    if (u0 > t0) t0 = u0;
+    if (u1 < t1) t1 = u1;
+    if (t0 > t1) return 0;
+  }
+  return 1;
+}
+
+/*
+ * Blocks met by segment a-b: writes up to max_cells (x, y, z) triples and a flag per
+ * cell (bit 0: the segment meets the block's closed cube; bit 1: the decision is a
+ * tie). Returns the number of cells with either bit set.
+ */
+int om_segment_blocks(const double* a, const double* b, double block_size, const double* origin, int32_t* cells,
+                      uint8_t* flags, int max_cells) {
+  double A[3], d[3];
+  int lo[3], hi[3];
+  for (int k = 0; k < 3; ++k) {
+    A[k] = a[k] - origin[k];
+    d[k] = b[k] - a[k];
+    const double mn = fmin(a[k], b[k]) - origin[k] - TIE_X, mx = fmax(a[k], b[k]) - origin[k] + TIE_X;
+    lo[k] = (int)floor(mn / block_size);
+    hi[k] = (int)floor(mx / block_size);
   }
   int n = 0;
-  for (int it = 0; it < 64; ++it) {
-    if (n < max_cells) {
-      cells[3 * n] = c[0];
-      cells[3 * n + 1] = c[1];
-      cells[3 * n + 2] = c[2];
-    }
-    n++;
-    if (c[0] == e[0] && c[1] == e[1] && c[2] == e[2]) break;
-    int ax = 0;
-    if (tmax[1] < tmax[ax]) ax = 1;
-    if (tmax[2] < tmax[ax]) ax = 2;
-    if (tmax[ax] > 1.0f) break;
-    c[ax] += st[ax];
-    tmax[ax] += tdel[ax];
-  }
+  for (int z = lo[2]; z <= hi[2]; ++z)
+    for (int y = lo[1]; y <= hi[1]; ++y)
+      for (int x = lo[0]; x <= hi[0]; ++x) {
+        const int c[3] = {x, y, z};
+        double l0[3], h0[3], lg[3], hg[3], ls[3], hs[3];
+        for (int k = 0; k < 3; ++k) {
+          l0[k] = c[k] * block_size;
+          h0[k] = (c[k] + 1) * block_size;
+          lg[k] = l0[k] - TIE_X;
+          hg[k] = h0[k] + TIE_X;
+          ls[k] = l0[k] + TIE_X;
+          hs[k] = h0[k] - TIE_X;
+        }
+        const int met = seg_box(A, d, l0, h0);
+        const int tie = seg_box(A, d, lg, hg) && !seg_box(A, d, ls, hs);
+        if (!met && !tie) continue;
+        if (n < max_cells) {
+          cells[3 * n] = x;
+          cells[3 * n + 1] = y;
+          cells[3 * n + 2] = z;
+          flags[n] = (uint8_t)(met | (tie << 1));
+        }
+        ++n;
+      }
   return n;
 }
 
-/* Single-precision world transform of a camera-frame vector, fixed order, no contraction. */
-static void rot_f(const float R[9], const float* x, float* y) {
-  for (int a = 0; a < 3; ++a) y[a] = (R[3 * a] * x[0] + R[3 * a + 1] * x[1]) + R[3 * a + 2] * x[2];
-}
-
-static void pose_f(const double* T, float R[9], float t[3]) {
+static void pose_d(const double* T, double R[9], double t[3]) {
   for (int a = 0; a < 3; ++a) {
-    for (int b = 0; b < 3; ++b) R[3 * a + b] = (float)T[4 * a + b];
-    t[a] = (float)T[4 * a + 3];
+    for (int b = 0; b < 3; ++b) R[3 * a + b] = T[4 * a + b];
+    t[a] = T[4 * a + 3];
   }
 }
 
+static void rot_d(const double R[9], const double* x, double* y) {
+  for (int a = 0; a < 3; ++a) y[a] = R[3 * a] * x[0] + R[3 * a + 1] * x[1] + R[3 * a + 2] * x[2];
+}
+
+#define MAX_SEG_CELLS 128
+
+/*
+ * Allocate the (block, D) of one frame. A pixel allocates (block, D) when its normal
+ * belongs to D and the segment meets the block; the decision is a tie when the
+ * membership cosine is within TIE_N of cos(theta), the block is a tie of the segment
+ * test, or the normal's orientation is a tie (a flipped normal belongs to the opposite
+ * directions). A key that some pixel allocates with no tie is firm; the other keys a
+ * pixel decides with a tie are recorded as allocation ties of this frame.
+ */
 static int allocate_frame(omap* m, const oframe* f, const double* T, int frame) {
-  float R[9], t[3];
-  pose_f(T, R, t);
-  float bs = 8.0f * m->hf;
-  int32_t cells[3 * 64];
+  double R[9], t[3];
+  pose_d(T, R, t);
+  const double bs = 8.0 * m->h;
+  int32_t cells[3 * MAX_SEG_CELLS];
+  uint8_t flags[MAX_SEG_CELLS];
+  /* candidate tie keys of this frame: (x, y, z, D) */
+  size_t ncand = 0, capc = 1024;
+  int32_t* cand = (int32_t*)malloc(capc * 4 * sizeof(int32_t));
+  /* bricks allocated firmly in this frame */
+  size_t fcap = m->brick_cap ? m->brick_cap : 1024;
+  uint8_t* firm = NULL;
+  if (!cand) return -1;
   for (int v = 0; v < f->H; ++v)
     for (int u = 0; u < f->W; ++u) {
       size_t i = (size_t)v * f->W + u;
       if (!f->nok[i]) continue;
-      float nw[3], rv[3], pw[3];
-      rot_f(R, f->nf + 3 * i, nw);
-      unsigned mask = 0;
+      double nw[3], rv[3], pw[3];
+      rot_d(R, f->n + 3 * i, nw);
+      int mem[ND], tD[ND], any = 0;
       for (int D = 0; D < ND; ++D) {
-        float c = (D & 1) ? -nw[D >> 1] : nw[D >> 1];
-        if (c > m->costhf) mask |= 1u << D;
+        const double c = (D & 1) ? -nw[D >> 1] : nw[D >> 1];
+        mem[D] = c > m->costh;
+        tD[D] = fabs(c - m->costh) < TIE_N;
       }
-      if (!mask) continue;
-      rot_f(R, f->Pf + 3 * i, rv);
+      for (int D = 0; D < ND; ++D) {
+        if (f->tie[i]) tD[D] |= mem[D] != mem[D ^ 1];
+        any |= mem[D] | tD[D];
+      }
+      if (!any) continue;
+      rot_d(R, f->P + 3 * i, rv);
       for (int a = 0; a < 3; ++a) pw[a] = rv[a] + t[a];
-      float len = sqrtf((rv[0] * rv[0] + rv[1] * rv[1]) + rv[2] * rv[2]);
-      float rh[3], A[3], B[3];
+      const double len = sqrt(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
+      double A[3], B[3];
       for (int a = 0; a < 3; ++a) {
-        rh[a] = rv[a] / len;
-        A[a] = pw[a] - m->tauf * rh[a];
-        B[a] = pw[a] + m->tauf * rh[a];
+        A[a] = pw[a] - m->tau * (rv[a] / len);
+        B[a] = pw[a] + m->tau * (rv[a] / len);
       }
-      int n = om_segment_blocks(A, B, bs, m->originf, cells, 64);
-      if (n > 64) n = 64;
-      for (int k = 0; k < n; ++k)
-        for (int D = 0; D < ND; ++D)
-          if (mask & (1u << D))
-            if (brick_alloc(m, cells[3 * k], cells[3 * k + 1], cells[3 * k + 2], D, frame) < 0) return -1;
+      int nc = om_segment_blocks(A, B, bs, m->origin, cells, flags, MAX_SEG_CELLS);
+      if (nc > MAX_SEG_CELLS) nc = MAX_SEG_CELLS;
+      for (int k = 0; k < nc; ++k) {
+        const int met = flags[k] & 1, near = (flags[k] >> 1) & 1;
+        for (int D = 0; D < ND; ++D) {
+          const int* c = cells + 3 * k;
+          if (mem[D] && met) {
+            const int32_t b = brick_alloc(m, c[0], c[1], c[2], D, frame);
+            if (b < 0) {
+              free(cand);
+              free(firm);
+              return -1;
+            }
+            if (!near && !tD[D]) {
+              if ((size_t)b >= fcap || !firm) {
+                size_t nf = fcap;
+                while ((size_t)b >= nf) nf *= 2;
+                uint8_t* x = (uint8_t*)realloc(firm, nf);
+                if (!x) {
+                  free(cand);
+                  free(firm);
+                  return -1;
+                }
+                memset(x + (firm ? fcap : 0), 0, nf - (firm ? fcap : 0));
+                firm = x;
+                fcap = nf;
+              }
+              firm[b] = 1;
+            }
+          }
+          if ((mem[D] || tD[D]) && (near || tD[D])) {
+            if (ncand == capc) {
+              capc *= 2;
+              int32_t* x = (int32_t*)realloc(cand, capc * 4 * sizeof(int32_t));
+              if (!x) {
+                free(cand);
+                free(firm);
+                return -1;
+              }
+              cand = x;
+            }
+            cand[4 * ncand] = c[0];
+            cand[4 * ncand + 1] = c[1];
+            cand[4 * ncand + 2] = c[2];
+            cand[4 * ncand + 3] = D;
+            ++ncand;
+          }
+        }
+      }
     }
-  return 0;
+  int rc = 0;
+  for (size_t k = 0; k < ncand && rc == 0; ++k) {
+    const int32_t* c = cand + 4 * k;
+    const int32_t b = hash_find(m, c[0], c[1], c[2], c[3]);
+    if (b >= 0 && firm && (size_t)b < fcap && firm[b]) continue;
+    rc = tie_key_put(m, c[0], c[1], c[2], c[3], frame);
+  }
+  free(cand);
+  free(firm);
+  return rc;
 }
 
 /* ============================================================ fusion (A2) == */
@@ -502,57 +668,93 @@ double om_w_dir(double cos_angle, double theta) {
   return clampd((theta - alpha) / (2.0 * theta - M_PI / 2.0), 0.0, 1.0);
 }
 
+/* distance of x + 1/2 to the nearest integer: the rounding floor(x + 1/2) is a tie below TIE_PX */
+static int round_tie(double x) {
+  const double s = x + 0.5;
+  return fabs(s - floor(s + 0.5)) < TIE_PX;
+}
+
+/*
+ * Voxel-projection fusion (Sec. 3). Every voxel of every allocated (block, D) is
+ * projected into the frame; the nearest pixel supplies p and n; the point-to-plane
+ * distance decides between carving (in front of the band, Sec. 3), the running-average
+ * update with the combined weight of Eq. combined_fusion_weight (inside the band) and
+ * nothing (behind it). A voxel is marked as a tie (bit 0; bit 1 for colour alone) when
+ * one of the decisions about it in this frame lies within its margin: camera depth
+ * near 0, a projection near a pixel boundary, a tie of the pixel's normal, the band
+ * edges (TIE_X plus TIE_N times |x - p|), the direction membership or the colour radius.
+ * The whole brick is marked when its allocation was a tie in a frame before or at the
+ * one that allocated it here.
+ */
 static int fuse_frame(omap* m, const oframe* f, const uint8_t* rgb, const double* T) {
-  float R[9], t[3];
-  pose_f(T, R, t);
+  double R[9], t[3];
+  pose_d(T, R, t);
   const int W = f->W, H = f->H;
-  const float tau = m->tauf;
-  const float bsz = m->hf;
-  double Rd[9], td[3];
-  for (int a = 0; a < 3; ++a) {
-    for (int b = 0; b < 3; ++b) Rd[3 * a + b] = T[4 * a + b];
-    td[a] = T[4 * a + 3];
-  }
+  const double tau = m->tau;
 #pragma omp parallel for schedule(dynamic, 16)
   for (long b = 0; b < (long)m->nbricks; ++b) {
     const int32_t* bc = m->coord + 4 * b;
     const int D = bc[3];
     ovox* vb = m->vox + (size_t)b * BVOX;
+    uint8_t* tb = m->tie + (size_t)b * BVOX;
+    if (m->dense_dim <= 0) {
+      const int32_t tf = tie_key_find(m, bc[0], bc[1], bc[2], D);
+      if (tf >= 0 && tf <= m->first_frame[b]) memset(tb, 3, BVOX);
+    }
     for (int k = 0; k < BLK; ++k)
       for (int j = 0; j < BLK; ++j)
         for (int i = 0; i < BLK; ++i) {
-          int gi[3] = {BLK * bc[0] + i, BLK * bc[1] + j, BLK * bc[2] + k};
-          /* FP32 decision path: voxel centre, camera frame, projection, band test */
-          float x[3], dxw[3], xc[3];
+          const int vi = (k * BLK + j) * BLK + i;
+          const int gi[3] = {BLK * bc[0] + i, BLK * bc[1] + j, BLK * bc[2] + k};
+          double x[3], rel[3], xc[3];
           for (int a = 0; a < 3; ++a) {
-            x[a] = (float)gi[a] * bsz + m->originf[a];
-            dxw[a] = x[a] - t[a];
+            x[a] = gi[a] * m->h + m->origin[a];
+            rel[a] = x[a] - t[a];
           }
-          for (int a = 0; a < 3; ++a) xc[a] = (R[a] * dxw[0] + R[3 + a] * dxw[1]) + R[6 + a] * dxw[2];
-          if (!(xc[2] > 0.0f)) continue;
-          float uf = (xc[0] / xc[2]) * f->fx + f->cx;
-          float vf = (xc[1] / xc[2]) * f->fy + f->cy;
-          float ur = floorf(uf + 0.5f), vr = floorf(vf + 0.5f);
-          if (!(ur >= 0.0f && vr >= 0.0f && ur < (float)W && vr < (float)H)) continue;
-          int u = (int)ur, v = (int)vr;
-          size_t pi = (size_t)v * W + u;
-          if (!f->nok[pi]) continue;
-          const float* P = f->Pf + 3 * pi;
-          const float* n = f->nf + 3 * pi;
-          float draw = ((xc[0] - P[0]) * n[0] + (xc[1] - P[1]) * n[1]) + (xc[2] - P[2]) * n[2];
-          if (draw < -tau) continue;
-          ovox* vx = vb + (k * BLK + j) * BLK + i;
+          for (int a = 0; a < 3; ++a) xc[a] = R[a] * rel[0] + R[3 + a] * rel[1] + R[6 + a] * rel[2];
+          if (!(xc[2] > 0.0)) {
+            if (fabs(xc[2]) < TIE_X) tb[vi] |= 3;
+            continue;
+          }
+          const double uf = (xc[0] / xc[2]) * f->fx + f->cx;
+          const double vf = (xc[1] / xc[2]) * f->fy + f->cy;
+          const int tie_proj = round_tie(uf) || round_tie(vf);
+          const double ur = floor(uf + 0.5), vr = floor(vf + 0.5);
+          if (!(ur >= 0.0 && vr >= 0.0 && ur < (double)W && vr < (double)H)) {
+            if (tie_proj) tb[vi] |= 3;
+            continue;
+          }
+          const int u = (int)ur, v = (int)vr;
+          const size_t pi = (size_t)v * W + u;
+          if (!f->nok[pi]) {
+            if (tie_proj) tb[vi] |= 3;
+            continue;
+          }
+          const double* P = f->P + 3 * pi;
+          const double* n = f->n + 3 * pi;
+          double e[3];
+          for (int a = 0; a < 3; ++a) e[a] = xc[a] - P[a];
+          const double draw = e[0] * n[0] + e[1] * n[1] + e[2] * n[2];
+          const double dist = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+          const double band_eps = TIE_X + TIE_N * dist;
+          int tie = tie_proj || f->tie[pi];
+          ovox* vx = vb + vi;
+          if (draw < -tau) {
+            if (tie || fabs(draw + tau) < band_eps) tb[vi] |= 3;
+            continue;
+          }
           if (draw > tau) {
+            if (tie || fabs(draw - tau) < band_eps) tb[vi] |= 3;
             /* free-space carving, unless a depth jump > tau lies within the carve radius */
             int jump = 0;
-            float zc = f->z[pi];
+            const double zc = f->z[pi];
             for (int dv = -m->carve_r; dv <= m->carve_r && !jump; ++dv)
               for (int du = -m->carve_r; du <= m->carve_r; ++du) {
                 int uu = u + du, vv = v + dv;
                 if (uu < 0 || vv < 0 || uu >= W || vv >= H) continue;
                 size_t qi = (size_t)vv * W + uu;
                 if (!f->ok[qi]) continue;
-                if (fabsf(f->z[qi] - zc) > tau) {
+                if (fabs((double)f->z[qi] - zc) > tau) {
                   jump = 1;
                   break;
                 }
@@ -563,49 +765,30 @@ static int fuse_frame(omap* m, const oframe* f, const uint8_t* rgb, const double
             vx->w = wn < m->wmax ? wn : m->wmax;
             continue;
           }
-          /* membership of the pixel normal in direction D (single-precision decision) */
-          float nw[3];
-          rot_f(R, n, nw);
-          float cd = (D & 1) ? -nw[D >> 1] : nw[D >> 1];
-          if (!(cd > m->costhf)) continue;
-          if (!(((n[0] * P[0] + n[1] * P[1]) + n[2] * P[2]) < 0.0f)) continue;
-          /* FP64 values */
-          double xd[3], xcd[3], rel[3];
-          for (int a = 0; a < 3; ++a) {
-            xd[a] = (double)gi[a] * m->h + m->origin[a];
-            rel[a] = xd[a] - td[a];
-          }
-          for (int a = 0; a < 3; ++a) xcd[a] = Rd[a] * rel[0] + Rd[3 + a] * rel[1] + Rd[6 + a] * rel[2];
-          /* the pixel normal is estimated once, in single precision (it decides the
-             direction membership above); every value below is computed in double */
-          const double* Pd = f->Pd + 3 * pi;
-          const double nd[3] = {(double)n[0], (double)n[1], (double)n[2]};
-          double dr = (xcd[0] - Pd[0]) * nd[0] + (xcd[1] - Pd[1]) * nd[1] + (xcd[2] - Pd[2]) * nd[2];
-          double d = clampd(dr / m->tau, -1.0, 1.0);
-          double zp = Pd[2];
-          double w_depth = 1.0 / ((zp + 1.0 - m->zmin) * (zp + 1.0 - m->zmin));
-          double pl = sqrt(Pd[0] * Pd[0] + Pd[1] * Pd[1] + Pd[2] * Pd[2]);
-          double w_angle = -(nd[0] * Pd[0] + nd[1] * Pd[1] + nd[2] * Pd[2]) / pl;
-          if (w_angle < 0) w_angle = 0;
-          double nwd[3];
-          for (int a = 0; a < 3; ++a) nwd[a] = Rd[3 * a] * nd[0] + Rd[3 * a + 1] * nd[1] + Rd[3 * a + 2] * nd[2];
-          double cdd = (D & 1) ? -nwd[D >> 1] : nwd[D >> 1];
-          /* an update the single-precision tests admitted always carries a positive weight */
-          double w_d = w_depth * w_angle * om_w_dir(cdd, m->theta);
-          if (!(w_d > W_FLOOR)) w_d = W_FLOOR;
-          double wn = vx->w + w_d;
+          if (fabs(draw + tau) < band_eps || fabs(draw - tau) < band_eps) tie = 1;
+          /* membership of the pixel normal in direction D (Eq. angular_threshold) */
+          double nw[3];
+          rot_d(R, n, nw);
+          const double cd = (D & 1) ? -nw[D >> 1] : nw[D >> 1];
+          if (fabs(cd - m->costh) < TIE_N) tie = 1;
+          if (tie) tb[vi] |= 3;
+          if (!(cd > m->costh)) continue;
+          const double np = n[0] * P[0] + n[1] * P[1] + n[2] * P[2];
+          if (!(np < 0.0)) continue;
+          const double d = clampd(draw / tau, -1.0, 1.0);
+          const double zp = P[2];
+          const double w_depth = 1.0 / ((zp + 1.0 - m->zmin) * (zp + 1.0 - m->zmin));
+          const double pl = sqrt(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+          const double w_angle = -np / pl;
+          const double w_d = w_depth * w_angle * om_w_dir(cd, m->theta);
+          const double wn = vx->w + w_d;
           vx->sdf = (vx->w * vx->sdf + w_d * d) / wn;
           vx->w = wn < m->wmax ? wn : m->wmax;
           if (m->color && rgb) {
-            /* colour is fused only within tau of the observed point (Eq. color_weight);
-               that test is a single-precision decision */
-            float e0 = P[0] - xc[0], e1 = P[1] - xc[1], e2 = P[2] - xc[2];
-            float distf = sqrtf((e0 * e0 + e1 * e1) + e2 * e2);
-            if (distf < tau) {
-              double dist = sqrt((Pd[0] - xcd[0]) * (Pd[0] - xcd[0]) + (Pd[1] - xcd[1]) * (Pd[1] - xcd[1]) +
-                                 (Pd[2] - xcd[2]) * (Pd[2] - xcd[2]));
-              double w_c = w_d * (1.0 - (dist / m->tau < 1.0 ? dist / m->tau : 1.0));
-              if (!(w_c > W_FLOOR)) w_c = W_FLOOR;
+            /* colour is fused only within tau of the observed point (Eq. color_weight) */
+            if (fabs(dist - tau) < TIE_X) tb[vi] |= 2;
+            if (dist < tau) {
+              const double w_c = w_d * (1.0 - dist / tau);
               const uint8_t* c = rgb + 3 * pi;
               double wcn = vx->wc + w_c;
               vx->r = (vx->wc * vx->r + w_c * c[0]) / wcn;
@@ -624,7 +807,7 @@ int om_integrate(omap* m, const float* depth, const uint8_t* rgb, int W, int H, 
                  float cy, const double* T_wc) {
   oframe f;
   memset(&f, 0, sizeof(f));
-  int rc = frame_prepare(&f, depth, W, H, fx, fy, cx, cy, m->zminf, m->zmaxf, m->dsupf);
+  int rc = frame_prepare(&f, depth, W, H, fx, fy, cx, cy, m->zmin, m->zmax, m->dsup);
   if (rc == 0 && m->dense_dim <= 0) rc = allocate_frame(m, &f, T_wc, m->frames);
   if (rc == 0) rc = fuse_frame(m, &f, rgb, T_wc);
   frame_free(&f);
@@ -825,45 +1008,24 @@ static int render_pixel(const omap* m, const double* T, double fx, double fy, do
       continue;
     }
     if (prev_def && prev_phi > 0 && cb.phi <= 0) {
-      /* refine the crossing in [prev_t, t] by small regular steps (Sec. 4): a scan of 4
-         sub-steps keeps the first sub-interval where Phi turns <= 0 (an undefined probe
-         counts as free space); the root is the linear interpolation of Phi over that
-         h/8-wide bracket */
+      /* the hit: the root of the continuous Phi(t) in [prev_t, t] (Sec. 4: small steps
+         after the regular probing), by bisection; an undefined midpoint counts as free
+         space. Normal and colour at the root; a miss if no direction has a combination
+         weight there (the normal is undefined). */
       double lo = prev_t, hi = t;
-      for (int lvl = 0; lvl < 1; ++lvl) {
-        double a0 = lo, dt = (hi - lo) / 4.0, prev = lo;
-        for (int j = 1; j < 4; ++j) {
-          double tj = a0 + j * dt;
-          double xj[3] = {o[0] + tj * r[0], o[1] + tj * r[1], o[2] + tj * r[2]};
-          combo cj;
-          if (combine(m, xj, r, &cj) && cj.phi <= 0) {
-            hi = tj;
-            break;
-          }
-          prev = tj;
-        }
-        lo = prev;
+      while (hi - lo > ROOT_TOL) {
+        const double tm = 0.5 * (lo + hi);
+        const double xm[3] = {o[0] + tm * r[0], o[1] + tm * r[1], o[2] + tm * r[2]};
+        combo cm;
+        if (combine(m, xm, r, &cm) && cm.phi <= 0)
+          hi = tm;
+        else
+          lo = tm;
       }
-      double ts;
-      {
-        double xa[3] = {o[0] + lo * r[0], o[1] + lo * r[1], o[2] + lo * r[2]};
-        double xb[3] = {o[0] + hi * r[0], o[1] + hi * r[1], o[2] + hi * r[2]};
-        combo ca, cbb;
-        int da = combine(m, xa, r, &ca) && ca.phi > 0;
-        int db = combine(m, xb, r, &cbb) && cbb.phi <= 0;
-        ts = (da && db) ? lo + (hi - lo) * ca.phi / (ca.phi - cbb.phi) : 0.5 * (lo + hi);
-      }
-      /* normal and colour: at the first grid sample behind the crossing (the one that
-         decided the hit), else at the sample in front of it, else at the root; a miss if
-         the combination weights vanish at all three */
+      const double ts = 0.5 * (lo + hi);
+      const double xs[3] = {o[0] + ts * r[0], o[1] + ts * r[1], o[2] + ts * r[2]};
       combo ch;
-      int have = 0;
-      double ends[3] = {t, prev_t, ts};
-      for (int e = 0; e < 3 && !have; ++e) {
-        double xs[3] = {o[0] + ends[e] * r[0], o[1] + ends[e] * r[1], o[2] + ends[e] * r[2]};
-        have = combine(m, xs, r, &ch) && ch.wsum_comb > 0 && ch.ncomb;
-      }
-      if (!have) return 0;
+      if (!(combine(m, xs, r, &ch) && ch.wsum_comb > 0 && ch.ncomb)) return 0;
       *depth = ts / rl;
       for (int a = 0; a < 3; ++a) ncam[a] = T[a] * ch.n[0] + T[4 + a] * ch.n[1] + T[8 + a] * ch.n[2];
       if (ch.col_ok)
@@ -922,9 +1084,8 @@ int om_render(const omap* m, const double* T_wc, int W, int H, float fx, float f
  *   Here every allocated block is combined (the kernels combine the blocks of the padded view
  *   frustum, which hold every voxel a ray of that view reads).
  *   ray-cast: the rules of the direct render (samples at t = k h/2, the first pair of
- *   consecutive defined samples with Phi > 0 >= Phi, one scan of 4 sub-steps and linear
- *   interpolation, outputs at the first grid sample behind the crossing, else in front of
- *   it, else at the root) with Phi the trilinear interpolation of the combined values
+ *   consecutive defined samples with Phi > 0 >= Phi, bisection to the root of Phi(t) in
+ *   that bracket, outputs at the root) with Phi the trilinear interpolation of the combined values
  *   (defined if all 8 corners are), the normal the central difference of that field at +-h
  *   (defined if the 6 offset samples are, norm > 1e-12) and the colour the trilinear
  *   interpolation of the combined colours (where all 8 corners have one).
@@ -1166,37 +1327,21 @@ static int render_pixel_comb(const omap* m, const double* T, double fx, double f
       continue;
     }
     if (prev_def && prev_phi > 0 && cs.phi <= 0) {
-      /* one regular scan of 4 sub-steps, then linear interpolation (as the direct render) */
-      double lo = prev_t, hi = t, prev = lo;
-      const double dt = (hi - lo) / 4.0;
-      for (int j = 1; j < 4; ++j) {
-        const double tj = lo + j * dt;
-        const double xj[3] = {o[0] + tj * r[0], o[1] + tj * r[1], o[2] + tj * r[2]};
-        csample cj;
-        if (comb_eval(m, xj, &cj) && cj.phi <= 0) {
-          hi = tj;
-          break;
-        }
-        prev = tj;
+      /* bisection to the root of the combined field, outputs at the root (as the direct render) */
+      double lo = prev_t, hi = t;
+      while (hi - lo > ROOT_TOL) {
+        const double tm = 0.5 * (lo + hi);
+        const double xm[3] = {o[0] + tm * r[0], o[1] + tm * r[1], o[2] + tm * r[2]};
+        csample cm;
+        if (comb_eval(m, xm, &cm) && cm.phi <= 0)
+          hi = tm;
+        else
+          lo = tm;
       }
-      lo = prev;
-      double ts;
-      {
-        const double xa[3] = {o[0] + lo * r[0], o[1] + lo * r[1], o[2] + lo * r[2]};
-        const double xb[3] = {o[0] + hi * r[0], o[1] + hi * r[1], o[2] + hi * r[2]};
-        csample ca, cb;
-        const int da = comb_eval(m, xa, &ca) && ca.phi > 0;
-        const int db = comb_eval(m, xb, &cb) && cb.phi <= 0;
-        ts = (da && db) ? lo + (hi - lo) * ca.phi / (ca.phi - cb.phi) : 0.5 * (lo + hi);
-      }
-      const double ends[3] = {t, prev_t, ts};
+      const double ts = 0.5 * (lo + hi);
+      const double xs[3] = {o[0] + ts * r[0], o[1] + ts * r[1], o[2] + ts * r[2]};
       csample ch;
-      int have = 0;
-      for (int e = 0; e < 3 && !have; ++e) {
-        const double xs[3] = {o[0] + ends[e] * r[0], o[1] + ends[e] * r[1], o[2] + ends[e] * r[2]};
-        have = comb_eval(m, xs, &ch) && ch.has_n;
-      }
-      if (!have) return 0;
+      if (!(comb_eval(m, xs, &ch) && ch.has_n)) return 0;
       *depth = ts / rl;
       for (int a = 0; a < 3; ++a) ncam[a] = T[a] * ch.n[0] + T[4 + a] * ch.n[1] + T[8 + a] * ch.n[2];
       *col_ok = ch.col_ok;
@@ -1284,8 +1429,9 @@ int om_set_brick(omap* m, int bx, int by, int bz, int D, const double* vox) {
  *    <n^D~(q), -r> > 0;
  *  - the value is the fused-weight average of Phi^D over F (free space) or O (occupied);
  *    undefined when that set is empty.
- * The march, refinement and output rules are those of the direct render (reading of Sec. 4),
- * with the normal as the normalised fused-weight sum of the chosen set's normals. No colour.
+ * The march and the root (bisection in the first Phi > 0 >= Phi bracket) are those of the
+ * direct render (reading of Sec. 4); the normal, at the root, is the normalised fused-weight
+ * sum of the chosen set's normals. No colour.
  */
 typedef struct {
   int present, part;
@@ -1399,48 +1545,32 @@ static int render_pixel_fs(const omap* m, const double* T, double fx, double fy,
     if (cell_has_any(m, c[0], c[1], c[2])) fs_all(m, x, &G[i * ND]);
     gdef[i] = fs_value(m, o, r, &G[i * ND], t, G, gt, i - 1, &gphi[i], &gn[3 * i]);
     if (!(i > 0 && gdef[i - 1] && gdef[i] && gphi[i - 1] > 0 && gphi[i] <= 0)) continue;
-    /* refinement in [t_{i-1}, t_i]: 4 regular sub-steps, the first that turns <= 0 */
-    double lo = gt[i - 1], hi = t, dt = (hi - lo) / 4.0, prev = lo;
-    int dlo = 1, dhi = 1;
-    double plo = gphi[i - 1], phi_hi = gphi[i];
-    for (int j = 1; j < 4; ++j) {
-      double tj = lo + j * dt;
-      double xj[3] = {o[0] + tj * r[0], o[1] + tj * r[1], o[2] + tj * r[2]};
+    /* the root in [t_{i-1}, t_i] by bisection (an undefined midpoint counts as free space);
+       the normal is the fused-weight normal sum at the root */
+    double lo = gt[i - 1], hi = t;
+    while (hi - lo > ROOT_TOL) {
+      const double tm = 0.5 * (lo + hi);
+      const double xm[3] = {o[0] + tm * r[0], o[1] + tm * r[1], o[2] + tm * r[2]};
       fsamp P[ND];
-      fs_all(m, xj, P);
-      double pj, nj[3];
-      int dj = fs_value(m, o, r, P, tj, G, gt, i - 1, &pj, nj);
-      if (dj && pj <= 0) {
-        hi = tj;
-        phi_hi = pj;
-        dhi = 1;
-        break;
-      }
-      prev = tj;
-      dlo = dj;
-      plo = pj;
+      fs_all(m, xm, P);
+      double pm, nm[3];
+      if (fs_value(m, o, r, P, tm, G, gt, i - 1, &pm, nm) && pm <= 0)
+        hi = tm;
+      else
+        lo = tm;
     }
-    lo = prev;
-    double ts = (dlo && plo > 0 && dhi && phi_hi <= 0) ? lo + (hi - lo) * (plo / (plo - phi_hi)) : 0.5 * (lo + hi);
-    /* normal: grid sample behind the crossing, else the one in front of it, else the root */
-    const double* nn = NULL;
-    double nr[3];
-    if (gn[3 * i] != 0 || gn[3 * i + 1] != 0 || gn[3 * i + 2] != 0) {
-      nn = &gn[3 * i];
-    } else if (gn[3 * (i - 1)] != 0 || gn[3 * (i - 1) + 1] != 0 || gn[3 * (i - 1) + 2] != 0) {
-      nn = &gn[3 * (i - 1)];
-    } else {
-      double xs[3] = {o[0] + ts * r[0], o[1] + ts * r[1], o[2] + ts * r[2]};
+    const double ts = 0.5 * (lo + hi);
+    {
+      const double xs[3] = {o[0] + ts * r[0], o[1] + ts * r[1], o[2] + ts * r[2]};
       fsamp P[ND];
       fs_all(m, xs, P);
-      double ps;
-      if (fs_value(m, o, r, P, ts, G, gt, i - 1, &ps, nr) && (nr[0] != 0 || nr[1] != 0 || nr[2] != 0)) nn = nr;
-    }
-    if (nn) {
-      double ln = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
-      *depth = ts / rl;
-      for (int a = 0; a < 3; ++a) ncam[a] = (T[a] * nn[0] + T[4 + a] * nn[1] + T[8 + a] * nn[2]) / ln;
-      hit = 1;
+      double ps, nr[3];
+      if (fs_value(m, o, r, P, ts, G, gt, i - 1, &ps, nr) && (nr[0] != 0 || nr[1] != 0 || nr[2] != 0)) {
+        const double ln = sqrt(nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2]);
+        *depth = ts / rl;
+        for (int a = 0; a < 3; ++a) ncam[a] = (T[a] * nr[0] + T[4 + a] * nr[1] + T[8 + a] * nr[2]) / ln;
+        hit = 1;
+      }
     }
     break;
   }

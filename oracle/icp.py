@@ -23,9 +23,17 @@ Paper passages followed (Splietker & Behnke):
     full-resolution render and rounding to the nearest pixel, distance outlier
     threshold 0.05 m coarse / 0.005 m finest, intensity threshold 0.175 / 0.05.
 
-Decisions (pixel association, inlier distance, image bounds) are taken in
-single precision with the kernel's operation order: x = p + ((A p) + t) with
-A = sR - I. Values are computed in double.
+Every value and every decision (pixel association, inlier distance, image bounds,
+intensity threshold) is computed in double precision. A decision within a stated
+margin of its threshold is a tie: the rounding floor(x + 1/2) of a projected pixel
+coordinate within TIE_PX = 2e-3 px of a half-integer (about 10x the single-precision
+rounding of f x / z at f = 910), a camera depth within TIE_X = 1e-5 m of zero, the
+inlier distance within TIE_X of eps, an image-bound test within TIE_PX, and an
+intensity residual within 1e-6 + TIE_PX |grad I| of its threshold. ``Rows`` reports
+the number of tie pixels and, for the normal equations, a bound on how much the
+other outcomes of those decisions could change H and g (``tie_H``: Frobenius norm,
+``tie_g``: per component), so that a comparison with an implementation that decides in
+single precision can allow exactly that.
 """
 from __future__ import annotations
 
@@ -34,7 +42,8 @@ from dataclasses import dataclass
 import numpy as np
 import scipy.linalg
 
-F32 = np.float32
+TIE_PX = 2e-3
+TIE_X = 1e-5
 
 
 # ----------------------------------------------------------------- Lie ----
@@ -67,28 +76,17 @@ def intensity(rgb: np.ndarray) -> np.ndarray:
     return (0.299 * c[..., 0] + 0.587 * c[..., 1] + 0.114 * c[..., 2]) / 255.0
 
 
-def intensity_f32(rgb: np.ndarray) -> np.ndarray:
-    c = rgb.astype(F32)
-    return ((F32(0.299) * c[..., 0] + F32(0.587) * c[..., 1]) + F32(0.114) * c[..., 2]) / F32(255.0)
-
-
-def downsample_depth(d32: np.ndarray, d64: np.ndarray):
-    """2x2 mean of the valid (> 0) children, in the child order (0,0),(1,0),(0,1),(1,1).
-    Single precision (sum in that order, then divide by the count) and double."""
-    H, W = d32.shape[0] // 2, d32.shape[1] // 2
-    s32 = np.zeros((H, W), F32)
-    s64 = np.zeros((H, W))
+def downsample_depth(d64: np.ndarray) -> np.ndarray:
+    """2x2 mean of the valid (> 0) children (Sec. 7 pyramid)."""
+    H, W = d64.shape[0] // 2, d64.shape[1] // 2
+    s = np.zeros((H, W))
     n = np.zeros((H, W), np.int32)
     for dy, dx in ((0, 0), (0, 1), (1, 0), (1, 1)):
-        c32 = d32[dy:2 * H:2, dx:2 * W:2]
-        c64 = d64[dy:2 * H:2, dx:2 * W:2]
-        v = c32 > 0
-        s32 = np.where(v, (s32 + c32).astype(F32), s32)
-        s64 = np.where(v, s64 + c64, s64)
+        c = d64[dy:2 * H:2, dx:2 * W:2]
+        v = c > 0
+        s = np.where(v, s + c, s)
         n += v
-    out32 = np.where(n > 0, s32 / np.maximum(n, 1).astype(F32), F32(0)).astype(F32)
-    out64 = np.where(n > 0, s64 / np.maximum(n, 1), 0.0)
-    return out32, out64
+    return np.where(n > 0, s / np.maximum(n, 1), 0.0)
 
 
 def downsample_mean(img: np.ndarray) -> np.ndarray:
@@ -108,7 +106,6 @@ def grad_image(I: np.ndarray):
 
 @dataclass
 class Level:
-    d32: np.ndarray
     d64: np.ndarray
     K: object
     I: np.ndarray | None = None
@@ -117,27 +114,17 @@ class Level:
 def pyramid(depth_filtered: np.ndarray, K, levels: int, rgb: np.ndarray | None = None) -> list[Level]:
     """Levels 0..levels-1 of the current frame. ``depth_filtered`` is the
     outlier-filtered depth (Sec. 7)."""
-    d32 = np.ascontiguousarray(depth_filtered, F32)
-    d64 = d32.astype(np.float64)
+    d64 = np.asarray(depth_filtered, np.float64)
     I = None if rgb is None else intensity(rgb)
-    out = [Level(d32, d64, K, I)]
+    out = [Level(d64, K, I)]
     for _ in range(1, levels):
-        d32, d64 = downsample_depth(d32, d64)
+        d64 = downsample_depth(d64)
         I = None if I is None else downsample_mean(I)
-        out.append(Level(d32, d64, out[-1].K.scaled(1), I))
+        out.append(Level(d64, out[-1].K.scaled(1), I))
     return out
 
 
 # -------------------------------------------------------- association -----
-
-def _backproject32(z32, K):
-    H, W = z32.shape
-    u = np.arange(W, dtype=F32)[None, :]
-    v = np.arange(H, dtype=F32)[:, None]
-    a = (u - F32(K.cx)) / F32(K.fx)
-    b = (v - F32(K.cy)) / F32(K.fy)
-    return np.stack([(z32 * a).astype(F32), (z32 * b).astype(F32), z32], axis=-1)
-
 
 def _backproject64(z64, K):
     H, W = z64.shape
@@ -146,14 +133,15 @@ def _backproject64(z64, K):
     return np.stack([z64 * ((u - K.cx) / K.fx), z64 * ((v - K.cy) / K.fy), z64], axis=-1)
 
 
-def _transform32(dT: np.ndarray, p32: np.ndarray):
-    """delta = (A p) + t with A = (sR - I) in single precision, x = p + delta."""
-    A = (dT[:3, :3] - np.eye(3)).astype(F32)
-    t = dT[:3, 3].astype(F32)
-    d = [(((A[a, 0] * p32[..., 0]).astype(F32) + (A[a, 1] * p32[..., 1]).astype(F32)).astype(F32)
-          + (A[a, 2] * p32[..., 2]).astype(F32)).astype(F32) for a in range(3)]
-    delta = np.stack([(d[a] + t[a]).astype(F32) for a in range(3)], axis=-1)
-    return (p32 + delta).astype(F32)
+def _round_alt(x):
+    """floor(x + 1/2) and the other integer it could round to when x + 1/2 is within TIE_PX of
+    an integer (else the same value)."""
+    s = x + 0.5
+    fl = np.floor(s)
+    lo = (s - fl) < TIE_PX
+    hi = (fl + 1.0 - s) < TIE_PX
+    alt = np.where(lo, fl - 1.0, np.where(hi, fl + 1.0, fl))
+    return fl, alt
 
 
 @dataclass
@@ -163,51 +151,92 @@ class Rows:
     w: np.ndarray    # N
     n_geo: int
     n_photo: int
+    n_tie: int = 0                    # pixels with a tie decision
+    tie_H: float = 0.0                # bound on |dH|_F from their other outcomes
+    tie_g: np.ndarray | None = None   # bound on |dg| per component
+    tie_E: float = 0.0                # bound on |dE|
+    pix: np.ndarray | None = None     # N x 2 (v, u): the current-level pixel of each row
+    ref: np.ndarray | None = None     # N x 2 (v, u): the associated render pixel (geometric rows)
 
 
-def geometric_rows(level: Level, ref_depth32: np.ndarray, ref_normals32: np.ndarray, K_ref, dT: np.ndarray,
-                   eps: float, z_min: float, sim3: bool) -> Rows:
-    """Point-to-plane rows (Eq. geometric_ICP, Eq. ICP_geometric_dx, Eq. sim3_derivative,
-    Eq. ICP_weight) for the pixels of one pyramid level."""
-    z32 = level.d32
-    p32 = _backproject32(z32, level.K)
-    x32 = _transform32(dT, p32)
-    Hr, Wr = ref_depth32.shape
-    valid = z32 > 0
-    with np.errstate(divide="ignore", invalid="ignore"):
-        zpos = x32[..., 2] > 0
-        uf = ((x32[..., 0] / x32[..., 2]).astype(F32) * F32(K_ref.fx)).astype(F32) + F32(K_ref.cx)
-        vf = ((x32[..., 1] / x32[..., 2]).astype(F32) * F32(K_ref.fy)).astype(F32) + F32(K_ref.cy)
-        ur = np.floor((uf + F32(0.5)).astype(F32))
-        vr = np.floor((vf + F32(0.5)).astype(F32))
-    inb = valid & zpos & (ur >= 0) & (vr >= 0) & (ur < Wr) & (vr < Hr)
-    ui = np.where(inb, ur, 0).astype(np.int64)
-    vi = np.where(inb, vr, 0).astype(np.int64)
-    dr32 = np.where(inb, ref_depth32[vi, ui], F32(0))
-    ok = inb & (dr32 > 0)
-    ar = ((ui.astype(F32) - F32(K_ref.cx)) / F32(K_ref.fx)).astype(F32)
-    br = ((vi.astype(F32) - F32(K_ref.cy)) / F32(K_ref.fy)).astype(F32)
-    q32 = np.stack([(dr32 * ar).astype(F32), (dr32 * br).astype(F32), dr32], axis=-1)
-    e = (q32 - x32).astype(F32)
-    d2 = (((e[..., 0] * e[..., 0]).astype(F32) + (e[..., 1] * e[..., 1]).astype(F32)).astype(F32)
-          + (e[..., 2] * e[..., 2]).astype(F32)).astype(F32)
-    ok &= d2 <= F32(eps) * F32(eps)
-    # values in double
-    idx = np.nonzero(ok)
-    p = _backproject64(level.d64, level.K)[idx]
-    x = p @ dT[:3, :3].T + dT[:3, 3]
-    dr = dr32[idx].astype(np.float64)
-    uu, vv = ui[idx].astype(np.float64), vi[idx].astype(np.float64)
-    q = np.stack([dr * ((uu - K_ref.cx) / K_ref.fx), dr * ((vv - K_ref.cy) / K_ref.fy), dr], axis=-1)
-    n = ref_normals32[vi[idx], ui[idx], :3].astype(np.float64)
+def _contrib(J, r, w):
+    """(w J J^T, w J r, w r^2) of single rows; J: k x d."""
+    return w[:, None, None] * J[:, :, None] * J[:, None, :], (w * r)[:, None] * J, w * r * r
+
+
+def _geo_row(x, q, n, z, z_min, sim3):
     r = np.einsum("ij,ij->i", q - x, n)
     cols = [-n, -np.cross(x, n)]
     if sim3:
         cols.append(-np.einsum("ij,ij->i", n, x)[:, None])
     J = np.concatenate(cols, axis=1)
-    z = level.d64[idx]
     w = 1.0 / (z + (1.0 - z_min)) ** 2
-    return Rows(J, r, w, J.shape[0], 0)
+    return J, r, w
+
+
+def geometric_rows(level: Level, ref_depth32: np.ndarray, ref_normals32: np.ndarray, K_ref, dT: np.ndarray,
+                   eps: float, z_min: float, sim3: bool) -> Rows:
+    """Point-to-plane rows (Eq. geometric_ICP, Eq. ICP_geometric_dx, Eq. sim3_derivative,
+    Eq. ICP_weight) for the pixels of one pyramid level: x = dT p is projected with the
+    render intrinsics and rounded to the nearest pixel q (reading C11); the row exists when
+    both depths are valid and |q - x| <= eps."""
+    z = level.d64
+    p = _backproject64(z, level.K)
+    x = p @ dT[:3, :3].T + dT[:3, 3]
+    Hr, Wr = ref_depth32.shape
+    dref = ref_depth32.astype(np.float64)
+    nref = ref_normals32[..., :3].astype(np.float64)
+    valid = z > 0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        zpos = x[..., 2] > 0
+        uf = (x[..., 0] / x[..., 2]) * K_ref.fx + K_ref.cx
+        vf = (x[..., 1] / x[..., 2]) * K_ref.fy + K_ref.cy
+        ur, ua = _round_alt(np.where(zpos, uf, -1e9))
+        vr, va = _round_alt(np.where(zpos, vf, -1e9))
+
+    def assoc(uu, vv):
+        inb = valid & zpos & (uu >= 0) & (vv >= 0) & (uu < Wr) & (vv < Hr)
+        ui = np.where(inb, uu, 0).astype(np.int64)
+        vi = np.where(inb, vv, 0).astype(np.int64)
+        dr = np.where(inb, dref[vi, ui], 0.0)
+        q = np.stack([dr * ((ui - K_ref.cx) / K_ref.fx), dr * ((vi - K_ref.cy) / K_ref.fy), dr], axis=-1)
+        dist = np.linalg.norm(q - x, axis=-1)
+        ok = inb & (dr > 0)
+        return ok & (dist <= eps), ok & (np.abs(dist - eps) < TIE_X), ui, vi, q
+
+    ok, near, ui, vi, q = assoc(ur, vr)
+    idx = np.nonzero(ok)
+    J, r, w = _geo_row(x[idx], q[idx], nref[vi[idx], ui[idx]], z[idx], z_min, sim3)
+    # ties and the bound on what their other outcomes change
+    tie = valid & ((ur != ua) | (vr != va) | near | (np.abs(x[..., 2]) < TIE_X))
+    dim = 7 if sim3 else 6
+    tie_H, tie_g, tie_E = 0.0, np.zeros(dim), 0.0
+    tix = np.nonzero(tie)
+    if tix[0].size:
+        rows_now = np.zeros((tix[0].size, dim, dim)), np.zeros((tix[0].size, dim)), np.zeros(tix[0].size)
+        sel = ok[tix]
+        if sel.any():
+            t2 = (tix[0][sel], tix[1][sel])
+            Jt, rt, wt = _geo_row(x[t2], q[t2], nref[vi[t2], ui[t2]], z[t2], z_min, sim3)
+            cH, cg, cE = _contrib(Jt, rt, wt)
+            rows_now[0][sel], rows_now[1][sel], rows_now[2][sel] = cH, cg, cE
+        dH = np.linalg.norm(rows_now[0], axis=(1, 2))  # the "no row" outcome
+        dg = np.abs(rows_now[1])
+        dE = np.abs(rows_now[2])
+        for uu, vv in ((ua, vr), (ur, va), (ua, va)):
+            okc, nearc, uic, vic, qc = assoc(uu, vv)
+            cand = (okc | nearc)[tix]
+            if not cand.any():
+                continue
+            t2 = (tix[0][cand], tix[1][cand])
+            Jc, rc, wc = _geo_row(x[t2], qc[t2], nref[vic[t2], uic[t2]], z[t2], z_min, sim3)
+            cH, cg, cE = _contrib(Jc, rc, wc)
+            dH[cand] = np.maximum(dH[cand], np.linalg.norm(cH - rows_now[0][cand], axis=(1, 2)))
+            dg[cand] = np.maximum(dg[cand], np.abs(cg - rows_now[1][cand]))
+            dE[cand] = np.maximum(dE[cand], np.abs(cE - rows_now[2][cand]))
+        tie_H, tie_g, tie_E = float(dH.sum()), dg.sum(0), float(dE.sum())
+    return Rows(J, r, w, J.shape[0], 0, int(tix[0].size), tie_H, tie_g, tie_E,
+                np.stack(idx, -1), np.stack([vi[idx], ui[idx]], -1))
 
 
 def bilinear(img: np.ndarray, u: np.ndarray, v: np.ndarray) -> np.ndarray:
@@ -224,53 +253,62 @@ def photometric_rows(level: Level, kf_I: np.ndarray, K_kf, T_rs: np.ndarray, dT:
     """Frame-to-keyframe photometric rows (Eq. keyframe_icp, Eq. combined_icp).
 
     kf_I: keyframe intensity at this level; K_kf: its intrinsics; T_rs: transform
-    from the render camera frame to the keyframe camera frame."""
-    z32 = level.d32
-    p32 = _backproject32(z32, level.K)
-    x32 = _transform32(dT, p32)
-    Rf = T_rs[:3, :3].astype(F32)
-    tf = T_rs[:3, 3].astype(F32)
-    y32 = np.stack([(((Rf[a, 0] * x32[..., 0]).astype(F32) + (Rf[a, 1] * x32[..., 1]).astype(F32)).astype(F32)
-                     + (Rf[a, 2] * x32[..., 2]).astype(F32) + tf[a]).astype(F32) for a in range(3)], axis=-1)
-    Hk, Wk = kf_I.shape
-    valid = z32 > 0
-    with np.errstate(divide="ignore", invalid="ignore"):
-        zpos = y32[..., 2] > 0
-        uk = ((y32[..., 0] / y32[..., 2]).astype(F32) * F32(K_kf.fx)).astype(F32) + F32(K_kf.cx)
-        vk = ((y32[..., 1] / y32[..., 2]).astype(F32) * F32(K_kf.fy)).astype(F32) + F32(K_kf.cy)
-    ok = valid & zpos & (uk >= 1) & (vk >= 1) & (uk < Wk - 2) & (vk < Hk - 2)
-    idx = np.nonzero(ok)
-    p = _backproject64(level.d64, level.K)[idx]
+    from the render camera frame to the keyframe camera frame. A row exists where the
+    point projects into [1, W - 2) x [1, H - 2) of the keyframe (the bilinear taps of the
+    central-difference gradient stay inside) and |r| <= thr."""
+    z = level.d64
+    p = _backproject64(z, level.K)
     x = p @ dT[:3, :3].T + dT[:3, 3]
     y = x @ T_rs[:3, :3].T + T_rs[:3, 3]
-    # sampling position in double; the single-precision path only decided the bounds
-    us = K_kf.fx * y[:, 0] / y[:, 2] + K_kf.cx
-    vs = K_kf.fy * y[:, 1] / y[:, 2] + K_kf.cy
-    us = np.clip(us, 1.0, Wk - 2 - 1e-9)
-    vs = np.clip(vs, 1.0, Hk - 2 - 1e-9)
+    Hk, Wk = kf_I.shape
+    valid = z > 0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        zpos = y[..., 2] > 0
+        uk = np.where(zpos, K_kf.fx * y[..., 0] / y[..., 2] + K_kf.cx, -1e9)
+        vk = np.where(zpos, K_kf.fy * y[..., 1] / y[..., 2] + K_kf.cy, -1e9)
+    inb = valid & zpos & (uk >= 1) & (vk >= 1) & (uk < Wk - 2) & (vk < Hk - 2)
+    tie_b = valid & ((np.abs(uk - 1) < TIE_PX) | (np.abs(vk - 1) < TIE_PX) | (np.abs(uk - (Wk - 2)) < TIE_PX)
+                     | (np.abs(vk - (Hk - 2)) < TIE_PX) | (np.abs(y[..., 2]) < TIE_X))
     gx, gy = grad_image(kf_I)
+    # sample every pixel that is inside or a bound tie (clamped so the taps exist)
+    cand = inb | tie_b
+    idx = np.nonzero(cand)
+    us = np.clip(uk[idx], 1.0, Wk - 2 - 1e-9)
+    vs = np.clip(vk[idx], 1.0, Hk - 2 - 1e-9)
     Ik = bilinear(kf_I, us, vs)
     gxs = bilinear(gx, us, vs)
     gys = bilinear(gy, us, vs)
     r = level.I[idx] - Ik
-    keep = np.abs(r) <= thr
-    y, x, r, gxs, gys = y[keep], x[keep], r[keep], gxs[keep], gys[keep]
-    z = level.d64[idx][keep]
-    X, Y, Z = y[:, 0], y[:, 1], y[:, 2]
-    # d(pi)/dy in pixels, rows (u, v)
-    dpi = np.zeros((y.shape[0], 2, 3))
-    dpi[:, 0, 0] = K_kf.fx / Z
-    dpi[:, 0, 2] = -K_kf.fx * X / Z ** 2
-    dpi[:, 1, 1] = K_kf.fy / Z
-    dpi[:, 1, 2] = -K_kf.fy * Y / Z ** 2
-    gI = np.stack([gxs, gys], axis=-1)                      # N x 2
-    a = -np.einsum("ni,nij->nj", gI, dpi) @ T_rs[:3, :3]    # N x 3  (d r / d x in render frame)
-    cols = [a, np.cross(x, a)]                               # a . (-x^ e_k) = (x x a)_k
-    if sim3:
-        cols.append(np.einsum("ij,ij->i", a, x)[:, None])
-    J = np.concatenate(cols, axis=1)
-    w = lam / (z + (1.0 - z_min)) ** 2
-    return Rows(J, r, w, 0, J.shape[0])
+    tie_r = np.abs(np.abs(r) - thr) < 1e-6 + TIE_PX * np.hypot(gxs, gys)
+    keep_all = inb[idx] & (np.abs(r) <= thr)
+    tie_all = tie_b[idx] | tie_r
+
+    def rows(sel):
+        yy, xx, rr, gxx, gyy = y[idx][sel], x[idx][sel], r[sel], gxs[sel], gys[sel]
+        zz = z[idx][sel]
+        X, Y, Z = yy[:, 0], yy[:, 1], yy[:, 2]
+        # d(pi)/dy in pixels, rows (u, v)
+        dpi = np.zeros((yy.shape[0], 2, 3))
+        dpi[:, 0, 0] = K_kf.fx / Z
+        dpi[:, 0, 2] = -K_kf.fx * X / Z ** 2
+        dpi[:, 1, 1] = K_kf.fy / Z
+        dpi[:, 1, 2] = -K_kf.fy * Y / Z ** 2
+        gI = np.stack([gxx, gyy], axis=-1)                      # N x 2
+        a = -np.einsum("ni,nij->nj", gI, dpi) @ T_rs[:3, :3]    # N x 3  (d r / d x in render frame)
+        cols = [a, np.cross(xx, a)]                              # a . (-x^ e_k) = (x x a)_k
+        if sim3:
+            cols.append(np.einsum("ij,ij->i", a, xx)[:, None])
+        return np.concatenate(cols, axis=1), rr, lam / (zz + (1.0 - z_min)) ** 2
+
+    J, rr, w = rows(keep_all)
+    dim = 7 if sim3 else 6
+    tie_H, tie_g, tie_E = 0.0, np.zeros(dim), 0.0
+    if tie_all.any():
+        Jt, rt, wt = rows(tie_all)
+        cH, cg, cE = _contrib(Jt, rt, wt)
+        tie_H, tie_g, tie_E = float(np.linalg.norm(cH, axis=(1, 2)).sum()), np.abs(cg).sum(0), float(np.abs(cE).sum())
+    pix = np.stack([idx[0][keep_all], idx[1][keep_all]], -1)
+    return Rows(J, rr, w, 0, J.shape[0], int(tie_all.sum()), tie_H, tie_g, tie_E, pix, None)
 
 
 def normal_equations(rows: list[Rows]):
@@ -283,6 +321,15 @@ def normal_equations(rows: list[Rows]):
     E = float(np.sum(w * r * r))
     n = int(sum(x.n_geo + x.n_photo for x in rows))
     return H, g, E, n
+
+
+def tie_bounds(rows: list[Rows]):
+    """(tie pixels, bound on |dH|_F, bound on |dg| per component, bound on |dE|) of the rows' ties."""
+    g = None
+    for x in rows:
+        if x.tie_g is not None:
+            g = x.tie_g.copy() if g is None else g + x.tie_g
+    return (sum(x.n_tie for x in rows), sum(x.tie_H for x in rows), g, sum(x.tie_E for x in rows))
 
 
 DEGENERATE_PIVOT = 1e-10

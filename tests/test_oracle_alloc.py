@@ -32,45 +32,64 @@ def slab_blocks(a, b, bs, origin=(0, 0, 0)):
     return out
 
 
-def boundary_distance(a, b, bs):
-    """Smallest distance of the segment's points (sampled densely) to a block face plane."""
-    ts = np.linspace(0, 1, 2001)[:, None]
-    p = np.asarray(a) + ts * (np.asarray(b) - np.asarray(a))
-    r = np.abs(p / bs - np.round(p / bs)) * bs
-    return float(r.min())
+def sampled_blocks(a, b, bs, n=20001):
+    """Blocks of n points spread evenly along the segment (each lies in its block's closed cube)."""
+    ts = np.linspace(0.0, 1.0, n)[:, None]
+    p = np.asarray(a, np.float64) + ts * (np.asarray(b, np.float64) - np.asarray(a, np.float64))
+    return {tuple(c) for c in np.floor(p / bs).astype(int)}
 
 
-def test_segment_blocks_match_brute_force():
+def _oracle_sets(a, b, bs):
+    cells, met, tie = oracle.segment_blocks(a, b, bs)
+    return ({tuple(c) for c, x in zip(cells, met) if x}, {tuple(c) for c, x in zip(cells, tie) if x})
+
+
+def test_segment_blocks_match_dense_sampling_and_slab_test():
+    """Every point of the segment lies in a met block; a met block that no sample falls in has
+    a chord shorter than the sample spacing (< 1e-5 m), so it must be a tie; the independent
+    half-open slab test agrees except on ties."""
     rng = np.random.default_rng(1)
-    bs = np.float32(0.04)
-    mism = 0
-    for _ in range(3000):
-        a = rng.uniform(-1, 1, 3).astype(np.float32)
+    bs = 0.04
+    nties = 0
+    for _ in range(2000):
+        a = rng.uniform(-1, 1, 3)
         d = rng.normal(size=3)
         d /= np.linalg.norm(d)
-        b = (a + rng.uniform(0.0, 0.12) * d).astype(np.float32)
-        got = {tuple(c) for c in oracle.segment_blocks(a, b, bs)}
-        exp = slab_blocks(a.astype(np.float64), b.astype(np.float64), float(bs))
-        if got != exp:
-            # only admissible where the segment grazes a block boundary within float rounding
-            assert boundary_distance(a, b, float(bs)) < 1e-5, (a, b, got, exp)
-            mism += 1
-    assert mism <= 3
+        b = a + rng.uniform(0.0, 0.12) * d
+        met, tie = _oracle_sets(a, b, bs)
+        samp = sampled_blocks(a, b, bs)
+        assert samp <= met | tie, (a, b)
+        assert met - samp <= tie, (a, b)
+        assert slab_blocks(a, b, bs) ^ met <= tie, (a, b)
+        nties += len(tie)
+    # segments that graze a block boundary within 1e-5 m are rare
+    assert nties < 20
+
+
+def test_segments_on_block_faces_are_ties():
+    """A segment lying in a face plane meets the blocks on both sides; all of them are ties."""
+    bs = 0.04
+    a = np.array([0.04, 0.01, 0.01])
+    b = np.array([0.04, 0.03, 0.01])
+    met, tie = _oracle_sets(a, b, bs)
+    assert met == {(0, 0, 0), (1, 0, 0)} and tie == met
 
 
 def test_axis_parallel_and_degenerate_segments():
-    bs = np.float32(0.04)
-    a = np.array([0.01, 0.01, 0.01], np.float32)
-    assert {tuple(c) for c in oracle.segment_blocks(a, a, bs)} == {(0, 0, 0)}
-    b = np.array([0.13, 0.01, 0.01], np.float32)
-    assert {tuple(c) for c in oracle.segment_blocks(a, b, bs)} == {(0, 0, 0), (1, 0, 0), (2, 0, 0), (3, 0, 0)}
-    c = np.array([0.01, -0.05, 0.01], np.float32)
-    assert {tuple(x) for x in oracle.segment_blocks(a, c, bs)} == {(0, 0, 0), (0, -1, 0), (0, -2, 0)}
+    bs = 0.04
+    a = np.array([0.01, 0.01, 0.01])
+    assert _oracle_sets(a, a, bs) == ({(0, 0, 0)}, set())
+    b = np.array([0.13, 0.01, 0.01])
+    assert _oracle_sets(a, b, bs) == ({(0, 0, 0), (1, 0, 0), (2, 0, 0), (3, 0, 0)}, set())
+    c = np.array([0.01, -0.05, 0.01])
+    assert _oracle_sets(a, c, bs) == ({(0, 0, 0), (0, -1, 0), (0, -2, 0)}, set())
 
 
 def test_frame_allocation_is_union_of_pixel_segments():
     """The bricks allocated by one frame equal the union over pixels with a normal of
-    (slab-test blocks of [p - tau r, p + tau r]) x (directions the normal belongs to)."""
+    (slab-test blocks of [p - tau r, p + tau r]) x (directions the normal belongs to), computed
+    here from the oracle's preprocessing with this file's own half-open slab test; the two
+    differ only on keys the oracle reports as allocation ties."""
     s = scenes.planes_scene()
     K = scenes.Intrinsics(40, 30, 30.0, 30.0, 19.5, 14.5)
     f = s.render(s.poses[0], K=K, noise=False)
@@ -82,23 +101,22 @@ def test_frame_allocation_is_union_of_pixel_segments():
     R = f.pose[:3, :3]
     t = f.pose[:3, 3]
     expected = set()
-    graze = 0
-    cos_t = np.cos(P.theta)
-    bs = 8 * P.voxel_size
+    cos_t = np.cos(np.float32(P.theta))
+    bs = 8 * float(np.float32(P.voxel_size))
+    tau = float(np.float32(P.truncation))
     for v in range(K.height):
         for u in range(K.width):
             if not pre["nok"][v, u]:
                 continue
-            nw = R @ pre["nd"][v, u]
+            nw = R @ pre["n"][v, u]
             dirs = [D for D in range(6) if (nw[D >> 1] if D % 2 == 0 else -nw[D >> 1]) > cos_t]
-            rv = R @ pre["Pd"][v, u]
+            rv = R @ pre["P"][v, u]
             p = rv + t
             rh = rv / np.linalg.norm(rv)
-            a, b = p - P.truncation * rh, p + P.truncation * rh
+            a, b = p - tau * rh, p + tau * rh
             for c in slab_blocks(a, b, bs):
                 for D in dirs:
                     expected.add((*c, D))
-            graze += boundary_distance(a, b, bs) < 1e-5
     diff = got ^ expected
-    assert len(diff) <= 2 * graze + 2, (len(diff), graze)
-    assert len(got) > 50
+    assert all(m.alloc_tie(*k) >= 0 for k in diff), [k for k in diff if m.alloc_tie(*k) < 0]
+    assert len(diff) <= 4 and len(got) > 50

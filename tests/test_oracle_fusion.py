@@ -44,7 +44,7 @@ def test_plane_normals_exact():
     out = oracle.preprocess(f.depth, s.K, 0.1, 6.0, 0.01)
     m = out["nok"].astype(bool)
     assert m.mean() > 0.9
-    ang = np.arccos(np.clip(np.sum(out["nd"][m] * f.normals[m], -1), -1, 1))
+    ang = np.arccos(np.clip(np.sum(out["n"][m] * f.normals[m], -1), -1, 1))
     assert ang.max() < 2e-4   # limited only by the float32 depth input
 
 

@@ -103,10 +103,14 @@ def test_geometric_jacobian_matches_finite_differences():
             # fixed association: recompute x with the perturbed pose at the same pixels
             rp = icp.geometric_rows(lv, rd, rn, K, icp.exp(e) @ dT, 0.05, 0.1, sim3)
             rm = icp.geometric_rows(lv, rd, rn, K, icp.exp(-e) @ dT, 0.05, 0.1, sim3)
-            if rp.r.shape != rows.r.shape or rm.r.shape != rows.r.shape:
-                continue
-            fd = (rp.r - rm.r) / (2 * h)
-            assert np.allclose(fd, rows.J[:, j], rtol=1e-6, atol=1e-7)
+            # rows whose pixel and association are the same at both perturbed poses
+            key = lambda R: {(a, b, c, d): i for i, (a, b, c, d) in enumerate(np.hstack([R.pix, R.ref]))}
+            kp, km = key(rp), key(rm)
+            both = [(i, kp[k], km[k]) for k, i in key(rows).items() if k in kp and k in km]
+            assert len(both) >= 0.99 * rows.r.shape[0]
+            i0, ip, im = (np.array(x) for x in zip(*both))
+            fd = (rp.r[ip] - rm.r[im]) / (2 * h)
+            assert np.allclose(fd, rows.J[i0, j], rtol=1e-6, atol=1e-7)
 
 
 def test_photometric_jacobian_matches_finite_differences():
@@ -179,11 +183,11 @@ def test_sim3_single_plane_is_degenerate():
     assert out[-1] is False
 
 
-def test_pyramid_single_and_double_precision_agree():
+def test_pyramid_is_the_mean_of_valid_children():
     rng = np.random.default_rng(2)
     d = rng.uniform(0.5, 3.0, size=(48, 64)).astype(np.float32)
     d[rng.random(d.shape) < 0.3] = 0
-    d32, d64 = icp.downsample_depth(d, d.astype(np.float64))
+    d64 = icp.downsample_depth(d.astype(np.float64))
     # brute force mean of valid children
     for v in range(24):
         for u in range(32):
@@ -191,7 +195,6 @@ def test_pyramid_single_and_double_precision_agree():
             c = c[c > 0]
             exp = c.mean() if c.size else 0.0
             assert d64[v, u] == pytest.approx(exp, rel=1e-15)
-            assert d32[v, u] == pytest.approx(exp, rel=1e-6)
 
 
 # ------------------------------------------- Levenberg-Marquardt (Sec. 7) ----
@@ -353,3 +356,42 @@ def test_lm_recovers_depth_scale_in_sim3():
     E = true[:3, :3].T @ R
     assert np.arccos(np.clip((np.trace(E) - 1) / 2, -1, 1)) < 1e-6
     assert np.linalg.norm(dT[:3, 3] - true[:3, 3]) < 1e-6
+
+
+def _photometric_only(cl, kl, K, T_rs, thr=0.1, iters=15):
+    dT = np.eye(4)
+    for l in (2, 1, 0):
+        for _ in range(iters):
+            rows = icp.photometric_rows(cl[l], kl[l].I, K.scaled(l), T_rs, dT, thr, 1.0, 0.1, False)
+            H, g, E, n = icp.normal_equations([rows])
+            xi, ok = icp.solve(H, g)
+            if not ok:
+                return dT
+            dT = icp.exp(xi) @ dT
+    return dT
+
+
+def test_photometric_only_schedule_recovers_known_motion():
+    """Eq. keyframe_icp alone (no geometric rows) on a textured plane seen by a keyframe camera
+    3 deg / 4 cm away from the render camera: Gauss-Newton from the identity recovers the
+    current frame's 1 deg / 1 cm motion to the texture's interpolation limit. This fixes the
+    direction of T_RS (render -> keyframe frame) and the sign of the residual and of its
+    Jacobian: with T_RS inverted the schedule ends centimetres away."""
+    s = scenes.plane_scene()
+    K = scenes.Intrinsics(160, 120, 120.0, 120.0, 79.5, 59.5)
+    T_ref = s.poses[0]
+    rng = np.random.default_rng(11)
+    T_kf = T_ref @ scenes.perturbation(rng, 3.0, 0.04)
+    T_cur = T_ref @ scenes.perturbation(rng, 1.0, 0.01)
+    cur = s.render(T_cur, K=K, noise=False)
+    kf = s.render(T_kf, K=K, noise=False)
+    T_rs = np.linalg.inv(T_kf) @ T_ref
+    true = np.linalg.inv(T_ref) @ T_cur
+    z = oracle.preprocess(cur.depth, K, 0.1, 6.0, 0.02)["z"]
+    cl = icp.pyramid(z, K, 3, cur.rgb)
+    kl = icp.pyramid(z, K, 3, kf.rgb)
+    dT = _photometric_only(cl, kl, K, T_rs)
+    ang = np.arccos(np.clip((np.trace(dT[:3, :3].T @ true[:3, :3]) - 1) / 2, -1, 1))
+    assert np.linalg.norm(dT[:3, 3] - true[:3, 3]) < 2e-4 and ang < np.deg2rad(0.02)
+    wrong = _photometric_only(cl, kl, K, np.linalg.inv(T_rs))
+    assert np.linalg.norm(wrong[:3, 3] - true[:3, 3]) > 5e-3

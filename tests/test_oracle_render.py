@@ -81,7 +81,7 @@ def test_thin_plate_renders_the_visible_side(fi):
     err = d[plate] - ex.depth[plate]
     # the far face lies >= 5 mm behind the near one along the view ray; the few pixels off
     # the near face hit spurious fused surfaces in front of it (err < 0), never the far face
-    assert np.mean(np.abs(err) < 1e-3) > 0.98
+    assert np.mean(np.abs(err) < 1e-3) > 0.99
     assert np.mean(err > 3e-3) < 0.002
 
 
@@ -91,3 +91,74 @@ def test_unobserved_space_is_a_miss():
     s = scenes.tiny_scene(1)
     d, n, c, cok = m.render(s.K, s.poses[0])
     assert np.all(d == 0)
+
+
+def _coloured_plane_scene(colA, colB):
+    """scenes.plane_scene's slab split in two along its first in-plane axis: one half of constant
+    colour colA, the other of constant colour colB (top faces coplanar)."""
+    s = scenes.plane_scene()
+    p = s.prims[0]
+    R = p[8:17].reshape(3, 3)
+    a = R[0]
+    left, right = p.copy(), p.copy()
+    left[2:5] = p[2:5] - 1.5 * a
+    right[2:5] = p[2:5] + 1.5 * a
+    left[5] = right[5] = 1.5
+    left[17:20] = left[20:23] = colA
+    right[17:20] = right[20:23] = colB
+    s.prims = np.stack([left, right])
+    s.extra["split_axis"] = a
+    return s
+
+
+def _fused_colour_plane(colA, colB):
+    s = _coloured_plane_scene(colA, colB)
+    P = oracle.Params(voxel_size=0.01, truncation=0.04)
+    m = oracle.OracleMap(P)
+    for i in range(4):
+        f = s.frame(i)
+        m.integrate(f.depth, f.rgb, s.K, f.pose)
+    T = s.poses[1].copy()
+    T[:3, 3] += np.array([0.01, -0.02, 0.01])
+    return s, P, m, T
+
+
+def test_constant_colour_plane_renders_that_colour():
+    """Eq. color_weight and the colour output of Sec. 4: every voxel of a constant-colour surface
+    holds that colour, so every convex combination of them (trilinear, then over directions)
+    renders exactly it."""
+    col = (37, 150, 211)
+    s, P, m, T = _fused_colour_plane(col, col)
+    d, n, c, cok = m.render(s.K, T)
+    hit = d > 0
+    assert hit.mean() > 0.85 and cok[hit].mean() > 0.8
+    sel = cok > 0
+    assert np.abs(c[sel] - np.array(col, float)).max() < 1e-9
+
+
+def test_two_colour_plane_renders_each_side_and_mixes_only_at_the_seam():
+    """Two coplanar halves of constant colours A and B: a hit farther than tau + 2 voxels from
+    the seam renders exactly its side's colour (colour is fused only within tau of the observed
+    point, the trilinear corners and direction sum reach one voxel further); every rendered
+    colour lies on the segment from A to B (a dropped weight or swapped channel leaves it)."""
+    A, B = np.array((200.0, 30.0, 90.0)), np.array((10.0, 220.0, 140.0))
+    s, P, m, T = _fused_colour_plane(A, B)
+    d, n, c, cok = m.render(s.K, T)
+    sel = cok > 0
+    assert sel.mean() > 0.8
+    K = s.K
+    v, u = np.nonzero(sel)
+    pts = np.stack([(u - K.cx) / K.fx, (v - K.cy) / K.fy, np.ones_like(u, float)], -1) * d[v, u][:, None]
+    side = (pts @ T[:3, :3].T + T[:3, 3]) @ s.extra["split_axis"]
+    far = P.truncation + 2 * P.voxel_size
+    ca, cb = c[v, u][side < -far], c[v, u][side > far]
+    assert len(ca) > 300 and len(cb) > 300
+    assert np.abs(ca - A).max() < 1e-9 and np.abs(cb - B).max() < 1e-9
+    # on the segment A-B: c = A + s (B - A), 0 <= s <= 1, nothing orthogonal to it
+    AB = B - A
+    x = c[v, u] - A
+    sp = x @ AB / (AB @ AB)
+    assert sp.min() > -1e-9 and sp.max() < 1 + 1e-9
+    assert np.abs(x - sp[:, None] * AB).max() < 1e-9
+    mixed = (sp > 1e-6) & (sp < 1 - 1e-6)
+    assert mixed.any() and np.abs(side[mixed]).max() <= far
