@@ -87,6 +87,8 @@ def _load():
             L.om_brick_ties.restype = I
             L.om_alloc_tie.argtypes = [P, I, I, I, I]
             L.om_alloc_tie.restype = I
+            L.om_export.argtypes = [P, ctypes.c_long, ctypes.c_long, P, P, P]
+            L.om_export.restype = ctypes.c_long
             L.om_preprocess.argtypes = [P, I, I, F, F, F, F, F, F, F, P, P, P, P, P, P]
             L.om_preprocess.restype = I
             L.om_segment_blocks.argtypes = [P, P, D, P, P, P, I]
@@ -109,6 +111,10 @@ def _load():
             L.om_set_brick.restype = I
             L.om_render_freespace.argtypes = [P, P, I, I, F, F, F, F, P, ctypes.c_long, P, P]
             L.om_render_freespace.restype = I
+            L.om_render_count.argtypes = [P, P, I, I, F, F, F, F, P, ctypes.c_long, P]
+            L.om_render_count.restype = I
+            L.om_threads.argtypes = [I]
+            L.om_threads.restype = I
             L.om_recycle.argtypes = [P, D]
             L.om_recycle.restype = ctypes.c_int64
             _lib = L
@@ -122,6 +128,11 @@ def _p(a):
 def w_dir(cos_angle: float, theta: float) -> float:
     """Eq. direction_weight (as read: clamp((theta - acos<n,v>) / (2 theta - pi/2), 0, 1))."""
     return _load().om_w_dir(float(cos_angle), float(theta))
+
+
+def threads(n: int = 0) -> int:
+    """Set the oracle's OpenMP thread count (n > 0) and return the count its loops use."""
+    return int(_load().om_threads(int(n)))
 
 
 def preprocess(depth: np.ndarray, K, z_min: float, z_max: float, delta_sup: float) -> dict:
@@ -227,6 +238,18 @@ class OracleMap:
         rc = self._L.om_brick_ties(self._h, int(bx), int(by), int(bz), int(D), _p(out))
         return None if rc != 0 else out
 
+    def export(self, start: int = 0, count: int | None = None):
+        """Bricks [start, start + count) in map order: (coords int32 [n, 4], voxels float64
+        [n, 512, 6] as brick(), ties uint8 [n, 512] as brick_ties())."""
+        nb = self.num_bricks()
+        count = nb - start if count is None else max(0, min(count, nb - start))
+        coords = np.zeros((count, 4), np.int32)
+        vox = np.zeros((count, 512, 6), np.float64)
+        ties = np.zeros((count, 512), np.uint8)
+        if count:
+            self._L.om_export(self._h, int(start), int(count), _p(coords), _p(vox), _p(ties))
+        return coords, vox, ties
+
     def alloc_tie(self, bx, by, bz, D) -> int:
         """First frame whose allocation of (bx, by, bz, D) was a tie, -1 if none was."""
         return int(self._L.om_alloc_tie(self._h, int(bx), int(by), int(bz), int(D)))
@@ -262,6 +285,17 @@ class OracleMap:
     def render(self, K, T_wc, pixels: np.ndarray | None = None):
         """Ray-cast depth (0 = miss), camera-frame normals, colour, colour validity."""
         return self._render(self._L.om_render, K, T_wc, pixels)
+
+    def render_count(self, K, T_wc, pixels: np.ndarray | None = None) -> dict:
+        """Distinct bricks read by the march, block cells whose hash entry it reads, colour voxels
+        entering the outputs, and hits, for a render of the pixels (all if None)."""
+        T = np.ascontiguousarray(T_wc, np.float64)
+        pix = None if pixels is None else np.ascontiguousarray(pixels, np.int32).reshape(-1, 2)
+        n = K.width * K.height if pix is None else pix.shape[0]
+        c = np.zeros(4, np.int64)
+        if self._L.om_render_count(self._h, _p(T), K.width, K.height, K.fx, K.fy, K.cx, K.cy, _p(pix), n, _p(c)) != 0:
+            raise MemoryError("oracle render_count failed")
+        return dict(bricks=int(c[0]), cells=int(c[1]), colour_voxels=int(c[2]), hits=int(c[3]))
 
     def render_freespace(self, K, T_wc, pixels: np.ndarray | None = None):
         """Ray-cast with the free-space combination of Alg. 1: depth (0 = miss), camera-frame

@@ -14,10 +14,9 @@
  * (block, D) key and per voxel) so that a comparison can check that every element on
  * which two implementations disagree is a tie of the oracle. The margins bound the
  * difference between an FP32 and an FP64 evaluation of the quantity:
- *   TIE_N  2e-4    cosines between a pixel normal and an axis or the view ray: FP32
- *                  normals are cross products of back-projected neighbours two pixels
- *                  apart; at 3 m and f = 525 the points carry ~1e-6 m of rounding over
- *                  a 1.1e-2 m baseline (~1e-4 rad)
+ *   TIE_N  2e-5    cosines between a pixel normal and an axis or the view ray: the
+ *                  single-precision rounding of a normal computed in double precision
+ *                  and of the pose's rotation (~1e-7), with a wide margin
  *   TIE_X  1e-5 m  camera- and world-frame coordinates and distances (FP32 keeps ~1e-6 m
  *                  at 8 m), plus TIE_N times the lever arm where a normal multiplies a
  *                  distance
@@ -54,12 +53,18 @@
  *                     hit; the hit is the root of the continuous Phi(t) in that
  *                     bracket, found by bisection to 1e-10 m (an undefined midpoint
  *                     counts as free space); normal and colour are evaluated at the
- *                     root; a miss if the combination weights vanish there
+ *                     root's side of Phi <= 0 (the non-positive end of the final
+ *                     bracket, where Phi is defined: the root itself can sit on the
+ *                     edge of the defined region); a miss if no direction has a
+ *                     combination weight there
  *
  * Build: gcc -O2 -fPIC -shared -fopenmp -ffp-contract=off (see oracle/__init__.py; no contraction,
  * so that x86 and Arm builds give the same bits).
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -67,7 +72,7 @@
 #define ND 6
 #define BLK 8
 #define BVOX 512
-#define TIE_N 2e-4
+#define TIE_N 2e-5
 #define TIE_X 1e-5
 #define TIE_PX 2e-3
 /* bisection of the crossing bracket ends when it is narrower than this (metres along the ray) */
@@ -334,6 +339,28 @@ int om_brick_ties(const omap* m, int bx, int by, int bz, int D, uint8_t* out) {
   if (b < 0) return -1;
   memcpy(out, m->tie + (size_t)b * BVOX, BVOX);
   return 0;
+}
+
+/* Bricks [start, start + count) in map order: coordinates (n x 4: bx, by, bz, D), voxels
+ * (n x 512 x 6, as om_brick_data) and tie flags (n x 512, as om_brick_ties). Returns the number
+ * written. */
+long om_export(const omap* m, long start, long count, int32_t* coords, double* vox, uint8_t* ties) {
+  long n = 0;
+  for (long b = start; b < (long)m->nbricks && n < count; ++b, ++n) {
+    for (int a = 0; a < 4; ++a) coords[4 * n + a] = m->coord[4 * b + a];
+    const ovox* v = m->vox + (size_t)b * BVOX;
+    double* o = vox + (size_t)n * BVOX * 6;
+    for (int i = 0; i < BVOX; ++i) {
+      o[6 * i] = v[i].sdf;
+      o[6 * i + 1] = v[i].w;
+      o[6 * i + 2] = v[i].r;
+      o[6 * i + 3] = v[i].g;
+      o[6 * i + 4] = v[i].b;
+      o[6 * i + 5] = v[i].wc;
+    }
+    memcpy(ties + (size_t)n * BVOX, m->tie + (size_t)b * BVOX, BVOX);
+  }
+  return n;
 }
 
 /* First frame in which the allocation of (bx, by, bz, D) was a tie, -1 if it never was. */
@@ -824,6 +851,19 @@ typedef struct {
   double n[3];
 } dsample;
 
+/* Counting context of om_render_count (per thread; NULL in ordinary renders): the bricks whose
+   voxels the march reads, the block cells whose hash entry it reads, and the colour voxels that
+   enter the outputs. */
+typedef struct {
+  uint8_t* geom;   /* per brick */
+  uint8_t* probe;  /* per brick: set on one brick of each probed block */
+  uint8_t* colvox; /* per voxel (brick * 512 + voxel) */
+} ocount;
+static __thread const ocount* g_cnt = NULL;
+static __thread int g_cnt_out = 0;
+
+static void mark(uint8_t* p) { __atomic_store_n(p, (uint8_t)1, __ATOMIC_RELAXED); }
+
 /* Trilinear sample of direction D at continuous voxel coordinate g (voxel units from the origin). */
 static int trilinear(const omap* m, int D, const double* g, double* phi, double* w, double* wc, double* col) {
   double fl[3], fr[3];
@@ -845,6 +885,7 @@ static int trilinear(const omap* m, int D, const double* g, double* phi, double*
     int bx = (int)floor(vi[0] / 8.0), by = (int)floor(vi[1] / 8.0), bz = (int)floor(vi[2] / 8.0);
     int32_t br = hash_find(m, bx, by, bz, D);
     if (br < 0) return 0;
+    if (g_cnt) mark(g_cnt->geom + br);
     const ovox* vx = m->vox + (size_t)br * BVOX + ((vi[2] - 8 * bz) * 8 + (vi[1] - 8 * by)) * 8 + (vi[0] - 8 * bx);
     if (!(vx->w > 0)) return 0;
     acc_s += wt * vx->sdf;
@@ -920,6 +961,17 @@ static int combine(const omap* m, const double* x, const double* r, combo* out) 
     if (s[D].wc > 0) {
       cw += wcomb;
       for (int a = 0; a < 3; ++a) cacc[a] += wcomb * s[D].col[a];
+      if (g_cnt && g_cnt_out) {
+        /* the 8 colour voxels of direction D that enter the output */
+        for (int q = 0; q < 8; ++q) {
+          int vi[3];
+          for (int a = 0; a < 3; ++a) vi[a] = (int)floor((x[a] - m->origin[a]) / m->h) + ((q >> a) & 1);
+          const int bx = (int)floor(vi[0] / 8.0), by = (int)floor(vi[1] / 8.0), bz = (int)floor(vi[2] / 8.0);
+          const int32_t br = hash_find(m, bx, by, bz, D);
+          if (br >= 0)
+            mark(g_cnt->colvox + (size_t)br * BVOX + ((vi[2] - 8 * bz) * 8 + (vi[1] - 8 * by)) * 8 + (vi[0] - 8 * bx));
+        }
+      }
     }
   }
   if (!any) return 0;
@@ -969,8 +1021,13 @@ int om_eval(const omap* m, const double* x, const double* r, double* info) {
 }
 
 static int cell_has_any(const omap* m, int cx, int cy, int cz) {
-  for (int D = 0; D < ND; ++D)
-    if (hash_find(m, cx, cy, cz, D) >= 0) return 1;
+  for (int D = 0; D < ND; ++D) {
+    const int32_t b = hash_find(m, cx, cy, cz, D);
+    if (b >= 0) {
+      if (g_cnt) mark(g_cnt->probe + b);
+      return 1;
+    }
+  }
   return 0;
 }
 
@@ -1010,8 +1067,8 @@ static int render_pixel(const omap* m, const double* T, double fx, double fy, do
     if (prev_def && prev_phi > 0 && cb.phi <= 0) {
       /* the hit: the root of the continuous Phi(t) in [prev_t, t] (Sec. 4: small steps
          after the regular probing), by bisection; an undefined midpoint counts as free
-         space. Normal and colour at the root; a miss if no direction has a combination
-         weight there (the normal is undefined). */
+         space. Normal and colour at the root's non-positive side (hi, within 1e-10 m),
+         where Phi is defined; a miss if no direction has a combination weight there. */
       double lo = prev_t, hi = t;
       while (hi - lo > ROOT_TOL) {
         const double tm = 0.5 * (lo + hi);
@@ -1023,9 +1080,12 @@ static int render_pixel(const omap* m, const double* T, double fx, double fy, do
           lo = tm;
       }
       const double ts = 0.5 * (lo + hi);
-      const double xs[3] = {o[0] + ts * r[0], o[1] + ts * r[1], o[2] + ts * r[2]};
+      const double xs[3] = {o[0] + hi * r[0], o[1] + hi * r[1], o[2] + hi * r[2]};
       combo ch;
-      if (!(combine(m, xs, r, &ch) && ch.wsum_comb > 0 && ch.ncomb)) return 0;
+      g_cnt_out = 1;
+      const int have = combine(m, xs, r, &ch) && ch.wsum_comb > 0 && ch.ncomb;
+      g_cnt_out = 0;
+      if (!have) return 0;
       *depth = ts / rl;
       for (int a = 0; a < 3; ++a) ncam[a] = T[a] * ch.n[0] + T[4 + a] * ch.n[1] + T[8 + a] * ch.n[2];
       if (ch.col_ok)
@@ -1069,6 +1129,64 @@ int om_render(const omap* m, const double* T_wc, int W, int H, float fx, float f
   return 0;
 }
 
+/*
+ * The algorithmic bytes of a render: render pixels as om_render does (pix NULL: all W*H) and
+ * count the distinct bricks whose voxels the march reads (counts[0]), the distinct allocated
+ * block cells whose hash entry it reads (counts[1]), the distinct colour voxels that enter the
+ * outputs (counts[2]) and the hits (counts[3]).
+ */
+int om_render_count(const omap* m, const double* T_wc, int W, int H, float fx, float fy, float cx, float cy,
+                    const int32_t* pix, long npix, int64_t* counts) {
+  ocount c;
+  c.geom = (uint8_t*)calloc(m->nbricks + 1, 1);
+  c.probe = (uint8_t*)calloc(m->nbricks + 1, 1);
+  c.colvox = (uint8_t*)calloc((m->nbricks + 1) * BVOX, 1);
+  if (!c.geom || !c.probe || !c.colvox) {
+    free(c.geom);
+    free(c.probe);
+    free(c.colvox);
+    return -1;
+  }
+  long n = pix ? npix : (long)W * H;
+  int64_t hits = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : hits)
+  for (long i = 0; i < n; ++i) {
+    g_cnt = &c;
+    int u = pix ? pix[2 * i] : (int)(i % W);
+    int v = pix ? pix[2 * i + 1] : (int)(i / W);
+    double d = 0, nc[3], col[3];
+    int cok = 0;
+    hits += render_pixel(m, T_wc, fx, fy, cx, cy, u, v, &d, nc, col, &cok);
+    g_cnt = NULL;
+  }
+  int64_t ng = 0, np = 0, nc = 0;
+  for (size_t b = 0; b < m->nbricks; ++b) {
+    ng += c.geom[b];
+    np += c.probe[b];
+  }
+  for (size_t i = 0; i < m->nbricks * BVOX; ++i) nc += c.colvox[i];
+  counts[0] = ng;
+  counts[1] = np;
+  counts[2] = nc;
+  counts[3] = hits;
+  free(c.geom);
+  free(c.probe);
+  free(c.colvox);
+  return 0;
+}
+
+/* Threads of the oracle's parallel loops (OpenMP); 0 keeps the current setting. Returns the
+   number that the next parallel loop will use. */
+int om_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 /* ====================================================== combined TSDF (Sec. 4, Sec. 7) */
 /*
  * View-dependent combined TSDF. Sec. 4: the combined SDF can be pre-computed for every voxel of
@@ -1085,7 +1203,7 @@ int om_render(const omap* m, const double* T_wc, int W, int H, float fx, float f
  *   frustum, which hold every voxel a ray of that view reads).
  *   ray-cast: the rules of the direct render (samples at t = k h/2, the first pair of
  *   consecutive defined samples with Phi > 0 >= Phi, bisection to the root of Phi(t) in
- *   that bracket, outputs at the root) with Phi the trilinear interpolation of the combined values
+ *   that bracket, outputs at its non-positive side) with Phi the trilinear interpolation of the combined values
  *   (defined if all 8 corners are), the normal the central difference of that field at +-h
  *   (defined if the 6 offset samples are, norm > 1e-12) and the colour the trilinear
  *   interpolation of the combined colours (where all 8 corners have one).
@@ -1339,7 +1457,7 @@ static int render_pixel_comb(const omap* m, const double* T, double fx, double f
           lo = tm;
       }
       const double ts = 0.5 * (lo + hi);
-      const double xs[3] = {o[0] + ts * r[0], o[1] + ts * r[1], o[2] + ts * r[2]};
+      const double xs[3] = {o[0] + hi * r[0], o[1] + hi * r[1], o[2] + hi * r[2]};
       csample ch;
       if (!(comb_eval(m, xs, &ch) && ch.has_n)) return 0;
       *depth = ts / rl;
@@ -1430,7 +1548,7 @@ int om_set_brick(omap* m, int bx, int by, int bz, int D, const double* vox) {
  *  - the value is the fused-weight average of Phi^D over F (free space) or O (occupied);
  *    undefined when that set is empty.
  * The march and the root (bisection in the first Phi > 0 >= Phi bracket) are those of the
- * direct render (reading of Sec. 4); the normal, at the root, is the normalised fused-weight
+ * direct render (reading of Sec. 4); the normal, at the root's non-positive side, is the normalised fused-weight
  * sum of the chosen set's normals. No colour.
  */
 typedef struct {
@@ -1546,7 +1664,7 @@ static int render_pixel_fs(const omap* m, const double* T, double fx, double fy,
     gdef[i] = fs_value(m, o, r, &G[i * ND], t, G, gt, i - 1, &gphi[i], &gn[3 * i]);
     if (!(i > 0 && gdef[i - 1] && gdef[i] && gphi[i - 1] > 0 && gphi[i] <= 0)) continue;
     /* the root in [t_{i-1}, t_i] by bisection (an undefined midpoint counts as free space);
-       the normal is the fused-weight normal sum at the root */
+       the normal is the fused-weight normal sum at the root's non-positive side */
     double lo = gt[i - 1], hi = t;
     while (hi - lo > ROOT_TOL) {
       const double tm = 0.5 * (lo + hi);
@@ -1561,11 +1679,11 @@ static int render_pixel_fs(const omap* m, const double* T, double fx, double fy,
     }
     const double ts = 0.5 * (lo + hi);
     {
-      const double xs[3] = {o[0] + ts * r[0], o[1] + ts * r[1], o[2] + ts * r[2]};
+      const double xs[3] = {o[0] + hi * r[0], o[1] + hi * r[1], o[2] + hi * r[2]};
       fsamp P[ND];
       fs_all(m, xs, P);
       double ps, nr[3];
-      if (fs_value(m, o, r, P, ts, G, gt, i - 1, &ps, nr) && (nr[0] != 0 || nr[1] != 0 || nr[2] != 0)) {
+      if (fs_value(m, o, r, P, hi, G, gt, i - 1, &ps, nr) && (nr[0] != 0 || nr[1] != 0 || nr[2] != 0)) {
         const double ln = sqrt(nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2]);
         *depth = ts / rl;
         for (int a = 0; a < 3; ++a) ncam[a] = (T[a] * nr[0] + T[4 + a] * nr[1] + T[8 + a] * nr[2]) / ln;
