@@ -308,18 +308,18 @@ DTSDF_API dtsdf_status dtsdf_icp_solve(dtsdf_icp icp, const dtsdf_render_out* re
 
 /* One Gauss-Newton iteration of geometric point-to-plane ICP (SE(3) or Sim(3)) that allocates
  * no device memory. The paper has no counterpart: this serves callers that cannot allocate when
- * they run ICP - inside CUDA stream capture (cudaMalloc is not allowed there), in real-time loops
- * where cudaMalloc's implicit device synchronisation would stall other streams, or under a host
- * application that owns all device memory. Every input and output is a caller-owned device
+ * they run ICP - real-time loops where cudaMalloc's implicit device synchronisation would stall
+ * other streams, or a host application that owns all device memory. Every input and output is a caller-owned device
  * buffer: depth (K_cur->height x K_cur->width float32, already outlier-filtered, 0 invalid),
  * ref (the render's normals, float4 with the depth in w; K_ref its intrinsics), T_rel_dev
  * (16 doubles, current -> render camera, read and updated in place unless degenerate) and
  * stats_dev (one dtsdf_icp_stats, overwritten). The reduction's scratch is a fixed file-scope
  * device array of 256 KB that every GPU loading the library keeps until exit; images of more
  * than 1048576 pixels are rejected (DTSDF_ERR_INVALID_ARG). The first call on a device looks up
- * that array's device address (cudaGetSymbolAddress) and should be made before any stream
- * capture. All calls share the scratch and it keeps the last call's contents; calls that
- * overlap on the GPU race on it. Asynchronous on `stream`. */
+ * that array's device address (cudaGetSymbolAddress) and keeps it, so that first call should be
+ * made before any stream capture, and the library must not be used across cudaDeviceReset. All
+ * calls share the scratch and it keeps the last call's contents; calls that overlap on the GPU
+ * race on it. Asynchronous on `stream`. */
 DTSDF_API dtsdf_status dtsdf_icp_step_noalloc(const float* depth, const dtsdf_intrinsics* K_cur,
                                               const dtsdf_render_out* ref, const dtsdf_intrinsics* K_ref,
                                               int32_t sim3, float eps, float z_min, int32_t min_rows,
@@ -450,8 +450,9 @@ DTSDF_API dtsdf_status dtsdf_server_create(const dtsdf_map* maps, int32_t n_maps
 DTSDF_API dtsdf_status dtsdf_server_submit(dtsdf_server s, const dtsdf_request* r, uint64_t* seq);
 
 /* Move up to cap completed results, oldest completion first, into out (host); *n receives the
- * count. Waits up to wait_us microseconds when none is ready. DTSDF_ERR_CUDA if a batch failed
- * on the device (message in dtsdf_last_error). */
+ * count. Waits up to wait_us microseconds when none is ready; DTSDF_ERR_TIMEOUT (with *n = 0)
+ * when that wait runs out with no result (wait_us = 0 never waits and returns DTSDF_OK).
+ * DTSDF_ERR_CUDA if a batch failed on the device (message in dtsdf_last_error). */
 DTSDF_API dtsdf_status dtsdf_server_poll(dtsdf_server s, dtsdf_result* out, int32_t cap, int32_t* n,
                                          int32_t wait_us);
 
@@ -568,6 +569,15 @@ DTSDF_API const char* dtsdf_last_error(void);
 
 /* Library version string. */
 DTSDF_API const char* dtsdf_version(void);
+
+/* Device and pinned host allocations the library holds right now (maps, registration contexts,
+ * servers and their buffers; stream-ordered scratch is not counted). The paper has no
+ * counterpart: a diagnostic for error paths. Every create call that fails (for instance under
+ * the allocation-failure injection: with the environment variable DTSDF_FAIL_ALLOC set to N,
+ * the N-th allocation of a dtsdf_create, dtsdf_icp_create or dtsdf_server_create call, counted
+ * from 0, and every later one fails as if the device were out of memory, and the call returns
+ * DTSDF_ERR_OOM) leaves this count where it was. */
+DTSDF_API int64_t dtsdf_live_allocations(void);
 
 #ifdef __cplusplus
 }

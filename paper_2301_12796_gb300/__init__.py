@@ -137,6 +137,7 @@ SIGNATURES = {
     "dtsdf_combine": ([P, ctypes.POINTER(Intrinsics), P, c_int32, P], c_int32),
     "dtsdf_combine_dev": ([P, ctypes.POINTER(Intrinsics), P, c_int32, P], c_int32),
     "dtsdf_combined_blocks": ([P, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64), P], c_int32),
+    "dtsdf_live_allocations": ([], ctypes.c_int64),
     "dtsdf_set_render_opts": ([P, ctypes.POINTER(RenderOpts)], c_int32),
     "dtsdf_render_tune": ([P, ctypes.POINTER(Intrinsics), P, ctypes.POINTER(RenderOut), ctypes.POINTER(RenderOpts),
                            ctypes.POINTER(ctypes.c_float), P], c_int32),
@@ -616,9 +617,13 @@ class Server:
         return seq.value
 
     def poll(self, cap: int = 64, wait_us: int = 0):
+        """Completed results (at most cap); waits up to wait_us for one. A wait that runs out with
+        no result returns [] (the library reports DTSDF_ERR_TIMEOUT)."""
         out = (Result * max(cap, 1))()
         n = c_int32()
-        check(lib().dtsdf_server_poll(self._h, out, cap, ctypes.byref(n), int(wait_us)), "dtsdf_server_poll")
+        st = lib().dtsdf_server_poll(self._h, out, cap, ctypes.byref(n), int(wait_us))
+        if st != ERR_TIMEOUT:
+            check(st, "dtsdf_server_poll")
         res = [out[i] for i in range(n.value)]
         for r in res:
             self._keep.pop(r.seq, None)

@@ -2,6 +2,7 @@
 // status codes around the kernels of map.cu, render.cu and icp.cu.
 #include <math.h>
 #include <stddef.h>
+#include <stdlib.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -11,6 +12,54 @@
 #include <vector>
 
 #include "internal.h"
+
+namespace dtsdf {
+namespace {
+thread_local int g_alloc_seq = 0;
+std::atomic<int64_t> g_live_allocs{0};
+bool alloc_injected() {
+  const int n = g_alloc_seq++;
+  const char* v = getenv("DTSDF_FAIL_ALLOC");
+  return v && *v && n >= atoi(v);
+}
+}  // namespace
+
+void alloc_hook_begin() { g_alloc_seq = 0; }
+
+cudaError_t dt_malloc(void** p, size_t bytes) {
+  if (alloc_injected()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) ++g_live_allocs;
+  return e;
+}
+
+cudaError_t dt_malloc_host(void** p, size_t bytes) {
+  if (alloc_injected()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  const cudaError_t e = cudaMallocHost(p, bytes);
+  if (e == cudaSuccess) ++g_live_allocs;
+  return e;
+}
+
+cudaError_t dt_free(void* p) {
+  if (!p) return cudaSuccess;
+  --g_live_allocs;
+  return cudaFree(p);
+}
+
+cudaError_t dt_free_host(void* p) {
+  if (!p) return cudaSuccess;
+  --g_live_allocs;
+  return cudaFreeHost(p);
+}
+
+int64_t live_allocations() { return g_live_allocs.load(); }
+}  // namespace dtsdf
 
 using namespace dtsdf;
 
@@ -126,34 +175,34 @@ constexpr uint32_t RENDER_Q_SLOTS = 1024;
 
 static void map_free(dtsdf_map m) {
   if (!m) return;
-  cudaFree(m->v.keys);
-  cudaFree(m->v.vals);
-  cudaFree(m->v.req);
-  cudaFree(m->v.dir_slots);
-  cudaFree(m->v.dir_coord);
-  cudaFree(m->v.geom);
-  cudaFree(m->v.geom16);
-  cudaFree(m->v.col);
-  cudaFree(m->v.col8);
-  cudaFree(m->v.brick_dir);
-  cudaFree(m->v.free_ring);
-  cudaFree(m->v.bound);
-  cudaFree(m->v.stamp);
-  cudaFree(m->v.occ);
-  cudaFree(m->v.counters);
-  cudaFree(m->v.work);
-  cudaFree(m->render_q);
-  cudaFree(m->P);
-  cudaFree(m->N);
-  cudaFree(m->J);
-  cudaFree(m->F);
-  if (m->err_host) cudaFreeHost(m->err_host);
+  dt_free(m->v.keys);
+  dt_free(m->v.vals);
+  dt_free(m->v.req);
+  dt_free(m->v.dir_slots);
+  dt_free(m->v.dir_coord);
+  dt_free(m->v.geom);
+  dt_free(m->v.geom16);
+  dt_free(m->v.col);
+  dt_free(m->v.col8);
+  dt_free(m->v.brick_dir);
+  dt_free(m->v.free_ring);
+  dt_free(m->v.bound);
+  dt_free(m->v.stamp);
+  dt_free(m->v.occ);
+  dt_free(m->v.counters);
+  dt_free(m->v.work);
+  dt_free(m->render_q);
+  dt_free(m->P);
+  dt_free(m->N);
+  dt_free(m->J);
+  dt_free(m->F);
+  if (m->err_host) dt_free_host(m->err_host);
   if (m->err_event) cudaEventDestroy(m->err_event);
   if (m->pool) cudaMemPoolDestroy(m->pool);
-  cudaFree(m->v.comb);
-  cudaFree(m->v.comb_col);
-  cudaFree(m->v.comb_gen);
-  cudaFree(m->comb_state);
+  dt_free(m->v.comb);
+  dt_free(m->v.comb_col);
+  dt_free(m->v.comb_gen);
+  dt_free(m->comb_state);
   delete m;
 }
 
@@ -182,9 +231,12 @@ extern "C" {
 
 const char* dtsdf_last_error(void) { return g_last_error.c_str(); }
 
+int64_t dtsdf_live_allocations(void) { return live_allocations(); }
+
 const char* dtsdf_version(void) { return "dtsdf-gb300 0.1 (sm_103a)"; }
 
 dtsdf_status dtsdf_create(const dtsdf_params* params, void* stream, dtsdf_map* out) {
+  alloc_hook_begin();
   if (!params || !out) return fail(DTSDF_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
   const dtsdf_params& p = *params;
@@ -231,7 +283,7 @@ dtsdf_status dtsdf_create(const dtsdf_params* params, void* stream, dtsdf_map* o
   v.work_cap = v.dir_cap;
   cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, bytes)                                    \
-  if (e == cudaSuccess) e = cudaMalloc((void**)&(ptr), (bytes));
+  if (e == cudaSuccess) e = dt_malloc((void**)&(ptr), (bytes));
   ALLOC(v.keys, sizeof(unsigned long long) * hcap);
   ALLOC(v.vals, sizeof(int32_t) * hcap);
   ALLOC(v.req, sizeof(uint32_t) * hcap);
@@ -253,7 +305,7 @@ dtsdf_status dtsdf_create(const dtsdf_params* params, void* stream, dtsdf_map* o
   ALLOC(v.work, sizeof(int32_t) * (size_t)v.work_cap);
   ALLOC(m->render_q, sizeof(unsigned) * RENDER_Q_SLOTS);
 #undef ALLOC
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&m->err_host, sizeof(uint32_t));
+  if (e == cudaSuccess) e = dt_malloc_host((void**)&m->err_host, sizeof(uint32_t));
   if (e == cudaSuccess) {
     int dev = 0;
     e = cudaGetDevice(&dev);
@@ -322,17 +374,17 @@ dtsdf_status dtsdf_destroy(dtsdf_map map) {
 
 static dtsdf_status ensure_ws(dtsdf_map m, size_t npix) {
   if (m->ws_pixels >= npix) return DTSDF_OK;
-  cudaFree(m->P);
-  cudaFree(m->N);
-  cudaFree(m->J);
-  cudaFree(m->F);
+  dt_free(m->P);
+  dt_free(m->N);
+  dt_free(m->J);
+  dt_free(m->F);
   m->P = m->N = m->F = nullptr;
   m->J = nullptr;
   m->ws_pixels = 0;
-  CK(cudaMalloc((void**)&m->P, sizeof(float4) * npix));
-  CK(cudaMalloc((void**)&m->N, sizeof(float4) * npix));
-  CK(cudaMalloc((void**)&m->J, npix));
-  CK(cudaMalloc((void**)&m->F, sizeof(float4) * npix));
+  CK(dt_malloc((void**)&m->P, sizeof(float4) * npix));
+  CK(dt_malloc((void**)&m->N, sizeof(float4) * npix));
+  CK(dt_malloc((void**)&m->J, npix));
+  CK(dt_malloc((void**)&m->F, sizeof(float4) * npix));
   m->ws_pixels = npix;
   return DTSDF_OK;
 }
@@ -455,17 +507,17 @@ static dtsdf_status ensure_combined(dtsdf_map m, cudaStream_t s) {
   float4* col = nullptr;
   uint32_t* gen = nullptr;
   CombState* st = nullptr;
-  cudaError_t e = cudaMalloc((void**)&comb, sizeof(float2) * CVOX * nd);
-  if (e == cudaSuccess && m->p.color) e = cudaMalloc((void**)&col, sizeof(float4) * CVOX * nd);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&gen, sizeof(uint32_t) * nd);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&st, sizeof(CombState));
+  cudaError_t e = dt_malloc((void**)&comb, sizeof(float2) * CVOX * nd);
+  if (e == cudaSuccess && m->p.color) e = dt_malloc((void**)&col, sizeof(float4) * CVOX * nd);
+  if (e == cudaSuccess) e = dt_malloc((void**)&gen, sizeof(uint32_t) * nd);
+  if (e == cudaSuccess) e = dt_malloc((void**)&st, sizeof(CombState));
   if (e == cudaSuccess) e = cudaMemsetAsync(gen, 0xFF, sizeof(uint32_t) * nd, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(CombState), s);
   if (e != cudaSuccess) {
-    cudaFree(comb);
-    cudaFree(col);
-    cudaFree(gen);
-    cudaFree(st);
+    dt_free(comb);
+    dt_free(col);
+    dt_free(gen);
+    dt_free(st);
     return cuda_fail(e, "combined TSDF allocation");
   }
   m->v.comb = comb;
@@ -635,10 +687,10 @@ dtsdf_status dtsdf_render_touched(dtsdf_map m, const dtsdf_intrinsics* K, const 
   float* depth = nullptr;
   float4* nrm = nullptr;
   float4* col = nullptr;
-  cudaError_t e = cudaMalloc((void**)&flags, nflags);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&depth, sizeof(float) * npix);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&nrm, sizeof(float4) * npix);
-  if (e == cudaSuccess && m->p.color) e = cudaMalloc((void**)&col, sizeof(float4) * npix);
+  cudaError_t e = dt_malloc((void**)&flags, nflags);
+  if (e == cudaSuccess) e = dt_malloc((void**)&depth, sizeof(float) * npix);
+  if (e == cudaSuccess) e = dt_malloc((void**)&nrm, sizeof(float4) * npix);
+  if (e == cudaSuccess && m->p.color) e = dt_malloc((void**)&col, sizeof(float4) * npix);
   if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, nflags, s);
   if (e == cudaSuccess) {
     unsigned* q = render_slot(m);
@@ -670,10 +722,10 @@ dtsdf_status dtsdf_render_touched(dtsdf_map m, const dtsdf_intrinsics* K, const 
     if (counters) memcpy(counters, host + 2 * (size_t)m->v.pool_cap, 8 * sizeof(int64_t));
   }
   delete[] host;
-  cudaFree(flags);
-  cudaFree(depth);
-  cudaFree(nrm);
-  cudaFree(col);
+  dt_free(flags);
+  dt_free(depth);
+  dt_free(nrm);
+  dt_free(col);
   if (e != cudaSuccess) return cuda_fail(e, "render_touched");
   return DTSDF_OK;
 }
@@ -727,8 +779,8 @@ dtsdf_status dtsdf_map_export(dtsdf_map m, int32_t* coords, float* voxels, int64
   if (n == 0) return DTSDF_OK;
   int32_t* dc = nullptr;
   float* dv = nullptr;
-  cudaError_t e = cudaMalloc((void**)&dc, sizeof(int32_t) * 4 * n);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&dv, sizeof(float) * 6 * BVOX * n);
+  cudaError_t e = dt_malloc((void**)&dc, sizeof(int32_t) * 4 * n);
+  if (e == cudaSuccess) e = dt_malloc((void**)&dv, sizeof(float) * 6 * BVOX * n);
   if (e == cudaSuccess) {
     launch_export(m->v, n, dc, dv, num_sms(), s);
     e = cudaGetLastError();
@@ -736,8 +788,8 @@ dtsdf_status dtsdf_map_export(dtsdf_map m, int32_t* coords, float* voxels, int64
   if (e == cudaSuccess) e = cudaMemcpyAsync(coords, dc, sizeof(int32_t) * 4 * n, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(voxels, dv, sizeof(float) * 6 * BVOX * n, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(dc);
-  cudaFree(dv);
+  dt_free(dc);
+  dt_free(dv);
   if (e != cudaSuccess) return cuda_fail(e, "map_export");
   return DTSDF_OK;
 }
@@ -751,8 +803,8 @@ dtsdf_status dtsdf_map_import(dtsdf_map m, const int32_t* coords, const float* v
   cudaStream_t s = (cudaStream_t)stream;
   int32_t* dc = nullptr;
   float* dv = nullptr;
-  cudaError_t e = cudaMalloc((void**)&dc, sizeof(int32_t) * 4 * n);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&dv, sizeof(float) * 6 * BVOX * n);
+  cudaError_t e = dt_malloc((void**)&dc, sizeof(int32_t) * 4 * n);
+  if (e == cudaSuccess) e = dt_malloc((void**)&dv, sizeof(float) * 6 * BVOX * n);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dc, coords, sizeof(int32_t) * 4 * n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dv, voxels, sizeof(float) * 6 * BVOX * n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && m->p.dense_dim <= 0) e = cudaMemsetAsync(m->v.counters + C_WORK, 0, sizeof(uint32_t), s);
@@ -762,8 +814,8 @@ dtsdf_status dtsdf_map_import(dtsdf_map m, const int32_t* coords, const float* v
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(dc);
-  cudaFree(dv);
+  dt_free(dc);
+  dt_free(dv);
   if (e != cudaSuccess) return cuda_fail(e, "map_import");
   uint32_t flags = 0;
   e = cudaMemcpy(&flags, m->v.counters + C_ERR, sizeof(uint32_t), cudaMemcpyDeviceToHost);
@@ -803,22 +855,22 @@ struct dtsdf_icp_s {
 static void icp_free(dtsdf_icp c) {
   if (!c) return;
   for (int l = 0; l < 4; ++l) {
-    cudaFree(c->depth[l]);
-    cudaFree(c->inten[l]);
-    cudaFree(c->kf_tmp[l]);
-    cudaFree(c->kf[l]);
+    dt_free(c->depth[l]);
+    dt_free(c->inten[l]);
+    dt_free(c->kf_tmp[l]);
+    dt_free(c->kf[l]);
   }
-  cudaFree(c->P);
-  cudaFree(c->N);
-  cudaFree(c->F);
-  cudaFree(c->partials);
-  cudaFree(c->pose);
-  cudaFree(c->stats);
-  cudaFree(c->ticket);
-  cudaFree(c->stop);
-  cudaFree(c->lm);
-  if (c->host_pose) cudaFreeHost(c->host_pose);
-  if (c->host_stats) cudaFreeHost(c->host_stats);
+  dt_free(c->P);
+  dt_free(c->N);
+  dt_free(c->F);
+  dt_free(c->partials);
+  dt_free(c->pose);
+  dt_free(c->stats);
+  dt_free(c->ticket);
+  dt_free(c->stop);
+  dt_free(c->lm);
+  if (c->host_pose) dt_free_host(c->host_pose);
+  if (c->host_stats) dt_free_host(c->host_stats);
   delete c;
 }
 
@@ -839,6 +891,7 @@ static Intr level_intr(Intr k, int level) {
 extern "C" {
 
 dtsdf_status dtsdf_icp_create(int32_t max_width, int32_t max_height, int32_t levels, dtsdf_icp* out) {
+  alloc_hook_begin();
   if (!out || max_width < 8 || max_height < 8 || max_width > 16384 || max_height > 16384 || levels < 1 || levels > 4)
     return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
   *out = nullptr;
@@ -851,23 +904,23 @@ dtsdf_status dtsdf_icp_create(int32_t max_width, int32_t max_height, int32_t lev
   const size_t n0 = (size_t)max_width * max_height;
   for (int l = 0; l < levels && e == cudaSuccess; ++l) {
     const size_t n = (size_t)(max_width >> l) * (max_height >> l);
-    e = cudaMalloc((void**)&c->depth[l], sizeof(float) * n);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&c->inten[l], sizeof(float) * n);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&c->kf_tmp[l], sizeof(float) * n);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&c->kf[l], sizeof(float4) * n);
+    e = dt_malloc((void**)&c->depth[l], sizeof(float) * n);
+    if (e == cudaSuccess) e = dt_malloc((void**)&c->inten[l], sizeof(float) * n);
+    if (e == cudaSuccess) e = dt_malloc((void**)&c->kf_tmp[l], sizeof(float) * n);
+    if (e == cudaSuccess) e = dt_malloc((void**)&c->kf[l], sizeof(float4) * n);
   }
   c->grid = num_sms() * 2;
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->P, sizeof(float4) * n0);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->N, sizeof(float4) * n0);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->F, sizeof(float4) * n0);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->partials, sizeof(float) * 64 * c->grid);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->pose, sizeof(double) * 16);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->stats, sizeof(dtsdf_icp_stats));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->ticket, sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->stop, sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->lm, sizeof(LmState));
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->host_pose, sizeof(double) * 16);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->host_stats, sizeof(dtsdf_icp_stats));
+  if (e == cudaSuccess) e = dt_malloc((void**)&c->P, sizeof(float4) * n0);
+  if (e == cudaSuccess) e = dt_malloc((void**)&c->N, sizeof(float4) * n0);
+  if (e == cudaSuccess) e = dt_malloc((void**)&c->F, sizeof(float4) * n0);
+  if (e == cudaSuccess) e = dt_malloc((void**)&c->partials, sizeof(float) * 64 * c->grid);
+  if (e == cudaSuccess) e = dt_malloc((void**)&c->pose, sizeof(double) * 16);
+  if (e == cudaSuccess) e = dt_malloc((void**)&c->stats, sizeof(dtsdf_icp_stats));
+  if (e == cudaSuccess) e = dt_malloc((void**)&c->ticket, sizeof(uint32_t));
+  if (e == cudaSuccess) e = dt_malloc((void**)&c->stop, sizeof(int32_t));
+  if (e == cudaSuccess) e = dt_malloc((void**)&c->lm, sizeof(LmState));
+  if (e == cudaSuccess) e = dt_malloc_host((void**)&c->host_pose, sizeof(double) * 16);
+  if (e == cudaSuccess) e = dt_malloc_host((void**)&c->host_stats, sizeof(dtsdf_icp_stats));
   if (e == cudaSuccess) e = cudaMemset(c->ticket, 0, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(c->stop, 0, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(c->stats, 0, sizeof(dtsdf_icp_stats));
@@ -1085,7 +1138,7 @@ dtsdf_status dtsdf_icp_batch_tune(const dtsdf_icp_problem* problems, int32_t n, 
   double* scratch = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   std::vector<double*> poses((size_t)n);
-  cudaError_t e = cudaMalloc((void**)&scratch, sizeof(double) * 16 * (size_t)n);
+  cudaError_t e = dt_malloc((void**)&scratch, sizeof(double) * 16 * (size_t)n);
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   float bt = 3.4e38f;
@@ -1127,7 +1180,7 @@ dtsdf_status dtsdf_icp_batch_tune(const dtsdf_icp_problem* problems, int32_t n, 
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
-  cudaFree(scratch);
+  dt_free(scratch);
   if (e != cudaSuccess) return cuda_fail(e, "dtsdf_icp_batch_tune");
   if (!(bt < 3.4e38f)) return fail(DTSDF_ERR_CUDA, "no batch shape could be scheduled");
   *best = bb;
@@ -1251,14 +1304,14 @@ dtsdf_status dtsdf_depth_scale(const float* in, float* out, int64_t n, float sca
 dtsdf_status dtsdf_exp(int32_t sim3, const double* xi, double out[16]) {
   if (!xi || !out || (sim3 != 0 && sim3 != 1)) return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
   double* d = nullptr;
-  CK(cudaMalloc((void**)&d, sizeof(double) * 23));
+  CK(dt_malloc((void**)&d, sizeof(double) * 23));
   cudaError_t e = cudaMemcpy(d, xi, sizeof(double) * (sim3 ? 7 : 6), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
     launch_exp(sim3 ? 7 : 6, d, d + 7, 0);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpy(out, d + 7, sizeof(double) * 16, cudaMemcpyDeviceToHost);
-  cudaFree(d);
+  dt_free(d);
   if (e != cudaSuccess) return cuda_fail(e, "dtsdf_exp");
   return DTSDF_OK;
 }

@@ -18,9 +18,10 @@
 // direction, whether a transition (Phi^D <= 0 at t_{k-1}, > 0 at t_k, both present) was seen and
 // whether its point q (the linear root in that pair) was blocked. A refinement point p between
 // t_{k-1} and t_k first checks the pair (t_{k-1}, p), then falls back to the state at t_{k-1}.
-// The crossing is refined as in the direct render (4 regular sub-steps, linear root of the final
-// bracket) and the normal is the normalised fused-weight sum of the chosen set's normals at the
-// grid sample behind the crossing, else the one in front of it, else at the root. No colour.
+// The crossing is refined as in the direct render (bisection on the sign of the value, linear
+// root of the final bracket) and the normal is the normalised fused-weight sum of the chosen
+// set's normals at the final bracket's non-positive end; a miss where that sum vanishes. No
+// colour.
 #include "internal.h"
 
 namespace dtsdf {
@@ -324,39 +325,28 @@ __global__ void __launch_bounds__(FS_THREADS) k_render_freespace(MapView m, Intr
     }
     const Value cur = fs_value(S, pres, hasq, blk);
     if (prev_def && cur.defined && prev_val.phi > 0.0f && cur.phi <= 0.0f) {
-      // refine in [t_{k-1}, t_k]: 4 regular sub-steps, first sub-interval that turns <= 0
+      // the root in [t_{k-1}, t_k]: bisection (an undefined point counts as free space), then
+      // the linear root of the final bracket
       float lo = tprev, hi = t;
       Value vlo = prev_val, vhi = cur;
-      const float dt = (hi - lo) * 0.25f;
-      float prev_t = lo;
-      Value prev_v = prev_val;
 #pragma unroll 1
-      for (int j = 1; j < 4; ++j) {
-        const float tj = lo + (float)j * dt;
-        const Value vj = fs_subpoint<STORE>(m, R, tj, tprev, pphi, ppres, hasq0, blk0);
-        if (vj.defined && vj.phi <= 0.0f) {
-          hi = tj;
-          vhi = vj;
-          break;
+      for (int j = 0; j < REFINE_HALVINGS; ++j) {
+        const float tm = 0.5f * (lo + hi);
+        const Value vm = fs_subpoint<STORE>(m, R, tm, tprev, pphi, ppres, hasq0, blk0);
+        if (vm.defined && vm.phi <= 0.0f) {
+          hi = tm;
+          vhi = vm;
+        } else {
+          lo = tm;
+          vlo = vm;
         }
-        prev_t = tj;
-        prev_v = vj;
       }
-      lo = prev_t;
-      vlo = prev_v;
       const bool da = vlo.defined && vlo.phi > 0.0f, db = vhi.defined && vhi.phi <= 0.0f;
       const float ts = (da && db) ? lo + (hi - lo) * (vlo.phi / (vlo.phi - vhi.phi)) : 0.5f * (lo + hi);
-      // normal: grid sample behind the crossing, else in front of it, else the root
+      // normal at the root's non-positive side (the final bracket's end hi)
       const float* nn = nullptr;
-      Value vr;
-      if (cur.defined && (cur.n[0] != 0.f || cur.n[1] != 0.f || cur.n[2] != 0.f)) {
-        nn = cur.n;
-      } else if (prev_val.defined && (prev_val.n[0] != 0.f || prev_val.n[1] != 0.f || prev_val.n[2] != 0.f)) {
-        nn = prev_val.n;
-      } else {
-        vr = fs_subpoint<STORE>(m, R, ts, tprev, pphi, ppres, hasq0, blk0);
-        if (vr.defined && (vr.n[0] != 0.f || vr.n[1] != 0.f || vr.n[2] != 0.f)) nn = vr.n;
-      }
+      const Value vr = fs_subpoint<STORE>(m, R, hi, tprev, pphi, ppres, hasq0, blk0);
+      if (vr.defined && (vr.n[0] != 0.f || vr.n[1] != 0.f || vr.n[2] != 0.f)) nn = vr.n;
       if (nn) {
         const float ln = sqrtf(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
         const float w0 = nn[0] / ln, w1 = nn[1] / ln, w2 = nn[2] / ln;

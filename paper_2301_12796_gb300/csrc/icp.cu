@@ -27,17 +27,19 @@ __global__ void k_extract_depth(const float4* __restrict__ P, int n, float* __re
   }
 }
 
-__global__ void k_intensity(const uint8_t* __restrict__ rgb, int n, float* __restrict__ I) {
+// Intensity I = (0.299 R + 0.587 G + 0.114 B) / 255 is kept through the pyramid as the integer
+// sum S = 299 R + 587 G + 114 B over the level's 4^l source pixels (at most 255000 * 4^3 < 2^24,
+// so every sum and difference of sums is exact in FP32); a level's intensity is S / (255000 4^l)
+// and its central-difference gradient (S(+1) - S(-1)) / (2 * 255000 4^l), each correctly rounded.
+__global__ void k_intensity(const uint8_t* __restrict__ rgb, int n, float* __restrict__ S) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) {
-    const float r = rgb[3 * i], g = rgb[3 * i + 1], b = rgb[3 * i + 2];
-    I[i] = rdiv(radd(radd(rmul(0.299f, r), rmul(0.587f, g)), rmul(0.114f, b)), 255.0f);
-  }
+  if (i < n) S[i] = (float)(299 * (int)rgb[3 * i] + 587 * (int)rgb[3 * i + 1] + 114 * (int)rgb[3 * i + 2]);
 }
 
-// 2x2 mean of the valid children in the order (0,0), (1,0), (0,1), (1,1); plain 2x2 mean of intensity.
-__global__ void k_down(const float* __restrict__ din, const float* __restrict__ Iin, int Win, int Wout, int Hout,
-                       float* __restrict__ dout, float* __restrict__ Iout) {
+// 2x2 mean of the valid depth children in the order (0,0), (1,0), (0,1), (1,1); 2x2 sum of the
+// intensity sums.
+__global__ void k_down(const float* __restrict__ din, const float* __restrict__ Sin, int Win, int Wout, int Hout,
+                       float* __restrict__ dout, float* __restrict__ Sout) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = blockIdx.y * blockDim.y + threadIdx.y;
   if (u >= Wout || v >= Hout) return;
@@ -52,26 +54,33 @@ __global__ void k_down(const float* __restrict__ din, const float* __restrict__ 
       ++n;
     }
   dout[v * Wout + u] = n ? rdiv(s, (float)n) : 0.0f;
-  if (Iin) Iout[v * Wout + u] = 0.25f * (Iin[i00] + Iin[i00 + 1] + Iin[i00 + Win] + Iin[i00 + Win + 1]);
+  if (Sin) Sout[v * Wout + u] = (Sin[i00] + Sin[i00 + 1]) + (Sin[i00 + Win] + Sin[i00 + Win + 1]);
 }
 
-__global__ void k_down_intensity(const float* __restrict__ Iin, int Win, int Wout, int Hout, float* __restrict__ Iout) {
+__global__ void k_down_intensity(const float* __restrict__ Sin, int Win, int Wout, int Hout, float* __restrict__ Sout) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = blockIdx.y * blockDim.y + threadIdx.y;
   if (u >= Wout || v >= Hout) return;
   const int i00 = (2 * v) * Win + 2 * u;
-  Iout[v * Wout + u] = 0.25f * (Iin[i00] + Iin[i00 + 1] + Iin[i00 + Win] + Iin[i00 + Win + 1]);
+  Sout[v * Wout + u] = (Sin[i00] + Sin[i00 + 1]) + (Sin[i00 + Win] + Sin[i00 + Win + 1]);
 }
 
-// Keyframe level: (I, dI/du, dI/dv, 0) with central differences / 2, zero on the border.
-__global__ void k_kf_grad(const float* __restrict__ I, int W, int H, float4* __restrict__ out) {
+// intensity sums of a level -> intensities (in place)
+__global__ void k_norm_intensity(float* __restrict__ S, int n, float c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) S[i] = rdiv(S[i], c);
+}
+
+// Keyframe level: (I, dI/du, dI/dv, 0) from the intensity sums, central differences / 2, zero on
+// the border.
+__global__ void k_kf_grad(const float* __restrict__ S, int W, int H, float c, float4* __restrict__ out) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = blockIdx.y * blockDim.y + threadIdx.y;
   if (u >= W || v >= H) return;
   const int i = v * W + u;
-  const float gx = (u >= 1 && u < W - 1) ? 0.5f * (I[i + 1] - I[i - 1]) : 0.0f;
-  const float gy = (v >= 1 && v < H - 1) ? 0.5f * (I[i + W] - I[i - W]) : 0.0f;
-  out[i] = make_float4(I[i], gx, gy, 0.0f);
+  const float gx = (u >= 1 && u < W - 1) ? rdiv(S[i + 1] - S[i - 1], 2.0f * c) : 0.0f;
+  const float gy = (v >= 1 && v < H - 1) ? rdiv(S[i + W] - S[i - W], 2.0f * c) : 0.0f;
+  out[i] = make_float4(rdiv(S[i], c), gx, gy, 0.0f);
 }
 
 // ------------------------------------------------------------- FP64 math --
@@ -809,6 +818,9 @@ void launch_icp_batch(const IcpBatchArgs& a, int kahan, int cluster, int threads
 }
 
 // ------------------------------------------------------------ launchers ---
+// scale of the intensity sums of level l: 255000 * 4^l
+static inline float intensity_scale(int l) { return 255000.0f * (float)(1 << (2 * l)); }
+
 void launch_frame_pyramid(const float4* P, const uint8_t* rgb, int levels, const Intr* K, float* const* depth,
                           float* const* inten, cudaStream_t s) {
   const int n0 = K[0].W * K[0].H;
@@ -819,6 +831,11 @@ void launch_frame_pyramid(const float4* P, const uint8_t* rgb, int levels, const
     k_down<<<grd, blk, 0, s>>>(depth[l - 1], rgb ? inten[l - 1] : nullptr, K[l - 1].W, K[l].W, K[l].H, depth[l],
                                rgb ? inten[l] : nullptr);
   }
+  if (rgb)
+    for (int l = 0; l < levels; ++l) {
+      const int n = K[l].W * K[l].H;
+      k_norm_intensity<<<(n + 255) / 256, 256, 0, s>>>(inten[l], n, intensity_scale(l));
+    }
 }
 
 void launch_keyframe_pyramid(const uint8_t* rgb, int levels, const Intr* K, float* const* tmpI, float4* const* kf,
@@ -831,7 +848,7 @@ void launch_keyframe_pyramid(const uint8_t* rgb, int levels, const Intr* K, floa
   }
   for (int l = 0; l < levels; ++l) {
     dim3 blk(32, 8), grd((K[l].W + 31) / 32, (K[l].H + 7) / 8);
-    k_kf_grad<<<grd, blk, 0, s>>>(tmpI[l], K[l].W, K[l].H, kf[l]);
+    k_kf_grad<<<grd, blk, 0, s>>>(tmpI[l], K[l].W, K[l].H, intensity_scale(l), kf[l]);
   }
 }
 

@@ -40,6 +40,19 @@ struct IcpLaunch {
 // Record a message for dtsdf_last_error() and return the status.
 dtsdf_status set_error(dtsdf_status s, const char* msg);
 
+// Device and pinned host allocations of the library go through these. Failure injection for
+// tests of the error paths: with the environment variable DTSDF_FAIL_ALLOC set to N, the N-th
+// allocation (counted from 0) after alloc_hook_begin() on the calling thread, and every later
+// one, fails with cudaErrorMemoryAllocation without allocating.
+// dt_free / dt_free_host release them (null is a no-op), and the library keeps the count of its
+// live allocations for dtsdf_live_allocations().
+void alloc_hook_begin();
+cudaError_t dt_malloc(void** p, size_t bytes);
+cudaError_t dt_malloc_host(void** p, size_t bytes);
+cudaError_t dt_free(void* p);
+cudaError_t dt_free_host(void* p);
+int64_t live_allocations();
+
 // Bilateral input filters (radius 0 = off); layout of dtsdf_filter_opts.
 struct FilterOpts {
   int depth_radius;

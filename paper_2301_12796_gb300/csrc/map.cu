@@ -45,17 +45,22 @@ __global__ void k_filter(const float* __restrict__ depth, Intr K, float zmin, fl
         if (fabsf(rsub(zn, z)) <= dsup) ++support;
       }
     if (support >= 2) {
-      const float a = rdiv(rsub((float)u, K.cx), K.fx);
-      const float b = rdiv(rsub((float)v, K.cy), K.fy);
-      out = make_float4(rmul(z, a), rmul(z, b), z, 1.0f);
+      // Eq. reprojection in double precision, rounded once
+      const double zd = z;
+      out = make_float4((float)(zd * (((double)u - (double)K.cx) / (double)K.fx)),
+                        (float)(zd * (((double)v - (double)K.cy) / (double)K.fy)), z, 1.0f);
     }
   }
   P[i] = out;
 }
 
 // Normals: cross product of the central differences of the back-projected x and y
-// neighbours (Sec. 7), normalised and turned toward the camera. N.w = 1 marks a normal.
-__global__ void k_normals(const float4* __restrict__ P, Intr K, float4* __restrict__ N) {
+// neighbours (Sec. 7), normalised and turned toward the camera. N.w = 1 marks a normal. The
+// cross product of nearby points cancels most of their digits (at grazing incidence a single-
+// precision normal is off by up to ~5e-4 rad), so the points are re-formed from the exact input
+// depths and the normal computed in double precision, then rounded once; it feeds the direction
+// membership and the band tests of allocation and fusion. ifx, ify: 1/fx, 1/fy in double.
+__global__ void k_normals(const float4* __restrict__ P, Intr K, double ifx, double ify, float4* __restrict__ N) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = blockIdx.y * blockDim.y + threadIdx.y;
   if (u >= K.W || v >= K.H) return;
@@ -64,22 +69,27 @@ __global__ void k_normals(const float4* __restrict__ P, Intr K, float4* __restri
   if (u >= 1 && v >= 1 && u < K.W - 1 && v < K.H - 1) {
     const float4 c = P[i], l = P[i - 1], r = P[i + 1], t = P[i - K.W], b = P[i + K.W];
     if (c.w > 0 && l.w > 0 && r.w > 0 && t.w > 0 && b.w > 0) {
-      const float dx0 = rsub(r.x, l.x), dx1 = rsub(r.y, l.y), dx2 = rsub(r.z, l.z);
-      const float dy0 = rsub(b.x, t.x), dy1 = rsub(b.y, t.y), dy2 = rsub(b.z, t.z);
-      float n0 = rsub(rmul(dx1, dy2), rmul(dx2, dy1));
-      float n1 = rsub(rmul(dx2, dy0), rmul(dx0, dy2));
-      float n2 = rsub(rmul(dx0, dy1), rmul(dx1, dy0));
-      const float len = rsqrt_exact(radd(radd(rmul(n0, n0), rmul(n1, n1)), rmul(n2, n2)));
-      if (len > 0.0f) {
-        n0 = rdiv(n0, len);
-        n1 = rdiv(n1, len);
-        n2 = rdiv(n2, len);
-        if (rdot3(n0, n1, n2, c.x, c.y, c.z) > 0.0f) {
+      const double cx = K.cx, cy = K.cy;
+      const double am = ((double)(u - 1) - cx) * ifx, a0 = ((double)u - cx) * ifx, ap = ((double)(u + 1) - cx) * ifx;
+      const double bm = ((double)(v - 1) - cy) * ify, b0 = ((double)v - cy) * ify, bp = ((double)(v + 1) - cy) * ify;
+      const double zl = l.z, zr = r.z, zt = t.z, zb = b.z, zc = c.z;
+      const double dx0 = zr * ap - zl * am, dx1 = zr * b0 - zl * b0, dx2 = zr - zl;
+      const double dy0 = zb * a0 - zt * a0, dy1 = zb * bp - zt * bm, dy2 = zb - zt;
+      double n0 = dx1 * dy2 - dx2 * dy1;
+      double n1 = dx2 * dy0 - dx0 * dy2;
+      double n2 = dx0 * dy1 - dx1 * dy0;
+      const double len = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+      if (len > 0.0) {
+        const double il = 1.0 / len;
+        n0 *= il;
+        n1 *= il;
+        n2 *= il;
+        if (n0 * (zc * a0) + n1 * (zc * b0) + n2 * zc > 0.0) {
           n0 = -n0;
           n1 = -n1;
           n2 = -n2;
         }
-        out = make_float4(n0, n1, n2, 1.0f);
+        out = make_float4((float)n0, (float)n1, (float)n2, 1.0f);
       }
     }
   }
@@ -838,10 +848,10 @@ void launch_preprocess(const float* depth, const Intr& K, float zmin, float zmax
     k_filter<<<grd, blk, 0, s>>>(depth, K, zmin, zmax, dsup, P);
   }
   if (fn) {
-    k_normals<<<grd, blk, 0, s>>>(P, K, tmp);
+    k_normals<<<grd, blk, 0, s>>>(P, K, 1.0 / (double)K.fx, 1.0 / (double)K.fy, tmp);
     k_bilateral_normals<<<grd, blk, 0, s>>>(tmp, K, f->normal_radius, f->normal_sigma_d, f->normal_sigma_r, N);
   } else {
-    k_normals<<<grd, blk, 0, s>>>(P, K, N);
+    k_normals<<<grd, blk, 0, s>>>(P, K, 1.0 / (double)K.fx, 1.0 / (double)K.fy, N);
   }
 }
 

@@ -2,12 +2,11 @@
 // allocates device memory.
 //
 // Who needs this: callers that cannot call cudaMalloc at the moment they want an ICP
-// iteration - code being recorded into a CUDA graph (allocation is not allowed during
-// stream capture), real-time loops where cudaMalloc's implicit synchronisation would stall
-// every other stream on the device, and host applications that hand out all device memory
-// from their own pool and forbid libraries from allocating behind their back. They pass in
-// device buffers for every input and output; the only memory this entry point uses beyond
-// them is the fixed scratch below, which exists as soon as the library is loaded.
+// iteration - real-time loops where cudaMalloc's implicit synchronisation would stall every
+// other stream on the device, and host applications that hand out all device memory from
+// their own pool and forbid libraries from allocating behind their back. They pass in device
+// buffers for every input and output; the only memory this entry point uses beyond them is
+// the fixed scratch below, which exists as soon as the library is loaded.
 //
 // Scratch: the per-CTA partial sums of the reduction, the completion ticket and the stop
 // flag live in one file-scope __device__ array. Every device that loads the library holds
@@ -40,7 +39,9 @@ std::mutex g_setup_mutex;
 void* g_scratch_addr[MAX_DEVICES] = {};
 
 // Device address of the scratch array on the current device (set up once per device, with
-// that device current). The host-side symbol is only a stand-in and must never reach a kernel.
+// that device current, and kept for the life of the library: after cudaDeviceReset the module
+// may load at another address, so the library must not be used across a reset). The host-side
+// symbol is only a stand-in and must never reach a kernel.
 cudaError_t scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -12,10 +12,12 @@
 // whenever they agree (8 voxel reads per direction); the full combination with
 // central-difference gradients (7 trilinear gathers per direction) is computed only where
 // the signs disagree and for the outputs. The reported crossing is the first pair of
-// consecutive defined samples with Phi > 0 >= Phi; it is refined by a scan of 4 regular
-// sub-steps to the first sign change and linear interpolation over the final h/8-wide
-// bracket. The per-block occupancy filters let empty space be crossed without probes, and
-// per-brick lower bounds let cells whose present directions are all positive be jumped.
+// consecutive defined samples with Phi > 0 >= Phi; the hit is the root of Phi(t) in that
+// bracket, found by REFINE_HALVINGS bisection steps on the sign of Phi (an undefined point
+// counts as free space) and linear interpolation over the final bracket (h / 2^17 wide);
+// normal and colour are evaluated at the bracket's non-positive end, where Phi is defined.
+// The per-block occupancy filters let empty space be crossed without probes, and per-brick
+// lower bounds let cells whose present directions are all positive be jumped.
 #include <math.h>
 
 #include "internal.h"
@@ -116,6 +118,10 @@ __device__ __forceinline__ float w_dir_r(float c, float theta, float cos_lo, flo
   return fminf(fmaxf((theta - alpha) / (2.0f * theta - 1.57079632679489662f), 0.0f), 1.0f);
 }
 
+// component a (0..2) of a 3-vector held in registers, by selects: every index stays in range
+// even where the compiler evaluates it ahead of the branch that guards it
+__device__ __forceinline__ float ray_comp(const float v[3], int a) { return a == 0 ? v[0] : (a == 1 ? v[1] : v[2]); }
+
 struct Combined {
   int defined;   // 0 undefined, 1 defined
   float phi;
@@ -175,7 +181,8 @@ __device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, cons
     const float WD = tri(w, fx, fy, fz);
     any = true;
     // fallback weight W^D max(0, <v^D, -r>)
-    const float vr = (D & 1) ? r[D >> 1] : -r[D >> 1];
+    const float rc = ray_comp(r, D >> 1);
+    const float vr = (D & 1) ? rc : -rc;
     const float wf = WD * fmaxf(vr, 0.0f);
     fw += wf;
     facc += wf * phiD;
@@ -284,7 +291,7 @@ __device__ __forceinline__ int sign_fast(const MapView& m, Cell& c, const float 
 #pragma unroll
     for (int q = 0; q < 8; ++q) v0[q] = ld_geom<STORE, COUNT>(m, b0 + coff(q), touched);
     if (D1 >= 0) {
-      const size_t b1 = (size_t)c.slot[D1 * RT_N] * PVOX + lofs;
+      const size_t b1 = (size_t)c.slot[(D1 >= 0 ? D1 : D0) * RT_N] * PVOX + lofs;
 #pragma unroll
       for (int q = 0; q < 8; ++q) v1[q] = ld_geom<STORE, COUNT>(m, b1 + coff(q), touched);
     }
@@ -306,7 +313,8 @@ __device__ __forceinline__ int sign_fast(const MapView& m, Cell& c, const float 
       ++np;
       mn = fminf(mn, phiD);
       mx = fmaxf(mx, phiD);
-      const float vr = (D & 1) ? r[D >> 1] : -r[D >> 1];
+      const float rc = ray_comp(r, D >> 1);
+      const float vr = (D & 1) ? rc : -rc;
       facing |= vr > 0.0f;
     }
   }
@@ -443,9 +451,9 @@ __device__ __forceinline__ Combined full_comb(const MapView& m, const Cell& c, c
   return out;
 }
 
-// One loop, one state machine per lane: marching (MARCH), the regular sub-step scan
-// of the refinement (SCAN), the full evaluations at the final bracket ends (ENDS_A/B) and
-// the output evaluations (OUT) all evaluate the field at one call site of the sign test
+// One loop, one state machine per lane: marching (MARCH), the bisection of the crossing
+// bracket (SCAN), the evaluations at the final bracket ends (ENDS_A/B) and the output
+// evaluation at the root (OUT) all evaluate the field at one call site of the sign test
 // and one of the full combination, so lanes in different phases stay converged. A lane
 // whose ray is finished (DONE) takes the next ray from the launch's work counter at the
 // top of the loop once its refill group has finished. Work items are the pixels of tiles of
@@ -480,10 +488,9 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
   float r[3] = {0.f, 0.f, 0.f}, o[3] = {0.f, 0.f, 0.f}, ri[3] = {0.f, 0.f, 0.f}, rl = 1.f;
   bool prev_def = false;
   float prev_phi = 0.f;
-  int hit_k = -1;
   // refinement state
-  float ta = 0.f, tb = 0.f, a0 = 0.f, dt = 0.f, sprev = 0.f, fa = 0.f, ts = 0.f;
-  int j = 0, out_e = 0;
+  float ta = 0.f, tb = 0.f, fa = 0.f, ts = 0.f;
+  int j = 0;
   bool da = false;
   float out_depth = 0.f;
   float4 out_n = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -550,7 +557,6 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
             it = 0;
             prev_def = false;
             prev_phi = 0.f;
-            hit_k = -1;
             out_depth = 0.f;
             out_n = make_float4(0.f, 0.f, 0.f, 0.f);
             out_c = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -572,13 +578,11 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
       finish |= k > k1;
       t = (float)k * step;
     } else if (state == S_SCAN) {
-      t = a0 + (float)j * dt;
+      t = 0.5f * (ta + tb);
     } else if (state == S_ENDS_A) {
       t = ta;
-    } else if (state == S_ENDS_B) {
-      t = tb;
     } else {
-      t = out_e == 0 ? (float)hit_k * step : (out_e == 1 ? (float)(hit_k - 1) * step : ts);
+      t = tb;  // S_ENDS_B, and S_OUT: the outputs at the bracket's non-positive end
     }
     if (finish) {
       // a miss (or the sample limit): write the zero outputs
@@ -697,14 +701,10 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
         prev_def = false;
         ++k;
       } else if (sg < 0 && prev_def && prev_phi > 0.f) {
-        // crossing between samples k-1 and k: a scan of 4 regular sub-steps
-        hit_k = k;
+        // crossing between samples k-1 and k: bisection of the bracket
         ta = (float)(k - 1) * step;
         tb = (float)k * step;
-        a0 = ta;
-        dt = (tb - ta) * 0.25f;
-        sprev = ta;
-        j = 1;
+        j = 0;
         state = S_SCAN;
       } else {
         prev_def = true;
@@ -712,19 +712,12 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
         ++k;
       }
     } else if (state == S_SCAN) {
-      // an undefined probe counts as free space
-      bool level_done = false;
-      if (sg < 0) {
+      // an undefined midpoint counts as free space
+      if (sg < 0)
         tb = t;
-        level_done = true;
-      } else {
-        sprev = t;
-        level_done = ++j == 4;
-      }
-      if (level_done) {
-        ta = sprev;
-        state = S_ENDS_A;
-      }
+      else
+        ta = t;
+      if (++j == REFINE_HALVINGS) state = S_ENDS_A;
     } else if (state == S_ENDS_A) {
       da = C.defined && C.phi > 0.f;
       fa = C.phi;
@@ -733,13 +726,12 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
       // root: linear interpolation of Phi over the final bracket
       const bool db = C.defined && C.phi <= 0.f;
       ts = (da && db) ? ta + (tb - ta) * fa / (fa - C.phi) : 0.5f * (ta + tb);
-      out_e = 0;
       state = S_OUT;
     } else {
-      // normal and colour at the first grid sample behind the crossing, else at the
-      // sample in front of it, else at the root
+      // normal and colour at the root's non-positive side (the final bracket's end tb, where Phi
+      // is defined); a miss if no direction has a combination weight there
       const float nl = sqrtf(C.n[0] * C.n[0] + C.n[1] * C.n[1] + C.n[2] * C.n[2]);
-      bool done = false;
+      bool done = true;
       if (C.defined && C.wsum > 0.f && nl > 0.f) {
         const Pose32& T = s_pose[jb];
         const float n0 = C.n[0] / nl, n1 = C.n[1] / nl, n2 = C.n[2] / nl;
@@ -750,9 +742,6 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
         out_depth = ts / rl;
         out_n = make_float4(c0, c1, c2, out_depth);
         if (COLOR && C.cw > 0.f) out_c = make_float4(C.rgb[0] / C.cw, C.rgb[1] / C.cw, C.rgb[2] / C.cw, 1.0f);
-        done = true;
-      } else if (++out_e == 3) {
-        done = true;
       }
       if (done) {
         const RenderJob& J = a.job[jb];
@@ -894,6 +883,7 @@ void dispatch_render(const MapView& m, const RenderBatch<NJ>& a, bool col, int c
       if (col) DTSDF_RENDER(DTSDF_STORE_FP32, true, true); else DTSDF_RENDER(DTSDF_STORE_FP32, false, true);
     }
   } else {
+    // the direct ray-cast: the per-lane march
     if (m.storage == DTSDF_STORE_FP16) {
       if (col) DTSDF_RENDER(DTSDF_STORE_FP16, true, false); else DTSDF_RENDER(DTSDF_STORE_FP16, false, false);
     } else {

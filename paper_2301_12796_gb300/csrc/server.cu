@@ -452,6 +452,7 @@ extern "C" {
 
 dtsdf_status dtsdf_server_create(const dtsdf_map* maps, int32_t n_maps, const dtsdf_server_params* params,
                                  dtsdf_server* out) {
+  alloc_hook_begin();
   if (!maps || n_maps < 1 || !params || !out) return set_error(DTSDF_ERR_INVALID_ARG, "server: bad argument");
   *out = nullptr;
   const dtsdf_server_params& p = *params;
@@ -474,8 +475,8 @@ dtsdf_status dtsdf_server_create(const dtsdf_map* maps, int32_t n_maps, const dt
   cudaError_t e = cudaGetDevice(&s->device);
   const size_t npix = (size_t)p.max_width * p.max_height;
   s->host_slot_bytes = align_up(IO_BYTES) + align_up(sizeof(float) * npix);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&s->arena_base, (size_t)p.hbm_budget);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&s->host_base, s->host_slot_bytes * (size_t)p.max_inflight);
+  if (e == cudaSuccess) e = dt_malloc((void**)&s->arena_base, (size_t)p.hbm_budget);
+  if (e == cudaSuccess) e = dt_malloc_host((void**)&s->host_base, s->host_slot_bytes * (size_t)p.max_inflight);
   for (int i = 0; i < p.streams && e == cudaSuccess; ++i)
     e = cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
   for (int i = 0; i < p.streams && e == cudaSuccess; ++i) {
@@ -487,8 +488,8 @@ dtsdf_status dtsdf_server_create(const dtsdf_map* maps, int32_t n_maps, const dt
     for (cudaEvent_t ev : s->events) cudaEventDestroy(ev);
     for (int i = 0; i < p.streams; ++i)
       if (s->streams[i]) cudaStreamDestroy(s->streams[i]);
-    cudaFree(s->arena_base);
-    if (s->host_base) cudaFreeHost(s->host_base);
+    dt_free(s->arena_base);
+    if (s->host_base) dt_free_host(s->host_base);
     delete s;
     return set_error(e == cudaErrorMemoryAllocation ? DTSDF_ERR_OOM : DTSDF_ERR_CUDA, "server: allocation failed");
   }
@@ -539,8 +540,9 @@ dtsdf_status dtsdf_server_submit(dtsdf_server s, const dtsdf_request* r, uint64_
 dtsdf_status dtsdf_server_poll(dtsdf_server s, dtsdf_result* out, int32_t cap, int32_t* n, int32_t wait_us) {
   if (!s || !n || cap < 0 || (cap > 0 && !out) || wait_us < 0) return set_error(DTSDF_ERR_INVALID_ARG, "server: bad argument");
   std::unique_lock<std::mutex> lk(s->mu);
+  bool waited_out = false;
   if (s->done.empty() && wait_us > 0)
-    s->cv_done.wait_for(lk, std::chrono::microseconds(wait_us), [&] { return !s->done.empty(); });
+    waited_out = !s->cv_done.wait_for(lk, std::chrono::microseconds(wait_us), [&] { return !s->done.empty(); });
   int32_t k = 0;
   while (k < cap && !s->done.empty()) {
     out[k++] = s->done.front();
@@ -548,6 +550,7 @@ dtsdf_status dtsdf_server_poll(dtsdf_server s, dtsdf_result* out, int32_t cap, i
   }
   *n = k;
   if (!s->error.empty()) return set_error(DTSDF_ERR_CUDA, s->error.c_str());
+  if (waited_out) return set_error(DTSDF_ERR_TIMEOUT, "server: no result within the wait");
   return DTSDF_OK;
 }
 
@@ -580,8 +583,8 @@ dtsdf_status dtsdf_server_destroy(dtsdf_server s) {
     if (s->streams[i]) cudaStreamDestroy(s->streams[i]);
   }
   for (cudaEvent_t ev : s->events) cudaEventDestroy(ev);
-  cudaFree(s->arena_base);
-  if (s->host_base) cudaFreeHost(s->host_base);
+  dt_free(s->arena_base);
+  if (s->host_base) dt_free_host(s->host_base);
   delete s;
   return DTSDF_OK;
 }

@@ -8,6 +8,7 @@ Tolerances as for the direct render: hit mask >= 99.9 %, depth <= 1e-4 m and nor
 import numpy as np
 import pytest
 
+import angles
 import oracle
 import scenes
 
@@ -43,7 +44,7 @@ def compare(g, o, pix=None):
     hg, ho = dg > 0, do > 0
     both = hg & ho
     derr = np.abs(dg[both] - do[both])
-    nerr = np.arccos(np.clip(np.sum(ng[both][..., :3] * no[both], -1), -1, 1))
+    nerr = angles.between(ng[both][..., :3], no[both])
     cb = both & (cg[..., 3] > 0) & (cok > 0)
     cerr = np.abs(cg[cb][..., :3] - co[cb]).max() if cb.any() else 0.0
     return float(np.mean(hg == ho)), derr, nerr, cerr, int(both.sum())

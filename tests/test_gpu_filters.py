@@ -1,8 +1,10 @@
 """Input preprocessing, bilateral filters and the post-fusion error through the C ABI
 (dtsdf_preprocess, dtsdf_set_filters, dtsdf_icp_set_filters, dtsdf_depth_mae) against the oracle.
 
-Tolerances: unfiltered preprocessing is bit-exact (both sides take it in single precision with
-the same operation order); filtered depth within 1e-5 relative (FP32 sums of up to 121 weighted
+Tolerances: unfiltered preprocessing: the kept and normal masks are identical (the filter compares
+differences of input depths, exact in either precision near its threshold), points within 1e-7
+relative and normals within 1e-6 rad (both formed in double precision and rounded once), except
+at the oracle's orientation ties, where the normal may point the other way; filtered depth within 1e-5 relative (FP32 sums of up to 121 weighted
 taps against FP64) with identical presence masks; filtered normals within 1e-3 rad on 99.9 % of
 the pixels with a normal (a normal whose camera-facing decision flips at a grazing pixel differs
 by pi); the MAE sums within 1e-12 relative (FP64 on both sides, different summation order) and
@@ -11,6 +13,7 @@ import numpy as np
 import pytest
 import torch
 
+import angles
 import oracle
 from oracle import filters as OF
 import scenes
@@ -37,7 +40,11 @@ def _frames():
     return s, [s.frame(i) for i in range(10)]
 
 
-def test_unfiltered_preprocessing_is_bit_exact():
+def _angles(a, b):
+    return angles.between(a, b)
+
+
+def test_unfiltered_preprocessing_matches_oracle():
     s, frames = _frames()
     for f in frames[:3]:
         P, N = dt.preprocess(cu(f.depth), s.K, ZMIN, ZMAX, DSUP)
@@ -46,11 +53,13 @@ def test_unfiltered_preprocessing_is_bit_exact():
         o = oracle.preprocess(f.depth, s.K, ZMIN, ZMAX, DSUP)
         assert np.array_equal(P[..., 3] > 0, o["ok"] > 0)
         assert np.array_equal(N[..., 3] > 0, o["nok"] > 0)
-        assert np.array_equal(P[..., :3], o["Pf"]) and np.array_equal(N[..., :3], o["nf"])
-
-
-def _angles(a, b):
-    return np.arccos(np.clip(np.sum(a * b, -1), -1.0, 1.0))
+        ok = o["ok"] > 0
+        assert np.all(np.abs(P[ok][:, :3] - o["P"][ok]) <= 1e-7 * np.linalg.norm(o["P"][ok], axis=-1)[:, None])
+        nk = o["nok"] > 0
+        ang = _angles(N[nk][:, :3].astype(np.float64), o["n"][nk])
+        tie = o["tie"][nk] > 0
+        print(f"normals: max {ang[~tie].max():.2e} rad off ties, {tie.sum()} orientation ties")
+        assert np.all((ang <= 1e-6) | (tie & (ang >= np.pi - 1e-6)))
 
 
 @pytest.mark.parametrize("which", ["depth", "normals", "both"])

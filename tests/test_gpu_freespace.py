@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 import torch
 
+import angles
 import oracle
 import scenes
 import paper_2301_12796_gb300 as dt
@@ -47,7 +48,7 @@ def _compare(d, n, do, no):
     agree = float(np.mean(hg == ho))
     both = hg & ho
     derr = np.abs(d[both] - do[both])
-    nerr = np.arccos(np.clip(np.sum(n[both][:, :3] * no[both], -1), -1, 1))
+    nerr = angles.between(n[both][:, :3], no[both])
     return agree, derr, nerr, int(both.sum())
 
 

@@ -12,6 +12,7 @@ torch = pytest.importorskip("torch")
 HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 sys.path.insert(0, HERE)
 
+import angles  # noqa: E402
 import make_golden  # noqa: E402
 import paper_2301_12796_gb300 as dt  # noqa: E402
 
@@ -39,7 +40,7 @@ def test_device_render_matches_golden_plane():
     d, n = d.cpu().numpy(), n.cpu().numpy()
     u, v = g[:, 0].astype(int), g[:, 1].astype(int)
     assert np.abs(d[v, u] - g[:, 2]).max() <= 1e-4
-    ang = np.arccos(np.clip(np.sum(n[v, u, :3] * g[:, 3:6], -1), -1, 1))
+    ang = angles.between(n[v, u, :3], g[:, 3:6])
     assert ang.max() <= 1e-3
     gm.close()
 

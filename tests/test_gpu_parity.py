@@ -10,16 +10,22 @@ Tolerances (the required values where they exist, otherwise derived from the ari
   tolerance on >= 99.9 % of the pixels both sides hit; the largest deviation is bounded
   separately.
   fused voxels: FP32 running averages vs FP64: sdf |d| <= 2e-4 (units of tau), weights
-  |d| <= 1e-4 w + 1e-5, colour |d| <= 1e-2 (0..255); the set of voxels with weight > 0 and
-  the set of allocated bricks are compared exactly.
+  |d| <= 1e-4 w + 1e-5, colour |d| <= 1e-2 (0..255). The oracle decides every allocation and
+  voxel update in FP64 and records its ties (decisions within the FP32 rounding of their
+  thresholds); the allocated (block, D) sets, the voxels with weight > 0 and the voxel values
+  may differ only on those (tests/mapcheck.py), and the counts of such differences are printed.
+  ICP: the row counts may differ by at most the oracle's tie pixels, H and g by at most the
+  bound on their other outcomes (oracle.icp.tie_bounds) on top of the arithmetic tolerance.
 """
 import numpy as np
 import pytest
 import torch
 
+import angles
 import oracle
 from oracle import icp as oicp
 import scenes
+from mapcheck import compare_maps as _compare
 import paper_2301_12796_gb300 as dt
 from paper_2301_12796_gb300 import build as B
 
@@ -32,12 +38,22 @@ NORMAL_TOL = 1e-3
 # FP16 storage form: share of mask-agreeing pixels whose depth is within DEPTH_TOL
 FP16_DEPTH_FRAC = 0.999
 NORMAL_AGREE = 0.999
+# end to end (each side renders its own fused map): the maps agree except on the oracle's ties, where a
+# voxel's presence can differ; a sample whose corners include such a voxel can change the crossing
+DEPTH_AGREE = 0.999
+# colour (0..255): FP32 trilinear colour of FP32 running averages against FP64, on 99.9 % of the
+# pixels (a direction whose combination weight vanishes at the evaluation point changes the mix)
+COLOUR_TOL = 0.5
 # a fusion weight is Lipschitz in the pixel normal (w_dir has slope 1/(2 theta - pi/2) per radian)
 # and FP32 normals differ from FP64 ones by ~1e-7 rad: an absolute allowance per voxel
 W_ABS = 1e-5
 # sdf (units of tau): FP32 cross-product normals carry ~1e-5 rad error at 2-pixel baselines,
 # times |x - p| <= tau, accumulated over the running average
 SDF_TOL = 2e-4
+# photometric rows: the keyframe sampling position is a single-precision projection (~1e-4 px at
+# f = 525), which moves the bilinear gradient by |grad^2 I| 1e-4 px; intensities and gradients
+# themselves are correctly rounded (exact integer intensity sums)
+PHOTO_H_TOL = 1e-5
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -81,30 +97,10 @@ def oracle_map_on_device(om, **kw):
 
 
 def compare_maps(gm, om):
-    coords, vox = gm.export()
-    ob = om.bricks()
-    gset = {tuple(c) for c in coords}
-    oset = {tuple(b[:4]) for b in ob}
-    assert gset == oset, (len(gset - oset), len(oset - gset))
-    idx = {tuple(c): i for i, c in enumerate(coords)}
-    nchk = 0
-    for b in ob:
-        g = vox[idx[tuple(b[:4])]].astype(np.float64)
-        o = om.brick(*b[:4])
-        pres_g, pres_o = g[:, 1] > 0, o[:, 1] > 0
-        assert np.array_equal(pres_g, pres_o)
-        p = pres_o
-        if not p.any():
-            continue
-        assert np.abs(g[p, 0] - o[p, 0]).max() <= SDF_TOL
-        assert np.all(np.abs(g[p, 1] - o[p, 1]) <= 1e-4 * o[p, 1] + W_ABS)
-        cg, co = g[:, 5] > 0, o[:, 5] > 0
-        assert np.array_equal(cg, co)
-        if co.any():
-            assert np.abs(g[co, 2:5] - o[co, 2:5]).max() <= 1e-2
-            assert np.all(np.abs(g[co, 5] - o[co, 5]) <= 1e-4 * o[co, 5] + W_ABS)
-        nchk += p.sum()
-    return nchk
+    r = _compare(gm, om, sdf_tol=SDF_TOL, w_abs=W_ABS)
+    print(f"map parity: {r['checked']} voxels checked in {r['bricks']} bricks; differing on ties: "
+          f"{r['tie_keys']} keys, {r['tie_voxels']} voxels, {r['tie_colour']} colours")
+    return r["checked"]
 
 
 def test_exp_map_matches_matrix_exponential():
@@ -130,11 +126,15 @@ def test_hash_allocation_and_fusion_match_oracle():
     assert compare_maps(gm, om) > 20000
 
 
-def test_hash_allocation_kinect_frames_bit_exact():
+def test_hash_allocation_kinect_frames_match_up_to_ties():
     s = scenes.kinect_room(1)
     gm, om = fuse_both(s, range(0, 300, 60), dense=False, voxel=0.005, tau=0.02, max_blocks=1 << 18)
     coords, _ = gm.export()
-    assert {tuple(c) for c in coords} == {tuple(b[:4]) for b in om.bricks()}
+    g, o = {tuple(c) for c in coords}, {tuple(b[:4]) for b in om.bricks()}
+    diff = g ^ o
+    print(f"kinect allocation: {len(o)} keys, {len(diff)} differ (all ties)")
+    assert all(om.alloc_tie(*k) >= 0 for k in diff)
+    assert len(diff) <= 1e-3 * len(o)
 
 
 def _render_parity(gm, om, K, T, color=True):
@@ -144,13 +144,18 @@ def _render_parity(gm, om, K, T, color=True):
     agree = float(np.mean(hg == ho))
     both = hg & ho
     derr = np.abs(dg[both] - do[both])
-    cosang = np.clip(np.sum(ng[both][:, :3] * no[both], -1), -1, 1)
-    nerr = np.arccos(cosang)
+    nerr = angles.between(ng[both][:, :3], no[both])
     cerr = None
     if color:
         cb = both & (cg[..., 3] > 0) & (cok > 0)
-        cerr = np.abs(cg[cb][:, :3] - co[cb]).max() if cb.any() else 0.0
+        cerr = np.abs(cg[cb][:, :3] - co[cb]).max(-1) if cb.any() else np.zeros(1)
     return agree, derr, nerr, cerr, both.sum()
+
+
+def _report(tag, agree, derr, nerr, cerr):
+    print(f"{tag}: mask {agree:.5f} depth max {derr.max():.2e} q999 {np.quantile(derr, 0.999):.2e} "
+          f"normals <= 1e-3: {np.mean(nerr <= NORMAL_TOL):.5f} max {nerr.max():.2e} "
+          f"colour q999 {np.quantile(cerr, 0.999):.3f} max {cerr.max():.3f}")
 
 
 @pytest.mark.parametrize("fi", [0, 3, 5, 9])
@@ -163,11 +168,12 @@ def test_renderer_matches_oracle_on_the_same_map(fi):
     gm = oracle_map_on_device(om, voxel_size=0.01, truncation=0.04, dense_dim=64)
     T = s.poses[fi] @ scenes.perturbation(np.random.default_rng(fi), 1.0, 0.005)
     agree, derr, nerr, cerr, n = _render_parity(gm, om, s.K, T)
+    _report(f"renderer pose {fi}", agree, derr, nerr, cerr)
     assert n > 5000
     assert agree >= MASK_AGREE, agree
     assert derr.max() <= DEPTH_TOL, derr.max()
     assert np.mean(nerr <= NORMAL_TOL) >= NORMAL_AGREE, np.mean(nerr <= NORMAL_TOL)
-    assert cerr <= 0.5
+    assert np.quantile(cerr, 0.999) <= COLOUR_TOL
 
 
 @pytest.mark.parametrize("fi", [0, 3, 5, 9])
@@ -176,11 +182,12 @@ def test_fuse_and_render_match_oracle_dense(fi):
     gm, om = fuse_both(s, range(10), dense=True)
     T = s.poses[fi] @ scenes.perturbation(np.random.default_rng(fi), 1.0, 0.005)
     agree, derr, nerr, cerr, n = _render_parity(gm, om, s.K, T)
+    _report(f"end to end pose {fi}", agree, derr, nerr, cerr)
     assert n > 5000
     assert agree >= MASK_AGREE, agree
-    assert derr.max() <= DEPTH_TOL, derr.max()
+    assert np.mean(derr <= DEPTH_TOL) >= DEPTH_AGREE, np.mean(derr <= DEPTH_TOL)
     assert np.mean(nerr <= NORMAL_TOL) >= NORMAL_AGREE, np.mean(nerr <= NORMAL_TOL)
-    assert cerr <= 0.5
+    assert np.quantile(cerr, 0.999) <= COLOUR_TOL
 
 
 def test_render_matches_oracle_hash_planes():
@@ -191,11 +198,13 @@ def test_render_matches_oracle_hash_planes():
     gm, om = fuse_both(s, range(6), dense=False, voxel=0.01, tau=0.04)
     T = poses[2] @ scenes.perturbation(np.random.default_rng(99), 2.0, 0.02)
     agree, derr, nerr, cerr, n = _render_parity(gm, om, s.K, T)
-    assert n > 5000 and agree >= MASK_AGREE and derr.max() <= DEPTH_TOL
+    _report("planes end to end", agree, derr, nerr, cerr)
+    assert n > 5000 and agree >= MASK_AGREE and np.mean(derr <= DEPTH_TOL) >= DEPTH_AGREE
     assert np.mean(nerr <= NORMAL_TOL) >= NORMAL_AGREE
     # and the renderer alone, on the oracle's map
     gm2 = oracle_map_on_device(om, voxel_size=0.01, truncation=0.04)
     agree, derr, nerr, cerr, n = _render_parity(gm2, om, s.K, T)
+    _report("planes renderer", agree, derr, nerr, cerr)
     assert n > 5000 and agree >= MASK_AGREE and derr.max() <= DEPTH_TOL and np.mean(nerr <= NORMAL_TOL) >= NORMAL_AGREE
 
 
@@ -241,11 +250,13 @@ def test_icp_normal_equations_match_oracle(sim3, level):
     lv = oicp.pyramid(pre["z"], K, 3)[level]
     rows = oicp.geometric_rows(lv, rd, rn, K, dT, opts.eps[level], 0.1, sim3)
     H, g, E, n = oicp.normal_equations([rows])
-    assert st.rows == n
+    nt, tH, tg, tE = oicp.tie_bounds([rows])
+    print(f"level {level} sim3 {sim3}: rows {st.rows} vs {n}, tie pixels {nt}")
+    assert abs(st.rows - n) <= nt
     Hg = st.H_matrix()
-    assert np.linalg.norm(Hg - H) <= 1e-5 * np.linalg.norm(H)
+    assert np.linalg.norm(Hg - H) <= 1e-5 * np.linalg.norm(H) + tH
     scale_g = np.abs(rows.J).T @ (rows.w * np.abs(rows.r)) + np.abs(rows.J).T @ rows.w * 1e-7
-    assert np.all(np.abs(st.g_vector() - g) <= 1e-5 * np.abs(g) + 1e-3 * scale_g)
+    assert np.all(np.abs(st.g_vector() - g) <= 1e-5 * np.abs(g) + 1e-3 * scale_g + tg)
     xi, ok = oicp.solve(H, g)
     assert ok and st.status == 0
     assert np.allclose(T1, oicp.exp(xi) @ dT, atol=1e-6)
@@ -280,8 +291,15 @@ def test_icp_photometric_rows_match_oracle(mode):
         geo = oicp.geometric_rows(lv, rd, rn, K, dT, opts.eps[level], 0.1, False)
         ph = oicp.photometric_rows(lv, kI, K.scaled(level), T_rs, dT, opts.photo_thr[level], 0.1, 0.1, False)
         H, g, E, n = oicp.normal_equations([geo, ph])
-        assert abs(st.rows_photo - ph.J.shape[0]) <= max(3, 1e-3 * ph.J.shape[0])
-        assert np.linalg.norm(st.H_matrix() - H) <= 1e-3 * np.linalg.norm(H)
+        nt, tH, tg, tE = oicp.tie_bounds([geo, ph])
+        rel = np.linalg.norm(st.H_matrix() - H) / np.linalg.norm(H)
+        Hp = ph.J.T @ (ph.w[:, None] * ph.J)
+        print(f"{mode} level {level}: photometric rows {st.rows_photo} vs {ph.J.shape[0]} (ties {ph.n_tie}), "
+              f"geometric {st.rows - st.rows_photo} vs {geo.J.shape[0]} (ties {geo.n_tie}); H rel {rel:.2e}, "
+              f"photometric share of |H| {np.linalg.norm(Hp) / np.linalg.norm(H):.2e}, tie bound {tH:.2e}")
+        assert abs(st.rows_photo - ph.J.shape[0]) <= ph.n_tie
+        assert abs((st.rows - st.rows_photo) - geo.J.shape[0]) <= geo.n_tie
+        assert np.linalg.norm(st.H_matrix() - H) <= PHOTO_H_TOL * np.linalg.norm(H) + tH
 
 
 @pytest.mark.parametrize("sim3", [False, True])
@@ -413,8 +431,9 @@ def test_fp16_storage_map_matches_oracle():
     for b in om.bricks():
         g = vox[idx[tuple(b[:4])]].astype(np.float64)
         o = om.brick(*b[:4])
-        p = o[:, 1] > 0
-        assert np.array_equal(g[:, 1] > 0, p)
+        tie = (om.brick_ties(*b[:4]) & 1) > 0
+        assert np.all(((g[:, 1] > 0) == (o[:, 1] > 0)) | tie)
+        p = (o[:, 1] > 0) & (g[:, 1] > 0) & ~tie
         if p.any():
             errs.append(np.abs(g[p, 0] - o[p, 0]))
             assert np.all(np.abs(g[p, 1] - o[p, 1]) <= 0.01 * o[p, 1] + 1e-5)
@@ -443,7 +462,7 @@ def test_fp16_render_matches_oracle(fi):
     # then stops at a neighbouring crossing. Those pixels are counted, not excluded.
     close = both & (derr <= DEPTH_TOL)
     frac = close.sum() / both.sum()
-    nerr = np.arccos(np.clip(np.sum(ng[both][:, :3] * no[both], -1), -1, 1))
+    nerr = angles.between(ng[both][:, :3], no[both])
     cb = close & (cg[..., 3] > 0) & (cok > 0)
     cerr = np.abs(cg[cb][:, :3] - co[cb]).max(-1)
     print(f"fp16 fi={fi}: mask {agree:.5f} depth<=1e-4 {frac:.5f} median {np.median(derr[both]):.2e} "

@@ -1,10 +1,12 @@
 """dtsdf_icp_step_noalloc: the ICP iteration for callers that cannot allocate device memory
-(inside stream capture, in real-time loops, under a host that owns all device memory).
+(real-time loops that cannot afford cudaMalloc's implicit synchronisation, hosts that own all
+device memory).
 
-It must give the same normal equations and pose update as the allocating entry point
-dtsdf_icp_step (within the tolerances of the other ICP parity tests), on consecutive calls
-that share its fixed scratch. This file is collected last so that a run stopping at the first
-failure has already run every other test.
+It must give the same normal equations and pose update as the allocating entry points
+dtsdf_icp_step / dtsdf_icp_sim3_step (within the tolerances of the other ICP parity tests), in
+SE(3) and Sim(3), on consecutive calls that share its fixed scratch. The filtered depth it takes
+comes from the library's own preprocessing (dtsdf_preprocess). This file is collected last so
+that a run stopping at the first failure has already run every other test.
 """
 import ctypes
 
@@ -12,7 +14,6 @@ import numpy as np
 import pytest
 import torch
 
-import oracle
 import scenes
 import paper_2301_12796_gb300 as dt
 from paper_2301_12796_gb300 import build as B
@@ -24,7 +25,8 @@ def _stats_from_device(buf):
     return dt.IcpStats.from_buffer_copy(bytes(buf.cpu().numpy().tobytes()))
 
 
-def test_noalloc_step_matches_allocating_step_on_consecutive_calls():
+@pytest.mark.parametrize("sim3", [False, True])
+def test_noalloc_step_matches_allocating_step_on_consecutive_calls(sim3):
     B.build()
     L = dt.lib()
     dev = torch.device("cuda:0")
@@ -32,7 +34,7 @@ def test_noalloc_step_matches_allocating_step_on_consecutive_calls():
     K = s.K
     T_ref = s.poses[0]
     T_cur = T_ref @ scenes.perturbation(np.random.default_rng(17), 2.0, 0.02)
-    cur = s.render(T_cur, noise=True)
+    cur = s.render(T_cur, noise=True, depth_scale=1.03 if sim3 else 1.0)
     ref = s.render(T_ref, noise=False, exact=True)
     rn = np.zeros(ref.normals.shape[:2] + (4,), np.float32)
     rn[..., :3] = ref.normals
@@ -46,12 +48,12 @@ def test_noalloc_step_matches_allocating_step_on_consecutive_calls():
     ic = dt.Icp(K.width, K.height, 1)
     ic.set_frame(torch.from_numpy(cur.depth).to(dev), None, K, z_min, z_max, dsup)
     opts = dt.icp_opts(levels=1, iters=(2,), eps=(eps,), z_min=z_min, min_rows=10)
-    T1, st1 = ic.step(rd_t, rn_t, K, 0, np.eye(4), opts)
-    T2, st2 = ic.step(rd_t, rn_t, K, 0, T1, opts)
+    T1, st1 = ic.step(rd_t, rn_t, K, 0, np.eye(4), opts, sim3=sim3)
+    T2, st2 = ic.step(rd_t, rn_t, K, 0, T1, opts, sim3=sim3)
 
-    # allocation-free path on the same filtered depth (the filter's decisions are exact)
-    filtered = oracle.preprocess(cur.depth, K, z_min, z_max, dsup)["z"]
-    depth_t = torch.from_numpy(filtered).to(dev)
+    # allocation-free path on the same filtered depth, from the library's preprocessing
+    P, _ = dt.preprocess(torch.from_numpy(cur.depth).to(dev), K, z_min, z_max, dsup)
+    depth_t = torch.where(P[..., 3] > 0, P[..., 2], torch.zeros_like(P[..., 2])).contiguous()
     pose = torch.eye(4, dtype=torch.float64, device=dev)
     stats = torch.zeros(ctypes.sizeof(dt.IcpStats), dtype=torch.uint8, device=dev)
     Ki = dt.intrinsics(K)
@@ -59,8 +61,8 @@ def test_noalloc_step_matches_allocating_step_on_consecutive_calls():
     stream = torch.cuda.current_stream().cuda_stream
     results = []
     for _ in range(2):
-        rc = L.dtsdf_icp_step_noalloc(depth_t.data_ptr(), ctypes.byref(Ki), ctypes.byref(out), ctypes.byref(Ki), 0,
-                                      eps, z_min, 10, 1e-6, pose.data_ptr(), stats.data_ptr(), stream)
+        rc = L.dtsdf_icp_step_noalloc(depth_t.data_ptr(), ctypes.byref(Ki), ctypes.byref(out), ctypes.byref(Ki),
+                                      int(sim3), eps, z_min, 10, 1e-6, pose.data_ptr(), stats.data_ptr(), stream)
         assert rc == dt.OK, L.dtsdf_last_error()
         torch.cuda.synchronize()
         results.append((pose.cpu().numpy().copy(), _stats_from_device(stats)))
