@@ -68,7 +68,8 @@ def parse():
     ap.add_argument("--frames", type=int, default=300)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-serve", action="store_true", help="tracking: skip the compact serving measurement")
+    ap.add_argument("--no-serve", action="store_true", help="tracking: skip the serving block")
+    ap.add_argument("--no-multi", action="store_true", help="tracking: skip the multi-sensor Sim(3) block")
     ap.add_argument("--profile", action="store_true", help="small run for ncu: map of 60 frames, few steps")
     ap.add_argument("--workload", default="tracking", choices=["tracking", "multi_sensor", "serve"],
                     help="tracking: Kinect-shaped tracking frames (default); multi_sensor: batched Sim(3) "
@@ -107,6 +108,8 @@ class ClockSampler:
                                                                         f"dtsdf_clocks_{os.getpid()}.csv")
 
     def start(self):
+        """Start sampling and return once the first sample is written: nvidia-smi's start-up
+        (NVML initialisation, some hundred milliseconds) stays out of the timed region."""
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
@@ -115,6 +118,12 @@ class ClockSampler:
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        deadline = time.time() + 10.0
+        while time.time() < deadline and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -264,57 +273,69 @@ def flush_l2(buf):
 
 
 # --------------------------------------------------------------- cpu side ---
-class OracleBench:
-    """The FP64 oracle on a bounded sample of one tracking frame of the workload."""
+class OracleFrame:
+    """The FP64 oracle on whole tracking frames of the workload: the CPU baseline of the tracking
+    line and every step of the reference arm. Its map is fused from the workload's frames (setup,
+    untimed); one frame is then, as on the device: the render of every pixel at the previous
+    frame's pose (the oracle's own render, which is the registration's reference), the whole
+    coarse-to-fine schedule (3 levels, 4/5/10 Gauss-Newton iterations, point-to-plane plus
+    frame-to-keyframe photometric rows, keyframe every 10 frames) and the fusion of the frame
+    at the pose found. threads sets the OpenMP threads of the C oracle (render, fusion); the
+    numpy schedule runs with numpy's own threading."""
 
-    def __init__(self, s, frames):
+    def __init__(self, s, frames, map_frames):
         import oracle
         from oracle import icp as oicp
         self.oracle, self.oicp = oracle, oicp
         self.s, self.frames = s, frames
+        oracle.threads(cpu_cores())
         t0 = time.perf_counter()
         P = oracle.Params(voxel_size=0.005, truncation=0.02, z_max=s.z_max, color=True)
         self.om = oracle.OracleMap(P)
-        self.map_frames = list(range(0, len(frames), max(1, len(frames) // 6)))
+        self.map_frames = list(map_frames)
         for i in self.map_frames:
             self.om.integrate(frames[i].depth, frames[i].rgb, s.K, frames[i].pose)
-        self.f = len(frames) // 2
-        f, K = self.f, s.K
-        ref = s.render(frames[f - 1].pose, noise=False, exact=True)
-        self.ref_d = ref.depth
-        self.ref_n = np.zeros(ref.normals.shape[:2] + (4,), np.float32)
-        self.ref_n[..., :3] = ref.normals
-        pre = oracle.preprocess(frames[f].depth, K, 0.1, s.z_max, 0.01)
-        self.levels = oicp.pyramid(pre["z"], K, 3, frames[f].rgb)
-        self.kf_levels = oicp.pyramid(pre["z"], K, 3, frames[f - 1].rgb)
         self.setup_s = time.perf_counter() - t0
 
-    def step(self, stride: int = 16):
-        """Returns (frames/s extrapolated to one whole frame, parts)."""
-        s, frames, K, f = self.s, self.frames, self.s.K, self.f
-        vv, uu = np.mgrid[0:K.height:stride, 0:K.width:stride]
-        pix = np.stack([uu.ravel(), vv.ravel()], 1).astype(np.int32)
+    def frame(self, f: int, threads: int):
+        """Seconds for whole frame f on `threads` OpenMP threads, and the parts."""
+        oracle, oicp, s, frames = self.oracle, self.oicp, self.s, self.frames
+        K = s.K
+        used = oracle.threads(threads)
+        T_ref = frames[f - 1].pose
+        kf = 10 * ((f - 1) // 10)
+        T_rs = np.linalg.inv(frames[kf].pose) @ T_ref
         t0 = time.perf_counter()
-        self.om.render(K, frames[f - 1].pose, pix)
-        t_render = (time.perf_counter() - t0) * (K.width * K.height) / len(pix)
-        st = self.oicp.Settings(eps=(0.005, 0.05, 0.05))
-        t_icp = 0.0
-        for l, iters in zip(range(3), (10, 5, 4)):
-            t0 = time.perf_counter()
-            self.oicp.step(self.levels[l], self.ref_d, self.ref_n, K, np.eye(4), st.eps[l], st,
-                           photo=(self.kf_levels[l].I, K.scaled(l), np.eye(4)), level_index=l)
-            t_icp += (time.perf_counter() - t0) * iters
-        t0 = time.perf_counter()
-        self.om.integrate(frames[f].depth, frames[f].rgb, K, frames[f].pose)
-        t_fuse = time.perf_counter() - t0
-        return 1.0 / (t_render + t_icp + t_fuse), dict(render_s=t_render, icp_s=t_icp, fuse_s=t_fuse, stride=stride)
+        d, n, _, _ = self.om.render(K, T_ref)
+        t1 = time.perf_counter()
+        rn = np.zeros(n.shape[:2] + (4,), np.float32)
+        rn[..., :3] = n
+        rn[..., 3] = d
+        pre = oracle.preprocess(frames[f].depth, K, 0.1, s.z_max, 0.01)
+        levels = oicp.pyramid(pre["z"], K, 3, frames[f].rgb)
+        kI = oicp.pyramid(pre["z"], K, 3, frames[kf].rgb)
+        photo = [(kI[l].I, K.scaled(l), T_rs) for l in range(3)]
+        st = oicp.Settings(eps=(0.005, 0.05, 0.05), iters=(10, 5, 4), photo_thr=(0.05, 0.175, 0.175), lam=0.1)
+        dT, log = oicp.track(levels, d.astype(np.float32), rn, K, np.eye(4), st, photo)
+        t2 = time.perf_counter()
+        self.om.integrate(frames[f].depth, frames[f].rgb, K, T_ref @ dT)
+        t3 = time.perf_counter()
+        return t3 - t0, dict(render_s=t1 - t0, icp_s=t2 - t1, fuse_s=t3 - t2, iterations=len(log), threads=used)
 
-    def describe(self, parts) -> str:
-        st = parts["stride"]
-        return (f"oracle map fused from {len(self.map_frames)} of the frames; per frame: render of 1/{st * st} of the "
-                f"640x480 pixels scaled up ({parts['render_s']:.1f} s/frame), one ICP iteration per level on the full "
-                f"frame with photometric rows scaled to 4/5/10 iterations ({parts['icp_s']:.1f} s), one full "
-                f"fusion ({parts['fuse_s']:.1f} s)")
+    def counts(self, f: int) -> dict:
+        """The oracle's count of what the render of frame f reads (all threads)."""
+        self.oracle.threads(cpu_cores())
+        return self.om.render_count(self.s.K, self.frames[f - 1].pose)
+
+    def describe(self, parts, single=None) -> str:
+        out = (f"oracle map fused from {len(self.map_frames)} frames of the workload (setup, {self.setup_s:.0f} s); "
+               f"one whole 640x480 frame on {parts['threads']} threads: render of every pixel "
+               f"({parts['render_s']:.2f} s), the full f2kf schedule of {parts['iterations']} iterations against "
+               f"that render ({parts['icp_s']:.2f} s, numpy), fusion of the frame ({parts['fuse_s']:.2f} s)")
+        if single is not None:
+            out += (f"; single-threaded: {single['render_s']:.1f} + {single['icp_s']:.1f} + "
+                    f"{single['fuse_s']:.1f} s")
+        return out
 
 
 def cpu_cores() -> int:
@@ -342,23 +363,25 @@ def cpu_model() -> str:
 
 # ---------------------------------------------------------------- reference --
 def run_reference(args, rank, world):
-    """The oracle as it stands, on the host cores, one bounded sample of a tracking frame per step."""
+    """The oracle as it stands, on the host cores, one whole tracking frame of the workload per
+    step (after fusing the map from the workload's frames)."""
     if rank != 0:
         return
     s, frames = make_workload(args.frames)
-    ob = OracleBench(s, frames)
-    vals, parts = [], None
+    ob = OracleFrame(s, frames, range(0, len(frames), 2))
+    secs, parts = [], None
     for i in range(args.warmup + args.steps):
-        v, parts = ob.step(stride=32)
+        f = 1 + i % (len(frames) - 1)
+        dt_s, parts = ob.frame(f, cpu_cores())
         if i >= args.warmup:
-            vals.append(v)
-    value = float(np.mean(vals))
+            secs.append(dt_s)
+    value = len(secs) / float(np.sum(secs))
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD},
-           "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cpu_cores(), "cpu": cpu_model(), "kind": "oracle",
-                            "sample": ob.describe(parts)},
+           "cpu_baseline": {"value": value, "unit": "frames/s", "cores": parts["threads"], "cpu": cpu_model(),
+                            "kind": "oracle", "sample": ob.describe(parts)},
            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -367,6 +390,39 @@ def run_reference(args, rank, world):
 def voxel_bytes(storage: int) -> tuple[int, int]:
     """Bytes per voxel of a geometry brick and of a colour brick."""
     return (4, 4) if storage == 1 else (8, 16)
+
+
+def march_bytes(ob, tr, s, frames, args, storage):
+    """Algorithmic bytes of one render of the timed loop: the distinct bricks the march reads x
+    512 x (8 B FP32 sdf + weight | 4 B FP16 + u16), the distinct allocated block cells whose
+    hash entry it reads x 16 B, the colour voxels that enter the outputs x (12 B FP32 RGB |
+    3 B u8), and the outputs W H x (4 B depth + 12 B normal + 3 B RGB). The counts are the
+    FP64 oracle's (its instrumented render of its own map at the same poses); without the
+    oracle (--no-cpu), the device's instrumented march counts the bricks instead."""
+    npix = s.K.width * s.K.height
+    b_geom, b_col = (4, 3) if storage == 1 else (8, 12)
+    fr = [1 + (args.warmup + k) % (tr.n - 1) for k in range(min(4, args.steps))]
+    if ob is not None:
+        c = [ob.counts(f) for f in fr]
+        g, p, cv = (float(np.mean([x[k] for x in c])) for k in ("bricks", "cells", "colour_voxels"))
+        b = g * 512 * b_geom + p * 16 + cv * b_col + npix * 19
+        return b, (f"oracle count at {len(fr)} timed poses: {g:.0f} bricks x 512 x {b_geom} B + {p:.0f} block "
+                   f"cells x 16 B + {cv:.0f} colour voxels x {b_col} B + {npix} x 19 B outputs")
+    tb = [tr.map.touched(s.K, frames[f - 1].pose) for f in fr]
+    g, cb = float(np.mean([x[0] for x in tb])), float(np.mean([x[1] for x in tb]))
+    b = g * 512 * b_geom + cb * 512 * b_col + npix * 19
+    return b, (f"device count (instrumented march) at {len(fr)} timed poses: {g:.0f} geometry bricks x 512 x "
+               f"{b_geom} B + {cb:.0f} colour bricks x 512 x {b_col} B + {npix} x 19 B outputs")
+
+
+def icp_algorithmic_bytes(K) -> float:
+    """Sum over the pyramid levels of iterations x pixels x bytes per pixel-iteration: 4 B current
+    depth, 24 B gathered render point and normal, 4 B current intensity and 48 B of keyframe
+    taps (4 bilinear taps x intensity and gradient)."""
+    total = 0.0
+    for l, it in zip(range(3), (10, 5, 4)):
+        total += it * (K.width >> l) * (K.height >> l) * (4 + 24 + 4 + 48)
+    return total
 
 
 def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
@@ -383,16 +439,10 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
     for i in range(args.warmup):
         tr.step(i)
     torch.cuda.synchronize()
-    # algorithmic bytes of the render at the poses rendered in the timed loop (first 8)
-    tb = []
-    for i in range(args.warmup, args.warmup + min(8, args.steps)):
-        f = 1 + i % (tr.n - 1)
-        tb.append(tr.map.touched(s.K, frames[f - 1].pose))
-    geom_b, col_b = np.mean([x[0] for x in tb]), np.mean([x[1] for x in tb])
-    march = tr.map.touched(s.K, frames[1 + args.warmup % (tr.n - 1) - 1].pose, counters=True)[2]
     npix = s.K.width * s.K.height
-    gvb, cvb = voxel_bytes(storage)
-    render_bytes = geom_b * 512 * gvb + col_b * 512 * cvb + npix * (4 + 16 + 16)
+    # event counts of one render (instrumented build of the march: samples, full combinations,
+    # block cells entered, allocated cells, hits, cell jumps)
+    march = tr.map.touched(s.K, frames[1 + args.warmup % (tr.n - 1) - 1].pose, counters=True)[2]
     # ---------------- timed region
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     clk = ClockSampler(local)
@@ -491,6 +541,14 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
         comb = {"blocks": int(blocks), "bricks": int(cbricks), "full_combine_ms": comb_ms,
                 "algorithmic_bytes": float(comb_bytes)}
     peak, peak_kind = measured_hbm_peak()
+    # the FP64 oracle on the host: its count of what the renders read (algorithmic bytes) and the
+    # CPU baseline (one whole frame on all cores, one single-threaded)
+    ob = None
+    if rank == 0 and not args.no_cpu and not args.profile:
+        ob = OracleFrame(s, frames, range(0, n_frames, 2))
+    render_bytes, bytes_def = march_bytes(ob, tr, s, frames, args, storage)
+    icp_ms = float(ph[:, 1].mean())
+    icp_bytes = icp_algorithmic_bytes(s.K)
     achieved = render_bytes / (render_ms / 1000.0) / 1e9
     if comb is not None:
         a_c = comb["algorithmic_bytes"] / (comb["full_combine_ms"] / 1000.0) / 1e9
@@ -506,21 +564,31 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
         roof = {"kernel": "k_render_freespace (Alg. 1 free-space combination ray-cast)", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                 "traffic": None, "algorithmic_bytes_per_launch": render_bytes, "launch_ms": render_ms,
-                "bytes_definition": "the bricks the direct march touches at the same poses (a lower bound of "
-                                    "what this march reads: it walks every sample of allocated block cells)"}
+                "bytes_definition": bytes_def}
     roof = roof or {"kernel": "k_render (direct DTSDF ray-cast)", "bound": "hbm", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
             "traffic": render_traffic() if storage == 0 and not args.profile else None,
-            "algorithmic_bytes_per_launch": render_bytes, "geom_bricks": geom_b, "color_bricks": col_b,
-            "launch_ms": render_ms}
-    serve = None
+            "algorithmic_bytes_per_launch": render_bytes, "launch_ms": render_ms, "bytes_definition": bytes_def,
+            "render_and_icp": {"bytes": render_bytes + icp_bytes, "icp_bytes": icp_bytes, "ms": render_ms + icp_ms,
+                               "achieved": (render_bytes + icp_bytes) / ((render_ms + icp_ms) / 1000.0) / 1e9,
+                               "frac": (render_bytes + icp_bytes) / ((render_ms + icp_ms) / 1000.0) / 1e9 / peak,
+                               "icp_definition": "sum over levels of iterations x pixels x (4 B depth + 24 B gathered "
+                                                 "point and normal + 4 B intensity + 48 B keyframe taps), schedule "
+                                                 "4/5/10 at 160x120/320x240/640x480"}}
+    serve = multi = None
     if not args.profile and not args.no_serve:
-        serve = serve_summary(dt, torch, dev)
+        serve = side_block(run_serve(side_args(args, steps=0), dt, torch, tdist, dev, rank, world, local,
+                                     emit=False))
+    if not args.profile and not args.no_multi:
+        multi = side_block(run_multi_sensor(side_args(args, steps=MS_BLOCK_STEPS), dt, torch, tdist, dev, rank,
+                                            world, local, emit=False))
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu and not args.profile:
-        ob = OracleBench(s, frames)
-        v, parts = ob.step(stride=2)
-        cpu = {"value": v, "unit": "frames/s", "cores": cpu_cores(), "cpu": cpu_model(), "kind": "oracle", "sample": ob.describe(parts)}
+    if ob is not None and world == 1:
+        f = 1 + args.warmup % (len(frames) - 1)
+        secs, parts = ob.frame(f, cpu_cores())
+        secs1, parts1 = ob.frame(f + 1, 1)
+        cpu = {"value": 1.0 / secs, "unit": "frames/s", "cores": parts["threads"], "cpu": cpu_model(),
+               "kind": "oracle", "single_thread_value": 1.0 / secs1, "sample": ob.describe(parts, parts1)}
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -541,7 +609,7 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
                           "march_counts_per_frame": march,
                           "wall_s_timed_loop": t_wall, "median_translation_error_m": terr,
                           "post_fusion_mae_mm": post_mae_mm},
-               "serve": serve, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "serve": serve, "multi_sensor": multi, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clocks}
         print(json.dumps(out), flush=True)
 
@@ -647,7 +715,7 @@ def ms_cpu_baseline(ms, n_frames):
     return 1.0 / per_problem, sample
 
 
-def run_multi_sensor(args, dt, torch, tdist, dev, rank, world, local):
+def run_multi_sensor(args, dt, torch, tdist, dev, rank, world, local, emit=True):
     storage = 1 if args.storage == "fp16" else 0
     n_frames = 60 if args.profile else args.frames
     ms = MultiSensor(dt, torch, dev, args.problems, n_frames, storage)
@@ -759,10 +827,18 @@ def run_multi_sensor(args, dt, torch, tdist, dev, rank, world, local):
                           "errors_vs_truth": {"rot_deg_median": float(np.median(rot)),
                                               "trans_m_median": float(np.median(tr)),
                                               "scale_median": float(np.median(sc)),
-                                              "success_rate": float(np.mean((rot < 1.0) & (tr < 0.02)))}},
+                                              "success_rate": float(np.mean((rot < 1.0) & (tr < 0.02))),
+                                              "failed": [{"problem": int(k), "rot_deg": float(rot[k]),
+                                                          "trans_m": float(tr[k]), "scale": float(sc[k])}
+                                                         for k in np.nonzero(~((rot < 1.0) & (tr < 0.02)))[0]]}},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": n * MS_LAUNCHES_PER_FRAME + 2 * ((n + 63) // 64), "clocks": clocks}
-        print(json.dumps(out), flush=True)
+        if emit:
+            print(json.dumps(out), flush=True)
+        ms.map.close()
+        return out
+    ms.map.close()
+    return None
 
 
 # ------------------------------------------------------------------ serve --
@@ -866,7 +942,7 @@ def serve_cpu_baseline(rooms, q):
     return 1.0 / (t_render + t_icp), sample
 
 
-def run_serve(args, dt, torch, tdist, dev, rank, world, local):
+def run_serve(args, dt, torch, tdist, dev, rank, world, local, emit=True):
     import scenes
     n_frames = 20 if args.profile else args.map_frames
     rooms = [scenes.kinect_room(1 + i, n_frames=n_frames) for i in range(args.maps)]
@@ -986,9 +1062,11 @@ def run_serve(args, dt, torch, tdist, dev, rank, world, local):
                "e2e": {"value": value, "unit": "requests/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": ctypes_result_bytes(dt)},
                "gpu_launches": int(st.batches) * (2 + args.maps) + 5 * len(reqs), "clocks": clocks}
-        print(json.dumps(out), flush=True)
+        if emit:
+            print(json.dumps(out), flush=True)
     for m in maps16 + maps32:
         m.close()
+    return out if rank == 0 else None
 
 
 def serve_requests_low(srv, rooms, n, rate):
@@ -1002,40 +1080,27 @@ def serve_requests_low(srv, rooms, n, rate):
             "mean_batch": float(np.mean([r.batch_size for r in res]))}
 
 
-def serve_summary(dt, torch, dev, n_req=256, rate=2000.0, n_maps=2, n_frames=40):
-    """Compact serving measurement for the tracking line: the continuous-batching server over
-    FP16 maps of seeded rooms, a Poisson stream of mixed-size SE(3)/Sim(3) requests at `rate`,
-    and a stream at a tenth of that rate."""
-    import scenes
-    rooms = [scenes.kinect_room(1 + i, n_frames=n_frames) for i in range(n_maps)]
-    maps = []
-    for room in rooms:
-        m = dt.Map(dt.params(voxel_size=0.005, truncation=0.02, max_blocks=1 << 18, z_max=room.z_max, color=False,
-                             storage=dt.STORE_FP16))
-        for i in range(room.n_frames):
-            f = room.frame(i)
-            m.integrate(torch.from_numpy(f.depth).to(dev), None, room.K, f.pose)
-        maps.append(m)
-    torch.cuda.synchronize()
-    reqs = scenes.serve_requests(rooms, n_req, seed=1, rate=rate, pool=min(n_req, 64))
-    pinned = [torch.from_numpy(q["depth"]).pin_memory().numpy() for q in reqs]
-    p = dt.server_params(hbm_budget=8 << 30, max_inflight=128, max_batch=32, streams=4,
-                         opts=dt.icp_opts(**SERVE_OPTS), shape=(8, 256))
-    srv = dt.Server(maps, p)
-    warm = scenes.serve_requests(rooms, 32, seed=2, rate=rate, pool=8)
-    serve_stream(srv, warm, [q["depth"] for q in warm])
-    res = serve_stream(srv, reqs, pinned)
-    lat = np.array([r.t_done - r.t_submit for r in res])
-    span = max(r.t_done for r in res) - min(r.t_submit for r in res)
-    low = serve_requests_low(srv, rooms, 128, rate / 10.0)
-    srv.close()
-    for m in maps:
-        m.close()
-    return {"workload": f"{n_req} requests, Poisson {rate:g}/s, 320x240 / 640x480 / 1280x720 (0.3 / 0.5 / 0.2), "
-                        f"SE(3):Sim(3) 3:1, {n_maps} FP16 room maps of {n_frames} frames (bench.py --workload serve: "
-                        f"512 requests, 3 maps of 100 frames, against serial FP32)",
-            "requests_per_s": len(reqs) / span, "p50_ms": float(np.percentile(lat, 50) * 1e3),
-            "p99_ms": float(np.percentile(lat, 99) * 1e3), "below_capacity": low}
+MS_BLOCK_STEPS = 10
+
+
+def side_args(args, steps):
+    """Arguments of a side workload run inside the tracking line: its own defaults (FP32 maps for
+    the multi-sensor batch, 512 requests at 2000/s over 3 FP16 maps for serving), the tracking
+    line's warm-up, no oracle leg of its own (the tracking line carries the CPU baseline)."""
+    a = argparse.Namespace(**vars(args))
+    a.steps = steps or args.steps
+    a.no_cpu = True
+    a.storage = "fp32"
+    return a
+
+
+def side_block(out):
+    """The fields of a side workload's JSON line that the tracking line carries as a block."""
+    if out is None:
+        return None
+    keep = ("metric", "value", "unit", "steps", "ms_per_step", "config", "latency_ms", "latency_below_capacity",
+            "serial_fp32", "accuracy", "roofline", "e2e", "gpu_launches", "clocks")
+    return {k: out[k] for k in keep if k in out}
 
 
 def ctypes_result_bytes(dt):

@@ -108,6 +108,16 @@ Pose32 to_pose32(const double* T) {
   return p;
 }
 
+// A host pose into a render job: rounded to single precision for the march, kept in double for
+// the positions of the crossing refinement.
+void set_job_pose(RenderJob& J, const double* T) {
+  J.T = to_pose32(T);
+  for (int a = 0; a < 3; ++a) {
+    for (int b = 0; b < 3; ++b) J.T64[3 * a + b] = T[4 * a + b];
+    J.T64[9 + a] = T[4 * a + 3];
+  }
+}
+
 Intr to_intr(const dtsdf_intrinsics& K) {
   Intr k;
   k.W = K.width;
@@ -211,7 +221,7 @@ static unsigned* render_slot(dtsdf_map m) {
   return m->render_q + (m->render_q_next.fetch_add(1, std::memory_order_relaxed) % RENDER_Q_SLOTS);
 }
 
-static dtsdf_status render_launch(dtsdf_map m, const dtsdf_intrinsics& K, const Pose32& T, const double* Tdev,
+static dtsdf_status render_launch(dtsdf_map m, const dtsdf_intrinsics& K, const double* T_host, const double* Tdev,
                                   const dtsdf_render_out* out, cudaStream_t s, uint8_t* touched) {
   unsigned* q = render_slot(m);
   CK(cudaMemsetAsync(q, 0, sizeof(unsigned), s));
@@ -219,7 +229,7 @@ static dtsdf_status render_launch(dtsdf_map m, const dtsdf_intrinsics& K, const 
   memset(&J, 0, sizeof(J));
   J.K = to_intr(K);
   J.Tdev = Tdev;
-  J.T = T;
+  if (T_host) set_job_pose(J, T_host);
   J.depth = out->depth;
   J.normals = (float4*)out->normals;
   J.color = (float4*)out->color;
@@ -444,16 +454,14 @@ dtsdf_status dtsdf_render(dtsdf_map m, const dtsdf_intrinsics* K, const double T
                           void* stream) {
   if (!m || !intr_ok(K) || !pose_ok(T_wc) || !out || !out->depth || !out->normals)
     return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
-  return render_launch(m, *K, to_pose32(T_wc), nullptr, out, (cudaStream_t)stream, nullptr);
+  return render_launch(m, *K, T_wc, nullptr, out, (cudaStream_t)stream, nullptr);
 }
 
 dtsdf_status dtsdf_render_dev(dtsdf_map m, const dtsdf_intrinsics* K, const double* T_wc_dev,
                               const dtsdf_render_out* out, void* stream) {
   if (!m || !intr_ok(K) || !T_wc_dev || !out || !out->depth || !out->normals)
     return fail(DTSDF_ERR_INVALID_ARG, "bad argument");
-  Pose32 T;
-  memset(&T, 0, sizeof(T));
-  return render_launch(m, *K, T, T_wc_dev, out, (cudaStream_t)stream, nullptr);
+  return render_launch(m, *K, nullptr, T_wc_dev, out, (cudaStream_t)stream, nullptr);
 }
 
 dtsdf_status dtsdf_recycle(dtsdf_map m, float free_sdf, int64_t* recycled, void* stream) {
@@ -542,7 +550,7 @@ static dtsdf_status render_combined_impl(dtsdf_map m, const dtsdf_intrinsics* K,
   memset(&J, 0, sizeof(J));
   J.K = to_intr(*K);
   J.Tdev = T_dev;
-  if (T_host) J.T = to_pose32(T_host);
+  if (T_host) set_job_pose(J, T_host);
   J.depth = out->depth;
   J.normals = (float4*)out->normals;
   J.color = (float4*)out->color;
@@ -641,7 +649,6 @@ dtsdf_status dtsdf_render_tune(dtsdf_map m, const dtsdf_intrinsics* K, const dou
   RenderShape bs = keep;
   float bt = 3.4e38f;
   const int widths[5] = {2, 4, 8, 16, 32}, groups[3] = {8, 16, 32};
-  const Pose32 T = to_pose32(T_wc);
   for (int wi = 0; wi < 5 && e == cudaSuccess; ++wi)
     for (int gi = 0; gi < 3 && e == cudaSuccess; ++gi) {
       m->shape.ctas = 0;
@@ -650,7 +657,7 @@ dtsdf_status dtsdf_render_tune(dtsdf_map m, const dtsdf_intrinsics* K, const dou
       float best_rep = 3.4e38f;
       for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
         e = cudaEventRecord(e0, s);
-        if (e == cudaSuccess && render_launch(m, *K, T, nullptr, out, s, nullptr) != DTSDF_OK) e = cudaErrorUnknown;
+        if (e == cudaSuccess && render_launch(m, *K, T_wc, nullptr, out, s, nullptr) != DTSDF_OK) e = cudaErrorUnknown;
         if (e == cudaSuccess) e = cudaEventRecord(e1, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -699,7 +706,7 @@ dtsdf_status dtsdf_render_touched(dtsdf_map m, const dtsdf_intrinsics* K, const 
       RenderJob J;
       memset(&J, 0, sizeof(J));
       J.K = to_intr(*K);
-      J.T = to_pose32(T_wc);
+      set_job_pose(J, T_wc);
       J.depth = depth;
       J.normals = nrm;
       J.color = col;

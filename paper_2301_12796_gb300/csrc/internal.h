@@ -90,6 +90,7 @@ struct RenderJob {
   Intr K;
   const double* Tdev;
   Pose32 T;
+  double T64[12];  // the host pose in double precision (rotation rows, then translation); unused with Tdev
   float* depth;
   float4* normals;
   float4* color;
@@ -116,6 +117,10 @@ struct RenderBatch {
   // blocks whose box covers one of the tile's pixels; zlo = 0xFFFFFFFF: no block. Null: none.
   const uint32_t* zlo;
   const uint32_t* zhi;
+  // crossings found by the march, refined by the second pass: (pixel, k << 6 | job) per ray
+  // with a crossing between samples k - 1 and k; nhits counts them (zero at launch)
+  int2* hits;
+  unsigned* nhits;
 };
 
 // Launch shape of a render: persistent CTAs (0 = one wave of resident CTAs), the lanes per

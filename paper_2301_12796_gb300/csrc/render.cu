@@ -16,6 +16,8 @@
 // bracket, found by REFINE_HALVINGS bisection steps on the sign of Phi (an undefined point
 // counts as free space) and linear interpolation over the final bracket (h / 2^17 wide);
 // normal and colour are evaluated at the bracket's non-positive end, where Phi is defined.
+// The refinement places its samples from the bracket's first sample computed in double
+// precision from the pose, so its positions carry the rounding of a small offset only.
 // The per-block occupancy filters let empty space be crossed without probes, and per-brick
 // lower bounds let cells whose present directions are all positive be jumped.
 #include <math.h>
@@ -26,7 +28,7 @@ namespace dtsdf {
 
 constexpr int RT_N = 128;  // threads per CTA of the persistent render grid
 #ifndef DTSDF_RENDER_MINB
-#define DTSDF_RENDER_MINB 3   // resident CTAs per SM the register allocation is sized for (159 registers, no spills)
+#define DTSDF_RENDER_MINB 4   // resident CTAs per SM the register allocation is sized for (128 registers, no spills)
 #endif
 
 // Out-of-line hash probe over explicit pointers (keeps callers' state in registers).
@@ -145,8 +147,8 @@ __device__ __forceinline__ int col_slot(const MapView& m, const Cell& c, int D, 
 // the central differences (phi(+h) - phi(-h)) / 2h of the trilinear field along each axis,
 // whose further 24 taps (4 per side and axis) lie in the same padded brick.
 template <int STORE, bool COLOR, bool COUNT>
-__device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, const float g[3], const float r[3],
-                                                 uint8_t* touched, bool want_color) {
+__device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, const int gi[3], const float fr[3],
+                                                 const float r[3], uint8_t* touched, bool want_color) {
   Combined out;
   out.defined = 0;
   out.phi = 0.f;
@@ -154,9 +156,8 @@ __device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, cons
   out.n[0] = out.n[1] = out.n[2] = 0.f;
   out.rgb[0] = out.rgb[1] = out.rgb[2] = 0.f;
   out.cw = 0.f;
-  const float f0 = floorf(g[0]), f1 = floorf(g[1]), f2 = floorf(g[2]);
-  const int g0 = (int)f0, g1 = (int)f1, g2 = (int)f2;
-  const float fx = g[0] - f0, fy = g[1] - f1, fz = g[2] - f2;
+  const int g0 = gi[0], g1 = gi[1], g2 = gi[2];
+  const float fx = fr[0], fy = fr[1], fz = fr[2];
   const int lofs = pad_index(g0 - 8 * c.cx, g1 - 8 * c.cy, g2 - 8 * c.cz);
   float acc = 0.f, facc = 0.f, fw = 0.f;
   bool any = false;
@@ -270,12 +271,11 @@ __device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, cons
 // npres receives the number of present directions: with one present direction that faces
 // the ray (return value 1 or -1), Phi is that direction's value lo itself.
 template <int STORE, bool COUNT>
-__device__ __forceinline__ int sign_fast(const MapView& m, Cell& c, const float g[3], const float r[3], float& lo,
+__device__ __forceinline__ int sign_fast(const MapView& m, Cell& c, const int gi[3], const float fr[3], const float r[3],
+                                         float& lo,
                                          int& npres, uint8_t* touched) {
-  const float f0 = floorf(g[0]), f1 = floorf(g[1]), f2 = floorf(g[2]);
-  const int g0 = (int)f0, g1 = (int)f1, g2 = (int)f2;
-  const float fx = g[0] - f0, fy = g[1] - f1, fz = g[2] - f2;
-  const int lofs = pad_index(g0 - 8 * c.cx, g1 - 8 * c.cy, g2 - 8 * c.cz);
+  const float fx = fr[0], fy = fr[1], fz = fr[2];
+  const int lofs = pad_index(gi[0] - 8 * c.cx, gi[1] - 8 * c.cy, gi[2] - 8 * c.cz);
   float mn = 2.f, mx = -2.f;
   bool any = false, facing = false;
   int np = 0;
@@ -366,11 +366,10 @@ __device__ __forceinline__ bool comb_at(const MapView& m, const Cell& c, int lx,
   return e.y > 0.0f;
 }
 
-__device__ __forceinline__ int sign_comb(const MapView& m, const Cell& c, const float g[3], float& val, int& npres) {
-  const float f0 = floorf(g[0]), f1 = floorf(g[1]), f2 = floorf(g[2]);
-  const float fx = g[0] - f0, fy = g[1] - f1, fz = g[2] - f2;
-  const size_t base = (size_t)c.slot[0] * CVOX +
-                      comb_index((int)f0 - 8 * c.cx, (int)f1 - 8 * c.cy, (int)f2 - 8 * c.cz);
+__device__ __forceinline__ int sign_comb(const MapView& m, const Cell& c, const int gi[3], const float fr[3], float& val,
+                                         int& npres) {
+  const float fx = fr[0], fy = fr[1], fz = fr[2];
+  const size_t base = (size_t)c.slot[0] * CVOX + comb_index(gi[0] - 8 * c.cx, gi[1] - 8 * c.cy, gi[2] - 8 * c.cz);
   float2 v[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) v[q] = __ldg(m.comb + base + ccoff(q));
@@ -388,8 +387,8 @@ __device__ __forceinline__ int sign_comb(const MapView& m, const Cell& c, const 
 }
 
 template <bool COLOR>
-__device__ __forceinline__ Combined full_comb(const MapView& m, const Cell& c, const float g[3], bool want_color,
-                                              uint32_t gen) {
+__device__ __forceinline__ Combined full_comb(const MapView& m, const Cell& c, const int gi[3], const float fr[3],
+                                              bool want_color, uint32_t gen) {
   Combined out;
   out.defined = 0;
   out.phi = 0.f;
@@ -399,12 +398,11 @@ __device__ __forceinline__ Combined full_comb(const MapView& m, const Cell& c, c
   out.cw = 0.f;
   int np = 0;
   float val = 0.f;
-  if (sign_comb(m, c, g, val, np) == 0) return out;
+  if (sign_comb(m, c, gi, fr, val, np) == 0) return out;
   out.defined = 1;
   out.phi = val;
-  const float f0 = floorf(g[0]), f1 = floorf(g[1]), f2 = floorf(g[2]);
-  const float fx = g[0] - f0, fy = g[1] - f1, fz = g[2] - f2;
-  const int l0 = (int)f0 - 8 * c.cx, l1 = (int)f1 - 8 * c.cy, l2 = (int)f2 - 8 * c.cz;
+  const float fx = fr[0], fy = fr[1], fz = fr[2];
+  const int l0 = gi[0] - 8 * c.cx, l1 = gi[1] - 8 * c.cy, l2 = gi[2] - 8 * c.cz;
   float gr[3];
   bool gok = true;
 #pragma unroll 1
@@ -451,21 +449,21 @@ __device__ __forceinline__ Combined full_comb(const MapView& m, const Cell& c, c
   return out;
 }
 
-// One loop, one state machine per lane: marching (MARCH), the bisection of the crossing
-// bracket (SCAN), the evaluations at the final bracket ends (ENDS_A/B) and the output
-// evaluation at the root (OUT) all evaluate the field at one call site of the sign test
-// and one of the full combination, so lanes in different phases stay converged. A lane
-// whose ray is finished (DONE) takes the next ray from the launch's work counter at the
-// top of the loop once its refill group has finished. Work items are the pixels of tiles of
-// 32 rays (tile_w x 32 / tile_w pixels), handed out tile after tile.
-enum { S_MARCH = 0, S_SCAN = 1, S_ENDS_A = 2, S_ENDS_B = 3, S_OUT = 4, S_DONE = 5 };
+// Two passes. The march (k_render): one lane per ray, marching the global sample grid until the
+// first crossing, which it appends to the crossing list (a miss writes the zero outputs); a lane
+// whose ray is finished takes the next ray from the launch's work counter at the top of the
+// loop once its refill group has finished. Work items are the pixels of tiles of 32 rays
+// (tile_w x 32 / tile_w pixels), handed out tile after tile. The refinement (k_refine): one
+// lane per crossing, the same number of field evaluations on every lane.
+enum { S_MARCH = 0, S_DONE = 1 };
 
 template <int STORE, bool COLOR, bool COUNT, int NJ>
 __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, RenderBatch<NJ> a) {
   __shared__ int s_slot[ND * RT_N];
   __shared__ Pose32 s_pose[NJ];
   uint8_t* touched = a.touched;
-  // COUNT build: per-ray event counts (samples, full combinations, cells, allocated cells, hits, jumps)
+  // COUNT build: per-ray event counts (samples, full combinations, cells, allocated cells,
+  // crossings, jumps)
   unsigned long long* ctr = COUNT ? (unsigned long long*)(touched + 2 * (size_t)m.pool_cap) : nullptr;
   uint32_t n_samples = 0, n_full = 0, n_cells = 0, n_acells = 0, n_jumps = 0, n_hits = 0;
   const int tid = threadIdx.x;
@@ -485,16 +483,9 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
   bool alive = true;
   int state = S_DONE;
   int jb = 0, pix = 0, it = 0, k = 0, k1 = 0;
-  float r[3] = {0.f, 0.f, 0.f}, o[3] = {0.f, 0.f, 0.f}, ri[3] = {0.f, 0.f, 0.f}, rl = 1.f;
+  float r[3] = {0.f, 0.f, 0.f}, o[3] = {0.f, 0.f, 0.f}, ri[3] = {0.f, 0.f, 0.f};
   bool prev_def = false;
   float prev_phi = 0.f;
-  // refinement state
-  float ta = 0.f, tb = 0.f, fa = 0.f, ts = 0.f;
-  int j = 0;
-  bool da = false;
-  float out_depth = 0.f;
-  float4 out_n = make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 out_c = make_float4(0.f, 0.f, 0.f, 0.f);
 
   for (;;) {
     // ---- lanes without a ray take the next work items (warp-aggregated atomic). A group of
@@ -530,7 +521,7 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
             const Pose32& T = s_pose[jb];
             // unit ray in camera and world frame
             const float rc0 = (u - J.K.cx) / J.K.fx, rc1 = (v - J.K.cy) / J.K.fy;
-            rl = sqrtf(rc0 * rc0 + rc1 * rc1 + 1.0f);
+            const float rl = sqrtf(rc0 * rc0 + rc1 * rc1 + 1.0f);
             const float q0 = rc0 / rl, q1 = rc1 / rl, q2 = 1.0f / rl;
             r[0] = T.R[0] * q0 + T.R[1] * q1 + T.R[2] * q2;
             r[1] = T.R[3] * q0 + T.R[4] * q1 + T.R[5] * q2;
@@ -557,9 +548,6 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
             it = 0;
             prev_def = false;
             prev_phi = 0.f;
-            out_depth = 0.f;
-            out_n = make_float4(0.f, 0.f, 0.f, 0.f);
-            out_c = make_float4(0.f, 0.f, 0.f, 0.f);
             cell.cx = cell.cy = cell.cz = 0x7fffffff;
             cell.cmask = 0;
             cell.positive = false;
@@ -572,19 +560,7 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
     if (!alive || state == S_DONE) continue;
 
     // ---- one sample of this lane's ray
-    bool finish = ++it > a.max_samples;
-    float t = 0.f;
-    if (state == S_MARCH) {
-      finish |= k > k1;
-      t = (float)k * step;
-    } else if (state == S_SCAN) {
-      t = 0.5f * (ta + tb);
-    } else if (state == S_ENDS_A) {
-      t = ta;
-    } else {
-      t = tb;  // S_ENDS_B, and S_OUT: the outputs at the bracket's non-positive end
-    }
-    if (finish) {
+    if (++it > a.max_samples || k > k1) {
       // a miss (or the sample limit): write the zero outputs
       const RenderJob& J = a.job[jb];
       J.depth[pix] = 0.f;
@@ -593,164 +569,114 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
       state = S_DONE;
       continue;
     }
-    float g[3];
+    const float t = (float)k * step;
+    // sample position: voxel index and fraction from the single-precision ray (position error
+    // ~1e-4 voxel at metres from the origin, which only moves a grid sample)
+    int gi[3];
+    float fr[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) g[q] = (o[q] + t * r[q] - org[q]) * inv_h;
-    const int cx = ((int)floorf(g[0])) >> 3, cy = ((int)floorf(g[1])) >> 3, cz = ((int)floorf(g[2])) >> 3;
+    for (int q = 0; q < 3; ++q) {
+      const float gq = (o[q] + t * r[q] - org[q]) * inv_h;
+      const float fq = floorf(gq);
+      gi[q] = (int)fq;
+      fr[q] = gq - fq;
+    }
+    const int cx = gi[0] >> 3, cy = gi[1] >> 3, cz = gi[2] >> 3;
     if (cx != cell.cx || cy != cell.cy || cz != cell.cz) {
-      if (state == S_MARCH) {
-        // occupancy filters: cross an empty super-cell (4^3 blocks) or block without a probe
-        const int lv = occ_test(m, cx, cy, cz, 1) ? (occ_test(m, cx, cy, cz, 0) ? -1 : 0) : 1;
-        if (lv >= 0) {
-          const int sh = lv ? 2 : 0;
-          const float cs = bsz * (float)(1 << sh);
-          const int cc[3] = {cx >> sh, cy >> sh, cz >> sh};
-          float tex = 3.4e38f;
+      // occupancy filters: cross an empty super-cell (4^3 blocks) or block without a probe
+      const int lv = occ_test(m, cx, cy, cz, 1) ? (occ_test(m, cx, cy, cz, 0) ? -1 : 0) : 1;
+      if (lv >= 0) {
+        const int sh = lv ? 2 : 0;
+        const float cs = bsz * (float)(1 << sh);
+        const int cc[3] = {cx >> sh, cy >> sh, cz >> sh};
+        float tex = 3.4e38f;
 #pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            if (r[q] > 0.f)
-              tex = fminf(tex, (org[q] + (cc[q] + 1) * cs - o[q]) * ri[q]);
-            else if (r[q] < 0.f)
-              tex = fminf(tex, (org[q] + cc[q] * cs - o[q]) * ri[q]);
-          }
-          if (COUNT) {
-            ++n_cells;
-            ++n_samples;
-          }
-          prev_def = false;
-          k = max(k + 1, (int)ceilf(tex / step - 1e-3f));
-          continue;
+        for (int q = 0; q < 3; ++q) {
+          if (r[q] > 0.f)
+            tex = fminf(tex, (org[q] + (cc[q] + 1) * cs - o[q]) * ri[q]);
+          else if (r[q] < 0.f)
+            tex = fminf(tex, (org[q] + cc[q] * cs - o[q]) * ri[q]);
         }
+        if (COUNT) {
+          ++n_cells;
+          ++n_samples;
+        }
+        prev_def = false;
+        k = max(k + 1, (int)ceilf(tex / step - 1e-3f));
+        continue;
       }
       if constexpr (STORE == STORE_COMBINED)
         cell_enter_comb(m, cell, cx, cy, cz, cgen);
       else
         cell_enter(m, cell, cx, cy, cz);
-      if (COUNT && state == S_MARCH) {
+      if (COUNT) {
         ++n_cells;
         n_acells += cell.cmask != 0;
       }
     }
-    if (state == S_MARCH) {
-      const bool empty = cell.cmask == 0;
-      if (empty || (cell.positive && !cell.jumped)) {
-        // an empty cell holds no defined sample; in an all-positive cell (brick bounds cover
-        // the +1 apron its trilinear corners reach) no sample can end a crossing: resume two
-        // samples before its exit, the first of which fixes the state
-        float tex = 3.4e38f;
-        const int cc[3] = {cx, cy, cz};
+    const bool empty = cell.cmask == 0;
+    if (empty || (cell.positive && !cell.jumped)) {
+      // an empty cell holds no defined sample; in an all-positive cell (brick bounds cover
+      // the +1 apron its trilinear corners reach) no sample can end a crossing: resume two
+      // samples before its exit, the first of which fixes the state
+      float tex = 3.4e38f;
+      const int cc[3] = {cx, cy, cz};
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          if (r[q] > 0.f)
-            tex = fminf(tex, (org[q] + (cc[q] + 1) * bsz - o[q]) * ri[q]);
-          else if (r[q] < 0.f)
-            tex = fminf(tex, (org[q] + cc[q] * bsz - o[q]) * ri[q]);
-        }
-        if (empty) {
-          if (COUNT) ++n_samples;
-          prev_def = false;
-          k = max(k + 1, (int)ceilf(tex / step - 1e-3f));
-          continue;
-        }
-        cell.jumped = true;
-        const int kj = (int)floorf(tex / step) - 1;
-        if (kj > k) {
-          if (COUNT) ++n_jumps;
-          k = kj;
-          prev_def = false;
-          continue;
-        }
+      for (int q = 0; q < 3; ++q) {
+        if (r[q] > 0.f)
+          tex = fminf(tex, (org[q] + (cc[q] + 1) * bsz - o[q]) * ri[q]);
+        else if (r[q] < 0.f)
+          tex = fminf(tex, (org[q] + cc[q] * bsz - o[q]) * ri[q]);
       }
-      if (COUNT) ++n_samples;
+      if (empty) {
+        if (COUNT) ++n_samples;
+        prev_def = false;
+        k = max(k + 1, (int)ceilf(tex / step - 1e-3f));
+        continue;
+      }
+      cell.jumped = true;
+      const int kj = (int)floorf(tex / step) - 1;
+      if (kj > k) {
+        if (COUNT) ++n_jumps;
+        k = kj;
+        prev_def = false;
+        continue;
+      }
     }
-    // ---- evaluate the field at t (single call sites)
+    if (COUNT) ++n_samples;
+    // ---- the sign of Phi at the sample: from the present directions' values where they agree,
+    // else from the full combination
     int sg = 0;
     float val = 0.f;
-    Combined C;
-    C.defined = 0;
-    C.wsum = 0.f;
-    if (cell.cmask) {
-      // the bracket ends need Phi's value: from the sign test when one facing direction is
-      // present, else from the full combination; the outputs always need the full combination
-      bool full = state >= S_OUT;
-      if (!full) {
-        int npres = 0;
-        if constexpr (STORE == STORE_COMBINED)
-          sg = sign_comb(m, cell, g, val, npres);
-        else
-          sg = sign_fast<STORE, COUNT>(m, cell, g, r, val, npres, touched);
-        full = sg == 2 || (state >= S_ENDS_A && npres > 1);
-        if (!full && state >= S_ENDS_A) {
-          C.defined = sg != 0;
-          C.phi = val;
-        }
-      }
-      if (full) {
-        if (COUNT && state == S_MARCH) ++n_full;
-        if constexpr (STORE == STORE_COMBINED)
-          C = full_comb<COLOR>(m, cell, g, state == S_OUT, cgen);
-        else
-          C = combine_full<STORE, COLOR, COUNT>(m, cell, g, r, touched, state == S_OUT);
-        sg = C.defined ? (C.phi > 0.f ? 1 : -1) : 0;
-        val = C.phi;
-      }
+    int npres = 0;
+    if constexpr (STORE == STORE_COMBINED)
+      sg = sign_comb(m, cell, gi, fr, val, npres);
+    else
+      sg = sign_fast<STORE, COUNT>(m, cell, gi, fr, r, val, npres, touched);
+    if (sg == 2) {
+      if (COUNT) ++n_full;
+      Combined C;
+      if constexpr (STORE == STORE_COMBINED)
+        C = full_comb<false>(m, cell, gi, fr, false, cgen);
+      else
+        C = combine_full<STORE, false, COUNT>(m, cell, gi, fr, r, touched, false);
+      sg = C.defined ? (C.phi > 0.f ? 1 : -1) : 0;
+      val = C.phi;
     }
     // ---- transitions
-    if (state == S_MARCH) {
-      if (sg == 0) {
-        prev_def = false;
-        ++k;
-      } else if (sg < 0 && prev_def && prev_phi > 0.f) {
-        // crossing between samples k-1 and k: bisection of the bracket
-        ta = (float)(k - 1) * step;
-        tb = (float)k * step;
-        j = 0;
-        state = S_SCAN;
-      } else {
-        prev_def = true;
-        prev_phi = sg > 0 ? val : -1.f;
-        ++k;
-      }
-    } else if (state == S_SCAN) {
-      // an undefined midpoint counts as free space
-      if (sg < 0)
-        tb = t;
-      else
-        ta = t;
-      if (++j == REFINE_HALVINGS) state = S_ENDS_A;
-    } else if (state == S_ENDS_A) {
-      da = C.defined && C.phi > 0.f;
-      fa = C.phi;
-      state = S_ENDS_B;
-    } else if (state == S_ENDS_B) {
-      // root: linear interpolation of Phi over the final bracket
-      const bool db = C.defined && C.phi <= 0.f;
-      ts = (da && db) ? ta + (tb - ta) * fa / (fa - C.phi) : 0.5f * (ta + tb);
-      state = S_OUT;
+    if (sg == 0) {
+      prev_def = false;
+      ++k;
+    } else if (sg < 0 && prev_def && prev_phi > 0.f) {
+      // crossing between samples k-1 and k: handed to the refinement pass
+      const unsigned h = atomicAdd(a.nhits, 1u);
+      a.hits[h] = make_int2(pix, (k << 6) | jb);
+      if (COUNT) ++n_hits;
+      state = S_DONE;
     } else {
-      // normal and colour at the root's non-positive side (the final bracket's end tb, where Phi
-      // is defined); a miss if no direction has a combination weight there
-      const float nl = sqrtf(C.n[0] * C.n[0] + C.n[1] * C.n[1] + C.n[2] * C.n[2]);
-      bool done = true;
-      if (C.defined && C.wsum > 0.f && nl > 0.f) {
-        const Pose32& T = s_pose[jb];
-        const float n0 = C.n[0] / nl, n1 = C.n[1] / nl, n2 = C.n[2] / nl;
-        // world -> camera: R^T n
-        const float c0 = T.R[0] * n0 + T.R[3] * n1 + T.R[6] * n2;
-        const float c1 = T.R[1] * n0 + T.R[4] * n1 + T.R[7] * n2;
-        const float c2 = T.R[2] * n0 + T.R[5] * n1 + T.R[8] * n2;
-        out_depth = ts / rl;
-        out_n = make_float4(c0, c1, c2, out_depth);
-        if (COLOR && C.cw > 0.f) out_c = make_float4(C.rgb[0] / C.cw, C.rgb[1] / C.cw, C.rgb[2] / C.cw, 1.0f);
-      }
-      if (done) {
-        const RenderJob& J = a.job[jb];
-        J.depth[pix] = out_depth;
-        J.normals[pix] = out_n;
-        if (COLOR && J.color) J.color[pix] = out_c;
-        if (COUNT) n_hits += out_depth > 0.f;
-        state = S_DONE;
-      }
+      prev_def = true;
+      prev_phi = sg > 0 ? val : -1.f;
+      ++k;
     }
   }
   if (COUNT) {
@@ -760,6 +686,163 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
     atomicAdd(ctr + 3, (unsigned long long)n_acells);
     atomicAdd(ctr + 4, (unsigned long long)n_hits);
     atomicAdd(ctr + 5, (unsigned long long)n_jumps);
+  }
+}
+
+// The refinement of one crossing per lane (Sec. 4): REFINE_HALVINGS bisection steps of the
+// bracket [t_{k-1}, t_k] on the sign of Phi (an undefined midpoint counts as free space), Phi at
+// the final bracket's two ends for the linear root, then the outputs at its non-positive end,
+// where Phi is defined (a miss if no direction has a combination weight there). The samples are
+// placed from the bracket's first sample, computed in double precision from the pose, plus the
+// offset along the ray, so that the root and the outputs are placed to ~1e-6 voxel like the
+// double-precision definition (the combined normal can turn by milliradians over 1e-4 voxel).
+template <int STORE, bool COLOR, bool COUNT, int NJ>
+__global__ void __launch_bounds__(RT_N, 3) k_refine(MapView m, RenderBatch<NJ> a) {
+  __shared__ int s_slot[ND * RT_N];
+  __shared__ Pose32 s_pose[NJ];
+  uint8_t* touched = a.touched;
+  const int tid = threadIdx.x;
+  for (int jb = tid; jb < a.njobs; jb += RT_N) s_pose[jb] = a.job[jb].Tdev ? pose_from_device(a.job[jb].Tdev) : a.job[jb].T;
+  __syncthreads();
+  Cell cell;
+  cell.slot = s_slot + tid;
+  const uint32_t cgen = STORE == STORE_COMBINED ? __ldg(m.comb_cur) : 0u;
+  const float inv_h = 1.0f / m.h;
+  const float step = 0.5f * m.h;
+  const unsigned n = min(*((volatile unsigned*)a.nhits), (unsigned)a.total);
+  for (unsigned i = blockIdx.x * RT_N + tid; i < n; i += gridDim.x * RT_N) {
+    const int2 hr = a.hits[i];
+    const int pix = hr.x, k = hr.y >> 6, jb = hr.y & 63;
+    const RenderJob& J = a.job[jb];
+    const Pose32& T = s_pose[jb];
+    const int pu = pix % J.K.W, pv = pix / J.K.W;
+    // the march's single-precision ray (weights and offsets), and the bracket's first sample in
+    // double precision: integer voxel coordinates and fractions
+    float r[3], rl;
+    {
+      const float rc0 = (pu - J.K.cx) / J.K.fx, rc1 = (pv - J.K.cy) / J.K.fy;
+      rl = sqrtf(rc0 * rc0 + rc1 * rc1 + 1.0f);
+      const float q0 = rc0 / rl, q1 = rc1 / rl, q2 = 1.0f / rl;
+      r[0] = T.R[0] * q0 + T.R[1] * q1 + T.R[2] * q2;
+      r[1] = T.R[3] * q0 + T.R[4] * q1 + T.R[5] * q2;
+      r[2] = T.R[6] * q0 + T.R[7] * q1 + T.R[8] * q2;
+    }
+    int bi[3];
+    float bf[3];
+    {
+      double Rd[9], Od[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+#pragma unroll
+        for (int e = 0; e < 3; ++e) Rd[3 * q + e] = J.Tdev ? __ldg(J.Tdev + 4 * q + e) : J.T64[3 * q + e];
+        Od[q] = J.Tdev ? __ldg(J.Tdev + 4 * q + 3) : J.T64[9 + q];
+      }
+      const double q0 = ((double)pu - (double)J.K.cx) / (double)J.K.fx;
+      const double q1 = ((double)pv - (double)J.K.cy) / (double)J.K.fy;
+      const double ql = sqrt(q0 * q0 + q1 * q1 + 1.0);
+      const double hd = (double)m.h;
+      const double t0 = (double)(k - 1) * (0.5 * hd);
+      const double org[3] = {(double)m.ox, (double)m.oy, (double)m.oz};
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const double rq = (Rd[3 * q] * q0 + Rd[3 * q + 1] * q1 + Rd[3 * q + 2]) / ql;
+        const double gq = (Od[q] + t0 * rq - org[q]) / hd;
+        const double fq = floor(gq);
+        bi[q] = (int)fq;
+        bf[q] = (float)(gq - fq);
+      }
+    }
+    cell.cx = cell.cy = cell.cz = 0x7fffffff;
+    cell.cmask = 0;
+    float ta = 0.f, tb = step, fa = 0.f, ts = 0.f;
+    bool da = false;
+    float out_depth = 0.f;
+    float4 out_n = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 out_c = make_float4(0.f, 0.f, 0.f, 0.f);
+    // phases: 0 bisection (REFINE_HALVINGS steps), 1 and 2 the final bracket's ends, 3 outputs
+#pragma unroll 1
+    for (int j = 0; j < REFINE_HALVINGS + 3; ++j) {
+      const int phase = j < REFINE_HALVINGS ? 0 : j - REFINE_HALVINGS + 1;
+      const float t = phase == 0 ? 0.5f * (ta + tb) : (phase == 1 ? ta : tb);
+      int gi[3];
+      float fr[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float gq = bf[q] + t * (r[q] * inv_h);
+        const float fq = floorf(gq);
+        gi[q] = bi[q] + (int)fq;
+        fr[q] = gq - fq;
+      }
+      const int cx = gi[0] >> 3, cy = gi[1] >> 3, cz = gi[2] >> 3;
+      if (cx != cell.cx || cy != cell.cy || cz != cell.cz) {
+        if constexpr (STORE == STORE_COMBINED)
+          cell_enter_comb(m, cell, cx, cy, cz, cgen);
+        else
+          cell_enter(m, cell, cx, cy, cz);
+      }
+      // the bracket ends need Phi's value: from the sign test when one facing direction is
+      // present, else from the full combination; the outputs always need the full combination
+      int sg = 0;
+      Combined C;
+      C.defined = 0;
+      C.phi = 0.f;
+      C.wsum = 0.f;
+      C.n[0] = C.n[1] = C.n[2] = 0.f;
+      C.rgb[0] = C.rgb[1] = C.rgb[2] = 0.f;
+      C.cw = 0.f;
+      if (cell.cmask) {
+        bool full = phase == 3;
+        if (!full) {
+          int npres = 0;
+          float val = 0.f;
+          if constexpr (STORE == STORE_COMBINED)
+            sg = sign_comb(m, cell, gi, fr, val, npres);
+          else
+            sg = sign_fast<STORE, COUNT>(m, cell, gi, fr, r, val, npres, touched);
+          full = sg == 2 || (phase >= 1 && npres > 1);
+          if (!full) {
+            C.defined = sg != 0;
+            C.phi = val;
+          }
+        }
+        if (full) {
+          if constexpr (STORE == STORE_COMBINED)
+            C = full_comb<COLOR>(m, cell, gi, fr, phase == 3, cgen);
+          else
+            C = combine_full<STORE, COLOR, COUNT>(m, cell, gi, fr, r, touched, phase == 3);
+          sg = C.defined ? (C.phi > 0.f ? 1 : -1) : 0;
+        }
+      }
+      if (phase == 0) {
+        // an undefined midpoint counts as free space
+        if (sg < 0)
+          tb = t;
+        else
+          ta = t;
+      } else if (phase == 1) {
+        da = C.defined && C.phi > 0.f;
+        fa = C.phi;
+      } else if (phase == 2) {
+        // root: linear interpolation of Phi over the final bracket
+        const bool db = C.defined && C.phi <= 0.f;
+        ts = (da && db) ? ta + (tb - ta) * fa / (fa - C.phi) : 0.5f * (ta + tb);
+      } else {
+        const float nl = sqrtf(C.n[0] * C.n[0] + C.n[1] * C.n[1] + C.n[2] * C.n[2]);
+        if (C.defined && C.wsum > 0.f && nl > 0.f) {
+          const float n0 = C.n[0] / nl, n1 = C.n[1] / nl, n2 = C.n[2] / nl;
+          // world -> camera: R^T n
+          const float c0 = T.R[0] * n0 + T.R[3] * n1 + T.R[6] * n2;
+          const float c1 = T.R[1] * n0 + T.R[4] * n1 + T.R[7] * n2;
+          const float c2 = T.R[2] * n0 + T.R[5] * n1 + T.R[8] * n2;
+          out_depth = ((float)(k - 1) * step + ts) / rl;
+          out_n = make_float4(c0, c1, c2, out_depth);
+          if (COLOR && C.cw > 0.f) out_c = make_float4(C.rgb[0] / C.cw, C.rgb[1] / C.cw, C.rgb[2] / C.cw, 1.0f);
+        }
+      }
+    }
+    J.depth[pix] = out_depth;
+    J.normals[pix] = out_n;
+    if (COLOR && J.color) J.color[pix] = out_c;
   }
 }
 
@@ -850,11 +933,12 @@ int resident_ctas(KernelT kern) {
 
 template <int STORE, bool COLOR, bool COUNT, int NJ>
 void launch_k_render(const MapView& m, const RenderBatch<NJ>& a, int ctas, cudaStream_t s) {
-  static thread_local int cached_dev = -1, cached_ctas = 0;
+  static thread_local int cached_dev = -1, cached_ctas = 0, cached_refine = 0;
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev != cached_dev) {
     cached_ctas = resident_ctas(k_render<STORE, COLOR, COUNT, NJ>);
+    cached_refine = resident_ctas(k_refine<STORE, COLOR, COUNT, NJ>);
     cached_dev = dev;
   }
   int grid = ctas > 0 ? ctas : cached_ctas;
@@ -862,6 +946,11 @@ void launch_k_render(const MapView& m, const RenderBatch<NJ>& a, int ctas, cudaS
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
   k_render<STORE, COLOR, COUNT, NJ><<<grid, RT_N, 0, s>>>(m, a);
+  // the crossings are at most one per ray; their count is known on the device only
+  int rgrid = cached_refine;
+  if (rgrid > need) rgrid = need;
+  if (rgrid < 1) rgrid = 1;
+  k_refine<STORE, COLOR, COUNT, NJ><<<rgrid, RT_N, 0, s>>>(m, a);
 }
 
 template <int NJ>
@@ -920,31 +1009,40 @@ void fill_batch(RenderBatch<NJ>& a, const RenderJob* jobs, int njobs, unsigned* 
 template <int NJ>
 cudaError_t range_and_render(const MapView& m, RenderBatch<NJ>& a, bool col, int ctas, cudaStream_t s,
                              cudaMemPool_t pool, bool combined) {
-  uint32_t* buf = nullptr;
+  // scratch: the crossing list (8 bytes per ray), its counter (16 bytes), then the depth
+  // ranges of the ray tiles (2 words per tile)
   const size_t ntiles = (size_t)a.total / 32;
+  const size_t hit_bytes = (size_t)a.total * sizeof(int2);
+  const size_t bytes = hit_bytes + 16 + 2 * ntiles * sizeof(uint32_t);
+  char* buf = nullptr;
+  cudaError_t e = pool ? cudaMallocFromPoolAsync((void**)&buf, bytes, pool, s) : cudaMallocAsync((void**)&buf, bytes, s);
+  if (e != cudaSuccess) return e;
+  a.hits = (int2*)buf;
+  a.nhits = (unsigned*)(buf + hit_bytes);
+  uint32_t* zr = (uint32_t*)(buf + hit_bytes + 16);
   a.zlo = a.zhi = nullptr;
-  if (pool && ntiles) {
-    cudaError_t e = cudaMallocFromPoolAsync((void**)&buf, 2 * ntiles * sizeof(uint32_t), pool, s);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(buf, 0xFF, ntiles * sizeof(uint32_t), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(buf + ntiles, 0, ntiles * sizeof(uint32_t), s);
-    if (e != cudaSuccess) return e;
-    static thread_local int sms = 0;
-    if (!sms) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 132;
+  e = cudaMemsetAsync(a.nhits, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess && ntiles) {
+    e = cudaMemsetAsync(zr, 0xFF, ntiles * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(zr + ntiles, 0, ntiles * sizeof(uint32_t), s);
+    if (e == cudaSuccess) {
+      static thread_local int sms = 0;
+      if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 132;
+      }
+      k_tile_range<NJ><<<sms * 4, 256, 0, s>>>(m, a, zr, zr + ntiles);
+      a.zlo = zr;
+      a.zhi = zr + ntiles;
     }
-    k_tile_range<NJ><<<sms * 4, 256, 0, s>>>(m, a, buf, buf + ntiles);
-    a.zlo = buf;
-    a.zhi = buf + ntiles;
   }
-  dispatch_render(m, a, col, ctas, s, combined);
-  cudaError_t e = cudaGetLastError();
-  if (buf) {
-    const cudaError_t f = cudaFreeAsync(buf, s);
-    if (e == cudaSuccess) e = f;
+  if (e == cudaSuccess) {
+    dispatch_render(m, a, col, ctas, s, combined);
+    e = cudaGetLastError();
   }
+  const cudaError_t f = cudaFreeAsync(buf, s);
+  if (e == cudaSuccess) e = f;
   return e;
 }
 

@@ -7,6 +7,7 @@ import time
 import numpy as np
 import pytest
 
+import angles
 import scenes
 
 torch = pytest.importorskip("torch")
@@ -130,3 +131,62 @@ def test_admission_by_memory_budget(setup):
     alone, _ = serve(maps, reqs, sel)
     for i in sel:
         assert np.array_equal(pose(res[i]), pose(alone[i]))
+
+
+@pytest.fixture(scope="module")
+def oracle_setup():
+    """One room's map fused by the oracle (FP64) from every fourth of 20 frames, loaded into an FP32
+    and an FP16 device map (the FP16 one holds the oracle's values rounded to its storage)."""
+    import oracle
+    room = scenes.kinect_room(1, n_frames=20)
+    om = oracle.OracleMap(oracle.Params(voxel_size=0.005, truncation=0.02, z_max=room.z_max, color=False))
+    for i in range(0, 20, 4):
+        f = room.frame(i)
+        om.integrate(f.depth, None, room.K, f.pose)
+    ob = om.bricks()
+    vox = np.stack([om.brick(*b[:4]) for b in ob]).astype(np.float32)
+    maps = []
+    for storage in (dt.STORE_FP32, dt.STORE_FP16):
+        m = dt.Map(dt.params(voxel_size=0.005, truncation=0.02, max_blocks=len(ob) + 64, z_max=room.z_max,
+                             color=False, storage=storage))
+        m.import_bricks(ob[:, :4], vox)
+        maps.append(m)
+    torch.cuda.synchronize()
+    # 640x480 and 320x240 SE(3) on the FP32 map, 1280x720 SE(3) and 320x240 Sim(3) on the FP16 map
+    reqs = scenes.serve_requests([room, room], 4, seed=2)
+    yield om, maps, reqs
+    for m in maps:
+        m.close()
+
+
+def test_served_poses_match_oracle_schedule(oracle_setup):
+    """Each served registration against the oracle's own pipeline on the same request: its render of
+    the map at the prior, its preprocessing and pyramid of the request's depth, its coarse-to-fine
+    schedule (SE(3) or Sim(3), 3 levels x 10 iterations). Pose within 1e-4 rad / 1e-4 m and scale
+    within 1e-5 on the FP32 map; the FP16 map's rounding of the sdf (at most 2^-11 of its value,
+    about 1e-6 m near the surface) and of the weights is held to the same bounds."""
+    import oracle
+    from oracle import icp as oicp
+    om, maps, reqs = oracle_setup
+    assert [(q["K"].width, q["sim3"], q["map"]) for q in reqs] == [(640, False, 0), (320, False, 0),
+                                                                     (1280, False, 1), (320, True, 1)]
+    res, _ = serve(maps, reqs, list(range(len(reqs))))
+    for i, q in enumerate(reqs):
+        K = q["K"]
+        do, no, _, _ = om.render(K, q["prior"])
+        rn = np.zeros(no.shape[:2] + (4,), np.float32)
+        rn[..., :3] = no
+        rn[..., 3] = do
+        pre = oracle.preprocess(q["depth"], K, 0.1, 6.0, 0.01)
+        levels = oicp.pyramid(pre["z"], K, 3)
+        st = oicp.Settings(sim3=bool(q["sim3"]), eps=OPTS["eps"], iters=OPTS["iters"], lam=0.0, z_min=0.1,
+                           stop=OPTS["stop_norm"], min_rows=OPTS["min_rows"])
+        To, _ = oicp.track(levels, do.astype(np.float32), rn, K, np.eye(4), st)
+        Tg = pose(res[i])
+        sg, so = np.cbrt(np.linalg.det(Tg[:3, :3])), np.cbrt(np.linalg.det(To[:3, :3]))
+        ang = angles.rotation(Tg[:3, :3] / sg, To[:3, :3] / so)
+        dtr = np.linalg.norm(Tg[:3, 3] - To[:3, 3])
+        print(f"served {K.width}x{K.height} {'Sim(3)' if q['sim3'] else 'SE(3)'} map {q['map']}: "
+              f"{ang:.2e} rad, {dtr:.2e} m, scale {abs(sg / so - 1):.2e} from the oracle")
+        assert ang <= 1e-4 and dtr <= 1e-4 and abs(sg / so - 1) <= 1e-5, i
+        assert np.allclose(pose(res[i], "T_wc"), q["prior"] @ Tg, atol=1e-9)
