@@ -759,6 +759,10 @@ __global__ void __launch_bounds__(RT_N, 3) k_refine(MapView m, RenderBatch<NJ> a
     float out_depth = 0.f;
     float4 out_n = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 out_c = make_float4(0.f, 0.f, 0.f, 0.f);
+    // after an evaluation that needed the full combination, the next one (a nearby point) goes
+    // to it directly: the sign test's corners would be read twice (both give the same sign
+    // where the sign test decides)
+    bool went_full = false;
     // phases: 0 bisection (REFINE_HALVINGS steps), 1 and 2 the final bracket's ends, 3 outputs
 #pragma unroll 1
     for (int j = 0; j < REFINE_HALVINGS + 3; ++j) {
@@ -791,7 +795,7 @@ __global__ void __launch_bounds__(RT_N, 3) k_refine(MapView m, RenderBatch<NJ> a
       C.rgb[0] = C.rgb[1] = C.rgb[2] = 0.f;
       C.cw = 0.f;
       if (cell.cmask) {
-        bool full = phase == 3;
+        bool full = phase == 3 || (STORE != STORE_COMBINED && went_full);
         if (!full) {
           int npres = 0;
           float val = 0.f;
@@ -805,6 +809,7 @@ __global__ void __launch_bounds__(RT_N, 3) k_refine(MapView m, RenderBatch<NJ> a
             C.phi = val;
           }
         }
+        went_full = full;
         if (full) {
           if constexpr (STORE == STORE_COMBINED)
             C = full_comb<COLOR>(m, cell, gi, fr, phase == 3, cgen);
