@@ -559,7 +559,9 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
     if (!__any_sync(0xffffffffu, alive)) break;
     if (!alive || state == S_DONE) continue;
 
-    // ---- one sample of this lane's ray
+    // ---- samples of this lane's ray: one per pass of the refill loop, or, when the whole warp
+    // refills together, every sample until the ray is finished (no warp vote per sample)
+    do {
     if (++it > a.max_samples || k > k1) {
       // a miss (or the sample limit): write the zero outputs
       const RenderJob& J = a.job[jb];
@@ -678,6 +680,7 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
       prev_phi = sg > 0 ? val : -1.f;
       ++k;
     }
+    } while (a.refill >= 32 && state == S_MARCH);
   }
   if (COUNT) {
     atomicAdd(ctr + 0, (unsigned long long)n_samples);
