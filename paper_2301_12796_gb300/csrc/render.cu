@@ -14,8 +14,9 @@
 // the signs disagree and for the outputs. The reported crossing is the first pair of
 // consecutive defined samples with Phi > 0 >= Phi; the hit is the root of Phi(t) in that
 // bracket, found by REFINE_HALVINGS bisection steps on the sign of Phi (an undefined point
-// counts as free space) and linear interpolation over the final bracket (h / 2^17 wide);
-// normal and colour are evaluated at the bracket's non-positive end, where Phi is defined.
+// counts as free space): the depth is the final bracket's midpoint (h / 2^17 wide, so within
+// 2e-8 m of the root at h = 5 mm); normal and colour are evaluated at the bracket's
+// non-positive end, where Phi is defined.
 // The refinement places its samples from the bracket's first sample computed in double
 // precision from the pose, so its positions carry the rounding of a small offset only.
 // The per-block occupancy filters let empty space be crossed without probes, and per-brick
@@ -693,9 +694,9 @@ __global__ void __launch_bounds__(RT_N, DTSDF_RENDER_MINB) k_render(MapView m, R
 }
 
 // The refinement of one crossing per lane (Sec. 4): REFINE_HALVINGS bisection steps of the
-// bracket [t_{k-1}, t_k] on the sign of Phi (an undefined midpoint counts as free space), Phi at
-// the final bracket's two ends for the linear root, then the outputs at its non-positive end,
-// where Phi is defined (a miss if no direction has a combination weight there). The samples are
+// bracket [t_{k-1}, t_k] on the sign of Phi (an undefined midpoint counts as free space), then
+// the outputs at the final bracket's non-positive end, where Phi is defined (a miss if no
+// direction has a combination weight there); the depth is the final bracket's midpoint. The samples are
 // placed from the bracket's first sample, computed in double precision from the pose, plus the
 // offset along the ray, so that the root and the outputs are placed to ~1e-6 voxel like the
 // double-precision definition (the combined normal can turn by milliradians over 1e-4 voxel).
@@ -757,8 +758,7 @@ __global__ void __launch_bounds__(RT_N, 3) k_refine(MapView m, RenderBatch<NJ> a
     }
     cell.cx = cell.cy = cell.cz = 0x7fffffff;
     cell.cmask = 0;
-    float ta = 0.f, tb = step, fa = 0.f, ts = 0.f;
-    bool da = false;
+    float ta = 0.f, tb = step;
     float out_depth = 0.f;
     float4 out_n = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 out_c = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -766,11 +766,11 @@ __global__ void __launch_bounds__(RT_N, 3) k_refine(MapView m, RenderBatch<NJ> a
     // to it directly: the sign test's corners would be read twice (both give the same sign
     // where the sign test decides)
     bool went_full = false;
-    // phases: 0 bisection (REFINE_HALVINGS steps), 1 and 2 the final bracket's ends, 3 outputs
+    // phases: 0 bisection (REFINE_HALVINGS steps), 3 outputs at the final bracket's end tb
 #pragma unroll 1
-    for (int j = 0; j < REFINE_HALVINGS + 3; ++j) {
-      const int phase = j < REFINE_HALVINGS ? 0 : j - REFINE_HALVINGS + 1;
-      const float t = phase == 0 ? 0.5f * (ta + tb) : (phase == 1 ? ta : tb);
+    for (int j = 0; j <= REFINE_HALVINGS; ++j) {
+      const int phase = j < REFINE_HALVINGS ? 0 : 3;
+      const float t = phase == 0 ? 0.5f * (ta + tb) : tb;
       int gi[3];
       float fr[3];
 #pragma unroll
@@ -827,14 +827,9 @@ __global__ void __launch_bounds__(RT_N, 3) k_refine(MapView m, RenderBatch<NJ> a
           tb = t;
         else
           ta = t;
-      } else if (phase == 1) {
-        da = C.defined && C.phi > 0.f;
-        fa = C.phi;
-      } else if (phase == 2) {
-        // root: linear interpolation of Phi over the final bracket
-        const bool db = C.defined && C.phi <= 0.f;
-        ts = (da && db) ? ta + (tb - ta) * fa / (fa - C.phi) : 0.5f * (ta + tb);
       } else {
+        // the root: the final bracket's midpoint (within h / 2^(REFINE_HALVINGS + 2) of it)
+        const float ts = 0.5f * (ta + tb);
         const float nl = sqrtf(C.n[0] * C.n[0] + C.n[1] * C.n[1] + C.n[2] * C.n[2]);
         if (C.defined && C.wsum > 0.f && nl > 0.f) {
           const float n0 = C.n[0] / nl, n1 = C.n[1] / nl, n2 = C.n[2] / nl;
