@@ -41,11 +41,13 @@ WORKLOAD_MS = ("multi-sensor Sim(3): map of the 4x4x3 m room from 300 sensor-A f
                "(3 levels x 20 iterations), the step captured in a CUDA graph")
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_render launch of the
-# default workload (FP32 storage with colour, first timed render), from one ncu capture of
-# ``bench.py --steps 2 --warmup 3 --no-e2e --no-cpu`` (profiles/k_render_kinect640.md). It
-# belongs to the kernel sources it was taken with: reported only while their hash matches.
-RENDER_TRAFFIC = {"bytes": 272414720 + 11687424, "sources_sha1_16": "b8d9a7b899f1164f",
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one render of the default
+# workload (FP32 storage with colour, a render of the timed steps): the march (k_render) and the
+# crossing refinement (k_refine), from one ncu capture of
+# ``bench.py --steps 2 --warmup 3 --no-e2e --no-cpu --no-serve --no-multi``
+# (profiles/k_render_kinect640.md). It belongs to the kernel sources it was taken with: reported
+# only while their hash matches.
+RENDER_TRAFFIC = {"bytes": 232785408 + 5401344 + 198563584 + 6508800, "sources_sha1_16": "254c698a9b355030",
                   "files": ("render.cu", "common.cuh", "internal.h")}
 
 
@@ -439,6 +441,11 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
     for i in range(args.warmup):
         tr.step(i)
     torch.cuda.synchronize()
+    # autotuner: launch shape of the render (persistent CTAs, refill group, ray tile) at the pose
+    # of the first timed frame's reference, chosen before the timed region
+    shape_pose = frames[1 + args.warmup % (tr.n - 1) - 1].pose
+    render_shape, render_tune_ms = tr.map.tune_render(s.K, shape_pose, tr.ref_d, tr.ref_n, tr.ref_c)
+    torch.cuda.synchronize()
     npix = s.K.width * s.K.height
     # event counts of one render (instrumented build of the march: samples, full combinations,
     # block cells entered, allocated cells, hits, cell jumps)
@@ -565,7 +572,8 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                 "traffic": None, "algorithmic_bytes_per_launch": render_bytes, "launch_ms": render_ms,
                 "bytes_definition": bytes_def}
-    roof = roof or {"kernel": "k_render (direct DTSDF ray-cast)", "bound": "hbm", "achieved": achieved, "peak": peak,
+    roof = roof or {"kernel": "k_render + k_refine (direct DTSDF ray-cast: the march, then the crossing refinement)",
+            "bound": "hbm", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
             "traffic": render_traffic() if storage == 0 and not args.profile else None,
             "algorithmic_bytes_per_launch": render_bytes, "launch_ms": render_ms, "bytes_definition": bytes_def,
@@ -601,6 +609,8 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
                                                                                       for x in st.bricks_per_dir],
                           "l2": "flushed between steps (512 MB write outside the timed events)",
                           "parallelism": f"replicas x{world}",
+                          "render_shape": {"ctas": render_shape[0], "refill": render_shape[1],
+                                           "tile_w": render_shape[2], "tuned_ms": render_tune_ms},
                           "phase_ms": {"render": render_ms, "preprocess_pyramid_icp": float(ph[:, 1].mean()),
                                        "fusion": float(ph[:, 2].mean())},
                           "rays_per_s": world * npix * args.steps / (total_ms / 1000.0),
