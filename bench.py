@@ -438,6 +438,7 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
                  freespace=args.render_mode == "freespace")
     st = tr.map.stats()
     l2 = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MB > L2
+    flush_l2(l2)  # the flush kernel's first launch loads its module (~0.8 s): keep it out of the timed loop
     for i in range(args.warmup):
         tr.step(i)
     torch.cuda.synchronize()
@@ -762,6 +763,7 @@ def run_multi_sensor(args, dt, torch, tdist, dev, rank, world, local, emit=True)
             ms.step(side)
     stream.wait_stream(side)
     l2 = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
+    flush_l2(l2)
     for _ in range(args.warmup):
         g.replay()
     torch.cuda.synchronize()
