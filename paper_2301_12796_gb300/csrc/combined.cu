@@ -67,13 +67,28 @@ __global__ void k_comb_policy(CombState* st, const double* Tdev, Pose64 Tv, cons
   }
 }
 
+// Bricks of the blocks {0, 1}^3 from block d for the 6 directions (src[D][j], -1: none): voxel
+// (x, y, z) of [0, 8]^3 belongs to block (x >> 3, y >> 3, z >> 3) and is combined from that
+// block's directions (a voxel's data is its own block's). One thread per neighbour j.
+__device__ __forceinline__ void comb_sources(const MapView& m, uint32_t d, int j, int (*src)[8]) {
+  const int bx = m.dir_coord[4 * d], by = m.dir_coord[4 * d + 1], bz = m.dir_coord[4 * d + 2];
+  const int dd = j == 0 ? (int)d : hash_find(m, bx + (j & 1), by + ((j >> 1) & 1), bz + (j >> 2));
+  const uint32_t mask = dd >= 0 ? (uint32_t)m.dir_slots[(size_t)dd * 8 + SLOT_MASK] : 0u;
+#pragma unroll
+  for (int D = 0; D < ND; ++D) src[D][j] = ((mask >> D) & 1u) ? m.dir_slots[(size_t)dd * 8 + D] : -1;
+}
+
 // Register budget for 8 resident CTAs per SM (32 registers, a few spilled bytes): the pass is
 // bound by the latency of its dependent reads, and more warps in flight beat fewer spills
 // (forced whole-frustum pass on the 300-frame Kinect map: 1.00 ms at 5 CTAs per SM, 0.93 ms at
-// 6, 0.86 ms at 8).
+// 6, 0.86 ms at 8). The CTA walks its blocks with the bricks of the next block looked up (hash
+// probes of its 7 neighbours) by 8 threads of its last warp while the others combine the
+// current one.
+constexpr int COMB_PREFETCH_T0 = 224;  // threads 224..231: 2 voxels each instead of 3
+
 template <int STORE, bool COLOR>
 __global__ void __launch_bounds__(256, 8) k_combine(MapView m, const CombState* st, CombFrame f) {
-  __shared__ int s_src[ND][8];
+  __shared__ int s_src[2][ND][8];
   __shared__ float s_c[3];
   __shared__ float s_R[9];
   __shared__ uint32_t s_full, s_gen, s_from;
@@ -90,18 +105,21 @@ __global__ void __launch_bounds__(256, 8) k_combine(MapView m, const CombState* 
   const uint32_t ndir = min(*((volatile uint32_t*)(m.counters + C_DIR)), m.dir_cap);
   const float h = m.h;
   const float cos_lo = m.costh, cos_hi = m.sinth;
-  for (uint32_t d = blockIdx.x; d < ndir; d += gridDim.x) {
-    const uint32_t mask = (uint32_t)m.dir_slots[(size_t)d * 8 + SLOT_MASK];
-    bool take = mask != 0;
-    if (take && !s_full) {  // incremental: blocks with a brick allocated since the last combination
-      bool fresh = false;
-      for (uint32_t mm = mask; mm; mm &= mm - 1) fresh |= (uint32_t)m.dir_slots[(size_t)d * 8 + __ffs(mm) - 1] >= s_from;
-      take = fresh;
-    }
-    const int bx = m.dir_coord[4 * d], by = m.dir_coord[4 * d + 1], bz = m.dir_coord[4 * d + 2];
-    if (take) {
+  // the next block from d on (stride gridDim.x) that this pass combines (ndir if none); uniform
+  auto next_taken = [&](uint32_t d) -> uint32_t {
+    for (; d < ndir; d += gridDim.x) {
+      const uint32_t mask = (uint32_t)m.dir_slots[(size_t)d * 8 + SLOT_MASK];
+      bool take = mask != 0;
+      if (take && !s_full) {  // incremental: blocks with a brick allocated since the last combination
+        bool fresh = false;
+        for (uint32_t mm = mask; mm; mm &= mm - 1)
+          fresh |= (uint32_t)m.dir_slots[(size_t)d * 8 + __ffs(mm) - 1] >= s_from;
+        take = fresh;
+      }
+      if (!take) continue;
       // padded frustum of the combination pose: bounding sphere of the block against the four
       // side planes (image grown by 1/8) and the camera's half-space
+      const int bx = m.dir_coord[4 * d], by = m.dir_coord[4 * d + 1], bz = m.dir_coord[4 * d + 2];
       const float rad = 0.8660254f * 8.0f * h + h;
       const float p0 = m.ox + (8.0f * bx + 3.5f) * h - s_c[0];
       const float p1 = m.oy + (8.0f * by + 3.5f) * h - s_c[1];
@@ -112,24 +130,20 @@ __global__ void __launch_bounds__(256, 8) k_combine(MapView m, const CombState* 
       take = cz > -rad;
 #pragma unroll
       for (int q = 0; q < 4; ++q) take &= (f.pl[q][0] * cx + f.pl[q][1] * cy + f.pl[q][2] * cz) >= -rad;
+      if (take) return d;
     }
-    if (!take) continue;  // uniform over the CTA
-    if (threadIdx.x < 8 * ND) {
-      // bricks of the blocks {0, 1}^3 from this one: voxel (x, y, z) of [0, 8]^3 belongs to block
-      // (x >> 3, y >> 3, z >> 3) and is combined from that block's directions (a voxel's data is
-      // its own block's), not only from the directions this block holds
-      const int D = threadIdx.x >> 3, j = threadIdx.x & 7;
-      int sl = -1;
-      if (j == 0) {
-        if ((mask >> D) & 1u) sl = m.dir_slots[(size_t)d * 8 + D];
-      } else {
-        const int dd = hash_find(m, bx + (j & 1), by + ((j >> 1) & 1), bz + (j >> 2));
-        if (dd >= 0 && ((uint32_t)m.dir_slots[(size_t)dd * 8 + SLOT_MASK] >> D) & 1u)
-          sl = m.dir_slots[(size_t)dd * 8 + D];
-      }
-      s_src[D][j] = sl;
-    }
-    __syncthreads();
+    return ndir;
+  };
+  const int pj = (int)threadIdx.x - COMB_PREFETCH_T0;  // 0..7 on the prefetching threads
+  uint32_t d = next_taken(blockIdx.x);
+  if (d < ndir && pj >= 0 && pj < 8) comb_sources(m, d, pj, s_src[0]);
+  __syncthreads();
+  int cb = 0;
+  while (d < ndir) {
+    const uint32_t dn = next_taken(d + gridDim.x);
+    if (dn < ndir && pj >= 0 && pj < 8) comb_sources(m, dn, pj, s_src[cb ^ 1]);
+    const int bx = m.dir_coord[4 * d], by = m.dir_coord[4 * d + 1], bz = m.dir_coord[4 * d + 2];
+    int (*src)[8] = s_src[cb];
     const float inv2h = 0.5f / h;
     for (int vi = threadIdx.x; vi < CVOX; vi += blockDim.x) {
       const int x = vi % CEDGE, y = (vi / CEDGE) % CEDGE, z = vi / (CEDGE * CEDGE);
@@ -145,7 +159,7 @@ __global__ void __launch_bounds__(256, 8) k_combine(MapView m, const CombState* 
 #pragma unroll 1
       const int own = (x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2);
       for (int D = 0; D < ND; ++D) {
-        const int sl = s_src[D][own];
+        const int sl = src[D][own];
         if (sl < 0) continue;
         const size_t base = (size_t)sl * PVOX + pad_index(x & 7, y & 7, z & 7);
         const float2 v0 = src_geom<STORE>(m, base);
@@ -198,7 +212,9 @@ __global__ void __launch_bounds__(256, 8) k_combine(MapView m, const CombState* 
       if (COLOR) m.comb_col[(size_t)d * CVOX + vi] = oc;
     }
     if (threadIdx.x == 0) m.comb_gen[d] = s_gen;
-    __syncthreads();
+    __syncthreads();  // the next block's sources are in place; this block's may be overwritten
+    cb ^= 1;
+    d = dn;
   }
 }
 
