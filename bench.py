@@ -193,7 +193,10 @@ def opts_kinect(dt, solver="gn"):
                        lam=0.1, z_min=0.1, stop_norm=1e-6, min_rows=10, lm=solver == "lm")
 
 
-LAUNCHES = {"render": 2, "set_frame": 6, "set_keyframe": 6, "compose": 1, "solve": 19, "integrate": 9}
+# kernels per call of the tracking step (counted from the ncu launch list of a step): render =
+# depth-range pass + march + refinement; set_frame = outlier filter, normals, depth extraction,
+# intensity, two pyramid levels, three intensity normalisations
+LAUNCHES = {"render": 3, "set_frame": 9, "set_keyframe": 6, "compose": 1, "solve": 19, "integrate": 9}
 
 
 class Tracker:
@@ -628,7 +631,8 @@ def run_tracking(args, dt, torch, tdist, dev, rank, world, local):
 # ----------------------------------------------------------- multi-sensor --
 MS_ITERS = (20, 20, 20)
 MS_EPS = (0.01, 0.1, 0.2)
-MS_LAUNCHES_PER_FRAME = 5  # outlier filter, normals, depth extraction, 2 pyramid levels
+MS_LAUNCHES_PER_FRAME = 5  # outlier filter, normals, depth extraction, 2 pyramid levels; per batch of 64 also
+# the depth-range pass, march and refinement of the batched render and one batched registration
 
 
 class MultiSensor:
@@ -844,7 +848,7 @@ def run_multi_sensor(args, dt, torch, tdist, dev, rank, world, local, emit=True)
                                                           "trans_m": float(tr[k]), "scale": float(sc[k])}
                                                          for k in np.nonzero(~((rot < 1.0) & (tr < 0.02)))[0]]}},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-               "gpu_launches": n * MS_LAUNCHES_PER_FRAME + 2 * ((n + 63) // 64), "clocks": clocks}
+               "gpu_launches": n * MS_LAUNCHES_PER_FRAME + 4 * ((n + 63) // 64), "clocks": clocks}
         if emit:
             print(json.dumps(out), flush=True)
         ms.map.close()
@@ -1073,7 +1077,7 @@ def run_serve(args, dt, torch, tdist, dev, rank, world, local, emit=True):
                "roofline": roof, "cpu_baseline": cpu,
                "e2e": {"value": value, "unit": "requests/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": ctypes_result_bytes(dt)},
-               "gpu_launches": int(st.batches) * (2 + args.maps) + 5 * len(reqs), "clocks": clocks}
+               "gpu_launches": int(st.batches) * (2 + 3 * args.maps) + 5 * len(reqs), "clocks": clocks}
         if emit:
             print(json.dumps(out), flush=True)
     for m in maps16 + maps32:
