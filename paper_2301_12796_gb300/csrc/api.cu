@@ -512,11 +512,11 @@ static dtsdf_status ensure_combined(dtsdf_map m, cudaStream_t s) {
   if (m->comb_state) return DTSDF_OK;
   const size_t nd = m->v.dir_cap;
   float2* comb = nullptr;
-  float4* col = nullptr;
+  uint2* col = nullptr;
   uint32_t* gen = nullptr;
   CombState* st = nullptr;
   cudaError_t e = dt_malloc((void**)&comb, sizeof(float2) * CVOX * nd);
-  if (e == cudaSuccess && m->p.color) e = dt_malloc((void**)&col, sizeof(float4) * CVOX * nd);
+  if (e == cudaSuccess && m->p.color) e = dt_malloc((void**)&col, sizeof(uint2) * CVOX * nd);
   if (e == cudaSuccess) e = dt_malloc((void**)&gen, sizeof(uint32_t) * nd);
   if (e == cudaSuccess) e = dt_malloc((void**)&st, sizeof(CombState));
   if (e == cudaSuccess) e = cudaMemsetAsync(gen, 0xFF, sizeof(uint32_t) * nd, s);

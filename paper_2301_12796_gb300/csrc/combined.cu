@@ -201,10 +201,10 @@ __global__ void __launch_bounds__(256, 8) k_combine(MapView m, const CombState* 
         }
       }
       float2 out = make_float2(0.f, 0.f);
-      float4 oc = make_float4(0.f, 0.f, 0.f, 0.f);
+      uint2 oc = make_uint2(0u, 0u);
       if (any && ws > 0.0f) {
         out = make_float2(acc / ws, 1.0f);
-        if (COLOR && cw > 0.0f) oc = make_float4(cr / cw, cg / cw, cb / cw, 1.0f);
+        if (COLOR && cw > 0.0f) oc = pack_comb_col(cr / cw, cg / cw, cb / cw, true);
       } else if (any && wf > 0.0f) {
         out = make_float2(af / wf, 1.0f);
       }

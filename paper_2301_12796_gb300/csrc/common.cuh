@@ -170,7 +170,9 @@ struct MapView {
   // view-dependent combined TSDF (allocated on first use): per directory entry the combined
   // values of local voxels [0, 8]^3 (CVOX), x fastest, and the generation they belong to
   float2* comb;        // (phi, 1 if defined else 0)
-  float4* comb_col;    // (r, g, b, 1 if defined else 0), colour maps only
+  uint2* comb_col;     // r, g, b as 16-bit fixed point (c * 257, exact for 8-bit colours; the
+                       // combination of colours rounds to 1/257) and 1 if defined else 0,
+                       // colour maps only
   uint32_t* comb_gen;  // per directory entry
   const uint32_t* comb_cur;  // device word: the current generation
   uint32_t* occ;       // occupancy filters: 2 x OCC_WORDS words (blocks, then 4^3-block super-cells)
@@ -266,6 +268,19 @@ __device__ __forceinline__ uint32_t pack_col8(float r, float g, float b, float w
   const uint32_t G = (uint32_t)fminf(fmaxf(rintf(g), 0.f), 255.f);
   const uint32_t B = (uint32_t)fminf(fmaxf(rintf(b), 0.f), 255.f);
   return R | (G << 8) | (B << 16) | (col_weight_encode(w) << 24);
+}
+
+// Combined colour: r, g, b in [0, 255] as round(c * 257) in 16 bits, and a defined flag.
+__device__ __forceinline__ uint2 pack_comb_col(float r, float g, float b, bool defined) {
+  const uint32_t qr = (uint32_t)__float2uint_rn(fminf(fmaxf(r, 0.f), 255.f) * 257.f);
+  const uint32_t qg = (uint32_t)__float2uint_rn(fminf(fmaxf(g, 0.f), 255.f) * 257.f);
+  const uint32_t qb = (uint32_t)__float2uint_rn(fminf(fmaxf(b, 0.f), 255.f) * 257.f);
+  return make_uint2(qr | (qg << 16), qb | (defined ? 0x10000u : 0u));
+}
+__device__ __forceinline__ float4 unpack_comb_col(uint2 v) {
+  const float s = 1.0f / 257.0f;
+  return make_float4((float)(v.x & 0xFFFFu) * s, (float)(v.x >> 16) * s, (float)(v.y & 0xFFFFu) * s,
+                     (v.y >> 16) ? 1.0f : 0.0f);
 }
 
 __device__ __forceinline__ float4 unpack_col8(uint32_t v) {

@@ -433,7 +433,7 @@ __device__ __forceinline__ Combined full_comb(const MapView& m, const Cell& c, c
     bool cok = true;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const float4 cv = __ldg(m.comb_col + base + ccoff(q));
+      const float4 cv = unpack_comb_col(__ldg(m.comb_col + base + ccoff(q)));
       cok &= cv.w > 0.0f;
       const float wq = corner_w(q, fx, fy, fz);
       cr += wq * cv.x;

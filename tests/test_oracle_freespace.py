@@ -3,6 +3,7 @@ the same closed forms and the same Lemma 1 property as the direct render."""
 import numpy as np
 import pytest
 
+import angles
 import oracle
 import scenes
 
@@ -30,9 +31,10 @@ def test_plane_render_is_exact():
     inner = np.zeros_like(hit)
     inner[6:-6, 6:-6] = True
     sel = hit & inner
-    assert np.abs(d[sel] - ex.depth[sel]).max() < 2e-6
-    ang = np.arccos(np.clip(np.sum(n[sel] * ex.normals[sel], -1), -1, 1))
-    assert ang.max() < 1e-4
+    # the float32 depth input bounds it (test_oracle_render.test_plane_render_is_exact)
+    assert np.abs(d[sel] - ex.depth[sel]).max() < 5e-7
+    ang = angles.between(n[sel], ex.normals[sel])
+    assert ang.max() < 2e-5
 
 
 def _tiny():
