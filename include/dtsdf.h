@@ -127,10 +127,13 @@ DTSDF_API dtsdf_status dtsdf_integrate_dev(dtsdf_map map, const dtsdf_frame* fra
 /* Ray-cast depth, normals and colour at pose T_wc with intrinsics K (Sec. 4): per pixel,
  * march the combined SDF of Eq. combine_weight (fallback Eq. combine_tsdf_weight) along
  * the ray from z_min to z_max, find the first positive-to-negative crossing between
- * consecutive samples of the h/2 grid and refine it. A pre-pass records per tile of 32 rays
- * the depth range of the allocated blocks in view, and each ray marches only that range
- * (outside it no sample can be defined). Asynchronous; the pre-pass scratch (8 bytes per ray
- * tile) is stream-ordered memory from a pool the map keeps cached. */
+ * consecutive samples of the h/2 grid and refine it by 16 bisection steps on the sign of the
+ * continuous combined SDF (an undefined point counts as free space): the depth is the final
+ * bracket's midpoint, normal and colour are taken at its non-positive end. A pre-pass records
+ * per tile of 32 rays the depth range of the allocated blocks in view, and each ray marches
+ * only that range (outside it no sample can be defined). Asynchronous; the scratch (8 bytes per
+ * ray tile for the pre-pass, 8 bytes per ray for the crossings the march hands to the
+ * refinement) is stream-ordered memory from a pool the map keeps cached. */
 DTSDF_API dtsdf_status dtsdf_render(dtsdf_map map, const dtsdf_intrinsics* K, const double T_wc[16],
                           const dtsdf_render_out* out, void* stream);
 

@@ -36,8 +36,9 @@ constexpr unsigned long long EMPTY_KEY = ~0ull;
 constexpr int MAX_PROBE = 256;  // linear-probe bound; the table is kept at most half full
 constexpr int SLOT_MASK = 6;    // dir_slots[d * 8 + 6]: bitmask of allocated directions
 // Bisection steps that refine a crossing bracket of h/2 (Sec. 4: small steps after the regular
-// probing) before the final linear interpolation: h / 2^17 (38 nm at 5 mm voxels), about the
-// single-precision spacing of ray parameters of a metre.
+// probing) to h / 2^17 (38 nm at 5 mm voxels), about the single-precision spacing of ray
+// parameters of a metre. The direct render takes the final bracket's midpoint as the root, the
+// free-space render the linear root of the final bracket (its bisection keeps Phi's values).
 constexpr int REFINE_HALVINGS = 16;
 
 // error flags (MapView::counters[C_ERR])
