@@ -539,7 +539,7 @@ __device__ void push_borders(const MapView& m, int b, int bx, int by, int bz, in
 }
 
 template <int STORE>
-__global__ void __launch_bounds__(256) k_fuse(MapView m, FuseFrame f) {
+__global__ void __launch_bounds__(128, 16) k_fuse(MapView m, FuseFrame f) {
   const uint32_t nb = min(*((volatile uint32_t*)(m.counters + C_POOL)), m.pool_cap);
   if (f.Tdev) f.T = pose_from_device(f.Tdev);
   const float h = m.h;
@@ -1005,14 +1005,27 @@ void launch_fuse(const MapView& m, const Intr& K, const Pose32& T, const double*
   set(3, 0.f, -K.fy, (float)K.H - 0.5f - K.cy);
   const bool sparse = m.dense_dim <= 0;
   // fusion: CTAs of 128 threads (4 voxels each), so that twice as many bricks are in flight per
-  // SM as with 256 (each brick's update is a chain of dependent gathers and barriers)
+  // SM as with 256 (each brick's update is a chain of dependent gathers and barriers), with a
+  // register budget for 16 of them per SM (32 registers, a few spilled bytes); the grid-stride
+  // loop runs as one wave of the CTAs that fit on the device at once (a grid of 16 per SM at 48
+  // registers, 10 of them resident, ran its last 6 as a second, under-filled wave)
+  auto fuse_grid = [&](auto kern) {
+    static thread_local int cached_dev = -1, per_sm = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != cached_dev) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0) != cudaSuccess || per_sm < 1) per_sm = 8;
+      cached_dev = dev;
+    }
+    return num_sms * per_sm;
+  };
   if (m.storage == DTSDF_STORE_FP16) {
     if (sparse) k_apron_pull<DTSDF_STORE_FP16><<<num_sms * 4, 256, 0, s>>>(m, 0);
-    k_fuse<DTSDF_STORE_FP16><<<num_sms * 16, 128, 0, s>>>(m, f);
+    k_fuse<DTSDF_STORE_FP16><<<fuse_grid(k_fuse<DTSDF_STORE_FP16>), 128, 0, s>>>(m, f);
     k_bounds_exact<DTSDF_STORE_FP16><<<num_sms * 8, 256, 0, s>>>(m);
   } else {
     if (sparse) k_apron_pull<DTSDF_STORE_FP32><<<num_sms * 4, 256, 0, s>>>(m, 0);
-    k_fuse<DTSDF_STORE_FP32><<<num_sms * 16, 128, 0, s>>>(m, f);
+    k_fuse<DTSDF_STORE_FP32><<<fuse_grid(k_fuse<DTSDF_STORE_FP32>), 128, 0, s>>>(m, f);
     k_bounds_exact<DTSDF_STORE_FP32><<<num_sms * 8, 256, 0, s>>>(m);
   }
 }
