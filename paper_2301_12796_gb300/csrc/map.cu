@@ -704,12 +704,26 @@ __global__ void __launch_bounds__(256) k_apron_pull(MapView m, int all) {
   }
 }
 
-// Exact bounds of the bricks whose bound region changed this frame (stamped by fusion).
+// Exact bounds of the bricks whose bound region changed this frame (stamped by fusion): one warp
+// per brick (23 voxels of [0, 8]^3 per lane, a shuffle reduction), without CTA barriers.
 template <int STORE>
 __global__ void __launch_bounds__(256) k_bounds_exact(MapView m) {
   const uint32_t nb = min(*((volatile uint32_t*)(m.counters + C_POOL)), m.pool_cap);
-  for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x)
-    if (m.stamp[b] == m.frame && m.brick_dir[b] >= 0) exact_bound<STORE>(m, b);
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < nb; b += warps) {
+    if (!(m.stamp[b] == m.frame && m.brick_dir[b] >= 0)) continue;  // uniform over the warp
+    const size_t base = (size_t)b * PVOX;
+    float mn = INFINITY;
+    for (int vi = lane; vi < 729; vi += 32) {
+      const int x = vi % 9, y = (vi / 9) % 9, z = vi / 81;
+      const float2 g = load_geom<STORE>(m, base + pad_index(x, y, z));
+      if (g.y > 0.0f) mn = fminf(mn, g.x);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    if (lane == 0) m.bound[b] = mn;
+  }
 }
 
 // ------------------------------------------------------------------ import
