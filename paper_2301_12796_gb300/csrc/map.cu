@@ -18,15 +18,18 @@
 #include <string.h>
 
 #include "internal.h"
+#include "dsfloat.cuh"
 
 namespace dtsdf {
 
 // ------------------------------------------------------------ preprocessing
 // Depth outlier filter: a depth in [z_min, z_max] survives if at least two of its eight
 // neighbours are in range and within delta_sup of it. Survivors are back-projected with
-// Eq. reprojection: P = (z (u - cx)/fx, z (v - cy)/fy, z). P.w = 1 marks a survivor.
-__global__ void k_filter(const float* __restrict__ depth, Intr K, float zmin, float zmax, float dsup,
-                         float4* __restrict__ P) {
+// Eq. reprojection: P = (z (u - cx)/fx, z (v - cy)/fy, z). P.w = 1 marks a survivor. The
+// back-projection runs in double-single arithmetic (u - cx exact, then times 1/fx and z, about
+// 48 bits) and is rounded once. ifx, ify: 1/fx, 1/fy split into two floats.
+__global__ void k_filter(const float* __restrict__ depth, Intr K, float zmin, float zmax, float dsup, dsf ifx,
+                         dsf ify, float4* __restrict__ P) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = blockIdx.y * blockDim.y + threadIdx.y;
   if (u >= K.W || v >= K.H) return;
@@ -45,10 +48,9 @@ __global__ void k_filter(const float* __restrict__ depth, Intr K, float zmin, fl
         if (fabsf(rsub(zn, z)) <= dsup) ++support;
       }
     if (support >= 2) {
-      // Eq. reprojection in double precision, rounded once
-      const double zd = z;
-      out = make_float4((float)(zd * (((double)u - (double)K.cx) / (double)K.fx)),
-                        (float)(zd * (((double)v - (double)K.cy) / (double)K.fy)), z, 1.0f);
+      const dsf x = ds_mul_f(ds_mul(ds_two_sum((float)u, -K.cx), ifx), z);
+      const dsf y = ds_mul_f(ds_mul(ds_two_sum((float)v, -K.cy), ify), z);
+      out = make_float4(ds_to_float(x), ds_to_float(y), z, 1.0f);
     }
   }
   P[i] = out;
@@ -58,9 +60,11 @@ __global__ void k_filter(const float* __restrict__ depth, Intr K, float zmin, fl
 // neighbours (Sec. 7), normalised and turned toward the camera. N.w = 1 marks a normal. The
 // cross product of nearby points cancels most of their digits (at grazing incidence a single-
 // precision normal is off by up to ~5e-4 rad), so the points are re-formed from the exact input
-// depths and the normal computed in double precision, then rounded once; it feeds the direction
-// membership and the band tests of allocation and fusion. ifx, ify: 1/fx, 1/fy in double.
-__global__ void k_normals(const float4* __restrict__ P, Intr K, double ifx, double ify, float4* __restrict__ N) {
+// depths and the normal computed in double-single arithmetic (about 48 bits), then rounded once;
+// it feeds the direction membership and the band tests of allocation and fusion. The
+// orientation is decided on the unnormalised double-single normal: n . P has the sign of
+// n . (a, b, 1) since z > 0. ifx, ify: 1/fx, 1/fy split into two floats.
+__global__ void k_normals(const float4* __restrict__ P, Intr K, dsf ifx, dsf ify, float4* __restrict__ N) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = blockIdx.y * blockDim.y + threadIdx.y;
   if (u >= K.W || v >= K.H) return;
@@ -69,27 +73,27 @@ __global__ void k_normals(const float4* __restrict__ P, Intr K, double ifx, doub
   if (u >= 1 && v >= 1 && u < K.W - 1 && v < K.H - 1) {
     const float4 c = P[i], l = P[i - 1], r = P[i + 1], t = P[i - K.W], b = P[i + K.W];
     if (c.w > 0 && l.w > 0 && r.w > 0 && t.w > 0 && b.w > 0) {
-      const double cx = K.cx, cy = K.cy;
-      const double am = ((double)(u - 1) - cx) * ifx, a0 = ((double)u - cx) * ifx, ap = ((double)(u + 1) - cx) * ifx;
-      const double bm = ((double)(v - 1) - cy) * ify, b0 = ((double)v - cy) * ify, bp = ((double)(v + 1) - cy) * ify;
-      const double zl = l.z, zr = r.z, zt = t.z, zb = b.z, zc = c.z;
-      const double dx0 = zr * ap - zl * am, dx1 = zr * b0 - zl * b0, dx2 = zr - zl;
-      const double dy0 = zb * a0 - zt * a0, dy1 = zb * bp - zt * bm, dy2 = zb - zt;
-      double n0 = dx1 * dy2 - dx2 * dy1;
-      double n1 = dx2 * dy0 - dx0 * dy2;
-      double n2 = dx0 * dy1 - dx1 * dy0;
-      const double len = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
-      if (len > 0.0) {
-        const double il = 1.0 / len;
-        n0 *= il;
-        n1 *= il;
-        n2 *= il;
-        if (n0 * (zc * a0) + n1 * (zc * b0) + n2 * zc > 0.0) {
-          n0 = -n0;
-          n1 = -n1;
-          n2 = -n2;
-        }
-        out = make_float4((float)n0, (float)n1, (float)n2, 1.0f);
+      // ray slopes (u - cx)/fx and (v - cy)/fy of the centre and its four neighbours
+      const dsf am = ds_mul(ds_two_sum((float)(u - 1), -K.cx), ifx);
+      const dsf a0 = ds_mul(ds_two_sum((float)u, -K.cx), ifx);
+      const dsf ap = ds_mul(ds_two_sum((float)(u + 1), -K.cx), ifx);
+      const dsf bm = ds_mul(ds_two_sum((float)(v - 1), -K.cy), ify);
+      const dsf b0 = ds_mul(ds_two_sum((float)v, -K.cy), ify);
+      const dsf bp = ds_mul(ds_two_sum((float)(v + 1), -K.cy), ify);
+      // central differences P(u+1) - P(u-1) and P(v+1) - P(v-1)
+      const dsf dx2 = ds_two_sum(r.z, -l.z), dy2 = ds_two_sum(b.z, -t.z);
+      const dsf dx0 = ds_sub(ds_mul_f(ap, r.z), ds_mul_f(am, l.z)), dx1 = ds_mul(dx2, b0);
+      const dsf dy0 = ds_mul(dy2, a0), dy1 = ds_sub(ds_mul_f(bp, b.z), ds_mul_f(bm, t.z));
+      dsf n0 = ds_sub(ds_mul(dx1, dy2), ds_mul(dx2, dy1));
+      dsf n1 = ds_sub(ds_mul(dx2, dy0), ds_mul(dx0, dy2));
+      dsf n2 = ds_sub(ds_mul(dx0, dy1), ds_mul(dx1, dy0));
+      const dsf len = ds_sqrt(ds_add(ds_add(ds_mul(n0, n0), ds_mul(n1, n1)), ds_mul(n2, n2)));
+      if (len.hi > 0.0f) {
+        const dsf il = ds_recip(len);
+        const dsf facing = ds_add(ds_add(ds_mul(n0, a0), ds_mul(n1, b0)), n2);
+        const float sg = facing.hi > 0.0f ? -1.0f : 1.0f;
+        out = make_float4(sg * ds_to_float(ds_mul(n0, il)), sg * ds_to_float(ds_mul(n1, il)),
+                          sg * ds_to_float(ds_mul(n2, il)), 1.0f);
       }
     }
   }
@@ -855,17 +859,18 @@ void launch_preprocess(const float* depth, const Intr& K, float zmin, float zmax
                        cudaStream_t s, const FilterOpts* f, float4* tmp) {
   dim3 blk(32, 8), grd((K.W + 31) / 32, (K.H + 7) / 8);
   const bool fd = f && f->depth_radius > 0 && tmp, fn = f && f->normal_radius > 0 && tmp;
+  const dsf ifx = ds_from_double(1.0 / (double)K.fx), ify = ds_from_double(1.0 / (double)K.fy);
   if (fd) {
-    k_filter<<<grd, blk, 0, s>>>(depth, K, zmin, zmax, dsup, tmp);
+    k_filter<<<grd, blk, 0, s>>>(depth, K, zmin, zmax, dsup, ifx, ify, tmp);
     k_bilateral_depth<<<grd, blk, 0, s>>>(tmp, K, f->depth_radius, f->depth_sigma_d, f->depth_sigma_r, P);
   } else {
-    k_filter<<<grd, blk, 0, s>>>(depth, K, zmin, zmax, dsup, P);
+    k_filter<<<grd, blk, 0, s>>>(depth, K, zmin, zmax, dsup, ifx, ify, P);
   }
   if (fn) {
-    k_normals<<<grd, blk, 0, s>>>(P, K, 1.0 / (double)K.fx, 1.0 / (double)K.fy, tmp);
+    k_normals<<<grd, blk, 0, s>>>(P, K, ifx, ify, tmp);
     k_bilateral_normals<<<grd, blk, 0, s>>>(tmp, K, f->normal_radius, f->normal_sigma_d, f->normal_sigma_r, N);
   } else {
-    k_normals<<<grd, blk, 0, s>>>(P, K, 1.0 / (double)K.fx, 1.0 / (double)K.fy, N);
+    k_normals<<<grd, blk, 0, s>>>(P, K, ifx, ify, N);
   }
 }
 
