@@ -98,7 +98,9 @@ typedef struct {
   int64_t bricks_per_dir[6];
   int64_t capacity;        /* max_blocks */
   uint32_t error_flags;    /* bit 0: pool full, bit 1: directory full, bit 2: hash probe limit,
-                              bit 3: allocation work list full */
+                              bit 3: allocation work list full, bit 4: a bounded device wait
+                              of the combine pass ran out (that pass stopped early; the next
+                              dtsdf_integrate returns DTSDF_ERR_TIMEOUT) */
   int32_t frames;          /* frames integrated */
 } dtsdf_map_stats_t;
 

@@ -300,10 +300,12 @@ dtsdf_status dtsdf_create(const dtsdf_params* params, void* stream, dtsdf_map* o
   ALLOC(v.dir_slots, sizeof(int32_t) * 8 * (size_t)v.dir_cap);
   ALLOC(v.dir_coord, sizeof(int32_t) * 4 * (size_t)v.dir_cap);
   if (p.storage == DTSDF_STORE_FP16) {
-    ALLOC(v.geom16, sizeof(uint32_t) * PVOX * (size_t)bricks);
+    // 16 bytes of slack: a bulk copy of a padded brick starts at the 16-byte boundary at or below
+    // the brick and ends at one above it (combined.cu)
+    ALLOC(v.geom16, sizeof(uint32_t) * PVOX * (size_t)bricks + 16);
     if (p.color) ALLOC(v.col8, sizeof(uint32_t) * BVOX * (size_t)bricks);
   } else {
-    ALLOC(v.geom, sizeof(float2) * PVOX * (size_t)bricks);
+    ALLOC(v.geom, sizeof(float2) * PVOX * (size_t)bricks + 16);
     if (p.color) ALLOC(v.col, sizeof(float4) * BVOX * (size_t)bricks);
   }
   ALLOC(v.brick_dir, sizeof(int32_t) * (size_t)bricks);
@@ -409,6 +411,7 @@ static dtsdf_status integrate_impl(dtsdf_map m, const dtsdf_frame* f, const doub
     m->err_pending = false;
     if (*m->err_host & (ERR_POOL_FULL | ERR_DIR_FULL | ERR_HASH_FULL | ERR_WORK_FULL))
       return fail(DTSDF_ERR_MAP_FULL, "map capacity exhausted (max_blocks)");
+    if (*m->err_host & ERR_TIMEOUT) return fail(DTSDF_ERR_TIMEOUT, "a bounded device wait ran out (combine pass)");
   }
   const Intr K = to_intr(f->K);
   const size_t npix = (size_t)K.W * K.H;

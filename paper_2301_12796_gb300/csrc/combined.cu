@@ -19,18 +19,13 @@
 namespace dtsdf {
 
 // Eq. direction_weight as read; the clamped ranges (angle <= pi/2 - theta: 1, >= theta: 0)
-// are decided on the cosine (cos_hi = sin theta, cos_lo = cos theta) without the arc cosine.
-__device__ __forceinline__ float w_dir_c(float c, float theta, float cos_lo, float cos_hi) {
+// are decided on the cosine (cos_hi = sin theta, cos_lo = cos theta) without the arc cosine;
+// inv_span = 1 / (2 theta - pi/2).
+__device__ __forceinline__ float w_dir_c(float c, float theta, float cos_lo, float cos_hi, float inv_span) {
   if (c >= cos_hi) return 1.0f;
   if (c <= cos_lo) return 0.0f;
   const float alpha = acosf(c);
-  return fminf(fmaxf((theta - alpha) / (2.0f * theta - 1.57079632679489662f), 0.0f), 1.0f);
-}
-
-template <int STORE>
-__device__ __forceinline__ float2 src_geom(const MapView& m, size_t i) {
-  if (STORE == DTSDF_STORE_FP16) return unpack_geom16(__ldg(m.geom16 + i));
-  return __ldg(m.geom + i);
+  return fminf(fmaxf((theta - alpha) * inv_span, 0.0f), 1.0f);
 }
 
 // Conditional combination (Sec. 4): recombine while fewer than 5 frames were rendered, after
@@ -78,21 +73,171 @@ __device__ __forceinline__ void comb_sources(const MapView& m, uint32_t d, int j
   for (int D = 0; D < ND; ++D) src[D][j] = ((mask >> D) & 1u) ? m.dir_slots[(size_t)dd * 8 + D] : -1;
 }
 
-// Register budget for 8 resident CTAs per SM (32 registers, a few spilled bytes): the pass is
-// bound by the latency of its dependent reads, and more warps in flight beat fewer spills
-// (forced whole-frustum pass on the 300-frame Kinect map: 1.00 ms at 5 CTAs per SM, 0.93 ms at
-// 6, 0.86 ms at 8). The CTA walks its blocks with the bricks of the next block looked up (hash
-// probes of its 7 neighbours) by 8 threads of its last warp while the others combine the
-// current one.
-constexpr int COMB_PREFETCH_T0 = 224;  // threads 224..231: 2 voxels each instead of 3
+// ---- the block cache (Sec. 7: a block's bricks are held in shared memory while it is combined).
+// A stage is one (block, direction): the block's padded geometry brick of that direction and its
+// colour brick, fetched by two bulk copies (cp.async.bulk) that complete on the stage's "full"
+// mbarrier. One producer warp walks the blocks, looks up each block's upper neighbours and issues
+// the copies into a ring of COMB_NS stage buffers; the consumer warps combine the stages in order
+// and free each buffer on its "empty" mbarrier. No CTA-wide barrier couples the two sides, so the
+// producer's hash probes and the copies of the next stages overlap the combination.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// orders the CTA's earlier generic-proxy accesses of shared memory before later bulk copies into it
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> shared bulk copy: both addresses 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Waits for the completion of the barrier's phase of the given parity (the current phase or the
+// one before it); gives up after 2^31 clock cycles (about a second) and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity))
+    if (clock64() - t0 > (1ll << 31)) return false;
+  return true;
+}
+
+// Element types of the source bricks per storage form, and the size of one stage buffer.
+template <int STORE>
+struct CombSrc {
+  using G = float2;  // (sdf, weight)
+  using C = float4;  // (r, g, b, colour weight)
+};
+template <>
+struct CombSrc<DTSDF_STORE_FP16> {
+  using G = uint32_t;  // half sdf | half-coded weight
+  using C = uint32_t;  // u8 r, g, b | log colour-weight code
+};
+template <int STORE, bool COLOR>
+struct CombLayout {
+  static constexpr uint32_t GBYTES = (uint32_t)sizeof(typename CombSrc<STORE>::G) * PVOX;
+  // a padded brick copied from the 16-byte boundary at or below it: at most GBYTES + 15 bytes,
+  // rounded up to 16
+  static constexpr uint32_t GBUF = (GBYTES + 30) / 16 * 16;
+  static constexpr uint32_t CBUF = COLOR ? (uint32_t)sizeof(typename CombSrc<STORE>::C) * BVOX : 0u;
+  static constexpr uint32_t STAGE = GBUF + CBUF;
+};
+__device__ __forceinline__ float2 geom_val(float2 v) { return v; }
+__device__ __forceinline__ float2 geom_val(uint32_t v) { return unpack_geom16(v); }
+__device__ __forceinline__ float4 col_val(float4 v) { return v; }
+__device__ __forceinline__ float4 col_val(uint32_t v) { return unpack_col8(v); }
+
+// Running sums of one voxel's combination.
+struct CombAcc {
+  float ws, acc;  // sum of w^D, sum of w^D phi^D (Eq. combine_weight)
+  float wf, af;   // fallback weights of Eq. combine_tsdf_weight and their weighted sum
+  float cw, cr, cg, cb;
+  bool any;       // some direction has weight at the voxel
+};
+
+// Contribution of direction D at one voxel: v(o) is the (sdf, weight) at offset o (in padded-brick
+// elements) from the voxel, col() its colour; r is the unit view ray to the voxel.
+template <bool COLOR, typename GF, typename CF>
+__device__ __forceinline__ void comb_dir(CombAcc& a, int D, const GF& v, const CF& col, float r0, float r1, float r2,
+                                         float inv2h, float theta, float cos_lo, float cos_hi, float inv_span) {
+  const float2 v0 = v(0);
+  if (!(v0.y > 0.0f)) return;
+  a.any = true;
+  const float vr = (D & 1) ? ((D >> 1) == 0 ? r0 : (D >> 1) == 1 ? r1 : r2)
+                           : -((D >> 1) == 0 ? r0 : (D >> 1) == 1 ? r1 : r2);
+  const float w_f = v0.y * fmaxf(vr, 0.0f);
+  if (w_f > 0.0f) {
+    a.wf += w_f;
+    a.af += w_f * v0.x;
+  }
+  const float2 xp = v(1), xm = v(-1), yp = v(PAD), ym = v(-PAD), zp = v(PAD * PAD), zm = v(-PAD * PAD);
+  if (!(xp.y > 0.f && xm.y > 0.f && yp.y > 0.f && ym.y > 0.f && zp.y > 0.f && zm.y > 0.f)) return;
+  const float g0 = (xp.x - xm.x) * inv2h, g1 = (yp.x - ym.x) * inv2h, g2 = (zp.x - zm.x) * inv2h;
+  const float gg = g0 * g0 + g1 * g1 + g2 * g2;
+  if (!(gg > 1e-24f)) return;  // |g| > 1e-12
+  const float ig = rsqrtf(gg);
+  const float n0 = g0 * ig, n1 = g1 * ig, n2 = g2 * ig;
+  const float facing = -(n0 * r0 + n1 * r1 + n2 * r2);
+  if (!(facing > 0.0f)) return;  // the weight of Eq. combine_weight vanishes
+  const float cosv = (D == 0) ? n0 : (D == 1) ? -n0 : (D == 2) ? n1 : (D == 3) ? -n1 : (D == 4) ? n2 : -n2;
+  const float wc = w_dir_c(cosv, theta, cos_lo, cos_hi, inv_span) * facing * v0.y;
+  if (!(wc > 0.0f)) return;
+  a.ws += wc;
+  a.acc += wc * v0.x;
+  if (COLOR) {
+    const float4 c = col();
+    if (c.w > 0.0f) {
+      a.cw += wc;
+      a.cr += wc * c.x;
+      a.cg += wc * c.y;
+      a.cb += wc * c.z;
+    }
+  }
+}
+
+// A stage as the producer hands it to the consumers.
+struct CombStageDesc {
+  int d;       // directory index of the block
+  int D;       // direction, -1: none (a block without stages, whose voxels are all undefined)
+  int slot;    // the block's brick of D, staged in the buffer; -1: only upper neighbours have D
+  int flags;   // COMB_FIRST | COMB_LAST | COMB_END
+  int bc[3];   // block coordinates
+  int src[8];  // brick of D of the blocks {0, 1}^3 from this one (j = x | y << 1 | z << 2), -1: none
+};
+enum { COMB_FIRST = 1, COMB_LAST = 2, COMB_END = 4 };
+
+// One CTA combines one block at a time, the resident CTAs walking the directory. A block's stages
+// are its directions D = 0..5 that it has (staged: every voxel of [0, 8]^3 whose own block has D
+// reads its 7 stencil values from the staged padded brick, whose apron mirrors the upper
+// neighbours' voxels at local 8 and 9; the colour of a voxel of [0, 7]^3 from the staged colour
+// brick, of the upper layer from its own block's colour brick), and the directions only upper
+// neighbours have (combined at the upper layer's voxels from those blocks' bricks in global
+// memory). Every voxel sums its directions in the order D = 0..5.
+#ifndef DTSDF_COMB_CWARPS
+#define DTSDF_COMB_CWARPS 23
+#endif
+constexpr int COMB_CWARPS = DTSDF_COMB_CWARPS;       // consumer warps
+constexpr int COMB_CT = 32 * COMB_CWARPS;            // consumer threads
+constexpr int COMB_T = COMB_CT + 32;                 // + the producer warp
+constexpr int COMB_VPT = (CVOX + COMB_CT - 1) / COMB_CT;  // voxels per consumer thread
+#ifndef DTSDF_COMB_STAGES
+#define DTSDF_COMB_STAGES 5  // stage buffers in the ring
+#endif
+#ifndef DTSDF_COMB_MINB
+#define DTSDF_COMB_MINB 2    // resident CTAs per SM the register allocation is sized for
+#endif
+constexpr int COMB_NS = DTSDF_COMB_STAGES;
 
 template <int STORE, bool COLOR>
-__global__ void __launch_bounds__(256, 8) k_combine(MapView m, const CombState* st, CombFrame f) {
-  __shared__ int s_src[2][ND][8];
+__global__ void __launch_bounds__(COMB_T, DTSDF_COMB_MINB) k_combine(MapView m, const CombState* st, CombFrame f) {
+  using G = typename CombSrc<STORE>::G;
+  using C = typename CombSrc<STORE>::C;
+  using L = CombLayout<STORE, COLOR>;
+  extern __shared__ __align__(128) unsigned char s_buf[];  // COMB_NS x L::STAGE bytes
+  __shared__ __align__(8) uint64_t s_fullbar[COMB_NS], s_emptybar[COMB_NS];
+  __shared__ CombStageDesc s_desc[COMB_NS];
   __shared__ float s_c[3];
   __shared__ float s_R[9];
   __shared__ uint32_t s_full, s_gen, s_from;
-  if (threadIdx.x == 0) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
     s_full = st->full;
     s_gen = st->gen;
     s_from = st->pool_from;
@@ -100,122 +245,270 @@ __global__ void __launch_bounds__(256, 8) k_combine(MapView m, const CombState* 
       s_c[a] = (float)st->pose[4 * a + 3];
       for (int b = 0; b < 3; ++b) s_R[3 * a + b] = (float)st->pose[4 * a + b];
     }
+    for (int q = 0; q < COMB_NS; ++q) {
+      mbar_init(&s_fullbar[q], 1);
+      mbar_init(&s_emptybar[q], COMB_CWARPS);
+    }
+    mbar_init_fence();
   }
-  __syncthreads();
+  __syncthreads();  // the last CTA-wide barrier: from here on the two sides meet on mbarriers only
+  const G* gpool = reinterpret_cast<const G*>(STORE == DTSDF_STORE_FP16 ? (const void*)m.geom16 : (const void*)m.geom);
+  const C* cpool = reinterpret_cast<const C*>(STORE == DTSDF_STORE_FP16 ? (const void*)m.col8 : (const void*)m.col);
   const uint32_t ndir = min(*((volatile uint32_t*)(m.counters + C_DIR)), m.dir_cap);
   const float h = m.h;
-  const float cos_lo = m.costh, cos_hi = m.sinth;
-  // the next block from d on (stride gridDim.x) that this pass combines (ndir if none); uniform
-  auto next_taken = [&](uint32_t d) -> uint32_t {
-    for (; d < ndir; d += gridDim.x) {
-      const uint32_t mask = (uint32_t)m.dir_slots[(size_t)d * 8 + SLOT_MASK];
-      bool take = mask != 0;
-      if (take && !s_full) {  // incremental: blocks with a brick allocated since the last combination
-        bool fresh = false;
-        for (uint32_t mm = mask; mm; mm &= mm - 1)
-          fresh |= (uint32_t)m.dir_slots[(size_t)d * 8 + __ffs(mm) - 1] >= s_from;
-        take = fresh;
-      }
-      if (!take) continue;
-      // padded frustum of the combination pose: bounding sphere of the block against the four
-      // side planes (image grown by 1/8) and the camera's half-space
-      const int bx = m.dir_coord[4 * d], by = m.dir_coord[4 * d + 1], bz = m.dir_coord[4 * d + 2];
-      const float rad = 0.8660254f * 8.0f * h + h;
-      const float p0 = m.ox + (8.0f * bx + 3.5f) * h - s_c[0];
-      const float p1 = m.oy + (8.0f * by + 3.5f) * h - s_c[1];
-      const float p2 = m.oz + (8.0f * bz + 3.5f) * h - s_c[2];
-      const float cx = s_R[0] * p0 + s_R[3] * p1 + s_R[6] * p2;
-      const float cy = s_R[1] * p0 + s_R[4] * p1 + s_R[7] * p2;
-      const float cz = s_R[2] * p0 + s_R[5] * p1 + s_R[8] * p2;
-      take = cz > -rad;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) take &= (f.pl[q][0] * cx + f.pl[q][1] * cy + f.pl[q][2] * cz) >= -rad;
-      if (take) return d;
-    }
-    return ndir;
-  };
-  const int pj = (int)threadIdx.x - COMB_PREFETCH_T0;  // 0..7 on the prefetching threads
-  uint32_t d = next_taken(blockIdx.x);
-  if (d < ndir && pj >= 0 && pj < 8) comb_sources(m, d, pj, s_src[0]);
-  __syncthreads();
-  int cb = 0;
-  while (d < ndir) {
-    const uint32_t dn = next_taken(d + gridDim.x);
-    if (dn < ndir && pj >= 0 && pj < 8) comb_sources(m, dn, pj, s_src[cb ^ 1]);
-    const int bx = m.dir_coord[4 * d], by = m.dir_coord[4 * d + 1], bz = m.dir_coord[4 * d + 2];
-    int (*src)[8] = s_src[cb];
-    const float inv2h = 0.5f / h;
-    for (int vi = threadIdx.x; vi < CVOX; vi += blockDim.x) {
-      const int x = vi % CEDGE, y = (vi / CEDGE) % CEDGE, z = vi / (CEDGE * CEDGE);
-      float r0 = m.ox + (float)(8 * bx + x) * h - s_c[0];
-      float r1 = m.oy + (float)(8 * by + y) * h - s_c[1];
-      float r2 = m.oz + (float)(8 * bz + z) * h - s_c[2];
-      const float rinv = 1.0f / sqrtf(r0 * r0 + r1 * r1 + r2 * r2);
-      r0 *= rinv;
-      r1 *= rinv;
-      r2 *= rinv;
-      float ws = 0.f, acc = 0.f, wf = 0.f, af = 0.f, cw = 0.f, cr = 0.f, cg = 0.f, cb = 0.f;
-      bool any = false;
-#pragma unroll 1
-      const int own = (x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2);
-      for (int D = 0; D < ND; ++D) {
-        const int sl = src[D][own];
-        if (sl < 0) continue;
-        const size_t base = (size_t)sl * PVOX + pad_index(x & 7, y & 7, z & 7);
-        const float2 v0 = src_geom<STORE>(m, base);
-        if (!(v0.y > 0.0f)) continue;
-        any = true;
-        const float vr = (D & 1) ? ((D >> 1) == 0 ? r0 : (D >> 1) == 1 ? r1 : r2)
-                                 : -((D >> 1) == 0 ? r0 : (D >> 1) == 1 ? r1 : r2);
-        const float w_f = v0.y * fmaxf(vr, 0.0f);
-        if (w_f > 0.0f) {
-          wf += w_f;
-          af += w_f * v0.x;
+
+  if (warp == COMB_CWARPS) {
+    // ------------------------------------------------------------------ producer warp
+    // the next block from d on (stride gridDim.x) that this pass combines (ndir if none)
+    auto next_taken = [&](uint32_t d) -> uint32_t {
+      for (; d < ndir; d += gridDim.x) {
+        const uint32_t mask = (uint32_t)m.dir_slots[(size_t)d * 8 + SLOT_MASK];
+        bool take = mask != 0;
+        if (take && !s_full) {  // incremental: blocks with a brick allocated since the last combination
+          bool fresh = false;
+          for (uint32_t mm = mask; mm; mm &= mm - 1)
+            fresh |= (uint32_t)m.dir_slots[(size_t)d * 8 + __ffs(mm) - 1] >= s_from;
+          take = fresh;
         }
-        const float2 xp = src_geom<STORE>(m, base + 1), xm = src_geom<STORE>(m, base - 1);
-        const float2 yp = src_geom<STORE>(m, base + PAD), ym = src_geom<STORE>(m, base - PAD);
-        const float2 zp = src_geom<STORE>(m, base + PAD * PAD), zm = src_geom<STORE>(m, base - PAD * PAD);
-        if (!(xp.y > 0.f && xm.y > 0.f && yp.y > 0.f && ym.y > 0.f && zp.y > 0.f && zm.y > 0.f)) continue;
-        const float g0 = (xp.x - xm.x) * inv2h, g1 = (yp.x - ym.x) * inv2h, g2 = (zp.x - zm.x) * inv2h;
-        const float gn = sqrtf(g0 * g0 + g1 * g1 + g2 * g2);
-        if (!(gn > 1e-12f)) continue;
-        const float n0 = g0 / gn, n1 = g1 / gn, n2 = g2 / gn;
-        const float facing = -(n0 * r0 + n1 * r1 + n2 * r2);
-        if (!(facing > 0.0f)) continue;  // the weight of Eq. combine_weight vanishes
-        const float cosv = (D == 0) ? n0 : (D == 1) ? -n0 : (D == 2) ? n1 : (D == 3) ? -n1 : (D == 4) ? n2 : -n2;
-        const float wc = w_dir_c(cosv, m.theta, cos_lo, cos_hi) * facing * v0.y;
-        if (!(wc > 0.0f)) continue;
-        ws += wc;
-        acc += wc * v0.x;
-        if (COLOR) {
-          {
-            const size_t ci = (size_t)sl * BVOX + ((z & 7) * 8 + (y & 7)) * 8 + (x & 7);
-            const float4 c = STORE == DTSDF_STORE_FP16 ? unpack_col8(__ldg(m.col8 + ci)) : __ldg(m.col + ci);
-            if (c.w > 0.0f) {
-              cw += wc;
-              cr += wc * c.x;
-              cg += wc * c.y;
-              cb += wc * c.z;
-            }
+        if (!take) continue;
+        // padded frustum of the combination pose: bounding sphere of the block against the four
+        // side planes (image grown by 1/8) and the camera's half-space
+        const int bx = m.dir_coord[4 * d], by = m.dir_coord[4 * d + 1], bz = m.dir_coord[4 * d + 2];
+        const float rad = 0.8660254f * 8.0f * h + h;
+        const float p0 = m.ox + (8.0f * bx + 3.5f) * h - s_c[0];
+        const float p1 = m.oy + (8.0f * by + 3.5f) * h - s_c[1];
+        const float p2 = m.oz + (8.0f * bz + 3.5f) * h - s_c[2];
+        const float cx = s_R[0] * p0 + s_R[3] * p1 + s_R[6] * p2;
+        const float cy = s_R[1] * p0 + s_R[4] * p1 + s_R[7] * p2;
+        const float cz = s_R[2] * p0 + s_R[5] * p1 + s_R[8] * p2;
+        take = cz > -rad;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) take &= (f.pl[q][0] * cx + f.pl[q][1] * cy + f.pl[q][2] * cz) >= -rad;
+        if (take) return d;
+      }
+      return ndir;
+    };
+    int q = 0;
+    uint32_t pe = (1u << COMB_NS) - 1u;  // parity to wait for per empty barrier: a fresh ring is free
+    uint32_t issued = 0u, pfull = 0u;    // slots that received copies; parity of each slot's last use
+    bool fail = false;
+    uint32_t d = next_taken(blockIdx.x);
+    for (;;) {
+      const bool end = d >= ndir;
+      int bc[3] = {0, 0, 0};
+      int bsl[ND];  // lanes 0..7: bricks of block j = lane of {0, 1}^3 from this one
+#pragma unroll
+      for (int D = 0; D < ND; ++D) bsl[D] = -1;
+      uint32_t todo;
+      if (!end) {
+        bc[0] = m.dir_coord[4 * d];
+        bc[1] = m.dir_coord[4 * d + 1];
+        bc[2] = m.dir_coord[4 * d + 2];
+        if (lane < 8) {
+          const int dd = lane == 0 ? (int)d : hash_find(m, bc[0] + (lane & 1), bc[1] + ((lane >> 1) & 1), bc[2] + (lane >> 2));
+          const uint32_t mask = dd >= 0 ? (uint32_t)m.dir_slots[(size_t)dd * 8 + SLOT_MASK] : 0u;
+#pragma unroll
+          for (int D = 0; D < ND; ++D) bsl[D] = ((mask >> D) & 1u) ? m.dir_slots[(size_t)dd * 8 + D] : -1;
+        }
+        todo = 0u;
+#pragma unroll
+        for (int D = 0; D < ND; ++D) {
+          const bool own = __shfl_sync(0xffffffffu, bsl[D], 0) >= 0;
+          const bool up = __ballot_sync(0xffffffffu, lane >= 1 && lane < 8 && bsl[D] >= 0) != 0u;
+          if (own || up) todo |= 1u << D;
+        }
+        if (!todo) todo = 1u << ND;  // no stage: one empty stage writes the block's undefined voxels
+      } else {
+        todo = 1u << 7;  // the end marker
+      }
+      bool first = true;
+      while (todo) {
+        const int bit = __ffs(todo) - 1;
+        todo &= todo - 1;
+        bool ok = true;
+        if (lane == 0) ok = mbar_wait_bounded(&s_emptybar[q], (pe >> q) & 1u);
+        if (!__shfl_sync(0xffffffffu, (int)ok, 0)) {
+          fail = true;
+          break;
+        }
+        pe ^= 1u << q;
+        const int D = bit < ND ? bit : -1;
+        int mine = -1;
+#pragma unroll
+        for (int E = 0; E < ND; ++E)
+          if (E == D) mine = bsl[E];
+        int src[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) src[j] = __shfl_sync(0xffffffffu, mine, j);
+        if (lane == 0) {
+          CombStageDesc& sd = s_desc[q];
+          const int slot = D >= 0 ? src[0] : -1;
+          sd.d = (int)d;
+          sd.D = D;
+          sd.slot = slot;
+          sd.flags = (first ? COMB_FIRST : 0) | (todo == 0u ? COMB_LAST : 0) | (end ? COMB_END : 0);
+          sd.bc[0] = bc[0];
+          sd.bc[1] = bc[1];
+          sd.bc[2] = bc[2];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) sd.src[j] = src[j];
+          if (slot >= 0) {
+            const uintptr_t a = reinterpret_cast<uintptr_t>(gpool + (size_t)slot * PVOX);
+            const uintptr_t a16 = a & ~(uintptr_t)15;
+            const uint32_t gb = (uint32_t)((a - a16 + L::GBYTES + 15) & ~(uintptr_t)15);
+            unsigned char* buf = s_buf + (size_t)q * L::STAGE;
+            fence_proxy_async_smem();
+            mbar_arrive_expect(&s_fullbar[q], gb + L::CBUF);
+            bulk_g2s(buf, (const void*)a16, gb, &s_fullbar[q]);
+            if (COLOR) bulk_g2s(buf + L::GBUF, cpool + (size_t)slot * BVOX, L::CBUF, &s_fullbar[q]);
+          } else {
+            mbar_arrive(&s_fullbar[q]);
           }
         }
+        __syncwarp();
+        issued |= 1u << q;
+        pfull ^= 1u << q;
+        first = false;
+        q = q + 1 == COMB_NS ? 0 : q + 1;
       }
-      float2 out = make_float2(0.f, 0.f);
-      uint2 oc = make_uint2(0u, 0u);
-      if (any && ws > 0.0f) {
-        out = make_float2(acc / ws, 1.0f);
-        if (COLOR && cw > 0.0f) oc = pack_comb_col(cr / cw, cg / cw, cb / cw, true);
-      } else if (any && wf > 0.0f) {
-        out = make_float2(af / wf, 1.0f);
-      }
-      m.comb[(size_t)d * CVOX + vi] = out;
-      if (COLOR) m.comb_col[(size_t)d * CVOX + vi] = oc;
+      if (end || fail) break;
+      d = next_taken(d + gridDim.x);
     }
-    if (threadIdx.x == 0) m.comb_gen[d] = s_gen;
-    __syncthreads();  // the next block's sources are in place; this block's may be overwritten
-    cb ^= 1;
-    d = dn;
+    if (fail) {
+      // the consumers stopped: flag it and let this warp's copies in flight land before leaving
+      if (lane == 0) {
+        atomicOr(m.counters + C_ERR, ERR_TIMEOUT);
+        for (int s = 0; s < COMB_NS; ++s)
+          if ((issued >> s) & 1u) mbar_wait_bounded(&s_fullbar[s], ((pfull >> s) & 1u) ^ 1u);
+      }
+    }
+    return;
   }
+
+  // -------------------------------------------------------------------- consumer warps
+  const float inv2h = 0.5f / h;
+  const float theta = m.theta, cos_lo = m.costh, cos_hi = m.sinth;
+  const float inv_span = 1.0f / (2.0f * theta - 1.57079632679489662f);
+  // this thread's voxels of [0, 8]^3: vi = tid + i COMB_CT, packed as x | y << 4 | z << 8 (-1 if
+  // none), and their stage indices: padded-brick index p | owner block j << 11 | index ci of the
+  // voxel in its owner's brick << 14
+  int vx[COMB_VPT], vp[COMB_VPT];
+#pragma unroll
+  for (int i = 0; i < COMB_VPT; ++i) {
+    const int vi = tid + i * COMB_CT;
+    const int x = vi % CEDGE, y = (vi / CEDGE) % CEDGE, z = vi / (CEDGE * CEDGE);
+    vx[i] = vi < CVOX ? x | (y << 4) | (z << 8) : -1;
+    vp[i] = pad_index(x, y, z) | (((x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2)) << 11) |
+            ((((z & 7) * 8 + (y & 7)) * 8 + (x & 7)) << 14);
+  }
+  CombAcc A[COMB_VPT];
+  float ray[COMB_VPT][3];
+  int q = 0;
+  uint32_t pf = 0u;  // parity to wait for per full barrier
+  for (;;) {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&s_fullbar[q], (pf >> q) & 1u));
+    if (!ok) {
+      if (lane == 0) atomicOr(m.counters + C_ERR, ERR_TIMEOUT);
+      return;
+    }
+    pf ^= 1u << q;
+    const CombStageDesc& sd = s_desc[q];
+    const int flags = sd.flags;
+    if (flags & COMB_END) break;
+    const int d = sd.d, D = sd.D, slot = sd.slot;
+    if (flags & COMB_FIRST) {
+      const int bx = sd.bc[0], by = sd.bc[1], bz = sd.bc[2];
+#pragma unroll
+      for (int i = 0; i < COMB_VPT; ++i) {
+        A[i].ws = A[i].acc = A[i].wf = A[i].af = A[i].cw = A[i].cr = A[i].cg = A[i].cb = 0.f;
+        A[i].any = false;
+        const int x = vx[i] & 15, y = (vx[i] >> 4) & 15, z = (vx[i] >> 8) & 15;
+        float r0 = m.ox + (float)(8 * bx + x) * h - s_c[0];
+        float r1 = m.oy + (float)(8 * by + y) * h - s_c[1];
+        float r2 = m.oz + (float)(8 * bz + z) * h - s_c[2];
+        const float rinv = 1.0f / sqrtf(r0 * r0 + r1 * r1 + r2 * r2);
+        ray[i][0] = r0 * rinv;
+        ray[i][1] = r1 * rinv;
+        ray[i][2] = r2 * rinv;
+      }
+    }
+    if (D >= 0 && slot >= 0) {
+      const uint32_t off = (uint32_t)((reinterpret_cast<uintptr_t>(gpool + (size_t)slot * PVOX) & 15) / sizeof(G));
+      const unsigned char* buf = s_buf + (size_t)q * L::STAGE;
+      const G* sg = reinterpret_cast<const G*>(buf) + off;
+      const C* sc = reinterpret_cast<const C*>(buf + L::GBUF);
+#pragma unroll
+      for (int i = 0; i < COMB_VPT; ++i) {
+        if (vx[i] < 0) continue;
+        const int p = vp[i] & 2047, j = (vp[i] >> 11) & 7, ci = vp[i] >> 14;
+        const int osl = sd.src[j];  // the brick of D of the voxel's own block
+        if (osl < 0) continue;
+        comb_dir<COLOR>(
+            A[i], D, [&](int o) { return geom_val(sg[p + o]); },
+            [&]() { return col_val(j == 0 ? sc[ci] : __ldg(cpool + (size_t)osl * BVOX + ci)); }, ray[i][0],
+            ray[i][1], ray[i][2], inv2h, theta, cos_lo, cos_hi, inv_span);
+      }
+    } else if (D >= 0) {
+      // only upper neighbours have D: their voxels on this block's upper layer, from their bricks
+#pragma unroll
+      for (int i = 0; i < COMB_VPT; ++i) {
+        if (vx[i] < 0) continue;
+        const int x = vx[i] & 15, y = (vx[i] >> 4) & 15, z = (vx[i] >> 8) & 15;
+        const int j = (x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2);
+        const int osl = j ? sd.src[j] : -1;
+        if (osl < 0) continue;
+        const G* gb = gpool + (size_t)osl * PVOX + pad_index(x & 7, y & 7, z & 7);
+        const int ci = ((z & 7) * 8 + (y & 7)) * 8 + (x & 7);
+        comb_dir<COLOR>(
+            A[i], D, [&](int o) { return geom_val(__ldg(gb + o)); },
+            [&]() { return col_val(__ldg(cpool + (size_t)osl * BVOX + ci)); }, ray[i][0], ray[i][1], ray[i][2], inv2h,
+            theta, cos_lo, cos_hi, inv_span);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&s_emptybar[q]);  // this warp is done with the buffer and the descriptor
+    q = q + 1 == COMB_NS ? 0 : q + 1;
+    if (flags & COMB_LAST) {
+#pragma unroll
+      for (int i = 0; i < COMB_VPT; ++i) {
+        if (vx[i] < 0) continue;
+        const int vi = tid + i * COMB_CT;
+        float2 out = make_float2(0.f, 0.f);
+        uint2 oc = make_uint2(0u, 0u);
+        if (A[i].any && A[i].ws > 0.0f) {
+          out = make_float2(A[i].acc / A[i].ws, 1.0f);
+          if (COLOR && A[i].cw > 0.0f)
+            oc = pack_comb_col(A[i].cr / A[i].cw, A[i].cg / A[i].cw, A[i].cb / A[i].cw, true);
+        } else if (A[i].any && A[i].wf > 0.0f) {
+          out = make_float2(A[i].af / A[i].wf, 1.0f);
+        }
+        m.comb[(size_t)d * CVOX + vi] = out;
+        if (COLOR) m.comb_col[(size_t)d * CVOX + vi] = oc;
+      }
+      if (tid == 0) m.comb_gen[d] = s_gen;
+    }
+  }
+}
+
+template <int STORE, bool COLOR>
+void launch_k_combine(const MapView& m, CombState* st, const CombFrame& f, int num_sms, cudaStream_t s) {
+  auto kern = k_combine<STORE, COLOR>;
+  constexpr size_t smem = (size_t)COMB_NS * CombLayout<STORE, COLOR>::STAGE;
+  // the ring exceeds the default 48 KB of dynamic shared memory: raise the limit once per device
+  static uint64_t opted = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && !((opted >> dev) & 1u)) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess)
+      opted |= 1ull << dev;
+  } else if (dev >= 64) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  // one wave of resident CTAs walks the directory
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, COMB_T, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  kern<<<num_sms * per_sm, COMB_T, smem, s>>>(m, st, f);
 }
 
 void launch_combine(const MapView& m, CombState* st, const Intr& K, const double* Tdev, const double* Thost, int force,
@@ -237,18 +530,12 @@ void launch_combine(const MapView& m, CombState* st, const Intr& K, const double
   set(2, 0.f, K.fy, K.cy + 0.5f + pv);
   set(3, 0.f, -K.fy, (float)K.H - 0.5f + pv - K.cy);
   const bool col = m.color && m.comb_col;
-  // one wave of resident CTAs walks the directory
-  auto go = [&](auto kern) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 4;
-    kern<<<num_sms * per_sm, 256, 0, s>>>(m, st, f);
-  };
   if (m.storage == DTSDF_STORE_FP16) {
-    if (col) go(k_combine<DTSDF_STORE_FP16, true>);
-    else go(k_combine<DTSDF_STORE_FP16, false>);
+    if (col) launch_k_combine<DTSDF_STORE_FP16, true>(m, st, f, num_sms, s);
+    else launch_k_combine<DTSDF_STORE_FP16, false>(m, st, f, num_sms, s);
   } else {
-    if (col) go(k_combine<DTSDF_STORE_FP32, true>);
-    else go(k_combine<DTSDF_STORE_FP32, false>);
+    if (col) launch_k_combine<DTSDF_STORE_FP32, true>(m, st, f, num_sms, s);
+    else launch_k_combine<DTSDF_STORE_FP32, false>(m, st, f, num_sms, s);
   }
 }
 

@@ -46,6 +46,7 @@ constexpr uint32_t ERR_POOL_FULL = 1u;
 constexpr uint32_t ERR_DIR_FULL = 2u;
 constexpr uint32_t ERR_HASH_FULL = 4u;
 constexpr uint32_t ERR_WORK_FULL = 8u;
+constexpr uint32_t ERR_TIMEOUT = 16u;  // a bounded wait of a kernel ran out (the kernel stopped early)
 
 // hash values pack the directory index (26 bits) with the allocated-direction mask (6 bits)
 constexpr uint32_t VAL_EMPTY = 0xFFFFFFFFu;

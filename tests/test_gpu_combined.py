@@ -157,3 +157,37 @@ def test_combined_render_after_recycling_matches_oracle():
     assert n > 5000 and agree >= 0.999
     assert np.mean(derr <= 1e-4) >= 0.999
     assert np.mean(nerr <= 1e-3) >= 0.999
+
+
+@pytest.mark.parametrize("dense", [True, False])
+def test_fp16_combined_render_matches_oracle_on_the_same_values(dense):
+    """FP16 storage form: the combine pass stages half-precision bricks (4-byte voxels, a brick
+    starting 0, 4, 8 or 12 bytes past a 16-byte boundary). The map is fused on the device in FP16,
+    and the oracle is given the map's own (decoded) voxel values, so both combine and ray-cast the
+    same field and the FP32 bars apply. The hash map has blocks whose upper neighbours hold
+    directions the block lacks."""
+    s = scenes.tiny_scene(1)
+    kw = dict(voxel_size=0.01, truncation=0.04, dense_dim=64 if dense else 0, color=True)
+    gm = dt.Map(dt.params(max_blocks=1 << 16, storage=dt.STORE_FP16, **kw))
+    for i in range(10):
+        f = s.frame(i)
+        gm.integrate(torch.from_numpy(f.depth).to(DEV), torch.from_numpy(np.ascontiguousarray(f.rgb)).to(DEV),
+                     s.K, f.pose)
+    torch.cuda.synchronize()
+    coords, vox = gm.export()
+    om = oracle.OracleMap(oracle.Params(**kw))
+    for c, v in zip(coords, vox):
+        om.set_brick(int(c[0]), int(c[1]), int(c[2]), int(c[3]), v.astype(np.float64))
+    for fi in (2, 6):
+        T = s.poses[fi] @ scenes.perturbation(np.random.default_rng(fi), 1.0, 0.005)
+        gm.combined_reset()
+        g = render_comb(gm, s.K, T)
+        om.combine(T[:3, 3])
+        agree, derr, nerr, cerr, n = compare(g, om.render_combined(s.K, T))
+        print(f"fp16 combined dense={dense} fi={fi}: mask {agree:.5f} depth max {derr.max():.2e} "
+              f"normals {np.mean(nerr <= 1e-3):.5f} colour {cerr:.3f}")
+        assert n > 5000
+        assert agree >= 0.999
+        assert np.mean(derr <= 1e-4) >= 0.999 and np.median(derr) < 1e-6
+        assert np.mean(nerr <= 1e-3) >= 0.999
+        assert cerr <= 0.5
