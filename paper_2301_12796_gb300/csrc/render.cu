@@ -113,12 +113,12 @@ __device__ __forceinline__ float tri(const float* v, float fx, float fy, float f
 }
 
 // Eq. direction_weight as read; the clamped ranges (angle <= pi/2 - theta: 1, >= theta: 0) are
-// decided on the cosine (sin theta, cos theta) without the arc cosine.
-__device__ __forceinline__ float w_dir_r(float c, float theta, float cos_lo, float cos_hi) {
+// decided on the cosine (sin theta, cos theta) without the arc cosine; inv_span = 1 / (2 theta - pi/2).
+__device__ __forceinline__ float w_dir_r(float c, float theta, float cos_lo, float cos_hi, float inv_span) {
   if (c >= cos_hi) return 1.0f;
   if (c <= cos_lo) return 0.0f;
   const float alpha = acosf(c);
-  return fminf(fmaxf((theta - alpha) / (2.0f * theta - 1.57079632679489662f), 0.0f), 1.0f);
+  return fminf(fmaxf((theta - alpha) * inv_span, 0.0f), 1.0f);
 }
 
 // component a (0..2) of a 3-vector held in registers, by selects: every index stays in range
@@ -163,6 +163,7 @@ __device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, cons
   float acc = 0.f, facc = 0.f, fw = 0.f;
   bool any = false;
   const float inv2h = 0.5f / m.h;
+  const float inv_span = 1.0f / (2.0f * m.theta - 1.57079632679489662f);
 #pragma unroll 1
   for (uint32_t mm = c.cmask; mm; mm &= mm - 1) {
     const int D = __ffs(mm) - 1;
@@ -214,13 +215,14 @@ __device__ __forceinline__ Combined combine_full(const MapView& m, Cell& c, cons
       gr[a] = tri(dv, fx, fy, fz) * inv2h;
     }
     if (!gok) continue;
-    const float gn = sqrtf(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
-    if (!(gn > 1e-12f)) continue;
-    const float n0 = gr[0] / gn, n1 = gr[1] / gn, n2 = gr[2] / gn;
+    const float gg = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
+    if (!(gg > 1e-24f)) continue;  // |gradient| > 1e-12
+    const float ig = rsqrtf(gg);
+    const float n0 = gr[0] * ig, n1 = gr[1] * ig, n2 = gr[2] * ig;
     const float facing = -(n0 * r[0] + n1 * r[1] + n2 * r[2]);
     if (!(facing > 0.0f)) continue;  // the weight of Eq. combine_weight vanishes
     const float cosv = (D == 0) ? n0 : (D == 1) ? -n0 : (D == 2) ? n1 : (D == 3) ? -n1 : (D == 4) ? n2 : -n2;
-    const float wc = w_dir_r(cosv, m.theta, m.costh, m.sinth) * facing * WD;
+    const float wc = w_dir_r(cosv, m.theta, m.costh, m.sinth, inv_span) * facing * WD;
     if (!(wc > 0.0f)) continue;
     out.wsum += wc;
     acc += wc * phiD;
