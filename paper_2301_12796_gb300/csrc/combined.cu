@@ -12,6 +12,7 @@
 // weight and a colour weight > 0. The result is then ray-cast like a regular TSDF (render.cu,
 // STORE_COMBINED) from any pose near the combination pose.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include "internal.h"
@@ -259,6 +260,7 @@ __global__ void __launch_bounds__(COMB_T, DTSDF_COMB_MINB) k_combine(MapView m, 
 
   if (warp == COMB_CWARPS) {
     // ------------------------------------------------------------------ producer warp
+    if (f.stall) return;  // test hook: no stage is issued
     // the next block from d on (stride gridDim.x) that this pass combines (ndir if none)
     auto next_taken = [&](uint32_t d) -> uint32_t {
       for (; d < ndir; d += gridDim.x) {
@@ -529,6 +531,8 @@ void launch_combine(const MapView& m, CombState* st, const Intr& K, const double
   set(1, -K.fx, 0.f, (float)K.W - 0.5f + pu - K.cx);
   set(2, 0.f, K.fy, K.cy + 0.5f + pv);
   set(3, 0.f, -K.fy, (float)K.H - 0.5f + pv - K.cy);
+  const char* stall = getenv("DTSDF_TEST_COMBINE_STALL");
+  f.stall = stall && *stall && atoi(stall) != 0;
   const bool col = m.color && m.comb_col;
   if (m.storage == DTSDF_STORE_FP16) {
     if (col) launch_k_combine<DTSDF_STORE_FP16, true>(m, st, f, num_sms, s);

@@ -148,6 +148,9 @@ struct Pose64 {
 };
 struct CombFrame {
   float pl[4][3];  // inward unit normals of the padded frustum's side planes (camera frame)
+  // Failure-detection test hook (environment variable DTSDF_TEST_COMBINE_STALL set and not 0):
+  // the combine pass's producer warp issues no stage, so the consumers' bounded waits run out.
+  int stall;
 };
 // Conditional combination and the combine pass for a render at T (device pose, else host).
 void launch_combine(const MapView& m, CombState* st, const Intr& K, const double* Tdev, const double* Thost, int force,

@@ -6,7 +6,9 @@ allocation of a create call (counted from 0) and every later one fail as if the 
 of memory. For every N up to the number of allocations the call makes, dtsdf_create,
 dtsdf_icp_create and dtsdf_server_create must return DTSDF_ERR_OOM and free what they had
 allocated: the library's count of live allocations (dtsdf_live_allocations) is back where it
-was. A server poll whose bounded wait runs out with no result reports DTSDF_ERR_TIMEOUT."""
+was. A server poll whose bounded wait runs out with no result reports DTSDF_ERR_TIMEOUT, and so
+does a map whose combine pass had a bounded device wait run out (test hook
+DTSDF_TEST_COMBINE_STALL: the pass's producer warp issues nothing)."""
 import ctypes
 import os
 
@@ -15,6 +17,7 @@ import pytest
 import torch
 
 import paper_2301_12796_gb300 as dt
+import scenes
 from paper_2301_12796_gb300 import build as B
 
 pytestmark = pytest.mark.gpu
@@ -26,6 +29,7 @@ def built():
     dt.lib()
     yield
     os.environ.pop("DTSDF_FAIL_ALLOC", None)
+    os.environ.pop("DTSDF_TEST_COMBINE_STALL", None)
 
 
 def _walk(create, max_n=64):
@@ -85,3 +89,42 @@ def test_server_create_fails_cleanly_and_bounded_poll_times_out():
     srv.close()
     assert dt.lib().dtsdf_live_allocations() == live
     m.close()
+
+
+def test_combine_wait_that_runs_out_is_reported():
+    """The combine pass's consumer warps wait for each stage on an mbarrier with a bounded wait
+    (2^31 clock cycles). With the producer warp issuing nothing, every such wait runs out (about
+    a second): the pass stops, the map's error flags carry bit 4, and the next dtsdf_integrate
+    that reads the flags back returns DTSDF_ERR_TIMEOUT. The device stays usable."""
+    s = scenes.tiny_scene(1)
+    dev = torch.device("cuda:0")
+    frames = [s.frame(i) for i in range(4)]
+    cu = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    m = dt.Map(dt.params(voxel_size=0.01, truncation=0.04, max_blocks=1 << 14, color=True))
+    m.integrate(cu(frames[0].depth), cu(frames[0].rgb), s.K, frames[0].pose)
+    m.combine(s.K, frames[0].pose, force=True)  # the combined field is allocated by the first call
+    torch.cuda.synchronize()
+    assert m.stats().error_flags == 0
+    os.environ["DTSDF_TEST_COMBINE_STALL"] = "1"
+    try:
+        m.combine(s.K, frames[0].pose, force=True)
+        torch.cuda.synchronize()
+    finally:
+        os.environ.pop("DTSDF_TEST_COMBINE_STALL", None)
+    assert m.stats().error_flags & 16
+    with pytest.raises(dt.DtsdfError) as e:
+        for f in frames[1:]:
+            m.integrate(cu(f.depth), cu(f.rgb), s.K, f.pose)
+            torch.cuda.synchronize()
+    assert e.value.status == dt.ERR_TIMEOUT
+    assert b"bounded device wait" in dt.lib().dtsdf_last_error()
+    m.close()
+    # the device is still usable: a fresh map fuses, combines and renders
+    m2 = dt.Map(dt.params(voxel_size=0.01, truncation=0.04, max_blocks=1 << 14, color=True))
+    m2.integrate(cu(frames[0].depth), cu(frames[0].rgb), s.K, frames[0].pose)
+    d = torch.zeros(s.K.height, s.K.width, device=dev)
+    n = torch.zeros(s.K.height, s.K.width, 4, device=dev)
+    m2.render_combined(s.K, frames[0].pose, d, n)
+    torch.cuda.synchronize()
+    assert m2.stats().error_flags == 0 and (d > 0).float().mean().item() > 0.5
+    m2.close()
