@@ -15,6 +15,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
+
 #include "internal.h"
 
 namespace dtsdf {
@@ -497,14 +499,13 @@ void launch_k_combine(const MapView& m, CombState* st, const CombFrame& f, int n
   auto kern = k_combine<STORE, COLOR>;
   constexpr size_t smem = (size_t)COMB_NS * CombLayout<STORE, COLOR>::STAGE;
   // the ring exceeds the default 48 KB of dynamic shared memory: raise the limit once per device
-  static uint64_t opted = 0;
+  // (callers on several host threads may race here; setting the attribute twice is harmless)
+  static std::atomic<uint64_t> opted{0};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 64 && !((opted >> dev) & 1u)) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess)
-      opted |= 1ull << dev;
-  } else if (dev >= 64) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (dev >= 64 || !((opted.load(std::memory_order_relaxed) >> dev) & 1u)) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess && dev < 64)
+      opted.fetch_or(1ull << dev, std::memory_order_relaxed);
   }
   // one wave of resident CTAs walks the directory
   int per_sm = 0;
