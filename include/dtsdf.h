@@ -153,9 +153,10 @@ DTSDF_API dtsdf_status dtsdf_render_dev(dtsdf_map map, const dtsdf_intrinsics* K
  * frustum is recombined at this pose while fewer than 5 combined renders were made, after more
  * than 50 without recombination, or when the pose moved by more than 0.05 m or turned by more
  * than 0.05 pi/2 since the last combination; otherwise only blocks that received bricks since
- * the previous call are combined (at the last combination pose) and the render uses the stored
- * field. The decision is taken on the device. The first call allocates the combined field:
- * per directory entry 729 voxels x 8 B (+ 16 B with colour). Asynchronous. */
+ * the previous call, and the 26 blocks around each of them, are combined (at the last combination
+ * pose) and the render uses the stored field. The decision is taken on the device. The first call
+ * allocates the combined field: per directory entry 729 voxels x 8 B (+ 729 x 8 B with colour)
+ * and 5 B of state. Asynchronous. */
 DTSDF_API dtsdf_status dtsdf_render_combined(dtsdf_map map, const dtsdf_intrinsics* K, const double T_wc[16],
                                              const dtsdf_render_out* out, void* stream);
 

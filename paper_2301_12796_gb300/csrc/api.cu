@@ -212,6 +212,7 @@ static void map_free(dtsdf_map m) {
   dt_free(m->v.comb);
   dt_free(m->v.comb_col);
   dt_free(m->v.comb_gen);
+  dt_free(m->v.comb_dirty);
   dt_free(m->comb_state);
   delete m;
 }
@@ -517,23 +518,28 @@ static dtsdf_status ensure_combined(dtsdf_map m, cudaStream_t s) {
   float2* comb = nullptr;
   uint2* col = nullptr;
   uint32_t* gen = nullptr;
+  uint8_t* dirty = nullptr;
   CombState* st = nullptr;
   cudaError_t e = dt_malloc((void**)&comb, sizeof(float2) * CVOX * nd);
   if (e == cudaSuccess && m->p.color) e = dt_malloc((void**)&col, sizeof(uint2) * CVOX * nd);
   if (e == cudaSuccess) e = dt_malloc((void**)&gen, sizeof(uint32_t) * nd);
+  if (e == cudaSuccess) e = dt_malloc((void**)&dirty, nd);
   if (e == cudaSuccess) e = dt_malloc((void**)&st, sizeof(CombState));
   if (e == cudaSuccess) e = cudaMemsetAsync(gen, 0xFF, sizeof(uint32_t) * nd, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dirty, 0, nd, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(CombState), s);
   if (e != cudaSuccess) {
     dt_free(comb);
     dt_free(col);
     dt_free(gen);
+    dt_free(dirty);
     dt_free(st);
     return cuda_fail(e, "combined TSDF allocation");
   }
   m->v.comb = comb;
   m->v.comb_col = col;
   m->v.comb_gen = gen;
+  m->v.comb_dirty = dirty;
   m->v.comb_cur = (const uint32_t*)((const char*)st + offsetof(CombState, gen));
   m->comb_state = st;
   return DTSDF_OK;

@@ -34,8 +34,9 @@ __device__ __forceinline__ float w_dir_c(float c, float theta, float cos_lo, flo
 // Conditional combination (Sec. 4): recombine while fewer than 5 frames were rendered, after
 // more than 50 frames without an update, or when the camera moved by more than 0.05 m or
 // turned by more than 0.05 pi/2 since the last combination; otherwise only the blocks that
-// received bricks since then are combined, at the last combination pose. Recycled bricks handed
-// out again keep old pool indices, so a change of the recycled-brick count also recombines all.
+// received bricks since then, and the blocks around them, are combined, at the last combination
+// pose. Recycled bricks handed out again keep old pool indices, so a change of the recycled-brick
+// count also recombines all.
 __global__ void k_comb_policy(CombState* st, const double* Tdev, Pose64 Tv, const uint32_t* counters, int force) {
   double T[16];
   for (int i = 0; i < 16; ++i) T[i] = Tdev ? Tdev[i] : Tv.T[i];
@@ -62,6 +63,27 @@ __global__ void k_comb_policy(CombState* st, const double* Tdev, Pose64 Tv, cons
     for (int i = 0; i < 16; ++i) st->pose[i] = T[i];
   } else {
     st->since += 1;
+  }
+}
+
+// Incremental combination: every block around a block that received bricks since the last call
+// (pool indices [pool_from, pool_mark)) is marked for recombination, since its stored voxels next
+// to that block - the layer the two share at local 8, and the gradient stencils that reach into it -
+// depend on the new bricks. A full combination marks nothing.
+__global__ void k_comb_mark(MapView m, const CombState* st) {
+  if (st->full) return;
+  const uint32_t from = st->pool_from, to = min(st->pool_mark, m.pool_cap);
+  for (uint32_t p = from + blockIdx.x * blockDim.x + threadIdx.x; p < to; p += gridDim.x * blockDim.x) {
+    const int bd = m.brick_dir[p];
+    if (bd < 0) continue;
+    const int d = bd >> 3;
+    const int bx = m.dir_coord[4 * d], by = m.dir_coord[4 * d + 1], bz = m.dir_coord[4 * d + 2];
+#pragma unroll 1
+    for (int q = 0; q < 27; ++q) {
+      if (q == 13) continue;
+      const int dd = hash_find(m, bx + q % 3 - 1, by + (q / 3) % 3 - 1, bz + q / 9 - 1);
+      if (dd >= 0) m.comb_dirty[dd] = 1;
+    }
   }
 }
 
@@ -268,8 +290,10 @@ __global__ void __launch_bounds__(COMB_T, DTSDF_COMB_MINB) k_combine(MapView m, 
       for (; d < ndir; d += gridDim.x) {
         const uint32_t mask = (uint32_t)m.dir_slots[(size_t)d * 8 + SLOT_MASK];
         bool take = mask != 0;
-        if (take && !s_full) {  // incremental: blocks with a brick allocated since the last combination
-          bool fresh = false;
+        if (take && !s_full) {
+          // incremental: blocks with a brick allocated since the last combination, and the blocks
+          // around them (marked by k_comb_mark)
+          bool fresh = m.comb_dirty[d] != 0;
           for (uint32_t mm = mask; mm; mm &= mm - 1)
             fresh |= (uint32_t)m.dir_slots[(size_t)d * 8 + __ffs(mm) - 1] >= s_from;
           take = fresh;
@@ -489,7 +513,10 @@ __global__ void __launch_bounds__(COMB_T, DTSDF_COMB_MINB) k_combine(MapView m, 
         m.comb[(size_t)d * CVOX + vi] = out;
         if (COLOR) m.comb_col[(size_t)d * CVOX + vi] = oc;
       }
-      if (tid == 0) m.comb_gen[d] = s_gen;
+      if (tid == 0) {
+        m.comb_gen[d] = s_gen;
+        m.comb_dirty[d] = 0;
+      }
     }
   }
 }
@@ -519,6 +546,7 @@ void launch_combine(const MapView& m, CombState* st, const Intr& K, const double
   Pose64 Tv;
   for (int i = 0; i < 16; ++i) Tv.T[i] = Thost ? Thost[i] : 0.0;
   k_comb_policy<<<1, 1, 0, s>>>(st, Tdev, Tv, m.counters, force);
+  k_comb_mark<<<num_sms * 2, 256, 0, s>>>(m, st);
   CombFrame f;
   // inward unit normals of the four side planes of the image grown by 1/8 of its size
   const float pu = 0.125f * (float)K.W, pv = 0.125f * (float)K.H;

@@ -176,6 +176,7 @@ struct MapView {
                        // combination of colours rounds to 1/257) and 1 if defined else 0,
                        // colour maps only
   uint32_t* comb_gen;  // per directory entry
+  uint8_t* comb_dirty; // per directory entry: a neighbouring block received bricks since its combination
   const uint32_t* comb_cur;  // device word: the current generation
   uint32_t* occ;       // occupancy filters: 2 x OCC_WORDS words (blocks, then 4^3-block super-cells)
   uint32_t pool_cap;

@@ -191,3 +191,40 @@ def test_fp16_combined_render_matches_oracle_on_the_same_values(dense):
         assert np.mean(derr <= 1e-4) >= 0.999 and np.median(derr) < 1e-6
         assert np.mean(nerr <= 1e-3) >= 0.999
         assert cerr <= 0.5
+
+
+def test_incremental_combination_takes_new_blocks_and_their_neighbours():
+    """Conditional combination with new blocks (Sec. 4): after the boot-up the stored field is
+    reused, and only blocks that received bricks since the last combination are combined, with the
+    26 blocks around each of them, whose stored voxels next to a new block (the layer at local 8
+    a block keeps for its upper neighbours, the gradient stencils reaching into the new block)
+    depend on its bricks. The oracle's hash map is loaded without a slab of blocks, combined at
+    T through the boot-up, then given the slab (nothing else changes): the next combined render at
+    T recombines incrementally and must match the oracle's combination of the whole map at T."""
+    s = scenes.tiny_scene(1)
+    kw = dict(voxel_size=0.01, truncation=0.04, color=True)
+    om = oracle.OracleMap(oracle.Params(**kw))
+    for i in range(10):
+        f = s.frame(i)
+        om.integrate(f.depth, f.rgb, s.K, f.pose)
+    ob = om.bricks()
+    vox = np.stack([om.brick(*b[:4]) for b in ob]).astype(np.float32)
+    slab = ob[:, 0] == int(np.median(ob[:, 0]))
+    assert 100 < slab.sum() < len(ob) - 100
+    gm = dt.Map(dt.params(max_blocks=len(ob) + 64, **kw))
+    gm.import_bricks(ob[~slab, :4], vox[~slab])
+    T = s.poses[5]
+    for _ in range(5):  # boot-up: the whole frustum is combined at T
+        render_comb(gm, s.K, T)
+    gm.import_bricks(ob[slab, :4], vox[slab])
+    blocks_before, _ = gm.combined_blocks()
+    g = render_comb(gm, s.K, T)  # sixth call, same pose: incremental
+    om.combine(T[:3, 3])
+    agree, derr, nerr, cerr, n = compare(g, om.render_combined(s.K, T))
+    print(f"incremental: mask {agree:.5f} depth<=1e-4 {np.mean(derr <= 1e-4):.5f} normals {np.mean(nerr <= 1e-3):.5f} "
+          f"colour {cerr:.3f}, blocks {blocks_before} -> {gm.combined_blocks()[0]}")
+    assert n > 5000
+    assert agree >= 0.999
+    assert np.mean(derr <= 1e-4) >= 0.999 and np.median(derr) < 1e-6
+    assert np.mean(nerr <= 1e-3) >= 0.999
+    assert cerr <= 0.5
