@@ -47,7 +47,7 @@ FALLBACK_HBM_GBS = 6800.0
 # ``bench.py --steps 2 --warmup 3 --no-e2e --no-cpu --no-serve --no-multi``
 # (profiles/k_render_kinect640.md). It belongs to the kernel sources it was taken with: reported
 # only while their hash matches.
-RENDER_TRAFFIC = {"bytes": 232718848 + 4944896 + 200730624 + 6743808, "sources_sha1_16": "6082416bdfe302cd",
+RENDER_TRAFFIC = {"bytes": 232585984 + 5292032 + 199535104 + 6413568, "sources_sha1_16": "f6187b94391ff767",
                   "files": ("render.cu", "common.cuh", "internal.h")}
 
 
