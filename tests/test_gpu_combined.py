@@ -228,3 +228,35 @@ def test_incremental_combination_takes_new_blocks_and_their_neighbours():
     assert np.mean(derr <= 1e-4) >= 0.999 and np.median(derr) < 1e-6
     assert np.mean(nerr <= 1e-3) >= 0.999
     assert cerr <= 0.5
+
+
+def test_fp16_combined_render_full_size_sampled():
+    """The FP16 combine pass at the benchmark's scale: the Kinect-shaped room fused on the device
+    in FP16 from 15 of its frames (tens of thousands of staged bricks, starting at every 4-byte
+    offset from a 16-byte boundary), the oracle given the map's decoded values, both combined at
+    a trajectory pose and compared on every fourth pixel at the FP32 bars."""
+    s = scenes.kinect_room(1)
+    kw = dict(voxel_size=0.005, truncation=0.02, color=True, z_max=s.z_max)
+    gm = dt.Map(dt.params(max_blocks=1 << 18, storage=dt.STORE_FP16, **kw))
+    for i in range(0, 300, 20):
+        f = s.frame(i)
+        gm.integrate(torch.from_numpy(f.depth).to(DEV), torch.from_numpy(np.ascontiguousarray(f.rgb)).to(DEV),
+                     s.K, f.pose)
+    torch.cuda.synchronize()
+    coords, vox = gm.export()
+    assert len(coords) > 20000
+    om = oracle.OracleMap(oracle.Params(**kw))
+    for c, v in zip(coords, vox):
+        om.set_brick(int(c[0]), int(c[1]), int(c[2]), int(c[3]), v.astype(np.float64))
+    K, T = s.K, s.poses[150]
+    g = render_comb(gm, K, T)
+    om.combine(T[:3, 3])
+    vv, uu = np.mgrid[0:K.height:4, 0:K.width:4]
+    pix = np.stack([uu.ravel(), vv.ravel()], 1).astype(np.int32)
+    agree, derr, nerr, cerr, n = compare(g, om.render_combined(K, T, pix), pix)
+    print(f"fp16 combined full size: {len(coords)} bricks, mask {agree:.5f} depth<=1e-4 {np.mean(derr <= 1e-4):.5f} "
+          f"normals {np.mean(nerr <= 1e-3):.5f} colour {cerr:.3f}")
+    assert n > 10000 and agree >= 0.999
+    assert np.mean(derr <= 1e-4) >= 0.999
+    assert np.mean(nerr <= 1e-3) >= 0.999
+    assert cerr <= 0.5
