@@ -316,7 +316,7 @@ __device__ bool icp_solve_update_warp(const double* sum, int dsolve, double* pos
       ok = false;
       break;
     }
-    const double ljj = sqrt(s), inv = 1.0 / ljj;
+    const double inv = rsqrt(s), ljj = s * inv;  // one FP64 chain for the pivot and its reciprocal
     __syncwarp();
     if (lane == j) {
       sL[j][j] = ljj;
@@ -376,7 +376,8 @@ __device__ bool icp_solve_update_warp(const double* sum, int dsolve, double* pos
   const double th = sqrt(xi[3] * xi[3] + xi[4] * xi[4] + xi[5] * xi[5]);
   const double sg = D == 7 ? xi[6] : 0.0;
   double fs = 0.0, fc = 1.0, fe = 1.0, fm = 0.0;
-  if (lane == 1) sincos(th, &fs, &fc);
+  // sin and cos are used only beyond the series range of exp_sim3_warp (th >= 1e-4)
+  if (lane == 1 && !(th < 1e-4)) sincos(th, &fs, &fc);
   if (D == 7 && lane == 3) fe = exp(sg);
   if (D == 7 && lane == 4) fm = expm1(sg);
   const double s_th = __shfl_sync(FULL, fs, 1), c_th = __shfl_sync(FULL, fc, 1);
