@@ -117,8 +117,10 @@ DTSDF_API dtsdf_status dtsdf_destroy(dtsdf_map map);
  * of Eq. angular_threshold, then the weighted running average of Eq. point-to-plane with
  * the weights of Eq. combined_fusion_weight and Eq. color_weight, and free-space carving.
  * Asynchronous. Pool exhaustion sets an error flag reported by dtsdf_map_stats and by the
- * next dtsdf_integrate call (DTSDF_ERR_MAP_FULL). The first call with a new frame size
- * allocates scratch memory. */
+ * next dtsdf_integrate call (DTSDF_ERR_MAP_FULL); so does a bounded device wait of the combine
+ * pass that ran out (DTSDF_ERR_TIMEOUT). Flags are read back without stalling the stream, so
+ * they surface one or two calls after the launch that set them. The first call with a new frame
+ * size allocates scratch memory. */
 DTSDF_API dtsdf_status dtsdf_integrate(dtsdf_map map, const dtsdf_frame* frame, const double T_wc[16], void* stream);
 
 /* Same as dtsdf_integrate with the pose read from device memory (16 doubles, row-major),
